@@ -1,0 +1,849 @@
+// Plain FP64 CPU oracle of the differentiable radio ray tracer.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct reference
+// against which the CUDA library is checked.  Only the tests, the smoke check and
+// the CPU-baseline leg of the benchmark load it; the product path never does.  It
+// shares no code, header, table or helper with the CUDA library.
+//
+// Every step follows the paper "Learning Radio Environments by Differentiable Ray
+// Tracing" (Hoydis et al., arXiv 2311.18558) in its own order and notation:
+//   * path tracing: candidate primitives by shooting-and-bouncing rays, then exact
+//     specular chains by the image method (Sec. II-F);
+//   * transfer function of a path: basis changes D_j (Eq. rel1 / basis_transform),
+//     scattering maps F_j (Eq. rel2, Eq. init, Eq. specular_reflection), Fresnel
+//     coefficients (Eq. fresnel-1/2), complex permittivity eta (Sec. II-D);
+//   * path coefficient a_i and delay tau_i (Eq. cfr_cont, Eq. transfer_function);
+//   * CFR H[n] = H(f + n df), n = -N/2 .. N/2-1 (Sec. II-A).
+// Readings where the paper is silent (spreading factor, reflection basis vectors,
+// Fibonacci launch, hit rules, duplicate rule) are stated where they are used.
+//
+// Nothing here is blocked, fused or reordered for speed beyond one OpenMP loop
+// over independent rays or receivers.
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <set>
+#include <vector>
+
+typedef std::complex<double> cplx;
+
+static const double kC0 = 299792458.0;          // speed of light [m/s] (CODATA)
+static const double kEps0 = 8.8541878128e-12;   // vacuum permittivity [F/m] (CODATA)
+static const double kPi = 3.14159265358979323846;
+
+struct Vec3 {
+    double x, y, z;
+};
+static inline Vec3 v3(double x, double y, double z) { return Vec3{x, y, z}; }
+static inline Vec3 operator+(Vec3 a, Vec3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+static inline Vec3 operator-(Vec3 a, Vec3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+static inline Vec3 operator*(double s, Vec3 a) { return v3(s * a.x, s * a.y, s * a.z); }
+static inline double dot(Vec3 a, Vec3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static inline Vec3 cross(Vec3 a, Vec3 b) {
+    return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static inline double norm(Vec3 a) { return std::sqrt(dot(a, a)); }
+static inline Vec3 unit(Vec3 a) { return (1.0 / norm(a)) * a; }
+static inline double comp(Vec3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+// ---------------------------------------------------------------------------
+// Scene: triangles, their planes, and a median-split BVH used only to speed up
+// the closest-hit and any-hit queries.  The BVH never changes a result: every
+// query is also available by brute force over all triangles, and the tests check
+// that both give the identical answer.
+
+struct Box {
+    Vec3 lo, hi;
+};
+
+struct Node {
+    Box box;
+    int left, right;   // children, -1 for a leaf
+    int first, count;  // leaf range in `order`
+};
+
+struct Scene {
+    int T;
+    std::vector<Vec3> a, b, c;   // triangle vertices
+    std::vector<Vec3> n;         // unit geometric normal (b-a)x(c-a)
+    double diag;                 // diagonal of the scene's bounding box
+    std::vector<Node> nodes;
+    std::vector<int> order;
+};
+
+static Box tri_box(const Scene& s, int t) {
+    Box bx;
+    bx.lo = v3(std::min({s.a[t].x, s.b[t].x, s.c[t].x}), std::min({s.a[t].y, s.b[t].y, s.c[t].y}),
+               std::min({s.a[t].z, s.b[t].z, s.c[t].z}));
+    bx.hi = v3(std::max({s.a[t].x, s.b[t].x, s.c[t].x}), std::max({s.a[t].y, s.b[t].y, s.c[t].y}),
+               std::max({s.a[t].z, s.b[t].z, s.c[t].z}));
+    return bx;
+}
+
+static int build_node(Scene& s, int first, int count) {
+    Node nd;
+    nd.box = tri_box(s, s.order[first]);
+    for (int i = first + 1; i < first + count; ++i) {
+        Box b = tri_box(s, s.order[i]);
+        nd.box.lo = v3(std::min(nd.box.lo.x, b.lo.x), std::min(nd.box.lo.y, b.lo.y), std::min(nd.box.lo.z, b.lo.z));
+        nd.box.hi = v3(std::max(nd.box.hi.x, b.hi.x), std::max(nd.box.hi.y, b.hi.y), std::max(nd.box.hi.z, b.hi.z));
+    }
+    // Pad the box so that rounding in the slab test can never prune a triangle
+    // lying on the box boundary.
+    double pad = 1e-9 * s.diag;
+    nd.box.lo = nd.box.lo - v3(pad, pad, pad);
+    nd.box.hi = nd.box.hi + v3(pad, pad, pad);
+    nd.left = nd.right = -1;
+    nd.first = first;
+    nd.count = count;
+    int id = (int)s.nodes.size();
+    s.nodes.push_back(nd);
+    if (count <= 4) return id;
+    Vec3 ext = nd.box.hi - nd.box.lo;
+    int axis = (ext.x >= ext.y && ext.x >= ext.z) ? 0 : (ext.y >= ext.z ? 1 : 2);
+    std::vector<int>::iterator beg = s.order.begin() + first;
+    std::sort(beg, beg + count, [&](int p, int q) {
+        double cp = comp(s.a[p] + s.b[p] + s.c[p], axis), cq = comp(s.a[q] + s.b[q] + s.c[q], axis);
+        return cp < cq || (cp == cq && p < q);
+    });
+    int half = count / 2;
+    int l = build_node(s, first, half);
+    int r = build_node(s, first + half, count - half);
+    s.nodes[id].left = l;
+    s.nodes[id].right = r;
+    return id;
+}
+
+// Slab test: does the ray o + t d, t in [tmin, tmax], touch the box?
+static bool box_hit(const Box& bx, Vec3 o, Vec3 d, double tmin, double tmax) {
+    double t0 = tmin, t1 = tmax;
+    for (int k = 0; k < 3; ++k) {
+        double ok = comp(o, k), dk = comp(d, k), lo = comp(bx.lo, k), hi = comp(bx.hi, k);
+        if (dk == 0.0) {
+            if (ok < lo || ok > hi) return false;
+            continue;
+        }
+        double ta = (lo - ok) / dk, tb = (hi - ok) / dk;
+        if (ta > tb) std::swap(ta, tb);
+        t0 = std::max(t0, ta);
+        t1 = std::min(t1, tb);
+        if (t0 > t1) return false;
+    }
+    return true;
+}
+
+// Watertight ray/triangle intersection (Woop, Benthin and Wald, "Watertight
+// Ray/Triangle Intersection", JCGT 2013), evaluated in FP64.  Edges and vertices
+// count as hits (closed triangle).  Returns the ray parameter t or -1 for a miss.
+static double tri_hit(const Scene& s, int t, Vec3 o, Vec3 d) {
+    double dd[3] = {d.x, d.y, d.z};
+    int kz = 0;
+    if (std::fabs(dd[1]) > std::fabs(dd[kz])) kz = 1;
+    if (std::fabs(dd[2]) > std::fabs(dd[kz])) kz = 2;
+    int kx = (kz + 1) % 3, ky = (kx + 1) % 3;
+    if (dd[kz] < 0.0) std::swap(kx, ky);
+    double Sx = dd[kx] / dd[kz], Sy = dd[ky] / dd[kz], Sz = 1.0 / dd[kz];
+    Vec3 A = s.a[t] - o, B = s.b[t] - o, C = s.c[t] - o;
+    double Ax = comp(A, kx) - Sx * comp(A, kz), Ay = comp(A, ky) - Sy * comp(A, kz);
+    double Bx = comp(B, kx) - Sx * comp(B, kz), By = comp(B, ky) - Sy * comp(B, kz);
+    double Cx = comp(C, kx) - Sx * comp(C, kz), Cy = comp(C, ky) - Sy * comp(C, kz);
+    double U = Cx * By - Cy * Bx;
+    double V = Ax * Cy - Ay * Cx;
+    double W = Bx * Ay - By * Ax;
+    if ((U < 0.0 || V < 0.0 || W < 0.0) && (U > 0.0 || V > 0.0 || W > 0.0)) return -1.0;
+    double det = U + V + W;
+    if (det == 0.0) return -1.0;
+    double Az = Sz * comp(A, kz), Bz = Sz * comp(B, kz), Cz = Sz * comp(C, kz);
+    double T = U * Az + V * Bz + W * Cz;
+    return T / det;
+}
+
+// Closest hit with t > tmin, skipping triangle `skip`.  Exact ties in t go to the
+// lower triangle index.  Returns the triangle index or -1.
+static int closest_hit(const Scene& s, Vec3 o, Vec3 d, double tmin, int skip, bool use_bvh, double* t_out) {
+    int best = -1;
+    double bt = INFINITY;
+    if (!use_bvh) {
+        for (int t = 0; t < s.T; ++t) {
+            if (t == skip) continue;
+            double th = tri_hit(s, t, o, d);
+            if (th > tmin && (th < bt || (th == bt && t < best))) {
+                bt = th;
+                best = t;
+            }
+        }
+    } else {
+        std::vector<int> stack;
+        stack.push_back(0);
+        while (!stack.empty()) {
+            int ni = stack.back();
+            stack.pop_back();
+            const Node& nd = s.nodes[ni];
+            if (!box_hit(nd.box, o, d, tmin, bt)) continue;
+            if (nd.left < 0) {
+                for (int i = nd.first; i < nd.first + nd.count; ++i) {
+                    int t = s.order[i];
+                    if (t == skip) continue;
+                    double th = tri_hit(s, t, o, d);
+                    if (th > tmin && (th < bt || (th == bt && t < best))) {
+                        bt = th;
+                        best = t;
+                    }
+                }
+            } else {
+                stack.push_back(nd.left);
+                stack.push_back(nd.right);
+            }
+        }
+    }
+    *t_out = bt;
+    return best;
+}
+
+// Any hit with tmin < t < tmax, skipping triangles skip0 and skip1.
+static bool any_hit(const Scene& s, Vec3 o, Vec3 d, double tmin, double tmax, int skip0, int skip1) {
+    std::vector<int> stack;
+    stack.push_back(0);
+    while (!stack.empty()) {
+        int ni = stack.back();
+        stack.pop_back();
+        const Node& nd = s.nodes[ni];
+        if (!box_hit(nd.box, o, d, tmin, tmax)) continue;
+        if (nd.left < 0) {
+            for (int i = nd.first; i < nd.first + nd.count; ++i) {
+                int t = s.order[i];
+                if (t == skip0 || t == skip1) continue;
+                double th = tri_hit(s, t, o, d);
+                if (th > tmin && th < tmax) return true;
+            }
+        } else {
+            stack.push_back(nd.left);
+            stack.push_back(nd.right);
+        }
+    }
+    return false;
+}
+
+// Closed point-in-triangle test for a point on (or numerically next to) the
+// triangle's plane: all three edge functions, measured along the normal, >= 0.
+static bool point_in_tri(const Scene& s, int t, Vec3 p) {
+    Vec3 nn = cross(s.b[t] - s.a[t], s.c[t] - s.a[t]);
+    double e0 = dot(nn, cross(s.b[t] - s.a[t], p - s.a[t]));
+    double e1 = dot(nn, cross(s.c[t] - s.b[t], p - s.b[t]));
+    double e2 = dot(nn, cross(s.a[t] - s.c[t], p - s.c[t]));
+    return e0 >= 0.0 && e1 >= 0.0 && e2 >= 0.0;
+}
+
+static bool coplanar(const Scene& s, int t, int u) {
+    if (t == u) return true;
+    Vec3 cr = cross(s.n[t], s.n[u]);
+    if (norm(cr) > 1e-9) return false;
+    double dt = dot(s.n[t], s.a[t]);
+    double du = dot(s.n[t], s.a[u]);
+    return std::fabs(dt - du) <= 1e-9 * s.diag;
+}
+
+// ---------------------------------------------------------------------------
+// Fibonacci-sphere launch directions (the paper does not print its launch
+// pattern).  Reading: the Fibonacci lattice on the sphere (Gonzalez 2010),
+// z_i = 1 - (2i+1)/N, r_i = sqrt(1 - z_i^2), phi_i = 2 pi frac(i (sqrt5 - 1)/2),
+// evaluated in FP64 and rounded to FP32; the FP32 values are the canonical rays.
+static void fibonacci_dir(int64_t i, int64_t N, float out[3]) {
+    double g = (std::sqrt(5.0) - 1.0) / 2.0;
+    double z = 1.0 - (2.0 * (double)i + 1.0) / (double)N;
+    double r = std::sqrt(std::max(0.0, 1.0 - z * z));
+    double x = (double)i * g;
+    double phi = 2.0 * kPi * (x - std::floor(x));
+    out[0] = (float)(r * std::cos(phi));
+    out[1] = (float)(r * std::sin(phi));
+    out[2] = (float)z;
+}
+
+// One SBR ray: up to D specular bounces (reflected direction k_r = k_i - 2(k_i.n)n,
+// Sec. II-D), each leaving triangle excluded from the next closest-hit query.
+// Writes the triangle sequence (-1 after the ray escapes) and returns #hits.
+static int sbr_ray(const Scene& s, Vec3 tx, Vec3 dir, int D, double tmin, bool use_bvh, int* seq) {
+    Vec3 o = tx, d = dir;
+    int prev = -1, hits = 0;
+    for (int b = 0; b < D; ++b) seq[b] = -1;
+    for (int b = 0; b < D; ++b) {
+        double th;
+        int t = closest_hit(s, o, d, tmin, prev, use_bvh, &th);
+        if (t < 0) break;
+        seq[b] = t;
+        hits++;
+        Vec3 p = o + th * d;
+        Vec3 nn = s.n[t];
+        d = d - (2.0 * dot(d, nn)) * nn;
+        o = p;
+        prev = t;
+    }
+    return hits;
+}
+
+// ---------------------------------------------------------------------------
+// Image method (Sec. II-F): for a candidate sequence (t_1..t_q) and a receiver,
+// mirror the transmitter successively in the planes of t_1..t_q, then trace back
+// from the receiver towards the images; each back-traced segment must cross the
+// plane strictly between its end points (0 < u < 1) and the crossing must lie in
+// the closed triangle.  Then every segment s_j -> s_{j+1} must be free of other
+// triangles for t in (eps, len - eps), the end triangles excluded.
+// Returns true and fills pts (q+2 points: Tx, s_1..s_q, Rx) if the path is valid.
+static bool image_path(const Scene& s, Vec3 tx, Vec3 rx, const int* seq, int q, double eps, Vec3* pts,
+                       bool* on_edge) {
+    std::vector<Vec3> img(q + 1);
+    img[0] = tx;
+    for (int j = 1; j <= q; ++j) {
+        int t = seq[j - 1];
+        Vec3 nn = s.n[t];
+        img[j] = img[j - 1] - (2.0 * dot(img[j - 1] - s.a[t], nn)) * nn;
+    }
+    pts[0] = tx;
+    pts[q + 1] = rx;
+    for (int j = q; j >= 1; --j) {
+        int t = seq[j - 1];
+        Vec3 nn = s.n[t];
+        Vec3 from = pts[j + 1];
+        Vec3 dir = img[j] - from;
+        double den = dot(nn, dir);
+        if (den == 0.0) return false;
+        double u = dot(nn, s.a[t] - from) / den;
+        if (!(u > 0.0 && u < 1.0)) return false;
+        Vec3 p = from + u * dir;
+        if (!point_in_tri(s, t, p)) return false;
+        pts[j] = p;
+    }
+    *on_edge = false;
+    for (int j = 0; j <= q; ++j) {
+        Vec3 d = pts[j + 1] - pts[j];
+        double len = norm(d);
+        if (len <= eps) return false;
+        int s0 = j >= 1 ? seq[j - 1] : -1;
+        int s1 = j + 1 <= q ? seq[j] : -1;
+        if (any_hit(s, pts[j], d, eps / len, 1.0 - eps / len, s0, s1)) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Antenna basis vectors theta_hat, phi_hat of direction k (notation of Sec. I).
+static void sph_basis(Vec3 k, Vec3* th, Vec3* ph) {
+    double theta = std::acos(std::max(-1.0, std::min(1.0, k.z)));
+    double phi = std::atan2(k.y, k.x);
+    *th = v3(std::cos(theta) * std::cos(phi), std::cos(theta) * std::sin(phi), -std::sin(theta));
+    *ph = v3(-std::sin(phi), std::cos(phi), 0.0);
+}
+
+// Complex relative permittivity eta = eps_r - j sigma / (eps0 omega) (Sec. II-D).
+static cplx permittivity(double eps_r, double sigma, double freq) {
+    return cplx(eps_r, -sigma / (kEps0 * 2.0 * kPi * freq));
+}
+
+// Fresnel reflection coefficients (Eq. fresnel-1, fresnel-2) with the principal
+// complex square root.
+static void fresnel(cplx eta, double cos_i, cplx* r_perp, cplx* r_par) {
+    double sin2 = 1.0 - cos_i * cos_i;
+    cplx s = std::sqrt(eta - sin2);
+    *r_perp = (cos_i - s) / (cos_i + s);
+    *r_par = (eta * cos_i - s) / (eta * cos_i + s);
+}
+
+// d r_perp / d eta and d r_par / d eta (derivatives of Eq. fresnel-1/2).
+static void fresnel_deta(cplx eta, double cos_i, cplx* d_perp, cplx* d_par) {
+    double sin2 = 1.0 - cos_i * cos_i;
+    cplx s = std::sqrt(eta - sin2);
+    *d_perp = -cos_i / (s * (cos_i + s) * (cos_i + s));
+    *d_par = cos_i * (eta - 2.0 * sin2) / (s * (eta * cos_i + s) * (eta * cos_i + s));
+}
+
+struct PathMaterials {
+    const int32_t* tri_material;
+    const float* eps_r;
+    const float* sigma;
+    const uint8_t* is_pec;
+    int per_triangle;
+};
+
+// Transfer chain of one specular path (Sec. II-C, II-D):
+//   E_0 = C_T;  F_0(E) = e^{-j 2 pi d_1 / lambda} / d_1 E;
+//   for each bounce j: E <- D_j E (basis change), then
+//                      E <- diag(R r_perp, R r_par) E A_j e^{-j 2 pi d_{j+1} / lambda};
+//   E_{Q+1} = D_{Q+1} E = T(C_T) e^{-j 2 pi f tau},  a = lambda/(4 pi) C_R^H T(C_T).
+// Spreading factor (the paper cites it without printing it): for planar facets the
+// reflected wave front stays spherical about the image source, so
+// A_j = rho_j / (rho_j + d_{j+1}) with rho_j = d_1 + ... + d_j.  S = 0 (R = 1).
+// Polarisation model Eq. polarization_model with zeta = 0 (vertical) at both ends.
+// Reflection basis (McNamara Eq. 3.3-3.8, cited, not printed): e_perp = k_i x n / |k_i x n|,
+// e_par_in = e_perp x k_i, e_par_out = e_perp x k_r, n facing the incident wave.
+//
+// Outputs: a, and when `grad` is non-null, d a / d eta_j for every bounce.
+struct ChainOut {
+    cplx a;
+    cplx da_deta[8];
+    int mat[8];
+    bool pec[8];
+};
+
+static void path_chain(const Scene& s, const PathMaterials& m, const Vec3* pts, const int* seq, int q,
+                       double freq, double gain_tx, double gain_rx, int ni_mode, ChainOut* out) {
+    const double lam = kC0 / freq;
+    std::vector<double> d(q + 2);
+    std::vector<Vec3> k(q + 2);
+    double L = 0.0;
+    for (int j = 1; j <= q + 1; ++j) {
+        Vec3 dv = pts[j] - pts[j - 1];
+        d[j] = norm(dv);
+        k[j] = (1.0 / d[j]) * dv;
+        L += d[j];
+    }
+    const double tau = L / kC0;  // tau = (lambda f)^-1 sum d_q
+
+    // out_0 basis: the transmit antenna's theta_hat / phi_hat along the AoD k_1.
+    Vec3 out_p, out_q;
+    sph_basis(k[1], &out_p, &out_q);
+    cplx E[2] = {std::sqrt(gain_tx) * 1.0, std::sqrt(gain_tx) * 0.0};  // C_T, zeta = 0
+
+    // F_0
+    cplx ph1 = std::polar(1.0, -2.0 * kPi * d[1] / lam);
+    E[0] *= ph1 / d[1];
+    E[1] *= ph1 / d[1];
+
+    // Stored for the adjoint: incoming field after the basis change of bounce j,
+    // and the reflection matrix of bounce j.
+    std::vector<cplx> vin0(q + 1), vin1(q + 1), rp(q + 1), rl(q + 1);
+    std::vector<double> Dm(4 * (q + 2));
+    std::vector<double> spread(q + 1);
+    std::vector<cplx> phase(q + 1);
+
+    double rho = d[1];
+    for (int j = 1; j <= q; ++j) {
+        int t = seq[j - 1];
+        Vec3 nn = s.n[t];
+        if (dot(k[j], nn) > 0.0) nn = -1.0 * nn;   // normal facing the incident wave
+        double cos_i = -dot(k[j], nn);
+        Vec3 kr = k[j + 1];
+        Vec3 cr = cross(k[j], nn);
+        Vec3 e_perp;
+        if (norm(cr) > 1e-12) {
+            e_perp = unit(cr);
+        } else {
+            // Normal incidence: any unit vector transverse to k_i serves; take the
+            // previous outgoing p-vector (mode 0) or the world x axis (mode 1),
+            // made orthogonal to k_i.
+            Vec3 ref = ni_mode == 0 ? out_p : v3(1.0, 0.0, 0.0);
+            if (ni_mode != 0 && norm(cross(ref, k[j])) < 1e-6) ref = v3(0.0, 1.0, 0.0);
+            e_perp = unit(ref - dot(ref, k[j]) * k[j]);
+        }
+        Vec3 in_p = e_perp, in_q = cross(e_perp, k[j]);
+        // D_j (Eq. basis_transform)
+        double D00 = dot(in_p, out_p), D01 = dot(in_p, out_q);
+        double D10 = dot(in_q, out_p), D11 = dot(in_q, out_q);
+        Dm[4 * j + 0] = D00; Dm[4 * j + 1] = D01; Dm[4 * j + 2] = D10; Dm[4 * j + 3] = D11;
+        cplx e0 = D00 * E[0] + D01 * E[1];
+        cplx e1 = D10 * E[0] + D11 * E[1];
+        vin0[j] = e0;
+        vin1[j] = e1;
+        // F_j (Eq. specular_reflection)
+        int mi = m.per_triangle ? t : m.tri_material[t];
+        bool pec = m.is_pec[mi] != 0;
+        cplx r_perp, r_par;
+        if (pec) {
+            r_perp = -1.0;   // limit of Eq. fresnel-1/2 as |eta| -> infinity
+            r_par = 1.0;
+        } else {
+            fresnel(permittivity(m.eps_r[mi], m.sigma[mi], freq), cos_i, &r_perp, &r_par);
+        }
+        rp[j] = r_perp;
+        rl[j] = r_par;
+        out->mat[j - 1] = mi;
+        out->pec[j - 1] = pec;
+        double A = rho / (rho + d[j + 1]);
+        spread[j] = A;
+        phase[j] = std::polar(1.0, -2.0 * kPi * d[j + 1] / lam);
+        E[0] = r_perp * e0 * A * phase[j];
+        E[1] = r_par * e1 * A * phase[j];
+        rho += d[j + 1];
+        out_p = e_perp;
+        out_q = cross(e_perp, kr);
+    }
+    // D_{Q+1}: into the receive antenna's basis along the AoA direction -k_{Q+1}.
+    Vec3 rx_p, rx_q;
+    sph_basis(-1.0 * k[q + 1], &rx_p, &rx_q);
+    double D00 = dot(rx_p, out_p), D01 = dot(rx_p, out_q);
+    double D10 = dot(rx_q, out_p), D11 = dot(rx_q, out_q);
+    Dm[4 * (q + 1) + 0] = D00; Dm[4 * (q + 1) + 1] = D01; Dm[4 * (q + 1) + 2] = D10; Dm[4 * (q + 1) + 3] = D11;
+    cplx Ef0 = D00 * E[0] + D01 * E[1];
+    cplx Ef1 = D10 * E[0] + D11 * E[1];
+    (void)Ef1;
+    // Factor out exp(-j 2 pi f tau) and project on C_R = sqrt(g_R) [1, 0].
+    cplx unphase = std::polar(1.0, 2.0 * kPi * freq * tau);
+    cplx a = lam / (4.0 * kPi) * std::sqrt(gain_rx) * Ef0 * unphase;
+    out->a = a;
+
+    // Adjoint: a = K * l_j . diag(r_perp_j, r_par_j) . v_j, with the row vector
+    // l_j = C_R^T D_{Q+1} Gamma_Q D_Q ... D_{j+1} (times the scalar factors after
+    // bounce j) and v_j the field after D_j.  Walk j = Q..1 keeping l_j.
+    cplx l0 = lam / (4.0 * kPi) * std::sqrt(gain_rx) * unphase * Dm[4 * (q + 1) + 0];
+    cplx l1 = lam / (4.0 * kPi) * std::sqrt(gain_rx) * unphase * Dm[4 * (q + 1) + 1];
+    for (int j = q; j >= 1; --j) {
+        cplx fac = spread[j] * phase[j];
+        cplx da_drp = l0 * fac * vin0[j];
+        cplx da_drl = l1 * fac * vin1[j];
+        if (out->pec[j - 1]) {
+            out->da_deta[j - 1] = 0.0;
+        } else {
+            int mi = out->mat[j - 1];
+            Vec3 nn = s.n[seq[j - 1]];
+            if (dot(k[j], nn) > 0.0) nn = -1.0 * nn;
+            double cos_i = -dot(k[j], nn);
+            cplx dp, dl;
+            fresnel_deta(permittivity(m.eps_r[mi], m.sigma[mi], freq), cos_i, &dp, &dl);
+            out->da_deta[j - 1] = da_drp * dp + da_drl * dl;
+        }
+        // l_{j-1} = l_j . Gamma_j . (fac) . D_j
+        cplx g0 = l0 * rp[j] * fac, g1 = l1 * rl[j] * fac;
+        l0 = g0 * Dm[4 * j + 0] + g1 * Dm[4 * j + 2];
+        l1 = g0 * Dm[4 * j + 1] + g1 * Dm[4 * j + 3];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Path store returned to Python.
+
+struct Paths {
+    int Dmax;
+    std::vector<int32_t> rx, depth, seq;  // seq: P x Dmax, -1 padded
+    std::vector<double> pts;              // P x (Dmax+2) x 3
+    std::vector<double> tau;
+};
+
+static bool seq_less(const int* a, const int* b, int q) {
+    for (int j = 0; j < q; ++j)
+        if (a[j] != b[j]) return a[j] < b[j];
+    return false;
+}
+
+extern "C" {
+
+void* orc_scene_create(const float* verts, int n_verts, const int32_t* tris, int n_tris) {
+    (void)n_verts;
+    Scene* s = new Scene();
+    s->T = n_tris;
+    s->a.resize(n_tris);
+    s->b.resize(n_tris);
+    s->c.resize(n_tris);
+    s->n.resize(n_tris);
+    Vec3 lo = v3(INFINITY, INFINITY, INFINITY), hi = v3(-INFINITY, -INFINITY, -INFINITY);
+    for (int t = 0; t < n_tris; ++t) {
+        const float* p0 = verts + 3 * tris[3 * t + 0];
+        const float* p1 = verts + 3 * tris[3 * t + 1];
+        const float* p2 = verts + 3 * tris[3 * t + 2];
+        s->a[t] = v3(p0[0], p0[1], p0[2]);
+        s->b[t] = v3(p1[0], p1[1], p1[2]);
+        s->c[t] = v3(p2[0], p2[1], p2[2]);
+        s->n[t] = unit(cross(s->b[t] - s->a[t], s->c[t] - s->a[t]));
+        for (Vec3 p : {s->a[t], s->b[t], s->c[t]}) {
+            lo = v3(std::min(lo.x, p.x), std::min(lo.y, p.y), std::min(lo.z, p.z));
+            hi = v3(std::max(hi.x, p.x), std::max(hi.y, p.y), std::max(hi.z, p.z));
+        }
+    }
+    s->diag = norm(hi - lo);
+    s->order.resize(n_tris);
+    for (int t = 0; t < n_tris; ++t) s->order[t] = t;
+    build_node(*s, 0, n_tris);
+    return s;
+}
+
+void orc_scene_free(void* h) { delete (Scene*)h; }
+
+double orc_scene_diag(void* h) { return ((Scene*)h)->diag; }
+
+int orc_bvh_nodes(void* h) { return (int)((Scene*)h)->nodes.size(); }
+
+// Closest hit for n rays (o, d as FP64 triples).  skip[i] < 0 skips nothing.
+void orc_closest_hit(void* h, int64_t n, const double* o, const double* d, double tmin, const int32_t* skip,
+                     int use_bvh, int32_t* tri_out, double* t_out) {
+    const Scene& s = *(Scene*)h;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; ++i) {
+        double th;
+        int t = closest_hit(s, v3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), v3(d[3 * i], d[3 * i + 1], d[3 * i + 2]),
+                            tmin, skip ? skip[i] : -1, use_bvh != 0, &th);
+        tri_out[i] = t;
+        t_out[i] = t >= 0 ? th : INFINITY;
+    }
+}
+
+void orc_fibonacci(int64_t n, float* dirs) {
+    for (int64_t i = 0; i < n; ++i) fibonacci_dir(i, n, dirs + 3 * i);
+}
+
+// Per-ray SBR sequences (N x D, -1 padded), for checking the launch itself.
+void orc_sbr_rays(void* h, const double* tx, int64_t n_rays, int D, int use_bvh, int32_t* seqs) {
+    const Scene& s = *(Scene*)h;
+    double tmin = 1e-6 * s.diag;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n_rays; ++i) {
+        float f[3];
+        fibonacci_dir(i, n_rays, f);
+        sbr_ray(s, v3(tx[0], tx[1], tx[2]), v3(f[0], f[1], f[2]), D, tmin, use_bvh != 0, seqs + (size_t)D * i);
+    }
+}
+
+// Candidate set: the empty sequence (line of sight) and every non-empty prefix of
+// every ray's sequence, unique, ordered by (length, lexicographic).
+void* orc_candidates(void* h, const double* tx, int64_t n_rays, int D) {
+    const Scene& s = *(Scene*)h;
+    std::vector<int32_t> seqs((size_t)n_rays * D);
+    orc_sbr_rays(h, tx, n_rays, D, 1, seqs.data());
+    std::set<std::vector<int>> uniq;
+    uniq.insert(std::vector<int>());
+    for (int64_t i = 0; i < n_rays; ++i) {
+        std::vector<int> pre;
+        for (int b = 0; b < D; ++b) {
+            int t = seqs[(size_t)D * i + b];
+            if (t < 0) break;
+            pre.push_back(t);
+            uniq.insert(pre);
+        }
+    }
+    (void)s;
+    std::vector<std::vector<int>> v(uniq.begin(), uniq.end());
+    std::stable_sort(v.begin(), v.end(), [](const std::vector<int>& x, const std::vector<int>& y) {
+        if (x.size() != y.size()) return x.size() < y.size();
+        return x < y;
+    });
+    std::vector<int32_t>* out = new std::vector<int32_t>();
+    out->push_back(D);
+    out->push_back((int32_t)v.size());
+    for (auto& q : v) {
+        for (int b = 0; b < D; ++b) out->push_back(b < (int)q.size() ? q[b] : -1);
+    }
+    return out;
+}
+
+int64_t orc_candidates_count(void* c) { return (*(std::vector<int32_t>*)c)[1]; }
+
+void orc_candidates_get(void* c, int32_t* seqs) {
+    std::vector<int32_t>& v = *(std::vector<int32_t>*)c;
+    std::memcpy(seqs, v.data() + 2, sizeof(int32_t) * (v.size() - 2));
+}
+
+void orc_candidates_free(void* c) { delete (std::vector<int32_t>*)c; }
+
+// Image method over every (candidate, receiver) pair, then the coplanar-duplicate
+// rule (the paper is silent on it): two valid paths of one receiver whose
+// triangles are pairwise coplanar and whose points agree within 1e-9 * diag are
+// the same geometric path (a reflection point on an edge shared by coplanar
+// triangles); only the lexicographically smallest triangle sequence is kept.
+void* orc_image_method(void* h, const double* tx, const double* rx, int n_rx, void* cand_h) {
+    const Scene& s = *(Scene*)h;
+    std::vector<int32_t>& cv = *(std::vector<int32_t>*)cand_h;
+    int D = cv[0];
+    int64_t K = cv[1];
+    const int32_t* cands = cv.data() + 2;
+    double eps = 1e-6 * s.diag;
+    Vec3 txv = v3(tx[0], tx[1], tx[2]);
+    std::vector<Paths> per_rx(n_rx);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int r = 0; r < n_rx; ++r) {
+        Vec3 rxv = v3(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+        Paths& pr = per_rx[r];
+        std::vector<Vec3> pts(D + 2);
+        for (int64_t k = 0; k < K; ++k) {
+            const int32_t* sq = cands + (size_t)D * k;
+            int q = 0;
+            while (q < D && sq[q] >= 0) q++;
+            bool on_edge;
+            if (!image_path(s, txv, rxv, sq, q, eps, pts.data(), &on_edge)) continue;
+            pr.depth.push_back(q);
+            for (int b = 0; b < D; ++b) pr.seq.push_back(b < q ? sq[b] : -1);
+            for (int j = 0; j < D + 2; ++j) {
+                Vec3 p = j < q + 2 ? pts[j] : v3(0, 0, 0);
+                if (j == q + 1) p = rxv;
+                pr.pts.push_back(p.x);
+                pr.pts.push_back(p.y);
+                pr.pts.push_back(p.z);
+            }
+        }
+        // coplanar-duplicate rule
+        int P = (int)pr.depth.size();
+        std::vector<char> drop(P, 0);
+        for (int i = 0; i < P; ++i) {
+            for (int j = 0; j < P; ++j) {
+                if (i == j || drop[j] || pr.depth[i] != pr.depth[j]) continue;
+                int q = pr.depth[i];
+                bool same = true;
+                for (int b = 0; b < q && same; ++b)
+                    same = coplanar(s, pr.seq[(size_t)D * i + b], pr.seq[(size_t)D * j + b]);
+                for (int b = 1; b <= q && same; ++b) {
+                    const double* pi = &pr.pts[((size_t)(D + 2) * i + b) * 3];
+                    const double* pj = &pr.pts[((size_t)(D + 2) * j + b) * 3];
+                    double dd = std::sqrt((pi[0] - pj[0]) * (pi[0] - pj[0]) + (pi[1] - pj[1]) * (pi[1] - pj[1]) +
+                                          (pi[2] - pj[2]) * (pi[2] - pj[2]));
+                    same = dd <= 1e-9 * s.diag;
+                }
+                if (same && seq_less(&pr.seq[(size_t)D * j], &pr.seq[(size_t)D * i], q)) {
+                    drop[i] = 1;
+                    break;
+                }
+            }
+        }
+        Paths kept;
+        for (int i = 0; i < P; ++i) {
+            if (drop[i]) continue;
+            kept.depth.push_back(pr.depth[i]);
+            for (int b = 0; b < D; ++b) kept.seq.push_back(pr.seq[(size_t)D * i + b]);
+            double L = 0.0;
+            int q = pr.depth[i];
+            for (int j = 0; j < D + 2; ++j)
+                for (int c = 0; c < 3; ++c) kept.pts.push_back(pr.pts[((size_t)(D + 2) * i + j) * 3 + c]);
+            for (int j = 1; j <= q + 1; ++j) {
+                const double* p0 = &pr.pts[((size_t)(D + 2) * i + j - 1) * 3];
+                const double* p1 = &pr.pts[((size_t)(D + 2) * i + j) * 3];
+                L += std::sqrt((p1[0] - p0[0]) * (p1[0] - p0[0]) + (p1[1] - p0[1]) * (p1[1] - p0[1]) +
+                               (p1[2] - p0[2]) * (p1[2] - p0[2]));
+            }
+            kept.tau.push_back(L / kC0);
+        }
+        pr = kept;
+    }
+    Paths* all = new Paths();
+    all->Dmax = D;
+    for (int r = 0; r < n_rx; ++r) {
+        Paths& pr = per_rx[r];
+        for (size_t i = 0; i < pr.depth.size(); ++i) all->rx.push_back(r);
+        all->depth.insert(all->depth.end(), pr.depth.begin(), pr.depth.end());
+        all->seq.insert(all->seq.end(), pr.seq.begin(), pr.seq.end());
+        all->pts.insert(all->pts.end(), pr.pts.begin(), pr.pts.end());
+        all->tau.insert(all->tau.end(), pr.tau.begin(), pr.tau.end());
+    }
+    return all;
+}
+
+int64_t orc_paths_count(void* p) { return (int64_t)((Paths*)p)->depth.size(); }
+
+void orc_paths_get(void* p, int32_t* rx, int32_t* depth, int32_t* seq, double* pts, double* tau) {
+    Paths& P = *(Paths*)p;
+    std::memcpy(rx, P.rx.data(), sizeof(int32_t) * P.rx.size());
+    std::memcpy(depth, P.depth.data(), sizeof(int32_t) * P.depth.size());
+    std::memcpy(seq, P.seq.data(), sizeof(int32_t) * P.seq.size());
+    std::memcpy(pts, P.pts.data(), sizeof(double) * P.pts.size());
+    std::memcpy(tau, P.tau.data(), sizeof(double) * P.tau.size());
+}
+
+void orc_paths_free(void* p) { delete (Paths*)p; }
+
+// Path coefficients a_i (interleaved re/im) of P paths given by their points.
+// seq: P x Dmax, pts: P x (Dmax+2) x 3 (Tx, s_1..s_q, Rx, padding).
+void orc_fields(void* h, int64_t P, int Dmax, const int32_t* depth, const int32_t* seq, const double* pts,
+                const int32_t* tri_material, const float* eps_r, const float* sigma, const uint8_t* is_pec,
+                int per_triangle, double freq, double gain_tx, double gain_rx, int ni_mode, double* a_out) {
+    const Scene& s = *(Scene*)h;
+    PathMaterials m{tri_material, eps_r, sigma, is_pec, per_triangle};
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < P; ++i) {
+        int q = depth[i];
+        std::vector<Vec3> pv(q + 2);
+        for (int j = 0; j <= q; ++j) {
+            const double* p = pts + ((size_t)(Dmax + 2) * i + j) * 3;
+            pv[j] = v3(p[0], p[1], p[2]);
+        }
+        const double* pr = pts + ((size_t)(Dmax + 2) * i + q + 1) * 3;
+        pv[q + 1] = v3(pr[0], pr[1], pr[2]);
+        ChainOut co;
+        path_chain(s, m, pv.data(), seq + (size_t)Dmax * i, q, freq, gain_tx, gain_rx, ni_mode, &co);
+        a_out[2 * i] = co.a.real();
+        a_out[2 * i + 1] = co.a.imag();
+    }
+}
+
+// Gradients of a real loss L given g_a = dL/dRe a + j dL/dIm a for every path:
+// dL/dx = Re(conj(g_a) da/dx).  With eta = eps_r - j sigma/(eps0 omega):
+// da/deps_r = da/deta, da/dsigma = -j/(eps0 omega) da/deta, da/dg_T = a/(2 g_T),
+// da/dg_R = a/(2 g_R).  Results are accumulated into the outputs.
+void orc_fields_grad(void* h, int64_t P, int Dmax, const int32_t* depth, const int32_t* seq, const double* pts,
+                     const int32_t* tri_material, const float* eps_r, const float* sigma, const uint8_t* is_pec,
+                     int per_triangle, double freq, double gain_tx, double gain_rx, const double* grad_a,
+                     double* grad_eps, double* grad_sigma, double* grad_gain) {
+    const Scene& s = *(Scene*)h;
+    PathMaterials m{tri_material, eps_r, sigma, is_pec, per_triangle};
+    const cplx deta_dsigma(0.0, -1.0 / (kEps0 * 2.0 * kPi * freq));
+    for (int64_t i = 0; i < P; ++i) {
+        int q = depth[i];
+        std::vector<Vec3> pv(q + 2);
+        for (int j = 0; j <= q; ++j) {
+            const double* p = pts + ((size_t)(Dmax + 2) * i + j) * 3;
+            pv[j] = v3(p[0], p[1], p[2]);
+        }
+        const double* pr = pts + ((size_t)(Dmax + 2) * i + q + 1) * 3;
+        pv[q + 1] = v3(pr[0], pr[1], pr[2]);
+        ChainOut co;
+        path_chain(s, m, pv.data(), seq + (size_t)Dmax * i, q, freq, gain_tx, gain_rx, 0, &co);
+        cplx g(grad_a[2 * i], grad_a[2 * i + 1]);
+        for (int j = 0; j < q; ++j) {
+            if (co.pec[j]) continue;
+            grad_eps[co.mat[j]] += (std::conj(g) * co.da_deta[j]).real();
+            grad_sigma[co.mat[j]] += (std::conj(g) * co.da_deta[j] * deta_dsigma).real();
+        }
+        grad_gain[0] += (std::conj(g) * co.a).real() / (2.0 * gain_tx);
+        grad_gain[1] += (std::conj(g) * co.a).real() / (2.0 * gain_rx);
+    }
+}
+
+// Discrete CFR (Sec. II-A): H[r, n] = sum_{i in r} a_i exp(-j 2 pi (f_c + n df) tau_i),
+// n = -N/2 .. N/2-1, stored at column n + N/2.  a, H interleaved re/im.
+void orc_cfr(int64_t P, const double* a, const double* tau, const int64_t* rx_offsets, int n_rx, double fc,
+             double df, int N, double* H) {
+    (void)P;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int r = 0; r < n_rx; ++r) {
+        for (int c = 0; c < N; ++c) {
+            double f = fc + (double)(c - N / 2) * df;
+            cplx acc = 0.0;
+            for (int64_t i = rx_offsets[r]; i < rx_offsets[r + 1]; ++i)
+                acc += cplx(a[2 * i], a[2 * i + 1]) * std::polar(1.0, -2.0 * kPi * f * tau[i]);
+            H[2 * ((size_t)r * N + c)] = acc.real();
+            H[2 * ((size_t)r * N + c) + 1] = acc.imag();
+        }
+    }
+}
+
+// Adjoint of orc_cfr: g_a[i] = sum_n g_H[r(i), n] conj(exp(-j 2 pi f_n tau_i)).
+void orc_cfr_grad(int64_t P, const double* tau, const int64_t* rx_offsets, int n_rx, double fc, double df, int N,
+                  const double* grad_H, double* grad_a) {
+    (void)P;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int r = 0; r < n_rx; ++r) {
+        for (int64_t i = rx_offsets[r]; i < rx_offsets[r + 1]; ++i) {
+            cplx acc = 0.0;
+            for (int c = 0; c < N; ++c) {
+                double f = fc + (double)(c - N / 2) * df;
+                cplx g(grad_H[2 * ((size_t)r * N + c)], grad_H[2 * ((size_t)r * N + c) + 1]);
+                acc += g * std::conj(std::polar(1.0, -2.0 * kPi * f * tau[i]));
+            }
+            grad_a[2 * i] = acc.real();
+            grad_a[2 * i + 1] = acc.imag();
+        }
+    }
+}
+
+void orc_fresnel(double eps_r, double sigma, double freq, double cos_i, double* out) {
+    cplx rp, rl;
+    fresnel(permittivity(eps_r, sigma, freq), cos_i, &rp, &rl);
+    out[0] = rp.real(); out[1] = rp.imag(); out[2] = rl.real(); out[3] = rl.imag();
+    cplx dp, dl;
+    fresnel_deta(permittivity(eps_r, sigma, freq), cos_i, &dp, &dl);
+    out[4] = dp.real(); out[5] = dp.imag(); out[6] = dl.real(); out[7] = dl.imag();
+}
+
+void orc_permittivity(double eps_r, double sigma, double freq, double* out) {
+    cplx e = permittivity(eps_r, sigma, freq);
+    out[0] = e.real();
+    out[1] = e.imag();
+}
+
+}  // extern "C"
