@@ -1,0 +1,203 @@
+/*
+ * rt103.h -- C ABI of librt103, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of differentiable radio ray tracing as described in
+ * Hoydis et al., "Learning Radio Environments by Differentiable Ray Tracing"
+ * (arXiv 2311.18558):
+ *
+ *   specular path tracing (shoot-and-bounce candidates, image method,
+ *   visibility; Sec. II-F)  ->  path coefficients a_i and delays tau_i
+ *   (Eq. cfr_cont, Sec. II-C/D)  ->  CFR H[n] = sum_i a_i exp(-j2pi f_n tau_i)
+ *   (Sec. II-A), with adjoints of the field and CFR steps for gradient-based
+ *   calibration (Sec. III, Algorithm 1) and a neural-material MLP (Sec. III-D).
+ *
+ * Conventions shared by every call
+ *   - Units are SI (m, s, Hz, S/m).  Complex numbers are interleaved {re, im}
+ *     float32 pairs ("complex64").  The time convention is exp(+j omega t), so a
+ *     delay tau contributes exp(-j 2 pi f tau) and eta = eps_r - j sigma/(eps0 omega).
+ *   - Pointers named *_dev are device pointers owned by the caller; *_host are
+ *     host pointers read during the call only.  Opaque handles (rt_ctx,
+ *     rt_scene, rt_paths) are owned by the library and released with the
+ *     matching *_free / rt_destroy call.  A paths object refers to its scene:
+ *     free the paths before the scene.
+ *   - Every call is ordered on the context's CUDA stream (rt_create /
+ *     rt_set_stream) and returns before the GPU work finishes, except where a
+ *     call says it synchronises.  Device buffers must stay valid until then.
+ *   - Every call returns an rt_status.  Invalid arguments are rejected on the
+ *     host before any launch.  Kernels never trap: a device-side problem (a
+ *     bounded loop that ran out, a full buffer) sets a sticky status word that
+ *     rt_status_word reads.  rt_last_error gives a message for the last failure
+ *     of a context (valid until the next call on that context).
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef RT103_H
+#define RT103_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_ctx rt_ctx;
+typedef struct rt_scene rt_scene;
+typedef struct rt_paths rt_paths;
+
+typedef enum {
+    RT_OK = 0,
+    RT_ERR_INVALID_ARG = 1,     /* rejected on the host, nothing launched           */
+    RT_ERR_CUDA = 2,            /* a CUDA runtime call failed                        */
+    RT_ERR_OOM = 3,             /* device allocation failed                          */
+    RT_ERR_CAPACITY = 4,        /* an internal buffer overflowed (see message)       */
+    RT_ERR_STACK_OVERFLOW = 5,  /* BVH traversal stack overflow (device status)      */
+    RT_ERR_ITER_LIMIT = 6,      /* a bounded device loop ran out (device status)     */
+    RT_ERR_TIMEOUT = 7,         /* a bounded device wait ran out (device status)     */
+    RT_ERR_NUMERIC = 8,         /* NaN/Inf or out-of-domain input                    */
+    RT_ERR_UNSUPPORTED = 9      /* valid but not supported by this build             */
+} rt_status;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`, ordering work on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  *out receives the handle. */
+rt_status rt_create(int device, void* cuda_stream, rt_ctx** out);
+rt_status rt_destroy(rt_ctx* ctx);
+/* Change the stream subsequent calls are ordered on. */
+rt_status rt_set_stream(rt_ctx* ctx, void* cuda_stream);
+/* Message of the last failed call on ctx (never NULL; "" if none). */
+const char* rt_last_error(const rt_ctx* ctx);
+/* Synchronises the stream, writes the sticky device status word (an
+ * rt_status value, RT_OK if none) to *device_error and clears it. */
+rt_status rt_status_word(rt_ctx* ctx, int32_t* device_error);
+/* Library version string. */
+const char* rt_version(void);
+
+/* ------------------------------------------------------------------ scene */
+
+/* Upload a triangle mesh (Sec. II-F: the scene is a set of triangles, each
+ * belonging to an object with a material, Sec. II-D) and build its BVH.
+ *   verts_host       n_verts x 3 float32 positions [m]
+ *   tris_host        n_tris x 3 int32 vertex indices; the geometric normal is
+ *                    (v1-v0) x (v2-v0); reflection is two-sided
+ *   tri_material_host n_tris int32 material index in [0, n_materials)
+ *   material_is_pec_host n_materials uint8, 1 = perfect electric conductor
+ *                    (r_perp = -1, r_par = +1, the |eta| -> inf limit of
+ *                    Eq. fresnel-1/2)
+ * Limits: 1 <= n_tris <= 65535 (triangle sequences are packed in 16-bit
+ * fields), finite coordinates, non-degenerate triangles.  Synchronises. */
+rt_status rt_scene_upload(rt_ctx* ctx, const float* verts_host, int32_t n_verts,
+                          const int32_t* tris_host, int32_t n_tris,
+                          const int32_t* tri_material_host, int32_t n_materials,
+                          const uint8_t* material_is_pec_host, rt_scene** out);
+rt_status rt_scene_free(rt_scene* scene);
+/* n_tris, BVH node count and bounding-box diagonal [m] of a scene. */
+rt_status rt_scene_info(const rt_scene* scene, int32_t* n_tris, int32_t* n_nodes, double* diag);
+
+/* ------------------------------------------------------------------ tracing */
+
+/* Specular path tracing, Sec. II-F: n_rays rays leave the transmitter along a
+ * Fibonacci lattice (direction i: z = 1-(2i+1)/N, r = sqrt(1-z^2),
+ * phi = 2 pi frac(i (sqrt5-1)/2), evaluated in FP64 and rounded to FP32) and
+ * bounce specularly up to max_depth times (k_r = k_i - 2 (k_i.n) n, Sec. II-D);
+ * every prefix of every ray's triangle sequence, plus the empty sequence (line
+ * of sight), is a candidate; duplicates are removed; the image method turns each
+ * (candidate, receiver) pair into an exact specular chain or rejects it; every
+ * segment of a surviving chain must be unobstructed.  Paths whose reflection
+ * points coincide on coplanar triangles are kept once (lowest triangle
+ * sequence).
+ *   tx_host    transmitter position, 3 doubles [m]
+ *   rx_dev     n_rx x 3 doubles, receiver positions [m]
+ *   1 <= max_depth <= 4, 1 <= n_rays <= 2^31-1, 1 <= n_rx <= 2^24
+ * *out receives the paths, grouped by receiver and, within a receiver, ordered
+ * by (depth, triangle sequence).  Synchronises (the number of candidates and
+ * paths sizes the outputs). */
+rt_status rt_trace_paths(rt_ctx* ctx, const rt_scene* scene, const double* tx_host,
+                         const double* rx_dev, int32_t n_rx, int64_t n_rays,
+                         int32_t max_depth, rt_paths** out);
+
+/* Build a paths object from externally supplied chains (e.g. another tracer):
+ *   rx_dev n_paths int32 receiver index in [0, n_rx), non-decreasing
+ *   depth_dev n_paths int32 in [0, max_depth]
+ *   tri_seq_dev n_paths x max_depth int32 triangle indices (-1 padded)
+ *   points_dev n_paths x (max_depth+2) x 3 doubles: Tx, s_1..s_q, Rx, padding.
+ * The per-path geometry records (delays, angles, basis changes) are derived on
+ * the device exactly as for traced paths. */
+rt_status rt_paths_import(rt_ctx* ctx, const rt_scene* scene, int64_t n_paths, int32_t max_depth,
+                          int32_t n_rx, const int32_t* rx_dev, const int32_t* depth_dev,
+                          const int32_t* tri_seq_dev, const double* points_dev, rt_paths** out);
+/* Number of paths and of deduplicated candidates (0 for imported paths). */
+rt_status rt_paths_count(const rt_paths* paths, int64_t* n_paths, int64_t* n_candidates);
+/* Copies the n_rx+1 int64 path offsets per receiver to rx_offsets_dev. */
+rt_status rt_paths_rx_offsets(const rt_paths* paths, int64_t* rx_offsets_dev);
+/* Copies path data into caller buffers (any pointer may be NULL to skip):
+ * tri_seq n_paths x max_depth int32 (-1 padded), depth n_paths int32,
+ * rx n_paths int32, tau n_paths double [s] = path length / c (Eq.
+ * transfer_function), points n_paths x (max_depth+2) x 3 double. */
+rt_status rt_paths_export(const rt_paths* paths, int32_t* tri_seq_dev, int32_t* depth_dev,
+                          int32_t* rx_dev, double* tau_dev, double* points_dev);
+/* Copies the candidate list, n_candidates x max_depth int32 (-1 padded), in
+ * (length, lexicographic) order; candidate 0 is the empty sequence. */
+rt_status rt_paths_candidates(const rt_paths* paths, int32_t* seq_dev);
+rt_status rt_paths_free(rt_paths* paths);
+
+/* ------------------------------------------------------------------ fields */
+
+/* Path coefficients a_i of Eq. cfr_cont for every path:
+ *   a_i = lambda/(4 pi) * sqrt(g_T g_R) / L_i * C_R^T D_{Q+1} G_Q D_Q ... G_1 D_1 C_T
+ * with the basis changes D_j of Eq. basis_transform, G_j = diag(r_perp, r_par)
+ * from Eq. fresnel-1/2 at eta = eps_r - j sigma/(eps0 2 pi freq), spreading of
+ * a spherical wave about the image source (product 1/L over the path), S = 0,
+ * and vertically polarised isotropic antennas (Eq. polarization_model, zeta=0).
+ *   eps_r_dev, sigma_dev  float32, indexed by material (per_triangle = 0, length
+ *                         n_materials) or by triangle (per_triangle = 1, n_tris)
+ *   freq_hz              frequency of lambda and eta (> 0)
+ *   gain_tx, gain_rx     antenna gains g_T, g_R (> 0)
+ *   a_dev                n_paths complex64 output
+ *   tau_dev              n_paths double output (may be NULL) */
+rt_status rt_eval_fields(rt_ctx* ctx, const rt_paths* paths, const float* eps_r_dev,
+                         const float* sigma_dev, int32_t per_triangle, double freq_hz,
+                         float gain_tx, float gain_rx, void* a_dev, double* tau_dev);
+/* Adjoint of rt_eval_fields with the geometry held fixed (Sec. II-F): given
+ * grad_a = dL/dRe a + j dL/dIm a (complex64, n_paths), ACCUMULATES (+=)
+ *   grad_eps_r[m] += sum Re(conj(g) da/deps_r),  grad_sigma[m] += sum Re(conj(g) da/dsigma)
+ * (da/dsigma = -j/(eps0 omega) da/deta), and grad_gain[0..1] += dL/dg_T, dL/dg_R.
+ * Any of the three gradient pointers may be NULL. */
+rt_status rt_eval_fields_backward(rt_ctx* ctx, const rt_paths* paths, const float* eps_r_dev,
+                                  const float* sigma_dev, int32_t per_triangle, double freq_hz,
+                                  float gain_tx, float gain_rx, const void* grad_a_dev,
+                                  float* grad_eps_r_dev, float* grad_sigma_dev,
+                                  float* grad_gain_dev);
+
+/* ------------------------------------------------------------------ CFR */
+
+/* Discrete CFR (Sec. II-A): H[r, n] = sum_{i in r} a_i exp(-j 2 pi (f_c + n df) tau_i),
+ * n = -N/2 .. N/2-1, written to column n + N/2 of row r.
+ *   rx_offsets_dev  n_rx+1 int64, paths of receiver r are [off[r], off[r+1])
+ *   a_dev           complex64 per path;  tau_dev double per path [s]
+ *   n_sub           N, even (or 1: a single frequency f_c), N <= 4096
+ *   H_dev           n_rx x N complex64 output */
+rt_status rt_cfr(rt_ctx* ctx, const int64_t* rx_offsets_dev, int32_t n_rx, const void* a_dev,
+                 const double* tau_dev, double f_center_hz, double delta_f_hz, int32_t n_sub,
+                 void* H_dev);
+/* Adjoint of rt_cfr: grad_a[i] = sum_n grad_H[r(i), n] conj(exp(-j 2 pi f_n tau_i))
+ * (overwrites grad_a_dev, complex64 per path). */
+rt_status rt_cfr_backward(rt_ctx* ctx, const int64_t* rx_offsets_dev, int32_t n_rx,
+                          const double* tau_dev, double f_center_hz, double delta_f_hz,
+                          int32_t n_sub, const void* grad_H_dev, void* grad_a_dev);
+/* CFR, power loss and CFR adjoint in one launch:
+ *   L = 1/(n_rx N) sum_{r,n} (w_r (|H[r,n]|^2 - P*[r,n]))^2
+ * (an MSE on CFR power; the paper's Algorithm 1 admits any differentiable loss,
+ * Sec. III-E), then grad_a = adjoint of rt_cfr applied to dL/dH.
+ *   target_power_dev n_rx x N float32 P*;  rx_weight_dev n_rx float32 w_r
+ *   loss_dev  one float32 (overwritten);  grad_a_dev complex64 per path (overwritten)
+ *   H_dev     n_rx x N complex64 output, or NULL not to store H */
+rt_status rt_cfr_power_mse_fused(rt_ctx* ctx, const int64_t* rx_offsets_dev, int32_t n_rx,
+                                 const void* a_dev, const double* tau_dev, double f_center_hz,
+                                 double delta_f_hz, int32_t n_sub, const float* target_power_dev,
+                                 const float* rx_weight_dev, float* loss_dev, void* grad_a_dev,
+                                 void* H_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RT103_H */

@@ -135,9 +135,17 @@ static bool box_hit(const Box& bx, Vec3 o, Vec3 d, double tmin, double tmax) {
     return true;
 }
 
+// Degenerate geometry (the paper is silent on it).  Reading: a triangle counts
+// as closed and grown by kTol relative to its size, so a point or ray exactly on
+// an edge shared by two triangles belongs to both, whatever the rounding; the
+// duplicate rule and the tie rule below then pick one of them.
+static const double kTol = 1e-9;      // relative growth of every triangle
+static const double kTieTol = 1e-12;  // relative t-difference treated as a tie
+
 // Watertight ray/triangle intersection (Woop, Benthin and Wald, "Watertight
-// Ray/Triangle Intersection", JCGT 2013), evaluated in FP64.  Edges and vertices
-// count as hits (closed triangle).  Returns the ray parameter t or -1 for a miss.
+// Ray/Triangle Intersection", JCGT 2013), evaluated in FP64, with the scaled
+// barycentrics U, V, W allowed down to -kTol (|U| + |V| + |W|).  A ray lying in
+// the triangle's plane misses.  Returns the ray parameter t or -1 for a miss.
 static double tri_hit(const Scene& s, int t, Vec3 o, Vec3 d) {
     double dd[3] = {d.x, d.y, d.z};
     int kz = 0;
@@ -153,53 +161,59 @@ static double tri_hit(const Scene& s, int t, Vec3 o, Vec3 d) {
     double U = Cx * By - Cy * Bx;
     double V = Ax * Cy - Ay * Cx;
     double W = Bx * Ay - By * Ax;
-    if ((U < 0.0 || V < 0.0 || W < 0.0) && (U > 0.0 || V > 0.0 || W > 0.0)) return -1.0;
+    double m = kTol * (std::fabs(U) + std::fabs(V) + std::fabs(W));
+    if ((U < -m || V < -m || W < -m) && (U > m || V > m || W > m)) return -1.0;
     double det = U + V + W;
-    if (det == 0.0) return -1.0;
+    if (!(std::fabs(det) > 3.0 * m)) return -1.0;
     double Az = Sz * comp(A, kz), Bz = Sz * comp(B, kz), Cz = Sz * comp(C, kz);
     double T = U * Az + V * Bz + W * Cz;
     return T / det;
 }
 
-// Closest hit with t > tmin, skipping triangle `skip`.  Exact ties in t go to the
-// lower triangle index.  Returns the triangle index or -1.
-static int closest_hit(const Scene& s, Vec3 o, Vec3 d, double tmin, int skip, bool use_bvh, double* t_out) {
-    int best = -1;
-    double bt = INFINITY;
+// All hits with tmin < t <= tmax (skipping `skip`): calls f(t, triangle).
+template <typename F>
+static void each_hit(const Scene& s, Vec3 o, Vec3 d, double tmin, double tmax, int skip, bool use_bvh, F f) {
     if (!use_bvh) {
         for (int t = 0; t < s.T; ++t) {
             if (t == skip) continue;
             double th = tri_hit(s, t, o, d);
-            if (th > tmin && (th < bt || (th == bt && t < best))) {
-                bt = th;
-                best = t;
-            }
+            if (th > tmin && th <= tmax) f(th, t);
         }
-    } else {
-        std::vector<int> stack;
-        stack.push_back(0);
-        while (!stack.empty()) {
-            int ni = stack.back();
-            stack.pop_back();
-            const Node& nd = s.nodes[ni];
-            if (!box_hit(nd.box, o, d, tmin, bt)) continue;
-            if (nd.left < 0) {
-                for (int i = nd.first; i < nd.first + nd.count; ++i) {
-                    int t = s.order[i];
-                    if (t == skip) continue;
-                    double th = tri_hit(s, t, o, d);
-                    if (th > tmin && (th < bt || (th == bt && t < best))) {
-                        bt = th;
-                        best = t;
-                    }
-                }
-            } else {
-                stack.push_back(nd.left);
-                stack.push_back(nd.right);
+        return;
+    }
+    std::vector<int> stack;
+    stack.push_back(0);
+    while (!stack.empty()) {
+        int ni = stack.back();
+        stack.pop_back();
+        const Node& nd = s.nodes[ni];
+        if (!box_hit(nd.box, o, d, tmin, tmax)) continue;
+        if (nd.left < 0) {
+            for (int i = nd.first; i < nd.first + nd.count; ++i) {
+                int t = s.order[i];
+                if (t == skip) continue;
+                double th = tri_hit(s, t, o, d);
+                if (th > tmin && th <= tmax) f(th, t);
             }
+        } else {
+            stack.push_back(nd.left);
+            stack.push_back(nd.right);
         }
     }
+}
+
+// Closest hit with t > tmin, skipping triangle `skip`: the smallest t over all
+// hits, then, among the hits with t within kTieTol (relative) of it, the lowest
+// triangle index -- an answer that does not depend on the visiting order.
+static int closest_hit(const Scene& s, Vec3 o, Vec3 d, double tmin, int skip, bool use_bvh, double* t_out) {
+    double bt = INFINITY;
+    each_hit(s, o, d, tmin, INFINITY, skip, use_bvh, [&](double th, int) { bt = std::min(bt, th); });
     *t_out = bt;
+    if (!(bt < INFINITY)) return -1;
+    int best = -1;
+    each_hit(s, o, d, tmin, bt + kTieTol * bt, skip, use_bvh, [&](double, int t) {
+        if (best < 0 || t < best) best = t;
+    });
     return best;
 }
 
@@ -227,14 +241,16 @@ static bool any_hit(const Scene& s, Vec3 o, Vec3 d, double tmin, double tmax, in
     return false;
 }
 
-// Closed point-in-triangle test for a point on (or numerically next to) the
-// triangle's plane: all three edge functions, measured along the normal, >= 0.
+// Point-in-triangle test for a point on (or numerically next to) the triangle's
+// plane: the three edge functions along the normal, divided by |n|^2 (i.e. the
+// barycentric coordinates), are >= -kTol (closed triangle grown by kTol).
 static bool point_in_tri(const Scene& s, int t, Vec3 p) {
     Vec3 nn = cross(s.b[t] - s.a[t], s.c[t] - s.a[t]);
-    double e0 = dot(nn, cross(s.b[t] - s.a[t], p - s.a[t]));
-    double e1 = dot(nn, cross(s.c[t] - s.b[t], p - s.b[t]));
-    double e2 = dot(nn, cross(s.a[t] - s.c[t], p - s.c[t]));
-    return e0 >= 0.0 && e1 >= 0.0 && e2 >= 0.0;
+    double n2 = dot(nn, nn);
+    double e0 = dot(nn, cross(s.b[t] - s.a[t], p - s.a[t])) / n2;
+    double e1 = dot(nn, cross(s.c[t] - s.b[t], p - s.b[t])) / n2;
+    double e2 = dot(nn, cross(s.a[t] - s.c[t], p - s.c[t])) / n2;
+    return e0 >= -kTol && e1 >= -kTol && e2 >= -kTol;
 }
 
 static bool coplanar(const Scene& s, int t, int u) {
@@ -330,9 +346,10 @@ static bool image_path(const Scene& s, Vec3 tx, Vec3 rx, const int* seq, int q, 
 
 // ---------------------------------------------------------------------------
 // Antenna basis vectors theta_hat, phi_hat of direction k (notation of Sec. I).
+// The azimuth of a vertical direction is undefined; reading: phi = 0 there.
 static void sph_basis(Vec3 k, Vec3* th, Vec3* ph) {
     double theta = std::acos(std::max(-1.0, std::min(1.0, k.z)));
-    double phi = std::atan2(k.y, k.x);
+    double phi = (k.x == 0.0 && k.y == 0.0) ? 0.0 : std::atan2(k.y, k.x);
     *th = v3(std::cos(theta) * std::cos(phi), std::cos(theta) * std::sin(phi), -std::sin(theta));
     *ph = v3(-std::sin(phi), std::cos(phi), 0.0);
 }

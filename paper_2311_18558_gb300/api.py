@@ -1,0 +1,253 @@
+"""Thin Python binding of librt103: argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; PyTorch provides device
+memory and the current stream.  Names follow include/rt103.h.
+"""
+from __future__ import annotations
+
+import ctypes
+import sys
+from typing import Optional
+
+import numpy as np
+import torch
+
+from ._lib import RtError, load
+
+_c = ctypes
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else _c.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A library context on one CUDA device (rt_create).  Each call is ordered on
+    the torch stream that is current when the call is made."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.device = int(device)
+        h = _c.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.rt_create(self.device, _c.c_void_p(torch.cuda.current_stream().cuda_stream), _c.byref(h))
+        if st != 0:
+            raise RtError(st, "rt_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        # at interpreter exit the process releases everything; calling into CUDA
+        # while Python and the runtime tear down is not safe
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        self.lib.rt_set_stream(self.h, _c.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+
+    def check(self, st: int, what: str):
+        if st != 0:
+            msg = self.lib.rt_last_error(self.h).decode()
+            raise RtError(st, f"{what}: {msg}")
+
+    def status_word(self) -> int:
+        """Synchronise and return (and clear) the sticky device status word."""
+        v = _c.c_int32(0)
+        self._stream()
+        self.check(self.lib.rt_status_word(self.h, _c.byref(v)), "rt_status_word")
+        return int(v.value)
+
+
+class Scene:
+    """A triangle mesh uploaded to the device with its BVH (rt_scene_upload)."""
+
+    def __init__(self, ctx: Context, verts, tris, tri_material, is_pec):
+        self.ctx = ctx
+        self._v = np.ascontiguousarray(verts, np.float32)
+        self._t = np.ascontiguousarray(tris, np.int32)
+        self._m = np.ascontiguousarray(tri_material, np.int32)
+        self._p = np.ascontiguousarray(is_pec, np.uint8)
+        h = _c.c_void_p()
+        ctx._stream()
+        ctx.check(ctx.lib.rt_scene_upload(ctx.h, self._v.ctypes.data_as(_c.c_void_p), self._v.shape[0],
+                                          self._t.ctypes.data_as(_c.c_void_p), self._t.shape[0],
+                                          self._m.ctypes.data_as(_c.c_void_p), self._p.shape[0],
+                                          self._p.ctypes.data_as(_c.c_void_p), _c.byref(h)), "rt_scene_upload")
+        self.h = h
+        nt, nn, dg = _c.c_int32(), _c.c_int32(), _c.c_double()
+        ctx.lib.rt_scene_info(h, _c.byref(nt), _c.byref(nn), _c.byref(dg))
+        self.n_tris, self.n_nodes, self.diag = nt.value, nn.value, dg.value
+        self.n_materials = int(self._p.shape[0])
+
+    @classmethod
+    def from_synthetic(cls, ctx: Context, sc) -> "Scene":
+        return cls(ctx, sc.verts, sc.tris, sc.tri_material, sc.is_pec)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.rt_scene_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        # at interpreter exit the process releases everything; calling into CUDA
+        # while Python and the runtime tear down is not safe
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Paths:
+    """Traced (or imported) paths with their frozen geometry records."""
+
+    def __init__(self, ctx: Context, scene: Scene, h, n_rx: int, max_depth: int):
+        self.ctx, self.scene, self.h = ctx, scene, h
+        self.n_rx, self.max_depth = int(n_rx), int(max_depth)
+        p, k = _c.c_int64(), _c.c_int64()
+        ctx.lib.rt_paths_count(h, _c.byref(p), _c.byref(k))
+        self.n_paths, self.n_candidates = int(p.value), int(k.value)
+        dev = torch.device("cuda", ctx.device)
+        self.rx_offsets = torch.empty(self.n_rx + 1, dtype=torch.int64, device=dev)
+        ctx._stream()
+        ctx.check(ctx.lib.rt_paths_rx_offsets(h, _ptr(self.rx_offsets)), "rt_paths_rx_offsets")
+        self.tau = torch.empty(max(self.n_paths, 1), dtype=torch.float64, device=dev)[: self.n_paths]
+        if self.n_paths:
+            ctx.check(ctx.lib.rt_paths_export(h, None, None, None, _ptr(self.tau), None), "rt_paths_export")
+
+    def export(self):
+        """Triangle sequences, depths, receivers, delays and points as device tensors."""
+        dev = torch.device("cuda", self.ctx.device)
+        P, D = self.n_paths, self.max_depth
+        out = dict(seq=torch.empty((P, D), dtype=torch.int32, device=dev),
+                   depth=torch.empty(P, dtype=torch.int32, device=dev),
+                   rx=torch.empty(P, dtype=torch.int32, device=dev),
+                   tau=torch.empty(P, dtype=torch.float64, device=dev),
+                   pts=torch.empty((P, D + 2, 3), dtype=torch.float64, device=dev))
+        self.ctx._stream()
+        if P:
+            self.ctx.check(self.ctx.lib.rt_paths_export(self.h, _ptr(out["seq"]), _ptr(out["depth"]), _ptr(out["rx"]),
+                                                        _ptr(out["tau"]), _ptr(out["pts"])), "rt_paths_export")
+        out["rx_offsets"] = self.rx_offsets
+        return out
+
+    def candidates(self) -> torch.Tensor:
+        dev = torch.device("cuda", self.ctx.device)
+        out = torch.empty((max(self.n_candidates, 1), self.max_depth), dtype=torch.int32, device=dev)
+        self.ctx._stream()
+        self.ctx.check(self.ctx.lib.rt_paths_candidates(self.h, _ptr(out)), "rt_paths_candidates")
+        return out[: self.n_candidates]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.rt_paths_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        # at interpreter exit the process releases everything; calling into CUDA
+        # while Python and the runtime tear down is not safe
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trace_paths(ctx: Context, scene: Scene, tx, rx: torch.Tensor, n_rays: int, max_depth: int) -> Paths:
+    """Specular path tracing (rt_trace_paths); rx is a CUDA float64 (R, 3) tensor."""
+    rx = rx.to(device=torch.device("cuda", ctx.device), dtype=torch.float64).contiguous()
+    txa = (_c.c_double * 3)(*[float(v) for v in tx])
+    h = _c.c_void_p()
+    ctx._stream()
+    ctx.check(ctx.lib.rt_trace_paths(ctx.h, scene.h, txa, _ptr(rx), rx.shape[0], int(n_rays), int(max_depth),
+                                     _c.byref(h)), "rt_trace_paths")
+    return Paths(ctx, scene, h, rx.shape[0], max_depth)
+
+
+def import_paths(ctx: Context, scene: Scene, rx_idx, depth, seq, pts, n_rx: int) -> Paths:
+    """Paths given by their receivers, depths, triangle sequences and points (rt_paths_import)."""
+    dev = torch.device("cuda", ctx.device)
+    rx_idx = torch.as_tensor(rx_idx, dtype=torch.int32).to(dev).contiguous()
+    depth = torch.as_tensor(depth, dtype=torch.int32).to(dev).contiguous()
+    seq = torch.as_tensor(seq, dtype=torch.int32).to(dev).contiguous()
+    pts = torch.as_tensor(pts, dtype=torch.float64).to(dev).contiguous()
+    D = int(seq.shape[1])
+    h = _c.c_void_p()
+    ctx._stream()
+    ctx.check(ctx.lib.rt_paths_import(ctx.h, scene.h, int(seq.shape[0]), D, int(n_rx), _ptr(rx_idx), _ptr(depth),
+                                      _ptr(seq), _ptr(pts), _c.byref(h)), "rt_paths_import")
+    return Paths(ctx, scene, h, n_rx, D)
+
+
+def eval_fields(ctx: Context, paths: Paths, eps_r: torch.Tensor, sigma: torch.Tensor, freq_hz: float,
+                gain_tx: float = 1.0, gain_rx: float = 1.0, per_triangle: bool = False,
+                out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Path coefficients a_i (complex64) of Eq. cfr_cont (rt_eval_fields)."""
+    dev = torch.device("cuda", ctx.device)
+    a = out if out is not None else torch.empty(paths.n_paths, dtype=torch.complex64, device=dev)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_eval_fields(ctx.h, paths.h, _ptr(eps_r), _ptr(sigma), int(per_triangle), float(freq_hz),
+                                     float(gain_tx), float(gain_rx), _ptr(a), None), "rt_eval_fields")
+    return a
+
+
+def eval_fields_backward(ctx: Context, paths: Paths, eps_r, sigma, freq_hz, grad_a, grad_eps=None, grad_sigma=None,
+                         grad_gain=None, gain_tx=1.0, gain_rx=1.0, per_triangle=False):
+    """Accumulates dL/deps_r, dL/dsigma, dL/d(g_T, g_R) given dL/da (rt_eval_fields_backward)."""
+    dev = torch.device("cuda", ctx.device)
+    if grad_eps is None:
+        grad_eps = torch.zeros_like(eps_r, dtype=torch.float32)
+    if grad_sigma is None:
+        grad_sigma = torch.zeros_like(sigma, dtype=torch.float32)
+    if grad_gain is None:
+        grad_gain = torch.zeros(2, dtype=torch.float32, device=dev)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_eval_fields_backward(ctx.h, paths.h, _ptr(eps_r), _ptr(sigma), int(per_triangle),
+                                              float(freq_hz), float(gain_tx), float(gain_rx),
+                                              _ptr(grad_a.contiguous()), _ptr(grad_eps), _ptr(grad_sigma),
+                                              _ptr(grad_gain)), "rt_eval_fields_backward")
+    return grad_eps, grad_sigma, grad_gain
+
+
+def cfr(ctx: Context, rx_offsets: torch.Tensor, a: torch.Tensor, tau: torch.Tensor, f_center_hz: float,
+        delta_f_hz: float, n_sub: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """H[r, n] of Sec. II-A (rt_cfr); complex64 (R, N), column n + N/2."""
+    R = rx_offsets.shape[0] - 1
+    H = out if out is not None else torch.empty((R, n_sub), dtype=torch.complex64, device=a.device)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_cfr(ctx.h, _ptr(rx_offsets), R, _ptr(a), _ptr(tau), float(f_center_hz), float(delta_f_hz),
+                             int(n_sub), _ptr(H)), "rt_cfr")
+    return H
+
+
+def cfr_backward(ctx: Context, rx_offsets, tau, f_center_hz, delta_f_hz, n_sub, grad_H,
+                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    R = rx_offsets.shape[0] - 1
+    ga = out if out is not None else torch.empty(tau.shape[0], dtype=torch.complex64, device=tau.device)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_cfr_backward(ctx.h, _ptr(rx_offsets), R, _ptr(tau), float(f_center_hz), float(delta_f_hz),
+                                      int(n_sub), _ptr(grad_H.contiguous()), _ptr(ga)), "rt_cfr_backward")
+    return ga
+
+
+def cfr_power_mse_fused(ctx: Context, rx_offsets, a, tau, f_center_hz, delta_f_hz, n_sub, target_power, rx_weight,
+                        loss=None, grad_a=None, H=None):
+    """CFR + power MSE + CFR adjoint in one launch (rt_cfr_power_mse_fused)."""
+    R = rx_offsets.shape[0] - 1
+    loss = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=a.device)
+    grad_a = grad_a if grad_a is not None else torch.empty_like(a)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_cfr_power_mse_fused(ctx.h, _ptr(rx_offsets), R, _ptr(a), _ptr(tau), float(f_center_hz),
+                                             float(delta_f_hz), int(n_sub), _ptr(target_power), _ptr(rx_weight),
+                                             _ptr(loss), _ptr(grad_a), _ptr(H)), "rt_cfr_power_mse_fused")
+    return loss, grad_a, H

@@ -1,0 +1,89 @@
+"""torch.autograd glue over the library's hand-written adjoint kernels.
+
+The calibration of Algorithm 1 (arXiv 2311.18558, Sec. III-G) differentiates the
+field computation with the path geometry held fixed (Sec. II-F): gradients flow
+from the loss through the CFR (rt_cfr_backward or the fused kernel) into the
+path coefficients and from there into eps_r, sigma (rt_eval_fields_backward).
+PyTorch only stores the parameters and runs the optimiser.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import api
+
+
+class EvalFields(torch.autograd.Function):
+    """a = eval_fields(eps_r, sigma) with the hand-written adjoint as backward."""
+
+    @staticmethod
+    def forward(fctx, eps_r, sigma, ctx, paths, freq_hz, gain_tx, gain_rx, per_triangle):
+        eps_r = eps_r.contiguous()
+        sigma = sigma.contiguous()
+        a = api.eval_fields(ctx, paths, eps_r, sigma, freq_hz, gain_tx, gain_rx, per_triangle)
+        fctx.save_for_backward(eps_r, sigma)
+        fctx.args = (ctx, paths, freq_hz, gain_tx, gain_rx, per_triangle)
+        return a
+
+    @staticmethod
+    def backward(fctx, grad_a):
+        eps_r, sigma = fctx.saved_tensors
+        ctx, paths, freq_hz, gain_tx, gain_rx, per_triangle = fctx.args
+        ge, gs, _ = api.eval_fields_backward(ctx, paths, eps_r, sigma, freq_hz, grad_a.contiguous(),
+                                             gain_tx=gain_tx, gain_rx=gain_rx, per_triangle=per_triangle)
+        return ge, gs, None, None, None, None, None, None
+
+
+class Cfr(torch.autograd.Function):
+    """H = cfr(a) (Sec. II-A) with rt_cfr_backward as backward."""
+
+    @staticmethod
+    def forward(fctx, a, tau, rx_offsets, ctx, f_center_hz, delta_f_hz, n_sub):
+        H = api.cfr(ctx, rx_offsets, a.contiguous(), tau, f_center_hz, delta_f_hz, n_sub)
+        fctx.args = (ctx, rx_offsets, tau, f_center_hz, delta_f_hz, n_sub)
+        return H
+
+    @staticmethod
+    def backward(fctx, grad_H):
+        ctx, rx_offsets, tau, fc, df, n = fctx.args
+        return api.cfr_backward(ctx, rx_offsets, tau, fc, df, n, grad_H.contiguous()), None, None, None, None, None, None
+
+
+class CfrPowerMSE(torch.autograd.Function):
+    """Loss L = 1/(R N) sum (w_r (|H|^2 - P*))^2 of the CFR of a; the forward
+    launch also produces dL/da, which backward scales by the incoming gradient."""
+
+    @staticmethod
+    def forward(fctx, a, tau, rx_offsets, target_power, rx_weight, ctx, f_center_hz, delta_f_hz, n_sub):
+        loss, grad_a, _ = api.cfr_power_mse_fused(ctx, rx_offsets, a.contiguous(), tau, f_center_hz, delta_f_hz,
+                                                  n_sub, target_power, rx_weight)
+        fctx.save_for_backward(grad_a)
+        return loss[0]
+
+    @staticmethod
+    def backward(fctx, g):
+        (grad_a,) = fctx.saved_tensors
+        return grad_a * g, None, None, None, None, None, None, None, None
+
+
+class LogMaterials(torch.nn.Module):
+    """Per-material parameters in the log domain of Eq. trainable_materials_1/2:
+    sigma = exp(w_sigma), eps_r = 1 + exp(w_eps) (read-out vector v = 1, L = 1)."""
+
+    def __init__(self, eps_r_init, sigma_init):
+        super().__init__()
+        eps_r_init = torch.as_tensor(eps_r_init, dtype=torch.float32)
+        sigma_init = torch.as_tensor(sigma_init, dtype=torch.float32)
+        self.w_eps = torch.nn.Parameter(torch.log(eps_r_init - 1.0))
+        self.w_sigma = torch.nn.Parameter(torch.log(sigma_init))
+
+    def forward(self):
+        return 1.0 + torch.exp(self.w_eps), torch.exp(self.w_sigma)
+
+
+def calibration_loss(ctx, paths, eps_r, sigma, target_power, rx_weight, freq_hz, f_center_hz, delta_f_hz, n_sub,
+                     gain_tx=1.0, gain_rx=1.0, per_triangle=False):
+    """One forward pass of Algorithm 1's inner loop: RT(p; Omega) -> CFR -> loss."""
+    a = EvalFields.apply(eps_r, sigma, ctx, paths, freq_hz, gain_tx, gain_rx, per_triangle)
+    return CfrPowerMSE.apply(a, paths.tau, paths.rx_offsets, target_power, rx_weight, ctx, f_center_hz, delta_f_hz,
+                             n_sub)

@@ -1,0 +1,352 @@
+// Discrete CFR of arXiv 2311.18558, Sec. II-A:
+//   H[r, c] = sum_{i in r} a_i exp(-j 2 pi (f_0 + c df) tau_i),  c = 0..N-1,
+// with f_0 = f_c - (N/2) df (column c holds subcarrier n = c - N/2), and its
+// adjoint g_a[i] = sum_c g_H[r, c] conj(exp(-j 2 pi (f_0 + c df) tau_i)).
+//
+// Split-Vandermonde evaluation: write c = N2 c1 + c2 (N2 | 256, N1 = N / N2).
+// Then exp(-j 2 pi c df tau) = A_i[c1] B_i[c2] with
+//   A_i[c1] = exp(-j 2 pi N2 c1 u_i),  B_i[c2] = exp(-j 2 pi c2 u_i),  u_i = df tau_i,
+// so a receiver needs N1 + N2 phasors per path instead of N, and the CFR is the
+// complex product (N1 x P) . (P x N2) of c_i A_i[c1] with B_i[c2].
+//
+// Phase accuracy: the only FP64 work per path is reducing f_0 tau_i and u_i to
+// their fractional parts (in cycles).  u is split as u_hi + u_lo with u_hi a
+// multiple of 2^-12, so m u_hi is exact in FP32 for every integer m < 4096 and
+// frac(m u_hi) + m u_lo carries ~1e-7 cycles of error; sin/cos(pi x) of the
+// doubled phase then gives each phasor to FP32 accuracy.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <type_traits>
+
+#include "rt_internal.cuh"
+
+namespace {
+
+constexpr int CFR_THREADS = 256;
+constexpr int CH = 32;   // paths per shared-memory chunk
+
+struct PathPhase {
+    float p0;     // frac(f_0 tau) in cycles
+    float uhi;    // multiple of 2^-12, |uhi| <= 1/2
+    float ulo;
+};
+
+__device__ __forceinline__ PathPhase path_phase(double tau, double f0, double df) {
+    PathPhase p;
+    double x = f0 * tau;
+    p.p0 = (float)(x - rint(x));
+    double u = df * tau;
+    double ur = u - rint(u);
+    double hi = rint(ur * 4096.0) * (1.0 / 4096.0);
+    p.uhi = (float)hi;
+    p.ulo = (float)(ur - hi);
+    return p;
+}
+
+// exp(-j 2 pi phase(m)), phase(m) = frac(m u_hi) + m u_lo (+ extra)
+__device__ __forceinline__ float2 phasor(const PathPhase& p, int m) {
+    float x = (float)m * p.uhi;
+    x = x - rintf(x);
+    x = x + (float)m * p.ulo;
+    float s, c;
+    sincospif(2.0f * x, &s, &c);
+    return make_float2(c, -s);
+}
+
+__device__ __forceinline__ float2 base_phasor(const PathPhase& p) {
+    float s, c;
+    sincospif(2.0f * p.p0, &s, &c);
+    return make_float2(c, -s);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {   // a * conj(b)
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+
+struct CfrShape {
+    int N, N1, N2;
+    double f0, df;
+};
+
+// Forward CFR of receiver r into registers acc[OPT]: thread t owns columns
+// c = t + 256 m (m < OPT); with N2 | 256 all of them share c2 = t % N2.
+template <int OPT>
+__device__ __forceinline__ void cfr_rx_forward(const CfrShape& S, int64_t i0, int64_t i1, const float2* __restrict__ a,
+                                               const double* __restrict__ tau, float2* sA, float2* sB, PathPhase* sP,
+                                               float2 (&acc)[OPT]) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int m = 0; m < OPT; ++m) acc[m] = make_float2(0.0f, 0.0f);
+    const int c2 = t % S.N2;
+    for (int64_t base = i0; base < i1; base += CH) {
+        const int n = (int)min((int64_t)CH, i1 - base);
+        __syncthreads();
+        if (t < n) {
+            PathPhase p = path_phase(tau[base + t], S.f0, S.df);
+            sP[t] = p;
+            // c_i = a_i exp(-j 2 pi f_0 tau_i), kept in the B row slot N2 (scratch)
+            sB[t * (S.N2 + 1) + S.N2] = cmul(a[base + t], base_phasor(p));
+        }
+        __syncthreads();
+        for (int e = t; e < n * S.N2; e += CFR_THREADS) {
+            int ii = e / S.N2, k = e - ii * S.N2;
+            sB[ii * (S.N2 + 1) + k] = phasor(sP[ii], k);
+        }
+        for (int e = t; e < n * S.N1; e += CFR_THREADS) {
+            int ii = e / S.N1, k = e - ii * S.N1;
+            sA[ii * S.N1 + k] = cmul(sB[ii * (S.N2 + 1) + S.N2], phasor(sP[ii], k * S.N2));
+        }
+        __syncthreads();
+        for (int ii = 0; ii < n; ++ii) {
+            float2 b = sB[ii * (S.N2 + 1) + c2];
+#pragma unroll
+            for (int m = 0; m < OPT; ++m) {
+                int c = t + CFR_THREADS * m;
+                if (c < S.N) cfma(acc[m], sA[ii * S.N1 + c / S.N2], b);
+            }
+        }
+    }
+}
+
+// Adjoint for receiver r given g_H (N values in shared memory): one thread per
+// path, g_c = sum_c1 conj(A[c1]) sum_c2 g[c1, c2] conj(B[c2]), g_a = conj(phi) g_c.
+__device__ __forceinline__ void cfr_rx_backward(const CfrShape& S, int64_t i0, int64_t i1,
+                                                const double* __restrict__ tau, const float2* sG,
+                                                float2* __restrict__ grad_a) {
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += CFR_THREADS) {
+        PathPhase p = path_phase(tau[i], S.f0, S.df);
+        float2 B[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < S.N2) B[k] = phasor(p, k);
+        float2 acc = make_float2(0.0f, 0.0f);
+        for (int c1 = 0; c1 < S.N1; ++c1) {
+            float2 inner = make_float2(0.0f, 0.0f);
+            const float2* g = sG + c1 * S.N2;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (k < S.N2) {
+                    float2 gk = g[k];
+                    // inner += g * conj(B)
+                    inner.x = fmaf(gk.x, B[k].x, fmaf(gk.y, B[k].y, inner.x));
+                    inner.y = fmaf(gk.y, B[k].x, fmaf(-gk.x, B[k].y, inner.y));
+                }
+            float2 A = phasor(p, c1 * S.N2);
+            // acc += inner * conj(A)
+            acc.x = fmaf(inner.x, A.x, fmaf(inner.y, A.y, acc.x));
+            acc.y = fmaf(inner.y, A.x, fmaf(-inner.x, A.y, acc.y));
+        }
+        grad_a[i] = cmulc(acc, base_phasor(p));
+    }
+}
+
+template <int OPT>
+__global__ void __launch_bounds__(CFR_THREADS) k_cfr_fwd(CfrShape S, const int64_t* __restrict__ offs,
+                                                         const float2* __restrict__ a, const double* __restrict__ tau,
+                                                         float2* __restrict__ H) {
+    extern __shared__ float4 smem4[];
+    float2* sA = reinterpret_cast<float2*>(smem4);
+    float2* sB = sA + CH * S.N1;
+    PathPhase* sP = reinterpret_cast<PathPhase*>(sB + CH * (S.N2 + 1));
+    const int r = blockIdx.x;
+    float2 acc[OPT];
+    cfr_rx_forward<OPT>(S, offs[r], offs[r + 1], a, tau, sA, sB, sP, acc);
+#pragma unroll
+    for (int m = 0; m < OPT; ++m) {
+        int c = threadIdx.x + CFR_THREADS * m;
+        if (c < S.N) H[(int64_t)r * S.N + c] = acc[m];
+    }
+}
+
+__global__ void __launch_bounds__(CFR_THREADS) k_cfr_bwd(CfrShape S, const int64_t* __restrict__ offs,
+                                                         const double* __restrict__ tau, const float2* __restrict__ gH,
+                                                         float2* __restrict__ ga) {
+    extern __shared__ float4 smem4[];
+    float2* sG = reinterpret_cast<float2*>(smem4);
+    const int r = blockIdx.x;
+    for (int c = threadIdx.x; c < S.N; c += CFR_THREADS) sG[c] = gH[(int64_t)r * S.N + c];
+    __syncthreads();
+    cfr_rx_backward(S, offs[r], offs[r + 1], tau, sG, ga);
+}
+
+// Fused forward + power-MSE loss + adjoint for one receiver per CTA.  The loss
+// partial of each receiver goes to part[r]; the last CTA to finish (counter)
+// sums them in receiver order, so the loss is deterministic.
+template <int OPT>
+__global__ void __launch_bounds__(CFR_THREADS) k_cfr_fused(CfrShape S, const int64_t* __restrict__ offs, int R,
+                                                           const float2* __restrict__ a, const double* __restrict__ tau,
+                                                           const float* __restrict__ target, const float* __restrict__ w,
+                                                           float* __restrict__ loss, float2* __restrict__ ga,
+                                                           float2* __restrict__ H, double* __restrict__ part,
+                                                           unsigned int* __restrict__ done) {
+    extern __shared__ float4 smem4[];
+    float2* sA = reinterpret_cast<float2*>(smem4);
+    float2* sB = sA + CH * S.N1;
+    PathPhase* sP = reinterpret_cast<PathPhase*>(sB + CH * (S.N2 + 1));
+    float2* sG = reinterpret_cast<float2*>(sP + CH);
+    __shared__ double red[CFR_THREADS / 32];
+    __shared__ bool last;
+    const int r = blockIdx.x;
+    const int64_t i0 = offs[r], i1 = offs[r + 1];
+    float2 acc[OPT];
+    cfr_rx_forward<OPT>(S, i0, i1, a, tau, sA, sB, sP, acc);
+    const float wr = w[r];
+    const float inv_rn = 1.0f / ((float)R * (float)S.N);
+    double lsum = 0.0;
+#pragma unroll
+    for (int m = 0; m < OPT; ++m) {
+        int c = threadIdx.x + CFR_THREADS * m;
+        if (c < S.N) {
+            float2 h = acc[m];
+            if (H) H[(int64_t)r * S.N + c] = h;
+            float e = h.x * h.x + h.y * h.y - target[(int64_t)r * S.N + c];
+            float we = wr * e;
+            lsum += (double)(we * we);
+            float s = 4.0f * wr * wr * e * inv_rn;   // dL/dH = 4 w^2 (|H|^2 - P*) H / (R N)
+            sG[c] = make_float2(s * h.x, s * h.y);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < CFR_THREADS / 32; ++k) s += red[k];
+        part[r] = s;
+        __threadfence();
+        unsigned int prev = atomicAdd(done, 1u);
+        last = (prev == (unsigned)R - 1);
+    }
+    cfr_rx_backward(S, i0, i1, tau, sG, ga);
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        double s = 0.0;
+        for (int k = threadIdx.x; k < R; k += CFR_THREADS) s += ((volatile double*)part)[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int k = 0; k < CFR_THREADS / 32; ++k) tot += red[k];
+            *loss = (float)(tot * (double)inv_rn);
+            *done = 0u;   // ready for the next launch
+        }
+    }
+}
+
+bool make_shape(int n_sub, double fc, double df, CfrShape& S) {
+    if (n_sub < 1 || n_sub > 4096 || (n_sub > 1 && (n_sub & 1))) return false;
+    S.N = n_sub;
+    S.N2 = 1;
+    while (S.N2 < 16 && n_sub % (S.N2 * 2) == 0) S.N2 *= 2;
+    S.N1 = n_sub / S.N2;
+    S.f0 = fc - (double)(n_sub / 2) * df;
+    S.df = df;
+    return true;
+}
+
+size_t fwd_smem(const CfrShape& S) {
+    return (size_t)CH * S.N1 * 8 + (size_t)CH * (S.N2 + 1) * 8 + (size_t)CH * sizeof(PathPhase) + 16;
+}
+
+template <typename F>
+rt_status dispatch_opt(rt_ctx* ctx, int N, F&& f) {
+    int opt = (N + CFR_THREADS - 1) / CFR_THREADS;
+    if (opt <= 1) return f(std::integral_constant<int, 1>());
+    if (opt <= 2) return f(std::integral_constant<int, 2>());
+    if (opt <= 4) return f(std::integral_constant<int, 4>());
+    if (opt <= 8) return f(std::integral_constant<int, 8>());
+    return f(std::integral_constant<int, 16>());
+}
+
+}  // namespace
+
+static rt_status check_cfr(rt_ctx* ctx, const int64_t* offs, int32_t n_rx, const double* tau, int32_t n_sub, double fc,
+                           double df, CfrShape& S) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (!offs || !tau) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null device pointer");
+    if (n_rx < 1) return rt_fail(ctx, RT_ERR_INVALID_ARG, "n_rx must be >= 1");
+    if (!(fc > 0.0) || !(df >= 0.0) || !std::isfinite(fc) || !std::isfinite(df))
+        return rt_fail(ctx, RT_ERR_INVALID_ARG, "frequencies must be finite, f_c > 0, df >= 0");
+    if (!make_shape(n_sub, fc, df, S)) return rt_fail(ctx, RT_ERR_INVALID_ARG, "n_sub must be 1 or even and <= 4096");
+    return RT_OK;
+}
+
+template <typename K>
+static rt_status set_smem(rt_ctx* ctx, K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) RT_CK(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return RT_OK;
+}
+
+extern "C" __attribute__((visibility("default"))) rt_status rt_cfr(rt_ctx* ctx, const int64_t* rx_offsets_dev, int32_t n_rx, const void* a_dev,
+                            const double* tau_dev, double f_center_hz, double delta_f_hz, int32_t n_sub, void* H_dev) {
+    CfrShape S;
+    rt_status s = check_cfr(ctx, rx_offsets_dev, n_rx, tau_dev, n_sub, f_center_hz, delta_f_hz, S);
+    if (s != RT_OK) return s;
+    if (!a_dev || !H_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null device pointer");
+    const size_t smem = fwd_smem(S);
+    return dispatch_opt(ctx, S.N, [&](auto opt) -> rt_status {
+        constexpr int O = decltype(opt)::value;
+        rt_status e = set_smem(ctx, k_cfr_fwd<O>, smem);
+        if (e != RT_OK) return e;
+        k_cfr_fwd<O><<<n_rx, CFR_THREADS, smem, ctx->stream>>>(S, rx_offsets_dev, (const float2*)a_dev, tau_dev,
+                                                                (float2*)H_dev);
+        RT_CK_LAUNCH(ctx);
+        return RT_OK;
+    });
+}
+
+extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_backward(rt_ctx* ctx, const int64_t* rx_offsets_dev, int32_t n_rx, const double* tau_dev,
+                                     double f_center_hz, double delta_f_hz, int32_t n_sub, const void* grad_H_dev,
+                                     void* grad_a_dev) {
+    CfrShape S;
+    rt_status s = check_cfr(ctx, rx_offsets_dev, n_rx, tau_dev, n_sub, f_center_hz, delta_f_hz, S);
+    if (s != RT_OK) return s;
+    if (!grad_H_dev || !grad_a_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null device pointer");
+    const size_t smem = (size_t)S.N * 8;
+    s = set_smem(ctx, k_cfr_bwd, smem);
+    if (s != RT_OK) return s;
+    k_cfr_bwd<<<n_rx, CFR_THREADS, smem, ctx->stream>>>(S, rx_offsets_dev, tau_dev, (const float2*)grad_H_dev,
+                                                        (float2*)grad_a_dev);
+    RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}
+
+// Loss partials and completion counter of the fused kernel (api.cu).
+rt_status rt_cfr_fused_scratch(rt_ctx* ctx, int R, double** part, unsigned int** done);
+
+extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fused(rt_ctx* ctx, const int64_t* rx_offsets_dev, int32_t n_rx,
+                                            const void* a_dev, const double* tau_dev, double f_center_hz,
+                                            double delta_f_hz, int32_t n_sub, const float* target_power_dev,
+                                            const float* rx_weight_dev, float* loss_dev, void* grad_a_dev,
+                                            void* H_dev) {
+    CfrShape S;
+    rt_status s = check_cfr(ctx, rx_offsets_dev, n_rx, tau_dev, n_sub, f_center_hz, delta_f_hz, S);
+    if (s != RT_OK) return s;
+    if (!a_dev || !target_power_dev || !rx_weight_dev || !loss_dev || !grad_a_dev)
+        return rt_fail(ctx, RT_ERR_INVALID_ARG, "null device pointer");
+    double* part;
+    unsigned int* done;
+    s = rt_cfr_fused_scratch(ctx, n_rx, &part, &done);
+    if (s != RT_OK) return s;
+    const size_t smem = fwd_smem(S) + (size_t)S.N * 8;
+    return dispatch_opt(ctx, S.N, [&](auto opt) -> rt_status {
+        constexpr int O = decltype(opt)::value;
+        rt_status e = set_smem(ctx, k_cfr_fused<O>, smem);
+        if (e != RT_OK) return e;
+        k_cfr_fused<O><<<n_rx, CFR_THREADS, smem, ctx->stream>>>(
+            S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, target_power_dev, rx_weight_dev, loss_dev,
+            (float2*)grad_a_dev, (float2*)H_dev, part, done);
+        RT_CK_LAUNCH(ctx);
+        return RT_OK;
+    });
+}

@@ -1,0 +1,345 @@
+// Per-path geometry records and the field computation of arXiv 2311.18558,
+// Sec. II-B..D (Eq. cfr_cont, rel1, basis_transform, rel2, init,
+// specular_reflection, fresnel-1/2), with its adjoint (Sec. III, Algorithm 1:
+// gradients w.r.t. eps_r, sigma and the antenna gains, geometry held fixed).
+//
+// Record kernel (once per trace): FP64 directions k_j = (s_j - s_{j-1}) / d_j,
+// delay tau = sum d_j / c, total length L, cos(theta_i) of every bounce and the
+// real 2x2 basis changes D_1 .. D_{q+1}, stored FP32 in depth-slot-major SoA.
+//
+// Field kernels (every calibration step; HBM-bound streaming of the records):
+//   v = D_1 C_T;  v <- D_{j+1} diag(r_perp,j, r_par,j) v  (j = 1..q);
+//   a = lambda/(4 pi) sqrt(g_T g_R) / L * C_R^T v,
+// with C_T = C_R = [1, 0] (vertical polarisation, zeta = 0, isotropic gain).
+// The product of the spherical spreading factors of a chain of planar
+// reflections is 1/L; the carrier phase exp(-j 2 pi f tau) is kept in tau.
+#include <cuda_runtime.h>
+
+#include "rt_internal.cuh"
+
+namespace {
+
+struct D3 {
+    double x, y, z;
+};
+__device__ __forceinline__ D3 d3(double x, double y, double z) { return D3{x, y, z}; }
+__device__ __forceinline__ D3 sub(D3 a, D3 b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ D3 scl(double s, D3 a) { return d3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ double dotd(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ D3 crossd(D3 a, D3 b) {
+    return d3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ D3 unitd(D3 a) { return scl(1.0 / sqrt(dotd(a, a)), a); }
+
+// theta_hat, phi_hat of direction k (unit), written without trigonometry:
+// cos(theta) = k_z, sin(theta) = |k_xy|, (cos phi, sin phi) = k_xy / |k_xy|,
+// phi = 0 for a vertical direction.
+__device__ __forceinline__ void sph_basis(D3 k, D3* th, D3* ph) {
+    double st = sqrt(k.x * k.x + k.y * k.y);
+    double cp = 1.0, sp = 0.0;
+    if (st > 0.0) {
+        cp = k.x / st;
+        sp = k.y / st;
+    }
+    *th = d3(k.z * cp, k.z * sp, -st);
+    *ph = d3(-sp, cp, 0.0);
+}
+
+__global__ void k_records(int64_t P, int D, const double* __restrict__ pts, const int32_t* __restrict__ depth,
+                          const int32_t* __restrict__ tri, const double* __restrict__ tri_n64, double* tau,
+                          float* len, float* cosv, float4* Dm) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        const int q = depth[i];
+        const double* pp = pts + (int64_t)i * (D + 2) * 3;
+        D3 prev = d3(pp[0], pp[1], pp[2]);
+        D3 k[RT_MAX_DEPTH + 2];
+        double L = 0.0;
+        for (int j = 1; j <= q + 1; ++j) {
+            D3 cur = d3(pp[3 * j], pp[3 * j + 1], pp[3 * j + 2]);
+            D3 dv = sub(cur, prev);
+            double dj = sqrt(dotd(dv, dv));
+            k[j] = scl(1.0 / dj, dv);
+            L += dj;
+            prev = cur;
+        }
+        tau[i] = L / RT_C0;
+        len[i] = (float)L;
+        D3 out_p, out_q;
+        sph_basis(k[1], &out_p, &out_q);
+        for (int j = 1; j <= q; ++j) {
+            int t = tri[(int64_t)(j - 1) * P + i];
+            D3 n = d3(tri_n64[4 * t], tri_n64[4 * t + 1], tri_n64[4 * t + 2]);
+            if (dotd(k[j], n) > 0.0) n = scl(-1.0, n);
+            double cos_i = -dotd(k[j], n);
+            D3 cr = crossd(k[j], n);
+            D3 e_perp;
+            if (sqrt(dotd(cr, cr)) > 1e-12) {
+                e_perp = unitd(cr);
+            } else {
+                // normal incidence: any transverse unit vector serves; continue the
+                // previous outgoing p-vector
+                e_perp = unitd(sub(out_p, scl(dotd(out_p, k[j]), k[j])));
+            }
+            D3 in_q = crossd(e_perp, k[j]);
+            Dm[(int64_t)(j - 1) * P + i] = make_float4((float)dotd(e_perp, out_p), (float)dotd(e_perp, out_q),
+                                                       (float)dotd(in_q, out_p), (float)dotd(in_q, out_q));
+            cosv[(int64_t)(j - 1) * P + i] = (float)cos_i;
+            out_p = e_perp;
+            out_q = crossd(e_perp, k[j + 1]);
+        }
+        D3 rp, rq;
+        sph_basis(scl(-1.0, k[q + 1]), &rp, &rq);
+        Dm[(int64_t)q * P + i] = make_float4((float)dotd(rp, out_p), (float)dotd(rp, out_q), (float)dotd(rq, out_p),
+                                             (float)dotd(rq, out_q));
+    }
+}
+
+// ------------------------------------------------------------------ complex FP32
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
+    float inv = 1.0f / (b.x * b.x + b.y * b.y);
+    return make_float2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
+}
+// Principal square root from |z|: sqrt(z) = t + j y/(2t) with t = sqrt((|z| + x)/2)
+// for x >= 0, and the mirrored form for x < 0 (no cancellation either way).
+__device__ __forceinline__ float2 csqrt(float2 z) {
+    float r = hypotf(z.x, z.y);
+    if (z.x >= 0.0f) {
+        float t = sqrtf(0.5f * (r + z.x));
+        return make_float2(t, t > 0.0f ? z.y / (2.0f * t) : 0.0f);
+    }
+    float t = sqrtf(0.5f * (r - z.x));
+    return make_float2(fabsf(z.y) / (2.0f * t), copysignf(t, z.y));
+}
+
+// Fresnel coefficients (Eq. fresnel-1/2) and their derivatives w.r.t. eta:
+//   d r_perp / d eta = -c / (s (c + s)^2),  d r_par / d eta = c (eta - 2 sin^2) / (s (eta c + s)^2),
+// s = sqrt(eta - sin^2 theta), c = cos theta.
+template <bool GRAD>
+__device__ __forceinline__ void fresnel(float2 eta, float c, float2& rp, float2& rl, float2& drp, float2& drl) {
+    float s2 = fmaxf(0.0f, 1.0f - c * c);
+    float2 s = csqrt(make_float2(eta.x - s2, eta.y));
+    float2 cps = make_float2(c + s.x, s.y);
+    float2 cms = make_float2(c - s.x, -s.y);
+    rp = cdiv(cms, cps);
+    float2 ec = cscale(c, eta);
+    float2 ecs = cadd(ec, s);
+    rl = cdiv(make_float2(ec.x - s.x, ec.y - s.y), ecs);
+    if (GRAD) {
+        drp = cdiv(make_float2(-c, 0.0f), cmul(s, cmul(cps, cps)));
+        drl = cdiv(cscale(c, make_float2(eta.x - 2.0f * s2, eta.y)), cmul(s, cmul(ecs, ecs)));
+    }
+}
+
+struct FieldArgs {
+    int64_t P;
+    int D;
+    const int32_t* depth;
+    const int32_t* tri;
+    const float* len;
+    const float* cosv;
+    const float4* Dm;
+    const double* tau;
+    const int32_t* tri_material;
+    const uint8_t* is_pec;
+    const float* eps;
+    const float* sig;
+    int per_tri;
+    float inv_eps0w;   // 1 / (eps0 omega)
+    float amp;         // lambda / (4 pi) sqrt(g_T g_R)
+};
+
+__global__ void __launch_bounds__(256) k_fields_fwd(FieldArgs A, float2* __restrict__ a_out, double* __restrict__ tau_out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.P; i += (int64_t)gridDim.x * blockDim.x) {
+        const int q = __ldg(A.depth + i);
+        // slot s of the record holds D_{s+1}; v = D_1 C_T with C_T = [1, 0]
+        float4 d = __ldg(A.Dm + i);
+        float2 v0 = make_float2(d.x, 0.0f), v1 = make_float2(d.z, 0.0f);
+#pragma unroll
+        for (int j = 0; j < RT_MAX_DEPTH; ++j) {
+            if (j < q) {
+                int t = __ldg(A.tri + (int64_t)j * A.P + i);
+                int mat = __ldg(A.tri_material + t);
+                int m = A.per_tri ? t : mat;
+                float2 rp, rl, unused;
+                if (__ldg(A.is_pec + mat)) {
+                    rp = make_float2(-1.0f, 0.0f);
+                    rl = make_float2(1.0f, 0.0f);
+                } else {
+                    float2 eta = make_float2(__ldg(A.eps + m), -__ldg(A.sig + m) * A.inv_eps0w);
+                    fresnel<false>(eta, __ldg(A.cosv + (int64_t)j * A.P + i), rp, rl, unused, unused);
+                }
+                float2 g0 = cmul(rp, v0), g1 = cmul(rl, v1);
+                float4 e = __ldg(A.Dm + (int64_t)(j + 1) * A.P + i);
+                v0 = cadd(cscale(e.x, g0), cscale(e.y, g1));
+                v1 = cadd(cscale(e.z, g0), cscale(e.w, g1));
+            }
+        }
+        a_out[i] = cscale(A.amp / __ldg(A.len + i), v0);
+        if (tau_out) tau_out[i] = A.tau[i];
+    }
+}
+
+template <int MAXM>
+__global__ void __launch_bounds__(256) k_fields_bwd(FieldArgs A, const float2* __restrict__ ga, float* __restrict__ geps,
+                                                    float* __restrict__ gsig, float* __restrict__ ggain, float inv_gtx,
+                                                    float inv_grx, int n_mat) {
+    __shared__ float s_eps[MAXM > 0 ? MAXM : 1], s_sig[MAXM > 0 ? MAXM : 1], s_gain[2];
+    if (MAXM > 0)
+        for (int m = threadIdx.x; m < n_mat; m += blockDim.x) s_eps[m] = s_sig[m] = 0.0f;
+    if (threadIdx.x < 2) s_gain[threadIdx.x] = 0.0f;
+    __syncthreads();
+    float gain_acc = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.P; i += (int64_t)gridDim.x * blockDim.x) {
+        const int q = __ldg(A.depth + i);
+        const float scale = A.amp / __ldg(A.len + i);
+        float4 d = __ldg(A.Dm + i);
+        float2 v0 = make_float2(d.x, 0.0f), v1 = make_float2(d.z, 0.0f);
+        float2 in0[RT_MAX_DEPTH], in1[RT_MAX_DEPTH], rp[RT_MAX_DEPTH], rl[RT_MAX_DEPTH], drp[RT_MAX_DEPTH],
+            drl[RT_MAX_DEPTH];
+        int mid[RT_MAX_DEPTH];
+        bool pec[RT_MAX_DEPTH];
+#pragma unroll
+        for (int j = 0; j < RT_MAX_DEPTH; ++j) {
+            if (j < q) {
+                int t = __ldg(A.tri + (int64_t)j * A.P + i);
+                int mat = __ldg(A.tri_material + t);
+                int m = A.per_tri ? t : mat;
+                mid[j] = m;
+                pec[j] = __ldg(A.is_pec + mat) != 0;
+                if (pec[j]) {
+                    rp[j] = make_float2(-1.0f, 0.0f);
+                    rl[j] = make_float2(1.0f, 0.0f);
+                    drp[j] = drl[j] = make_float2(0.0f, 0.0f);
+                } else {
+                    float2 eta = make_float2(__ldg(A.eps + m), -__ldg(A.sig + m) * A.inv_eps0w);
+                    fresnel<true>(eta, __ldg(A.cosv + (int64_t)j * A.P + i), rp[j], rl[j], drp[j], drl[j]);
+                }
+                in0[j] = v0;
+                in1[j] = v1;
+                float2 g0 = cmul(rp[j], v0), g1 = cmul(rl[j], v1);
+                float4 e = __ldg(A.Dm + (int64_t)(j + 1) * A.P + i);
+                v0 = cadd(cscale(e.x, g0), cscale(e.y, g1));
+                v1 = cadd(cscale(e.z, g0), cscale(e.w, g1));
+            }
+        }
+        float4 last = __ldg(A.Dm + (int64_t)q * A.P + i);   // D_{q+1}
+        float2 a = cscale(scale, v0);
+        float2 g = __ldg(ga + i);
+        // Re(conj(g) a) / (2 g_T) and / (2 g_R) share Re(conj(g) a)
+        gain_acc += g.x * a.x + g.y * a.y;
+        // adjoint walk: l = scale * (row 0 of D_{q+1}) . Gamma_q D_q ... ; the row
+        // vector before bounce j is l_j, da/dr_perp_j = l_j[0] in0_j, da/dr_par_j = l_j[1] in1_j
+        float2 l0 = make_float2(scale * last.x, 0.0f), l1 = make_float2(scale * last.y, 0.0f);
+#pragma unroll
+        for (int j = RT_MAX_DEPTH - 1; j >= 0; --j) {
+            if (j < q) {
+                if (!pec[j]) {
+                    float2 da = cadd(cmul(cmul(l0, in0[j]), drp[j]), cmul(cmul(l1, in1[j]), drl[j]));
+                    // Re(conj(g) da) and Im(conj(g) da)
+                    float re = g.x * da.x + g.y * da.y;
+                    float im = g.x * da.y - g.y * da.x;
+                    float de = re, ds = im * A.inv_eps0w;   // da/dsigma = -j/(eps0 w) da/deta
+                    if (MAXM > 0) {
+                        atomicAdd(&s_eps[mid[j]], de);
+                        atomicAdd(&s_sig[mid[j]], ds);
+                    } else {
+                        if (geps) atomicAdd(geps + mid[j], de);
+                        if (gsig) atomicAdd(gsig + mid[j], ds);
+                    }
+                }
+                float2 h0 = cmul(l0, rp[j]), h1 = cmul(l1, rl[j]);
+                float4 e = j == 0 ? d : __ldg(A.Dm + (int64_t)j * A.P + i);
+                l0 = cadd(cscale(e.x, h0), cscale(e.z, h1));
+                l1 = cadd(cscale(e.y, h0), cscale(e.w, h1));
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) gain_acc += __shfl_down_sync(0xffffffffu, gain_acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_gain[0], gain_acc);
+    __syncthreads();
+    if (MAXM > 0) {
+        for (int m = threadIdx.x; m < n_mat; m += blockDim.x) {
+            if (geps && s_eps[m] != 0.0f) atomicAdd(geps + m, s_eps[m]);
+            if (gsig && s_sig[m] != 0.0f) atomicAdd(gsig + m, s_sig[m]);
+        }
+    }
+    if (threadIdx.x == 0 && ggain) {
+        atomicAdd(ggain + 0, 0.5f * s_gain[0] * inv_gtx);
+        atomicAdd(ggain + 1, 0.5f * s_gain[0] * inv_grx);
+    }
+}
+
+FieldArgs make_args(const rt_paths* p, const float* eps, const float* sig, int per_tri, double freq, float gtx,
+                    float grx) {
+    FieldArgs A;
+    A.P = p->P;
+    A.D = p->D;
+    A.depth = p->d_depth;
+    A.tri = p->d_tri;
+    A.len = p->d_len;
+    A.cosv = p->d_cos;
+    A.Dm = p->d_Dm;
+    A.tau = p->d_tau;
+    A.tri_material = p->scene->d_tri_material;
+    A.is_pec = p->scene->d_is_pec;
+    A.eps = eps;
+    A.sig = sig;
+    A.per_tri = per_tri;
+    A.inv_eps0w = (float)(1.0 / (RT_EPS0 * 2.0 * RT_PI * freq));
+    A.amp = (float)(RT_C0 / freq / (4.0 * RT_PI) * std::sqrt((double)gtx * (double)grx));
+    return A;
+}
+
+int grid_for(const rt_ctx* ctx, int64_t n, int threads, int per_sm) {
+    int64_t g = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)ctx->num_sms * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+rt_status rt_launch_paths_records(rt_ctx* ctx, rt_paths* p) {
+    cudaStream_t st = ctx->stream;
+    const int64_t Pa = p->P > 0 ? p->P : 1;
+    RT_CK(ctx, cudaMallocAsync((void**)&p->d_tau, Pa * 8, st));
+    RT_CK(ctx, cudaMallocAsync((void**)&p->d_len, Pa * 4, st));
+    RT_CK(ctx, cudaMallocAsync((void**)&p->d_cos, Pa * p->D * 4, st));
+    RT_CK(ctx, cudaMallocAsync((void**)&p->d_Dm, Pa * (p->D + 1) * 16, st));
+    if (p->P == 0) return RT_OK;
+    k_records<<<grid_for(ctx, p->P, 128, 16), 128, 0, st>>>(p->P, p->D, p->d_pts, p->d_depth, p->d_tri,
+                                                           p->scene->d_tri_n64, p->d_tau, p->d_len, p->d_cos,
+                                                           p->d_Dm);
+    RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}
+
+rt_status rt_launch_fields_fwd(rt_ctx* ctx, const rt_paths* p, const float* eps, const float* sig, int per_tri,
+                               double freq, float gtx, float grx, float2* a, double* tau) {
+    if (p->P == 0) return RT_OK;
+    FieldArgs A = make_args(p, eps, sig, per_tri, freq, gtx, grx);
+    k_fields_fwd<<<grid_for(ctx, p->P, 256, 8), 256, 0, ctx->stream>>>(A, a, tau);
+    RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}
+
+rt_status rt_launch_fields_bwd(rt_ctx* ctx, const rt_paths* p, const float* eps, const float* sig, int per_tri,
+                               double freq, float gtx, float grx, const float2* ga, float* geps, float* gsig,
+                               float* ggain) {
+    if (p->P == 0) return RT_OK;
+    FieldArgs A = make_args(p, eps, sig, per_tri, freq, gtx, grx);
+    const int n_mat = per_tri ? p->scene->n_tris : p->scene->n_materials;
+    const int grid = grid_for(ctx, p->P, 256, 4);
+    if (!per_tri && n_mat <= 64)
+        k_fields_bwd<64><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx, n_mat);
+    else
+        k_fields_bwd<0><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx, n_mat);
+    RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}

@@ -1,0 +1,120 @@
+// Internal declarations of librt103 (GB300 / sm_103a).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "rt103.h"
+
+// ---------------------------------------------------------------- constants
+#define RT_C0 299792458.0              // speed of light [m/s] (CODATA)
+#define RT_EPS0 8.8541878128e-12       // vacuum permittivity [F/m] (CODATA)
+#define RT_PI 3.14159265358979323846
+#define RT_MAX_DEPTH 4
+#define RT_STACK 64                    // BVH traversal stack entries per thread
+#define RT_MAX_VISITS (1 << 20)        // node-visit bound of one traversal
+
+// ---------------------------------------------------------------- handles
+struct rt_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int32_t* d_status = nullptr;       // sticky device status word (first error wins)
+    // reusable scratch arena (grown on demand, freed with the context)
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // pinned host word for small readbacks
+    int64_t* h_pinned = nullptr;
+};
+
+// BVH2 node holding the boxes of both children (64 bytes).
+//   a = (c0.lo.x, c0.lo.y, c0.lo.z, c0.hi.x)
+//   b = (c0.hi.y, c0.hi.z, c1.lo.x, c1.lo.y)
+//   c = (c1.lo.z, c1.hi.x, c1.hi.y, c1.hi.z)
+//   d = (ref0, ref1, count0, count1): count > 0 -> leaf over BVH-ordered
+//       triangles [ref, ref + count); count == 0 -> inner node index ref.
+struct __align__(16) BvhNode {
+    float4 a, b, c;
+    int4 d;
+};
+
+struct rt_scene {
+    rt_ctx* ctx = nullptr;
+    int n_tris = 0, n_nodes = 0, n_materials = 0;
+    double diag = 0.0;
+    double eps = 0.0;                  // 1e-6 * diag: hit and segment guard [m]
+    BvhNode* d_nodes = nullptr;
+    float4* d_bvh_tris = nullptr;      // 3 float4 per triangle in BVH order: v0 (w = id bits), v1, v2
+    float4* d_tri_v = nullptr;         // 3 float4 per triangle in original order: v0, v1, v2
+    float4* d_tri_bary = nullptr;      // 3 float4 per triangle: plane (n, n.v0), g0 (h0), g1 (h1) (FP32)
+    double* d_tri_n64 = nullptr;       // 4 doubles per triangle: unit normal (FP64), n.v0
+    int32_t* d_tri_material = nullptr;
+    uint8_t* d_is_pec = nullptr;
+    size_t hash_cap = 1u << 20;        // learned dedup table capacity
+    size_t queue_cap = 1u << 20;       // learned visibility-queue capacity
+};
+
+struct rt_paths {
+    const rt_scene* scene = nullptr;
+    cudaStream_t stream = nullptr;     // stream the paths were made on (used to free them)
+    int64_t P = 0, K = 0;
+    int D = 0, R = 0;
+    int64_t* d_rx_offsets = nullptr;   // R + 1
+    int32_t* d_rx = nullptr;           // P
+    int32_t* d_depth = nullptr;        // P
+    int32_t* d_tri = nullptr;          // D x P (slot-major), -1 padded
+    double* d_tau = nullptr;           // P
+    float* d_len = nullptr;            // P
+    float* d_cos = nullptr;            // D x P, cos(theta_i) of bounce j
+    float4* d_Dm = nullptr;            // (D + 1) x P basis changes D_1 .. D_{q+1} (row major 2x2)
+    double* d_pts = nullptr;           // P x (D + 2) x 3
+    uint64_t* d_cand = nullptr;        // K packed candidate keys
+};
+
+// ---------------------------------------------------------------- error helpers
+rt_status rt_fail(rt_ctx* ctx, rt_status st, const char* fmt, ...);
+rt_status rt_cuda_fail(rt_ctx* ctx, cudaError_t e, const char* what);
+// Grow the context scratch arena to at least `bytes`; returns its base.
+rt_status rt_scratch(rt_ctx* ctx, size_t bytes, void** base);
+int32_t* rt_status_ptr(rt_ctx* ctx);
+
+#define RT_CK(ctx, call)                                              \
+    do {                                                              \
+        cudaError_t _e = (call);                                      \
+        if (_e != cudaSuccess) return rt_cuda_fail((ctx), _e, #call); \
+    } while (0)
+
+#define RT_CK_LAUNCH(ctx) RT_CK(ctx, cudaGetLastError())
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ void rt_set_status(int32_t* st, int32_t code) {
+    if (st) atomicCAS(st, 0, code);
+}
+
+// Pack / unpack triangle sequences: id+1 in 16-bit fields, first bounce in the
+// most significant field, 0 = no bounce.
+__host__ __device__ __forceinline__ uint64_t rt_key_push(uint64_t key, int depth_before, int tri) {
+    return key | ((uint64_t)(tri + 1) << (48 - 16 * depth_before));
+}
+__host__ __device__ __forceinline__ int rt_key_depth(uint64_t key) {
+    int q = 0;
+    for (int j = 0; j < 4; ++j) q += ((key >> (48 - 16 * j)) & 0xffffull) != 0;
+    return q;
+}
+__host__ __device__ __forceinline__ int rt_key_tri(uint64_t key, int j) {
+    return (int)((key >> (48 - 16 * j)) & 0xffffull) - 1;
+}
+
+// Kernel launchers (defined in the .cu files).
+rt_status rt_launch_fields_fwd(rt_ctx* ctx, const rt_paths* p, const float* eps, const float* sig,
+                               int per_tri, double freq, float gtx, float grx, float2* a, double* tau);
+rt_status rt_launch_fields_bwd(rt_ctx* ctx, const rt_paths* p, const float* eps, const float* sig,
+                               int per_tri, double freq, float gtx, float grx, const float2* ga,
+                               float* geps, float* gsig, float* ggain);
+// Geometry records (delay, length, cos(theta_i), basis changes) of every path
+// from its points and triangles (d_pts, d_tri, d_depth must be filled).
+rt_status rt_launch_paths_records(rt_ctx* ctx, rt_paths* p);

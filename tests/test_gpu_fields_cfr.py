@@ -1,0 +1,203 @@
+"""GPU field, CFR and adjoint kernels vs the FP64 oracle.
+
+Tolerances (FP32 GPU vs FP64 oracle): per-path |a - a*| / |a*| <= 1e-4; CFR
+normwise per receiver <= 1e-4; gradients normwise <= 1e-4; delays FP64.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenegen
+from gpu_helpers import assert_same_paths, gpu_trace, normwise_rows, oracle_trace, rel_err_per_item
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import paper_2311_18558_gb300 as rt
+    return rt
+
+
+@pytest.fixture(scope="module")
+def ctx(rt):
+    return rt.Context(0)
+
+
+def _dev(x, dtype):
+    return torch.as_tensor(np.asarray(x), dtype=dtype, device="cuda").contiguous()
+
+
+@pytest.fixture(scope="module")
+def indoor(rt, ctx):
+    sc = scenegen.indoor_diff()
+    rx = sc.rx[::16]
+    scene, p, ex = gpu_trace(rt, ctx, sc, n_rays=200_000, rx=rx)
+    o, tr = oracle_trace(sc, n_rays=200_000, rx=rx)
+    assert_same_paths(ex, tr, o.diag)
+    sc2 = sc.subset_rx(np.arange(0, sc.n_rx, 16))
+    return sc2, scene, p, ex, oracle.OracleScene(sc2), tr
+
+
+def test_fields_traced_paths(rt, ctx, indoor):
+    sc, scene, p, ex, o, tr = indoor
+    a = rt.eval_fields(ctx, p, _dev(sc.eps_r, torch.float32), _dev(sc.sigma, torch.float32), sc.freq_hz,
+                       1.7, 0.6).cpu().numpy()
+    a_ref = o.fields(tr, gain_tx=1.7, gain_rx=0.6)
+    err = rel_err_per_item(a, a_ref)
+    assert err.max() <= 1e-4, err.max()
+
+
+def test_fields_imported_paths_and_depths(rt, ctx):
+    # paths built by the oracle, imported into the library: isolates the field kernel
+    sc = scenegen.tiny_box()
+    o, tr = oracle_trace(sc, n_rays=100_000, depth=2)
+    scene = rt.Scene.from_synthetic(ctx, sc)
+    p = rt.import_paths(ctx, scene, tr["rx"], tr["depth"], tr["seq"], tr["pts"], sc.n_rx)
+    assert np.array_equal(p.rx_offsets.cpu().numpy(), tr["rx_offsets"])
+    np.testing.assert_allclose(p.tau.cpu().numpy(), tr["tau"], rtol=1e-14)
+    for eps, sig in [(5.24, 0.0462), (1.0, 0.0), (80.0, 4.0)]:
+        e = np.array([eps], np.float32)
+        s = np.array([sig], np.float32)
+        a = rt.eval_fields(ctx, p, _dev(e, torch.float32), _dev(s, torch.float32), sc.freq_hz).cpu().numpy()
+        a_ref = o.fields(tr, eps_r=e, sigma=s)
+        # r = 0 exactly for eta = 1: compare those entries against the largest path
+        nz = np.abs(a_ref) > 1e-6 * np.abs(a_ref).max()
+        assert rel_err_per_item(a[nz], a_ref[nz]).max() <= 1e-4
+        assert np.abs(a[~nz]).max(initial=0) <= 1e-6 * np.abs(a_ref).max()
+
+
+def test_fields_pec_city(rt, ctx):
+    sc = scenegen.street_canyon()
+    rx = sc.rx[::32]
+    scene, p, ex = gpu_trace(rt, ctx, sc, n_rays=300_000, rx=rx)
+    o, tr = oracle_trace(sc, n_rays=300_000, rx=rx)
+    assert_same_paths(ex, tr, o.diag)
+    a = rt.eval_fields(ctx, p, _dev(sc.eps_r, torch.float32), _dev(sc.sigma, torch.float32), sc.freq_hz).cpu().numpy()
+    a_ref = oracle.OracleScene(sc.subset_rx(np.arange(0, sc.n_rx, 32))).fields(tr)
+    assert rel_err_per_item(a, a_ref).max() <= 1e-4
+
+
+def test_fields_per_triangle(rt, ctx):
+    sc = scenegen.room_corridor(n_rx=32)
+    scene, p, ex = gpu_trace(rt, ctx, sc, n_rays=100_000)
+    o, tr = oracle_trace(sc, n_rays=100_000)
+    assert_same_paths(ex, tr, o.diag)
+    a = rt.eval_fields(ctx, p, _dev(sc.eps_r, torch.float32), _dev(sc.sigma, torch.float32), sc.freq_hz,
+                       per_triangle=True).cpu().numpy()
+    a_ref = o.fields(tr)
+    assert rel_err_per_item(a, a_ref).max() <= 1e-4
+    rng = np.random.default_rng(0)
+    g = (rng.normal(size=len(a)) + 1j * rng.normal(size=len(a))).astype(np.complex64)
+    ge, gs, gg = rt.eval_fields_backward(ctx, p, _dev(sc.eps_r, torch.float32), _dev(sc.sigma, torch.float32),
+                                         sc.freq_hz, _dev(g, torch.complex64), per_triangle=True)
+    re, rs, rg = o.fields_grad(tr, g.astype(np.complex128))
+    for x, r in ((ge, re), (gs, rs), (gg, rg)):
+        x = x.cpu().numpy()
+        assert np.linalg.norm(x - r) <= 1e-4 * np.linalg.norm(r)
+
+
+def test_fields_backward(rt, ctx, indoor):
+    sc, scene, p, ex, o, tr = indoor
+    rng = np.random.default_rng(1)
+    g = (rng.normal(size=p.n_paths) + 1j * rng.normal(size=p.n_paths)).astype(np.complex64)
+    ge, gs, gg = rt.eval_fields_backward(ctx, p, _dev(sc.eps_r, torch.float32), _dev(sc.sigma, torch.float32),
+                                         sc.freq_hz, _dev(g, torch.complex64), gain_tx=1.3, gain_rx=0.9)
+    re, rs, rg = o.fields_grad(tr, g.astype(np.complex128), gain_tx=1.3, gain_rx=0.9)
+    for x, r in ((ge, re), (gs, rs), (gg, rg)):
+        x = x.cpu().numpy()
+        assert np.linalg.norm(x - r) <= 1e-4 * np.linalg.norm(r), (x, r)
+
+
+@pytest.mark.parametrize("n_sub", [1, 2, 16, 64, 256, 1024, 4096])
+def test_cfr_forward_backward(rt, ctx, n_sub):
+    a, tau, offs = scenegen.random_cfr_inputs(11 + n_sub, 37, 40, empty_every=7)
+    fc, df = 1.272e9, 50e6 / max(n_sub, 1)
+    H = rt.cfr(ctx, _dev(offs, torch.int64), _dev(a, torch.complex64), _dev(tau, torch.float64), fc, df,
+               n_sub).cpu().numpy()
+    Href = oracle.cfr(a.astype(np.complex128), tau, offs, fc, df, n_sub)
+    num, den = normwise_rows(H, Href)
+    nz = den > 0
+    assert (num[nz] / den[nz]).max() <= 1e-4
+    assert np.all(H[~nz] == 0)
+    rng = np.random.default_rng(n_sub)
+    gH = (rng.normal(size=H.shape) + 1j * rng.normal(size=H.shape)).astype(np.complex64)
+    ga = rt.cfr_backward(ctx, _dev(offs, torch.int64), _dev(tau, torch.float64), fc, df, n_sub,
+                         _dev(gH, torch.complex64)).cpu().numpy()
+    ga_ref = oracle.cfr_grad(tau, offs, fc, df, n_sub, gH.astype(np.complex128))
+    assert np.linalg.norm(ga - ga_ref) <= 1e-4 * np.linalg.norm(ga_ref)
+
+
+def test_cfr_fused_loss_and_grad(rt, ctx):
+    a, tau, offs = scenegen.random_cfr_inputs(5, 64, 120, empty_every=9)
+    fc, df, N = 1.272e9, 50e6 / 1024, 1024
+    rng = np.random.default_rng(2)
+    Href = oracle.cfr(a.astype(np.complex128), tau, offs, fc, df, N)
+    T = (np.abs(Href) ** 2 * rng.uniform(0.5, 1.5, Href.shape)).astype(np.float32)
+    w = oracle.power_weights(T).astype(np.float32)
+    L_ref, gH = oracle.power_mse(Href, T, w)
+    ga_ref = oracle.cfr_grad(tau, offs, fc, df, N, gH)
+    Hd = torch.empty((64, N), dtype=torch.complex64, device="cuda")
+    for _ in range(2):   # twice: the completion counter must reset itself
+        loss, ga, H = rt.cfr_power_mse_fused(ctx, _dev(offs, torch.int64), _dev(a, torch.complex64),
+                                             _dev(tau, torch.float64), fc, df, N, _dev(T, torch.float32),
+                                             _dev(w, torch.float32), H=Hd)
+        assert abs(loss.item() - L_ref) <= 1e-4 * abs(L_ref)
+        ga = ga.cpu().numpy()
+        assert np.linalg.norm(ga - ga_ref) <= 1e-4 * np.linalg.norm(ga_ref)
+        num, den = normwise_rows(H.cpu().numpy(), Href)
+        assert (num[den > 0] / den[den > 0]).max() <= 1e-4
+
+
+def test_calibration_gradient_end_to_end(rt, ctx, indoor):
+    # autograd through the library kernels == the oracle's FP64 adjoint chain
+    sc, scene, p, ex, o, tr = indoor
+    fc, df, N = sc.f_center_hz, sc.delta_f_hz, sc.n_sub
+    a_gt = o.fields(tr)
+    T = np.abs(oracle.cfr(a_gt, tr["tau"], tr["rx_offsets"], fc, df, N)) ** 2
+    w = oracle.power_weights(T)
+    eps0 = np.full(8, 4.0, np.float32)
+    sig0 = np.full(8, 0.05, np.float32)
+    params = rt.LogMaterials(eps0, sig0).cuda()
+    eps, sig = params()
+    loss = rt.calibration_loss(ctx, p, eps, sig, _dev(T, torch.float32), _dev(w, torch.float32), sc.freq_hz, fc, df,
+                               N)
+    loss.backward()
+    a0 = o.fields(tr, eps_r=eps0, sigma=sig0)
+    L_ref, gH = oracle.power_mse(oracle.cfr(a0, tr["tau"], tr["rx_offsets"], fc, df, N), T, w)
+    ga = oracle.cfr_grad(tr["tau"], tr["rx_offsets"], fc, df, N, gH)
+    ge, gs, _ = o.fields_grad(tr, ga, eps_r=eps0, sigma=sig0)
+    # chain rule of the log parametrisation
+    g_weps = ge * (eps0 - 1.0)
+    g_wsig = gs * sig0
+    assert abs(loss.item() - L_ref) <= 1e-4 * L_ref
+    got_e = params.w_eps.grad.cpu().numpy()
+    got_s = params.w_sigma.grad.cpu().numpy()
+    assert np.linalg.norm(got_e - g_weps) <= 1e-4 * np.linalg.norm(g_weps)
+    assert np.linalg.norm(got_s - g_wsig) <= 1e-4 * np.linalg.norm(g_wsig)
+
+
+def test_full_size_calibration_sampled(rt, ctx):
+    # the full differentiation workload (1e6 rays, 1024 receivers, 1024 subcarriers)
+    # in the benchmark's launch configuration; the oracle checks a sample of receivers
+    sc = scenegen.indoor_diff()
+    scene, p, ex = gpu_trace(rt, ctx, sc)
+    a = rt.eval_fields(ctx, p, _dev(sc.eps_r, torch.float32), _dev(sc.sigma, torch.float32), sc.freq_hz)
+    H = rt.cfr(ctx, p.rx_offsets, a, p.tau, sc.f_center_hz, sc.delta_f_hz, sc.n_sub).cpu().numpy()
+    sample = np.arange(0, sc.n_rx, 97)
+    o, tr = oracle_trace(sc, rx=sc.rx[sample])
+    offs = ex["rx_offsets"]
+    for j, r in enumerate(sample):
+        sl = slice(offs[r], offs[r + 1])
+        tsl = slice(tr["rx_offsets"][j], tr["rx_offsets"][j + 1])
+        assert np.array_equal(ex["seq"][sl], tr["seq"][tsl])
+        assert np.array_equal(ex["depth"][sl], tr["depth"][tsl])
+    sc_s = sc.subset_rx(sample)
+    a_ref = oracle.OracleScene(sc_s).fields(tr)
+    a_gpu = a.cpu().numpy()
+    a_gpu_s = np.concatenate([a_gpu[offs[r]:offs[r + 1]] for r in sample])
+    assert rel_err_per_item(a_gpu_s, a_ref).max() <= 1e-4
+    Href = oracle.cfr(a_ref, tr["tau"], tr["rx_offsets"], sc.f_center_hz, sc.delta_f_hz, sc.n_sub)
+    num, den = normwise_rows(H[sample], Href)
+    assert (num / den).max() <= 1e-4
