@@ -71,6 +71,21 @@ rt_status rt_status_word(rt_ctx* ctx, int32_t* device_error);
 /* Library version string. */
 const char* rt_version(void);
 
+/* Instrumentation (no counterpart in the paper; used by the benchmark).
+ * flags bit 0: time the stages of rt_trace_paths with CUDA events;
+ * flags bit 1: count BVH node visits and triangle tests in the tracing kernels
+ * (adds atomics; leave off when timing). */
+rt_status rt_set_profiling(rt_ctx* ctx, int32_t flags);
+/* Reads the instrumentation of ctx (any pointer may be NULL):
+ *   launches      number of kernels this context launched so far
+ *   stage_ms[8]   last trace: SBR, dedup+sort, image method, visibility,
+ *                 emission+records, total, 0, 0  (bit 0 set, else zeros)
+ *   counters[8]   since the last rt_set_profiling: SBR node visits, SBR triangle
+ *                 tests, SBR closest-hit queries, FP64 re-traced rays,
+ *                 visibility node visits, visibility triangle tests, visibility
+ *                 segments, (candidate, receiver) pairs tested */
+rt_status rt_profile_read(rt_ctx* ctx, int64_t* launches, double* stage_ms, int64_t* counters);
+
 /* ------------------------------------------------------------------ scene */
 
 /* Upload a triangle mesh (Sec. II-F: the scene is a set of triangles, each

@@ -263,19 +263,56 @@ static bool coplanar(const Scene& s, int t, int u) {
 }
 
 // ---------------------------------------------------------------------------
-// Fibonacci-sphere launch directions (the paper does not print its launch
-// pattern).  Reading: the Fibonacci lattice on the sphere (Gonzalez 2010),
-// z_i = 1 - (2i+1)/N, r_i = sqrt(1 - z_i^2), phi_i = 2 pi frac(i (sqrt5 - 1)/2),
-// evaluated in FP64 and rounded to FP32; the FP32 values are the canonical rays.
+// Fibonacci-sphere launch directions.  The paper does not print its launch
+// pattern.  Reading: the Fibonacci lattice on the sphere (Gonzalez 2010),
+//   z_i = 1 - (2i+1)/N,  r_i = sqrt(1 - z_i^2),  phi_i = 2 pi frac(i g),  g = (sqrt5 - 1)/2,
+// with frac(i g) taken from the 32-bit golden-ratio Weyl sequence
+// (i * 0x9E3779B9 mod 2^32) / 2^32, and sin, cos of phi from the Taylor series
+// of sin (to theta^11) and cos (to theta^12) on the octant theta in [0, pi/4]
+// plus the octant symmetries.  z is one IEEE FP64 division and subtraction
+// rounded to FP32; every other step is one IEEE FP32 operation (no contraction),
+// so the canonical FP32 ray set is reproduced bit for bit by any IEEE
+// implementation.  The oracle traces these FP32 directions in FP64.
+static void sincos_turn(uint32_t k, float* s_out, float* c_out) {
+    uint32_t oct = k >> 29;                                           // octant of the turn
+    float y = (float)(k & 0x1fffffffu) * (1.0f / 536870912.0f);      // position in it, [0, 1)
+    float t = (oct & 1u) ? 1.0f - y : y;                              // distance to the nearest multiple of pi/2
+    float th = t * 0.785398185253143310546875f;                       // times pi/4 (FP32)
+    float x = th * th;
+    float ps = -2.50521083854417187751e-08f;                          // -1/11!
+    ps = ps * x + 2.75573192239858906526e-06f;                        // 1/9!
+    ps = ps * x + -1.98412698412698412698e-04f;                       // -1/7!
+    ps = ps * x + 8.33333333333333333333e-03f;                        // 1/5!
+    ps = ps * x + -1.66666666666666666667e-01f;                       // -1/3!
+    ps = ps * x + 1.0f;
+    float sn = ps * th;                                               // sin(theta)
+    float pc = 2.08767569878680989792e-09f;                           // 1/12!
+    pc = pc * x + -2.75573192239858906526e-07f;                       // -1/10!
+    pc = pc * x + 2.48015873015873015873e-05f;                        // 1/8!
+    pc = pc * x + -1.38888888888888888889e-03f;                       // -1/6!
+    pc = pc * x + 4.16666666666666666667e-02f;                        // 1/4!
+    pc = pc * x + -0.5f;                                              // -1/2!
+    pc = pc * x + 1.0f;                                               // cos(theta)
+    // angle = quadrant * pi/2 + sign * theta
+    uint32_t quadrant = ((oct + 1u) >> 1) & 3u;
+    float ss = (oct & 1u) ? -sn : sn;
+    float cs = pc;
+    switch (quadrant) {
+        case 0: *s_out = ss; *c_out = cs; break;
+        case 1: *s_out = cs; *c_out = -ss; break;
+        case 2: *s_out = -ss; *c_out = -cs; break;
+        default: *s_out = -cs; *c_out = ss; break;
+    }
+}
+
 static void fibonacci_dir(int64_t i, int64_t N, float out[3]) {
-    double g = (std::sqrt(5.0) - 1.0) / 2.0;
-    double z = 1.0 - (2.0 * (double)i + 1.0) / (double)N;
-    double r = std::sqrt(std::max(0.0, 1.0 - z * z));
-    double x = (double)i * g;
-    double phi = 2.0 * kPi * (x - std::floor(x));
-    out[0] = (float)(r * std::cos(phi));
-    out[1] = (float)(r * std::sin(phi));
-    out[2] = (float)z;
+    float z = (float)(1.0 - (double)(2 * i + 1) / (double)N);
+    float r = std::sqrt(1.0f - z * z);
+    float s, c;
+    sincos_turn((uint32_t)((uint64_t)i * 0x9E3779B9ull), &s, &c);
+    out[0] = r * c;
+    out[1] = r * s;
+    out[2] = z;
 }
 
 // One SBR ray: up to D specular bounces (reflected direction k_r = k_i - 2(k_i.n)n,

@@ -27,6 +27,8 @@ SIGNATURES = {
     "rt_last_error": (ctypes.c_char_p, [P]),
     "rt_status_word": (I32, [P, ctypes.POINTER(I32)]),
     "rt_version": (ctypes.c_char_p, []),
+    "rt_set_profiling": (I32, [P, I32]),
+    "rt_profile_read": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(F64), ctypes.POINTER(I64)]),
     "rt_scene_upload": (I32, [P, P, I32, P, I32, P, I32, P, PP]),
     "rt_scene_free": (I32, [P]),
     "rt_scene_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(F64)]),

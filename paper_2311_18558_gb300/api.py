@@ -58,6 +58,20 @@ class Context:
             msg = self.lib.rt_last_error(self.h).decode()
             raise RtError(st, f"{what}: {msg}")
 
+    def set_profiling(self, flags: int):
+        """Instrumentation: bit 0 trace stage timing, bit 1 traversal counters."""
+        self._stream()
+        self.check(self.lib.rt_set_profiling(self.h, int(flags)), "rt_set_profiling")
+
+    def profile(self):
+        """(kernel launches so far, trace stage ms [8], counters [8])."""
+        n = _c.c_int64()
+        ms = (_c.c_double * 8)()
+        cnt = (_c.c_int64 * 8)()
+        self._stream()
+        self.check(self.lib.rt_profile_read(self.h, _c.byref(n), ms, cnt), "rt_profile_read")
+        return int(n.value), list(ms), list(cnt)
+
     def status_word(self) -> int:
         """Synchronise and return (and clear) the sticky device status word."""
         v = _c.c_int32(0)

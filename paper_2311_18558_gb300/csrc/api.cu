@@ -125,9 +125,44 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_create(int device
     return RT_OK;
 }
 
+extern "C" __attribute__((visibility("default"))) rt_status rt_set_profiling(rt_ctx* ctx, int32_t flags) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (flags & ~3) return rt_fail(ctx, RT_ERR_INVALID_ARG, "profiling flags are bits 0 and 1");
+    if ((flags & 1) && !ctx->ev[0])
+        for (int k = 0; k < 6; ++k) RT_CK(ctx, cudaEventCreate(&ctx->ev[k]));
+    if ((flags & 2) && !ctx->d_counters) RT_CK(ctx, cudaMalloc((void**)&ctx->d_counters, 8 * sizeof(unsigned long long)));
+    if (ctx->d_counters) RT_CK(ctx, cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(unsigned long long), ctx->stream));
+    for (int k = 0; k < 8; ++k) {
+        ctx->h_counters[k] = 0;
+        ctx->stage_ms[k] = 0.0;
+    }
+    ctx->profile = flags;
+    return RT_OK;
+}
+
+extern "C" __attribute__((visibility("default"))) rt_status rt_profile_read(rt_ctx* ctx, int64_t* launches,
+                                                                            double* stage_ms, int64_t* counters) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (launches) *launches = ctx->launches;
+    if (stage_ms)
+        for (int k = 0; k < 8; ++k) stage_ms[k] = ctx->stage_ms[k];
+    if (counters) {
+        unsigned long long d[8] = {0};
+        if (ctx->d_counters) {
+            RT_CK(ctx, cudaStreamSynchronize(ctx->stream));
+            RT_CK(ctx, cudaMemcpy(d, ctx->d_counters, sizeof(d), cudaMemcpyDeviceToHost));
+        }
+        for (int k = 0; k < 8; ++k) counters[k] = (int64_t)d[k] + ctx->h_counters[k];
+    }
+    return RT_OK;
+}
+
 extern "C" __attribute__((visibility("default"))) rt_status rt_destroy(rt_ctx* ctx) {
     if (!ctx) return RT_ERR_INVALID_ARG;
     cudaStreamSynchronize(ctx->stream);
+    for (int k = 0; k < 6; ++k)
+        if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+    if (ctx->d_counters) cudaFree(ctx->d_counters);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -310,7 +345,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_upload(rt_c
         if (!std::isfinite(verts[i])) return rt_fail(ctx, RT_ERR_NUMERIC, "non-finite vertex coordinate");
     std::vector<BTri> bt(n_tris);
     std::vector<float4> tv(3 * (size_t)n_tris), tb(3 * (size_t)n_tris);
-    std::vector<double> tn(4 * (size_t)n_tris);
+    std::vector<double> tn(4 * (size_t)n_tris), tb64(8 * (size_t)n_tris);
     double glo[3] = {INFINITY, INFINITY, INFINITY}, ghi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int t = 0; t < n_tris; ++t) {
         double p[3][3];
@@ -340,16 +375,20 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_upload(rt_c
         for (int v = 0; v < 3; ++v) tv[3 * t + v] = make_float4((float)p[v][0], (float)p[v][1], (float)p[v][2], 0.0f);
         // barycentric planes: lambda_0 = g0.p + h0 with g0 = n x (v2 - v1) / |n|^2,
         // lambda_1 = g1.p + h1 with g1 = n x (v0 - v2) / |n|^2 (n unnormalised)
-        auto bary = [&](int a, int b, float4& out) {
+        auto bary = [&](int a, int b, float4& out, double* out64) {
             double d[3] = {p[b][0] - p[a][0], p[b][1] - p[a][1], p[b][2] - p[a][2]};
             double g[3] = {(n[1] * d[2] - n[2] * d[1]) / nn, (n[2] * d[0] - n[0] * d[2]) / nn,
                            (n[0] * d[1] - n[1] * d[0]) / nn};
             double h = -(g[0] * p[a][0] + g[1] * p[a][1] + g[2] * p[a][2]);
             out = make_float4((float)g[0], (float)g[1], (float)g[2], (float)h);
+            out64[0] = g[0];
+            out64[1] = g[1];
+            out64[2] = g[2];
+            out64[3] = h;
         };
         tb[3 * t] = make_float4((float)un[0], (float)un[1], (float)un[2], (float)tn[4 * t + 3]);
-        bary(1, 2, tb[3 * t + 1]);
-        bary(2, 0, tb[3 * t + 2]);
+        bary(1, 2, tb[3 * t + 1], &tb64[8 * t]);
+        bary(2, 0, tb[3 * t + 2], &tb64[8 * t + 4]);
         for (int k = 0; k < 3; ++k) {
             bt[t].lo[k] = (float)std::min({p[0][k], p[1][k], p[2][k]});
             bt[t].hi[k] = (float)std::max({p[0][k], p[1][k], p[2][k]});
@@ -455,6 +494,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_upload(rt_c
     if (e == cudaSuccess) e = up((void**)&sc->d_tri_v, tv.data(), tv.size() * sizeof(float4));
     if (e == cudaSuccess) e = up((void**)&sc->d_tri_bary, tb.data(), tb.size() * sizeof(float4));
     if (e == cudaSuccess) e = up((void**)&sc->d_tri_n64, tn.data(), tn.size() * sizeof(double));
+    if (e == cudaSuccess) e = up((void**)&sc->d_tri_bary64, tb64.data(), tb64.size() * sizeof(double));
     if (e == cudaSuccess) e = up((void**)&sc->d_tri_material, tri_material, (size_t)n_tris * 4);
     if (e == cudaSuccess) e = up((void**)&sc->d_is_pec, is_pec, (size_t)n_materials);
     if (e != cudaSuccess) {
@@ -472,6 +512,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_free(rt_sce
     cudaFree(sc->d_tri_v);
     cudaFree(sc->d_tri_bary);
     cudaFree(sc->d_tri_n64);
+    cudaFree(sc->d_tri_bary64);
     cudaFree(sc->d_tri_material);
     cudaFree(sc->d_is_pec);
     delete sc;
@@ -584,7 +625,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_paths_import(rt_c
     }
     if (e == cudaSuccess) {
         k_offsets_from_sorted<<<std::max(1, std::min(1024, (n_rx + 256) / 256)), 256, 0, st>>>(n_paths, n_rx, p->d_rx,
-                                                                                                p->d_rx_offsets);
+                                                                                                p->d_rx_offsets); RT_COUNT(ctx);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

@@ -299,7 +299,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr(rt_ctx* ctx, 
         rt_status e = set_smem(ctx, k_cfr_fwd<O>, smem);
         if (e != RT_OK) return e;
         k_cfr_fwd<O><<<n_rx, CFR_THREADS, smem, ctx->stream>>>(S, rx_offsets_dev, (const float2*)a_dev, tau_dev,
-                                                                (float2*)H_dev);
+                                                                (float2*)H_dev); RT_COUNT(ctx);
         RT_CK_LAUNCH(ctx);
         return RT_OK;
     });
@@ -316,7 +316,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_backward(rt_c
     s = set_smem(ctx, k_cfr_bwd, smem);
     if (s != RT_OK) return s;
     k_cfr_bwd<<<n_rx, CFR_THREADS, smem, ctx->stream>>>(S, rx_offsets_dev, tau_dev, (const float2*)grad_H_dev,
-                                                        (float2*)grad_a_dev);
+                                                        (float2*)grad_a_dev); RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;
 }
@@ -345,7 +345,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fus
         if (e != RT_OK) return e;
         k_cfr_fused<O><<<n_rx, CFR_THREADS, smem, ctx->stream>>>(
             S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, target_power_dev, rx_weight_dev, loss_dev,
-            (float2*)grad_a_dev, (float2*)H_dev, part, done);
+            (float2*)grad_a_dev, (float2*)H_dev, part, done); RT_COUNT(ctx);
         RT_CK_LAUNCH(ctx);
         return RT_OK;
     });

@@ -315,7 +315,7 @@ rt_status rt_launch_paths_records(rt_ctx* ctx, rt_paths* p) {
     if (p->P == 0) return RT_OK;
     k_records<<<grid_for(ctx, p->P, 128, 16), 128, 0, st>>>(p->P, p->D, p->d_pts, p->d_depth, p->d_tri,
                                                            p->scene->d_tri_n64, p->d_tau, p->d_len, p->d_cos,
-                                                           p->d_Dm);
+                                                           p->d_Dm); RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;
 }
@@ -324,7 +324,7 @@ rt_status rt_launch_fields_fwd(rt_ctx* ctx, const rt_paths* p, const float* eps,
                                double freq, float gtx, float grx, float2* a, double* tau) {
     if (p->P == 0) return RT_OK;
     FieldArgs A = make_args(p, eps, sig, per_tri, freq, gtx, grx);
-    k_fields_fwd<<<grid_for(ctx, p->P, 256, 8), 256, 0, ctx->stream>>>(A, a, tau);
+    k_fields_fwd<<<grid_for(ctx, p->P, 256, 8), 256, 0, ctx->stream>>>(A, a, tau); RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;
 }
@@ -340,6 +340,7 @@ rt_status rt_launch_fields_bwd(rt_ctx* ctx, const rt_paths* p, const float* eps,
         k_fields_bwd<64><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx, n_mat);
     else
         k_fields_bwd<0><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx, n_mat);
+    RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;
 }

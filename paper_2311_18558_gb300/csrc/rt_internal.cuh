@@ -29,7 +29,17 @@ struct rt_ctx {
     size_t scratch_bytes = 0;
     // pinned host word for small readbacks
     int64_t* h_pinned = nullptr;
+    // instrumentation
+    int64_t launches = 0;              // kernels launched through this context
+    int32_t profile = 0;               // bit 0: trace stage events, bit 1: traversal counters
+    double stage_ms[8] = {0};
+    unsigned long long* d_counters = nullptr;   // 8 device counters (bit 1)
+    int64_t h_counters[8] = {0};                // host-side counts of the same slots
+    cudaEvent_t ev[6] = {};                     // trace stage events (bit 0)
 };
+
+// Count one kernel launch of `ctx` (every launch site calls this).
+#define RT_COUNT(ctx) (++(ctx)->launches)
 
 // BVH2 node holding the boxes of both children (64 bytes).
 //   a = (c0.lo.x, c0.lo.y, c0.lo.z, c0.hi.x)
@@ -52,6 +62,7 @@ struct rt_scene {
     float4* d_tri_v = nullptr;         // 3 float4 per triangle in original order: v0, v1, v2
     float4* d_tri_bary = nullptr;      // 3 float4 per triangle: plane (n, n.v0), g0 (h0), g1 (h1) (FP32)
     double* d_tri_n64 = nullptr;       // 4 doubles per triangle: unit normal (FP64), n.v0
+    double* d_tri_bary64 = nullptr;    // 8 doubles per triangle: g0, h0, g1, h1 barycentric planes (FP64)
     int32_t* d_tri_material = nullptr;
     uint8_t* d_is_pec = nullptr;
     size_t hash_cap = 1u << 20;        // learned dedup table capacity

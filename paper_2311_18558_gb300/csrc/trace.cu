@@ -1,14 +1,22 @@
 // Specular path tracing on GB300 (Sec. II-F of arXiv 2311.18558):
-//   1. SBR: Fibonacci rays bounce specularly over a software BVH (FP32, with an
-//      FP64 re-trace of every ray whose FP32 decisions were marginal);
+//   1. SBR: Fibonacci rays bounce specularly over a software BVH in FP32; a ray
+//      with any marginal FP32 decision is traced again in FP64;
 //   2. dedup: every triangle-sequence prefix goes into an open-addressing hash
 //      set, then the unique keys are sorted by (length, lexicographic);
 //   3. image method over (candidate, receiver) pairs: FP32 prefilter with a
-//      conservative margin, FP64 confirmation of the survivors;
-//   4. visibility of every segment of the surviving chains (FP32 any-hit,
-//      FP64 recheck when marginal), recorded in a (receiver x candidate) bitmask;
+//      conservative margin; survivors are compacted into a queue;
+//   4. per queued pair (dense): FP64 image-method confirmation, then visibility
+//      of every segment (FP32 any-hit, FP64 recheck when marginal), recorded in
+//      a (receiver x candidate) bitmask;
 //   5. deterministic emission: per-receiver popcounts, scan, expansion in
 //      candidate order, FP64 points, coplanar-duplicate rule.
+//
+// GB300 has very little FP64 throughput, and a warp-wide FP64 instruction costs
+// the same with one active lane as with 32.  So FP64 work only runs on
+// compacted lists (re-traced rays, queued pairs, emitted paths), and it avoids
+// IEEE division and square root: reciprocals come from an FP32 seed refined by
+// Newton-Raphson, hit tests compare t = T/det by cross-multiplication, and
+// length tests compare squared lengths.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,6 +29,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int TRACE_THREADS = 128;
+constexpr int REDO_THREADS = 32;
 constexpr float SBR_MARGIN = 1e-3f;     // relative barycentric margin of the FP32 passes
 constexpr float PREFILTER_MARGIN = 1e-3f;
 // Degenerate geometry: every triangle is closed and grown by TRI_TOL (relative
@@ -54,6 +63,17 @@ __device__ __forceinline__ T comp(V3<T> a, int k) { return k == 0 ? a.x : (k == 
 template <typename T>
 __device__ __forceinline__ V3<T> from4(float4 v) { return mk((T)v.x, (T)v.y, (T)v.z); }
 
+// 1/x in FP64 without the IEEE division: FP32 reciprocal as seed, then two
+// Newton-Raphson steps r <- r + r (1 - x r), each doubling the correct bits
+// (24 -> 48 -> full precision).  For the moderate |x| used here.
+__device__ __forceinline__ double rcp64(double x) {
+    double r = (double)__frcp_rn((float)x);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
 // ------------------------------------------------------------------ watertight ray
 template <typename T>
 struct WRay {
@@ -62,6 +82,13 @@ struct WRay {
     T Sx, Sy, Sz;
     float3 of, inv;   // FP32 origin and reciprocal direction for the slab tests
 };
+
+template <typename T>
+__device__ __forceinline__ T recip(T x);
+template <>
+__device__ __forceinline__ float recip<float>(float x) { return 1.0f / x; }
+template <>
+__device__ __forceinline__ double recip<double>(double x) { return rcp64(x); }
 
 template <typename T>
 __device__ __forceinline__ void wray_init(WRay<T>& r) {
@@ -80,9 +107,10 @@ __device__ __forceinline__ void wray_init(WRay<T>& r) {
     r.kx = kx;
     r.ky = ky;
     r.kz = kz;
-    r.Sx = comp(r.d, kx) / dz;
-    r.Sy = comp(r.d, ky) / dz;
-    r.Sz = (T)1 / dz;
+    T iz = recip<T>(dz);
+    r.Sx = comp(r.d, kx) * iz;
+    r.Sy = comp(r.d, ky) * iz;
+    r.Sz = iz;
     r.of = make_float3((float)r.o.x, (float)r.o.y, (float)r.o.z);
     float dx = (float)r.d.x, dy = (float)r.d.y, dzz = (float)r.d.z;
     r.inv = make_float3(1.0f / (fabsf(dx) < 1e-30f ? copysignf(1e-30f, dx) : dx),
@@ -90,54 +118,59 @@ __device__ __forceinline__ void wray_init(WRay<T>& r) {
                         1.0f / (fabsf(dzz) < 1e-30f ? copysignf(1e-30f, dzz) : dzz));
 }
 
-// Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2013) with a margin:
-// returns 0 = miss, 1 = hit, 2 = undecided (some edge function lies within
-// `margin` of zero relative to their total magnitude).  With margin 0 this is the
-// final decision: the triangle grown by TRI_TOL, rays in its plane miss.
+// Sheared edge functions U, V, W and scaled distance Tn of the watertight
+// ray/triangle test (Woop, Benthin, Wald, JCGT 2013); t = Tn / (U + V + W).
 template <typename T>
-__device__ __forceinline__ int tri_test(const WRay<T>& r, float4 p0, float4 p1, float4 p2, T margin, T& t_out) {
+__device__ __forceinline__ void woop(const WRay<T>& r, float4 p0, float4 p1, float4 p2, T& U, T& V, T& W, T& Tn) {
     V3<T> A = from4<T>(p0) - r.o, B = from4<T>(p1) - r.o, C = from4<T>(p2) - r.o;
     T Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
     T Ax = comp(A, r.kx) - r.Sx * Akz, Ay = comp(A, r.ky) - r.Sy * Akz;
     T Bx = comp(B, r.kx) - r.Sx * Bkz, By = comp(B, r.ky) - r.Sy * Bkz;
     T Cx = comp(C, r.kx) - r.Sx * Ckz, Cy = comp(C, r.ky) - r.Sy * Ckz;
-    T U = Cx * By - Cy * Bx;
-    T V = Ax * Cy - Ay * Cx;
-    T W = Bx * Ay - By * Ax;
-    T det = U + V + W;
-    T Tn = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
-    if (margin == (T)0) {
-        // final decision (FP64): closed triangle grown by TRI_TOL
-        T mt = (T)TRI_TOL * (fabs(U) + fabs(V) + fabs(W));
-        if ((U < -mt || V < -mt || W < -mt) && (U > mt || V > mt || W > mt)) return 0;
-        if (!(fabs(det) > (T)3 * mt)) return 0;
-        t_out = Tn / det;
-        return 1;
-    }
-    T m = margin * (fabs(U) + fabs(V) + fabs(W));
+    U = Cx * By - Cy * Bx;
+    V = Ax * Cy - Ay * Cx;
+    W = Bx * Ay - By * Ax;
+    Tn = (U * Akz + V * Bkz + W * Ckz) * r.Sz;
+}
+
+// FP32 test with an undecided band: 0 = miss, 1 = hit (t_out), 2 = undecided
+// (an edge function within `margin` of zero relative to their total magnitude).
+__device__ __forceinline__ int tri_test32(const WRay<float>& r, float4 p0, float4 p1, float4 p2, float& t_out) {
+    float U, V, W, Tn;
+    woop(r, p0, p1, p2, U, V, W, Tn);
+    float m = SBR_MARGIN * (fabsf(U) + fabsf(V) + fabsf(W));
     bool pos = U > m && V > m && W > m;
     bool neg = U < -m && V < -m && W < -m;
+    float det = U + V + W;
     if (pos || neg) {
         t_out = Tn / det;
         return 1;
     }
-    bool mixed = (U < -m || V < -m || W < -m) && (U > m || V > m || W > m);
-    if (mixed) return 0;
-    t_out = det != (T)0 ? Tn / det : (T)0;
+    if ((U < -m || V < -m || W < -m) && (U > m || V > m || W > m)) return 0;
+    t_out = det != 0.0f ? Tn / det : 0.0f;
     return 2;
 }
 
-__device__ __forceinline__ bool slab(const WRay<float>& r, float lx, float ly, float lz, float hx, float hy, float hz,
-                                     float tlo, float thi, float& tn) {
-    float tx0 = (lx - r.of.x) * r.inv.x, tx1 = (hx - r.of.x) * r.inv.x;
-    float ty0 = (ly - r.of.y) * r.inv.y, ty1 = (hy - r.of.y) * r.inv.y;
-    float tz0 = (lz - r.of.z) * r.inv.z, tz1 = (hz - r.of.z) * r.inv.z;
-    tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tlo));
-    float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), thi));
-    return tn <= tf;
+// FP64 final decision: the triangle grown by TRI_TOL; a ray in its plane misses.
+// On a hit returns true with det > 0 and t = Tn / det (not divided here).
+__device__ __forceinline__ bool tri_test64(const WRay<double>& r, float4 p0, float4 p1, float4 p2, double& Tn,
+                                           double& det) {
+    double U, V, W;
+    woop(r, p0, p1, p2, U, V, W, Tn);
+    double mt = TRI_TOL * (fabs(U) + fabs(V) + fabs(W));
+    if ((U < -mt || V < -mt || W < -mt) && (U > mt || V > mt || W > mt)) return false;
+    det = U + V + W;
+    if (!(fabs(det) > 3.0 * mt)) return false;
+    if (det < 0.0) {
+        det = -det;
+        Tn = -Tn;
+    }
+    return true;
 }
-__device__ __forceinline__ bool slab(const WRay<double>& r, float lx, float ly, float lz, float hx, float hy, float hz,
-                                     float tlo, float thi, float& tn) {
+
+template <typename R>
+__device__ __forceinline__ bool slab(const R& r, float lx, float ly, float lz, float hx, float hy, float hz, float tlo,
+                                     float thi, float& tn) {
     float tx0 = (lx - r.of.x) * r.inv.x, tx1 = (hx - r.of.x) * r.inv.x;
     float ty0 = (ly - r.of.y) * r.inv.y, ty1 = (hy - r.of.y) * r.inv.y;
     float tz0 = (lz - r.of.z) * r.inv.z, tz1 = (hz - r.of.z) * r.inv.z;
@@ -148,138 +181,256 @@ __device__ __forceinline__ bool slab(const WRay<double>& r, float lx, float ly, 
 
 __device__ __forceinline__ int leaf_ref(int first, int count) { return ~((first << 3) | (count - 1)); }
 
-// Shared traversal over the two-child-box BVH with a per-thread stack in shared
-// memory (stack[k * blockDim.x + threadIdx.x]).  mode 0: closest hit; mode 1:
-// any hit.  Returns the BVH-order index of the hit (or -1); sets `undecided`
-// when an FP32 decision was marginal and `t_out` to the hit distance.
-template <typename T, int MODE>
-__device__ int bvh_query(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const WRay<T>& r,
-                         T tmin, T tmax, int skip0, int skip1, T margin, int* stack, T& t_out, bool& undecided,
-                         int32_t* status) {
+// Traversal of the two-child-box BVH with a per-thread stack in shared memory
+// (stack[k * blockDim.x + threadIdx.x]), nearer child first.  `leaf(first,
+// count)` tests the triangles of a leaf and returns true to stop; it may lower
+// `thi`, the far end of the box tests.  Node visits are bounded.
+template <typename R, typename Leaf>
+__device__ __forceinline__ void traverse(const BvhNode* __restrict__ nodes, const R& r, float tlo, const float& thi,
+                                         int* stack, int32_t* status, unsigned& nvis, Leaf&& leaf) {
     const int stride = blockDim.x;
     int sp = 0;
     int ref = 0;
-    int best = -1, best_id = 0x7fffffff;
-    T tb = tmax;
-    const float tlo = (float)tmin * 0.5f;
     int visits = 0;
     for (;;) {
         if (++visits > RT_MAX_VISITS) {
             rt_set_status(status, RT_ERR_ITER_LIMIT);
-            undecided = false;
-            return -1;
+            return;
         }
         if (ref >= 0) {
+            nvis++;
             const float4* np = reinterpret_cast<const float4*>(nodes + ref);
             float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
             int4 d = __ldg(reinterpret_cast<const int4*>(np + 3));
-            float thi = (float)tb * 1.00001f + 1e-30f;
             float t0, t1;
             bool h0 = slab(r, a.x, a.y, a.z, a.w, b.x, b.y, tlo, thi, t0);
             bool h1 = slab(r, b.z, b.w, c.x, c.y, c.z, c.w, tlo, thi, t1);
             int r0 = d.z > 0 ? leaf_ref(d.x, d.z) : d.x;
             int r1 = d.w > 0 ? leaf_ref(d.y, d.w) : d.y;
             if (h0 && h1) {
-                int nearr = t0 <= t1 ? r0 : r1, farr = t0 <= t1 ? r1 : r0;
                 if (sp >= RT_STACK) {
                     rt_set_status(status, RT_ERR_STACK_OVERFLOW);
-                    undecided = false;
-                    return -1;
+                    return;
                 }
-                stack[sp * stride] = farr;
+                stack[sp * stride] = t0 <= t1 ? r1 : r0;
                 sp++;
-                ref = nearr;
+                ref = t0 <= t1 ? r0 : r1;
                 continue;
             }
-            if (h0) {
-                ref = r0;
-                continue;
-            }
-            if (h1) {
-                ref = r1;
+            if (h0 || h1) {
+                ref = h0 ? r0 : r1;
                 continue;
             }
         } else {
             int e = ~ref;
-            int first = e >> 3, count = (e & 7) + 1;
-            for (int k = first; k < first + count; ++k) {
-                float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
-                int id = __float_as_int(p0.w);
-                if (id == skip0 || id == skip1) continue;
-                T th;
-                int cls = tri_test<T>(r, p0, p1, p2, margin, th);
-                if (cls == 0) continue;
-                if (cls == 2) {
-                    // undecided edge: only matters if the hit could be in range
-                    if (th > tmin * (T)0.5 && th < tb * (T)1.00001) undecided = true;
-                    continue;
-                }
-                if (!(th > tmin)) {
-                    if (margin != (T)0 && th > tmin * (T)0.1) undecided = true;
-                    continue;
-                }
-                if (MODE == 2) {
-                    if (th <= tmax && id < best_id) {
-                        best_id = id;
-                        best = k;
-                    }
-                    continue;
-                }
-                if (MODE == 1) {
-                    if (th < tmax) {
-                        if (margin != (T)0 && (th < tmin * (T)10 || th > tmax - tmin * (T)9))
-                            undecided = true;
-                        else {
-                            t_out = th;
-                            return id;
-                        }
-                    }
-                    continue;
-                }
-                if (margin != (T)0) {
-                    if (th < tmin * (T)10) undecided = true;
-                    if (best >= 0 && fabs(th - tb) <= (T)1e-4 * tb) undecided = true;
-                }
-                if (th < tb || (th == tb && id < best_id)) {
-                    tb = th;
-                    best = k;
-                    best_id = id;
-                }
-            }
+            if (leaf(e >> 3, (e & 7) + 1)) return;
         }
-        if (sp == 0) break;
+        if (sp == 0) return;
         sp--;
         ref = stack[sp * stride];
     }
-    t_out = tb;
-    return MODE != 1 ? (best >= 0 ? best_id : -1) : -1;
 }
 
-// FP64 closest hit: the smallest t, then the lowest triangle index among the hits
-// within TIE_TOL of it (independent of the visiting order).
+// FP32 closest hit with t > tmin (skipping `skip`): exact ties go to the lower
+// triangle index; `und` is set if any decision that could matter was marginal.
+__device__ __forceinline__ int closest32(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris,
+                                         const WRay<float>& r, float tmin, int skip, int* stack, float& t_out,
+                                         bool& und, int32_t* status, unsigned& nvis, unsigned& ntri) {
+    float tb = INFINITY, thi = INFINITY;
+    int best = -1;
+    traverse(nodes, r, tmin * 0.5f, thi, stack, status, nvis, [&](int first, int count) {
+        for (int k = first; k < first + count; ++k) {
+            float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+            int id = __float_as_int(p0.w);
+            if (id == skip) continue;
+            ntri++;
+            float th;
+            int cls = tri_test32(r, p0, p1, p2, th);
+            if (cls == 0) continue;
+            if (cls == 2) {
+                if (th > tmin * 0.5f && th < tb * 1.00001f) und = true;
+                continue;
+            }
+            if (!(th > tmin)) {
+                if (th > tmin * 0.1f) und = true;
+                continue;
+            }
+            if (th < tmin * 10.0f) und = true;
+            if (best >= 0 && fabsf(th - tb) <= 1e-4f * tb) und = true;
+            if (th < tb || (th == tb && id < best)) {
+                tb = th;
+                best = id;
+                thi = tb * 1.00001f;
+            }
+        }
+        return false;
+    });
+    t_out = tb;
+    return best;
+}
+
+// FP32 any hit with tmin < t < tmax (skipping skip0, skip1): true on a robust
+// hit; `und` set if no robust hit was found but a marginal one might exist.
+__device__ __forceinline__ bool any32(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris,
+                                     const WRay<float>& r, float tmin, float tmax, int skip0, int skip1, int* stack,
+                                     bool& und, int32_t* status, unsigned& nvis, unsigned& ntri) {
+    bool hit = false;
+    const float thi = tmax * 1.00001f;
+    traverse(nodes, r, tmin * 0.5f, thi, stack, status, nvis, [&](int first, int count) {
+        for (int k = first; k < first + count; ++k) {
+            float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+            int id = __float_as_int(p0.w);
+            if (id == skip0 || id == skip1) continue;
+            ntri++;
+            float th;
+            int cls = tri_test32(r, p0, p1, p2, th);
+            if (cls == 0) continue;
+            if (cls == 2) {
+                if (th > tmin * 0.5f && th < tmax * 1.00001f) und = true;
+                continue;
+            }
+            if (!(th > tmin)) {
+                if (th > tmin * 0.1f) und = true;
+                continue;
+            }
+            if (th < tmax) {
+                if (th < tmin * 10.0f || th > tmax - tmin * 9.0f) {
+                    und = true;
+                } else {
+                    hit = true;
+                    return true;
+                }
+            }
+        }
+        return false;
+    });
+    return hit;
+}
+
+// FP64 closest hit: the smallest t = Tn/det (compared by cross-multiplication),
+// then the lowest triangle index among the hits with t within TIE_TOL of it
+// (an answer independent of the visiting order).
 __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const WRay<double>& r,
                          double tmin, int skip, int* stack, double& t_out, int32_t* status) {
-    bool und = false;
-    double tb;
-    int id = bvh_query<double, 0>(nodes, tris, r, tmin, (double)INFINITY, skip, -1, 0.0, stack, tb, und, status);
-    if (id < 0) return -1;
-    double t2;
-    int id2 = bvh_query<double, 2>(nodes, tris, r, tmin, tb + TIE_TOL * tb, skip, -1, 0.0, stack, t2, und, status);
+    double bT = 0.0, bD = 1.0;
+    bool have = false;
+    float thi = INFINITY;
+    unsigned nv = 0;
+    traverse(nodes, r, (float)tmin * 0.5f, thi, stack, status, nv, [&](int first, int count) {
+        for (int k = first; k < first + count; ++k) {
+            float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+            if (__float_as_int(p0.w) == skip) continue;
+            double Tn, det;
+            if (!tri_test64(r, p0, p1, p2, Tn, det)) continue;
+            if (!(Tn > tmin * det)) continue;
+            if (!have || Tn * bD < bT * det) {
+                bT = Tn;
+                bD = det;
+                have = true;
+                thi = (float)(Tn * rcp64(det)) * 1.00001f + 1e-30f;
+            }
+        }
+        return false;
+    });
+    if (!have) return -1;
+    const double tb = bT * rcp64(bD);
+    const double tmax = tb + TIE_TOL * tb;
+    int best = 0x7fffffff;
+    thi = (float)tmax * 1.00001f + 1e-30f;
+    traverse(nodes, r, (float)tmin * 0.5f, thi, stack, status, nv, [&](int first, int count) {
+        for (int k = first; k < first + count; ++k) {
+            float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+            int id = __float_as_int(p0.w);
+            if (id == skip || id >= best) continue;
+            double Tn, det;
+            if (!tri_test64(r, p0, p1, p2, Tn, det)) continue;
+            if (Tn > tmin * det && Tn <= tmax * det) best = id;
+        }
+        return false;
+    });
     t_out = tb;
-    return id2 >= 0 ? id2 : id;
+    return best == 0x7fffffff ? -1 : best;
+}
+
+// FP64 any hit with tmin < t < tmax, skipping skip0 and skip1.
+__device__ bool any64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const WRay<double>& r,
+                      double tmin, double tmax, int skip0, int skip1, int* stack, int32_t* status) {
+    bool hit = false;
+    const float thi = (float)tmax * 1.00001f;
+    unsigned nv = 0;
+    traverse(nodes, r, (float)tmin * 0.5f, thi, stack, status, nv, [&](int first, int count) {
+        for (int k = first; k < first + count; ++k) {
+            float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+            int id = __float_as_int(p0.w);
+            if (id == skip0 || id == skip1) continue;
+            double Tn, det;
+            if (!tri_test64(r, p0, p1, p2, Tn, det)) continue;
+            if (Tn > tmin * det && Tn < tmax * det) {
+                hit = true;
+                return true;
+            }
+        }
+        return false;
+    });
+    return hit;
 }
 
 // ------------------------------------------------------------------ launch directions
-// Fibonacci lattice (Gonzalez 2010), FP64 evaluated and rounded to FP32.
-__device__ __forceinline__ float3 fib_dir(int64_t i, int64_t n) {
-    const double g = 0.6180339887498948482;   // (sqrt(5) - 1) / 2
-    double z = 1.0 - (2.0 * (double)i + 1.0) / (double)n;
-    double rr = sqrt(fmax(0.0, 1.0 - z * z));
-    double x = (double)i * g;
-    double phi = 2.0 * RT_PI * (x - floor(x));
-    double s, c;
-    sincos(phi, &s, &c);
-    return make_float3((float)(rr * c), (float)(rr * s), (float)z);
+// sin and cos of the angle 2 pi k / 2^32, evaluated with IEEE FP32 operations
+// that are never contracted (so any IEEE implementation gets the same bits):
+// the top three bits of k pick the octant; inside it the angle theta in
+// [0, pi/4] goes through the Taylor series of sin (to theta^11) and cos (to
+// theta^12) in Horner form, and the octant symmetries give the final pair.
+__device__ __forceinline__ void sincos_turn(uint32_t k, float& s_out, float& c_out) {
+    const uint32_t oct = k >> 29;
+    const float y = __fmul_rn(__uint2float_rn(k & 0x1fffffffu), 1.0f / 536870912.0f);   // 2^-29
+    const float t = (oct & 1u) ? __fsub_rn(1.0f, y) : y;
+    const float th = __fmul_rn(t, 0.785398185253143310546875f);   // pi/4 rounded to FP32
+    const float x = __fmul_rn(th, th);
+    float ps = -2.50521083854417187751e-08f;   // -1/11!
+    ps = __fadd_rn(__fmul_rn(ps, x), 2.75573192239858906526e-06f);    // 1/9!
+    ps = __fadd_rn(__fmul_rn(ps, x), -1.98412698412698412698e-04f);   // -1/7!
+    ps = __fadd_rn(__fmul_rn(ps, x), 8.33333333333333333333e-03f);    // 1/5!
+    ps = __fadd_rn(__fmul_rn(ps, x), -1.66666666666666666667e-01f);   // -1/3!
+    ps = __fadd_rn(__fmul_rn(ps, x), 1.0f);
+    const float sn = __fmul_rn(ps, th);
+    float pc = 2.08767569878680989792e-09f;    // 1/12!
+    pc = __fadd_rn(__fmul_rn(pc, x), -2.75573192239858906526e-07f);   // -1/10!
+    pc = __fadd_rn(__fmul_rn(pc, x), 2.48015873015873015873e-05f);    // 1/8!
+    pc = __fadd_rn(__fmul_rn(pc, x), -1.38888888888888888889e-03f);   // -1/6!
+    pc = __fadd_rn(__fmul_rn(pc, x), 4.16666666666666666667e-02f);    // 1/4!
+    pc = __fadd_rn(__fmul_rn(pc, x), -0.5f);                          // -1/2!
+    pc = __fadd_rn(__fmul_rn(pc, x), 1.0f);
+    const float cs = pc;
+    // angle = m pi/2 + sigma theta, m = (oct + 1) / 2, sigma = +1 (even oct) / -1 (odd)
+    const uint32_t m = ((oct + 1u) >> 1) & 3u;
+    const float ss = (oct & 1u) ? -sn : sn;   // sin(sigma theta)
+    if (m == 0) {
+        s_out = ss;
+        c_out = cs;
+    } else if (m == 1) {
+        s_out = cs;
+        c_out = -ss;
+    } else if (m == 2) {
+        s_out = -ss;
+        c_out = -cs;
+    } else {
+        s_out = -cs;
+        c_out = ss;
+    }
+}
+
+// Fibonacci-lattice launch direction i of N: z = 1 - (2i+1)/N (one correctly
+// rounded FP64 division and subtraction, rounded to FP32), r = sqrt(1 - z^2) and
+// azimuth fraction frac(i g) of the golden-ratio Weyl sequence in 32-bit fixed
+// point, (i * 0x9E3779B9) mod 2^32; every FP32 step is an uncontracted IEEE
+// operation, so both implementations produce the same bits.
+__device__ __forceinline__ float3 launch_dir(int64_t i, int64_t n) {
+    const float z = (float)(1.0 - (double)(2 * i + 1) / (double)n);
+    const float r = __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(z, z)));
+    float s, c;
+    sincos_turn((uint32_t)((uint64_t)i * 0x9E3779B9ull), s, c);
+    return make_float3(__fmul_rn(r, c), __fmul_rn(r, s), z);
 }
 
 // ------------------------------------------------------------------ hash set of keys
@@ -331,7 +482,14 @@ struct SbrArgs {
     unsigned long long* redo_count;
     int64_t redo_cap;
     int32_t* status;
+    unsigned long long* counters;   // optional instrumentation (slots 0..3)
 };
+
+// Adds a per-thread count to a device counter (one atomic per warp).
+__device__ __forceinline__ void warp_count(unsigned long long* c, unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(c, v);
+}
 
 __device__ __forceinline__ float3 tri_normal_f(const float4* tris_orig, int id) {
     float4 p0 = __ldg(tris_orig + 3 * id), p1 = __ldg(tris_orig + 3 * id + 1), p2 = __ldg(tris_orig + 3 * id + 2);
@@ -356,6 +514,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
     uint64_t key = 0;
     WRay<float> r;
     const float eps = (float)A.eps;
+    unsigned long long c_vis = 0, c_tri = 0, c_q = 0;
     for (;;) {
         bool need = (ray < 0) && !done;
         unsigned m = __ballot_sync(FULL, need);
@@ -371,7 +530,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
                     bounce = 0;
                     prev = -1;
                     key = 0;
-                    float3 d = fib_dir(idx, A.n_rays);
+                    float3 d = launch_dir(idx, A.n_rays);
                     r.o = mk((float)A.tx, (float)A.ty, (float)A.tz);
                     r.d = mk(d.x, d.y, d.z);
                     wray_init(r);
@@ -384,8 +543,11 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
         if (ray < 0) continue;
         float th;
         bool und = false;
-        int id = bvh_query<float, 0>(A.nodes, A.tris, r, eps, INFINITY, prev, -1, SBR_MARGIN, stack, th, und,
-                                     A.status);
+        unsigned nv = 0, nt = 0;
+        int id = closest32(A.nodes, A.tris, r, eps, prev, stack, th, und, A.status, nv, nt);
+        c_vis += nv;
+        c_tri += nt;
+        c_q++;
         if (und) {
             unsigned long long slot = atomicAdd(A.redo_count, 1ull);
             if ((int64_t)slot < A.redo_cap) A.redo[slot] = ray;
@@ -412,19 +574,26 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
         wray_init(r);
         prev = id;
     }
+    if (A.counters) {
+        warp_count(A.counters + 0, c_vis);
+        warp_count(A.counters + 1, c_tri);
+        warp_count(A.counters + 2, c_q);
+    }
 }
 
-// FP64 re-trace of the rays whose FP32 decisions were marginal (same rules, exact
-// classification).  Inserts every prefix again; duplicates are harmless.
-__global__ void __launch_bounds__(TRACE_THREADS) k_sbr_redo(SbrArgs A, const float4* __restrict__ tris_orig) {
+// FP64 re-trace of the rays whose FP32 decisions were marginal (same rules,
+// final decisions).  One warp per block spreads the few rays over all SMs.
+// Inserts every prefix again; duplicates are harmless.
+__global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const double* __restrict__ tri_n64) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
     unsigned long long n = *A.redo_count;
     if (n > (unsigned long long)A.redo_cap) n = A.redo_cap;
+    if (A.counters && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.counters + 3, n);
     for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
          w += (unsigned long long)gridDim.x * blockDim.x) {
         int64_t ray = A.redo[w];
-        float3 df = fib_dir(ray, A.n_rays);
+        float3 df = launch_dir(ray, A.n_rays);
         WRay<double> r;
         r.o = mk(A.tx, A.ty, A.tz);
         r.d = mk((double)df.x, (double)df.y, (double)df.z);
@@ -437,10 +606,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_redo(SbrArgs A, const flo
             if (id < 0) break;
             key = rt_key_push(key, b, id);
             hash_insert(A.table, A.mask, key, A.uniq, A.uniq_limit, A.overflow);
-            float4 p0 = __ldg(tris_orig + 3 * id), p1 = __ldg(tris_orig + 3 * id + 1), p2 = __ldg(tris_orig + 3 * id + 2);
-            V3<double> e1 = from4<double>(p1) - from4<double>(p0), e2 = from4<double>(p2) - from4<double>(p0);
-            V3<double> nn = cross(e1, e2);
-            nn = (1.0 / sqrt(dot(nn, nn))) * nn;
+            V3<double> nn = mk(tri_n64[4 * id], tri_n64[4 * id + 1], tri_n64[4 * id + 2]);
             V3<double> p = r.o + th * r.d;
             r.d = r.d - (2.0 * dot(r.d, nn)) * nn;
             r.o = p;
@@ -569,21 +735,17 @@ __global__ void k_candidates(const uint64_t* __restrict__ keys, int64_t K, int D
     }
 }
 
-// Point-in-triangle test in FP64: the barycentric coordinates (edge functions
-// along the normal over |n|^2) are >= -TRI_TOL.
-__device__ __forceinline__ bool point_in_tri64(const float4* __restrict__ tri_v, int t, V3<double> p, double* minbary) {
-    V3<double> a = from4<double>(__ldg(tri_v + 3 * t)), b = from4<double>(__ldg(tri_v + 3 * t + 1)),
-               c = from4<double>(__ldg(tri_v + 3 * t + 2));
-    V3<double> nn = cross(b - a, c - a);
-    double e0 = dot(nn, cross(b - a, p - a));
-    double e1 = dot(nn, cross(c - b, p - b));
-    double e2 = dot(nn, cross(a - c, p - c));
-    const double n2 = dot(nn, nn);
-    e0 /= n2;
-    e1 /= n2;
-    e2 /= n2;
-    if (minbary) *minbary = fmin(e0, fmin(e1, e2));
-    return e0 >= -TRI_TOL && e1 >= -TRI_TOL && e2 >= -TRI_TOL;
+// Barycentric coordinates of p in triangle t from its FP64 planes
+// lambda_0 = g0.p + h0, lambda_1 = g1.p + h1, lambda_2 = 1 - lambda_0 - lambda_1;
+// inside means all >= -TRI_TOL.
+__device__ __forceinline__ bool point_in_tri64(const double* __restrict__ bary64, int t, V3<double> p,
+                                               double* minbary) {
+    const double* g = bary64 + 8 * t;
+    double l0 = fma(g[0], p.x, fma(g[1], p.y, fma(g[2], p.z, g[3])));
+    double l1 = fma(g[4], p.x, fma(g[5], p.y, fma(g[6], p.z, g[7])));
+    double l2 = 1.0 - l0 - l1;
+    if (minbary) *minbary = fmin(l0, fmin(l1, l2));
+    return l0 >= -TRI_TOL && l1 >= -TRI_TOL && l2 >= -TRI_TOL;
 }
 
 struct CandView {
@@ -596,10 +758,11 @@ struct CandView {
 
 // Back-trace of candidate k from receiver position rx (image method, FP64):
 // fills pts[0..q+1] = Tx, s_1..s_q, Rx and returns validity of the geometry
-// (0 < u < 1, closed triangle, every segment longer than eps).
+// (0 < u < 1, point in the grown triangle, every segment longer than eps).
 __device__ __forceinline__ bool backtrace64(const CandView& C, int64_t k, int q, V3<double> tx, V3<double> rx,
                                             const float4* __restrict__ tri_v, const double* __restrict__ tri_n64,
-                                            double eps, V3<double>* pts, double* minbary) {
+                                            const double* __restrict__ bary64, double eps, V3<double>* pts,
+                                            double* minbary) {
     pts[0] = tx;
     pts[q + 1] = rx;
     double mb = 1.0;
@@ -613,17 +776,18 @@ __device__ __forceinline__ bool backtrace64(const CandView& C, int64_t k, int q,
         V3<double> dir = I - from;
         double den = dot(n, dir);
         if (den == 0.0) return false;
-        double u = dot(n, a - from) / den;
+        double u = dot(n, a - from) * rcp64(den);
         if (!(u > 0.0 && u < 1.0)) return false;
         V3<double> p = from + u * dir;
         double b;
-        if (!point_in_tri64(tri_v, t, p, &b)) return false;
+        if (!point_in_tri64(bary64, t, p, &b)) return false;
         mb = fmin(mb, b);
         pts[j] = p;
     }
+    const double eps2 = eps * eps;
     for (int j = 0; j <= q; ++j) {
         V3<double> d = pts[j + 1] - pts[j];
-        if (sqrt(dot(d, d)) <= eps) return false;
+        if (!(dot(d, d) > eps2)) return false;
     }
     if (minbary) *minbary = mb;
     return true;
@@ -659,20 +823,17 @@ struct PairArgs {
     CandView C;
     int R;
     const double* rx;
-    double tx, ty, tz;
-    const float4* tri_v;
     const float4* tri_bary;
-    const double* tri_n64;
-    double eps;
     uint2* queue;
     unsigned long long* qcount;
     unsigned long long qcap;
     int32_t* overflow;
 };
 
-// Image method over all (candidate, receiver) pairs; lanes of a warp take
-// consecutive receivers of the same candidate.  Survivors go to the visibility
-// queue (one atomic per warp).
+// Image-method prefilter over all (candidate, receiver) pairs, FP32 only; lanes
+// of a warp take consecutive receivers of the same candidate.  Survivors are
+// compacted into the queue (one atomic per warp); the FP64 work happens on the
+// dense queue.
 __global__ void k_pairs(PairArgs A) {
     const int lane = threadIdx.x & 31;
     const int64_t total = A.C.K * (int64_t)A.R;
@@ -687,13 +848,7 @@ __global__ void k_pairs(PairArgs A) {
             r = (int)(p - k * A.R);
             int q = A.C.depth[k];
             const double* rp = A.rx + 3 * (int64_t)r;
-            if (q == 0) {
-                ok = true;
-            } else if (prefilter32(A.C, k, q, make_float3((float)rp[0], (float)rp[1], (float)rp[2]), A.tri_bary)) {
-                V3<double> pts[RT_MAX_DEPTH + 2];
-                ok = backtrace64(A.C, k, q, mk(A.tx, A.ty, A.tz), mk(rp[0], rp[1], rp[2]), A.tri_v, A.tri_n64, A.eps,
-                                 pts, nullptr);
-            }
+            ok = q == 0 || prefilter32(A.C, k, q, make_float3((float)rp[0], (float)rp[1], (float)rp[2]), A.tri_bary);
         }
         unsigned m = __ballot_sync(FULL, ok);
         if (m) {
@@ -718,6 +873,7 @@ struct VisArgs {
     const float4* bvh_tris;
     const float4* tri_v;
     const double* tri_n64;
+    const double* bary64;
     double eps;
     const uint2* queue;
     const unsigned long long* qcount;
@@ -725,16 +881,19 @@ struct VisArgs {
     uint32_t* bits;
     int64_t words;   // words per receiver row
     int32_t* status;
+    unsigned long long* counters;   // optional instrumentation (slots 4..6)
 };
 
-// Visibility of every segment s_j -> s_{j+1} of a geometrically valid chain:
-// any hit with eps < t*len < len - eps, excluding the end triangles.  FP32
-// first, FP64 for marginal segments.  Valid pairs set their bit.
+// Per queued pair: FP64 image-method confirmation, then visibility of every
+// segment s_j -> s_{j+1}: any hit with eps < t*len < len - eps, the end
+// triangles excluded; FP32 first, FP64 for marginal segments.  Valid pairs set
+// their bit.
 __global__ void __launch_bounds__(TRACE_THREADS) k_visibility(VisArgs A) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
     unsigned long long n = *A.qcount;
     if (n > A.qcap) n = A.qcap;
+    unsigned long long c_vis = 0, c_tri = 0, c_seg = 0;
     for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
          w += (unsigned long long)gridDim.x * blockDim.x) {
         uint2 e = A.queue[w];
@@ -743,38 +902,43 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_visibility(VisArgs A) {
         int q = A.C.depth[k];
         const double* rp = A.rx + 3 * (int64_t)r;
         V3<double> pts[RT_MAX_DEPTH + 2];
-        if (!backtrace64(A.C, k, q, mk(A.tx, A.ty, A.tz), mk(rp[0], rp[1], rp[2]), A.tri_v, A.tri_n64, A.eps, pts,
-                         nullptr))
+        if (!backtrace64(A.C, k, q, mk(A.tx, A.ty, A.tz), mk(rp[0], rp[1], rp[2]), A.tri_v, A.tri_n64, A.bary64,
+                         A.eps, pts, nullptr))
             continue;
         bool visible = true;
         for (int j = 0; j <= q && visible; ++j) {
             V3<double> d = pts[j + 1] - pts[j];
-            double len = sqrt(dot(d, d));
+            double il = rsqrt(dot(d, d));   // 1 / len, only scales the guard band
             int s0 = j >= 1 ? A.C.tri[(int64_t)(j - 1) * A.C.K + k] : -1;
             int s1 = j + 1 <= q ? A.C.tri[(int64_t)j * A.C.K + k] : -1;
-            double tlo = A.eps / len, thi = 1.0 - A.eps / len;
+            double tlo = A.eps * il, thi = 1.0 - A.eps * il;
             WRay<float> rf;
             rf.o = mk((float)pts[j].x, (float)pts[j].y, (float)pts[j].z);
             rf.d = mk((float)d.x, (float)d.y, (float)d.z);
             wray_init(rf);
-            float th;
             bool und = false;
-            int hit = bvh_query<float, 1>(A.nodes, A.bvh_tris, rf, (float)tlo, (float)thi, s0, s1, SBR_MARGIN, stack,
-                                          th, und, A.status);
-            if (hit >= 0) {
+            unsigned nv = 0, nt = 0;
+            bool hit = any32(A.nodes, A.bvh_tris, rf, (float)tlo, (float)thi, s0, s1, stack, und, A.status, nv, nt);
+            c_vis += nv;
+            c_tri += nt;
+            c_seg++;
+            if (hit) {
                 visible = false;
             } else if (und) {
                 WRay<double> rd;
                 rd.o = pts[j];
                 rd.d = d;
                 wray_init(rd);
-                double t64;
-                bool u2 = false;
-                int h2 = bvh_query<double, 1>(A.nodes, A.bvh_tris, rd, tlo, thi, s0, s1, 0.0, stack, t64, u2, A.status);
-                if (h2 >= 0) visible = false;
+                if (any64(A.nodes, A.bvh_tris, rd, tlo, thi, s0, s1, stack, A.status)) visible = false;
             }
         }
         if (visible) atomicOr(A.bits + (int64_t)r * A.words + (k >> 5), 1u << (k & 31));
+    }
+    if (A.counters) {
+        // every thread of the block reaches this point (grid-stride loop above)
+        warp_count(A.counters + 4, c_vis);
+        warp_count(A.counters + 5, c_tri);
+        warp_count(A.counters + 6, c_seg);
     }
 }
 
@@ -848,9 +1012,9 @@ __global__ void k_expand(const uint32_t* __restrict__ bits, int R, int64_t words
 // reflection point lies on a triangle edge (input of the duplicate rule).
 __global__ void k_points(CandView C, int64_t P, int D, const int32_t* __restrict__ path_rx,
                          const int32_t* __restrict__ path_cand, const double* __restrict__ rx, double tx, double ty,
-                         double tz, const float4* __restrict__ tri_v, const double* __restrict__ tri_n64, double eps,
-                         double* pts_out, int32_t* depth_out, int32_t* rx_out, int32_t* tri_out, int32_t* edge_flag,
-                         int32_t* status) {
+                         double tz, const float4* __restrict__ tri_v, const double* __restrict__ tri_n64,
+                         const double* __restrict__ bary64, double eps, double* pts_out, int32_t* depth_out,
+                         int32_t* rx_out, int32_t* tri_out, int32_t* edge_flag, int32_t* status) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t k = path_cand[i];
         int r = path_rx[i];
@@ -858,7 +1022,7 @@ __global__ void k_points(CandView C, int64_t P, int D, const int32_t* __restrict
         const double* rp = rx + 3 * (int64_t)r;
         V3<double> pts[RT_MAX_DEPTH + 2];
         double mb = 1.0;
-        if (!backtrace64(C, k, q, mk(tx, ty, tz), mk(rp[0], rp[1], rp[2]), tri_v, tri_n64, eps, pts, &mb))
+        if (!backtrace64(C, k, q, mk(tx, ty, tz), mk(rp[0], rp[1], rp[2]), tri_v, tri_n64, bary64, eps, pts, &mb))
             rt_set_status(status, RT_ERR_NUMERIC);
         for (int j = 0; j < D + 2; ++j) {
             V3<double> v = j <= q + 1 ? pts[j] : mk(0.0, 0.0, 0.0);
@@ -882,7 +1046,7 @@ __device__ __forceinline__ bool coplanar64(const double* __restrict__ tri_n64, c
     V3<double> a = mk(tri_n64[4 * t], tri_n64[4 * t + 1], tri_n64[4 * t + 2]);
     V3<double> b = mk(tri_n64[4 * u], tri_n64[4 * u + 1], tri_n64[4 * u + 2]);
     V3<double> c = cross(a, b);
-    if (sqrt(dot(c, c)) > 1e-9) return false;
+    if (dot(c, c) > 1e-18) return false;
     double dt = dot(a, from4<double>(__ldg(tri_v + 3 * t)));
     double du = dot(a, from4<double>(__ldg(tri_v + 3 * u)));
     return fabs(dt - du) <= 1e-9 * diag;
@@ -897,6 +1061,7 @@ __global__ void k_dedup(int64_t P, int D, const int64_t* __restrict__ rx_offsets
                         const int32_t* __restrict__ edge_flag, const double* __restrict__ tri_n64,
                         const float4* __restrict__ tri_v, double diag, uint32_t* bits, int64_t words,
                         unsigned long long* drops) {
+    const double tol2 = (1e-9 * diag) * (1e-9 * diag);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         if (!edge_flag[i]) continue;
         int r = path_rx[i];
@@ -904,12 +1069,13 @@ __global__ void k_dedup(int64_t P, int D, const int64_t* __restrict__ rx_offsets
         for (int64_t j = rx_offsets[r]; j < rx_offsets[r + 1]; ++j) {
             if (j == i || !edge_flag[j] || depth[j] != q) continue;
             bool same = true;
-            for (int b = 0; b < q && same; ++b) same = coplanar64(tri_n64, tri_v, tri[(int64_t)b * P + i], tri[(int64_t)b * P + j], diag);
+            for (int b = 0; b < q && same; ++b)
+                same = coplanar64(tri_n64, tri_v, tri[(int64_t)b * P + i], tri[(int64_t)b * P + j], diag);
             for (int b = 1; b <= q && same; ++b) {
                 const double* pi = pts + ((int64_t)i * (D + 2) + b) * 3;
                 const double* pj = pts + ((int64_t)j * (D + 2) + b) * 3;
                 double dx = pi[0] - pj[0], dy = pi[1] - pj[1], dz = pi[2] - pj[2];
-                same = sqrt(dx * dx + dy * dy + dz * dz) <= 1e-9 * diag;
+                same = dx * dx + dy * dy + dz * dz <= tol2;
             }
             if (!same) continue;
             bool less = false;
@@ -944,6 +1110,10 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // ---------------------------------------------------------------------------
 // Host driver of the tracing pipeline.
+
+static void mark(rt_ctx* ctx, int k) {
+    if (ctx->profile & 1) cudaEventRecord(ctx->ev[k], ctx->stream);
+}
 
 struct Arena {
     char* base;
@@ -990,6 +1160,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         int32_t* flags = ar.take<int32_t>(8);
         int64_t* redo = ar.take<int64_t>(redo_cap);
         uint64_t* sorted = ar.take<uint64_t>(sort_cap);
+        mark(ctx, 0);
         RT_CK(ctx, cudaMemsetAsync(table, 0, cap * 8, st));
         RT_CK(ctx, cudaMemsetAsync(counters, 0, 8 * 8, st));
         RT_CK(ctx, cudaMemsetAsync(flags, 0, 8 * 4, st));
@@ -1012,10 +1183,14 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         A.redo_count = counters + 2;
         A.redo_cap = redo_cap;
         A.status = status;
+        A.counters = (ctx->profile & 2) ? ctx->d_counters : nullptr;
         int blocks = ctx->num_sms * 8;
-        k_sbr<<<blocks, TRACE_THREADS, stack_bytes, st>>>(A, sc->d_tri_v);
+        k_sbr<<<blocks, TRACE_THREADS, stack_bytes, st>>>(A, sc->d_tri_v); RT_COUNT(ctx);
         RT_CK_LAUNCH(ctx);
-        k_sbr_redo<<<ctx->num_sms * 2, TRACE_THREADS, stack_bytes, st>>>(A, sc->d_tri_v);
+        k_sbr_redo<<<ctx->num_sms * 4, REDO_THREADS, (size_t)RT_STACK * REDO_THREADS * sizeof(int), st>>>(
+            A, sc->d_tri_n64);
+        RT_COUNT(ctx);
+        mark(ctx, 1);
         RT_CK_LAUNCH(ctx);
         int64_t* hp = ctx->h_pinned;
         RT_CK(ctx, cudaMemcpyAsync(hp, counters, 8, cudaMemcpyDeviceToHost, st));
@@ -1034,14 +1209,16 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         int64_t n_pad = SORT_BLOCK;
         while (n_pad < n_uniq) n_pad <<= 1;
         d_sorted = sorted;
-        k_fill_u64<<<grid_for(ctx, n_pad, 256), 256, 0, st>>>(d_sorted, n_pad, ~0ull);
-        k_table_compact<<<grid_for(ctx, cap, 256, 16), 256, 0, st>>>(table, cap, d_sorted, counters + 3);
+        k_fill_u64<<<grid_for(ctx, n_pad, 256), 256, 0, st>>>(d_sorted, n_pad, ~0ull); RT_COUNT(ctx);
+        k_table_compact<<<grid_for(ctx, cap, 256, 16), 256, 0, st>>>(table, cap, d_sorted, counters + 3); RT_COUNT(ctx);
         RT_CK_LAUNCH(ctx);
-        k_bitonic_local<<<(unsigned)(n_pad / SORT_BLOCK), 1024, 0, st>>>(d_sorted);
+        k_bitonic_local<<<(unsigned)(n_pad / SORT_BLOCK), 1024, 0, st>>>(d_sorted); RT_COUNT(ctx);
         for (uint64_t k = 2 * SORT_BLOCK; k <= (uint64_t)n_pad; k <<= 1) {
-            for (uint64_t j = k >> 1; j >= (uint64_t)SORT_BLOCK; j >>= 1)
+            for (uint64_t j = k >> 1; j >= (uint64_t)SORT_BLOCK; j >>= 1) {
                 k_bitonic_global<<<grid_for(ctx, n_pad, 256, 16), 256, 0, st>>>(d_sorted, n_pad, j, k);
-            k_bitonic_merge_local<<<(unsigned)(n_pad / SORT_BLOCK), 1024, 0, st>>>(d_sorted, k);
+                RT_COUNT(ctx);
+            }
+            k_bitonic_merge_local<<<(unsigned)(n_pad / SORT_BLOCK), 1024, 0, st>>>(d_sorted, k); RT_COUNT(ctx);
         }
         RT_CK_LAUNCH(ctx);
         break;
@@ -1101,24 +1278,20 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         TCK(cudaMemsetAsync(bits, 0, (size_t)n_rx * words * 4, st));
         k_candidates<<<grid_for(ctx, K, 256), 256, 0, st>>>(p->d_cand, K, D, tx_host[0], tx_host[1], tx_host[2],
                                                             sc->d_tri_v, sc->d_tri_n64, cand_depth, cand_tri, img64,
-                                                            img32);
+                                                            img32); RT_COUNT(ctx);
         TCK(cudaGetLastError());
         PairArgs PA;
         PA.C = CandView{K, cand_depth, cand_tri, img64, img32};
         PA.R = n_rx;
         PA.rx = rx_dev;
-        PA.tx = tx_host[0];
-        PA.ty = tx_host[1];
-        PA.tz = tx_host[2];
-        PA.tri_v = sc->d_tri_v;
         PA.tri_bary = sc->d_tri_bary;
-        PA.tri_n64 = sc->d_tri_n64;
-        PA.eps = sc->eps;
         PA.queue = queue;
         PA.qcount = counters;
         PA.qcap = qcap;
         PA.overflow = flags;
-        k_pairs<<<grid_for(ctx, K * (int64_t)n_rx, 256, 16), 256, 0, st>>>(PA);
+        mark(ctx, 2);
+        k_pairs<<<grid_for(ctx, K * (int64_t)n_rx, 256, 16), 256, 0, st>>>(PA); RT_COUNT(ctx);
+        mark(ctx, 3);
         TCK(cudaGetLastError());
         VisArgs VA;
         VA.C = PA.C;
@@ -1130,6 +1303,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         VA.bvh_tris = sc->d_bvh_tris;
         VA.tri_v = sc->d_tri_v;
         VA.tri_n64 = sc->d_tri_n64;
+        VA.bary64 = sc->d_tri_bary64;
         VA.eps = sc->eps;
         VA.queue = queue;
         VA.qcount = counters;
@@ -1137,7 +1311,10 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         VA.bits = bits;
         VA.words = words;
         VA.status = status;
-        k_visibility<<<ctx->num_sms * 8, TRACE_THREADS, stack_bytes, st>>>(VA);
+        VA.counters = (ctx->profile & 2) ? ctx->d_counters : nullptr;
+        ctx->h_counters[7] += K * (int64_t)n_rx;
+        k_visibility<<<ctx->num_sms * 8, TRACE_THREADS, stack_bytes, st>>>(VA); RT_COUNT(ctx);
+        mark(ctx, 4);
         TCK(cudaGetLastError());
         int64_t* hp = ctx->h_pinned;
         TCK(cudaMemcpyAsync(hp, flags, 4, cudaMemcpyDeviceToHost, st));
@@ -1155,10 +1332,10 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
     int32_t* path_cand = nullptr;
     int32_t* edge = nullptr;
     for (int pass = 0;; ++pass) {
-        k_row_count<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, counts);
+        k_row_count<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, counts); RT_COUNT(ctx);
         TCK(cudaGetLastError());
         if (!p->d_rx_offsets) TCK(cudaMallocAsync((void**)&p->d_rx_offsets, (size_t)(n_rx + 1) * 8, st));
-        k_scan<<<1, 1024, 0, st>>>(counts, n_rx, p->d_rx_offsets);
+        k_scan<<<1, 1024, 0, st>>>(counts, n_rx, p->d_rx_offsets); RT_COUNT(ctx);
         TCK(cudaGetLastError());
         int64_t* hp = ctx->h_pinned;
         TCK(cudaMemcpyAsync(hp, p->d_rx_offsets + n_rx, 8, cudaMemcpyDeviceToHost, st));
@@ -1183,19 +1360,19 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         path_rx = p->d_rx;
         if (P > 0) {
             k_expand<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, p->d_rx_offsets,
-                                                                                 path_rx, path_cand);
+                                                                                 path_rx, path_cand); RT_COUNT(ctx);
             TCK(cudaGetLastError());
             CandView C{K, cand_depth, cand_tri, img64, img32};
             k_points<<<grid_for(ctx, P, 256), 256, 0, st>>>(C, P, D, path_rx, path_cand, rx_dev, tx_host[0], tx_host[1],
-                                                             tx_host[2], sc->d_tri_v, sc->d_tri_n64, sc->eps, p->d_pts,
-                                                             p->d_depth, p->d_rx, p->d_tri, edge, status);
+                                                             tx_host[2], sc->d_tri_v, sc->d_tri_n64, sc->d_tri_bary64, sc->eps, p->d_pts,
+                                                             p->d_depth, p->d_rx, p->d_tri, edge, status); RT_COUNT(ctx);
             TCK(cudaGetLastError());
         }
         if (pass > 0 || P == 0) break;
         TCK(cudaMemsetAsync(counters + 4, 0, 8, st));
         k_dedup<<<grid_for(ctx, P, 256), 256, 0, st>>>(P, D, p->d_rx_offsets, path_rx, path_cand, p->d_depth,
                                                        p->d_tri, p->d_pts, edge, sc->d_tri_n64, sc->d_tri_v, sc->diag, bits, words,
-                                                       counters + 4);
+                                                       counters + 4); RT_COUNT(ctx);
         TCK(cudaGetLastError());
         TCK(cudaMemcpyAsync(hp, counters + 4, 8, cudaMemcpyDeviceToHost, st));
         TCK(cudaStreamSynchronize(st));
@@ -1205,6 +1382,19 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
     cudaFreeAsync(edge, st);
     rt_status s = rt_launch_paths_records(ctx, p);
     if (s != RT_OK) return fail(s);
+    if (ctx->profile & 1) {
+        cudaEventRecord(ctx->ev[5], st);
+        TCK(cudaEventSynchronize(ctx->ev[5]));
+        float ms;
+        // stages: SBR, dedup + sort (incl. candidate setup), image method, visibility, emission
+        const int a[5] = {0, 1, 2, 3, 4}, b[5] = {1, 2, 3, 4, 5};
+        for (int k = 0; k < 5; ++k) {
+            cudaEventElapsedTime(&ms, ctx->ev[a[k]], ctx->ev[b[k]]);
+            ctx->stage_ms[k] = ms;
+        }
+        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
+        ctx->stage_ms[5] = ms;
+    }
 #undef TCK
     *out = p;
     return RT_OK;

@@ -299,6 +299,13 @@ def test_fibonacci_lattice_properties():
     inner = slice(10, n - 11)          # azimuth is ill-conditioned at the poles
     assert np.all(dphi[inner] < 1e-4)
     assert abs(d.mean(axis=0)).max() < 1e-3
+    # against the closed form of the lattice in FP64 (the 32-bit Weyl fraction
+    # drifts from i*g by i * 1.2e-10 turns, and the FP32 sine/cosine by ~1e-7)
+    i = np.arange(n)
+    zz = 1 - (2 * i + 1) / n
+    ph = 2 * np.pi * np.mod(i * g, 1.0)
+    ref = np.stack([np.sqrt(1 - zz * zz) * np.cos(ph), np.sqrt(1 - zz * zz) * np.sin(ph), zz], 1)
+    assert np.abs(d - ref).max() < 3e-6
 
 
 # ----------------------------------------------------------------------------- fields invariants
