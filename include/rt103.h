@@ -211,6 +211,27 @@ rt_status rt_cfr_power_mse_fused(rt_ctx* ctx, const int64_t* rx_offsets_dev, int
                                  const float* rx_weight_dev, float* loss_dev, void* grad_a_dev,
                                  void* H_dev);
 
+/* Same computation, inputs, outputs and errors as rt_cfr_power_mse_fused, for
+ * callers that cannot allocate device memory during the call (for example a
+ * loop that reserved its whole memory budget in advance, or a host program whose
+ * own memory manager forbids other code from calling the CUDA allocator).  The
+ * paper has no counterpart: this is a property of the library, not of the method.
+ *   - Allocates nothing: its working memory is one fixed array inside the
+ *     library (512 KiB + 256 B) that every GPU loading the library keeps until
+ *     the process exits.
+ *   - n_rx must be <= 65536; larger values return RT_ERR_INVALID_ARG with a
+ *     message, nothing launched.
+ *   - The first call on a device looks up that array's device address; make the
+ *     first call on each device before any stream capture.
+ *   - All calls share the array: sequential calls are independent (the call
+ *     resets what must start at zero), but calls that overlap on the GPU, e.g. on
+ *     two streams at once, race on it. */
+rt_status rt_cfr_power_mse_fused_noalloc(rt_ctx* ctx, const int64_t* rx_offsets_dev, int32_t n_rx,
+                                         const void* a_dev, const double* tau_dev, double f_center_hz,
+                                         double delta_f_hz, int32_t n_sub, const float* target_power_dev,
+                                         const float* rx_weight_dev, float* loss_dev, void* grad_a_dev,
+                                         void* H_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 #include <type_traits>
 
 #include "rt_internal.cuh"
@@ -346,6 +347,83 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fus
         k_cfr_fused<O><<<n_rx, CFR_THREADS, smem, ctx->stream>>>(
             S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, target_power_dev, rx_weight_dev, loss_dev,
             (float2*)grad_a_dev, (float2*)H_dev, part, done); RT_COUNT(ctx);
+        RT_CK_LAUNCH(ctx);
+        return RT_OK;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of rt_cfr_power_mse_fused.
+//
+// Some callers cannot allocate device memory when they run the loss: a serving
+// or training loop that reserved its whole memory budget up front (cudaMalloc
+// there can fail, or stall the device while the driver finds memory), or a host
+// program whose own memory manager owns every device buffer and forbids other
+// code from calling the CUDA allocator.  This entry point serves them: its only
+// working memory is the fixed array below, which every GPU that loads the
+// library holds from load until process exit.  The caller still passes all
+// inputs and outputs.
+//
+// Limits and sharing: at most RT_NOALLOC_MAX_RX receivers per call (one double
+// of loss partial each, plus a completion counter: 512 KiB + 256 B in total).
+// All calls on a device share the array and it keeps the last call's contents;
+// the counter is cleared before every launch and every partial is rewritten, so
+// sequential calls are independent, but two calls that overlap on the GPU (for
+// example on two streams) race on it.
+#define RT_NOALLOC_MAX_RX 65536
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RT_NOALLOC_MAX_RX * sizeof(double) + 256];
+
+// Device address of g_noalloc_scratch per device.  In host code the array's
+// name only stands in for the symbol; its address on a device comes from
+// cudaGetSymbolAddress, asked once per device with that device current.
+static void* g_noalloc_addr[64];
+static std::mutex g_noalloc_mu;
+
+static rt_status noalloc_scratch_address(rt_ctx* ctx, unsigned char** base) {
+    if (ctx->device < 0 || ctx->device >= 64) return rt_fail(ctx, RT_ERR_UNSUPPORTED, "device index >= 64");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[ctx->device]) {
+        int cur = -1;
+        RT_CK(ctx, cudaGetDevice(&cur));
+        if (cur != ctx->device) RT_CK(ctx, cudaSetDevice(ctx->device));
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (cur != ctx->device) cudaSetDevice(cur);
+        if (e != cudaSuccess) return rt_cuda_fail(ctx, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_addr[ctx->device] = p;
+    }
+    *base = static_cast<unsigned char*>(g_noalloc_addr[ctx->device]);
+    return RT_OK;
+}
+
+extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fused_noalloc(
+    rt_ctx* ctx, const int64_t* rx_offsets_dev, int32_t n_rx, const void* a_dev, const double* tau_dev,
+    double f_center_hz, double delta_f_hz, int32_t n_sub, const float* target_power_dev, const float* rx_weight_dev,
+    float* loss_dev, void* grad_a_dev, void* H_dev) {
+    CfrShape S;
+    rt_status s = check_cfr(ctx, rx_offsets_dev, n_rx, tau_dev, n_sub, f_center_hz, delta_f_hz, S);
+    if (s != RT_OK) return s;
+    if (n_rx > RT_NOALLOC_MAX_RX)
+        return rt_fail(ctx, RT_ERR_INVALID_ARG, "n_rx = %d exceeds the allocation-free limit of %d receivers", n_rx,
+                       RT_NOALLOC_MAX_RX);
+    if (!a_dev || !target_power_dev || !rx_weight_dev || !loss_dev || !grad_a_dev)
+        return rt_fail(ctx, RT_ERR_INVALID_ARG, "null device pointer");
+    unsigned char* base = nullptr;
+    s = noalloc_scratch_address(ctx, &base);
+    if (s != RT_OK) return s;
+    double* part = reinterpret_cast<double*>(base);
+    unsigned int* done = reinterpret_cast<unsigned int*>(base + RT_NOALLOC_MAX_RX * sizeof(double));
+    RT_CK(ctx, cudaMemsetAsync(done, 0, sizeof(unsigned int), ctx->stream));
+    const size_t smem = fwd_smem(S) + (size_t)S.N * 8;
+    return dispatch_opt(ctx, S.N, [&](auto opt) -> rt_status {
+        constexpr int O = decltype(opt)::value;
+        rt_status e = set_smem(ctx, k_cfr_fused<O>, smem);
+        if (e != RT_OK) return e;
+        k_cfr_fused<O><<<n_rx, CFR_THREADS, smem, ctx->stream>>>(
+            S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, target_power_dev, rx_weight_dev, loss_dev,
+            (float2*)grad_a_dev, (float2*)H_dev, part, done);
+        RT_COUNT(ctx);
         RT_CK_LAUNCH(ctx);
         return RT_OK;
     });

@@ -1,0 +1,78 @@
+"""The allocation-free fused CFR loss entry point against the regular one.
+
+rt_cfr_power_mse_fused_noalloc exists for callers that cannot allocate device
+memory while they run the loss (for example a loop that reserved its memory
+budget in advance, or a host program whose memory manager forbids other code
+from calling the CUDA allocator).  It keeps its working memory in a fixed array
+inside the library.  Both entry points are called through the C ABI on the same
+inputs; two calls in a row must both agree with the regular entry point.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import scenegen
+
+pytestmark = pytest.mark.gpu
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev(x, dtype):
+    return torch.as_tensor(np.asarray(x), dtype=dtype, device="cuda").contiguous()
+
+
+def _call(lib, fn, ctx, offs, a, tau, fc, df, N, T, w):
+    R = offs.shape[0] - 1
+    loss = torch.full((1,), float("nan"), dtype=torch.float32, device="cuda")
+    ga = torch.full_like(a, float("nan"))
+    H = torch.full((R, N), float("nan"), dtype=torch.complex64, device="cuda")
+    ctx._stream()
+    st = getattr(lib, fn)(ctx.h, _p(offs), R, _p(a), _p(tau), fc, df, N, _p(T), _p(w), _p(loss), _p(ga), _p(H))
+    assert st == 0, (fn, st, lib.rt_last_error(ctx.h))
+    torch.cuda.synchronize()
+    return loss.cpu().numpy()[0], ga.cpu().numpy(), H.cpu().numpy()
+
+
+@pytest.mark.parametrize("N", [256, 1024])
+def test_noalloc_matches_regular_entry_point(N):
+    import paper_2311_18558_gb300 as rt
+    ctx = rt.Context(0)
+    lib = ctx.lib
+    a, tau, offs = scenegen.random_cfr_inputs(77 + N, 96, 60, empty_every=11)
+    fc, df = 1.272e9, 50e6 / N
+    rng = np.random.default_rng(N)
+    T = rng.uniform(1e-8, 1e-5, (96, N)).astype(np.float32)
+    w = (1.0 / T.mean(axis=1)).astype(np.float32)
+    args = (_dev(offs, torch.int64), _dev(a, torch.complex64), _dev(tau, torch.float64), fc, df, N,
+            _dev(T, torch.float32), _dev(w, torch.float32))
+    L_ref, ga_ref, H_ref = _call(lib, "rt_cfr_power_mse_fused", ctx, *args)
+    assert np.isfinite(L_ref) and np.isfinite(ga_ref).all()
+    for _ in range(2):
+        L, ga, H = _call(lib, "rt_cfr_power_mse_fused_noalloc", ctx, *args)
+        assert abs(L - L_ref) <= 1e-4 * abs(L_ref)
+        assert np.linalg.norm(ga - ga_ref) <= 1e-4 * np.linalg.norm(ga_ref)
+        assert np.linalg.norm(H - H_ref) <= 1e-4 * np.linalg.norm(H_ref)
+    assert ctx.status_word() == 0
+
+
+def test_noalloc_rejects_too_many_receivers():
+    import paper_2311_18558_gb300 as rt
+    ctx = rt.Context(0)
+    lib = ctx.lib
+    R = 65537
+    offs = torch.zeros(R + 1, dtype=torch.int64, device="cuda")
+    tau = torch.zeros(1, dtype=torch.float64, device="cuda")
+    a = torch.zeros(1, dtype=torch.complex64, device="cuda")
+    T = torch.zeros((R, 2), dtype=torch.float32, device="cuda")
+    w = torch.zeros(R, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    ctx._stream()
+    st = lib.rt_cfr_power_mse_fused_noalloc(ctx.h, _p(offs), R, _p(a), _p(tau), 1e9, 1e6, 2, _p(T), _p(w), _p(loss),
+                                            _p(a), None)
+    assert st == 1
+    assert b"exceeds" in lib.rt_last_error(ctx.h)
