@@ -307,25 +307,36 @@ __device__ __forceinline__ bool any32(const BvhNode* __restrict__ nodes, const f
     return hit;
 }
 
-// FP64 closest hit: the smallest t = Tn/det (compared by cross-multiplication),
-// then the lowest triangle index among the hits with t within TIE_TOL of it
-// (an answer independent of the visiting order).
+// Closest hit of an FP64 ray, with final decisions in FP64: the smallest
+// t = Tn/det (compared by cross-multiplication), then the lowest triangle index
+// among the hits with t within TIE_TOL of it (independent of the visiting order).
+// Every triangle first gets the FP32 test with its margin on the ray rounded to
+// FP32 (rf); a robust FP32 miss is final, everything else gets the FP64 test,
+// so the FP64 work is a few tests per query.  The tie pass runs only if two
+// hits came within 1e-6 (relative) of each other.
 __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const WRay<double>& r,
-                         double tmin, int skip, int* stack, double& t_out, int32_t* status) {
+                         const WRay<float>& rf, double tmin, int skip, int* stack, double& t_out, int32_t* status) {
     double bT = 0.0, bD = 1.0;
-    bool have = false;
+    bool have = false, near_tie = false;
+    int best = -1;
     float thi = INFINITY;
     unsigned nv = 0;
-    traverse(nodes, r, (float)tmin * 0.5f, thi, stack, status, nv, [&](int first, int count) {
+    const float tminf = (float)tmin;
+    traverse(nodes, rf, tminf * 0.5f, thi, stack, status, nv, [&](int first, int count) {
         for (int k = first; k < first + count; ++k) {
             float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
-            if (__float_as_int(p0.w) == skip) continue;
+            int id = __float_as_int(p0.w);
+            if (id == skip) continue;
+            float tf;
+            if (tri_test32(rf, p0, p1, p2, tf) == 0) continue;
             double Tn, det;
             if (!tri_test64(r, p0, p1, p2, Tn, det)) continue;
             if (!(Tn > tmin * det)) continue;
-            if (!have || Tn * bD < bT * det) {
+            if (have && fabs(Tn * bD - bT * det) <= 1e-6 * bT * det) near_tie = true;
+            if (!have || Tn * bD < bT * det || (Tn * bD == bT * det && id < best)) {
                 bT = Tn;
                 bD = det;
+                best = id;
                 have = true;
                 thi = (float)(Tn * rcp64(det)) * 1.00001f + 1e-30f;
             }
@@ -334,35 +345,42 @@ __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __rest
     });
     if (!have) return -1;
     const double tb = bT * rcp64(bD);
+    t_out = tb;
+    if (!near_tie) return best;
     const double tmax = tb + TIE_TOL * tb;
-    int best = 0x7fffffff;
+    int low = 0x7fffffff;
     thi = (float)tmax * 1.00001f + 1e-30f;
-    traverse(nodes, r, (float)tmin * 0.5f, thi, stack, status, nv, [&](int first, int count) {
+    traverse(nodes, rf, tminf * 0.5f, thi, stack, status, nv, [&](int first, int count) {
         for (int k = first; k < first + count; ++k) {
             float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
             int id = __float_as_int(p0.w);
-            if (id == skip || id >= best) continue;
+            if (id == skip || id >= low) continue;
+            float tf;
+            if (tri_test32(rf, p0, p1, p2, tf) == 0) continue;
             double Tn, det;
             if (!tri_test64(r, p0, p1, p2, Tn, det)) continue;
-            if (Tn > tmin * det && Tn <= tmax * det) best = id;
+            if (Tn > tmin * det && Tn <= tmax * det) low = id;
         }
         return false;
     });
-    t_out = tb;
-    return best == 0x7fffffff ? -1 : best;
+    return low == 0x7fffffff ? best : low;
 }
 
-// FP64 any hit with tmin < t < tmax, skipping skip0 and skip1.
+// Any hit with tmin < t < tmax of an FP64 ray (skipping skip0 and skip1),
+// final decisions in FP64; robust FP32 misses on the rounded ray rf are final.
 __device__ bool any64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const WRay<double>& r,
-                      double tmin, double tmax, int skip0, int skip1, int* stack, int32_t* status) {
+                      const WRay<float>& rf, double tmin, double tmax, int skip0, int skip1, int* stack,
+                      int32_t* status) {
     bool hit = false;
     const float thi = (float)tmax * 1.00001f;
     unsigned nv = 0;
-    traverse(nodes, r, (float)tmin * 0.5f, thi, stack, status, nv, [&](int first, int count) {
+    traverse(nodes, rf, (float)tmin * 0.5f, thi, stack, status, nv, [&](int first, int count) {
         for (int k = first; k < first + count; ++k) {
             float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
             int id = __float_as_int(p0.w);
             if (id == skip0 || id == skip1) continue;
+            float tf;
+            if (tri_test32(rf, p0, p1, p2, tf) == 0) continue;
             double Tn, det;
             if (!tri_test64(r, p0, p1, p2, Tn, det)) continue;
             if (Tn > tmin * det && Tn < tmax * det) {
@@ -595,14 +613,18 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const doub
         int64_t ray = A.redo[w];
         float3 df = launch_dir(ray, A.n_rays);
         WRay<double> r;
+        WRay<float> rf;
         r.o = mk(A.tx, A.ty, A.tz);
         r.d = mk((double)df.x, (double)df.y, (double)df.z);
-        wray_init(r);
         int prev = -1;
         uint64_t key = 0;
         for (int b = 0; b < A.depth; ++b) {
+            wray_init(r);
+            rf.o = mk((float)r.o.x, (float)r.o.y, (float)r.o.z);
+            rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
+            wray_init(rf);
             double th;
-            int id = closest64(A.nodes, A.tris, r, A.eps, prev, stack, th, A.status);
+            int id = closest64(A.nodes, A.tris, r, rf, A.eps, prev, stack, th, A.status);
             if (id < 0) break;
             key = rt_key_push(key, b, id);
             hash_insert(A.table, A.mask, key, A.uniq, A.uniq_limit, A.overflow);
@@ -610,7 +632,6 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const doub
             V3<double> p = r.o + th * r.d;
             r.d = r.d - (2.0 * dot(r.d, nn)) * nn;
             r.o = p;
-            wray_init(r);
             prev = id;
         }
     }
@@ -929,7 +950,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_visibility(VisArgs A) {
                 rd.o = pts[j];
                 rd.d = d;
                 wray_init(rd);
-                if (any64(A.nodes, A.bvh_tris, rd, tlo, thi, s0, s1, stack, A.status)) visible = false;
+                if (any64(A.nodes, A.bvh_tris, rd, rf, tlo, thi, s0, s1, stack, A.status)) visible = false;
             }
         }
         if (visible) atomicOr(A.bits + (int64_t)r * A.words + (k >> 5), 1u << (k & 31));
