@@ -211,6 +211,35 @@ rt_status rt_cfr_power_mse_fused(rt_ctx* ctx, const int64_t* rx_offsets_dev, int
                                  const float* rx_weight_dev, float* loss_dev, void* grad_a_dev,
                                  void* H_dev);
 
+/* ------------------------------------------------------------------ neural materials */
+
+/* Neural materials, Sec. III-D: an MLP evaluated at every triangle's centroid c.
+ * The centroid is normalised to the unit cube, p = (c - b) / Delta_b with b the
+ * centre and Delta_b the longest edge of the scene's bounding box, and encoded
+ * as [p, sin(2^k pi p), cos(2^k pi p) for k = 1..6] (Eq. pos_encoding; per k the
+ * three sines then the three cosines; 39 features, padded with one zero to 40);
+ * then 40 -> 128 -> 128 -> 128 -> 2 with ReLU on the hidden layers, and
+ * sigma = exp(o_1), eps_r = 1 + exp(o_2) (Eq. trainable_materials_1/2).
+ * Weights are BF16, row major [in][out], packed W1 (40 x 128, row 39 unused),
+ * W2, W3 (128 x 128), W4 (128 x 2): 38144 values, 16-byte aligned.  Biases are
+ * float32 packed b1, b2, b3 (128 each), b4 (2): 386 values.  Every layer input is
+ * rounded to BF16, products are summed in FP32.
+ *   eps_r_dev, sigma_dev  n_tris float32 outputs (indexed by triangle)
+ *   act_dev   n_tris x 424 BF16: the inputs of layers 1..4 saved for the
+ *             backward pass (may be NULL if no backward pass follows). */
+rt_status rt_mlp_forward(rt_ctx* ctx, const rt_scene* scene, const uint16_t* weights_bf16_dev,
+                         const float* bias_dev, float* eps_r_dev, float* sigma_dev, uint16_t* act_dev);
+/* Adjoint of rt_mlp_forward given dL/deps_r and dL/dsigma per triangle (e.g. from
+ * rt_eval_fields_backward with per_triangle = 1): ACCUMULATES (+=) dL/dW into
+ * grad_weights_dev (38144 float32, same packing as the weights) and dL/db into
+ * grad_bias_dev (386 float32).  dz_work_dev: n_tris x 384 float32 scratch owned
+ * by the caller (overwritten).  act_dev, eps_r_dev, sigma_dev come from the
+ * forward call with the same weights. */
+rt_status rt_mlp_backward(rt_ctx* ctx, const rt_scene* scene, const uint16_t* weights_bf16_dev,
+                          const uint16_t* act_dev, const float* eps_r_dev, const float* sigma_dev,
+                          const float* grad_eps_r_dev, const float* grad_sigma_dev, float* dz_work_dev,
+                          float* grad_weights_dev, float* grad_bias_dev);
+
 /* Same computation, inputs, outputs and errors as rt_cfr_power_mse_fused, for
  * callers that cannot allocate device memory during the call (for example a
  * loop that reserved its whole memory budget in advance, or a host program whose

@@ -45,6 +45,8 @@ SIGNATURES = {
     "rt_cfr_backward": (I32, [P, P, I32, P, F64, F64, I32, P, P]),
     "rt_cfr_power_mse_fused": (I32, [P, P, I32, P, P, F64, F64, I32, P, P, P, P, P]),
     "rt_cfr_power_mse_fused_noalloc": (I32, [P, P, I32, P, P, F64, F64, I32, P, P, P, P, P]),
+    "rt_mlp_forward": (I32, [P, P, P, P, P, P, P]),
+    "rt_mlp_backward": (I32, [P, P, P, P, P, P, P, P, P, P, P]),
 }
 
 STATUS = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_CUDA", 3: "RT_ERR_OOM", 4: "RT_ERR_CAPACITY",

@@ -265,3 +265,49 @@ def cfr_power_mse_fused(ctx: Context, rx_offsets, a, tau, f_center_hz, delta_f_h
                                              float(delta_f_hz), int(n_sub), _ptr(target_power), _ptr(rx_weight),
                                              _ptr(loss), _ptr(grad_a), _ptr(H)), "rt_cfr_power_mse_fused")
     return loss, grad_a, H
+
+
+# ----------------------------------------------------------------------------- neural materials
+
+MLP_IN, MLP_IN_PAD, MLP_WIDTH, MLP_OUT = 39, 40, 128, 2
+MLP_NW = MLP_IN_PAD * MLP_WIDTH + 2 * MLP_WIDTH * MLP_WIDTH + MLP_WIDTH * MLP_OUT   # 38144
+MLP_NB = 3 * MLP_WIDTH + MLP_OUT                                                    # 386
+MLP_ACT = MLP_IN_PAD + 3 * MLP_WIDTH                                                # 424
+
+
+def pack_mlp(Ws, bs, device="cuda"):
+    """Packs [W1 (39x128), W2, W3 (128x128), W4 (128x2)] and biases into the flat
+    FP32 layout of rt_mlp_forward (W1 padded with a zero row to 40 x 128)."""
+    W1 = np.zeros((MLP_IN_PAD, MLP_WIDTH), np.float32)
+    W1[:MLP_IN] = Ws[0]
+    w = np.concatenate([W1.ravel()] + [np.asarray(W, np.float32).ravel() for W in Ws[1:]])
+    b = np.concatenate([np.asarray(x, np.float32).ravel() for x in bs])
+    assert w.size == MLP_NW and b.size == MLP_NB
+    return torch.tensor(w, device=device), torch.tensor(b, device=device)
+
+
+def mlp_forward(ctx: Context, scene: Scene, w_bf16: torch.Tensor, b: torch.Tensor, save_act: bool = True):
+    """(eps_r, sigma, act) per triangle from the neural-material MLP (rt_mlp_forward)."""
+    dev = torch.device("cuda", ctx.device)
+    assert w_bf16.dtype == torch.bfloat16 and w_bf16.numel() == MLP_NW
+    eps = torch.empty(scene.n_tris, dtype=torch.float32, device=dev)
+    sig = torch.empty(scene.n_tris, dtype=torch.float32, device=dev)
+    act = torch.empty((scene.n_tris, MLP_ACT), dtype=torch.bfloat16, device=dev) if save_act else None
+    ctx._stream()
+    ctx.check(ctx.lib.rt_mlp_forward(ctx.h, scene.h, _ptr(w_bf16.contiguous()), _ptr(b.contiguous()), _ptr(eps),
+                                     _ptr(sig), _ptr(act)), "rt_mlp_forward")
+    return eps, sig, act
+
+
+def mlp_backward(ctx: Context, scene: Scene, w_bf16, act, eps, sig, grad_eps, grad_sigma, grad_w=None, grad_b=None,
+                 dz=None):
+    """Accumulates dL/dW (FP32, packed) and dL/db (rt_mlp_backward)."""
+    dev = torch.device("cuda", ctx.device)
+    grad_w = grad_w if grad_w is not None else torch.zeros(MLP_NW, dtype=torch.float32, device=dev)
+    grad_b = grad_b if grad_b is not None else torch.zeros(MLP_NB, dtype=torch.float32, device=dev)
+    dz = dz if dz is not None else torch.empty((scene.n_tris, 3 * MLP_WIDTH), dtype=torch.float32, device=dev)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_mlp_backward(ctx.h, scene.h, _ptr(w_bf16.contiguous()), _ptr(act), _ptr(eps), _ptr(sig),
+                                      _ptr(grad_eps.contiguous()), _ptr(grad_sigma.contiguous()), _ptr(dz),
+                                      _ptr(grad_w), _ptr(grad_b)), "rt_mlp_backward")
+    return grad_w, grad_b

@@ -87,3 +87,41 @@ def calibration_loss(ctx, paths, eps_r, sigma, target_power, rx_weight, freq_hz,
     a = EvalFields.apply(eps_r, sigma, ctx, paths, freq_hz, gain_tx, gain_rx, per_triangle)
     return CfrPowerMSE.apply(a, paths.tau, paths.rx_offsets, target_power, rx_weight, ctx, f_center_hz, delta_f_hz,
                              n_sub)
+
+
+class NeuralMaterialsFn(torch.autograd.Function):
+    """(eps_r, sigma) per triangle = MLP(positional encoding of the centroid), with
+    the BF16 weights rounded from the FP32 master weights; the gradient of the
+    BF16 weights is applied to the masters (straight through the rounding)."""
+
+    @staticmethod
+    def forward(fctx, w, b, ctx, scene):
+        w16 = w.detach().to(torch.bfloat16).contiguous()
+        eps, sig, act = api.mlp_forward(ctx, scene, w16, b.detach())
+        fctx.save_for_backward(w16, act, eps, sig)
+        fctx.args = (ctx, scene)
+        return eps, sig
+
+    @staticmethod
+    def backward(fctx, g_eps, g_sig):
+        w16, act, eps, sig = fctx.saved_tensors
+        ctx, scene = fctx.args
+        if g_eps is None:
+            g_eps = torch.zeros_like(eps)
+        if g_sig is None:
+            g_sig = torch.zeros_like(sig)
+        gw, gb = api.mlp_backward(ctx, scene, w16, act, eps, sig, g_eps, g_sig)
+        return gw, gb, None, None
+
+
+class NeuralMaterials(torch.nn.Module):
+    """Neural materials of Sec. III-D evaluated at the triangle centroids."""
+
+    def __init__(self, Ws, bs, device="cuda"):
+        super().__init__()
+        w, b = api.pack_mlp(Ws, bs, device)
+        self.w = torch.nn.Parameter(w)
+        self.b = torch.nn.Parameter(b)
+
+    def forward(self, ctx, scene):
+        return NeuralMaterialsFn.apply(self.w, self.b, ctx, scene)

@@ -482,6 +482,10 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_upload(rt_c
     sc->n_nodes = (int)dn.size();
     sc->n_materials = n_materials;
     sc->diag = diag;
+    for (int k = 0; k < 3; ++k) {
+        sc->lo[k] = glo[k];
+        sc->hi[k] = ghi[k];
+    }
     sc->eps = 1e-6 * diag;
     auto up = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
         cudaError_t e = cudaMalloc(dst, bytes);

@@ -56,6 +56,7 @@ struct rt_scene {
     rt_ctx* ctx = nullptr;
     int n_tris = 0, n_nodes = 0, n_materials = 0;
     double diag = 0.0;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};   // bounding box of the vertices [m]
     double eps = 0.0;                  // 1e-6 * diag: hit and segment guard [m]
     BvhNode* d_nodes = nullptr;
     float4* d_bvh_tris = nullptr;      // 3 float4 per triangle in BVH order: v0 (w = id bits), v1, v2
