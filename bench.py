@@ -290,6 +290,9 @@ def run_ours(args):
     # ---------------- indoor calibration step (the second metric), graph-captured
     calib_indoor = time_indoor_calibration(rt, ctx, flush, args)
 
+    # ---------------- learned form (neural materials) vs the plain per-object form
+    learned = time_learned(rt, ctx, args)
+
     # ---------------- roofline of the dominant kernel
     stages = {"sbr": stage_mean[0], "dedup_sort": stage_mean[1], "image_method": stage_mean[2],
               "visibility": stage_mean[3], "emission_records": stage_mean[4]}
@@ -313,6 +316,7 @@ def run_ours(args):
             "stage_ms": {k: round(v, 4) for k, v in stages.items()},
             "calibration_ms": {k: round(v, 4) for k, v in cal.items()},
             "calibration_indoor": calib_indoor,
+            "learned": learned,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clock_info,
             "counters": {"sbr_node_visits": counters[0], "sbr_tri_tests": counters[1], "sbr_queries": counters[2],
@@ -447,6 +451,97 @@ def time_indoor_calibration(rt, ctx, flush, args):
     return {"workload": "indoor_diff", "n_rx": sc.n_rx, "n_sub": N, "n_paths": p.n_paths,
             "ms_per_step_median": float(np.median(times)), "graph": True, "replays": n,
             "l2": "flushed: 256 MiB written between replays"}
+
+
+def time_learned(rt, ctx, args, train_steps=100):
+    """Room-and-corridor scene (19,626 triangles, per-triangle ground truth):
+    MLP forward/backward kernel times, one training step of the neural form
+    (MLP -> fields -> CFR loss -> adjoints -> Adam) and of the plain per-object
+    form, and both held-out losses after the same number of Adam steps."""
+    import torch
+
+    import scenegen
+    sc = scenegen.room_corridor(n_rx=1536)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    scene_tri = rt.Scene.from_synthetic(ctx, sc)
+    scene_obj = rt.Scene(ctx, sc.verts, sc.tris, sc.tri_object, np.zeros(4, np.uint8))
+    rx_tr = torch.tensor(sc.rx[:1280], device=dev)
+    rx_te = torch.tensor(sc.rx[1280:], device=dev)
+    fc, df, N, f = sc.f_center_hz, sc.delta_f_hz, sc.n_sub, sc.freq_hz
+    eg, sg = torch.tensor(sc.eps_r, device=dev), torch.tensor(sc.sigma, device=dev)
+
+    def target(p):
+        a = rt.eval_fields(ctx, p, eg, sg, f, per_triangle=True)
+        T = (rt.cfr(ctx, p.rx_offsets, a, p.tau, fc, df, N).abs() ** 2).float().contiguous()
+        m = T.mean(1)
+        w = torch.where(m > 0, 1 / torch.where(m > 0, m, torch.ones_like(m)), torch.zeros_like(m)).float()
+        return T, w.contiguous()
+
+    tri_tr = rt.trace_paths(ctx, scene_tri, sc.tx, rx_tr, sc.n_rays, sc.max_depth)
+    tri_te = rt.trace_paths(ctx, scene_tri, sc.tx, rx_te, sc.n_rays, sc.max_depth)
+    obj_tr = rt.trace_paths(ctx, scene_obj, sc.tx, rx_tr, sc.n_rays, sc.max_depth)
+    obj_te = rt.trace_paths(ctx, scene_obj, sc.tx, rx_te, sc.n_rays, sc.max_depth)
+    Ttr, wtr = target(tri_tr)
+    Tte, wte = target(tri_te)
+    plain = rt.LogMaterials(np.full(4, 4.0), np.full(4, 0.05)).cuda()
+    opt_p = torch.optim.Adam(plain.parameters(), lr=0.05)
+    Ws, bs = scenegen.random_mlp_params(11)
+    Ws = [w * 0.5 for w in Ws]
+    bs[-1] = np.array([np.log(0.05), np.log(3.0)], np.float32)
+    neural = rt.NeuralMaterials(Ws, bs)
+    opt_n = torch.optim.Adam(neural.parameters(), lr=3e-3)
+
+    def plain_step(p, T, w, train=True):
+        e, s = plain()
+        L = rt.calibration_loss(ctx, p, e.contiguous(), s.contiguous(), T, w, f, fc, df, N)
+        if train:
+            opt_p.zero_grad()
+            L.backward()
+            opt_p.step()
+        return L
+
+    def neural_step(p, T, w, train=True):
+        e, s = neural(ctx, scene_tri)
+        L = rt.calibration_loss(ctx, p, e, s, T, w, f, fc, df, N, per_triangle=True)
+        if train:
+            opt_n.zero_grad()
+            L.backward()
+            opt_n.step()
+        return L
+
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(n):
+            fn()
+        e0.record(stream)
+        e0.synchronize()
+        return s0.elapsed_time(e0) / n
+
+    ms_plain = timed(lambda: plain_step(obj_tr, Ttr, wtr), train_steps)
+    ms_neural = timed(lambda: neural_step(tri_tr, Ttr, wtr), train_steps)
+    with torch.no_grad():
+        held_plain = plain_step(obj_te, Tte, wte, train=False).item()
+        held_neural = neural_step(tri_te, Tte, wte, train=False).item()
+    # MLP kernels alone (the a12 roofline inputs)
+    w16 = neural.w.detach().to(torch.bfloat16)
+    b = neural.b.detach()
+    eps, sig, act = rt.mlp_forward(ctx, scene_tri, w16, b)
+    g1 = torch.ones_like(eps)
+    ms_fwd = timed(lambda: rt.mlp_forward(ctx, scene_tri, w16, b), 20)
+    gw = torch.zeros(rt.MLP_NW, device=dev)
+    gb = torch.zeros(rt.MLP_NB, device=dev)
+    dz = torch.empty((sc.n_tris, 384), device=dev)
+    ms_bwd = timed(lambda: rt.mlp_backward(ctx, scene_tri, w16, act, eps, sig, g1, g1, gw, gb, dz), 20)
+    flops_fwd = 2.0 * sc.n_tris * (40 * 128 + 2 * 128 * 128 + 128 * 2)
+    return {"workload": "room_corridor", "n_tris": sc.n_tris, "train_rx": 1280, "heldout_rx": 256,
+            "adam_steps": train_steps, "neural_step_ms": ms_neural, "plain_step_ms": ms_plain,
+            "heldout_loss_neural": held_neural, "heldout_loss_plain": held_plain,
+            "mlp_fwd_ms": ms_fwd, "mlp_bwd_ms": ms_bwd,
+            "mlp_fwd_tflops": flops_fwd / (ms_fwd * 1e-3) / 1e12,
+            "mlp_bwd_tflops": 2 * flops_fwd / (ms_bwd * 1e-3) / 1e12}
 
 
 def roofline_for(name, ms, counters, cal, n_paths, sc, N, peaks, peak_src):

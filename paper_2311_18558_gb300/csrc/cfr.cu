@@ -77,75 +77,156 @@ struct CfrShape {
     double f0, df;
 };
 
-// Forward CFR of receiver r into registers acc[OPT]: thread t owns columns
+// Shared-memory tables of one chunk of n <= CH paths of a receiver:
+//   sP[ii]            phase parameters of path ii
+//   sA[ii N1 + c1]    A_i[c1]  = exp(-j 2 pi N2 c1 u_i)
+//   sB[ii N2 + c2]    B_i[c2]  = exp(-j 2 pi c2 u_i)
+//   sAc[ii N1 + c1]   c_i A_i[c1] with c_i = a_i exp(-j 2 pi f_0 tau_i)   (forward only)
+struct Tables {
+    PathPhase* sP;
+    float2* sC;    // c_i = a_i exp(-j 2 pi f_0 tau_i) per path
+    float2* sA;
+    float2* sB;
+    float2* sAc;   // reused as the partial sums of the adjoint
+    float2* sF;    // factor phasors: per path A_lo[8], A_hi[NAH], B_lo[4], B_hi[4]
+};
+
+constexpr int NAL = 8, NBL = 4;   // low factors of c1 and c2
+
+__device__ __forceinline__ int nah(const CfrShape& S) { return (S.N1 + NAL - 1) / NAL; }
+__device__ __forceinline__ int nfac(const CfrShape& S) { return NAL + nah(S) + 2 * NBL; }
+
+__device__ __forceinline__ Tables carve(const CfrShape& S, float4* smem4) {
+    Tables T;
+    T.sAc = reinterpret_cast<float2*>(smem4);
+    T.sA = T.sAc + CH * S.N1;
+    T.sB = T.sA + CH * S.N1;
+    T.sF = T.sB + CH * S.N2;
+    T.sC = T.sF + CH * nfac(S);
+    T.sP = reinterpret_cast<PathPhase*>(T.sC + CH);
+    return T;
+}
+
+__device__ __forceinline__ float2* carve_g(const CfrShape& S, float4* smem4) {   // N values after the tables
+    Tables T = carve(S, smem4);
+    return reinterpret_cast<float2*>(T.sP + CH + (CH & 1));
+}
+
+// Phasor tables of a chunk.  Each table entry is the product of two directly
+// evaluated phasors: A_i[c1] = A_hi[c1 / 8] A_lo[c1 % 8] and
+// B_i[c2] = B_hi[c2 / 4] B_lo[c2 % 4], which needs 8 + N1/8 + 8 sin/cos pairs per
+// path instead of N1 + N2 (each factor carries ~1e-7 relative error).
+__device__ __forceinline__ void build_tables(const CfrShape& S, int64_t base, int n, const float2* __restrict__ a,
+                                             const double* __restrict__ tau, const Tables& T) {
+    const int t = threadIdx.x;
+    const int NAH = nah(S), NF = nfac(S);
+    __syncthreads();
+    if (t < n) {
+        PathPhase p = path_phase(tau[base + t], S.f0, S.df);
+        T.sP[t] = p;
+        if (a) T.sC[t] = cmul(a[base + t], base_phasor(p));
+    }
+    __syncthreads();
+    for (int e = t; e < n * NF; e += CFR_THREADS) {
+        int ii = e / NF, k = e - ii * NF;
+        int m;
+        if (k < NAL) m = k * S.N2;                                    // A_lo: c1 = k
+        else if (k < NAL + NAH) m = (k - NAL) * NAL * S.N2;           // A_hi: c1 = 8 (k - 8)
+        else if (k < NAL + NAH + NBL) m = k - NAL - NAH;              // B_lo: c2 = k'
+        else m = (k - NAL - NAH - NBL) * NBL;                         // B_hi: c2 = 4 k'
+        T.sF[e] = phasor(T.sP[ii], m);
+    }
+    __syncthreads();
+    for (int e = t; e < n * S.N2; e += CFR_THREADS) {
+        int ii = e / S.N2, k = e - ii * S.N2;
+        const float2* F = T.sF + ii * NF + NAL + NAH;
+        T.sB[e] = cmul(F[NBL + k / NBL], F[k % NBL]);
+    }
+    for (int e = t; e < n * S.N1; e += CFR_THREADS) {
+        int ii = e / S.N1, k = e - ii * S.N1;
+        const float2* F = T.sF + ii * NF;
+        float2 A = cmul(F[NAL + k / NAL], F[k % NAL]);
+        T.sA[e] = A;
+        if (a) T.sAc[e] = cmul(T.sC[ii], A);
+    }
+    __syncthreads();
+}
+
+// Forward CFR of one receiver into registers acc[OPT]: thread t owns columns
 // c = t + 256 m (m < OPT); with N2 | 256 all of them share c2 = t % N2.
+// Returns the number of chunks (the tables of the last chunk stay in place).
 template <int OPT>
-__device__ __forceinline__ void cfr_rx_forward(const CfrShape& S, int64_t i0, int64_t i1, const float2* __restrict__ a,
-                                               const double* __restrict__ tau, float2* sA, float2* sB, PathPhase* sP,
-                                               float2 (&acc)[OPT]) {
+__device__ __forceinline__ int cfr_rx_forward(const CfrShape& S, int64_t i0, int64_t i1, const float2* __restrict__ a,
+                                              const double* __restrict__ tau, const Tables& T, float2 (&acc)[OPT]) {
     const int t = threadIdx.x;
 #pragma unroll
     for (int m = 0; m < OPT; ++m) acc[m] = make_float2(0.0f, 0.0f);
     const int c2 = t % S.N2;
+    int c1[OPT];   // row of each owned column, computed once (no division in the loop)
+#pragma unroll
+    for (int m = 0; m < OPT; ++m) {
+        int c = t + CFR_THREADS * m;
+        c1[m] = c < S.N ? c / S.N2 : -1;
+    }
+    int chunks = 0;
     for (int64_t base = i0; base < i1; base += CH) {
         const int n = (int)min((int64_t)CH, i1 - base);
-        __syncthreads();
-        if (t < n) {
-            PathPhase p = path_phase(tau[base + t], S.f0, S.df);
-            sP[t] = p;
-            // c_i = a_i exp(-j 2 pi f_0 tau_i), kept in the B row slot N2 (scratch)
-            sB[t * (S.N2 + 1) + S.N2] = cmul(a[base + t], base_phasor(p));
-        }
-        __syncthreads();
-        for (int e = t; e < n * S.N2; e += CFR_THREADS) {
-            int ii = e / S.N2, k = e - ii * S.N2;
-            sB[ii * (S.N2 + 1) + k] = phasor(sP[ii], k);
-        }
-        for (int e = t; e < n * S.N1; e += CFR_THREADS) {
-            int ii = e / S.N1, k = e - ii * S.N1;
-            sA[ii * S.N1 + k] = cmul(sB[ii * (S.N2 + 1) + S.N2], phasor(sP[ii], k * S.N2));
-        }
-        __syncthreads();
+        build_tables(S, base, n, a, tau, T);
+        chunks++;
         for (int ii = 0; ii < n; ++ii) {
-            float2 b = sB[ii * (S.N2 + 1) + c2];
+            const float2 b = T.sB[ii * S.N2 + c2];
+            const float2* row = T.sAc + ii * S.N1;
 #pragma unroll
-            for (int m = 0; m < OPT; ++m) {
-                int c = t + CFR_THREADS * m;
-                if (c < S.N) cfma(acc[m], sA[ii * S.N1 + c / S.N2], b);
-            }
+            for (int m = 0; m < OPT; ++m)
+                if (c1[m] >= 0) cfma(acc[m], row[c1[m]], b);
         }
     }
+    return chunks;
 }
 
-// Adjoint for receiver r given g_H (N values in shared memory): one thread per
-// path, g_c = sum_c1 conj(A[c1]) sum_c2 g[c1, c2] conj(B[c2]), g_a = conj(phi) g_c.
+// Adjoint for one receiver given g_H in shared memory, stored transposed as
+// sGt[c2 N1 + c1] (conflict-free for lanes with consecutive c1):
+//   g_c[i] = sum_c1 conj(A_i[c1]) sum_c2 g[c1, c2] conj(B_i[c2]),  g_a[i] = conj(phi_i) g_c[i].
+// The (path, c1) pairs of a chunk are spread over all threads (partial sums in
+// shared memory), then one warp per path reduces its N1 partials with shuffles,
+// so a receiver with few paths still keeps the whole CTA busy.  `reuse` = the
+// tables of the only chunk are already in place.
 __device__ __forceinline__ void cfr_rx_backward(const CfrShape& S, int64_t i0, int64_t i1,
-                                                const double* __restrict__ tau, const float2* sG,
-                                                float2* __restrict__ grad_a) {
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += CFR_THREADS) {
-        PathPhase p = path_phase(tau[i], S.f0, S.df);
-        float2 B[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < S.N2) B[k] = phasor(p, k);
-        float2 acc = make_float2(0.0f, 0.0f);
-        for (int c1 = 0; c1 < S.N1; ++c1) {
+                                                const double* __restrict__ tau, const float2* sGt, const Tables& T,
+                                                bool reuse, float2* __restrict__ grad_a) {
+    float2* part = T.sAc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t base = i0; base < i1; base += CH) {
+        const int n = (int)min((int64_t)CH, i1 - base);
+        if (!reuse) build_tables(S, base, n, nullptr, tau, T);
+        __syncthreads();
+        for (int e = threadIdx.x; e < n * S.N1; e += CFR_THREADS) {
+            int ii = e / S.N1, c1 = e - ii * S.N1;
+            const float2* B = T.sB + ii * S.N2;
             float2 inner = make_float2(0.0f, 0.0f);
-            const float2* g = sG + c1 * S.N2;
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if (k < S.N2) {
-                    float2 gk = g[k];
-                    // inner += g * conj(B)
-                    inner.x = fmaf(gk.x, B[k].x, fmaf(gk.y, B[k].y, inner.x));
-                    inner.y = fmaf(gk.y, B[k].x, fmaf(-gk.x, B[k].y, inner.y));
-                }
-            float2 A = phasor(p, c1 * S.N2);
-            // acc += inner * conj(A)
-            acc.x = fmaf(inner.x, A.x, fmaf(inner.y, A.y, acc.x));
-            acc.y = fmaf(inner.y, A.x, fmaf(-inner.x, A.y, acc.y));
+            for (int k = 0; k < S.N2; ++k) {
+                float2 gk = sGt[k * S.N1 + c1], bk = B[k];
+                // inner += g * conj(B)
+                inner.x = fmaf(gk.x, bk.x, fmaf(gk.y, bk.y, inner.x));
+                inner.y = fmaf(gk.y, bk.x, fmaf(-gk.x, bk.y, inner.y));
+            }
+            part[e] = cmulc(inner, T.sA[e]);
         }
-        grad_a[i] = cmulc(acc, base_phasor(p));
+        __syncthreads();
+        for (int ii = warp; ii < n; ii += CFR_THREADS / 32) {
+            float2 acc = make_float2(0.0f, 0.0f);
+            for (int c1 = lane; c1 < S.N1; c1 += 32) {
+                float2 v = part[ii * S.N1 + c1];
+                acc.x += v.x;
+                acc.y += v.y;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+                acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+            }
+            if (lane == 0) grad_a[base + ii] = cmulc(acc, base_phasor(T.sP[ii]));
+        }
+        reuse = false;
     }
 }
 
@@ -154,12 +235,10 @@ __global__ void __launch_bounds__(CFR_THREADS) k_cfr_fwd(CfrShape S, const int64
                                                          const float2* __restrict__ a, const double* __restrict__ tau,
                                                          float2* __restrict__ H) {
     extern __shared__ float4 smem4[];
-    float2* sA = reinterpret_cast<float2*>(smem4);
-    float2* sB = sA + CH * S.N1;
-    PathPhase* sP = reinterpret_cast<PathPhase*>(sB + CH * (S.N2 + 1));
+    Tables T = carve(S, smem4);
     const int r = blockIdx.x;
     float2 acc[OPT];
-    cfr_rx_forward<OPT>(S, offs[r], offs[r + 1], a, tau, sA, sB, sP, acc);
+    cfr_rx_forward<OPT>(S, offs[r], offs[r + 1], a, tau, T, acc);
 #pragma unroll
     for (int m = 0; m < OPT; ++m) {
         int c = threadIdx.x + CFR_THREADS * m;
@@ -171,11 +250,14 @@ __global__ void __launch_bounds__(CFR_THREADS) k_cfr_bwd(CfrShape S, const int64
                                                          const double* __restrict__ tau, const float2* __restrict__ gH,
                                                          float2* __restrict__ ga) {
     extern __shared__ float4 smem4[];
-    float2* sG = reinterpret_cast<float2*>(smem4);
+    Tables T = carve(S, smem4);
+    float2* sG = carve_g(S, smem4);
     const int r = blockIdx.x;
-    for (int c = threadIdx.x; c < S.N; c += CFR_THREADS) sG[c] = gH[(int64_t)r * S.N + c];
-    __syncthreads();
-    cfr_rx_backward(S, offs[r], offs[r + 1], tau, sG, ga);
+    for (int c = threadIdx.x; c < S.N; c += CFR_THREADS) {
+        int c1 = c / S.N2, c2 = c - c1 * S.N2;
+        sG[c2 * S.N1 + c1] = gH[(int64_t)r * S.N + c];
+    }
+    cfr_rx_backward(S, offs[r], offs[r + 1], tau, sG, T, false, ga);
 }
 
 // Fused forward + power-MSE loss + adjoint for one receiver per CTA.  The loss
@@ -189,16 +271,14 @@ __global__ void __launch_bounds__(CFR_THREADS) k_cfr_fused(CfrShape S, const int
                                                            float2* __restrict__ H, double* __restrict__ part,
                                                            unsigned int* __restrict__ done) {
     extern __shared__ float4 smem4[];
-    float2* sA = reinterpret_cast<float2*>(smem4);
-    float2* sB = sA + CH * S.N1;
-    PathPhase* sP = reinterpret_cast<PathPhase*>(sB + CH * (S.N2 + 1));
-    float2* sG = reinterpret_cast<float2*>(sP + CH);
+    Tables T = carve(S, smem4);
+    float2* sG = carve_g(S, smem4);
     __shared__ double red[CFR_THREADS / 32];
     __shared__ bool last;
     const int r = blockIdx.x;
     const int64_t i0 = offs[r], i1 = offs[r + 1];
     float2 acc[OPT];
-    cfr_rx_forward<OPT>(S, i0, i1, a, tau, sA, sB, sP, acc);
+    const int chunks = cfr_rx_forward<OPT>(S, i0, i1, a, tau, T, acc);
     const float wr = w[r];
     const float inv_rn = 1.0f / ((float)R * (float)S.N);
     double lsum = 0.0;
@@ -212,7 +292,8 @@ __global__ void __launch_bounds__(CFR_THREADS) k_cfr_fused(CfrShape S, const int
             float we = wr * e;
             lsum += (double)(we * we);
             float s = 4.0f * wr * wr * e * inv_rn;   // dL/dH = 4 w^2 (|H|^2 - P*) H / (R N)
-            sG[c] = make_float2(s * h.x, s * h.y);
+            int c1 = c / S.N2, c2 = c - c1 * S.N2;
+            sG[c2 * S.N1 + c1] = make_float2(s * h.x, s * h.y);   // transposed for the adjoint
         }
     }
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
@@ -226,7 +307,7 @@ __global__ void __launch_bounds__(CFR_THREADS) k_cfr_fused(CfrShape S, const int
         unsigned int prev = atomicAdd(done, 1u);
         last = (prev == (unsigned)R - 1);
     }
-    cfr_rx_backward(S, i0, i1, tau, sG, ga);
+    cfr_rx_backward(S, i0, i1, tau, sG, T, chunks == 1, ga);
     __syncthreads();
     if (last) {
         __threadfence();
@@ -255,8 +336,12 @@ bool make_shape(int n_sub, double fc, double df, CfrShape& S) {
     return true;
 }
 
+// sAc + sA (CH x N1 each), sB (CH x N2), factors (CH x (8 + N1/8 + 8)), sP
+// (CH + padding), then optionally sG (N).
 size_t fwd_smem(const CfrShape& S) {
-    return (size_t)CH * S.N1 * 8 + (size_t)CH * (S.N2 + 1) * 8 + (size_t)CH * sizeof(PathPhase) + 16;
+    const size_t nf = 8 + (S.N1 + 7) / 8 + 8;
+    return 2 * (size_t)CH * S.N1 * 8 + (size_t)CH * S.N2 * 8 + (size_t)CH * nf * 8 + (size_t)CH * 8 +
+           (size_t)(CH + (CH & 1)) * sizeof(PathPhase) + 16;
 }
 
 template <typename F>
@@ -313,7 +398,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_backward(rt_c
     rt_status s = check_cfr(ctx, rx_offsets_dev, n_rx, tau_dev, n_sub, f_center_hz, delta_f_hz, S);
     if (s != RT_OK) return s;
     if (!grad_H_dev || !grad_a_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null device pointer");
-    const size_t smem = (size_t)S.N * 8;
+    const size_t smem = fwd_smem(S) + (size_t)S.N * 8;
     s = set_smem(ctx, k_cfr_bwd, smem);
     if (s != RT_OK) return s;
     k_cfr_bwd<<<n_rx, CFR_THREADS, smem, ctx->stream>>>(S, rx_offsets_dev, tau_dev, (const float2*)grad_H_dev,

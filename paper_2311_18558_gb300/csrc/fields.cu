@@ -184,7 +184,11 @@ __global__ void __launch_bounds__(256) k_fields_fwd(FieldArgs A, float2* __restr
     }
 }
 
-template <int MAXM>
+// Reduction of the per-material gradients: REGM > 0 keeps one register
+// accumulator per material (few materials: no shared-memory atomics on a handful
+// of hot addresses), MAXM > 0 accumulates in shared memory, otherwise global
+// atomics (per-triangle materials: scattered, little contention).
+template <int MAXM, int REGM>
 __global__ void __launch_bounds__(256) k_fields_bwd(FieldArgs A, const float2* __restrict__ ga, float* __restrict__ geps,
                                                     float* __restrict__ gsig, float* __restrict__ ggain, float inv_gtx,
                                                     float inv_grx, int n_mat) {
@@ -193,6 +197,9 @@ __global__ void __launch_bounds__(256) k_fields_bwd(FieldArgs A, const float2* _
         for (int m = threadIdx.x; m < n_mat; m += blockDim.x) s_eps[m] = s_sig[m] = 0.0f;
     if (threadIdx.x < 2) s_gain[threadIdx.x] = 0.0f;
     __syncthreads();
+    float r_eps[REGM > 0 ? REGM : 1], r_sig[REGM > 0 ? REGM : 1];
+#pragma unroll
+    for (int m = 0; m < (REGM > 0 ? REGM : 1); ++m) r_eps[m] = r_sig[m] = 0.0f;
     float gain_acc = 0.0f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.P; i += (int64_t)gridDim.x * blockDim.x) {
         const int q = __ldg(A.depth + i);
@@ -244,7 +251,14 @@ __global__ void __launch_bounds__(256) k_fields_bwd(FieldArgs A, const float2* _
                     float re = g.x * da.x + g.y * da.y;
                     float im = g.x * da.y - g.y * da.x;
                     float de = re, ds = im * A.inv_eps0w;   // da/dsigma = -j/(eps0 w) da/deta
-                    if (MAXM > 0) {
+                    if (REGM > 0) {
+#pragma unroll
+                        for (int m = 0; m < (REGM > 0 ? REGM : 1); ++m)
+                            if (m == mid[j]) {
+                                r_eps[m] += de;
+                                r_sig[m] += ds;
+                            }
+                    } else if (MAXM > 0) {
                         atomicAdd(&s_eps[mid[j]], de);
                         atomicAdd(&s_sig[mid[j]], ds);
                     } else {
@@ -261,6 +275,20 @@ __global__ void __launch_bounds__(256) k_fields_bwd(FieldArgs A, const float2* _
     }
     for (int o = 16; o > 0; o >>= 1) gain_acc += __shfl_down_sync(0xffffffffu, gain_acc, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(&s_gain[0], gain_acc);
+    if (REGM > 0) {
+#pragma unroll
+        for (int m = 0; m < (REGM > 0 ? REGM : 1); ++m) {
+            float e = r_eps[m], g = r_sig[m];
+            for (int o = 16; o > 0; o >>= 1) {
+                e += __shfl_down_sync(0xffffffffu, e, o);
+                g += __shfl_down_sync(0xffffffffu, g, o);
+            }
+            if ((threadIdx.x & 31) == 0 && m < n_mat) {
+                atomicAdd(&s_eps[m], e);
+                atomicAdd(&s_sig[m], g);
+            }
+        }
+    }
     __syncthreads();
     if (MAXM > 0) {
         for (int m = threadIdx.x; m < n_mat; m += blockDim.x) {
@@ -336,10 +364,12 @@ rt_status rt_launch_fields_bwd(rt_ctx* ctx, const rt_paths* p, const float* eps,
     FieldArgs A = make_args(p, eps, sig, per_tri, freq, gtx, grx);
     const int n_mat = per_tri ? p->scene->n_tris : p->scene->n_materials;
     const int grid = grid_for(ctx, p->P, 256, 4);
-    if (!per_tri && n_mat <= 64)
-        k_fields_bwd<64><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx, n_mat);
+    if (!per_tri && n_mat <= 8)
+        k_fields_bwd<8, 8><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx, n_mat);
+    else if (!per_tri && n_mat <= 64)
+        k_fields_bwd<64, 0><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx, n_mat);
     else
-        k_fields_bwd<0><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx, n_mat);
+        k_fields_bwd<0, 0><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx, n_mat);
     RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;

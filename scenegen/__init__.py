@@ -65,6 +65,7 @@ class Scene:
     n_sub: int                 # number of subcarriers
     per_triangle: bool = False  # materials indexed by triangle instead of by material id
     seed: int = 0
+    tri_object: Optional[np.ndarray] = None   # (T,) object index of each triangle (when meaningful)
 
     @property
     def n_tris(self) -> int:
@@ -375,11 +376,12 @@ def room_corridor(seed: int = 3, n_rx: int = 100_000, target_tris: int = 20_000)
         return max(1, int(round(a / h)))
 
     mb = _MeshBuilder()
-    v, t, _ = box_faces((0, 0, 0), (Lx, Ly, Lz), (nsub(Lx), nsub(Ly), nsub(Lz)), inward=True)
-    mb.add(v, t, 0)
+    v, t, fid = box_faces((0, 0, 0), (Lx, Ly, Lz), (nsub(Lx), nsub(Ly), nsub(Lz)), inward=True)
+    # objects: 0 floor, 1 ceiling, 2 walls, 3 partition
+    mb.add_mats(v, t, np.where(fid == 4, 0, np.where(fid == 5, 1, 2)))
     v, t, _ = box_faces(part[:3], part[3:], (nsub(px), nsub(py), nsub(pz)), skip_faces=((0, 0), (2, 0), (2, 1)))
-    mb.add(v, t, 0)
-    v, t, _ = mb.build()
+    mb.add(v, t, 3)
+    v, t, objects = mb.build()
     T = t.shape[0]
     cen = v[t].astype(np.float64).mean(axis=1)
     s1 = _smooth_field(rng, cen)
@@ -397,7 +399,7 @@ def room_corridor(seed: int = 3, n_rx: int = 100_000, target_tris: int = 20_000)
     return Scene(name="room_corridor", verts=v, tris=t, tri_material=np.arange(T, dtype=np.int32),
                  eps_r=eps, sigma=sig, is_pec=np.zeros(T, np.uint8), tx=_f32(tx), rx=_f32(rx),
                  n_rays=1_000_000, max_depth=3, freq_hz=1.272e9, f_center_hz=1.272e9,
-                 delta_f_hz=50e6 / 256, n_sub=256, per_triangle=True, seed=seed)
+                 delta_f_hz=50e6 / 256, n_sub=256, per_triangle=True, seed=seed, tri_object=objects)
 
 
 # --------------------------------------------------------------------------- tensors
