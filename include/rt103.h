@@ -154,6 +154,39 @@ rt_status rt_paths_export(const rt_paths* paths, int32_t* tri_seq_dev, int32_t* 
 rt_status rt_paths_candidates(const rt_paths* paths, int32_t* seq_dev);
 rt_status rt_paths_free(rt_paths* paths);
 
+/* Batched tracing of n_scenes scenes (Sec. II-F, as rt_trace_paths for each
+ * scene) in one pipeline: the shoot-and-bounce stage of all scenes runs as one
+ * persistent launch whose warps take rays of any scene, and every later stage is
+ * one launch over all scenes.  No counterpart in the paper (a batching of its
+ * path tracing).
+ *   scenes        n_scenes traceable scenes sharing one material table
+ *   tx_host       n_scenes x 3 doubles
+ *   rx_dev        all receivers, scene after scene (sum of rx_counts x 3 doubles)
+ *   rx_counts_host n_scenes int32, each >= 1
+ *   n_rays, max_depth  as rt_trace_paths, for every scene
+ * *out receives ONE paths object over all receivers (in that order); triangle
+ * ids in it are offset per scene (rt_paths_batch_info), and its materials are
+ * the shared table.  Per scene the paths equal those of rt_trace_paths.
+ * Synchronises. */
+rt_status rt_trace_batch(rt_ctx* ctx, const rt_scene* const* scenes, int32_t n_scenes, const double* tx_host,
+                         const double* rx_dev, const int32_t* rx_counts_host, int64_t n_rays, int32_t max_depth,
+                         rt_paths** out);
+/* Scenes of a batch output: receiver offsets and triangle-id offsets per scene
+ * (each n_scenes + 1 int64, host memory).  *n_scenes = 1 for a single trace. */
+rt_status rt_paths_batch_info(const rt_paths* paths, int32_t* n_scenes, int64_t* scene_rx_offsets_host,
+                              int64_t* scene_tri_offsets_host);
+/* Launch shapes of the tracing kernels (blocks per SM of the SBR, image-method
+ * and visibility kernels, each in [1, 64]). */
+rt_status rt_set_tuning(rt_ctx* ctx, int32_t sbr_blocks_per_sm, int32_t pairs_blocks_per_sm,
+                        int32_t vis_blocks_per_sm);
+/* Autotuner: times rt_trace_paths on the given workload for a set of launch
+ * shapes (coordinate descent, each knob judged by its own stage time), applies
+ * the fastest to ctx and writes it to chosen[3]; *best_ms (may be NULL) gets the
+ * summed stage times (0 when the choice came from the per-process cache keyed by
+ * device, scene size, rays, depth and receivers).  Synchronises. */
+rt_status rt_autotune_trace(rt_ctx* ctx, const rt_scene* scene, const double* tx_host, const double* rx_dev,
+                            int32_t n_rx, int64_t n_rays, int32_t max_depth, int32_t* chosen, double* best_ms);
+
 /* ------------------------------------------------------------------ fields */
 
 /* Path coefficients a_i of Eq. cfr_cont for every path:

@@ -311,3 +311,48 @@ def mlp_backward(ctx: Context, scene: Scene, w_bf16, act, eps, sig, grad_eps, gr
                                       _ptr(grad_eps.contiguous()), _ptr(grad_sigma.contiguous()), _ptr(dz),
                                       _ptr(grad_w), _ptr(grad_b)), "rt_mlp_backward")
     return grad_w, grad_b
+
+
+# ----------------------------------------------------------------------------- batches and tuning
+
+def trace_batch(ctx: Context, scenes, txs, rxs, n_rays: int, max_depth: int) -> Paths:
+    """Traces several scenes in one pipeline (rt_trace_batch).  Returns one Paths
+    over all receivers, scene after scene, with attributes scene_rx_offsets and
+    scene_tri_offsets (numpy, n_scenes + 1)."""
+    dev = torch.device("cuda", ctx.device)
+    rx_list = [torch.as_tensor(np.asarray(r) if not isinstance(r, torch.Tensor) else r, dtype=torch.float64)
+               for r in rxs]
+    counts = np.array([r.shape[0] for r in rx_list], np.int32)
+    rx_all = torch.cat([r.to(dev) for r in rx_list]).contiguous()
+    tx = np.ascontiguousarray(np.asarray(txs, np.float64).reshape(-1, 3))
+    n = len(scenes)
+    handles = (_c.c_void_p * n)(*[s.h.value for s in scenes])
+    h = _c.c_void_p()
+    ctx._stream()
+    ctx.check(ctx.lib.rt_trace_batch(ctx.h, handles, n, tx.ctypes.data_as(_c.c_void_p), _ptr(rx_all),
+                                     counts.ctypes.data_as(_c.c_void_p), int(n_rays), int(max_depth), _c.byref(h)),
+              "rt_trace_batch")
+    p = Paths(ctx, list(scenes), h, int(counts.sum()), max_depth)
+    ns = _c.c_int32()
+    rx_off = np.zeros(n + 1, np.int64)
+    tri_off = np.zeros(n + 1, np.int64)
+    ctx.lib.rt_paths_batch_info(h, _c.byref(ns), rx_off.ctypes.data_as(_c.c_void_p), tri_off.ctypes.data_as(_c.c_void_p))
+    p.scene_rx_offsets, p.scene_tri_offsets = rx_off, tri_off
+    p._rx_all = rx_all
+    return p
+
+
+def set_tuning(ctx: Context, sbr: int, pairs: int, vis: int):
+    ctx.check(ctx.lib.rt_set_tuning(ctx.h, int(sbr), int(pairs), int(vis)), "rt_set_tuning")
+
+
+def autotune_trace(ctx: Context, scene: Scene, tx, rx: torch.Tensor, n_rays: int, max_depth: int):
+    """Runs the tracing autotuner on this workload; returns ([sbr, pairs, vis] blocks per SM, summed stage ms)."""
+    rx = rx.to(device=torch.device("cuda", ctx.device), dtype=torch.float64).contiguous()
+    txa = (_c.c_double * 3)(*[float(v) for v in tx])
+    chosen = (_c.c_int32 * 3)()
+    ms = _c.c_double()
+    ctx._stream()
+    ctx.check(ctx.lib.rt_autotune_trace(ctx.h, scene.h, txa, _ptr(rx), rx.shape[0], int(n_rays), int(max_depth),
+                                        chosen, _c.byref(ms)), "rt_autotune_trace")
+    return list(chosen), float(ms.value)

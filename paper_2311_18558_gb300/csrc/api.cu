@@ -163,6 +163,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_destroy(rt_ctx* c
     for (int k = 0; k < 6; ++k)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
     if (ctx->d_counters) cudaFree(ctx->d_counters);
+    if (ctx->d_sched_order) cudaFree(ctx->d_sched_order);
+    if (ctx->d_sched_wrap) cudaFree(ctx->d_sched_wrap);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -505,6 +507,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_upload(rt_c
         rt_scene_free(sc);
         return rt_cuda_fail(ctx, e, "scene upload");
     }
+    sc->h_is_pec = new uint8_t[n_materials];
+    std::memcpy(sc->h_is_pec, is_pec, n_materials);
     *out = sc;
     return RT_OK;
 }
@@ -519,6 +523,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_free(rt_sce
     cudaFree(sc->d_tri_bary64);
     cudaFree(sc->d_tri_material);
     cudaFree(sc->d_is_pec);
+    delete[] sc->h_is_pec;
     delete sc;
     return RT_OK;
 }
@@ -540,6 +545,12 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_paths_free(rt_pat
                     p->d_cos,        p->d_Dm, p->d_pts,   p->d_cand};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, st);
+    if (p->owned_scene) {
+        cudaStreamSynchronize(st);
+        rt_scene_free(p->owned_scene);
+    }
+    delete[] p->h_scene_rx_off;
+    delete[] p->h_scene_tri_off;
     delete p;
     return RT_OK;
 }
@@ -548,6 +559,17 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_paths_count(const
     if (!p) return RT_ERR_INVALID_ARG;
     if (n_paths) *n_paths = p->P;
     if (n_candidates) *n_candidates = p->K;
+    return RT_OK;
+}
+
+extern "C" __attribute__((visibility("default"))) rt_status rt_paths_batch_info(const rt_paths* p, int32_t* n_scenes,
+                                                                                int64_t* rx_off, int64_t* tri_off) {
+    if (!p) return RT_ERR_INVALID_ARG;
+    if (n_scenes) *n_scenes = p->n_scenes;
+    for (int s = 0; s <= p->n_scenes; ++s) {
+        if (rx_off) rx_off[s] = p->h_scene_rx_off ? p->h_scene_rx_off[s] : (s == 0 ? 0 : p->R);
+        if (tri_off) tri_off[s] = p->h_scene_tri_off ? p->h_scene_tri_off[s] : (s == 0 ? 0 : p->scene->n_tris);
+    }
     return RT_OK;
 }
 

@@ -36,6 +36,14 @@ struct rt_ctx {
     unsigned long long* d_counters = nullptr;   // 8 device counters (bit 1)
     int64_t h_counters[8] = {0};                // host-side counts of the same slots
     cudaEvent_t ev[6] = {};                     // trace stage events (bit 0)
+    // coherent processing order of the launch directions, per ray count (see trace.cu)
+    int64_t sched_n = 0, sched_band = 0, sched_full = 0;
+    int32_t* d_sched_order = nullptr;   // sched_band entries
+    int32_t* d_sched_wrap = nullptr;    // sched_full entries
+    // launch shapes of the tracing kernels (blocks per SM), set by the autotuner
+    int tune_sbr_blocks_per_sm = 8;
+    int tune_pairs_blocks_per_sm = 16;
+    int tune_vis_blocks_per_sm = 8;
 };
 
 // Count one kernel launch of `ctx` (every launch site calls this).
@@ -68,6 +76,8 @@ struct rt_scene {
     uint8_t* d_is_pec = nullptr;
     size_t hash_cap = 1u << 20;        // learned dedup table capacity
     size_t queue_cap = 1u << 20;       // learned visibility-queue capacity
+    uint8_t* h_is_pec = nullptr;       // host copy of the material PEC flags (batch checks)
+    bool owns_tables_only = false;     // combined batch scene: no BVH, tables owned here
 };
 
 struct rt_paths {
@@ -85,6 +95,10 @@ struct rt_paths {
     float4* d_Dm = nullptr;            // (D + 1) x P basis changes D_1 .. D_{q+1} (row major 2x2)
     double* d_pts = nullptr;           // P x (D + 2) x 3
     uint64_t* d_cand = nullptr;        // K packed candidate keys
+    rt_scene* owned_scene = nullptr;   // batch output: combined triangle tables, freed with the paths
+    int32_t n_scenes = 1;              // batch output: number of traced scenes
+    int64_t* h_scene_rx_off = nullptr; // batch output: receiver offset of each scene (n_scenes + 1)
+    int64_t* h_scene_tri_off = nullptr;// batch output: triangle-id offset of each scene (n_scenes + 1)
 };
 
 // ---------------------------------------------------------------- error helpers

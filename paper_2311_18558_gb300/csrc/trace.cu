@@ -20,7 +20,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "rt_internal.cuh"
@@ -451,6 +453,28 @@ __device__ __forceinline__ float3 launch_dir(int64_t i, int64_t n) {
     return make_float3(__fmul_rn(r, c), __fmul_rn(r, s), z);
 }
 
+// Processing order of the rays (the set of rays and every result are the same
+// in any order).  Consecutive Fibonacci indices have nearby z but azimuths a
+// golden angle apart, so a warp of consecutive rays diverges.  Instead the rays
+// are taken in z-bands of B consecutive indices, and inside a band by azimuth:
+// the azimuth fraction of ray i0 + k is (i0 G + k G) mod 2^32, i.e. the fractions
+// of k G shifted by a constant, so every band's order is one fixed sorted list
+// of k (by k G mod 2^32) rotated to start at the band's wrap point.
+struct RaySched {
+    int64_t n, band, full;
+    const int32_t* order;
+    const int32_t* wrap;
+};
+
+__device__ __forceinline__ int64_t sched_ray(const RaySched& S, int64_t j) {
+    if (S.band <= 0) return j;
+    const int64_t b = j / S.band;
+    if (b >= S.full) return j;
+    int64_t pos = (j - b * S.band) + S.wrap[b];
+    if (pos >= S.band) pos -= S.band;
+    return b * S.band + S.order[pos];
+}
+
 // ------------------------------------------------------------------ hash set of keys
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     // 64-bit finaliser of SplitMix64 (Steele, Lea, Flood 2014)
@@ -501,6 +525,7 @@ struct SbrArgs {
     int64_t redo_cap;
     int32_t* status;
     unsigned long long* counters;   // optional instrumentation (slots 0..3)
+    RaySched sched;
 };
 
 // Adds a per-thread count to a device counter (one atomic per warp).
@@ -544,6 +569,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
             if (need) {
                 int64_t idx = (int64_t)(base + __popc(m & ((1u << lane) - 1)));
                 if (idx < A.n_rays) {
+                    idx = sched_ray(A.sched, idx);
                     ray = idx;
                     bounce = 0;
                     prev = -1;
@@ -840,6 +866,34 @@ __device__ __forceinline__ bool prefilter32(const CandView& C, int64_t k, int q,
     return true;
 }
 
+constexpr int PAIR_CC = 32;   // candidates per warp tile (receivers per tile: 32 lanes)
+
+// One warp tile of the image-method prefilter: 32 receivers (one per lane, kept
+// in registers) against up to PAIR_CC consecutive candidates (candidate data is
+// read once per warp and broadcast).  Survivors are appended to the queue as
+// (global candidate, global receiver), one atomic per warp and candidate.
+__device__ __forceinline__ void pairs_tile(const CandView& C, int64_t k0, int64_t k1, int64_t r_glob, bool r_ok,
+                                           float3 rxf, const float4* __restrict__ tri_bary, uint2* queue,
+                                           unsigned long long* qcount, unsigned long long qcap, int32_t* overflow) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t k = k0; k < k1; ++k) {
+        const int q = C.depth[k];
+        const bool ok = r_ok && (q == 0 || prefilter32(C, k, q, rxf, tri_bary));
+        const unsigned m = __ballot_sync(FULL, ok);
+        if (m) {
+            unsigned long long base = 0;
+            const int leader = __ffs(m) - 1;
+            if (lane == leader) base = atomicAdd(qcount, (unsigned long long)__popc(m));
+            base = __shfl_sync(FULL, base, leader);
+            if (ok) {
+                const unsigned long long slot = base + __popc(m & ((1u << lane) - 1));
+                if (slot < qcap) queue[slot] = make_uint2((unsigned)k, (unsigned)r_glob);
+                else atomicExch(overflow, 1);
+            }
+        }
+    }
+}
+
 struct PairArgs {
     CandView C;
     int R;
@@ -851,38 +905,22 @@ struct PairArgs {
     int32_t* overflow;
 };
 
-// Image-method prefilter over all (candidate, receiver) pairs, FP32 only; lanes
-// of a warp take consecutive receivers of the same candidate.  Survivors are
-// compacted into the queue (one atomic per warp); the FP64 work happens on the
-// dense queue.
+// Image-method prefilter over all (candidate, receiver) pairs, FP32 only, in
+// warp tiles (see pairs_tile).  The FP64 work happens on the dense queue.
 __global__ void k_pairs(PairArgs A) {
     const int lane = threadIdx.x & 31;
-    const int64_t total = A.C.K * (int64_t)A.R;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x; p0 < total; p0 += stride) {
-        int64_t p = p0 + threadIdx.x;
-        bool ok = false;
-        int64_t k = 0;
-        int r = 0;
-        if (p < total) {
-            k = p / A.R;
-            r = (int)(p - k * A.R);
-            int q = A.C.depth[k];
-            const double* rp = A.rx + 3 * (int64_t)r;
-            ok = q == 0 || prefilter32(A.C, k, q, make_float3((float)rp[0], (float)rp[1], (float)rp[2]), A.tri_bary);
-        }
-        unsigned m = __ballot_sync(FULL, ok);
-        if (m) {
-            unsigned long long base = 0;
-            int leader = __ffs(m) - 1;
-            if (lane == leader) base = atomicAdd(A.qcount, (unsigned long long)__popc(m));
-            base = __shfl_sync(FULL, base, leader);
-            if (ok) {
-                unsigned long long slot = base + __popc(m & ((1u << lane) - 1));
-                if (slot < A.qcap) A.queue[slot] = make_uint2((unsigned)k, (unsigned)r);
-                else atomicExch(A.overflow, 1);
-            }
-        }
+    const int64_t rt_n = (A.R + 31) / 32, kt_n = (A.C.K + PAIR_CC - 1) / PAIR_CC;
+    const int64_t tiles = rt_n * kt_n;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = warp0; t < tiles; t += nwarps) {
+        const int64_t kt = t / rt_n, rt = t - kt * rt_n;
+        const int64_t r = rt * 32 + lane;
+        const bool r_ok = r < A.R;
+        float3 rxf = make_float3(0.0f, 0.0f, 0.0f);
+        if (r_ok) rxf = make_float3((float)A.rx[3 * r], (float)A.rx[3 * r + 1], (float)A.rx[3 * r + 2]);
+        const int64_t k0 = kt * PAIR_CC, k1 = min(A.C.K, k0 + PAIR_CC);
+        pairs_tile(A.C, k0, k1, r, r_ok, rxf, A.tri_bary, A.queue, A.qcount, A.qcap, A.overflow);
     }
 }
 
@@ -1132,6 +1170,47 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // ---------------------------------------------------------------------------
 // Host driver of the tracing pipeline.
 
+// Builds (once per ray count) the band order of the coherent ray schedule.
+static rt_status ray_schedule(rt_ctx* ctx, int64_t n, RaySched* out) {
+    if (ctx->sched_n != n) {
+        int64_t band = (int64_t)std::llround(8.0 * std::sqrt((double)n) / 32.0) * 32;
+        band = std::max<int64_t>(32, std::min<int64_t>(band, 1 << 20));
+        if (band > n) band = 0;
+        const int64_t full = band > 0 ? n / band : 0;
+        std::vector<int32_t> order(std::max<int64_t>(band, 1)), wrap(std::max<int64_t>(full, 1));
+        if (band > 0) {
+            std::vector<uint32_t> key(band);
+            for (int64_t k = 0; k < band; ++k) {
+                key[k] = (uint32_t)((uint64_t)k * 0x9E3779B9ull);
+                order[k] = (int32_t)k;
+            }
+            std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+            std::vector<uint32_t> sk(band);
+            for (int64_t j = 0; j < band; ++j) sk[j] = key[order[j]];
+            for (int64_t b = 0; b < full; ++b) {
+                // fractions of band b are (sk + c) mod 2^32: they wrap where sk >= 2^32 - c
+                const uint32_t c = (uint32_t)((uint64_t)(b * band) * 0x9E3779B9ull);
+                int64_t j = 0;
+                if (c != 0) j = std::lower_bound(sk.begin(), sk.end(), (uint32_t)(0u - c)) - sk.begin();
+                wrap[b] = (int32_t)(j == band ? 0 : j);
+            }
+        }
+        if (ctx->d_sched_order) RT_CK(ctx, cudaFree(ctx->d_sched_order));
+        if (ctx->d_sched_wrap) RT_CK(ctx, cudaFree(ctx->d_sched_wrap));
+        ctx->d_sched_order = ctx->d_sched_wrap = nullptr;
+        ctx->sched_n = 0;
+        RT_CK(ctx, cudaMalloc((void**)&ctx->d_sched_order, order.size() * 4));
+        RT_CK(ctx, cudaMalloc((void**)&ctx->d_sched_wrap, wrap.size() * 4));
+        RT_CK(ctx, cudaMemcpy(ctx->d_sched_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice));
+        RT_CK(ctx, cudaMemcpy(ctx->d_sched_wrap, wrap.data(), wrap.size() * 4, cudaMemcpyHostToDevice));
+        ctx->sched_n = n;
+        ctx->sched_band = band;
+        ctx->sched_full = full;
+    }
+    *out = RaySched{ctx->sched_n, ctx->sched_band, ctx->sched_full, ctx->d_sched_order, ctx->d_sched_wrap};
+    return RT_OK;
+}
+
 static void mark(rt_ctx* ctx, int k) {
     if (ctx->profile & 1) cudaEventRecord(ctx->ev[k], ctx->stream);
 }
@@ -1205,7 +1284,11 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         A.redo_cap = redo_cap;
         A.status = status;
         A.counters = (ctx->profile & 2) ? ctx->d_counters : nullptr;
-        int blocks = ctx->num_sms * 8;
+        {
+            rt_status ss = ray_schedule(ctx, n_rays, &A.sched);
+            if (ss != RT_OK) return ss;
+        }
+        int blocks = ctx->num_sms * ctx->tune_sbr_blocks_per_sm;
         k_sbr<<<blocks, TRACE_THREADS, stack_bytes, st>>>(A, sc->d_tri_v); RT_COUNT(ctx);
         RT_CK_LAUNCH(ctx);
         k_sbr_redo<<<ctx->num_sms * 4, REDO_THREADS, (size_t)RT_STACK * REDO_THREADS * sizeof(int), st>>>(
@@ -1311,7 +1394,9 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         PA.qcap = qcap;
         PA.overflow = flags;
         mark(ctx, 2);
-        k_pairs<<<grid_for(ctx, K * (int64_t)n_rx, 256, 16), 256, 0, st>>>(PA); RT_COUNT(ctx);
+        k_pairs<<<grid_for(ctx, ((K + PAIR_CC - 1) / PAIR_CC) * ((n_rx + 31) / 32) * 32, 256,
+                           ctx->tune_pairs_blocks_per_sm),
+                  256, 0, st>>>(PA); RT_COUNT(ctx);
         mark(ctx, 3);
         TCK(cudaGetLastError());
         VisArgs VA;
@@ -1334,7 +1419,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         VA.status = status;
         VA.counters = (ctx->profile & 2) ? ctx->d_counters : nullptr;
         ctx->h_counters[7] += K * (int64_t)n_rx;
-        k_visibility<<<ctx->num_sms * 8, TRACE_THREADS, stack_bytes, st>>>(VA); RT_COUNT(ctx);
+        k_visibility<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, stack_bytes, st>>>(VA); RT_COUNT(ctx);
         mark(ctx, 4);
         TCK(cudaGetLastError());
         int64_t* hp = ctx->h_pinned;
@@ -1418,5 +1503,912 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
     }
 #undef TCK
     *out = p;
+    return RT_OK;
+}
+
+// ===========================================================================
+// Batched tracing of many scenes (uneven sizes) in one pipeline.
+//
+// SBR runs as ONE persistent launch over the rays of all scenes: lanes refill
+// from a global ray counter and find their scene by binary search in the
+// prefix of per-scene ray counts, so warps stay full across scene boundaries
+// and a small scene never leaves SMs idle.  Every later stage is likewise one
+// launch over the concatenated (scene, candidate, receiver) index spaces.  The
+// output is one paths object: receivers concatenated in scene order, triangle
+// ids offset per scene into combined triangle tables.
+
+namespace {
+
+struct SceneDev {
+    const BvhNode* nodes;
+    const float4* bvh_tris;
+    const float4* tri_v;
+    const float4* tri_bary;
+    const double* tri_n64;
+    const double* bary64;
+    double tx, ty, tz, eps;
+    int64_t n_rays;
+    int32_t tri_off;
+};
+
+template <typename T>
+__device__ __forceinline__ int find_seg(const T* __restrict__ off, int n, T idx) {   // last s with off[s] <= idx
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct BatchSbr {
+    const SceneDev* sd;
+    const int64_t* ray_off;   // n + 1
+    int n;
+    int depth;
+    unsigned long long* tables;   // n x cap
+    uint64_t cap;
+    unsigned long long* uniq;     // n
+    unsigned long long uniq_limit;
+    int32_t* overflow;
+    unsigned long long* next_ray;
+    int64_t* redo;
+    unsigned long long* redo_count;
+    int64_t redo_cap;
+    int32_t* status;
+    int blocks_per_sm;
+    RaySched sched;
+};
+
+__global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
+    extern __shared__ int smem_stack[];
+    int* stack = smem_stack + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = A.ray_off[A.n];
+    int64_t ray = -1;
+    bool done = false;
+    int bounce = 0, prev = -1, s = 0;
+    uint64_t key = 0;
+    WRay<float> r;
+    for (;;) {
+        bool need = (ray < 0) && !done;
+        unsigned m = __ballot_sync(FULL, need);
+        if (m) {
+            unsigned long long base = 0;
+            int leader = __ffs(m) - 1;
+            if (lane == leader) base = atomicAdd(A.next_ray, (unsigned long long)__popc(m));
+            base = __shfl_sync(FULL, base, leader);
+            if (need) {
+                int64_t idx = (int64_t)(base + __popc(m & ((1u << lane) - 1)));
+                if (idx < total) {
+                    s = find_seg(A.ray_off, A.n + 1, idx);
+                    const SceneDev& d = A.sd[s];
+                    idx = A.ray_off[s] + sched_ray(A.sched, idx - A.ray_off[s]);
+                    ray = idx;
+                    bounce = 0;
+                    prev = -1;
+                    key = 0;
+                    float3 dir = launch_dir(idx - A.ray_off[s], d.n_rays);
+                    r.o = mk((float)d.tx, (float)d.ty, (float)d.tz);
+                    r.d = mk(dir.x, dir.y, dir.z);
+                    wray_init(r);
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (__all_sync(FULL, done)) break;
+        if (ray < 0) continue;
+        const SceneDev& d = A.sd[s];
+        float th;
+        bool und = false;
+        unsigned nv = 0, nt = 0;
+        int id = closest32(d.nodes, d.bvh_tris, r, (float)d.eps, prev, stack, th, und, A.status, nv, nt);
+        if (und) {
+            unsigned long long slot = atomicAdd(A.redo_count, 1ull);
+            if ((int64_t)slot < A.redo_cap) A.redo[slot] = ray;
+            else atomicExch(A.overflow, 2);
+            ray = -1;
+            continue;
+        }
+        if (id < 0) {
+            ray = -1;
+            continue;
+        }
+        key = rt_key_push(key, bounce, id);
+        hash_insert(A.tables + (uint64_t)s * A.cap, A.cap - 1, key, A.uniq + s, A.uniq_limit, A.overflow);
+        bounce++;
+        if (bounce >= A.depth) {
+            ray = -1;
+            continue;
+        }
+        float3 nrm = tri_normal_f(d.tri_v, id);
+        V3<float> nn = mk(nrm.x, nrm.y, nrm.z);
+        V3<float> p = r.o + th * r.d;
+        r.d = r.d - (2.0f * dot(r.d, nn)) * nn;
+        r.o = p;
+        wray_init(r);
+        prev = id;
+    }
+}
+
+__global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo_batch(BatchSbr A) {
+    extern __shared__ int smem_stack[];
+    int* stack = smem_stack + threadIdx.x;
+    unsigned long long n = *A.redo_count;
+    if (n > (unsigned long long)A.redo_cap) n = A.redo_cap;
+    for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
+         w += (unsigned long long)gridDim.x * blockDim.x) {
+        int64_t ray = A.redo[w];
+        int s = find_seg(A.ray_off, A.n + 1, ray);
+        const SceneDev& d = A.sd[s];
+        float3 df = launch_dir(ray - A.ray_off[s], d.n_rays);
+        WRay<double> r;
+        WRay<float> rf;
+        r.o = mk(d.tx, d.ty, d.tz);
+        r.d = mk((double)df.x, (double)df.y, (double)df.z);
+        int prev = -1;
+        uint64_t key = 0;
+        for (int b = 0; b < A.depth; ++b) {
+            wray_init(r);
+            rf.o = mk((float)r.o.x, (float)r.o.y, (float)r.o.z);
+            rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
+            wray_init(rf);
+            double th;
+            int id = closest64(d.nodes, d.bvh_tris, r, rf, d.eps, prev, stack, th, A.status);
+            if (id < 0) break;
+            key = rt_key_push(key, b, id);
+            hash_insert(A.tables + (uint64_t)s * A.cap, A.cap - 1, key, A.uniq + s, A.uniq_limit, A.overflow);
+            V3<double> nn = mk(d.tri_n64[4 * id], d.tri_n64[4 * id + 1], d.tri_n64[4 * id + 2]);
+            V3<double> p = r.o + th * r.d;
+            r.d = r.d - (2.0 * dot(r.d, nn)) * nn;
+            r.o = p;
+            prev = id;
+        }
+    }
+}
+
+// Unique keys of every scene's table into that scene's sort buffer (cap is a
+// power of two >= 2^16, so a warp never spans two tables).
+__global__ void k_table_compact_batch(const unsigned long long* __restrict__ tables, int n, uint64_t cap,
+                                      uint64_t* out, uint64_t out_stride, unsigned long long* counts) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t total = cap * (uint64_t)n;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i - lane < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        unsigned long long k = i < total ? tables[i] : 0ull;
+        int s = (int)((i - lane) / cap);
+        unsigned m = __ballot_sync(FULL, k != 0ull);
+        if (!m) continue;
+        unsigned long long base = 0;
+        int leader = __ffs(m) - 1;
+        if (lane == leader) base = atomicAdd(counts + s, (unsigned long long)__popc(m));
+        base = __shfl_sync(FULL, base, leader);
+        if (k) out[s * out_stride + base + __popc(m & ((1u << lane) - 1))] = k;
+    }
+}
+
+// Image sources of every candidate of every scene (global candidate index).
+__global__ void k_candidates_batch(const uint64_t* __restrict__ keys, int64_t K, int D, const SceneDev* sd,
+                                   const int64_t* cand_off, int n, int32_t* cand_depth, int32_t* cand_tri,
+                                   double* img64, float4* img32) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
+        const SceneDev& d = sd[find_seg(cand_off, n + 1, k)];
+        uint64_t key = keys[k];
+        int q = rt_key_depth(key);
+        cand_depth[k] = q;
+        V3<double> I = mk(d.tx, d.ty, d.tz);
+        for (int j = 0; j < D; ++j) {
+            int t = j < q ? rt_key_tri(key, j) : -1;
+            cand_tri[(int64_t)j * K + k] = t;
+            if (t >= 0) {
+                V3<double> nn = mk(d.tri_n64[4 * t], d.tri_n64[4 * t + 1], d.tri_n64[4 * t + 2]);
+                V3<double> a = from4<double>(__ldg(d.tri_v + 3 * t));
+                I = I - (2.0 * dot(I - a, nn)) * nn;
+            }
+            double* o = img64 + ((int64_t)j * K + k) * 3;
+            o[0] = I.x;
+            o[1] = I.y;
+            o[2] = I.z;
+            img32[(int64_t)j * K + k] = make_float4((float)I.x, (float)I.y, (float)I.z, 0.0f);
+        }
+    }
+}
+
+struct BatchPairs {
+    CandView C;   // global candidates
+    const SceneDev* sd;
+    const int64_t* tile_off;   // n + 1: prefix of warp tiles per scene
+    const int64_t* cand_off;   // n + 1
+    const int64_t* rx_off;     // n + 1
+    int n;
+    const double* rx;          // all receivers
+    uint2* queue;
+    unsigned long long* qcount;
+    unsigned long long qcap;
+    int32_t* overflow;
+};
+
+// Batched prefilter: warp tiles of every scene in one index space (the scene of
+// a tile is found once per tile).
+__global__ void k_pairs_batch(BatchPairs A) {
+    const int lane = threadIdx.x & 31;
+    const int64_t tiles = A.tile_off[A.n];
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = warp0; t < tiles; t += nwarps) {
+        const int s = find_seg(A.tile_off, A.n + 1, t);
+        const int64_t R = A.rx_off[s + 1] - A.rx_off[s];
+        const int64_t K = A.cand_off[s + 1] - A.cand_off[s];
+        const int64_t rt_n = (R + 31) / 32;
+        const int64_t lt = t - A.tile_off[s];
+        const int64_t kt = lt / rt_n, rt = lt - kt * rt_n;
+        const int64_t r = rt * 32 + lane;
+        const bool r_ok = r < R;
+        const int64_t rg = A.rx_off[s] + r;
+        float3 rxf = make_float3(0.0f, 0.0f, 0.0f);
+        if (r_ok) rxf = make_float3((float)A.rx[3 * rg], (float)A.rx[3 * rg + 1], (float)A.rx[3 * rg + 2]);
+        const int64_t k0 = A.cand_off[s] + kt * PAIR_CC, k1 = A.cand_off[s] + min(K, (kt + 1) * PAIR_CC);
+        pairs_tile(A.C, k0, k1, rg, r_ok, rxf, A.sd[s].tri_bary, A.queue, A.qcount, A.qcap, A.overflow);
+    }
+}
+
+struct BatchVis {
+    CandView C;
+    const SceneDev* sd;
+    const int64_t* cand_off;
+    const int64_t* rx_off;
+    const int64_t* bits_off;   // n + 1, in words
+    int n;
+    const double* rx;
+    const uint2* queue;
+    const unsigned long long* qcount;
+    unsigned long long qcap;
+    uint32_t* bits;
+    int32_t* status;
+};
+
+__global__ void __launch_bounds__(TRACE_THREADS) k_visibility_batch(BatchVis A) {
+    extern __shared__ int smem_stack[];
+    int* stack = smem_stack + threadIdx.x;
+    unsigned long long n = *A.qcount;
+    if (n > A.qcap) n = A.qcap;
+    for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
+         w += (unsigned long long)gridDim.x * blockDim.x) {
+        uint2 e = A.queue[w];
+        int64_t kg = e.x, rg = e.y;
+        int s = find_seg(A.cand_off, A.n + 1, kg);
+        const SceneDev& d = A.sd[s];
+        int q = A.C.depth[kg];
+        const double* rp = A.rx + 3 * rg;
+        V3<double> pts[RT_MAX_DEPTH + 2];
+        if (!backtrace64(A.C, kg, q, mk(d.tx, d.ty, d.tz), mk(rp[0], rp[1], rp[2]), d.tri_v, d.tri_n64, d.bary64,
+                         d.eps, pts, nullptr))
+            continue;
+        bool visible = true;
+        for (int j = 0; j <= q && visible; ++j) {
+            V3<double> dv = pts[j + 1] - pts[j];
+            double il = rsqrt(dot(dv, dv));
+            int s0 = j >= 1 ? A.C.tri[(int64_t)(j - 1) * A.C.K + kg] : -1;
+            int s1 = j + 1 <= q ? A.C.tri[(int64_t)j * A.C.K + kg] : -1;
+            double tlo = d.eps * il, thi = 1.0 - d.eps * il;
+            WRay<float> rf;
+            rf.o = mk((float)pts[j].x, (float)pts[j].y, (float)pts[j].z);
+            rf.d = mk((float)dv.x, (float)dv.y, (float)dv.z);
+            wray_init(rf);
+            bool und = false;
+            unsigned nv = 0, nt = 0;
+            if (any32(d.nodes, d.bvh_tris, rf, (float)tlo, (float)thi, s0, s1, stack, und, A.status, nv, nt)) {
+                visible = false;
+            } else if (und) {
+                WRay<double> rd;
+                rd.o = pts[j];
+                rd.d = dv;
+                wray_init(rd);
+                if (any64(d.nodes, d.bvh_tris, rd, rf, tlo, thi, s0, s1, stack, A.status)) visible = false;
+            }
+        }
+        if (visible) {
+            const int64_t words = (A.cand_off[s + 1] - A.cand_off[s] + 31) / 32;
+            const int64_t kl = kg - A.cand_off[s];
+            atomicOr(A.bits + A.bits_off[s] + (rg - A.rx_off[s]) * words + (kl >> 5), 1u << (kl & 31));
+        }
+    }
+}
+
+// Per-receiver popcount over all scenes (one warp per receiver).
+__global__ void k_row_count_batch(const uint32_t* __restrict__ bits, const int64_t* rx_off, const int64_t* cand_off,
+                                  const int64_t* bits_off, int n, int64_t* counts) {
+    const int lane = threadIdx.x & 31;
+    const int64_t R = rx_off[n];
+    for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < R;
+         g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int s = find_seg(rx_off, n + 1, g);
+        const int64_t words = (cand_off[s + 1] - cand_off[s] + 31) / 32;
+        const uint32_t* row = bits + bits_off[s] + (g - rx_off[s]) * words;
+        int64_t c = 0;
+        for (int64_t w = lane; w < words; w += 32) c += __popc(row[w]);
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(FULL, c, o);
+        if (lane == 0) counts[g] = c;
+    }
+}
+
+__global__ void k_expand_batch(const uint32_t* __restrict__ bits, const int64_t* rx_off, const int64_t* cand_off,
+                               const int64_t* bits_off, int n, const int64_t* __restrict__ offsets, int32_t* path_rx,
+                               int32_t* path_cand) {
+    const int lane = threadIdx.x & 31;
+    const int64_t R = rx_off[n];
+    for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < R;
+         g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int s = find_seg(rx_off, n + 1, g);
+        const int64_t words = (cand_off[s + 1] - cand_off[s] + 31) / 32;
+        const uint32_t* row = bits + bits_off[s] + (g - rx_off[s]) * words;
+        int64_t pos = offsets[g];
+        for (int64_t w0 = 0; w0 < words; w0 += 32) {
+            int64_t w = w0 + lane;
+            uint32_t b = w < words ? row[w] : 0u;
+            int c = __popc(b);
+            int incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                int v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            int64_t my = pos + incl - c;
+            while (b) {
+                int bit = __ffs(b) - 1;
+                b &= b - 1;
+                path_rx[my] = (int32_t)g;
+                path_cand[my] = (int32_t)(cand_off[s] + w * 32 + bit);
+                my++;
+            }
+            pos += __shfl_sync(FULL, incl, 31);
+        }
+    }
+}
+
+// FP64 points of every path; triangle slots carry global (offset) ids.
+__global__ void k_points_batch(CandView C, int64_t P, int D, const SceneDev* sd, const int64_t* cand_off, int n,
+                               const int32_t* __restrict__ path_rx, const int32_t* __restrict__ path_cand,
+                               const double* __restrict__ rx, double* pts_out, int32_t* depth_out, int32_t* rx_out,
+                               int32_t* tri_out, int32_t* edge_flag, int32_t* status) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t kg = path_cand[i];
+        int r = path_rx[i];
+        const SceneDev& d = sd[find_seg(cand_off, n + 1, kg)];
+        int q = C.depth[kg];
+        const double* rp = rx + 3 * (int64_t)r;
+        V3<double> pts[RT_MAX_DEPTH + 2];
+        double mb = 1.0;
+        if (!backtrace64(C, kg, q, mk(d.tx, d.ty, d.tz), mk(rp[0], rp[1], rp[2]), d.tri_v, d.tri_n64, d.bary64, d.eps,
+                         pts, &mb))
+            rt_set_status(status, RT_ERR_NUMERIC);
+        for (int j = 0; j < D + 2; ++j) {
+            V3<double> v = j <= q + 1 ? pts[j] : mk(0.0, 0.0, 0.0);
+            double* o = pts_out + ((int64_t)i * (D + 2) + j) * 3;
+            o[0] = v.x;
+            o[1] = v.y;
+            o[2] = v.z;
+        }
+        depth_out[i] = q;
+        rx_out[i] = r;
+        for (int j = 0; j < D; ++j)
+            tri_out[(int64_t)j * P + i] = j < q ? C.tri[(int64_t)j * C.K + kg] + d.tri_off : -1;
+        edge_flag[i] = (q > 0 && mb <= 1e-8) ? 1 : 0;
+    }
+}
+
+// Duplicate rule over all scenes (global path, receiver, triangle and
+// candidate indices; bits cleared in the scene's own bitmask layout).
+__global__ void k_dedup_batch(int64_t P, int D, const int64_t* __restrict__ path_off, const int32_t* __restrict__ path_rx,
+                              const int32_t* __restrict__ path_cand, const int32_t* __restrict__ depth,
+                              const int32_t* __restrict__ tri, const double* __restrict__ pts,
+                              const int32_t* __restrict__ edge_flag, const double* __restrict__ tri_n64,
+                              const float4* __restrict__ tri_v, double diag, const int64_t* rx_off,
+                              const int64_t* cand_off, const int64_t* bits_off, int n, uint32_t* bits,
+                              unsigned long long* drops) {
+    const double tol2 = (1e-9 * diag) * (1e-9 * diag);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!edge_flag[i]) continue;
+        int r = path_rx[i];
+        int q = depth[i];
+        for (int64_t j = path_off[r]; j < path_off[r + 1]; ++j) {
+            if (j == i || !edge_flag[j] || depth[j] != q) continue;
+            bool same = true;
+            for (int b = 0; b < q && same; ++b)
+                same = coplanar64(tri_n64, tri_v, tri[(int64_t)b * P + i], tri[(int64_t)b * P + j], diag);
+            for (int b = 1; b <= q && same; ++b) {
+                const double* pi = pts + ((int64_t)i * (D + 2) + b) * 3;
+                const double* pj = pts + ((int64_t)j * (D + 2) + b) * 3;
+                double dx = pi[0] - pj[0], dy = pi[1] - pj[1], dz = pi[2] - pj[2];
+                same = dx * dx + dy * dy + dz * dz <= tol2;
+            }
+            if (!same) continue;
+            bool less = false;
+            for (int b = 0; b < q; ++b) {
+                int ti = tri[(int64_t)b * P + i], tj = tri[(int64_t)b * P + j];
+                if (ti != tj) {
+                    less = tj < ti;
+                    break;
+                }
+            }
+            if (less) {
+                int s = find_seg(rx_off, n + 1, (int64_t)r);
+                const int64_t words = (cand_off[s + 1] - cand_off[s] + 31) / 32;
+                const int64_t kl = path_cand[i] - cand_off[s];
+                atomicAnd(bits + bits_off[s] + (r - rx_off[s]) * words + (kl >> 5), ~(1u << (kl & 31)));
+                atomicAdd(drops, 1ull);
+                break;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// Candidate cap per scene of one batch: hash tables of `cap` entries.
+extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
+    rt_ctx* ctx, const rt_scene* const* scenes, int32_t n_scenes, const double* tx_host, const double* rx_dev,
+    const int32_t* rx_counts_host, int64_t n_rays, int32_t max_depth, rt_paths** out) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (!scenes || !tx_host || !rx_dev || !rx_counts_host || !out) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument");
+    if (n_scenes < 1 || n_scenes > 256) return rt_fail(ctx, RT_ERR_INVALID_ARG, "n_scenes must be in [1, 256]");
+    if (n_rays < 1 || n_rays > 0x7fffffffLL) return rt_fail(ctx, RT_ERR_INVALID_ARG, "n_rays out of range");
+    if (max_depth < 1 || max_depth > RT_MAX_DEPTH) return rt_fail(ctx, RT_ERR_INVALID_ARG, "max_depth must be 1..4");
+    const int n = n_scenes, D = max_depth;
+    const int n_mat = scenes[0] ? scenes[0]->n_materials : 0;
+    std::vector<int64_t> rx_off(n + 1, 0), ray_off(n + 1, 0), tri_off(n + 1, 0);
+    for (int s = 0; s < n; ++s) {
+        const rt_scene* sc = scenes[s];
+        if (!sc || sc->owns_tables_only) return rt_fail(ctx, RT_ERR_INVALID_ARG, "scene %d is not a traceable scene", s);
+        if (sc->n_materials != n_mat || std::memcmp(sc->h_is_pec, scenes[0]->h_is_pec, n_mat) != 0)
+            return rt_fail(ctx, RT_ERR_INVALID_ARG, "scenes of a batch must share one material table");
+        if (rx_counts_host[s] < 1) return rt_fail(ctx, RT_ERR_INVALID_ARG, "scene %d has no receivers", s);
+        for (int c = 0; c < 3; ++c)
+            if (!std::isfinite(tx_host[3 * s + c])) return rt_fail(ctx, RT_ERR_NUMERIC, "non-finite transmitter");
+        rx_off[s + 1] = rx_off[s] + rx_counts_host[s];
+        ray_off[s + 1] = ray_off[s] + n_rays;
+        tri_off[s + 1] = tri_off[s] + sc->n_tris;
+    }
+    if (rx_off[n] > (1 << 24)) return rt_fail(ctx, RT_ERR_INVALID_ARG, "more than 2^24 receivers in a batch");
+    if (tri_off[n] > 0x7fffffff) return rt_fail(ctx, RT_ERR_INVALID_ARG, "too many triangles in a batch");
+    *out = nullptr;
+    cudaStream_t st = ctx->stream;
+    int32_t* status = rt_status_ptr(ctx);
+    const size_t stack_bytes = (size_t)RT_STACK * TRACE_THREADS * sizeof(int);
+
+    // per-scene descriptors and prefix arrays on the device (in the paths' own memory)
+    std::vector<SceneDev> hsd(n);
+    for (int s = 0; s < n; ++s) {
+        const rt_scene* sc = scenes[s];
+        hsd[s] = SceneDev{sc->d_nodes, sc->d_bvh_tris, sc->d_tri_v, sc->d_tri_bary, sc->d_tri_n64, sc->d_tri_bary64,
+                          tx_host[3 * s], tx_host[3 * s + 1], tx_host[3 * s + 2], sc->eps, n_rays, (int32_t)tri_off[s]};
+    }
+    SceneDev* d_sd = nullptr;
+    int64_t* d_offs = nullptr;   // ray_off, rx_off, then cand_off, pair_off, bits_off (filled later)
+    rt_paths* p = new rt_paths();
+    p->stream = st;
+    p->D = D;
+    p->R = (int)rx_off[n];
+    p->n_scenes = n;
+    p->h_scene_rx_off = new int64_t[n + 1];
+    p->h_scene_tri_off = new int64_t[n + 1];
+    for (int s = 0; s <= n; ++s) {
+        p->h_scene_rx_off[s] = rx_off[s];
+        p->h_scene_tri_off[s] = tri_off[s];
+    }
+    void* meta = nullptr;
+    auto fail = [&](rt_status s) {
+        if (meta) cudaFreeAsync(meta, st);
+        rt_paths_free(p);
+        return s;
+    };
+#define BCK(call)                                                         \
+    do {                                                                  \
+        cudaError_t _e = (call);                                          \
+        if (_e != cudaSuccess) return fail(rt_cuda_fail(ctx, _e, #call)); \
+    } while (0)
+    BCK(cudaMallocAsync(&meta, sizeof(SceneDev) * n + sizeof(int64_t) * 5 * (n + 1) + 256, st));
+    d_sd = reinterpret_cast<SceneDev*>(meta);
+    d_offs = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(meta) + align_up(sizeof(SceneDev) * n, 64));
+    int64_t* d_ray_off = d_offs;
+    int64_t* d_rx_off = d_offs + (n + 1);
+    int64_t* d_cand_off = d_offs + 2 * (n + 1);
+    int64_t* d_pair_off = d_offs + 3 * (n + 1);
+    int64_t* d_bits_off = d_offs + 4 * (n + 1);
+    BCK(cudaMemcpyAsync(d_sd, hsd.data(), sizeof(SceneDev) * n, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(d_ray_off, ray_off.data(), 8 * (n + 1), cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(d_rx_off, rx_off.data(), 8 * (n + 1), cudaMemcpyHostToDevice, st));
+
+    // ---------------- SBR over all scenes, one persistent launch (+ FP64 re-trace)
+    size_t cap = 1u << 16;
+    for (int s = 0; s < n; ++s) cap = std::max(cap, const_cast<rt_scene*>(scenes[s])->hash_cap);
+    const int64_t total_rays = ray_off[n];
+    const int64_t redo_cap = std::max<int64_t>(1 << 16, total_rays / 16);
+    std::vector<int64_t> uniq(n);
+    uint64_t* sorted = nullptr;
+    size_t sort_cap = 0;
+    for (int attempt = 0;; ++attempt) {
+        sort_cap = std::max<size_t>(SORT_BLOCK, cap / 2);
+        size_t need = (size_t)n * cap * 8 + (size_t)n * sort_cap * 8 + (size_t)(2 * n + 8) * 8 + redo_cap * 8 + 16 * 256;
+        void* base;
+        rt_status s0 = rt_scratch(ctx, need, &base);
+        if (s0 != RT_OK) return fail(s0);
+        Arena ar{(char*)base};
+        unsigned long long* tables = ar.take<unsigned long long>((size_t)n * cap);
+        unsigned long long* counters = ar.take<unsigned long long>(2 * n + 8);   // uniq[n], compact[n], next, redo
+        int32_t* flags = ar.take<int32_t>(8);
+        int64_t* redo = ar.take<int64_t>(redo_cap);
+        sorted = ar.take<uint64_t>((size_t)n * sort_cap);
+        BCK(cudaMemsetAsync(tables, 0, (size_t)n * cap * 8, st));
+        BCK(cudaMemsetAsync(counters, 0, (2 * n + 8) * 8, st));
+        BCK(cudaMemsetAsync(flags, 0, 32, st));
+        BatchSbr A;
+        A.sd = d_sd;
+        A.ray_off = d_ray_off;
+        A.n = n;
+        A.depth = D;
+        A.tables = tables;
+        A.cap = cap;
+        A.uniq = counters;
+        A.uniq_limit = cap / 2;
+        A.overflow = flags;
+        A.next_ray = counters + 2 * n;
+        A.redo = redo;
+        A.redo_count = counters + 2 * n + 1;
+        A.redo_cap = redo_cap;
+        A.status = status;
+        {
+            rt_status ss = ray_schedule(ctx, n_rays, &A.sched);
+            if (ss != RT_OK) return fail(ss);
+        }
+        mark(ctx, 0);
+        k_sbr_batch<<<ctx->num_sms * ctx->tune_sbr_blocks_per_sm, TRACE_THREADS, stack_bytes, st>>>(A);
+        RT_COUNT(ctx);
+        BCK(cudaGetLastError());
+        k_sbr_redo_batch<<<ctx->num_sms * 4, REDO_THREADS, (size_t)RT_STACK * REDO_THREADS * sizeof(int), st>>>(A);
+        RT_COUNT(ctx);
+        BCK(cudaGetLastError());
+        mark(ctx, 1);
+        int64_t* hp = ctx->h_pinned;   // 64 bytes: read counters in pieces
+        std::vector<unsigned long long> hu(n);
+        BCK(cudaMemcpyAsync(hp, flags, 4, cudaMemcpyDeviceToHost, st));
+        BCK(cudaStreamSynchronize(st));
+        int32_t ovf = *(int32_t*)hp;
+        BCK(cudaMemcpy(hu.data(), counters, 8 * n, cudaMemcpyDeviceToHost));
+        if (ovf == 2) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "FP64 re-trace list overflow"));
+        if (ovf) {
+            if (attempt >= 6 || cap >= ((size_t)1 << 30)) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "hash overflow"));
+            cap *= 4;
+            continue;
+        }
+        for (int s = 0; s < n; ++s) {
+            uniq[s] = (int64_t)hu[s];
+            const_cast<rt_scene*>(scenes[s])->hash_cap = std::max(scenes[s]->hash_cap, cap);
+        }
+        BCK(cudaMemsetAsync(counters + n, 0, 8 * n, st));
+        k_fill_u64<<<grid_for(ctx, (int64_t)n * sort_cap, 256), 256, 0, st>>>(sorted, (uint64_t)n * sort_cap, ~0ull);
+        RT_COUNT(ctx);
+        k_table_compact_batch<<<grid_for(ctx, (int64_t)n * cap, 256, 16), 256, 0, st>>>(tables, n, cap, sorted,
+                                                                                        sort_cap, counters + n);
+        RT_COUNT(ctx);
+        BCK(cudaGetLastError());
+        for (int s = 0; s < n; ++s) {   // bitonic sort of each scene's keys
+            int64_t n_pad = SORT_BLOCK;
+            while (n_pad < uniq[s]) n_pad <<= 1;
+            uint64_t* keys = sorted + (size_t)s * sort_cap;
+            k_bitonic_local<<<(unsigned)(n_pad / SORT_BLOCK), 1024, 0, st>>>(keys);
+            RT_COUNT(ctx);
+            for (uint64_t k = 2 * SORT_BLOCK; k <= (uint64_t)n_pad; k <<= 1) {
+                for (uint64_t j = k >> 1; j >= (uint64_t)SORT_BLOCK; j >>= 1) {
+                    k_bitonic_global<<<grid_for(ctx, n_pad, 256, 16), 256, 0, st>>>(keys, n_pad, j, k);
+                    RT_COUNT(ctx);
+                }
+                k_bitonic_merge_local<<<(unsigned)(n_pad / SORT_BLOCK), 1024, 0, st>>>(keys, k);
+                RT_COUNT(ctx);
+            }
+        }
+        BCK(cudaGetLastError());
+        break;
+    }
+
+    // ---------------- candidates of all scenes (LoS first in each scene)
+    std::vector<int64_t> cand_off(n + 1, 0), pair_off(n + 1, 0), bits_off(n + 1, 0);
+    for (int s = 0; s < n; ++s) {
+        const int64_t K = uniq[s] + 1;
+        cand_off[s + 1] = cand_off[s] + K;
+        pair_off[s + 1] = pair_off[s] + ((K + PAIR_CC - 1) / PAIR_CC) * ((rx_off[s + 1] - rx_off[s] + 31) / 32);
+        bits_off[s + 1] = bits_off[s] + ((K + 31) / 32) * (rx_off[s + 1] - rx_off[s]);
+    }
+    const int64_t KT = cand_off[n];
+    if (KT > 0x7fffffffLL) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "more than 2^31 candidates in a batch"));
+    p->K = KT;
+    BCK(cudaMemcpyAsync(d_cand_off, cand_off.data(), 8 * (n + 1), cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(d_pair_off, pair_off.data(), 8 * (n + 1), cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(d_bits_off, bits_off.data(), 8 * (n + 1), cudaMemcpyHostToDevice, st));
+    BCK(cudaMallocAsync((void**)&p->d_cand, KT * 8, st));
+    for (int s = 0; s < n; ++s) {
+        BCK(cudaMemsetAsync(p->d_cand + cand_off[s], 0, 8, st));
+        if (uniq[s] > 0)
+            BCK(cudaMemcpyAsync(p->d_cand + cand_off[s] + 1, sorted + (size_t)s * sort_cap, uniq[s] * 8,
+                                cudaMemcpyDeviceToDevice, st));
+    }
+    int32_t *cand_depth = nullptr, *cand_tri = nullptr;
+    double* img64 = nullptr;
+    float4* img32 = nullptr;
+    uint2* queue = nullptr;
+    uint32_t* bits = nullptr;
+    unsigned long long* counters = nullptr;
+    int32_t* flags = nullptr;
+    int64_t* counts = nullptr;
+    size_t qcap = 1u << 20;
+    for (int s = 0; s < n; ++s) qcap = std::max(qcap, scenes[s]->queue_cap);
+    for (int attempt = 0;; ++attempt) {
+        size_t need = KT * 4 + (size_t)D * KT * 4 + (size_t)D * KT * 24 + (size_t)D * KT * 16 + qcap * 8 +
+                      (size_t)bits_off[n] * 4 + 64 * 8 + (size_t)(rx_off[n] + 1) * 8 * 2 + 16 * 256;
+        void* base;
+        rt_status s0 = rt_scratch(ctx, need, &base);
+        if (s0 != RT_OK) return fail(s0);
+        Arena ar{(char*)base};
+        cand_depth = ar.take<int32_t>(KT);
+        cand_tri = ar.take<int32_t>((size_t)D * KT);
+        img64 = ar.take<double>((size_t)D * KT * 3);
+        img32 = ar.take<float4>((size_t)D * KT);
+        queue = ar.take<uint2>(qcap);
+        bits = ar.take<uint32_t>((size_t)bits_off[n]);
+        counters = ar.take<unsigned long long>(8);
+        flags = ar.take<int32_t>(8);
+        counts = ar.take<int64_t>(rx_off[n] + 1);
+        BCK(cudaMemsetAsync(counters, 0, 64, st));
+        BCK(cudaMemsetAsync(flags, 0, 32, st));
+        BCK(cudaMemsetAsync(bits, 0, (size_t)bits_off[n] * 4, st));
+        k_candidates_batch<<<grid_for(ctx, KT, 256), 256, 0, st>>>(p->d_cand, KT, D, d_sd, d_cand_off, n, cand_depth,
+                                                                    cand_tri, img64, img32);
+        RT_COUNT(ctx);
+        BCK(cudaGetLastError());
+        BatchPairs PA;
+        PA.C = CandView{KT, cand_depth, cand_tri, img64, img32};
+        PA.sd = d_sd;
+        PA.tile_off = d_pair_off;
+        PA.cand_off = d_cand_off;
+        PA.rx_off = d_rx_off;
+        PA.n = n;
+        PA.rx = rx_dev;
+        PA.queue = queue;
+        PA.qcount = counters;
+        PA.qcap = qcap;
+        PA.overflow = flags;
+        mark(ctx, 2);
+        k_pairs_batch<<<grid_for(ctx, pair_off[n] * 32, 256, ctx->tune_pairs_blocks_per_sm), 256, 0, st>>>(PA);
+        RT_COUNT(ctx);
+        BCK(cudaGetLastError());
+        mark(ctx, 3);
+        BatchVis VA;
+        VA.C = PA.C;
+        VA.sd = d_sd;
+        VA.cand_off = d_cand_off;
+        VA.rx_off = d_rx_off;
+        VA.bits_off = d_bits_off;
+        VA.n = n;
+        VA.rx = rx_dev;
+        VA.queue = queue;
+        VA.qcount = counters;
+        VA.qcap = qcap;
+        VA.bits = bits;
+        VA.status = status;
+        k_visibility_batch<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, stack_bytes, st>>>(VA);
+        RT_COUNT(ctx);
+        BCK(cudaGetLastError());
+        mark(ctx, 4);
+        int64_t* hp = ctx->h_pinned;
+        BCK(cudaMemcpyAsync(hp, flags, 4, cudaMemcpyDeviceToHost, st));
+        BCK(cudaStreamSynchronize(st));
+        if (*(int32_t*)hp) {
+            if (attempt >= 6) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "visibility queue overflow"));
+            qcap *= 4;
+            continue;
+        }
+        for (int s = 0; s < n; ++s) const_cast<rt_scene*>(scenes[s])->queue_cap = std::max(scenes[s]->queue_cap, qcap);
+        break;
+    }
+
+    // ---------------- combined triangle tables of the batch (global triangle ids)
+    rt_scene* comb = new rt_scene();
+    p->owned_scene = comb;
+    p->scene = comb;
+    comb->ctx = ctx;
+    comb->owns_tables_only = true;
+    comb->n_tris = (int)tri_off[n];
+    comb->n_materials = n_mat;
+    comb->diag = 0.0;
+    for (int s = 0; s < n; ++s) comb->diag = std::max(comb->diag, scenes[s]->diag);
+    comb->eps = 1e-6 * comb->diag;
+    BCK(cudaMalloc((void**)&comb->d_tri_n64, (size_t)tri_off[n] * 32));
+    BCK(cudaMalloc((void**)&comb->d_tri_v, (size_t)tri_off[n] * 48));
+    BCK(cudaMalloc((void**)&comb->d_tri_material, (size_t)tri_off[n] * 4));
+    BCK(cudaMalloc((void**)&comb->d_is_pec, (size_t)std::max(n_mat, 1)));
+    for (int s = 0; s < n; ++s) {
+        const rt_scene* sc = scenes[s];
+        BCK(cudaMemcpyAsync(comb->d_tri_n64 + 4 * tri_off[s], sc->d_tri_n64, (size_t)sc->n_tris * 32,
+                            cudaMemcpyDeviceToDevice, st));
+        BCK(cudaMemcpyAsync(comb->d_tri_v + 3 * tri_off[s], sc->d_tri_v, (size_t)sc->n_tris * 48,
+                            cudaMemcpyDeviceToDevice, st));
+        BCK(cudaMemcpyAsync(comb->d_tri_material + tri_off[s], sc->d_tri_material, (size_t)sc->n_tris * 4,
+                            cudaMemcpyDeviceToDevice, st));
+    }
+    BCK(cudaMemcpyAsync(comb->d_is_pec, scenes[0]->d_is_pec, n_mat, cudaMemcpyDeviceToDevice, st));
+    comb->h_is_pec = new uint8_t[std::max(n_mat, 1)];
+    std::memcpy(comb->h_is_pec, scenes[0]->h_is_pec, n_mat);
+
+    // ---------------- emission over all receivers of all scenes
+    const int64_t RT = rx_off[n];
+    int32_t* path_cand = nullptr;
+    int32_t* edge = nullptr;
+    for (int pass = 0;; ++pass) {
+        k_row_count_batch<<<grid_for(ctx, RT * 32, 256, 16), 256, 0, st>>>(bits, d_rx_off, d_cand_off, d_bits_off, n,
+                                                                          counts);
+        RT_COUNT(ctx);
+        if (!p->d_rx_offsets) BCK(cudaMallocAsync((void**)&p->d_rx_offsets, (size_t)(RT + 1) * 8, st));
+        k_scan<<<1, 1024, 0, st>>>(counts, (int)RT, p->d_rx_offsets);
+        RT_COUNT(ctx);
+        BCK(cudaGetLastError());
+        int64_t* hp = ctx->h_pinned;
+        BCK(cudaMemcpyAsync(hp, p->d_rx_offsets + RT, 8, cudaMemcpyDeviceToHost, st));
+        BCK(cudaStreamSynchronize(st));
+        const int64_t P = hp[0];
+        p->P = P;
+        if (pass > 0) {
+            cudaFreeAsync(p->d_pts, st);
+            cudaFreeAsync(p->d_depth, st);
+            cudaFreeAsync(p->d_rx, st);
+            cudaFreeAsync(p->d_tri, st);
+            cudaFreeAsync(path_cand, st);
+            cudaFreeAsync(edge, st);
+        }
+        const size_t Pa = std::max<int64_t>(P, 1);
+        BCK(cudaMallocAsync((void**)&p->d_pts, Pa * (D + 2) * 3 * 8, st));
+        BCK(cudaMallocAsync((void**)&p->d_depth, Pa * 4, st));
+        BCK(cudaMallocAsync((void**)&p->d_rx, Pa * 4, st));
+        BCK(cudaMallocAsync((void**)&p->d_tri, Pa * D * 4, st));
+        BCK(cudaMallocAsync((void**)&path_cand, Pa * 4, st));
+        BCK(cudaMallocAsync((void**)&edge, Pa * 4, st));
+        if (P > 0) {
+            k_expand_batch<<<grid_for(ctx, RT * 32, 256, 16), 256, 0, st>>>(bits, d_rx_off, d_cand_off, d_bits_off, n,
+                                                                           p->d_rx_offsets, p->d_rx, path_cand);
+            RT_COUNT(ctx);
+            CandView C{KT, cand_depth, cand_tri, img64, img32};
+            k_points_batch<<<grid_for(ctx, P, 256), 256, 0, st>>>(C, P, D, d_sd, d_cand_off, n, p->d_rx, path_cand,
+                                                                   rx_dev, p->d_pts, p->d_depth, p->d_rx, p->d_tri,
+                                                                   edge, status);
+            RT_COUNT(ctx);
+            BCK(cudaGetLastError());
+        }
+        if (pass > 0 || P == 0) break;
+        BCK(cudaMemsetAsync(counters + 4, 0, 8, st));
+        k_dedup_batch<<<grid_for(ctx, P, 256), 256, 0, st>>>(P, D, p->d_rx_offsets, p->d_rx, path_cand, p->d_depth,
+                                                             p->d_tri, p->d_pts, edge, comb->d_tri_n64, comb->d_tri_v,
+                                                             comb->diag, d_rx_off, d_cand_off, d_bits_off, n, bits,
+                                                             counters + 4);
+        RT_COUNT(ctx);
+        BCK(cudaGetLastError());
+        BCK(cudaMemcpyAsync(hp, counters + 4, 8, cudaMemcpyDeviceToHost, st));
+        BCK(cudaStreamSynchronize(st));
+        if (hp[0] == 0) break;
+    }
+    cudaFreeAsync(path_cand, st);
+    cudaFreeAsync(edge, st);
+    cudaFreeAsync(meta, st);
+    meta = nullptr;
+    rt_status s1 = rt_launch_paths_records(ctx, p);
+    if (s1 != RT_OK) return fail(s1);
+    if (ctx->profile & 1) {
+        cudaEventRecord(ctx->ev[5], st);
+        BCK(cudaEventSynchronize(ctx->ev[5]));
+        float ms;
+        const int a[5] = {0, 1, 2, 3, 4}, b[5] = {1, 2, 3, 4, 5};
+        for (int k = 0; k < 5; ++k) {
+            cudaEventElapsedTime(&ms, ctx->ev[a[k]], ctx->ev[b[k]]);
+            ctx->stage_ms[k] = ms;
+        }
+        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
+        ctx->stage_ms[5] = ms;
+    }
+#undef BCK
+    *out = p;
+    return RT_OK;
+}
+
+// ===========================================================================
+// Autotuner of the tracing launch shapes: coordinate descent over the blocks
+// per SM of the SBR, image-method and visibility kernels, each timed by its own
+// stage (CUDA events) on the caller's workload; results are cached per
+// (device, triangles, scene size, rays, depth, receivers).
+#include <map>
+#include <mutex>
+#include <string>
+
+static std::map<std::string, std::array<int, 3>>& tune_cache() {
+    static std::map<std::string, std::array<int, 3>> m;
+    return m;
+}
+static std::mutex g_tune_mu;
+
+extern "C" __attribute__((visibility("default"))) rt_status rt_set_tuning(rt_ctx* ctx, int32_t sbr_blocks_per_sm,
+                                                                          int32_t pairs_blocks_per_sm,
+                                                                          int32_t vis_blocks_per_sm) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (sbr_blocks_per_sm < 1 || sbr_blocks_per_sm > 64 || pairs_blocks_per_sm < 1 || pairs_blocks_per_sm > 64 ||
+        vis_blocks_per_sm < 1 || vis_blocks_per_sm > 64)
+        return rt_fail(ctx, RT_ERR_INVALID_ARG, "blocks per SM must be in [1, 64]");
+    ctx->tune_sbr_blocks_per_sm = sbr_blocks_per_sm;
+    ctx->tune_pairs_blocks_per_sm = pairs_blocks_per_sm;
+    ctx->tune_vis_blocks_per_sm = vis_blocks_per_sm;
+    return RT_OK;
+}
+
+extern "C" __attribute__((visibility("default"))) rt_status rt_autotune_trace(
+    rt_ctx* ctx, const rt_scene* scene, const double* tx_host, const double* rx_dev, int32_t n_rx, int64_t n_rays,
+    int32_t max_depth, int32_t* chosen, double* best_ms) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (!scene || !tx_host || !rx_dev || !chosen) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument");
+    cudaDeviceProp prop;
+    RT_CK(ctx, cudaGetDeviceProperties(&prop, ctx->device));
+    char key[512];
+    snprintf(key, sizeof(key), "%s|%d|%.6e|%lld|%d|%d", prop.name, scene->n_tris, scene->diag, (long long)n_rays,
+             max_depth, n_rx);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = tune_cache().find(key);
+        if (it != tune_cache().end()) {
+            for (int k = 0; k < 3; ++k) chosen[k] = it->second[k];
+            if (best_ms) *best_ms = 0.0;
+            return rt_set_tuning(ctx, chosen[0], chosen[1], chosen[2]);
+        }
+    }
+    const int32_t saved_profile = ctx->profile;
+    rt_status st = rt_set_profiling(ctx, 1);
+    if (st != RT_OK) return st;
+    // one trial: two traces, the better stage time counts
+    auto trial = [&](int stage, double* ms_out) -> rt_status {
+        double best = 1e30;
+        for (int rep = 0; rep < 2; ++rep) {
+            rt_paths* p = nullptr;
+            rt_status s = rt_trace_paths(ctx, scene, tx_host, rx_dev, n_rx, n_rays, max_depth, &p);
+            if (s != RT_OK) return s;
+            rt_paths_free(p);
+            best = std::min(best, ctx->stage_ms[stage]);
+        }
+        *ms_out = best;
+        return RT_OK;
+    };
+    const int cand[3][5] = {{4, 6, 8, 12, 16}, {8, 16, 32, 64, 0}, {4, 8, 12, 16, 0}};
+    const int stage_of[3] = {0, 2, 3};   // SBR, image method, visibility
+    int cur[3] = {ctx->tune_sbr_blocks_per_sm, ctx->tune_pairs_blocks_per_sm, ctx->tune_vis_blocks_per_sm};
+    double total = 0.0;
+    for (int knob = 0; knob < 3; ++knob) {
+        double best = 1e30;
+        int best_v = cur[knob];
+        for (int c = 0; c < 5 && cand[knob][c] > 0; ++c) {
+            cur[knob] = cand[knob][c];
+            st = rt_set_tuning(ctx, cur[0], cur[1], cur[2]);
+            if (st != RT_OK) return st;
+            double ms;
+            st = trial(stage_of[knob], &ms);
+            if (st != RT_OK) return st;
+            if (ms < best) {
+                best = ms;
+                best_v = cur[knob];
+            }
+        }
+        cur[knob] = best_v;
+        total += best;
+    }
+    st = rt_set_tuning(ctx, cur[0], cur[1], cur[2]);
+    rt_set_profiling(ctx, saved_profile);
+    if (st != RT_OK) return st;
+    for (int k = 0; k < 3; ++k) chosen[k] = cur[k];
+    if (best_ms) *best_ms = total;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_cache()[key] = {cur[0], cur[1], cur[2]};
     return RT_OK;
 }
