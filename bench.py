@@ -54,21 +54,77 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """SM clocks and clock-event (throttle) reasons sampled during the timed region.
+
+    Reads NVML through ctypes every few milliseconds (the timed regions here are
+    tens to hundreds of milliseconds, too short for nvidia-smi's 100 ms loop);
+    falls back to `nvidia-smi -lms 100` when the NVML library cannot be loaded.
+    Only reads; never changes a setting."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    # nvmlClocksEventReason* bits (nvml.h)
+    REASON_BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+                   0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+    NVML_CLOCK_SM = 1
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
+    def __init__(self, torch_device, period_s=0.005):
+        self.dev = torch_device
+        self.period = period_s
         self.proc = None
+        self.nvml = None
         self.lines = []
+        self.samples = []
+        self.stop_flag = threading.Event()
+
+    def _nvml_handle(self):
+        import ctypes
+
+        import torch
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        props = torch.cuda.get_device_properties(self.dev)
+        uuid = getattr(props, "uuid", None)
+        ok = False
+        if uuid is not None:
+            ok = lib.nvmlDeviceGetHandleByUUID(("GPU-" + str(uuid)).encode(), ctypes.byref(h)) == 0
+        if not ok:
+            ok = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.dev), ctypes.byref(h)) == 0
+        if not ok:
+            return None
+        self.max_mhz = ctypes.c_uint(0)
+        lib.nvmlDeviceGetMaxClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(self.max_mhz))
+        self.reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h
+
+    def _poll(self):
+        import ctypes
+        lib, h = self.nvml
+        mhz = ctypes.c_uint(0)
+        bits = ctypes.c_ulonglong(0)
+        while not self.stop_flag.is_set():
+            r0 = lib.nvmlDeviceGetClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(mhz))
+            r1 = self.reason_fn(h, ctypes.byref(bits))
+            if r0 == 0:
+                self.samples.append((mhz.value, bits.value if r1 == 0 else 0))
+            time.sleep(self.period)
 
     def start(self):
         try:
+            self.nvml = self._nvml_handle()
+        except (OSError, AttributeError):
+            self.nvml = None
+        if self.nvml is not None:
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return
+        try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -80,6 +136,13 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nvml is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=5)
+            sm = [m for m, _ in self.samples]
+            reasons = sorted({name for _, b in self.samples for bit, name in self.REASON_BITS.items() if b & bit})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz.value,
+                    "samples": len(sm), "source": "nvml", "reasons": reasons}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -102,7 +165,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "source": "nvidia-smi", "reasons": sorted(reasons)}
 
 
 def dist_setup(n_gpus):
@@ -250,7 +313,7 @@ def run_ours(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stage_acc = np.zeros(8)
     launches0, _, _ = ctx.profile()
-    clocks = ClockSampler(local if world > 1 else torch.cuda.current_device())
+    clocks = ClockSampler(torch.cuda.current_device())
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
@@ -293,6 +356,9 @@ def run_ours(args):
     # ---------------- learned form (neural materials) vs the plain per-object form
     learned = time_learned(rt, ctx, args)
 
+    # ---------------- batched form: 16 cities in one pipeline vs a per-scene loop
+    batch = time_batch(rt, ctx, args) if not args.no_batch else None
+
     # ---------------- roofline of the dominant kernel
     stages = {"sbr": stage_mean[0], "dedup_sort": stage_mean[1], "image_method": stage_mean[2],
               "visibility": stage_mean[3], "emission_records": stage_mean[4]}
@@ -317,6 +383,7 @@ def run_ours(args):
             "calibration_ms": {k: round(v, 4) for k, v in cal.items()},
             "calibration_indoor": calib_indoor,
             "learned": learned,
+            "batch": batch,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clock_info,
             "counters": {"sbr_node_visits": counters[0], "sbr_tri_tests": counters[1], "sbr_queries": counters[2],
@@ -451,6 +518,104 @@ def time_indoor_calibration(rt, ctx, flush, args):
     return {"workload": "indoor_diff", "n_rx": sc.n_rx, "n_sub": N, "n_paths": p.n_paths,
             "ms_per_step_median": float(np.median(times)), "graph": True, "replays": n,
             "l2": "flushed: 256 MiB written between replays"}
+
+
+def time_batch(rt, ctx, args, reps=3):
+    """16 procedural cities (1k-50k triangles, 65,536 receivers split unevenly,
+    10^7 rays per scene, depth 4): rt_trace_batch against a loop of per-scene
+    rt_trace_paths calls (both timed on the stream from the first launch to the
+    last, host round trips included), then the calibration step over all scenes
+    (fields + CFR at 256 subcarriers + loss + adjoints) as one CUDA graph against a
+    per-scene loop.  The tracing launch shapes come from the autotuner run on the
+    largest scene."""
+    import torch
+
+    import scenegen
+    cities = scenegen.city_batch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    scenes = [rt.Scene.from_synthetic(ctx, c) for c in cities]
+    rxs = [torch.tensor(c.rx, device=dev) for c in cities]
+    txs = [c.tx for c in cities]
+    n_rays, depth = cities[0].n_rays, cities[0].max_depth
+    big = max(range(len(cities)), key=lambda i: cities[i].n_tris)
+    tuned, tune_ms = rt.autotune_trace(ctx, scenes[big], txs[big], rxs[big], n_rays, depth)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s0.record(stream)
+        out = fn()
+        e0.record(stream)
+        e0.synchronize()
+        return s0.elapsed_time(e0), out
+
+    timed(lambda: rt.trace_batch(ctx, scenes, txs, rxs, n_rays, depth))
+    t_batch, t_loop = [], []
+    for _ in range(reps):
+        t, pb = timed(lambda: rt.trace_batch(ctx, scenes, txs, rxs, n_rays, depth))
+        t_batch.append(t)
+        del pb
+        t, pl = timed(lambda: [rt.trace_paths(ctx, scenes[i], txs[i], rxs[i], n_rays, depth)
+                               for i in range(len(cities))])
+        t_loop.append(t)
+        del pl
+    total_rays = n_rays * len(cities)
+    # calibration over all scenes: one paths object (batch) vs per-scene objects
+    pb = rt.trace_batch(ctx, scenes, txs, rxs, n_rays, depth)
+    pl = [rt.trace_paths(ctx, scenes[i], txs[i], rxs[i], n_rays, depth) for i in range(len(cities))]
+    c0 = cities[0]
+    fc, df, N, f = c0.f_center_hz, c0.delta_f_hz, c0.n_sub, c0.freq_hz
+    eps = torch.tensor(c0.eps_r, device=dev)
+    sig = torch.tensor(c0.sigma, device=dev)
+    eps_t, sig_t = (eps * 1.2).contiguous(), (sig * 0.7).contiguous()
+
+    def target(p):
+        a = rt.eval_fields(ctx, p, eps, sig, f)
+        T = (rt.cfr(ctx, p.rx_offsets, a, p.tau, fc, df, N).abs() ** 2).float().contiguous()
+        m = T.mean(1)
+        w = torch.where(m > 0, 1 / torch.where(m > 0, m, torch.ones_like(m)), torch.zeros_like(m)).float()
+        return T, w.contiguous()
+
+    def make_step(p):
+        T, w = target(p)
+        a = torch.empty(max(p.n_paths, 1), dtype=torch.complex64, device=dev)[: p.n_paths]
+        ga = torch.empty_like(a)
+        loss = torch.zeros(1, device=dev)
+        ge, gs, gg = torch.zeros_like(eps), torch.zeros_like(sig), torch.zeros(2, device=dev)
+
+        def step():
+            rt.eval_fields(ctx, p, eps_t, sig_t, f, out=a)
+            rt.cfr_power_mse_fused(ctx, p.rx_offsets, a, p.tau, fc, df, N, T, w, loss=loss, grad_a=ga)
+            rt.eval_fields_backward(ctx, p, eps_t, sig_t, f, ga, ge, gs, gg)
+        return step
+
+    step_b = make_step(pb)
+    steps_l = [make_step(p) for p in pl]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step_b()
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step_b()
+    for _ in range(3):
+        g.replay()
+        for st in steps_l:
+            st()
+    cal_graph = [timed(g.replay)[0] for _ in range(10)]
+    cal_loop = [timed(lambda: [st() for st in steps_l])[0] for _ in range(10)]
+    return {"workload": "city_batch", "n_scenes": len(cities), "n_tris": [c.n_tris for c in cities],
+            "n_rx": int(sum(c.n_rx for c in cities)), "rays_per_scene": n_rays, "max_depth": depth,
+            "n_paths": pb.n_paths, "n_candidates": pb.n_candidates,
+            "trace_batched_ms": float(np.median(t_batch)), "trace_loop_ms": float(np.median(t_loop)),
+            "rays_per_s_batched": total_rays / (np.median(t_batch) * 1e-3),
+            "rays_per_s_loop": total_rays / (np.median(t_loop) * 1e-3),
+            "calibration_graph_ms": float(np.median(cal_graph)), "calibration_loop_ms": float(np.median(cal_loop)),
+            "autotuned_blocks_per_sm": {"sbr": tuned[0], "pairs": tuned[1], "visibility": tuned[2]},
+            "autotune_stage_ms": tune_ms}
 
 
 def time_learned(rt, ctx, args, train_steps=100):
@@ -593,11 +758,12 @@ def cpu_baseline(sc, N):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-sub", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 16-city batched measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -1558,9 +1558,13 @@ struct BatchSbr {
     int64_t redo_cap;
     int32_t* status;
     int blocks_per_sm;
+    unsigned long long* counters;   // optional instrumentation (slots 0..3)
     RaySched sched;
 };
 
+// Scene descriptor fields a lane needs on every bounce are loaded once, when the
+// lane takes a ray, and kept in registers (lanes of one warp may hold rays of
+// different scenes).
 __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
@@ -1568,9 +1572,16 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
     const int64_t total = A.ray_off[A.n];
     int64_t ray = -1;
     bool done = false;
-    int bounce = 0, prev = -1, s = 0;
+    int bounce = 0, prev = -1;
     uint64_t key = 0;
     WRay<float> r;
+    const BvhNode* nodes = nullptr;
+    const float4* bvh_tris = nullptr;
+    const float4* tri_v = nullptr;
+    unsigned long long* table = nullptr;
+    unsigned long long* uniq = nullptr;
+    float eps = 0.f;
+    unsigned long long c_vis = 0, c_tri = 0, c_q = 0;
     for (;;) {
         bool need = (ray < 0) && !done;
         unsigned m = __ballot_sync(FULL, need);
@@ -1582,14 +1593,21 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
             if (need) {
                 int64_t idx = (int64_t)(base + __popc(m & ((1u << lane) - 1)));
                 if (idx < total) {
-                    s = find_seg(A.ray_off, A.n + 1, idx);
+                    const int s = find_seg(A.ray_off, A.n + 1, idx);
                     const SceneDev& d = A.sd[s];
-                    idx = A.ray_off[s] + sched_ray(A.sched, idx - A.ray_off[s]);
-                    ray = idx;
+                    const int64_t r0 = A.ray_off[s];
+                    const int64_t local = sched_ray(A.sched, idx - r0);
+                    ray = r0 + local;
                     bounce = 0;
                     prev = -1;
                     key = 0;
-                    float3 dir = launch_dir(idx - A.ray_off[s], d.n_rays);
+                    nodes = d.nodes;
+                    bvh_tris = d.bvh_tris;
+                    tri_v = d.tri_v;
+                    eps = (float)d.eps;
+                    table = A.tables + (uint64_t)s * A.cap;
+                    uniq = A.uniq + s;
+                    float3 dir = launch_dir(local, d.n_rays);
                     r.o = mk((float)d.tx, (float)d.ty, (float)d.tz);
                     r.d = mk(dir.x, dir.y, dir.z);
                     wray_init(r);
@@ -1600,11 +1618,13 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
         }
         if (__all_sync(FULL, done)) break;
         if (ray < 0) continue;
-        const SceneDev& d = A.sd[s];
         float th;
         bool und = false;
         unsigned nv = 0, nt = 0;
-        int id = closest32(d.nodes, d.bvh_tris, r, (float)d.eps, prev, stack, th, und, A.status, nv, nt);
+        int id = closest32(nodes, bvh_tris, r, eps, prev, stack, th, und, A.status, nv, nt);
+        c_vis += nv;
+        c_tri += nt;
+        c_q++;
         if (und) {
             unsigned long long slot = atomicAdd(A.redo_count, 1ull);
             if ((int64_t)slot < A.redo_cap) A.redo[slot] = ray;
@@ -1617,19 +1637,24 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
             continue;
         }
         key = rt_key_push(key, bounce, id);
-        hash_insert(A.tables + (uint64_t)s * A.cap, A.cap - 1, key, A.uniq + s, A.uniq_limit, A.overflow);
+        hash_insert(table, A.cap - 1, key, uniq, A.uniq_limit, A.overflow);
         bounce++;
         if (bounce >= A.depth) {
             ray = -1;
             continue;
         }
-        float3 nrm = tri_normal_f(d.tri_v, id);
+        float3 nrm = tri_normal_f(tri_v, id);
         V3<float> nn = mk(nrm.x, nrm.y, nrm.z);
         V3<float> p = r.o + th * r.d;
         r.d = r.d - (2.0f * dot(r.d, nn)) * nn;
         r.o = p;
         wray_init(r);
         prev = id;
+    }
+    if (A.counters) {
+        warp_count(A.counters + 0, c_vis);
+        warp_count(A.counters + 1, c_tri);
+        warp_count(A.counters + 2, c_q);
     }
 }
 
@@ -1638,6 +1663,7 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo_batch(BatchSbr A) {
     int* stack = smem_stack + threadIdx.x;
     unsigned long long n = *A.redo_count;
     if (n > (unsigned long long)A.redo_cap) n = A.redo_cap;
+    if (A.counters && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.counters + 3, n);
     for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
          w += (unsigned long long)gridDim.x * blockDim.x) {
         int64_t ray = A.redo[w];
@@ -1767,11 +1793,13 @@ struct BatchVis {
     unsigned long long qcap;
     uint32_t* bits;
     int32_t* status;
+    unsigned long long* counters;   // optional instrumentation (slots 4..6)
 };
 
 __global__ void __launch_bounds__(TRACE_THREADS) k_visibility_batch(BatchVis A) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
+    unsigned long long c_vis = 0, c_tri = 0, c_seg = 0;
     unsigned long long n = *A.qcount;
     if (n > A.qcap) n = A.qcap;
     for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
@@ -1799,7 +1827,12 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_visibility_batch(BatchVis A) 
             wray_init(rf);
             bool und = false;
             unsigned nv = 0, nt = 0;
-            if (any32(d.nodes, d.bvh_tris, rf, (float)tlo, (float)thi, s0, s1, stack, und, A.status, nv, nt)) {
+            const bool blocked = any32(d.nodes, d.bvh_tris, rf, (float)tlo, (float)thi, s0, s1, stack, und,
+                                       A.status, nv, nt);
+            c_vis += nv;
+            c_tri += nt;
+            c_seg++;
+            if (blocked) {
                 visible = false;
             } else if (und) {
                 WRay<double> rd;
@@ -1814,6 +1847,12 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_visibility_batch(BatchVis A) 
             const int64_t kl = kg - A.cand_off[s];
             atomicOr(A.bits + A.bits_off[s] + (rg - A.rx_off[s]) * words + (kl >> 5), 1u << (kl & 31));
         }
+    }
+    if (A.counters) {
+        // every thread of the block reaches this point (grid-stride loop above)
+        warp_count(A.counters + 4, c_vis);
+        warp_count(A.counters + 5, c_tri);
+        warp_count(A.counters + 6, c_seg);
     }
 }
 
@@ -2058,6 +2097,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         A.redo_count = counters + 2 * n + 1;
         A.redo_cap = redo_cap;
         A.status = status;
+        A.counters = (ctx->profile & 2) ? ctx->d_counters : nullptr;
         {
             rt_status ss = ray_schedule(ctx, n_rays, &A.sched);
             if (ss != RT_OK) return fail(ss);
@@ -2119,6 +2159,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         cand_off[s + 1] = cand_off[s] + K;
         pair_off[s + 1] = pair_off[s] + ((K + PAIR_CC - 1) / PAIR_CC) * ((rx_off[s + 1] - rx_off[s] + 31) / 32);
         bits_off[s + 1] = bits_off[s] + ((K + 31) / 32) * (rx_off[s + 1] - rx_off[s]);
+        ctx->h_counters[7] += K * (rx_off[s + 1] - rx_off[s]);
     }
     const int64_t KT = cand_off[n];
     if (KT > 0x7fffffffLL) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "more than 2^31 candidates in a batch"));
@@ -2196,6 +2237,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         VA.qcap = qcap;
         VA.bits = bits;
         VA.status = status;
+        VA.counters = (ctx->profile & 2) ? ctx->d_counters : nullptr;
         k_visibility_batch<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, stack_bytes, st>>>(VA);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
