@@ -461,7 +461,136 @@ def time_e2e(rt, ctx, sc, step, target, eps, sig, g_eps, g_sig, g_gain, loss_buf
             "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * total / steps}
 
 
-def time_indoor_calibration(rt, ctx, flush, args):
+EPS0 = 8.8541878128e-12
+C0 = 299792458.0
+
+
+def plain_records(ex, sc, dev):
+    """Frozen per-path geometry of the plain PyTorch arm, from the exported points
+    (float64 torch ops, once, untimed, like the library's own record pass):
+    per depth q the path indices, cos(theta_i) and material of every bounce, the
+    q + 1 real 2x2 basis-change matrices (Tx theta/phi basis -> reflection bases
+    -> Rx theta/phi basis along the AoA) and the path length."""
+    import torch
+    f64 = torch.float64
+    verts = torch.tensor(sc.verts, dtype=torch.float32, device=dev).double()
+    tris = torch.tensor(sc.tris, dtype=torch.int64, device=dev)
+    v0, v1, v2 = verts[tris[:, 0]], verts[tris[:, 1]], verts[tris[:, 2]]
+    nrm = torch.linalg.cross(v1 - v0, v2 - v0)
+    nrm = nrm / nrm.norm(dim=1, keepdim=True)
+    tri_mat = torch.tensor(sc.tri_material, dtype=torch.int64, device=dev)
+    is_pec = torch.tensor(sc.is_pec, dtype=torch.bool, device=dev)
+
+    def sph(k):
+        th = torch.acos(k[:, 2].clamp(-1, 1))
+        ph = torch.where((k[:, 0] == 0) & (k[:, 1] == 0), torch.zeros_like(th), torch.atan2(k[:, 1], k[:, 0]))
+        t = torch.stack([th.cos() * ph.cos(), th.cos() * ph.sin(), -th.sin()], 1)
+        p_ = torch.stack([-ph.sin(), ph.cos(), torch.zeros_like(ph)], 1)
+        return t, p_
+
+    def dots(a, b):
+        return (a * b).sum(1)
+
+    def dmat(ip, iq, op, oq):
+        return torch.stack([torch.stack([dots(ip, op), dots(ip, oq)], 1),
+                            torch.stack([dots(iq, op), dots(iq, oq)], 1)], 1)
+
+    groups = []
+    depth = ex["depth"].long()
+    for q in range(int(depth.max().item()) + 1 if depth.numel() else 0):
+        idx = torch.nonzero(depth == q).flatten()
+        if idx.numel() == 0:
+            continue
+        pts = ex["pts"][idx, : q + 2]
+        dv = pts[:, 1:] - pts[:, :-1]
+        d = dv.norm(dim=2)
+        k = dv / d[..., None]
+        out_p, out_q = sph(k[:, 0])
+        Ds, cos, mats, pec = [], [], [], []
+        for j in range(1, q + 1):
+            t = ex["seq"][idx, j - 1].long()
+            n = nrm[t]
+            kj = k[:, j - 1]
+            n = torch.where((dots(kj, n) > 0)[:, None], -n, n)
+            cos.append(-dots(kj, n))
+            cr = torch.linalg.cross(kj, n)
+            crn = cr.norm(dim=1, keepdim=True)
+            alt = out_p - dots(out_p, kj)[:, None] * kj
+            e_perp = torch.where(crn > 1e-12, cr / crn.clamp_min(1e-300), alt / alt.norm(dim=1, keepdim=True))
+            in_q = torch.linalg.cross(e_perp, kj)
+            Ds.append(dmat(e_perp, in_q, out_p, out_q))
+            out_p, out_q = e_perp, torch.linalg.cross(e_perp, k[:, j])
+            m = tri_mat[t]
+            mats.append(m)
+            pec.append(is_pec[m])
+        rp, rq = sph(-k[:, q])
+        Ds.append(dmat(rp, rq, out_p, out_q))
+        groups.append({"idx": idx, "L": d.sum(1).float(), "D": torch.stack(Ds, 1).to(torch.complex64),
+                       "cos": torch.stack(cos, 1).float() if q else None,
+                       "mat": torch.stack(mats, 1) if q else None, "pec": torch.stack(pec, 1) if q else None})
+    return groups
+
+
+def plain_step(groups, rx, tau, n_rx, eps_r, sigma, freq, fc, df, N, target, w):
+    """The calibration step as plain PyTorch complex64 ops: permittivity, Fresnel,
+    2x2 chain, a = lambda / (4 pi L) [D_{q+1} G_q ... G_1 D_1 C_T]_0, the CFR as a
+    dense P x N phasor matrix summed per receiver, and the weighted power MSE;
+    autograd gives the adjoint."""
+    import torch
+    P = tau.shape[0]
+    lam = C0 / freq
+    eta = torch.complex(eps_r, -sigma / (EPS0 * 2 * np.pi * freq))
+    a = torch.zeros(P, dtype=torch.complex64, device=tau.device)
+    for g in groups:
+        E = g["D"][:, 0, :, 0]                                   # D_1 C_T, C_T = [1, 0]
+        for j in range(g["D"].shape[1] - 1):
+            c = g["cos"][:, j].to(torch.complex64)
+            e = eta[g["mat"][:, j]]
+            s = torch.sqrt(e - (1 - c * c))
+            r_perp = torch.where(g["pec"][:, j], torch.full_like(s, -1), (c - s) / (c + s))
+            r_par = torch.where(g["pec"][:, j], torch.full_like(s, 1), (e * c - s) / (e * c + s))
+            E = torch.stack([r_perp * E[:, 0], r_par * E[:, 1]], 1)
+            E = torch.einsum("pab,pb->pa", g["D"][:, j + 1], E)
+        a = a.index_put((g["idx"],), (lam / (4 * np.pi)) * E[:, 0] / g["L"])
+    n = torch.arange(-N // 2, N // 2, device=tau.device, dtype=torch.float64)
+    frac = torch.frac(tau[:, None] * (fc + n * df)[None, :])
+    ang = (-2 * np.pi * frac).float()
+    ph = torch.polar(torch.ones_like(ang), ang)
+    H = torch.zeros((n_rx, N), dtype=torch.complex64, device=tau.device).index_add(0, rx, a[:, None] * ph)
+    e_ = H.real ** 2 + H.imag ** 2 - target
+    return ((w[:, None] * e_) ** 2).mean()
+
+
+def time_plain_calibration(p, sc, eps, sig, target, w, flush, n_reps):
+    """Times plain_step forward + autograd backward (eager, median of n_reps,
+    L2 flushed between reps) and returns it with its loss and gradients."""
+    import torch
+    dev = eps.device
+    ex = p.export()
+    groups = plain_records(ex, sc, dev)
+    rx = ex["rx"].long()
+    e = eps.clone().requires_grad_(True)
+    s_ = sig.clone().requires_grad_(True)
+    args = (groups, rx, ex["tau"], sc.n_rx, e, s_, sc.freq_hz, sc.f_center_hz, sc.delta_f_hz, sc.n_sub, target, w)
+    for _ in range(3):
+        e.grad = s_.grad = None
+        plain_step(*args).backward()
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(n_reps):
+        flush.zero_()
+        e.grad = s_.grad = None
+        s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        L = plain_step(*args)
+        L.backward()
+        e0.record(stream)
+        e0.synchronize()
+        times.append(s0.elapsed_time(e0))
+    return float(np.median(times)), float(L.item()), e.grad.detach(), s_.grad.detach()
+
+
+def time_indoor_calibration(rt, ctx, flush, args, plain=True):
     """Calibration step of the indoor differentiation workload (1024 receivers,
     1024 subcarriers around 1.272 GHz): eval_fields -> CFR + power MSE + CFR
     adjoint -> eval_fields adjoint, captured in one CUDA graph."""
@@ -515,9 +644,24 @@ def time_indoor_calibration(rt, ctx, flush, args):
         e0.record(stream)
         e0.synchronize()
         times.append(s0.elapsed_time(e0))
-    return {"workload": "indoor_diff", "n_rx": sc.n_rx, "n_sub": N, "n_paths": p.n_paths,
-            "ms_per_step_median": float(np.median(times)), "graph": True, "replays": n,
-            "l2": "flushed: 256 MiB written between replays"}
+    res = {"workload": "indoor_diff", "n_rx": sc.n_rx, "n_sub": N, "n_paths": p.n_paths,
+           "ms_per_step_median": float(np.median(times)), "graph": True, "replays": n,
+           "l2": "flushed: 256 MiB written between replays"}
+    if not plain:
+        return res
+    # the same step as plain PyTorch complex64 ops (eager, autograd), and how
+    # closely its loss and gradients agree with the library's
+    plain_ms, plain_loss, pe, ps = time_plain_calibration(p, sc, eps, sig, target, w, flush, min(n, 20))
+    g.replay()
+    torch.cuda.synchronize()
+
+    def rel(x, ref):
+        return float((x - ref).norm() / ref.norm().clamp_min(1e-30))
+    res["plain_pytorch"] = {"ms_per_step_median": plain_ms, "eager": True, "dtype": "complex64",
+                            "speedup": plain_ms / float(np.median(times)),
+                            "loss_rel_diff": abs(plain_loss - loss.item()) / max(abs(loss.item()), 1e-30),
+                            "grad_eps_rel_diff": rel(ge, pe), "grad_sigma_rel_diff": rel(gs, ps)}
+    return res
 
 
 def time_batch(rt, ctx, args, reps=3):
@@ -755,6 +899,52 @@ def cpu_baseline(sc, N):
             "ms_per_step": 1e3 * dt}
 
 
+def run_case(args):
+    """One workload alone, for profiler captures (prints a short line, not the
+    benchmark line): street_step = the street-canyon step (trace + fields +
+    fused CFR loss + adjoints); indoor_calibration = the indoor calibration step
+    (graph replays); city_batch = one batched trace of the 16 cities."""
+    import torch
+
+    import paper_2311_18558_gb300 as rt
+    import scenegen
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = rt.Context(torch.cuda.current_device())
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"case": args.case, "steps": args.steps, "warmup": args.warmup}
+    if args.case == "street_step":
+        sc = scenegen.street_canyon()
+        scene = rt.Scene.from_synthetic(ctx, sc)
+        rx = torch.tensor(sc.rx, dtype=torch.float64, device=dev)
+        eps = torch.tensor(sc.eps_r, device=dev)
+        sig = torch.tensor(sc.sigma, device=dev)
+        N, fc, df = args.n_sub, sc.f_center_hz, sc.delta_f_hz
+        p = rt.trace_paths(ctx, scene, sc.tx, rx, sc.n_rays, sc.max_depth)
+        a = rt.eval_fields(ctx, p, eps, sig, sc.freq_hz)
+        T = (rt.cfr(ctx, p.rx_offsets, a, p.tau, fc, df, N).abs() ** 2).float().contiguous()
+        w = torch.ones(sc.n_rx, device=dev)
+        for _ in range(args.warmup + args.steps):
+            flush.zero_()
+            p = rt.trace_paths(ctx, scene, sc.tx, rx, sc.n_rays, sc.max_depth)
+            a = rt.eval_fields(ctx, p, eps * 1.2, sig * 0.7, sc.freq_hz)
+            _, ga, _ = rt.cfr_power_mse_fused(ctx, p.rx_offsets, a, p.tau, fc, df, N, T, w)
+            rt.eval_fields_backward(ctx, p, eps * 1.2, sig * 0.7, sc.freq_hz, ga)
+        out["n_paths"] = p.n_paths
+    elif args.case == "indoor_calibration":
+        args.steps = max(args.steps, 1)
+        out.update(time_indoor_calibration(rt, ctx, flush, args, plain=False))
+    elif args.case == "city_batch":
+        cities = scenegen.city_batch()
+        scenes = [rt.Scene.from_synthetic(ctx, c) for c in cities]
+        rxs = [torch.tensor(c.rx, device=dev) for c in cities]
+        for _ in range(args.warmup + args.steps):
+            pb = rt.trace_batch(ctx, scenes, [c.tx for c in cities], rxs, cities[0].n_rays, cities[0].max_depth)
+        out["n_paths"] = pb.n_paths
+    torch.cuda.synchronize()
+    out["status_word"] = ctx.status_word()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -764,10 +954,14 @@ def main():
     ap.add_argument("--n-sub", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 16-city batched measurement")
+    ap.add_argument("--case", choices=["street_step", "indoor_calibration", "city_batch"], default=None,
+                    help="run one workload alone (for profiler captures) instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.case is not None:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -165,6 +165,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_destroy(rt_ctx* c
     if (ctx->d_counters) cudaFree(ctx->d_counters);
     if (ctx->d_sched_order) cudaFree(ctx->d_sched_order);
     if (ctx->d_sched_wrap) cudaFree(ctx->d_sched_wrap);
+    if (ctx->d_sched_z) cudaFree(ctx->d_sched_z);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);

@@ -40,6 +40,7 @@ struct rt_ctx {
     int64_t sched_n = 0, sched_band = 0, sched_full = 0;
     int32_t* d_sched_order = nullptr;   // sched_band entries
     int32_t* d_sched_wrap = nullptr;    // sched_full entries
+    float* d_sched_z = nullptr;         // sched_n entries: z of each launch direction
     // launch shapes of the tracing kernels (blocks per SM), set by the autotuner
     int tune_sbr_blocks_per_sm = 8;
     int tune_pairs_blocks_per_sm = 16;

@@ -32,6 +32,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int TRACE_THREADS = 128;
 constexpr int REDO_THREADS = 32;
+constexpr int REDO_BLOCKS_PER_SM = 16;
 constexpr float SBR_MARGIN = 1e-3f;     // relative barycentric margin of the FP32 passes
 constexpr float PREFILTER_MARGIN = 1e-3f;
 // Degenerate geometry: every triangle is closed and grown by TRI_TOL (relative
@@ -316,8 +317,9 @@ __device__ __forceinline__ bool any32(const BvhNode* __restrict__ nodes, const f
 // FP32 (rf); a robust FP32 miss is final, everything else gets the FP64 test,
 // so the FP64 work is a few tests per query.  The tie pass runs only if two
 // hits came within 1e-6 (relative) of each other.
-__device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const WRay<double>& r,
-                         const WRay<float>& rf, double tmin, int skip, int* stack, double& t_out, int32_t* status) {
+__device__ int closest64_inline(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris,
+                                const WRay<double>& r, const WRay<float>& rf, double tmin, int skip, int* stack,
+                                double& t_out, int32_t* status) {
     double bT = 0.0, bD = 1.0;
     bool have = false, near_tie = false;
     int best = -1;
@@ -368,11 +370,87 @@ __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __rest
     return low == 0x7fffffff ? best : low;
 }
 
+// Same decisions as closest64_inline, with the FP64 work taken out of the
+// divergent traversal.  An FP64 warp instruction costs the same with one active
+// lane as with 32, so FP64 tests inside the traversal loop are paid on every
+// step at which any lane sits at a leaf.  Here the FP32 traversal only collects
+// the triangles whose FP32 test is not a robust miss (at most CAND_CAP, in
+// `cand`, a per-thread list in shared memory with stride blockDim.x); a robust
+// FP32 hit at t > 2 tmin lowers the far end of the box tests to t (1 + 1e-3) +
+// 10 tmin, wider than the 1e-4 band in which the FP32 pass already treats two
+// hits as a tie.  The FP64 tests then run
+// over the list in one converged loop, and the tie pass over the same list
+// (every hit within TIE_TOL of the best is in it).  A list overflow falls back to
+// closest64_inline.
+constexpr int CAND_CAP = 32;
+
+__device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const WRay<double>& r,
+                         const WRay<float>& rf, double tmin, int skip, int* stack, int* cand, double& t_out,
+                         int32_t* status) {
+    const int stride = blockDim.x;
+    const float tminf = (float)tmin;
+    float thi = INFINITY;
+    int n = 0;
+    unsigned nv = 0;
+    traverse(nodes, rf, tminf * 0.5f, thi, stack, status, nv, [&](int first, int count) {
+        for (int k = first; k < first + count; ++k) {
+            float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+            int id = __float_as_int(p0.w);
+            if (id == skip) continue;
+            float tf;
+            int cls = tri_test32(rf, p0, p1, p2, tf);
+            if (cls == 0) continue;
+            if (cls == 1) {
+                if (tf > thi) continue;   // beyond a robust hit
+                if (tf > tminf * 2.0f) thi = fminf(thi, tf * 1.001f + 10.0f * tminf);
+            }
+            if (n < CAND_CAP) cand[n * stride] = k;
+            n++;
+        }
+        return false;
+    });
+    if (n > CAND_CAP) return closest64_inline(nodes, tris, r, rf, tmin, skip, stack, t_out, status);
+    double bT = 0.0, bD = 1.0;
+    bool have = false, near_tie = false;
+    int best = -1;
+    for (int i = 0; i < n; ++i) {
+        const int k = cand[i * stride];
+        float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+        int id = __float_as_int(p0.w);
+        double Tn, det;
+        if (!tri_test64(r, p0, p1, p2, Tn, det)) continue;
+        if (!(Tn > tmin * det)) continue;
+        if (have && fabs(Tn * bD - bT * det) <= 1e-6 * bT * det) near_tie = true;
+        if (!have || Tn * bD < bT * det || (Tn * bD == bT * det && id < best)) {
+            bT = Tn;
+            bD = det;
+            best = id;
+            have = true;
+        }
+    }
+    if (!have) return -1;
+    const double tb = bT * rcp64(bD);
+    t_out = tb;
+    if (!near_tie) return best;
+    const double tmax = tb + TIE_TOL * tb;
+    int low = 0x7fffffff;
+    for (int i = 0; i < n; ++i) {
+        const int k = cand[i * stride];
+        float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+        int id = __float_as_int(p0.w);
+        if (id >= low) continue;
+        double Tn, det;
+        if (!tri_test64(r, p0, p1, p2, Tn, det)) continue;
+        if (Tn > tmin * det && Tn <= tmax * det) low = id;
+    }
+    return low == 0x7fffffff ? best : low;
+}
+
 // Any hit with tmin < t < tmax of an FP64 ray (skipping skip0 and skip1),
 // final decisions in FP64; robust FP32 misses on the rounded ray rf are final.
-__device__ bool any64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const WRay<double>& r,
-                      const WRay<float>& rf, double tmin, double tmax, int skip0, int skip1, int* stack,
-                      int32_t* status) {
+__device__ bool any64_inline(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris,
+                             const WRay<double>& r, const WRay<float>& rf, double tmin, double tmax, int skip0,
+                             int skip1, int* stack, int32_t* status) {
     bool hit = false;
     const float thi = (float)tmax * 1.00001f;
     unsigned nv = 0;
@@ -393,6 +471,45 @@ __device__ bool any64(const BvhNode* __restrict__ nodes, const float4* __restric
         return false;
     });
     return hit;
+}
+
+// any64_inline with the FP64 tests taken out of the traversal (as closest64):
+// the FP32 traversal collects the triangles that are not a robust FP32 miss
+// and whose FP32 t is not beyond tmax (1 + 1e-3) + 10 tmin (at most
+// VIS_CAND_CAP, per-thread list in shared memory with stride blockDim.x); the
+// FP64 tests run over the list afterwards.  A list overflow falls back to
+// any64_inline.
+constexpr int VIS_CAND_CAP = 8;
+
+__device__ bool any64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const WRay<double>& r,
+                      const WRay<float>& rf, double tmin, double tmax, int skip0, int skip1, int* stack, int* cand,
+                      int32_t* status) {
+    const int stride = blockDim.x;
+    const float thi = (float)tmax * 1.00001f;
+    const float tcut = (float)tmax * 1.001f + 10.0f * (float)tmin;
+    int n = 0;
+    unsigned nv = 0;
+    traverse(nodes, rf, (float)tmin * 0.5f, thi, stack, status, nv, [&](int first, int count) {
+        for (int k = first; k < first + count; ++k) {
+            float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+            int id = __float_as_int(p0.w);
+            if (id == skip0 || id == skip1) continue;
+            float tf;
+            int cls = tri_test32(rf, p0, p1, p2, tf);
+            if (cls == 0 || (cls == 1 && tf > tcut)) continue;
+            if (n < VIS_CAND_CAP) cand[n * stride] = k;
+            n++;
+        }
+        return false;
+    });
+    if (n > VIS_CAND_CAP) return any64_inline(nodes, tris, r, rf, tmin, tmax, skip0, skip1, stack, status);
+    for (int i = 0; i < n; ++i) {
+        const int k = cand[i * stride];
+        double Tn, det;
+        if (!tri_test64(r, __ldg(tris + 3 * k), __ldg(tris + 3 * k + 1), __ldg(tris + 3 * k + 2), Tn, det)) continue;
+        if (Tn > tmin * det && Tn < tmax * det) return true;
+    }
+    return false;
 }
 
 // ------------------------------------------------------------------ launch directions
@@ -441,12 +558,12 @@ __device__ __forceinline__ void sincos_turn(uint32_t k, float& s_out, float& c_o
 }
 
 // Fibonacci-lattice launch direction i of N: z = 1 - (2i+1)/N (one correctly
-// rounded FP64 division and subtraction, rounded to FP32), r = sqrt(1 - z^2) and
+// rounded FP64 division and subtraction, rounded to FP32; the kernels read it
+// from a per-N table made on the host, see ray_schedule), r = sqrt(1 - z^2) and
 // azimuth fraction frac(i g) of the golden-ratio Weyl sequence in 32-bit fixed
 // point, (i * 0x9E3779B9) mod 2^32; every FP32 step is an uncontracted IEEE
 // operation, so both implementations produce the same bits.
-__device__ __forceinline__ float3 launch_dir(int64_t i, int64_t n) {
-    const float z = (float)(1.0 - (double)(2 * i + 1) / (double)n);
+__device__ __forceinline__ float3 launch_dir(int64_t i, float z) {
     const float r = __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(z, z)));
     float s, c;
     sincos_turn((uint32_t)((uint64_t)i * 0x9E3779B9ull), s, c);
@@ -464,15 +581,18 @@ struct RaySched {
     int64_t n, band, full;
     const int32_t* order;
     const int32_t* wrap;
+    const float* z;   // n entries: z of launch direction i
 };
 
+// j < n <= 2^31 - 1, so 32-bit division suffices.
 __device__ __forceinline__ int64_t sched_ray(const RaySched& S, int64_t j) {
     if (S.band <= 0) return j;
-    const int64_t b = j / S.band;
-    if (b >= S.full) return j;
-    int64_t pos = (j - b * S.band) + S.wrap[b];
-    if (pos >= S.band) pos -= S.band;
-    return b * S.band + S.order[pos];
+    const uint32_t band = (uint32_t)S.band;
+    const uint32_t b = (uint32_t)j / band;
+    if ((int64_t)b >= S.full) return j;
+    uint32_t pos = ((uint32_t)j - b * band) + (uint32_t)S.wrap[b];
+    if (pos >= band) pos -= band;
+    return (int64_t)b * S.band + S.order[pos];
 }
 
 // ------------------------------------------------------------------ hash set of keys
@@ -511,6 +631,7 @@ struct SbrArgs {
     const BvhNode* nodes;
     const float4* tris;       // BVH order
     double tx, ty, tz;
+    float3 txf;               // Tx rounded to FP32 (origin of the FP32 launch rays)
     int64_t n_rays;
     int depth;
     double eps;
@@ -574,8 +695,8 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
                     bounce = 0;
                     prev = -1;
                     key = 0;
-                    float3 d = launch_dir(idx, A.n_rays);
-                    r.o = mk((float)A.tx, (float)A.ty, (float)A.tz);
+                    float3 d = launch_dir(idx, __ldg(A.sched.z + idx));
+                    r.o = mk(A.txf.x, A.txf.y, A.txf.z);
                     r.d = mk(d.x, d.y, d.z);
                     wray_init(r);
                 } else {
@@ -631,13 +752,20 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
 __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const double* __restrict__ tri_n64) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
+    int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
     unsigned long long n = *A.redo_count;
     if (n > (unsigned long long)A.redo_cap) n = A.redo_cap;
     if (A.counters && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.counters + 3, n);
-    for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
-         w += (unsigned long long)gridDim.x * blockDim.x) {
+    // few redo rays: spread them over all warps, rpw lanes per warp, so that more
+    // warps hide the traversal latency and a warp carries fewer divergent rays
+    const unsigned long long W = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long rpw = n < W ? 1ull : (n + W - 1) / W < 32ull ? (n + W - 1) / W : 32ull;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (lane >= rpw) return;
+    for (unsigned long long w = warp * rpw + lane; w < n; w += W * rpw) {
         int64_t ray = A.redo[w];
-        float3 df = launch_dir(ray, A.n_rays);
+        float3 df = launch_dir(ray, __ldg(A.sched.z + ray));
         WRay<double> r;
         WRay<float> rf;
         r.o = mk(A.tx, A.ty, A.tz);
@@ -650,7 +778,7 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const doub
             rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
             wray_init(rf);
             double th;
-            int id = closest64(A.nodes, A.tris, r, rf, A.eps, prev, stack, th, A.status);
+            int id = closest64(A.nodes, A.tris, r, rf, A.eps, prev, stack, cand, th, A.status);
             if (id < 0) break;
             key = rt_key_push(key, b, id);
             hash_insert(A.table, A.mask, key, A.uniq, A.uniq_limit, A.overflow);
@@ -950,6 +1078,7 @@ struct VisArgs {
 __global__ void __launch_bounds__(TRACE_THREADS) k_visibility(VisArgs A) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
+    int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
     unsigned long long n = *A.qcount;
     if (n > A.qcap) n = A.qcap;
     unsigned long long c_vis = 0, c_tri = 0, c_seg = 0;
@@ -988,7 +1117,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_visibility(VisArgs A) {
                 rd.o = pts[j];
                 rd.d = d;
                 wray_init(rd);
-                if (any64(A.nodes, A.bvh_tris, rd, rf, tlo, thi, s0, s1, stack, A.status)) visible = false;
+                if (any64(A.nodes, A.bvh_tris, rd, rf, tlo, thi, s0, s1, stack, cand, A.status)) visible = false;
             }
         }
         if (visible) atomicOr(A.bits + (int64_t)r * A.words + (k >> 5), 1u << (k & 31));
@@ -1195,19 +1324,29 @@ static rt_status ray_schedule(rt_ctx* ctx, int64_t n, RaySched* out) {
                 wrap[b] = (int32_t)(j == band ? 0 : j);
             }
         }
+        // z of every launch direction, in FP64 as the definition states, once per N
+        // (an FP64 division per ray inside the tracing kernel would cost a
+        // full-warp FP64 sequence on every refill)
+        std::vector<float> z(n);
+        for (int64_t i = 0; i < n; ++i) z[i] = (float)(1.0 - (double)(2 * i + 1) / (double)n);
         if (ctx->d_sched_order) RT_CK(ctx, cudaFree(ctx->d_sched_order));
         if (ctx->d_sched_wrap) RT_CK(ctx, cudaFree(ctx->d_sched_wrap));
+        if (ctx->d_sched_z) RT_CK(ctx, cudaFree(ctx->d_sched_z));
         ctx->d_sched_order = ctx->d_sched_wrap = nullptr;
+        ctx->d_sched_z = nullptr;
         ctx->sched_n = 0;
         RT_CK(ctx, cudaMalloc((void**)&ctx->d_sched_order, order.size() * 4));
         RT_CK(ctx, cudaMalloc((void**)&ctx->d_sched_wrap, wrap.size() * 4));
+        RT_CK(ctx, cudaMalloc((void**)&ctx->d_sched_z, z.size() * 4));
         RT_CK(ctx, cudaMemcpy(ctx->d_sched_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice));
         RT_CK(ctx, cudaMemcpy(ctx->d_sched_wrap, wrap.data(), wrap.size() * 4, cudaMemcpyHostToDevice));
+        RT_CK(ctx, cudaMemcpy(ctx->d_sched_z, z.data(), z.size() * 4, cudaMemcpyHostToDevice));
         ctx->sched_n = n;
         ctx->sched_band = band;
         ctx->sched_full = full;
     }
-    *out = RaySched{ctx->sched_n, ctx->sched_band, ctx->sched_full, ctx->d_sched_order, ctx->d_sched_wrap};
+    *out = RaySched{ctx->sched_n, ctx->sched_band, ctx->sched_full, ctx->d_sched_order, ctx->d_sched_wrap,
+                    ctx->d_sched_z};
     return RT_OK;
 }
 
@@ -1242,6 +1381,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
     const int D = max_depth;
     int32_t* status = rt_status_ptr(ctx);
     const size_t stack_bytes = (size_t)RT_STACK * TRACE_THREADS * sizeof(int);
+    const size_t vis_bytes = (size_t)(RT_STACK + VIS_CAND_CAP) * TRACE_THREADS * sizeof(int);
 
     // ---------------- 1-2: SBR into the hash set (grow and retry on overflow)
     const int64_t redo_cap = std::max<int64_t>(1 << 16, n_rays / 16);
@@ -1270,6 +1410,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         A.tx = tx_host[0];
         A.ty = tx_host[1];
         A.tz = tx_host[2];
+        A.txf = make_float3((float)tx_host[0], (float)tx_host[1], (float)tx_host[2]);
         A.n_rays = n_rays;
         A.depth = D;
         A.eps = sc->eps;
@@ -1291,7 +1432,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         int blocks = ctx->num_sms * ctx->tune_sbr_blocks_per_sm;
         k_sbr<<<blocks, TRACE_THREADS, stack_bytes, st>>>(A, sc->d_tri_v); RT_COUNT(ctx);
         RT_CK_LAUNCH(ctx);
-        k_sbr_redo<<<ctx->num_sms * 4, REDO_THREADS, (size_t)RT_STACK * REDO_THREADS * sizeof(int), st>>>(
+        k_sbr_redo<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(
             A, sc->d_tri_n64);
         RT_COUNT(ctx);
         mark(ctx, 1);
@@ -1419,7 +1560,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         VA.status = status;
         VA.counters = (ctx->profile & 2) ? ctx->d_counters : nullptr;
         ctx->h_counters[7] += K * (int64_t)n_rx;
-        k_visibility<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, stack_bytes, st>>>(VA); RT_COUNT(ctx);
+        k_visibility<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st>>>(VA); RT_COUNT(ctx);
         mark(ctx, 4);
         TCK(cudaGetLastError());
         int64_t* hp = ctx->h_pinned;
@@ -1527,6 +1668,7 @@ struct SceneDev {
     const double* tri_n64;
     const double* bary64;
     double tx, ty, tz, eps;
+    float3 txf;   // Tx rounded to FP32 (origin of the FP32 launch rays)
     int64_t n_rays;
     int32_t tri_off;
 };
@@ -1607,8 +1749,8 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
                     eps = (float)d.eps;
                     table = A.tables + (uint64_t)s * A.cap;
                     uniq = A.uniq + s;
-                    float3 dir = launch_dir(local, d.n_rays);
-                    r.o = mk((float)d.tx, (float)d.ty, (float)d.tz);
+                    float3 dir = launch_dir(local, __ldg(A.sched.z + local));
+                    r.o = mk(d.txf.x, d.txf.y, d.txf.z);
                     r.d = mk(dir.x, dir.y, dir.z);
                     wray_init(r);
                 } else {
@@ -1661,15 +1803,22 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
 __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo_batch(BatchSbr A) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
+    int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
     unsigned long long n = *A.redo_count;
     if (n > (unsigned long long)A.redo_cap) n = A.redo_cap;
     if (A.counters && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.counters + 3, n);
-    for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
-         w += (unsigned long long)gridDim.x * blockDim.x) {
+    // few redo rays: spread them over all warps, rpw lanes per warp, so that more
+    // warps hide the traversal latency and a warp carries fewer divergent rays
+    const unsigned long long W = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long rpw = n < W ? 1ull : (n + W - 1) / W < 32ull ? (n + W - 1) / W : 32ull;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (lane >= rpw) return;
+    for (unsigned long long w = warp * rpw + lane; w < n; w += W * rpw) {
         int64_t ray = A.redo[w];
         int s = find_seg(A.ray_off, A.n + 1, ray);
         const SceneDev& d = A.sd[s];
-        float3 df = launch_dir(ray - A.ray_off[s], d.n_rays);
+        float3 df = launch_dir(ray - A.ray_off[s], __ldg(A.sched.z + (ray - A.ray_off[s])));
         WRay<double> r;
         WRay<float> rf;
         r.o = mk(d.tx, d.ty, d.tz);
@@ -1682,7 +1831,7 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo_batch(BatchSbr A) {
             rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
             wray_init(rf);
             double th;
-            int id = closest64(d.nodes, d.bvh_tris, r, rf, d.eps, prev, stack, th, A.status);
+            int id = closest64(d.nodes, d.bvh_tris, r, rf, d.eps, prev, stack, cand, th, A.status);
             if (id < 0) break;
             key = rt_key_push(key, b, id);
             hash_insert(A.tables + (uint64_t)s * A.cap, A.cap - 1, key, A.uniq + s, A.uniq_limit, A.overflow);
@@ -1799,6 +1948,7 @@ struct BatchVis {
 __global__ void __launch_bounds__(TRACE_THREADS) k_visibility_batch(BatchVis A) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
+    int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
     unsigned long long c_vis = 0, c_tri = 0, c_seg = 0;
     unsigned long long n = *A.qcount;
     if (n > A.qcap) n = A.qcap;
@@ -1839,7 +1989,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_visibility_batch(BatchVis A) 
                 rd.o = pts[j];
                 rd.d = dv;
                 wray_init(rd);
-                if (any64(d.nodes, d.bvh_tris, rd, rf, tlo, thi, s0, s1, stack, A.status)) visible = false;
+                if (any64(d.nodes, d.bvh_tris, rd, rf, tlo, thi, s0, s1, stack, cand, A.status)) visible = false;
             }
         }
         if (visible) {
@@ -2015,13 +2165,16 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
     cudaStream_t st = ctx->stream;
     int32_t* status = rt_status_ptr(ctx);
     const size_t stack_bytes = (size_t)RT_STACK * TRACE_THREADS * sizeof(int);
+    const size_t vis_bytes = (size_t)(RT_STACK + VIS_CAND_CAP) * TRACE_THREADS * sizeof(int);
 
     // per-scene descriptors and prefix arrays on the device (in the paths' own memory)
     std::vector<SceneDev> hsd(n);
     for (int s = 0; s < n; ++s) {
         const rt_scene* sc = scenes[s];
         hsd[s] = SceneDev{sc->d_nodes, sc->d_bvh_tris, sc->d_tri_v, sc->d_tri_bary, sc->d_tri_n64, sc->d_tri_bary64,
-                          tx_host[3 * s], tx_host[3 * s + 1], tx_host[3 * s + 2], sc->eps, n_rays, (int32_t)tri_off[s]};
+                          tx_host[3 * s], tx_host[3 * s + 1], tx_host[3 * s + 2], sc->eps,
+                          make_float3((float)tx_host[3 * s], (float)tx_host[3 * s + 1], (float)tx_host[3 * s + 2]),
+                          n_rays, (int32_t)tri_off[s]};
     }
     SceneDev* d_sd = nullptr;
     int64_t* d_offs = nullptr;   // ray_off, rx_off, then cand_off, pair_off, bits_off (filled later)
@@ -2106,7 +2259,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         k_sbr_batch<<<ctx->num_sms * ctx->tune_sbr_blocks_per_sm, TRACE_THREADS, stack_bytes, st>>>(A);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
-        k_sbr_redo_batch<<<ctx->num_sms * 4, REDO_THREADS, (size_t)RT_STACK * REDO_THREADS * sizeof(int), st>>>(A);
+        k_sbr_redo_batch<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(A);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
         mark(ctx, 1);
@@ -2238,7 +2391,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         VA.bits = bits;
         VA.status = status;
         VA.counters = (ctx->profile & 2) ? ctx->d_counters : nullptr;
-        k_visibility_batch<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, stack_bytes, st>>>(VA);
+        k_visibility_batch<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st>>>(VA);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
         mark(ctx, 4);
