@@ -451,7 +451,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_upload(rt_c
         r.a = make_float4(lo[0], lo[1], lo[2], hi[0]);
         r.b = make_float4(hi[1], hi[2], INFINITY, INFINITY);
         r.c = make_float4(INFINITY, -INFINITY, -INFINITY, -INFINITY);
-        r.d = make_int4(ref, 0, cnt, 1);
+        r.d = make_int4(cnt > 0 ? ~((ref << 3) | (cnt - 1)) : ref, ~0, cnt, 1);
         dn.push_back(r);
     } else {
         for (int n : inner) {
@@ -463,7 +463,9 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_upload(rt_c
             b.a = make_float4(lo0[0], lo0[1], lo0[2], hi0[0]);
             b.b = make_float4(hi0[1], hi0[2], lo1[0], lo1[1]);
             b.c = make_float4(lo1[2], hi1[0], hi1[1], hi1[2]);
-            b.d = make_int4(r0, r1, c0, c1);
+            // child references as the traversal uses them: an inner child by its
+            // node index (>= 0), a leaf as ~((first << 3) | (count - 1))
+            b.d = make_int4(c0 > 0 ? ~((r0 << 3) | (c0 - 1)) : r0, c1 > 0 ? ~((r1 << 3) | (c1 - 1)) : r1, c0, c1);
             dn.push_back(b);
         }
     }

@@ -54,8 +54,9 @@ struct rt_ctx {
 //   a = (c0.lo.x, c0.lo.y, c0.lo.z, c0.hi.x)
 //   b = (c0.hi.y, c0.hi.z, c1.lo.x, c1.lo.y)
 //   c = (c1.lo.z, c1.hi.x, c1.hi.y, c1.hi.z)
-//   d = (ref0, ref1, count0, count1): count > 0 -> leaf over BVH-ordered
-//       triangles [ref, ref + count); count == 0 -> inner node index ref.
+//   d = (ref0, ref1, count0, count1): ref >= 0 -> inner node index ref;
+//       ref < 0 -> leaf over the BVH-ordered triangles [first, first + count)
+//       with ~ref = (first << 3) | (count - 1), count <= 8 (also in countN).
 struct __align__(16) BvhNode {
     float4 a, b, c;
     int4 d;

@@ -84,6 +84,7 @@ struct WRay {
     int kx, ky, kz;
     T Sx, Sy, Sz;
     float3 of, inv;   // FP32 origin and reciprocal direction for the slab tests
+    float3 oinv;      // of * inv, so that a slab distance is one FMA: l * inv - oinv
 };
 
 template <typename T>
@@ -119,6 +120,7 @@ __device__ __forceinline__ void wray_init(WRay<T>& r) {
     r.inv = make_float3(1.0f / (fabsf(dx) < 1e-30f ? copysignf(1e-30f, dx) : dx),
                         1.0f / (fabsf(dy) < 1e-30f ? copysignf(1e-30f, dy) : dy),
                         1.0f / (fabsf(dzz) < 1e-30f ? copysignf(1e-30f, dzz) : dzz));
+    r.oinv = make_float3(r.of.x * r.inv.x, r.of.y * r.inv.y, r.of.z * r.inv.z);
 }
 
 // Sheared edge functions U, V, W and scaled distance Tn of the watertight
@@ -171,18 +173,31 @@ __device__ __forceinline__ bool tri_test64(const WRay<double>& r, float4 p0, flo
     return true;
 }
 
+// Three-input FP32 min / max (sm_100 and later).
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Ray/box slab test over [tlo, thi]; a slab distance is l * inv - o * inv in one
+// FMA (boxes carry a 4e-6 diag pad, far above this rounding).
 template <typename R>
 __device__ __forceinline__ bool slab(const R& r, float lx, float ly, float lz, float hx, float hy, float hz, float tlo,
                                      float thi, float& tn) {
-    float tx0 = (lx - r.of.x) * r.inv.x, tx1 = (hx - r.of.x) * r.inv.x;
-    float ty0 = (ly - r.of.y) * r.inv.y, ty1 = (hy - r.of.y) * r.inv.y;
-    float tz0 = (lz - r.of.z) * r.inv.z, tz1 = (hz - r.of.z) * r.inv.z;
-    tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tlo));
-    float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), thi));
+    float tx0 = fmaf(lx, r.inv.x, -r.oinv.x), tx1 = fmaf(hx, r.inv.x, -r.oinv.x);
+    float ty0 = fmaf(ly, r.inv.y, -r.oinv.y), ty1 = fmaf(hy, r.inv.y, -r.oinv.y);
+    float tz0 = fmaf(lz, r.inv.z, -r.oinv.z), tz1 = fmaf(hz, r.inv.z, -r.oinv.z);
+    tn = max3f(fminf(tx0, tx1), fminf(ty0, ty1), fmaxf(fminf(tz0, tz1), tlo));
+    float tf = min3f(fmaxf(tx0, tx1), fmaxf(ty0, ty1), fminf(fmaxf(tz0, tz1), thi));
     return tn <= tf;
 }
 
-__device__ __forceinline__ int leaf_ref(int first, int count) { return ~((first << 3) | (count - 1)); }
 
 // Traversal of the two-child-box BVH with a per-thread stack in shared memory
 // (stack[k * blockDim.x + threadIdx.x]), nearer child first.  `leaf(first,
@@ -208,8 +223,7 @@ __device__ __forceinline__ void traverse(const BvhNode* __restrict__ nodes, cons
             float t0, t1;
             bool h0 = slab(r, a.x, a.y, a.z, a.w, b.x, b.y, tlo, thi, t0);
             bool h1 = slab(r, b.z, b.w, c.x, c.y, c.z, c.w, tlo, thi, t1);
-            int r0 = d.z > 0 ? leaf_ref(d.x, d.z) : d.x;
-            int r1 = d.w > 0 ? leaf_ref(d.y, d.w) : d.y;
+            const int r0 = d.x, r1 = d.y;
             if (h0 && h1) {
                 if (sp >= RT_STACK) {
                     rt_set_status(status, RT_ERR_STACK_OVERFLOW);
@@ -382,11 +396,11 @@ __device__ int closest64_inline(const BvhNode* __restrict__ nodes, const float4*
 // over the list in one converged loop, and the tie pass over the same list
 // (every hit within TIE_TOL of the best is in it).  A list overflow falls back to
 // closest64_inline.
-constexpr int CAND_CAP = 32;
+constexpr int CAND_CAP = 16;
 
 __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const WRay<double>& r,
-                         const WRay<float>& rf, double tmin, int skip, int* stack, int* cand, double& t_out,
-                         int32_t* status) {
+                         const WRay<float>& rf, double tmin, int skip, int* stack, int* cand, float* cand_t,
+                         double& t_out, int32_t* status) {
     const int stride = blockDim.x;
     const float tminf = (float)tmin;
     float thi = INFINITY;
@@ -403,8 +417,13 @@ __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __rest
             if (cls == 1) {
                 if (tf > thi) continue;   // beyond a robust hit
                 if (tf > tminf * 2.0f) thi = fminf(thi, tf * 1.001f + 10.0f * tminf);
+            } else {
+                tf = -1.0f;   // undecided: always goes to the FP64 test
             }
-            if (n < CAND_CAP) cand[n * stride] = k;
+            if (n < CAND_CAP) {
+                cand[n * stride] = k;
+                cand_t[n * stride] = tf;
+            }
             n++;
         }
         return false;
@@ -414,6 +433,7 @@ __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __rest
     bool have = false, near_tie = false;
     int best = -1;
     for (int i = 0; i < n; ++i) {
+        if (cand_t[i * stride] > thi) continue;   // a robust hit beyond the final far end
         const int k = cand[i * stride];
         float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
         int id = __float_as_int(p0.w);
@@ -435,6 +455,7 @@ __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __rest
     const double tmax = tb + TIE_TOL * tb;
     int low = 0x7fffffff;
     for (int i = 0; i < n; ++i) {
+        if (cand_t[i * stride] > thi) continue;
         const int k = cand[i * stride];
         float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
         int id = __float_as_int(p0.w);
@@ -753,6 +774,7 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const doub
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
     int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
+    float* cand_t = reinterpret_cast<float*>(smem_stack + (RT_STACK + CAND_CAP) * blockDim.x) + threadIdx.x;
     unsigned long long n = *A.redo_count;
     if (n > (unsigned long long)A.redo_cap) n = A.redo_cap;
     if (A.counters && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.counters + 3, n);
@@ -778,7 +800,7 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const doub
             rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
             wray_init(rf);
             double th;
-            int id = closest64(A.nodes, A.tris, r, rf, A.eps, prev, stack, cand, th, A.status);
+            int id = closest64(A.nodes, A.tris, r, rf, A.eps, prev, stack, cand, cand_t, th, A.status);
             if (id < 0) break;
             key = rt_key_push(key, b, id);
             hash_insert(A.table, A.mask, key, A.uniq, A.uniq_limit, A.overflow);
@@ -1069,19 +1091,23 @@ struct VisArgs {
     int64_t words;   // words per receiver row
     int32_t* status;
     unsigned long long* counters;   // optional instrumentation (slots 4..6)
+    int D;                          // max depth
+    int32_t* seg_q;                 // qcap: depth of a confirmed pair, -1 otherwise
+    float4* seg_o;                  // (D + 1) x qcap: segment origin (FP32), 1 / length in .w
+    float4* seg_d;                  // (D + 1) x qcap: segment vector (FP32)
 };
 
-// Per queued pair: FP64 image-method confirmation, then visibility of every
-// segment s_j -> s_{j+1}: any hit with eps < t*len < len - eps, the end
-// triangles excluded; FP32 first, FP64 for marginal segments.  Valid pairs set
-// their bit.
-__global__ void __launch_bounds__(TRACE_THREADS) k_visibility(VisArgs A) {
-    extern __shared__ int smem_stack[];
-    int* stack = smem_stack + threadIdx.x;
-    int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
+// Visibility in two launches.  k_backtrace: one thread per queued pair, the
+// FP64 image-method confirmation (dense FP64 work); a confirmed pair sets its
+// bit and stores its segments in FP32.  k_segments: one thread per (pair,
+// segment), segment-major so that the first segments of all pairs run before
+// the second ones: any hit with eps < t*len < len - eps (end triangles
+// excluded), FP32 first and FP64 for a marginal segment; a blocked segment
+// clears the pair's bit, and a segment whose pair is already cleared is
+// skipped.
+__global__ void __launch_bounds__(TRACE_THREADS) k_backtrace(VisArgs A) {
     unsigned long long n = *A.qcount;
     if (n > A.qcap) n = A.qcap;
-    unsigned long long c_vis = 0, c_tri = 0, c_seg = 0;
     for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
          w += (unsigned long long)gridDim.x * blockDim.x) {
         uint2 e = A.queue[w];
@@ -1091,36 +1117,72 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_visibility(VisArgs A) {
         const double* rp = A.rx + 3 * (int64_t)r;
         V3<double> pts[RT_MAX_DEPTH + 2];
         if (!backtrace64(A.C, k, q, mk(A.tx, A.ty, A.tz), mk(rp[0], rp[1], rp[2]), A.tri_v, A.tri_n64, A.bary64,
-                         A.eps, pts, nullptr))
+                         A.eps, pts, nullptr)) {
+            A.seg_q[w] = -1;
             continue;
-        bool visible = true;
-        for (int j = 0; j <= q && visible; ++j) {
-            V3<double> d = pts[j + 1] - pts[j];
-            double il = rsqrt(dot(d, d));   // 1 / len, only scales the guard band
-            int s0 = j >= 1 ? A.C.tri[(int64_t)(j - 1) * A.C.K + k] : -1;
-            int s1 = j + 1 <= q ? A.C.tri[(int64_t)j * A.C.K + k] : -1;
-            double tlo = A.eps * il, thi = 1.0 - A.eps * il;
-            WRay<float> rf;
-            rf.o = mk((float)pts[j].x, (float)pts[j].y, (float)pts[j].z);
-            rf.d = mk((float)d.x, (float)d.y, (float)d.z);
-            wray_init(rf);
-            bool und = false;
-            unsigned nv = 0, nt = 0;
-            bool hit = any32(A.nodes, A.bvh_tris, rf, (float)tlo, (float)thi, s0, s1, stack, und, A.status, nv, nt);
-            c_vis += nv;
-            c_tri += nt;
-            c_seg++;
-            if (hit) {
-                visible = false;
-            } else if (und) {
-                WRay<double> rd;
-                rd.o = pts[j];
-                rd.d = d;
-                wray_init(rd);
-                if (any64(A.nodes, A.bvh_tris, rd, rf, tlo, thi, s0, s1, stack, cand, A.status)) visible = false;
-            }
         }
-        if (visible) atomicOr(A.bits + (int64_t)r * A.words + (k >> 5), 1u << (k & 31));
+        A.seg_q[w] = q;
+        for (int j = 0; j <= q; ++j) {
+            V3<double> d = pts[j + 1] - pts[j];
+            float dx = (float)d.x, dy = (float)d.y, dz = (float)d.z;
+            const float il = rsqrtf(dx * dx + dy * dy + dz * dz);   // only scales the guard band
+            A.seg_o[(size_t)j * A.qcap + w] = make_float4((float)pts[j].x, (float)pts[j].y, (float)pts[j].z, il);
+            A.seg_d[(size_t)j * A.qcap + w] = make_float4(dx, dy, dz, 0.0f);
+        }
+        atomicOr(A.bits + (int64_t)r * A.words + (k >> 5), 1u << (k & 31));
+    }
+}
+
+__global__ void __launch_bounds__(TRACE_THREADS) k_segments(VisArgs A) {
+    extern __shared__ int smem_stack[];
+    int* stack = smem_stack + threadIdx.x;
+    int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
+    unsigned long long n = *A.qcount;
+    if (n > A.qcap) n = A.qcap;
+    const unsigned long long total = n * (unsigned long long)(A.D + 1);
+    unsigned long long c_vis = 0, c_tri = 0, c_seg = 0;
+    for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < total;
+         t += (unsigned long long)gridDim.x * blockDim.x) {
+        const int j = (int)(t / n);
+        const unsigned long long w = t - (unsigned long long)j * n;
+        const int q = A.seg_q[w];
+        if (q < j) continue;
+        uint2 e = A.queue[w];
+        const int64_t k = e.x;
+        const int r = (int)e.y;
+        uint32_t* word = A.bits + (int64_t)r * A.words + (k >> 5);
+        const uint32_t bit = 1u << (k & 31);
+        if (!(*(volatile uint32_t*)word & bit)) continue;   // another segment already blocked it
+        const float4 o4 = A.seg_o[(size_t)j * A.qcap + w], d4 = A.seg_d[(size_t)j * A.qcap + w];
+        const int s0 = j >= 1 ? A.C.tri[(int64_t)(j - 1) * A.C.K + k] : -1;
+        const int s1 = j + 1 <= q ? A.C.tri[(int64_t)j * A.C.K + k] : -1;
+        const float epsf = (float)A.eps;
+        WRay<float> rf;
+        rf.o = mk(o4.x, o4.y, o4.z);
+        rf.d = mk(d4.x, d4.y, d4.z);
+        wray_init(rf);
+        bool und = false;
+        unsigned nv = 0, nt = 0;
+        bool hit = any32(A.nodes, A.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, stack, und, A.status, nv,
+                         nt);
+        c_vis += nv;
+        c_tri += nt;
+        c_seg++;
+        if (!hit && und) {
+            // marginal: the segment again from the FP64 points, final decision in FP64
+            const double* rp = A.rx + 3 * (int64_t)r;
+            V3<double> pts[RT_MAX_DEPTH + 2];
+            backtrace64(A.C, k, q, mk(A.tx, A.ty, A.tz), mk(rp[0], rp[1], rp[2]), A.tri_v, A.tri_n64, A.bary64,
+                        A.eps, pts, nullptr);
+            V3<double> d = pts[j + 1] - pts[j];
+            double il = rsqrt(dot(d, d));
+            WRay<double> rd;
+            rd.o = pts[j];
+            rd.d = d;
+            wray_init(rd);
+            hit = any64(A.nodes, A.bvh_tris, rd, rf, A.eps * il, 1.0 - A.eps * il, s0, s1, stack, cand, A.status);
+        }
+        if (hit) atomicAnd(word, ~bit);
     }
     if (A.counters) {
         // every thread of the block reaches this point (grid-stride loop above)
@@ -1129,6 +1191,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_visibility(VisArgs A) {
         warp_count(A.counters + 6, c_seg);
     }
 }
+
 
 // Per-receiver popcount of the validity bitmask (one warp per receiver).
 __global__ void k_row_count(const uint32_t* __restrict__ bits, int R, int64_t words, int64_t* counts) {
@@ -1432,7 +1495,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         int blocks = ctx->num_sms * ctx->tune_sbr_blocks_per_sm;
         k_sbr<<<blocks, TRACE_THREADS, stack_bytes, st>>>(A, sc->d_tri_v); RT_COUNT(ctx);
         RT_CK_LAUNCH(ctx);
-        k_sbr_redo<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(
+        k_sbr_redo<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 2 * CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(
             A, sc->d_tri_n64);
         RT_COUNT(ctx);
         mark(ctx, 1);
@@ -1504,7 +1567,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
     for (int attempt = 0;; ++attempt) {
         size_t qcap = sc->queue_cap;
         size_t need = K * 4 + (size_t)D * K * 4 + (size_t)D * K * 24 + (size_t)D * K * 16 + qcap * 8 +
-                      (size_t)n_rx * words * 4 + 64 * 8 + (size_t)(n_rx + 1) * 8 * 2 + 16 * 256;
+                      (size_t)n_rx * words * 4 + 64 * 8 + (size_t)(n_rx + 1) * 8 * 2 + qcap * 4 +
+                      2 * (size_t)(D + 1) * qcap * 16 + 20 * 256;
         void* base;
         rt_status s = rt_scratch(ctx, need, &base);
         if (s != RT_OK) return fail(s);
@@ -1518,6 +1582,9 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         counters = ar.take<unsigned long long>(8);
         flags = ar.take<int32_t>(8);
         counts = ar.take<int64_t>(n_rx + 1);
+        int32_t* seg_q = ar.take<int32_t>(qcap);
+        float4* seg_o = ar.take<float4>((size_t)(D + 1) * qcap);
+        float4* seg_d = ar.take<float4>((size_t)(D + 1) * qcap);
         TCK(cudaMemsetAsync(counters, 0, 64, st));
         TCK(cudaMemsetAsync(flags, 0, 32, st));
         TCK(cudaMemsetAsync(bits, 0, (size_t)n_rx * words * 4, st));
@@ -1559,8 +1626,14 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         VA.words = words;
         VA.status = status;
         VA.counters = (ctx->profile & 2) ? ctx->d_counters : nullptr;
+        VA.D = D;
+        VA.seg_q = seg_q;
+        VA.seg_o = seg_o;
+        VA.seg_d = seg_d;
         ctx->h_counters[7] += K * (int64_t)n_rx;
-        k_visibility<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st>>>(VA); RT_COUNT(ctx);
+        k_backtrace<<<ctx->num_sms * 8, TRACE_THREADS, 0, st>>>(VA); RT_COUNT(ctx);
+        TCK(cudaGetLastError());
+        k_segments<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st>>>(VA); RT_COUNT(ctx);
         mark(ctx, 4);
         TCK(cudaGetLastError());
         int64_t* hp = ctx->h_pinned;
@@ -1804,6 +1877,7 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo_batch(BatchSbr A) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
     int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
+    float* cand_t = reinterpret_cast<float*>(smem_stack + (RT_STACK + CAND_CAP) * blockDim.x) + threadIdx.x;
     unsigned long long n = *A.redo_count;
     if (n > (unsigned long long)A.redo_cap) n = A.redo_cap;
     if (A.counters && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.counters + 3, n);
@@ -1831,7 +1905,7 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo_batch(BatchSbr A) {
             rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
             wray_init(rf);
             double th;
-            int id = closest64(d.nodes, d.bvh_tris, r, rf, d.eps, prev, stack, cand, th, A.status);
+            int id = closest64(d.nodes, d.bvh_tris, r, rf, d.eps, prev, stack, cand, cand_t, th, A.status);
             if (id < 0) break;
             key = rt_key_push(key, b, id);
             hash_insert(A.tables + (uint64_t)s * A.cap, A.cap - 1, key, A.uniq + s, A.uniq_limit, A.overflow);
@@ -1943,13 +2017,15 @@ struct BatchVis {
     uint32_t* bits;
     int32_t* status;
     unsigned long long* counters;   // optional instrumentation (slots 4..6)
+    int D;
+    int32_t* seg_q;                 // as VisArgs
+    float4* seg_o;
+    float4* seg_d;
 };
 
-__global__ void __launch_bounds__(TRACE_THREADS) k_visibility_batch(BatchVis A) {
-    extern __shared__ int smem_stack[];
-    int* stack = smem_stack + threadIdx.x;
-    int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
-    unsigned long long c_vis = 0, c_tri = 0, c_seg = 0;
+// k_backtrace / k_segments over the concatenated (scene, candidate, receiver)
+// index spaces of a batch.
+__global__ void __launch_bounds__(TRACE_THREADS) k_backtrace_batch(BatchVis A) {
     unsigned long long n = *A.qcount;
     if (n > A.qcap) n = A.qcap;
     for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
@@ -1962,49 +2038,84 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_visibility_batch(BatchVis A) 
         const double* rp = A.rx + 3 * rg;
         V3<double> pts[RT_MAX_DEPTH + 2];
         if (!backtrace64(A.C, kg, q, mk(d.tx, d.ty, d.tz), mk(rp[0], rp[1], rp[2]), d.tri_v, d.tri_n64, d.bary64,
-                         d.eps, pts, nullptr))
+                         d.eps, pts, nullptr)) {
+            A.seg_q[w] = -1;
             continue;
-        bool visible = true;
-        for (int j = 0; j <= q && visible; ++j) {
+        }
+        A.seg_q[w] = q;
+        for (int j = 0; j <= q; ++j) {
+            V3<double> dv = pts[j + 1] - pts[j];
+            float dx = (float)dv.x, dy = (float)dv.y, dz = (float)dv.z;
+            const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+            A.seg_o[(size_t)j * A.qcap + w] = make_float4((float)pts[j].x, (float)pts[j].y, (float)pts[j].z, il);
+            A.seg_d[(size_t)j * A.qcap + w] = make_float4(dx, dy, dz, 0.0f);
+        }
+        const int64_t words = (A.cand_off[s + 1] - A.cand_off[s] + 31) / 32;
+        const int64_t kl = kg - A.cand_off[s];
+        atomicOr(A.bits + A.bits_off[s] + (rg - A.rx_off[s]) * words + (kl >> 5), 1u << (kl & 31));
+    }
+}
+
+__global__ void __launch_bounds__(TRACE_THREADS) k_segments_batch(BatchVis A) {
+    extern __shared__ int smem_stack[];
+    int* stack = smem_stack + threadIdx.x;
+    int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
+    unsigned long long n = *A.qcount;
+    if (n > A.qcap) n = A.qcap;
+    const unsigned long long total = n * (unsigned long long)(A.D + 1);
+    unsigned long long c_vis = 0, c_tri = 0, c_seg = 0;
+    for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < total;
+         t += (unsigned long long)gridDim.x * blockDim.x) {
+        const int j = (int)(t / n);
+        const unsigned long long w = t - (unsigned long long)j * n;
+        const int q = A.seg_q[w];
+        if (q < j) continue;
+        uint2 e = A.queue[w];
+        const int64_t kg = e.x, rg = e.y;
+        const int s = find_seg(A.cand_off, A.n + 1, kg);
+        const SceneDev& d = A.sd[s];
+        const int64_t words = (A.cand_off[s + 1] - A.cand_off[s] + 31) / 32;
+        const int64_t kl = kg - A.cand_off[s];
+        uint32_t* word = A.bits + A.bits_off[s] + (rg - A.rx_off[s]) * words + (kl >> 5);
+        const uint32_t bit = 1u << (kl & 31);
+        if (!(*(volatile uint32_t*)word & bit)) continue;
+        const float4 o4 = A.seg_o[(size_t)j * A.qcap + w], d4 = A.seg_d[(size_t)j * A.qcap + w];
+        const int s0 = j >= 1 ? A.C.tri[(int64_t)(j - 1) * A.C.K + kg] : -1;
+        const int s1 = j + 1 <= q ? A.C.tri[(int64_t)j * A.C.K + kg] : -1;
+        const float epsf = (float)d.eps;
+        WRay<float> rf;
+        rf.o = mk(o4.x, o4.y, o4.z);
+        rf.d = mk(d4.x, d4.y, d4.z);
+        wray_init(rf);
+        bool und = false;
+        unsigned nv = 0, nt = 0;
+        bool hit = any32(d.nodes, d.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, stack, und, A.status, nv,
+                         nt);
+        c_vis += nv;
+        c_tri += nt;
+        c_seg++;
+        if (!hit && und) {
+            const double* rp = A.rx + 3 * rg;
+            V3<double> pts[RT_MAX_DEPTH + 2];
+            backtrace64(A.C, kg, q, mk(d.tx, d.ty, d.tz), mk(rp[0], rp[1], rp[2]), d.tri_v, d.tri_n64, d.bary64,
+                        d.eps, pts, nullptr);
             V3<double> dv = pts[j + 1] - pts[j];
             double il = rsqrt(dot(dv, dv));
-            int s0 = j >= 1 ? A.C.tri[(int64_t)(j - 1) * A.C.K + kg] : -1;
-            int s1 = j + 1 <= q ? A.C.tri[(int64_t)j * A.C.K + kg] : -1;
-            double tlo = d.eps * il, thi = 1.0 - d.eps * il;
-            WRay<float> rf;
-            rf.o = mk((float)pts[j].x, (float)pts[j].y, (float)pts[j].z);
-            rf.d = mk((float)dv.x, (float)dv.y, (float)dv.z);
-            wray_init(rf);
-            bool und = false;
-            unsigned nv = 0, nt = 0;
-            const bool blocked = any32(d.nodes, d.bvh_tris, rf, (float)tlo, (float)thi, s0, s1, stack, und,
-                                       A.status, nv, nt);
-            c_vis += nv;
-            c_tri += nt;
-            c_seg++;
-            if (blocked) {
-                visible = false;
-            } else if (und) {
-                WRay<double> rd;
-                rd.o = pts[j];
-                rd.d = dv;
-                wray_init(rd);
-                if (any64(d.nodes, d.bvh_tris, rd, rf, tlo, thi, s0, s1, stack, cand, A.status)) visible = false;
-            }
+            WRay<double> rd;
+            rd.o = pts[j];
+            rd.d = dv;
+            wray_init(rd);
+            hit = any64(d.nodes, d.bvh_tris, rd, rf, d.eps * il, 1.0 - d.eps * il, s0, s1, stack, cand, A.status);
         }
-        if (visible) {
-            const int64_t words = (A.cand_off[s + 1] - A.cand_off[s] + 31) / 32;
-            const int64_t kl = kg - A.cand_off[s];
-            atomicOr(A.bits + A.bits_off[s] + (rg - A.rx_off[s]) * words + (kl >> 5), 1u << (kl & 31));
-        }
+        if (hit) atomicAnd(word, ~bit);
     }
     if (A.counters) {
-        // every thread of the block reaches this point (grid-stride loop above)
         warp_count(A.counters + 4, c_vis);
         warp_count(A.counters + 5, c_tri);
         warp_count(A.counters + 6, c_seg);
     }
 }
+
 
 // Per-receiver popcount over all scenes (one warp per receiver).
 __global__ void k_row_count_batch(const uint32_t* __restrict__ bits, const int64_t* rx_off, const int64_t* cand_off,
@@ -2259,7 +2370,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         k_sbr_batch<<<ctx->num_sms * ctx->tune_sbr_blocks_per_sm, TRACE_THREADS, stack_bytes, st>>>(A);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
-        k_sbr_redo_batch<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(A);
+        k_sbr_redo_batch<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 2 * CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(A);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
         mark(ctx, 1);
@@ -2339,7 +2450,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
     for (int s = 0; s < n; ++s) qcap = std::max(qcap, scenes[s]->queue_cap);
     for (int attempt = 0;; ++attempt) {
         size_t need = KT * 4 + (size_t)D * KT * 4 + (size_t)D * KT * 24 + (size_t)D * KT * 16 + qcap * 8 +
-                      (size_t)bits_off[n] * 4 + 64 * 8 + (size_t)(rx_off[n] + 1) * 8 * 2 + 16 * 256;
+                      (size_t)bits_off[n] * 4 + 64 * 8 + (size_t)(rx_off[n] + 1) * 8 * 2 + qcap * 4 +
+                      2 * (size_t)(D + 1) * qcap * 16 + 20 * 256;
         void* base;
         rt_status s0 = rt_scratch(ctx, need, &base);
         if (s0 != RT_OK) return fail(s0);
@@ -2353,6 +2465,9 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         counters = ar.take<unsigned long long>(8);
         flags = ar.take<int32_t>(8);
         counts = ar.take<int64_t>(rx_off[n] + 1);
+        int32_t* seg_q = ar.take<int32_t>(qcap);
+        float4* seg_o = ar.take<float4>((size_t)(D + 1) * qcap);
+        float4* seg_d = ar.take<float4>((size_t)(D + 1) * qcap);
         BCK(cudaMemsetAsync(counters, 0, 64, st));
         BCK(cudaMemsetAsync(flags, 0, 32, st));
         BCK(cudaMemsetAsync(bits, 0, (size_t)bits_off[n] * 4, st));
@@ -2391,7 +2506,14 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         VA.bits = bits;
         VA.status = status;
         VA.counters = (ctx->profile & 2) ? ctx->d_counters : nullptr;
-        k_visibility_batch<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st>>>(VA);
+        VA.D = D;
+        VA.seg_q = seg_q;
+        VA.seg_o = seg_o;
+        VA.seg_d = seg_d;
+        k_backtrace_batch<<<ctx->num_sms * 8, TRACE_THREADS, 0, st>>>(VA);
+        RT_COUNT(ctx);
+        BCK(cudaGetLastError());
+        k_segments_batch<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st>>>(VA);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
         mark(ctx, 4);
