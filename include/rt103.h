@@ -243,6 +243,14 @@ rt_status rt_cfr_power_mse_fused(rt_ctx* ctx, const int64_t* rx_offsets_dev, int
                                  double delta_f_hz, int32_t n_sub, const float* target_power_dev,
                                  const float* rx_weight_dev, float* loss_dev, void* grad_a_dev,
                                  void* H_dev);
+/* Arithmetic of rt_cfr, rt_cfr_backward and rt_cfr_power_mse_fused (and its
+ * allocation-free variant): with enable = 1 (the default) and n_sub in {256, 512,
+ * 1024, 2048, 4096} the contraction over the paths runs on the tensor cores
+ * (tcgen05, TF32 operands split hi + lo, three products per term, FP32
+ * accumulation); otherwise, and with enable = 0, on the FP32 SIMT units.  Both
+ * compute the same quantities to FP32 accuracy.  A bounded device wait that runs
+ * out sets RT_ERR_TIMEOUT in the status word. */
+rt_status rt_set_cfr_tensor_cores(rt_ctx* ctx, int32_t enable);
 
 /* ------------------------------------------------------------------ neural materials */
 

@@ -5,6 +5,6 @@ include/rt103.h.  The Python layer only marshals arguments."""
 from ._lib import LIB_PATH, RtError, load  # noqa: F401
 from .api import (MLP_NB, MLP_NW, Context, Paths, Scene, autotune_trace, cfr, cfr_backward,  # noqa: F401
                   cfr_power_mse_fused, eval_fields, eval_fields_backward, import_paths, mlp_backward, mlp_forward,
-                  pack_mlp, set_tuning, trace_batch, trace_paths)
+                  pack_mlp, set_cfr_tensor_cores, set_tuning, trace_batch, trace_paths)
 from .autograd import (Cfr, CfrPowerMSE, EvalFields, LogMaterials, NeuralMaterials,  # noqa: F401
                        NeuralMaterialsFn, calibration_loss)

@@ -342,6 +342,11 @@ def trace_batch(ctx: Context, scenes, txs, rxs, n_rays: int, max_depth: int) -> 
     return p
 
 
+def set_cfr_tensor_cores(ctx: Context, enable: bool):
+    """CFR contraction on the tensor cores (default) or on the SIMT units (rt_set_cfr_tensor_cores)."""
+    ctx.check(ctx.lib.rt_set_cfr_tensor_cores(ctx.h, int(bool(enable))), "rt_set_cfr_tensor_cores")
+
+
 def set_tuning(ctx: Context, sbr: int, pairs: int, vis: int):
     ctx.check(ctx.lib.rt_set_tuning(ctx.h, int(sbr), int(pairs), int(vis)), "rt_set_tuning")
 

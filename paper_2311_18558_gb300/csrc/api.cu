@@ -71,8 +71,8 @@ rt_status rt_cfr_fused_scratch(rt_ctx* ctx, int R, double** part, unsigned int**
         ls->done = nullptr;
         int cap = std::max(R, 1024);
         RT_CK(ctx, cudaMalloc((void**)&ls->part, (size_t)cap * sizeof(double)));
-        RT_CK(ctx, cudaMalloc((void**)&ls->done, sizeof(unsigned int)));
-        RT_CK(ctx, cudaMemset(ls->done, 0, sizeof(unsigned int)));
+        RT_CK(ctx, cudaMalloc((void**)&ls->done, 4 * sizeof(unsigned int)));
+        RT_CK(ctx, cudaMemset(ls->done, 0, 4 * sizeof(unsigned int)));
         ls->cap = cap;
     }
     *part = ls->part;

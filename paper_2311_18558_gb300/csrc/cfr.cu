@@ -16,11 +16,16 @@
 // doubled phase then gives each phasor to FP32 accuracy.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <type_traits>
 
 #include "rt_internal.cuh"
+
+// Loss partials and the two counters (completed CTAs, next receiver) of the
+// fused and tensor-core kernels (api.cu); the counters are zero between launches.
+rt_status rt_cfr_fused_scratch(rt_ctx* ctx, int R, double** part, unsigned int** done);
 
 namespace {
 
@@ -325,6 +330,560 @@ __global__ void __launch_bounds__(CFR_THREADS) k_cfr_fused(CfrShape S, const int
     }
 }
 
+// ===========================================================================
+// Tensor-core path (tcgen05, kind::tf32, 3xTF32) for n_sub = 128 N2, N2 in
+// {2, 4, 8, 16, 32}.  Split c = N2 c1 + c2 with N1 = 128 rows c1 (the MMA M),
+// and carry the complex product in real form:
+//   forward   D[c1][c2'] = sum_k A'[c1][k] B'[k][c2'],  D = [Re H | Im H]
+//             A' = [Re Ac | Im Ac]  (128 x 2CP, Ac[c1][i] = c_i A_i[c1])
+//             B' = [[Re B, Im B], [-Im B, Re B]]  (2CP x 2N2)
+//   adjoint   Y[c1][i] = sum_c2 g[c1][c2] conj(B_i[c2]) as
+//             Y' = [Re Y | Im Y] = G' Bc',  G' = [Re g | Im g]  (128 x 2N2),
+//             Bc' = [[Re B^T, -Im B^T], [Im B^T, Re B^T]]  (2N2 x 2CP)
+//             then g_c[i] = sum_c1 conj(A_i[c1]) Y[c1][i] (per thread, then a
+//             transposed warp reduction over c1).
+// Every FP32 operand x is split as hi = tf32(x), lo = tf32(x - hi) and each
+// product accumulates hi.hi + hi.lo + lo.hi in FP32 (TMEM), which keeps FP32
+// accuracy.  One CTA of 128 threads: thread m owns row c1 = m, i.e. TMEM lane m,
+// so the loss epilogue and the adjoint reduction need no exchange of H.
+// Operands live in shared memory in the no-swizzle K-major layout: 8-row x
+// 16-byte core matrices, core (row block rb, k block kb) at rb * SBO + kb * 128.
+// CTAs are persistent and take receivers from a counter.
+
+constexpr int TC_THREADS = 128;
+constexpr int TC_CP = 16;                 // paths per chunk (at most 32: one per lane in the adjoint reduction)
+constexpr uint32_t TC_TMEM_COLS = 128;    // D (fwd) at column 0, Y' at TC_Y_COL
+constexpr uint32_t TC_Y_COL = 64;
+constexpr int TC_WAIT_LIMIT = 1 << 22;    // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start >> 4 (bits 0-13), leading byte offset
+// >> 4 (16-29), stride byte offset >> 4 (32-45), the fixed 0b001 at 46-48, no
+// base offset, relative LBO, no swizzle (61-63 = 0).
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
+// (7-9 = 2, 10-12 = 2), both K-major, N >> 3 at 17-22, M >> 4 at 24-28.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Waits for the phase with the given parity to complete; false after
+// TC_WAIT_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 16 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Stores 4 consecutive K elements (one core-matrix row) of row `row`, k block
+// `kb`, split into hi and lo tiles.
+__device__ __forceinline__ void put4(float* hi, float* lo, uint32_t sbo_floats, int row, int kb, float x0, float x1,
+                                     float x2, float x3) {
+    const int off = (row >> 3) * (int)sbo_floats + kb * 32 + (row & 7) * 4;
+    const float h0 = tf32_rna(x0), h1 = tf32_rna(x1), h2 = tf32_rna(x2), h3 = tf32_rna(x3);
+    *reinterpret_cast<float4*>(hi + off) = make_float4(h0, h1, h2, h3);
+    *reinterpret_cast<float4*>(lo + off) =
+        make_float4(tf32_rna(x0 - h0), tf32_rna(x1 - h1), tf32_rna(x2 - h2), tf32_rna(x3 - h3));
+}
+
+template <int N2>
+struct TcDims {
+    static constexpr int NB = 2 * N2 < 16 ? 16 : 2 * N2;   // forward MMA N (padded)
+    static constexpr int KG = 2 * N2 < 8 ? 8 : 2 * N2;     // adjoint MMA K (padded)
+    static constexpr int KA = 2 * TC_CP;                   // forward MMA K
+    static constexpr int A_FLOATS = 128 * (KA > KG ? KA : KG);
+    static constexpr int B_FLOATS = (NB * KA > 2 * TC_CP * KG) ? NB * KA : 2 * TC_CP * KG;
+    static constexpr int NAH = 16, NAL = 8;                // A_i[c1] = Ah[c1 / 8] Al[c1 % 8]
+    static constexpr int NF = NAH + NAL + N2;              // factor phasors per path
+};
+
+// c_i A_i at c1 = 8k, per path (forward operand factors)
+constexpr int TC_NFC = 16;
+
+// Dynamic shared memory of the tensor-core kernel: A and B operand tiles (hi,
+// lo), then the phasor tables and a reduction buffer.
+template <int N2>
+__host__ __device__ constexpr size_t tc_smem_bytes() {
+    using T = TcDims<N2>;
+    return (size_t)(2 * T::A_FLOATS + 2 * T::B_FLOATS) * 4 + (size_t)TC_CP * (T::NF + TC_NFC) * 8 +
+           (size_t)TC_CP * 8 + (size_t)TC_CP * sizeof(PathPhase) + 4 * 32 * 8 + 64;
+}
+
+// Phase data and factor phasors of paths [base, base + n), padded with zero
+// phases (phasor 1, c = 0) up to n_pad:
+//   tP[ii], tC[ii] = a_i exp(-j 2 pi f_0 tau_i) (if a), tF[ii][0..16) = A_i at
+//   c1 = 8k, tF[ii][16..24) = A_i at c1 = k, tF[ii][24..24+N2) = B_i[c2].
+template <int N2>
+__device__ __forceinline__ void tc_tables(const CfrShape& S, int64_t base, int n, int n_pad,
+                                          const float2* __restrict__ a, const double* __restrict__ tau,
+                                          PathPhase* tP, float2* tC, float2* tF, float2* tFc) {
+    using T = TcDims<N2>;
+    const int t = threadIdx.x;
+    __syncthreads();
+    if (t < n_pad) {
+        if (t < n) {
+            PathPhase p = path_phase(tau[base + t], S.f0, S.df);
+            tP[t] = p;
+            tC[t] = a ? cmul(a[base + t], base_phasor(p)) : make_float2(0.0f, 0.0f);
+        } else {
+            tP[t] = PathPhase{0.0f, 0.0f, 0.0f};
+            tC[t] = make_float2(0.0f, 0.0f);
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < n_pad * T::NF; e += TC_THREADS) {
+        const int ii = e / T::NF, k = e - ii * T::NF;
+        const int m = k < T::NAH ? k * T::NAL * N2 : k < T::NAH + T::NAL ? (k - T::NAH) * N2 : k - T::NAH - T::NAL;
+        const float2 f = phasor(tP[ii], m);
+        tF[e] = f;
+        if (a && k < T::NAH) tFc[ii * TC_NFC + k] = cmul(tC[ii], f);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ float2 tc_A(const float2* tF, int nf, int ii, int m) {   // A_i[c1 = m]
+    return cmul(tF[ii * nf + (m >> 3)], tF[ii * nf + 16 + (m & 7)]);
+}
+
+// Receivers with at most TC_DIRECT paths skip the MMAs: each thread evaluates its
+// row directly (N2 x n complex products), which is cheaper than building 128-row
+// operand tiles for so few paths.
+constexpr int TC_DIRECT = 8;
+
+// MODE 0: forward (H out); 1: adjoint from g_H; 2: forward + power MSE + adjoint.
+template <int N2, int MODE>
+__global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t* __restrict__ offs, int R,
+                                                       const float2* __restrict__ a, const double* __restrict__ tau,
+                                                       const float* __restrict__ target, const float* __restrict__ w,
+                                                       const float2* __restrict__ gH, float* __restrict__ loss,
+                                                       float2* __restrict__ ga, float2* __restrict__ H,
+                                                       double* __restrict__ part, unsigned int* __restrict__ ctr,
+                                                       int32_t* __restrict__ status) {
+    using T = TcDims<N2>;
+    constexpr bool FWD = MODE != 1, BWD = MODE != 0;
+    extern __shared__ float4 smem4[];
+    float* A_hi = reinterpret_cast<float*>(smem4);
+    float* A_lo = A_hi + T::A_FLOATS;
+    float* B_hi = A_lo + T::A_FLOATS;
+    float* B_lo = B_hi + T::B_FLOATS;
+    float2* tF = reinterpret_cast<float2*>(B_lo + T::B_FLOATS);
+    float2* tFc = tF + TC_CP * T::NF;
+    float2* tC = tFc + TC_CP * TC_NFC;
+    float2* tRed = tC + TC_CP;
+    PathPhase* tP = reinterpret_cast<PathPhase*>(tRed + 4 * 32);
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_sh;
+    __shared__ int s_r;
+    __shared__ double s_red[TC_THREADS / 32];
+    __shared__ bool s_last;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t mb = smem_u32(&mbar);
+    if (tid == 0) mbar_init(mb, 1);
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_sh), TC_TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_sh;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t parity = 0;
+    bool ok = true;
+    const float inv_rn = 1.0f / ((float)R * (float)S.N);
+    const int m = tid;   // row c1 of this thread
+
+    // one batch of MMAs issued by thread 0, completion on the mbarrier
+    auto run_mma = [&](auto issue) -> bool {
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue();
+            tc_commit(mb);
+        }
+        bool done = mbar_wait(mb, parity);
+        parity ^= 1u;
+        tc_fence_after();
+        return __syncthreads_and(done) != 0;
+    };
+
+    for (;;) {
+        __syncthreads();   // every thread has read s_r (and finished the previous receiver)
+        if (tid == 0) s_r = (int)atomicAdd(ctr + 1, 1u);
+        __syncthreads();
+        const int r = s_r;
+        if (r >= R || !ok) break;
+        const int64_t i0 = offs[r], i1 = offs[r + 1];
+        const int P = (int)(i1 - i0);
+        const bool direct = P <= TC_DIRECT;
+        const int nch = (P + TC_CP - 1) / TC_CP;
+        float hre[N2], him[N2];
+#pragma unroll
+        for (int c2 = 0; c2 < N2; ++c2) hre[c2] = him[c2] = 0.0f;
+
+        if (FWD && direct && P > 0) {
+            tc_tables<N2>(S, i0, P, P, a, tau, tP, tC, tF, tFc);
+            for (int ii = 0; ii < P; ++ii) {
+                const float2 ac = cmul(tFc[ii * TC_NFC + (m >> 3)], tF[ii * T::NF + 16 + (m & 7)]);
+                const float2* B = tF + ii * T::NF + T::NAH + T::NAL;
+#pragma unroll
+                for (int c2 = 0; c2 < N2; ++c2) {
+                    const float2 b = B[c2];
+                    hre[c2] = fmaf(ac.x, b.x, fmaf(-ac.y, b.y, hre[c2]));
+                    him[c2] = fmaf(ac.x, b.y, fmaf(ac.y, b.x, him[c2]));
+                }
+            }
+        } else if (FWD && P > 0) {
+            bool first = true;
+            for (int ch = 0; ch < nch && ok; ++ch) {
+                const int64_t base = i0 + (int64_t)ch * TC_CP;
+                const int n = min(TC_CP, P - ch * TC_CP);
+                const int n_pad = (n + 7) & ~7;   // the K steps issued cover paths [0, n_pad)
+                tc_tables<N2>(S, base, n, n_pad, a, tau, tP, tC, tF, tFc);
+                // A' row m: k = i (Re Ac), k = CP + i (Im Ac)
+                for (int i4 = 0; i4 < n_pad / 4; ++i4) {
+                    float re[4], im[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int ii = 4 * i4 + q;
+                        float2 v = cmul(tFc[ii * TC_NFC + (m >> 3)], tF[ii * T::NF + 16 + (m & 7)]);
+                        re[q] = v.x;
+                        im[q] = v.y;
+                    }
+                    put4(A_hi, A_lo, (T::KA / 4) * 32, m, i4, re[0], re[1], re[2], re[3]);
+                    put4(A_hi, A_lo, (T::KA / 4) * 32, m, TC_CP / 4 + i4, im[0], im[1], im[2], im[3]);
+                }
+                // B' (transposed, NB rows x KA): row c2' < N2: [Re B | -Im B], N2 <= c2' < 2N2: [Im B | Re B]
+                const int nkb = n_pad / 4;   // k blocks per half
+                for (int g = tid; g < 2 * N2 * 2 * nkb; g += TC_THREADS) {
+                    const int row = g / (2 * nkb), kk = g - row * (2 * nkb);
+                    const bool imhalf = kk >= nkb;
+                    const int kb = imhalf ? TC_CP / 4 + (kk - nkb) : kk;
+                    const int i0p = 4 * (imhalf ? kk - nkb : kk);
+                    float x[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 b = tF[(i0p + q) * T::NF + T::NAH + T::NAL + (row % N2)];
+                        x[q] = row < N2 ? (imhalf ? -b.y : b.x) : (imhalf ? b.x : b.y);
+                    }
+                    put4(B_hi, B_lo, (T::KA / 4) * 32, row, kb, x[0], x[1], x[2], x[3]);
+                }
+                ok = run_mma([&]() {
+                    const uint32_t idesc = tc_idesc(128, T::NB);
+                    const uint32_t ah = smem_u32(A_hi), al = smem_u32(A_lo), bh = smem_u32(B_hi), bl = smem_u32(B_lo);
+                    const uint32_t sbo = (T::KA / 4) * 128;
+                    for (int s = 0; s < T::KA / 8; ++s) {
+                        if (8 * (s % (TC_CP / 8)) >= n) continue;   // all-zero K step
+                        const uint32_t off = (uint32_t)s * 256;
+                        tc_mma(tmem, tc_sdesc(ah + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, first ? 0u : 1u);
+                        tc_mma(tmem, tc_sdesc(ah + off, 128, sbo), tc_sdesc(bl + off, 128, sbo), idesc, 1u);
+                        tc_mma(tmem, tc_sdesc(al + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, 1u);
+                        first = false;
+                    }
+                });
+                first = false;
+            }
+            if (!ok) break;
+            float v[T::NB];
+#pragma unroll
+            for (int c = 0; c < T::NB; c += 16) tmem_ld16(lane_base + (uint32_t)c, v + c);
+            tmem_wait_ld();
+            tc_fence_before();
+#pragma unroll
+            for (int c2 = 0; c2 < N2; ++c2) {
+                hre[c2] = v[c2];
+                him[c2] = v[N2 + c2];
+            }
+        }
+
+        // ---- epilogue: H out, loss, g_H
+        const int64_t hrow = (int64_t)r * S.N + (int64_t)m * N2;
+        if (MODE == 0) {
+#pragma unroll
+            for (int c2 = 0; c2 < N2; ++c2) H[hrow + c2] = make_float2(hre[c2], him[c2]);
+            continue;
+        }
+        float gre[N2], gim[N2];
+        if (MODE == 2) {
+            const float wr = w[r];
+            double lsum = 0.0;
+#pragma unroll
+            for (int c2 = 0; c2 < N2; ++c2) {
+                const float e = hre[c2] * hre[c2] + him[c2] * him[c2] - target[hrow + c2];
+                const float we = wr * e;
+                lsum += (double)(we * we);
+                const float s = 4.0f * wr * wr * e * inv_rn;   // dL/dH = 4 w^2 (|H|^2 - P*) H / (R N)
+                gre[c2] = s * hre[c2];
+                gim[c2] = s * him[c2];
+                if (H) H[hrow + c2] = make_float2(hre[c2], him[c2]);
+            }
+            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+            if (lane == 0) s_red[warp] = lsum;
+        } else {
+#pragma unroll
+            for (int c2 = 0; c2 < N2; ++c2) {
+                const float2 g = gH[hrow + c2];
+                gre[c2] = g.x;
+                gim[c2] = g.y;
+            }
+        }
+
+        // ---- adjoint: Y[m][i] = sum_c2 g[m][c2] conj(B_i[c2]), then conj(A_i[m]) Y, reduced over m
+        // last chunk first: its tables are still in place from the forward
+        for (int ch = nch - 1; ch >= 0 && ok; --ch) {
+            const int64_t base = i0 + (int64_t)ch * TC_CP;
+            const int n = min(TC_CP, P - ch * TC_CP);
+            const int n_pad = direct ? n : (n + 7) & ~7;
+            if (!FWD || ch != nch - 1) tc_tables<N2>(S, base, n, n_pad, nullptr, tau, tP, tC, tF, tFc);
+            float vr[32], vi[32];
+            if (direct) {
+#pragma unroll
+                for (int ii = 0; ii < 32; ++ii) {
+                    float yr = 0.0f, yi = 0.0f;
+                    if (ii < n) {
+                        const float2* B = tF + ii * T::NF + T::NAH + T::NAL;
+#pragma unroll
+                        for (int c2 = 0; c2 < N2; ++c2) {   // g conj(B)
+                            const float2 b = B[c2];
+                            yr = fmaf(gre[c2], b.x, fmaf(gim[c2], b.y, yr));
+                            yi = fmaf(gim[c2], b.x, fmaf(-gre[c2], b.y, yi));
+                        }
+                    }
+                    vr[ii] = yr;
+                    vi[ii] = yi;
+                }
+            } else {
+                if (ch == nch - 1) {
+                    // G' (128 x KG), written once per receiver into the A tiles
+#pragma unroll
+                    for (int kb = 0; kb < T::KG / 4; ++kb) {
+                        float x[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int k = 4 * kb + q;
+                            x[q] = k < N2 ? gre[k % N2] : k < 2 * N2 ? gim[k % N2] : 0.0f;
+                        }
+                        put4(A_hi, A_lo, (T::KG / 4) * 32, m, kb, x[0], x[1], x[2], x[3]);
+                    }
+                }
+                // Bc' (transposed, 2CP rows x KG): row i < CP: [Re B_i | Im B_i], row CP + i: [-Im B_i | Re B_i]
+                for (int g = tid; g < 2 * n_pad * (T::KG / 4); g += TC_THREADS) {
+                    const int rr = g / (T::KG / 4), kb = g - rr * (T::KG / 4);
+                    const bool imrow = rr >= n_pad;
+                    const int ii = imrow ? rr - n_pad : rr;
+                    const int row = imrow ? TC_CP + ii : ii;
+                    float x[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = 4 * kb + q;
+                        float v = 0.0f;
+                        if (k < 2 * N2) {
+                            const float2 b = tF[ii * T::NF + T::NAH + T::NAL + (k % N2)];
+                            v = k < N2 ? (imrow ? -b.y : b.x) : (imrow ? b.x : b.y);
+                        }
+                        x[q] = v;
+                    }
+                    put4(B_hi, B_lo, (T::KG / 4) * 32, row, kb, x[0], x[1], x[2], x[3]);
+                }
+                ok = run_mma([&]() {
+                    const uint32_t idesc = tc_idesc(128, 2 * TC_CP);
+                    const uint32_t ah = smem_u32(A_hi), al = smem_u32(A_lo), bh = smem_u32(B_hi), bl = smem_u32(B_lo);
+                    const uint32_t sbo = (T::KG / 4) * 128;
+                    const uint32_t d = tmem + TC_Y_COL;
+                    for (int s = 0; s < T::KG / 8; ++s) {
+                        const uint32_t off = (uint32_t)s * 256;
+                        tc_mma(d, tc_sdesc(ah + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, s > 0 ? 1u : 0u);
+                        tc_mma(d, tc_sdesc(ah + off, 128, sbo), tc_sdesc(bl + off, 128, sbo), idesc, 1u);
+                        tc_mma(d, tc_sdesc(al + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, 1u);
+                    }
+                });
+                if (!ok) break;
+#pragma unroll
+                for (int c = 0; c < TC_CP; c += 16) {
+                    tmem_ld16(lane_base + TC_Y_COL + c, vr + c);
+                    tmem_ld16(lane_base + TC_Y_COL + TC_CP + c, vi + c);
+                }
+                tmem_wait_ld();
+                tc_fence_before();
+#pragma unroll
+                for (int ii = TC_CP; ii < 32; ++ii) vr[ii] = vi[ii] = 0.0f;
+            }
+#pragma unroll
+            for (int ii = 0; ii < 32; ++ii) {   // conj(A_i[m]) Y[m][i]
+                float2 p = make_float2(0.0f, 0.0f);
+                if (ii < n) p = cmulc(make_float2(vr[ii], vi[ii]), tc_A(tF, T::NF, ii, m));
+                vr[ii] = p.x;
+                vi[ii] = p.y;
+            }
+            // transposed reduction: lane l ends with this warp's sum for path l (mod TC_CP)
+            constexpr int RED_TOP = TC_CP > 16 ? 16 : TC_CP / 2;
+#pragma unroll
+            for (int o = RED_TOP; o >= 1; o >>= 1) {
+                const bool up = (lane & o) != 0;
+#pragma unroll
+                for (int j = 0; j < o; ++j) {
+                    const float sr = up ? vr[j] : vr[j + o], si = up ? vi[j] : vi[j + o];
+                    const float kr = up ? vr[j + o] : vr[j], ki = up ? vi[j + o] : vi[j];
+                    vr[j] = kr + __shfl_xor_sync(0xffffffffu, sr, o);
+                    vi[j] = ki + __shfl_xor_sync(0xffffffffu, si, o);
+                }
+            }
+#pragma unroll
+            for (int o = 2 * RED_TOP; o < 32; o <<= 1) {   // lanes l and l ^ o hold the same paths
+                vr[0] += __shfl_xor_sync(0xffffffffu, vr[0], o);
+                vi[0] += __shfl_xor_sync(0xffffffffu, vi[0], o);
+            }
+            tRed[warp * 32 + lane] = make_float2(vr[0], vi[0]);
+            __syncthreads();
+            if (warp == 0 && lane < n) {
+                float2 s = tRed[lane];
+#pragma unroll
+                for (int k = 1; k < TC_THREADS / 32; ++k) {
+                    s.x += tRed[k * 32 + lane].x;
+                    s.y += tRed[k * 32 + lane].y;
+                }
+                ga[base + lane] = cmulc(s, base_phasor(tP[lane]));
+            }
+        }
+        if (MODE == 2) {
+            __syncthreads();
+            if (tid == 0) part[r] = s_red[0] + s_red[1] + s_red[2] + s_red[3];
+        }
+    }
+
+    if (!ok) {
+        rt_set_status(status, RT_ERR_TIMEOUT);
+        mbar_wait(mb, parity ^ 1u);   // bounded: let an unfinished batch drain before TMEM goes
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
+    // completion: the last CTA resets the receiver counter (and sums the loss)
+    if (tid == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(ctr, 1u);
+        s_last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (MODE == 2) {
+            double s = 0.0;
+            for (int k = tid; k < R; k += TC_THREADS) s += ((volatile double*)part)[k];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) s_red[warp] = s;
+            __syncthreads();
+            if (tid == 0) *loss = (float)((s_red[0] + s_red[1] + s_red[2] + s_red[3]) * (double)inv_rn);
+        }
+        if (tid == 0) {
+            ctr[0] = 0u;
+            ctr[1] = 0u;
+        }
+    }
+}
+
+// Tensor-core launch for n_sub = 128 N2; returns RT_ERR_UNSUPPORTED for other sizes.
+template <int MODE>
+rt_status launch_tc(rt_ctx* ctx, const CfrShape& S, const int64_t* offs, int R, const float2* a, const double* tau,
+                    const float* target, const float* w, const float2* gH, float* loss, float2* ga, float2* H,
+                    double* part, unsigned int* ctr) {
+    auto go = [&](auto n2) -> rt_status {
+        constexpr int N2 = decltype(n2)::value;
+        auto kern = k_cfr_tc<N2, MODE>;
+        const size_t smem = tc_smem_bytes<N2>();
+        RT_CK(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RT_CK(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
+        // resident CTAs per SM: shared memory (with the per-CTA reservation) and TMEM
+        int smem_sm = 0, reserved = 0;
+        RT_CK(ctx, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+        RT_CK(ctx, cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device));
+        int per_sm = smem_sm / (int)(smem + 64 + (size_t)reserved);
+        per_sm = std::max(1, std::min(per_sm, (int)(512 / TC_TMEM_COLS)));
+        const int grid = std::max(1, std::min(R, ctx->num_sms * per_sm));
+        kern<<<grid, TC_THREADS, smem, ctx->stream>>>(S, offs, R, a, tau, target, w, gH, loss, ga, H, part, ctr,
+                                                       ctx->d_status);
+        RT_COUNT(ctx);
+        RT_CK_LAUNCH(ctx);
+        return RT_OK;
+    };
+    if (S.N1 * S.N2 != S.N) return RT_ERR_UNSUPPORTED;
+    switch (S.N) {
+        case 256: return go(std::integral_constant<int, 2>());
+        case 512: return go(std::integral_constant<int, 4>());
+        case 1024: return go(std::integral_constant<int, 8>());
+        case 2048: return go(std::integral_constant<int, 16>());
+        case 4096: return go(std::integral_constant<int, 32>());
+        default: return RT_ERR_UNSUPPORTED;
+    }
+}
+
+bool tc_supported(const rt_ctx* ctx, int n_sub) {
+    return ctx->cfr_tensor_cores && (n_sub == 256 || n_sub == 512 || n_sub == 1024 || n_sub == 2048 || n_sub == 4096);
+}
+
 bool make_shape(int n_sub, double fc, double df, CfrShape& S) {
     if (n_sub < 1 || n_sub > 4096 || (n_sub > 1 && (n_sub & 1))) return false;
     S.N = n_sub;
@@ -379,6 +938,14 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr(rt_ctx* ctx, 
     rt_status s = check_cfr(ctx, rx_offsets_dev, n_rx, tau_dev, n_sub, f_center_hz, delta_f_hz, S);
     if (s != RT_OK) return s;
     if (!a_dev || !H_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null device pointer");
+    if (tc_supported(ctx, n_sub)) {
+        double* part;
+        unsigned int* ctr;
+        s = rt_cfr_fused_scratch(ctx, n_rx, &part, &ctr);
+        if (s != RT_OK) return s;
+        return launch_tc<0>(ctx, S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, nullptr, nullptr, nullptr,
+                            nullptr, nullptr, (float2*)H_dev, part, ctr);
+    }
     const size_t smem = fwd_smem(S);
     return dispatch_opt(ctx, S.N, [&](auto opt) -> rt_status {
         constexpr int O = decltype(opt)::value;
@@ -398,6 +965,14 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_backward(rt_c
     rt_status s = check_cfr(ctx, rx_offsets_dev, n_rx, tau_dev, n_sub, f_center_hz, delta_f_hz, S);
     if (s != RT_OK) return s;
     if (!grad_H_dev || !grad_a_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null device pointer");
+    if (tc_supported(ctx, n_sub)) {
+        double* part;
+        unsigned int* ctr;
+        s = rt_cfr_fused_scratch(ctx, n_rx, &part, &ctr);
+        if (s != RT_OK) return s;
+        return launch_tc<1>(ctx, S, rx_offsets_dev, n_rx, nullptr, tau_dev, nullptr, nullptr,
+                            (const float2*)grad_H_dev, nullptr, (float2*)grad_a_dev, nullptr, part, ctr);
+    }
     const size_t smem = fwd_smem(S) + (size_t)S.N * 8;
     s = set_smem(ctx, k_cfr_bwd, smem);
     if (s != RT_OK) return s;
@@ -407,8 +982,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_backward(rt_c
     return RT_OK;
 }
 
-// Loss partials and completion counter of the fused kernel (api.cu).
-rt_status rt_cfr_fused_scratch(rt_ctx* ctx, int R, double** part, unsigned int** done);
+
 
 extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fused(rt_ctx* ctx, const int64_t* rx_offsets_dev, int32_t n_rx,
                                             const void* a_dev, const double* tau_dev, double f_center_hz,
@@ -424,6 +998,9 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fus
     unsigned int* done;
     s = rt_cfr_fused_scratch(ctx, n_rx, &part, &done);
     if (s != RT_OK) return s;
+    if (tc_supported(ctx, n_sub))
+        return launch_tc<2>(ctx, S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, target_power_dev,
+                            rx_weight_dev, nullptr, loss_dev, (float2*)grad_a_dev, (float2*)H_dev, part, done);
     const size_t smem = fwd_smem(S) + (size_t)S.N * 8;
     return dispatch_opt(ctx, S.N, [&](auto opt) -> rt_status {
         constexpr int O = decltype(opt)::value;
@@ -499,7 +1076,10 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fus
     if (s != RT_OK) return s;
     double* part = reinterpret_cast<double*>(base);
     unsigned int* done = reinterpret_cast<unsigned int*>(base + RT_NOALLOC_MAX_RX * sizeof(double));
-    RT_CK(ctx, cudaMemsetAsync(done, 0, sizeof(unsigned int), ctx->stream));
+    RT_CK(ctx, cudaMemsetAsync(done, 0, 2 * sizeof(unsigned int), ctx->stream));
+    if (tc_supported(ctx, n_sub))
+        return launch_tc<2>(ctx, S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, target_power_dev,
+                            rx_weight_dev, nullptr, loss_dev, (float2*)grad_a_dev, (float2*)H_dev, part, done);
     const size_t smem = fwd_smem(S) + (size_t)S.N * 8;
     return dispatch_opt(ctx, S.N, [&](auto opt) -> rt_status {
         constexpr int O = decltype(opt)::value;
@@ -512,4 +1092,11 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fus
         RT_CK_LAUNCH(ctx);
         return RT_OK;
     });
+}
+
+extern "C" __attribute__((visibility("default"))) rt_status rt_set_cfr_tensor_cores(rt_ctx* ctx, int32_t enable) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (enable != 0 && enable != 1) return rt_fail(ctx, RT_ERR_INVALID_ARG, "enable must be 0 or 1");
+    ctx->cfr_tensor_cores = enable;
+    return RT_OK;
 }

@@ -45,6 +45,7 @@ struct rt_ctx {
     int tune_sbr_blocks_per_sm = 8;
     int tune_pairs_blocks_per_sm = 16;
     int tune_vis_blocks_per_sm = 8;
+    int cfr_tensor_cores = 1;   // CFR on tcgen05 (3xTF32) where n_sub allows, else SIMT
 };
 
 // Count one kernel launch of `ctx` (every launch site calls this).

@@ -136,18 +136,22 @@ def test_cfr_fused_loss_and_grad(rt, ctx):
     Href = oracle.cfr(a.astype(np.complex128), tau, offs, fc, df, N)
     T = (np.abs(Href) ** 2 * rng.uniform(0.5, 1.5, Href.shape)).astype(np.float32)
     w = oracle.power_weights(T).astype(np.float32)
-    L_ref, gH = oracle.power_mse(Href, T, w)
-    ga_ref = oracle.cfr_grad(tau, offs, fc, df, N, gH)
+    L_ref, _ = oracle.power_mse(Href, T, w)
     Hd = torch.empty((64, N), dtype=torch.complex64, device="cuda")
     for _ in range(2):   # twice: the completion counter must reset itself
         loss, ga, H = rt.cfr_power_mse_fused(ctx, _dev(offs, torch.int64), _dev(a, torch.complex64),
                                              _dev(tau, torch.float64), fc, df, N, _dev(T, torch.float32),
                                              _dev(w, torch.float32), H=Hd)
         assert abs(loss.item() - L_ref) <= 1e-4 * abs(L_ref)
-        ga = ga.cpu().numpy()
-        assert np.linalg.norm(ga - ga_ref) <= 1e-4 * np.linalg.norm(ga_ref)
-        num, den = normwise_rows(H.cpu().numpy(), Href)
+        Hg = H.cpu().numpy()
+        num, den = normwise_rows(Hg, Href)
         assert (num[den > 0] / den[den > 0]).max() <= 1e-4
+        # dL/dH = 4 w^2 (|H|^2 - P*) H / (R N) magnifies the rounding of H where |H|^2
+        # is close to P*, so the adjoint is checked at the H the kernel used
+        _, gH_at = oracle.power_mse(Hg.astype(np.complex128), T, w)
+        ga_at = oracle.cfr_grad(tau, offs, fc, df, N, gH_at)
+        ga = ga.cpu().numpy()
+        assert np.linalg.norm(ga - ga_at) <= 1e-4 * np.linalg.norm(ga_at)
 
 
 def test_calibration_gradient_end_to_end(rt, ctx, indoor):
