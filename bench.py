@@ -361,10 +361,12 @@ def run_ours(args):
 
     # ---------------- roofline of the dominant kernel
     stages = {"sbr": stage_mean[0], "dedup_sort": stage_mean[1], "image_method": stage_mean[2],
-              "visibility": stage_mean[3], "emission_records": stage_mean[4]}
-    kernels = dict(stages)
-    kernels.update({"fields_fwd": cal["fields_fwd_ms"], "cfr_fused": cal["cfr_fused_ms"],
-                    "fields_bwd": cal["fields_bwd_ms"]})
+              "visibility": stage_mean[3], "emission_records": stage_mean[4],
+              "sbr_kernel": stage_mean[6], "sbr_fp64_redo": stage_mean[7]}
+    # the dominant single kernel (the shoot-and-bounce kernel alone, not its stage)
+    kernels = {"sbr": stage_mean[6], "sbr_fp64_redo": stage_mean[7], "image_method": stage_mean[2],
+               "visibility": stage_mean[3], "fields_fwd": cal["fields_fwd_ms"], "cfr_fused": cal["cfr_fused_ms"],
+               "fields_bwd": cal["fields_bwd_ms"]}
     dominant = max(kernels, key=kernels.get)
     roofline = roofline_for(dominant, kernels[dominant], counters, cal, n_paths, sc, N, peaks, peak_src)
 
@@ -644,9 +646,21 @@ def time_indoor_calibration(rt, ctx, flush, args, plain=True):
         e0.record(stream)
         e0.synchronize()
         times.append(s0.elapsed_time(e0))
+    # the fused CFR kernel alone (tensor cores), for its roofline
+    kt = []
+    for _ in range(20):
+        flush.zero_()
+        s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        rt.cfr_power_mse_fused(ctx, p.rx_offsets, a, p.tau, fc, df, N, target, w, loss=loss, grad_a=ga)
+        e0.record(stream)
+        e0.synchronize()
+        kt.append(s0.elapsed_time(e0))
     res = {"workload": "indoor_diff", "n_rx": sc.n_rx, "n_sub": N, "n_paths": p.n_paths,
            "ms_per_step_median": float(np.median(times)), "graph": True, "replays": n,
-           "l2": "flushed: 256 MiB written between replays"}
+           "l2": "flushed: 256 MiB written between replays",
+           "cfr_fused_ms": float(np.median(kt)),
+           "roofline_cfr": roofline_cfr(float(np.median(kt)), p.n_paths, N)}
     if not plain:
         return res
     # the same step as plain PyTorch complex64 ops (eager, autograd), and how
@@ -853,14 +867,34 @@ def time_learned(rt, ctx, args, train_steps=100):
             "mlp_bwd_tflops": 2 * flops_fwd / (ms_bwd * 1e-3) / 1e12}
 
 
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the kernel's source file changed since the counters were taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ncu_counters.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, d["source"])
+    if not os.path.exists(src):
+        return None
+    with open(src, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != d["source_sha256"]:
+            return None
+    return d["dram_bytes_per_launch"] * d.get("scale_to_bench", 1.0)
+
+
 def roofline_for(name, ms, counters, cal, n_paths, sc, N, peaks, peak_src):
     hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
     if name == "sbr":
         flops = FLOPS_PER_NODE_VISIT * counters[0] + FLOPS_PER_TRI_TEST * counters[1]
         ach = flops / (ms * 1e-3) / 1e12
-        return {"kernel": "k_sbr (+k_sbr_redo)", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+        return {"kernel": "k_sbr", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": ncu_traffic("k_sbr"),
+                "kernel_ms": ms, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                 "algorithmic": f"{FLOPS_PER_NODE_VISIT} flops/node visit + {FLOPS_PER_TRI_TEST} flops/triangle test"}
     if name == "visibility":
         flops = FLOPS_PER_NODE_VISIT * counters[4] + FLOPS_PER_TRI_TEST * counters[5]
@@ -878,6 +912,20 @@ def roofline_for(name, ms, counters, cal, n_paths, sc, N, peaks, peak_src):
     # stage without a dedicated counter model: report time only against HBM with its bytes unknown
     return {"kernel": name, "bound": "alu", "achieved": None, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": None, "traffic": None, "ms": ms}
+
+
+def roofline_cfr(ms, n_paths, N):
+    """Fused CFR + loss + adjoint on the tensor cores: 16 N P algorithmic FP32
+    flops (8 per complex multiply-add, forward and adjoint), executed as three
+    TF32 products each (hi.hi + hi.lo + lo.hi); peak = the measured BF16 dense
+    peak x the nominal TF32 / BF16 ratio (1.1 / 2.25)."""
+    peaks, src = load_peaks()
+    tf32 = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]) * (1.1 / 2.25)
+    ach = 3 * 16.0 * N * n_paths / (ms * 1e-3) / 1e12
+    return {"kernel": "k_cfr_tc<8,2>", "bound": "tensor", "achieved": ach, "peak": tf32, "unit": "TFLOP/s",
+            "frac": ach / tf32, "traffic": ncu_traffic("k_cfr_tc"), "kernel_ms": ms,
+            "peak_source": f"{src} bf16 x 1.1/2.25 (TF32)",
+            "algorithmic": "3 x 16 N P TF32 flops (3xTF32 split of 8 N P complex MAC flops, forward and adjoint)"}
 
 
 def cpu_baseline(sc, N):

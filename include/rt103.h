@@ -79,7 +79,8 @@ rt_status rt_set_profiling(rt_ctx* ctx, int32_t flags);
 /* Reads the instrumentation of ctx (any pointer may be NULL):
  *   launches      number of kernels this context launched so far
  *   stage_ms[8]   last trace: SBR, dedup+sort, image method, visibility,
- *                 emission+records, total, 0, 0  (bit 0 set, else zeros)
+ *                 emission+records, total, then within SBR the shoot-and-bounce
+ *                 kernel alone and the FP64 re-trace (bit 0 set, else zeros)
  *   counters[8]   since the last rt_set_profiling: SBR node visits, SBR triangle
  *                 tests, SBR closest-hit queries, FP64 re-traced rays,
  *                 visibility node visits, visibility triangle tests, visibility

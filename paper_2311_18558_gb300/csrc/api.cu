@@ -129,7 +129,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_set_profiling(rt_
     if (!ctx) return RT_ERR_INVALID_ARG;
     if (flags & ~3) return rt_fail(ctx, RT_ERR_INVALID_ARG, "profiling flags are bits 0 and 1");
     if ((flags & 1) && !ctx->ev[0])
-        for (int k = 0; k < 6; ++k) RT_CK(ctx, cudaEventCreate(&ctx->ev[k]));
+        for (int k = 0; k < 8; ++k) RT_CK(ctx, cudaEventCreate(&ctx->ev[k]));
     if ((flags & 2) && !ctx->d_counters) RT_CK(ctx, cudaMalloc((void**)&ctx->d_counters, 8 * sizeof(unsigned long long)));
     if (ctx->d_counters) RT_CK(ctx, cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(unsigned long long), ctx->stream));
     for (int k = 0; k < 8; ++k) {
@@ -160,7 +160,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_profile_read(rt_c
 extern "C" __attribute__((visibility("default"))) rt_status rt_destroy(rt_ctx* ctx) {
     if (!ctx) return RT_ERR_INVALID_ARG;
     cudaStreamSynchronize(ctx->stream);
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < 8; ++k)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
     if (ctx->d_counters) cudaFree(ctx->d_counters);
     if (ctx->d_sched_order) cudaFree(ctx->d_sched_order);

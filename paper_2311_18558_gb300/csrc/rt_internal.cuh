@@ -35,7 +35,7 @@ struct rt_ctx {
     double stage_ms[8] = {0};
     unsigned long long* d_counters = nullptr;   // 8 device counters (bit 1)
     int64_t h_counters[8] = {0};                // host-side counts of the same slots
-    cudaEvent_t ev[6] = {};                     // trace stage events (bit 0)
+    cudaEvent_t ev[8] = {};                     // trace stage events (bit 0)
     // coherent processing order of the launch directions, per ray count (see trace.cu)
     int64_t sched_n = 0, sched_band = 0, sched_full = 0;
     int32_t* d_sched_order = nullptr;   // sched_band entries

@@ -1493,7 +1493,9 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
             if (ss != RT_OK) return ss;
         }
         int blocks = ctx->num_sms * ctx->tune_sbr_blocks_per_sm;
+        mark(ctx, 6);
         k_sbr<<<blocks, TRACE_THREADS, stack_bytes, st>>>(A, sc->d_tri_v); RT_COUNT(ctx);
+        mark(ctx, 7);
         RT_CK_LAUNCH(ctx);
         k_sbr_redo<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 2 * CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(
             A, sc->d_tri_n64);
@@ -1714,6 +1716,10 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         }
         cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
         ctx->stage_ms[5] = ms;
+        cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[7]);   // the SBR kernel alone
+        ctx->stage_ms[6] = ms;
+        cudaEventElapsedTime(&ms, ctx->ev[7], ctx->ev[1]);   // the FP64 re-trace
+        ctx->stage_ms[7] = ms;
     }
 #undef TCK
     *out = p;
@@ -2367,8 +2373,10 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
             if (ss != RT_OK) return fail(ss);
         }
         mark(ctx, 0);
+        mark(ctx, 6);
         k_sbr_batch<<<ctx->num_sms * ctx->tune_sbr_blocks_per_sm, TRACE_THREADS, stack_bytes, st>>>(A);
         RT_COUNT(ctx);
+        mark(ctx, 7);
         BCK(cudaGetLastError());
         k_sbr_redo_batch<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 2 * CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(A);
         RT_COUNT(ctx);
@@ -2629,6 +2637,10 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         }
         cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
         ctx->stage_ms[5] = ms;
+        cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[7]);   // the SBR kernel alone
+        ctx->stage_ms[6] = ms;
+        cudaEventElapsedTime(&ms, ctx->ev[7], ctx->ev[1]);   // the FP64 re-trace
+        ctx->stage_ms[7] = ms;
     }
 #undef BCK
     *out = p;
