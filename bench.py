@@ -353,6 +353,9 @@ def run_ours(args):
     # ---------------- indoor calibration step (the second metric), graph-captured
     calib_indoor = time_indoor_calibration(rt, ctx, flush, args)
 
+    # ---------------- eval_fields / adjoint at an HBM-bound size
+    fields_hbm = time_fields_hbm(rt, ctx, scene, sc, flush)
+
     # ---------------- learned form (neural materials) vs the plain per-object form
     learned = time_learned(rt, ctx, args)
 
@@ -384,6 +387,7 @@ def run_ours(args):
             "stage_ms": {k: round(v, 4) for k, v in stages.items()},
             "calibration_ms": {k: round(v, 4) for k, v in cal.items()},
             "calibration_indoor": calib_indoor,
+            "fields_hbm": fields_hbm,
             "learned": learned,
             "batch": batch,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
@@ -678,6 +682,54 @@ def time_indoor_calibration(rt, ctx, flush, args, plain=True):
     return res
 
 
+def time_fields_hbm(rt, ctx, scene, sc, flush, reps=10, copies=1000):
+    """eval_fields and its adjoint at a size where HBM binds: the street-canyon
+    path set tiled `copies` times (each copy on its own receivers) through
+    rt_paths_import.  Algorithmic bytes per path of depth q: forward 4 (depth) +
+    4 (L) + 16 (D_1) + q (4 tri + 4 cos + 16 D) + 8 (a out); the adjoint reads the
+    same records plus 8 (dL/da).  The material table is L2-resident."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rx = torch.tensor(sc.rx, dtype=torch.float64, device=dev)
+    p0 = rt.trace_paths(ctx, scene, sc.tx, rx, sc.n_rays, sc.max_depth)
+    ex = p0.export()
+    P0, R0 = p0.n_paths, sc.n_rx
+    reps_rx = (ex["rx"].long()[None, :] + R0 * torch.arange(copies, device=dev)[:, None]).reshape(-1).int()
+    p = rt.import_paths(ctx, scene, reps_rx, ex["depth"].repeat(copies), ex["seq"].repeat(copies, 1),
+                        ex["pts"].repeat(copies, 1, 1), R0 * copies)
+    del reps_rx
+    q = ex["depth"].double()
+    fwd_bytes = float(copies * (4 + 4 + 16 + 24 * q + 8).sum().item())
+    bwd_bytes = fwd_bytes + 8.0 * copies * P0
+    eps = torch.tensor(sc.eps_r, device=dev)
+    sig = torch.tensor(sc.sigma, device=dev)
+    a = rt.eval_fields(ctx, p, eps, sig, sc.freq_hz)
+    ga = (a * 0.5).contiguous()
+    ge, gs, gg = torch.zeros_like(eps), torch.zeros_like(sig), torch.zeros(2, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            fn()
+            e0.record(stream)
+            e0.synchronize()
+            out.append(s0.elapsed_time(e0))
+        return float(np.median(out))
+    t_f = timed(lambda: rt.eval_fields(ctx, p, eps, sig, sc.freq_hz, out=a))
+    t_b = timed(lambda: rt.eval_fields_backward(ctx, p, eps, sig, sc.freq_hz, ga, ge, gs, gg))
+    peaks, src = load_peaks()
+    hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+    gf, gb = fwd_bytes / (t_f * 1e-3) / 1e9, bwd_bytes / (t_b * 1e-3) / 1e9
+    return {"workload": f"street_canyon paths x {copies} (rt_paths_import)", "n_paths": p.n_paths,
+            "fields_fwd": {"ms": t_f, "bytes": fwd_bytes, "achieved_gbs": gf, "peak_gbs": hbm, "frac": gf / hbm},
+            "fields_bwd": {"ms": t_b, "bytes": bwd_bytes, "achieved_gbs": gb, "peak_gbs": hbm, "frac": gb / hbm},
+            "peak_source": src}
+
+
 def time_batch(rt, ctx, args, reps=3):
     """16 procedural cities (1k-50k triangles, 65,536 receivers split unevenly,
     10^7 rays per scene, depth 4): rt_trace_batch against a loop of per-scene
@@ -951,7 +1003,8 @@ def run_case(args):
     """One workload alone, for profiler captures (prints a short line, not the
     benchmark line): street_step = the street-canyon step (trace + fields +
     fused CFR loss + adjoints); indoor_calibration = the indoor calibration step
-    (graph replays); city_batch = one batched trace of the 16 cities."""
+    (graph replays); fields_hbm = eval_fields and its adjoint on the tiled
+    street-canyon paths; city_batch = one batched trace of the 16 cities."""
     import torch
 
     import paper_2311_18558_gb300 as rt
@@ -981,6 +1034,10 @@ def run_case(args):
     elif args.case == "indoor_calibration":
         args.steps = max(args.steps, 1)
         out.update(time_indoor_calibration(rt, ctx, flush, args, plain=False))
+    elif args.case == "fields_hbm":
+        sc = scenegen.street_canyon()
+        scene = rt.Scene.from_synthetic(ctx, sc)
+        out.update(time_fields_hbm(rt, ctx, scene, sc, flush, reps=max(args.steps, 1)))
     elif args.case == "city_batch":
         cities = scenegen.city_batch()
         scenes = [rt.Scene.from_synthetic(ctx, c) for c in cities]
@@ -1002,7 +1059,7 @@ def main():
     ap.add_argument("--n-sub", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 16-city batched measurement")
-    ap.add_argument("--case", choices=["street_step", "indoor_calibration", "city_batch"], default=None,
+    ap.add_argument("--case", choices=["street_step", "indoor_calibration", "fields_hbm", "city_batch"], default=None,
                     help="run one workload alone (for profiler captures) instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -19,6 +19,8 @@
 
 namespace {
 
+constexpr int MAT_PEC = 1 << 30;   // flag in the per-bounce material word of the records
+
 struct D3 {
     double x, y, z;
 };
@@ -46,8 +48,9 @@ __device__ __forceinline__ void sph_basis(D3 k, D3* th, D3* ph) {
 }
 
 __global__ void k_records(int64_t P, int D, const double* __restrict__ pts, const int32_t* __restrict__ depth,
-                          const int32_t* __restrict__ tri, const double* __restrict__ tri_n64, double* tau,
-                          float* len, float* cosv, float4* Dm) {
+                          const int32_t* __restrict__ tri, const double* __restrict__ tri_n64,
+                          const int32_t* __restrict__ tri_material, const uint8_t* __restrict__ is_pec, double* tau,
+                          float* len, int2* mc, float4* Dm) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         const int q = depth[i];
         const double* pp = pts + (int64_t)i * (D + 2) * 3;
@@ -83,7 +86,8 @@ __global__ void k_records(int64_t P, int D, const double* __restrict__ pts, cons
             D3 in_q = crossd(e_perp, k[j]);
             Dm[(int64_t)(j - 1) * P + i] = make_float4((float)dotd(e_perp, out_p), (float)dotd(e_perp, out_q),
                                                        (float)dotd(in_q, out_p), (float)dotd(in_q, out_q));
-            cosv[(int64_t)(j - 1) * P + i] = (float)cos_i;
+            const int mt = tri_material[t];
+            mc[(int64_t)(j - 1) * P + i] = make_int2(mt | (is_pec[mt] ? MAT_PEC : 0), __float_as_int((float)cos_i));
             out_p = e_perp;
             out_q = crossd(e_perp, k[j + 1]);
         }
@@ -100,48 +104,55 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
-__device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
-    float inv = 1.0f / (b.x * b.x + b.y * b.y);
-    return make_float2((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
-}
 // Principal square root from |z|: sqrt(z) = t + j y/(2t) with t = sqrt((|z| + x)/2)
 // for x >= 0, and the mirrored form for x < 0 (no cancellation either way).
+// |z| of eta - sin^2 is O(1..1e3), so sqrt(x^2 + y^2) needs no scaling.
 __device__ __forceinline__ float2 csqrt(float2 z) {
-    float r = hypotf(z.x, z.y);
+    const float r = sqrtf(z.x * z.x + z.y * z.y);
     if (z.x >= 0.0f) {
-        float t = sqrtf(0.5f * (r + z.x));
-        return make_float2(t, t > 0.0f ? z.y / (2.0f * t) : 0.0f);
+        const float t = sqrtf(0.5f * (r + z.x));
+        return make_float2(t, t > 0.0f ? z.y * __frcp_rn(2.0f * t) : 0.0f);
     }
-    float t = sqrtf(0.5f * (r - z.x));
-    return make_float2(fabsf(z.y) / (2.0f * t), copysignf(t, z.y));
+    const float t = sqrtf(0.5f * (r - z.x));
+    return make_float2(fabsf(z.y) * __frcp_rn(2.0f * t), copysignf(t, z.y));
 }
 
-// Fresnel coefficients (Eq. fresnel-1/2) and their derivatives w.r.t. eta:
-//   d r_perp / d eta = -c / (s (c + s)^2),  d r_par / d eta = c (eta - 2 sin^2) / (s (eta c + s)^2),
-// s = sqrt(eta - sin^2 theta), c = cos theta.
+// 1 / z = conj(z) / |z|^2 with one correctly rounded reciprocal (|z|^2 of the
+// Fresnel denominators stays far from FP32 over- and underflow)
+__device__ __forceinline__ float2 crcp(float2 z) {
+    const float inv = __frcp_rn(z.x * z.x + z.y * z.y);
+    return make_float2(z.x * inv, -z.y * inv);
+}
+
+// Fresnel coefficients (Eq. fresnel-1/2) and their derivatives w.r.t. eta, with
+// s = sqrt(eta - sin^2 theta), c = cos theta, and p = 1 / (c + s),
+// l = 1 / (eta c + s), 1 / s shared:
+//   r_perp = (c - s) p,  r_par = (eta c - s) l,
+//   d r_perp / d eta = -c p^2 / s,  d r_par / d eta = c (eta - 2 sin^2) l^2 / s.
 template <bool GRAD>
 __device__ __forceinline__ void fresnel(float2 eta, float c, float2& rp, float2& rl, float2& drp, float2& drl) {
-    float s2 = fmaxf(0.0f, 1.0f - c * c);
-    float2 s = csqrt(make_float2(eta.x - s2, eta.y));
-    float2 cps = make_float2(c + s.x, s.y);
-    float2 cms = make_float2(c - s.x, -s.y);
-    rp = cdiv(cms, cps);
-    float2 ec = cscale(c, eta);
-    float2 ecs = cadd(ec, s);
-    rl = cdiv(make_float2(ec.x - s.x, ec.y - s.y), ecs);
+    const float s2 = fmaxf(0.0f, 1.0f - c * c);
+    const float2 s = csqrt(make_float2(eta.x - s2, eta.y));
+    const float2 ip = crcp(make_float2(c + s.x, s.y));
+    rp = cmul(make_float2(c - s.x, -s.y), ip);
+    const float2 ec = cscale(c, eta);
+    const float2 il = crcp(cadd(ec, s));
+    rl = cmul(make_float2(ec.x - s.x, ec.y - s.y), il);
     if (GRAD) {
-        drp = cdiv(make_float2(-c, 0.0f), cmul(s, cmul(cps, cps)));
-        drl = cdiv(cscale(c, make_float2(eta.x - 2.0f * s2, eta.y)), cmul(s, cmul(ecs, ecs)));
+        const float2 is = crcp(s);
+        drp = cscale(-c, cmul(cmul(ip, ip), is));
+        drl = cmul(cscale(c, make_float2(eta.x - 2.0f * s2, eta.y)), cmul(cmul(il, il), is));
     }
 }
 
 struct FieldArgs {
     int64_t P;
     int D;
+    int n_mat;                 // entries of eps / sig (materials, or triangles when per_tri)
     const int32_t* depth;
     const int32_t* tri;
     const float* len;
-    const float* cosv;
+    const int2* mc;
     const float4* Dm;
     const double* tau;
     const int32_t* tri_material;
@@ -153,34 +164,82 @@ struct FieldArgs {
     float amp;         // lambda / (4 pi) sqrt(g_T g_R)
 };
 
-__global__ void __launch_bounds__(256) k_fields_fwd(FieldArgs A, float2* __restrict__ a_out, double* __restrict__ tau_out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.P; i += (int64_t)gridDim.x * blockDim.x) {
-        const int q = __ldg(A.depth + i);
-        // slot s of the record holds D_{s+1}; v = D_1 C_T with C_T = [1, 0]
-        float4 d = __ldg(A.Dm + i);
-        float2 v0 = make_float2(d.x, 0.0f), v1 = make_float2(d.z, 0.0f);
+constexpr int FWD_NP = 2;     // paths per thread and iteration (independent loads in flight)
+constexpr int ETA_SMEM = 64;  // per-material eta table in shared memory up to this many materials
+
+// eta = eps_r - j sigma / (eps0 omega) of material (or triangle) m
+__device__ __forceinline__ float2 eta_of(const FieldArgs& A, const float2* s_eta, int m) {
+    if (s_eta) return s_eta[m];
+    return make_float2(__ldg(A.eps + m), -__ldg(A.sig + m) * A.inv_eps0w);
+}
+
+// FWD_NP paths per thread in lockstep, so that their record loads (depth, L,
+// material and cos, basis changes) are in flight together; the material gather
+// of the step is a shared-memory table (or an L2-resident per-triangle array).
+__global__ void __launch_bounds__(256, 6) k_fields_fwd(FieldArgs A, float2* __restrict__ a_out, double* __restrict__ tau_out) {
+    __shared__ float2 s_tab[ETA_SMEM];
+    const bool smem_eta = !A.per_tri && A.n_mat <= ETA_SMEM;
+    if (smem_eta) {
+        for (int m = threadIdx.x; m < A.n_mat; m += blockDim.x)
+            s_tab[m] = make_float2(A.eps[m], -A.sig[m] * A.inv_eps0w);
+        __syncthreads();
+    }
+    const float2* s_eta = smem_eta ? s_tab : nullptr;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < A.P; i0 += FWD_NP * stride) {
+        int64_t idx[FWD_NP];
+        int q[FWD_NP];
+        float len[FWD_NP];
+        float2 v0[FWD_NP], v1[FWD_NP];
+#pragma unroll
+        for (int k = 0; k < FWD_NP; ++k) {
+            idx[k] = i0 + k * stride;
+            const bool ok = idx[k] < A.P;
+            q[k] = ok ? __ldg(A.depth + idx[k]) : -1;
+            len[k] = ok ? __ldg(A.len + idx[k]) : 1.0f;
+            // slot s of the record holds D_{s+1}; v = D_1 C_T with C_T = [1, 0]
+            const float4 d = ok ? __ldg(A.Dm + idx[k]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            v0[k] = make_float2(d.x, 0.0f);
+            v1[k] = make_float2(d.z, 0.0f);
+        }
 #pragma unroll
         for (int j = 0; j < RT_MAX_DEPTH; ++j) {
-            if (j < q) {
-                int t = __ldg(A.tri + (int64_t)j * A.P + i);
-                int mat = __ldg(A.tri_material + t);
-                int m = A.per_tri ? t : mat;
-                float2 rp, rl, unused;
-                if (__ldg(A.is_pec + mat)) {
-                    rp = make_float2(-1.0f, 0.0f);
-                    rl = make_float2(1.0f, 0.0f);
-                } else {
-                    float2 eta = make_float2(__ldg(A.eps + m), -__ldg(A.sig + m) * A.inv_eps0w);
-                    fresnel<false>(eta, __ldg(A.cosv + (int64_t)j * A.P + i), rp, rl, unused, unused);
+            int2 w[FWD_NP];
+            int t[FWD_NP];
+            float4 e[FWD_NP];
+#pragma unroll
+            for (int k = 0; k < FWD_NP; ++k) {
+                if (j < q[k]) {
+                    const int64_t o = (int64_t)j * A.P + idx[k];
+                    w[k] = __ldg(A.mc + o);
+                    t[k] = A.per_tri ? __ldg(A.tri + o) : 0;
+                    e[k] = __ldg(A.Dm + o + A.P);
                 }
-                float2 g0 = cmul(rp, v0), g1 = cmul(rl, v1);
-                float4 e = __ldg(A.Dm + (int64_t)(j + 1) * A.P + i);
-                v0 = cadd(cscale(e.x, g0), cscale(e.y, g1));
-                v1 = cadd(cscale(e.z, g0), cscale(e.w, g1));
+            }
+#pragma unroll
+            for (int k = 0; k < FWD_NP; ++k) {
+                if (j < q[k]) {
+                    float2 rp, rl, unused;
+                    if (w[k].x & MAT_PEC) {
+                        rp = make_float2(-1.0f, 0.0f);
+                        rl = make_float2(1.0f, 0.0f);
+                    } else {
+                        const int m = A.per_tri ? t[k] : w[k].x;
+                        fresnel<false>(eta_of(A, s_eta, m), __int_as_float(w[k].y), rp, rl, unused, unused);
+                    }
+                    const float2 g0 = cmul(rp, v0[k]), g1 = cmul(rl, v1[k]);
+                    v0[k] = cadd(cscale(e[k].x, g0), cscale(e[k].y, g1));
+                    v1[k] = cadd(cscale(e[k].z, g0), cscale(e[k].w, g1));
+                }
             }
         }
-        a_out[i] = cscale(A.amp / __ldg(A.len + i), v0);
-        if (tau_out) tau_out[i] = A.tau[i];
+#pragma unroll
+        for (int k = 0; k < FWD_NP; ++k) {
+            if (q[k] >= 0) {
+                a_out[idx[k]] = cscale(A.amp / len[k], v0[k]);
+                if (tau_out) tau_out[idx[k]] = A.tau[idx[k]];
+            }
+        }
     }
 }
 
@@ -189,85 +248,97 @@ __global__ void __launch_bounds__(256) k_fields_fwd(FieldArgs A, float2* __restr
 // of hot addresses), MAXM > 0 accumulates in shared memory, otherwise global
 // atomics (per-triangle materials: scattered, little contention).
 template <int MAXM, int REGM>
-__global__ void __launch_bounds__(256) k_fields_bwd(FieldArgs A, const float2* __restrict__ ga, float* __restrict__ geps,
-                                                    float* __restrict__ gsig, float* __restrict__ ggain, float inv_gtx,
-                                                    float inv_grx, int n_mat) {
+__global__ void __launch_bounds__(256, 4) k_fields_bwd(FieldArgs A, const float2* __restrict__ ga,
+                                                       float* __restrict__ geps, float* __restrict__ gsig,
+                                                       float* __restrict__ ggain, float inv_gtx, float inv_grx,
+                                                       int n_mat) {
     __shared__ float s_eps[MAXM > 0 ? MAXM : 1], s_sig[MAXM > 0 ? MAXM : 1], s_gain[2];
+    __shared__ float2 s_tab[ETA_SMEM];
     if (MAXM > 0)
         for (int m = threadIdx.x; m < n_mat; m += blockDim.x) s_eps[m] = s_sig[m] = 0.0f;
     if (threadIdx.x < 2) s_gain[threadIdx.x] = 0.0f;
+    const bool smem_eta = !A.per_tri && A.n_mat <= ETA_SMEM;
+    if (smem_eta)
+        for (int m = threadIdx.x; m < A.n_mat; m += blockDim.x)
+            s_tab[m] = make_float2(A.eps[m], -A.sig[m] * A.inv_eps0w);
     __syncthreads();
-    float r_eps[REGM > 0 ? REGM : 1], r_sig[REGM > 0 ? REGM : 1];
-#pragma unroll
-    for (int m = 0; m < (REGM > 0 ? REGM : 1); ++m) r_eps[m] = r_sig[m] = 0.0f;
+    const float2* s_eta = smem_eta ? s_tab : nullptr;
+    // REGM materials: per-thread accumulator columns in shared memory
+    // (s_col[m][tid]), summed over the block at the end
+    __shared__ float s_col[REGM > 0 ? 2 * REGM * 256 : 1];
+    if (REGM > 0)
+        for (int k = threadIdx.x; k < 2 * REGM * 256; k += blockDim.x) s_col[k] = 0.0f;
+    __syncthreads();
     float gain_acc = 0.0f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.P; i += (int64_t)gridDim.x * blockDim.x) {
         const int q = __ldg(A.depth + i);
         const float scale = A.amp / __ldg(A.len + i);
-        float4 d = __ldg(A.Dm + i);
+        const float4 d = __ldg(A.Dm + i);
         float2 v0 = make_float2(d.x, 0.0f), v1 = make_float2(d.z, 0.0f);
-        float2 in0[RT_MAX_DEPTH], in1[RT_MAX_DEPTH], rp[RT_MAX_DEPTH], rl[RT_MAX_DEPTH], drp[RT_MAX_DEPTH],
-            drl[RT_MAX_DEPTH];
-        int mid[RT_MAX_DEPTH];
-        bool pec[RT_MAX_DEPTH];
+        // forward walk: keep only the field entering every bounce
+        float2 in0[RT_MAX_DEPTH], in1[RT_MAX_DEPTH];
 #pragma unroll
         for (int j = 0; j < RT_MAX_DEPTH; ++j) {
             if (j < q) {
-                int t = __ldg(A.tri + (int64_t)j * A.P + i);
-                int mat = __ldg(A.tri_material + t);
-                int m = A.per_tri ? t : mat;
-                mid[j] = m;
-                pec[j] = __ldg(A.is_pec + mat) != 0;
-                if (pec[j]) {
-                    rp[j] = make_float2(-1.0f, 0.0f);
-                    rl[j] = make_float2(1.0f, 0.0f);
-                    drp[j] = drl[j] = make_float2(0.0f, 0.0f);
+                const int64_t o = (int64_t)j * A.P + i;
+                const int2 w = __ldg(A.mc + o);
+                float2 rp, rl, unused;
+                if (w.x & MAT_PEC) {
+                    rp = make_float2(-1.0f, 0.0f);
+                    rl = make_float2(1.0f, 0.0f);
                 } else {
-                    float2 eta = make_float2(__ldg(A.eps + m), -__ldg(A.sig + m) * A.inv_eps0w);
-                    fresnel<true>(eta, __ldg(A.cosv + (int64_t)j * A.P + i), rp[j], rl[j], drp[j], drl[j]);
+                    const int m = A.per_tri ? __ldg(A.tri + o) : w.x;
+                    fresnel<false>(eta_of(A, s_eta, m), __int_as_float(w.y), rp, rl, unused, unused);
                 }
                 in0[j] = v0;
                 in1[j] = v1;
-                float2 g0 = cmul(rp[j], v0), g1 = cmul(rl[j], v1);
-                float4 e = __ldg(A.Dm + (int64_t)(j + 1) * A.P + i);
+                const float2 g0 = cmul(rp, v0), g1 = cmul(rl, v1);
+                const float4 e = __ldg(A.Dm + o + A.P);
                 v0 = cadd(cscale(e.x, g0), cscale(e.y, g1));
                 v1 = cadd(cscale(e.z, g0), cscale(e.w, g1));
             }
         }
-        float4 last = __ldg(A.Dm + (int64_t)q * A.P + i);   // D_{q+1}
-        float2 a = cscale(scale, v0);
-        float2 g = __ldg(ga + i);
+        const float4 last = __ldg(A.Dm + (int64_t)q * A.P + i);   // D_{q+1}
+        const float2 a = cscale(scale, v0);
+        const float2 g = __ldg(ga + i);
         // Re(conj(g) a) / (2 g_T) and / (2 g_R) share Re(conj(g) a)
         gain_acc += g.x * a.x + g.y * a.y;
-        // adjoint walk: l = scale * (row 0 of D_{q+1}) . Gamma_q D_q ... ; the row
-        // vector before bounce j is l_j, da/dr_perp_j = l_j[0] in0_j, da/dr_par_j = l_j[1] in1_j
+        // reverse walk: l = scale * (row 0 of D_{q+1}) . Gamma_q D_q ... is the row
+        // vector after bounce j; da/dr_perp_j = l[0] in0_j, da/dr_par_j = l[1] in1_j.
+        // The bounce's record is read again (cache hit) and its Fresnel
+        // coefficients are recomputed with their derivatives.
         float2 l0 = make_float2(scale * last.x, 0.0f), l1 = make_float2(scale * last.y, 0.0f);
 #pragma unroll
         for (int j = RT_MAX_DEPTH - 1; j >= 0; --j) {
             if (j < q) {
-                if (!pec[j]) {
-                    float2 da = cadd(cmul(cmul(l0, in0[j]), drp[j]), cmul(cmul(l1, in1[j]), drl[j]));
+                const int64_t o = (int64_t)j * A.P + i;
+                const int2 w = __ldg(A.mc + o);
+                float2 rp, rl;
+                if (w.x & MAT_PEC) {
+                    rp = make_float2(-1.0f, 0.0f);
+                    rl = make_float2(1.0f, 0.0f);
+                } else {
+                    const int m = A.per_tri ? __ldg(A.tri + o) : w.x;
+                    float2 drp, drl;
+                    fresnel<true>(eta_of(A, s_eta, m), __int_as_float(w.y), rp, rl, drp, drl);
+                    const float2 da = cadd(cmul(cmul(l0, in0[j]), drp), cmul(cmul(l1, in1[j]), drl));
                     // Re(conj(g) da) and Im(conj(g) da)
-                    float re = g.x * da.x + g.y * da.y;
-                    float im = g.x * da.y - g.y * da.x;
-                    float de = re, ds = im * A.inv_eps0w;   // da/dsigma = -j/(eps0 w) da/deta
+                    const float re = g.x * da.x + g.y * da.y;
+                    const float im = g.x * da.y - g.y * da.x;
+                    const float de = re, ds = im * A.inv_eps0w;   // da/dsigma = -j/(eps0 w) da/deta
                     if (REGM > 0) {
-#pragma unroll
-                        for (int m = 0; m < (REGM > 0 ? REGM : 1); ++m)
-                            if (m == mid[j]) {
-                                r_eps[m] += de;
-                                r_sig[m] += ds;
-                            }
+                        s_col[m * 256 + threadIdx.x] += de;
+                        s_col[(REGM + m) * 256 + threadIdx.x] += ds;
                     } else if (MAXM > 0) {
-                        atomicAdd(&s_eps[mid[j]], de);
-                        atomicAdd(&s_sig[mid[j]], ds);
+                        atomicAdd(&s_eps[m], de);
+                        atomicAdd(&s_sig[m], ds);
                     } else {
-                        if (geps) atomicAdd(geps + mid[j], de);
-                        if (gsig) atomicAdd(gsig + mid[j], ds);
+                        if (geps) atomicAdd(geps + m, de);
+                        if (gsig) atomicAdd(gsig + m, ds);
                     }
                 }
-                float2 h0 = cmul(l0, rp[j]), h1 = cmul(l1, rl[j]);
-                float4 e = j == 0 ? d : __ldg(A.Dm + (int64_t)j * A.P + i);
+                const float2 h0 = cmul(l0, rp), h1 = cmul(l1, rl);
+                const float4 e = j == 0 ? d : __ldg(A.Dm + o);
                 l0 = cadd(cscale(e.x, h0), cscale(e.z, h1));
                 l1 = cadd(cscale(e.y, h0), cscale(e.w, h1));
             }
@@ -276,16 +347,17 @@ __global__ void __launch_bounds__(256) k_fields_bwd(FieldArgs A, const float2* _
     for (int o = 16; o > 0; o >>= 1) gain_acc += __shfl_down_sync(0xffffffffu, gain_acc, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(&s_gain[0], gain_acc);
     if (REGM > 0) {
-#pragma unroll
-        for (int m = 0; m < (REGM > 0 ? REGM : 1); ++m) {
-            float e = r_eps[m], g = r_sig[m];
-            for (int o = 16; o > 0; o >>= 1) {
-                e += __shfl_down_sync(0xffffffffu, e, o);
-                g += __shfl_down_sync(0xffffffffu, g, o);
-            }
-            if ((threadIdx.x & 31) == 0 && m < n_mat) {
-                atomicAdd(&s_eps[m], e);
-                atomicAdd(&s_sig[m], g);
+        __syncthreads();
+        // one warp per (material, eps|sigma) column sum
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int col = warp; col < 2 * REGM; col += blockDim.x >> 5) {
+            float v = 0.0f;
+            for (int k = lane; k < 256; k += 32) v += s_col[col * 256 + k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            const int m = col % REGM;
+            if (lane == 0 && m < n_mat) {
+                if (col < REGM) atomicAdd(&s_eps[m], v);
+                else atomicAdd(&s_sig[m], v);
             }
         }
     }
@@ -309,8 +381,10 @@ FieldArgs make_args(const rt_paths* p, const float* eps, const float* sig, int p
     A.D = p->D;
     A.depth = p->d_depth;
     A.tri = p->d_tri;
+
+    A.n_mat = per_tri ? p->scene->n_tris : p->scene->n_materials;
     A.len = p->d_len;
-    A.cosv = p->d_cos;
+    A.mc = p->d_mc;
     A.Dm = p->d_Dm;
     A.tau = p->d_tau;
     A.tri_material = p->scene->d_tri_material;
@@ -338,11 +412,12 @@ rt_status rt_launch_paths_records(rt_ctx* ctx, rt_paths* p) {
     const int64_t Pa = p->P > 0 ? p->P : 1;
     RT_CK(ctx, cudaMallocAsync((void**)&p->d_tau, Pa * 8, st));
     RT_CK(ctx, cudaMallocAsync((void**)&p->d_len, Pa * 4, st));
-    RT_CK(ctx, cudaMallocAsync((void**)&p->d_cos, Pa * p->D * 4, st));
+    RT_CK(ctx, cudaMallocAsync((void**)&p->d_mc, Pa * p->D * 8, st));
     RT_CK(ctx, cudaMallocAsync((void**)&p->d_Dm, Pa * (p->D + 1) * 16, st));
     if (p->P == 0) return RT_OK;
     k_records<<<grid_for(ctx, p->P, 128, 16), 128, 0, st>>>(p->P, p->D, p->d_pts, p->d_depth, p->d_tri,
-                                                           p->scene->d_tri_n64, p->d_tau, p->d_len, p->d_cos,
+                                                           p->scene->d_tri_n64, p->scene->d_tri_material,
+                                                           p->scene->d_is_pec, p->d_tau, p->d_len, p->d_mc,
                                                            p->d_Dm); RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;
@@ -352,7 +427,7 @@ rt_status rt_launch_fields_fwd(rt_ctx* ctx, const rt_paths* p, const float* eps,
                                double freq, float gtx, float grx, float2* a, double* tau) {
     if (p->P == 0) return RT_OK;
     FieldArgs A = make_args(p, eps, sig, per_tri, freq, gtx, grx);
-    k_fields_fwd<<<grid_for(ctx, p->P, 256, 8), 256, 0, ctx->stream>>>(A, a, tau); RT_COUNT(ctx);
+    k_fields_fwd<<<grid_for(ctx, p->P, 256, 6), 256, 0, ctx->stream>>>(A, a, tau); RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;
 }

@@ -94,7 +94,8 @@ struct rt_paths {
     int32_t* d_tri = nullptr;          // D x P (slot-major), -1 padded
     double* d_tau = nullptr;           // P
     float* d_len = nullptr;            // P
-    float* d_cos = nullptr;            // D x P, cos(theta_i) of bounce j
+    int2* d_mc = nullptr;              // D x P per bounce j: .x material (bit 30 set for a PEC
+                                       // material), .y the bits of cos(theta_i) as float
     float4* d_Dm = nullptr;            // (D + 1) x P basis changes D_1 .. D_{q+1} (row major 2x2)
     double* d_pts = nullptr;           // P x (D + 2) x 3
     uint64_t* d_cand = nullptr;        // K packed candidate keys
