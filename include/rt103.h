@@ -253,6 +253,43 @@ rt_status rt_cfr_power_mse_fused(rt_ctx* ctx, const int64_t* rx_offsets_dev, int
  * out sets RT_ERR_TIMEOUT in the status word. */
 rt_status rt_set_cfr_tensor_cores(rt_ctx* ctx, int32_t enable);
 
+/* ------------------------------------------------------------------ CIR, loss and metrics */
+
+/* CIR by N-point IDFT (Sec. II-A): h[r, l + N/2] = N^-1/2 sum_n H[r, n + N/2]
+ * exp(+j 2 pi n l / N), n, l = -N/2 .. N/2-1.
+ *   H_dev, h_dev  n_rx x N complex64 (distinct buffers);  N a power of two in [2, 4096] */
+rt_status rt_cir(rt_ctx* ctx, const void* H_dev, int32_t n_rx, int32_t n_sub, void* h_dev);
+/* Per receiver, from its CFR: total channel gain P = sum_l |h[l]|^2 (Eq. channel_gain)
+ * and RMS delay spread tau_RMS [s] (Eq. delay_spread, W = N delta_f); tau_RMS = 0
+ * where P = 0.  Either output may be NULL. */
+rt_status rt_cir_stats(rt_ctx* ctx, const void* H_dev, int32_t n_rx, int32_t n_sub, double delta_f_hz,
+                       float* P_dev, float* tau_rms_dev);
+/* Power scale of the measurements (Eq. alpha_hat, scaling_param): alpha^ =
+ * sum P_meas P_pred / sum P_meas^2 over the n entries, then
+ * alpha <- decay alpha + (1 - decay) alpha^ (alpha <- alpha^ on the first call).
+ *   state_dev  2 floats {alpha, initialised}, device, updated in place; set to
+ *              {0, 0} before the first call.  decay in [0, 1). */
+rt_status rt_power_scale_ema(rt_ctx* ctx, const float* P_meas_dev, const float* P_pred_dev, int32_t n,
+                             float decay, float* state_dev);
+/* The paper's loss (Eq. loss, Eq. smape) averaged over the batch:
+ *   L = 1/n_rx sum_r [ SMAPE(tau_meas_r, tau^_r) + SMAPE(alpha P_meas_r, P^_r) ],
+ * SMAPE(x, y) = |x - y| / (x + y) (0 for x = y = 0), with P^, tau^ the statistics
+ * of rt_cir_stats for H and alpha = alpha_state_dev[0] (1 if NULL; no gradient).
+ *   loss_dev    one float (overwritten)
+ *   grad_H_dev  n_rx x N complex64, dL/dRe H + j dL/dIm H (overwritten); a CIR
+ *               with P^ = 0 or tau^ = 0 passes no gradient through its delay term
+ *   P_pred_dev, tau_pred_dev  per-receiver P^ and tau^ (may be NULL) */
+rt_status rt_delay_spread_power_loss(rt_ctx* ctx, const void* H_dev, int32_t n_rx, int32_t n_sub,
+                                     double delta_f_hz, const float* P_meas_dev, const float* tau_meas_dev,
+                                     const float* alpha_state_dev, float* loss_dev, void* grad_H_dev,
+                                     float* P_pred_dev, float* tau_pred_dev);
+/* Evaluation metrics per receiver (Sec. IV-C): ALE = |10 log10(alpha P_meas) -
+ * 10 log10 P_pred| [dB] and RAE = |tau_meas - tau_pred| / tau_meas; alpha from
+ * alpha_state_dev[0] (1 if NULL).  Either output may be NULL. */
+rt_status rt_cir_metrics(rt_ctx* ctx, const float* P_meas_dev, const float* tau_meas_dev,
+                         const float* P_pred_dev, const float* tau_pred_dev, int32_t n,
+                         const float* alpha_state_dev, float* ale_dev, float* rae_dev);
+
 /* ------------------------------------------------------------------ neural materials */
 
 /* Neural materials, Sec. III-D: an MLP evaluated at every triangle's centroid c.

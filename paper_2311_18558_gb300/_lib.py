@@ -43,6 +43,11 @@ SIGNATURES = {
     "rt_paths_batch_info": (I32, [P, ctypes.POINTER(I32), P, P]),
     "rt_set_tuning": (I32, [P, I32, I32, I32]),
     "rt_set_cfr_tensor_cores": (I32, [P, I32]),
+    "rt_cir": (I32, [P, P, I32, I32, P]),
+    "rt_cir_stats": (I32, [P, P, I32, I32, F64, P, P]),
+    "rt_power_scale_ema": (I32, [P, P, P, I32, F32, P]),
+    "rt_delay_spread_power_loss": (I32, [P, P, I32, I32, F64, P, P, P, P, P, P, P]),
+    "rt_cir_metrics": (I32, [P, P, P, P, P, I32, P, P, P]),
     "rt_autotune_trace": (I32, [P, P, P, P, I32, I64, I32, P, ctypes.POINTER(F64)]),
     "rt_eval_fields": (I32, [P, P, P, P, I32, F64, F32, F32, P, P]),
     "rt_eval_fields_backward": (I32, [P, P, P, P, I32, F64, F32, F32, P, P, P, P]),

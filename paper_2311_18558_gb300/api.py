@@ -267,6 +267,65 @@ def cfr_power_mse_fused(ctx: Context, rx_offsets, a, tau, f_center_hz, delta_f_h
     return loss, grad_a, H
 
 
+# ----------------------------------------------------------------------------- CIR, loss and metrics
+
+def cir(ctx: Context, H: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """CIR by N-point IDFT of every row of H (rt_cir); columns l + N/2."""
+    H = H.contiguous()
+    h = out if out is not None else torch.empty_like(H)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_cir(ctx.h, _ptr(H), int(H.shape[0]), int(H.shape[1]), _ptr(h)), "rt_cir")
+    return h
+
+
+def cir_stats(ctx: Context, H: torch.Tensor, delta_f_hz: float):
+    """Channel gain P and RMS delay spread tau_RMS [s] per receiver (rt_cir_stats)."""
+    H = H.contiguous()
+    R = int(H.shape[0])
+    P = torch.empty(R, dtype=torch.float32, device=H.device)
+    t = torch.empty(R, dtype=torch.float32, device=H.device)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_cir_stats(ctx.h, _ptr(H), R, int(H.shape[1]), float(delta_f_hz), _ptr(P), _ptr(t)),
+              "rt_cir_stats")
+    return P, t
+
+
+def power_scale_ema(ctx: Context, P_meas: torch.Tensor, P_pred: torch.Tensor, decay: float, state: torch.Tensor):
+    """Moving-average power scale of the measurements (rt_power_scale_ema); state = {alpha, initialised}."""
+    ctx._stream()
+    ctx.check(ctx.lib.rt_power_scale_ema(ctx.h, _ptr(P_meas.contiguous()), _ptr(P_pred.contiguous()),
+                                         int(P_meas.shape[0]), float(decay), _ptr(state)), "rt_power_scale_ema")
+    return state
+
+
+def delay_spread_power_loss(ctx: Context, H: torch.Tensor, delta_f_hz: float, P_meas: torch.Tensor,
+                            tau_meas: torch.Tensor, alpha_state: Optional[torch.Tensor] = None, loss=None,
+                            grad_H=None, P_pred=None, tau_pred=None):
+    """Eq. loss averaged over the receivers and dL/dH (rt_delay_spread_power_loss)."""
+    H = H.contiguous()
+    R = int(H.shape[0])
+    loss = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=H.device)
+    grad_H = grad_H if grad_H is not None else torch.empty_like(H)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_delay_spread_power_loss(ctx.h, _ptr(H), R, int(H.shape[1]), float(delta_f_hz),
+                                                 _ptr(P_meas.contiguous()), _ptr(tau_meas.contiguous()),
+                                                 _ptr(alpha_state), _ptr(loss), _ptr(grad_H), _ptr(P_pred),
+                                                 _ptr(tau_pred)), "rt_delay_spread_power_loss")
+    return loss, grad_H
+
+
+def cir_metrics(ctx: Context, P_meas, tau_meas, P_pred, tau_pred, alpha_state=None):
+    """ALE [dB] and RAE per receiver (rt_cir_metrics)."""
+    n = int(P_meas.shape[0])
+    ale = torch.empty(n, dtype=torch.float32, device=P_meas.device)
+    rae = torch.empty(n, dtype=torch.float32, device=P_meas.device)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_cir_metrics(ctx.h, _ptr(P_meas.contiguous()), _ptr(tau_meas.contiguous()),
+                                     _ptr(P_pred.contiguous()), _ptr(tau_pred.contiguous()), n, _ptr(alpha_state),
+                                     _ptr(ale), _ptr(rae)), "rt_cir_metrics")
+    return ale, rae
+
+
 # ----------------------------------------------------------------------------- neural materials
 
 MLP_IN, MLP_IN_PAD, MLP_WIDTH, MLP_OUT = 39, 40, 128, 2

@@ -66,6 +66,37 @@ class CfrPowerMSE(torch.autograd.Function):
         return grad_a * g, None, None, None, None, None, None, None, None
 
 
+class DelaySpreadPowerLoss(torch.autograd.Function):
+    """The paper's loss (Eq. loss): mean over receivers of SMAPE(tau_RMS, tau^_RMS) +
+    SMAPE(alpha P, P^) of the CIRs of H; the forward launch also produces dL/dH."""
+
+    @staticmethod
+    def forward(fctx, H, P_meas, tau_meas, alpha_state, ctx, delta_f_hz):
+        loss, grad_H = api.delay_spread_power_loss(ctx, H, delta_f_hz, P_meas, tau_meas, alpha_state)
+        fctx.save_for_backward(grad_H)
+        return loss[0]
+
+    @staticmethod
+    def backward(fctx, g):
+        (grad_H,) = fctx.saved_tensors
+        return grad_H * g, None, None, None, None, None
+
+
+def paper_calibration_loss(ctx, paths, eps_r, sigma, P_meas, tau_meas, alpha_state, freq_hz, f_center_hz,
+                           delta_f_hz, n_sub, decay=0.99, update_scale=True, per_triangle=False):
+    """One step of Algorithm 1 with the paper's loss: a = eval_fields(eps_r, sigma),
+    H = CFR(a), the power scale alpha updated by its moving average from this
+    batch (Eq. scaling_param; no gradient), then Eq. loss.  alpha_state is the
+    2-float device state of rt_power_scale_ema."""
+    a = EvalFields.apply(eps_r, sigma, ctx, paths, freq_hz, 1.0, 1.0, per_triangle)
+    H = Cfr.apply(a, paths.tau, paths.rx_offsets, ctx, f_center_hz, delta_f_hz, n_sub)
+    if update_scale:
+        with torch.no_grad():
+            P_pred, _ = api.cir_stats(ctx, H.detach(), delta_f_hz)
+            api.power_scale_ema(ctx, P_meas, P_pred, decay, alpha_state)
+    return DelaySpreadPowerLoss.apply(H, P_meas, tau_meas, alpha_state, ctx, delta_f_hz)
+
+
 class LogMaterials(torch.nn.Module):
     """Per-material parameters in the log domain of Eq. trainable_materials_1/2:
     sigma = exp(w_sigma), eps_r = 1 + exp(w_eps) (read-out vector v = 1, L = 1)."""
