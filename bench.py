@@ -667,6 +667,9 @@ def time_indoor_calibration(rt, ctx, flush, args, plain=True):
            "roofline_cfr": roofline_cfr(float(np.median(kt)), p.n_paths, N)}
     if not plain:
         return res
+    # the same step with the paper's loss (Eq. loss: SMAPE of the RMS delay spread
+    # and of the scaled channel gain, power scale by its moving average), one graph
+    res["paper_loss"] = time_paper_loss_step(rt, ctx, p, sc, eps, sig, flush, n)
     # the same step as plain PyTorch complex64 ops (eager, autograd), and how
     # closely its loss and gradients agree with the library's
     plain_ms, plain_loss, pe, ps = time_plain_calibration(p, sc, eps, sig, target, w, flush, min(n, 20))
@@ -728,6 +731,66 @@ def time_fields_hbm(rt, ctx, scene, sc, flush, reps=10, copies=1000):
             "fields_fwd": {"ms": t_f, "bytes": fwd_bytes, "achieved_gbs": gf, "peak_gbs": hbm, "frac": gf / hbm},
             "fields_bwd": {"ms": t_b, "bytes": bwd_bytes, "achieved_gbs": gb, "peak_gbs": hbm, "frac": gb / hbm},
             "peak_source": src}
+
+
+def time_paper_loss_step(rt, ctx, p, sc, eps, sig, flush, n):
+    """Calibration step of Algorithm 1 with the paper's loss on traced paths:
+    eval_fields -> CFR -> CIR statistics -> power scale (moving average) -> SMAPE
+    loss and dL/dH -> CFR adjoint -> eval_fields adjoint, captured in one graph."""
+    import torch
+    dev = eps.device
+    fc, df, N = sc.f_center_hz, sc.delta_f_hz, sc.n_sub
+    a = rt.eval_fields(ctx, p, torch.tensor(sc.eps_r, device=dev), torch.tensor(sc.sigma, device=dev), sc.freq_hz)
+    H = rt.cfr(ctx, p.rx_offsets, a, p.tau, fc, df, N)
+    Pm, tm = rt.cir_stats(ctx, H, df)
+    Pm = torch.where(Pm > 0, Pm * 0.25, torch.full_like(Pm, 1e-30)).contiguous()
+    tm = torch.where(tm > 0, tm, torch.full_like(tm, 1e-9)).contiguous()
+    R = sc.n_rx
+    Pp = torch.empty(R, device=dev)
+    state = torch.zeros(2, device=dev)
+    loss = torch.zeros(1, device=dev)
+    gH = torch.empty_like(H)
+    ga = torch.empty_like(a)
+    ge, gs, gg = torch.zeros_like(eps), torch.zeros_like(sig), torch.zeros(2, device=dev)
+
+    def step():
+        rt.eval_fields(ctx, p, eps, sig, sc.freq_hz, out=a)
+        rt.cfr(ctx, p.rx_offsets, a, p.tau, fc, df, N, out=H)
+        Pp_, _ = rt.cir_stats(ctx, H, df)
+        Pp.copy_(Pp_)
+        rt.power_scale_ema(ctx, Pm, Pp, 0.99, state)
+        rt.delay_spread_power_loss(ctx, H, df, Pm, tm, state, loss=loss, grad_H=gH)
+        rt.cfr_backward(ctx, p.rx_offsets, p.tau, fc, df, N, gH, out=ga)
+        ge.zero_()
+        gs.zero_()
+        gg.zero_()
+        rt.eval_fields_backward(ctx, p, eps, sig, sc.freq_hz, ga, ge, gs, gg)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        g.replay()
+    times = []
+    for _ in range(n):
+        flush.zero_()
+        s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        g.replay()
+        e0.record(stream)
+        e0.synchronize()
+        times.append(s0.elapsed_time(e0))
+    return {"ms_per_step_median": float(np.median(times)), "graph": True, "loss": float(loss.item()),
+            "alpha": float(state[0].item()),
+            "launches": "fields, CFR (tensor cores), CIR statistics, power scale, SMAPE loss + dL/dH, CFR adjoint "
+                        "(tensor cores), fields adjoint"}
 
 
 def time_batch(rt, ctx, args, reps=3):
