@@ -885,6 +885,40 @@ __global__ void k_bitonic_merge_local(uint64_t* keys, uint64_t k) {
     for (int i = threadIdx.x; i < SORT_BLOCK; i += blockDim.x) keys[base + i] = s[i];
 }
 
+// Small sets (n <= RANK_SORT_MAX unique keys): rank of every key = the number of
+// smaller keys, counted over all pairs spread across the grid (blockIdx.x: a
+// tile of RANK_TILE keys staged in shared memory, blockIdx.y: the keys being
+// ranked), then a scatter.  A bitonic network of a few thousand keys runs on
+// one or two CTAs through ~66 barrier-separated steps; this runs in a few.
+constexpr int RANK_SORT_MAX = 8192;
+constexpr int RANK_TILE = 512;
+
+// The order is key_less: depth first, then the key (left-aligned fields).
+__global__ void k_rank_count(const uint64_t* __restrict__ keys, int n, int* __restrict__ rank) {
+    __shared__ uint64_t sj[RANK_TILE];
+    __shared__ int sd[RANK_TILE];
+    const int j0 = blockIdx.x * RANK_TILE;
+    for (int t = threadIdx.x; t < RANK_TILE; t += blockDim.x) {
+        const bool in = j0 + t < n;
+        sj[t] = in ? keys[j0 + t] : ~0ull;
+        sd[t] = in ? rt_key_depth(sj[t]) : RT_MAX_DEPTH + 1;   // padding sorts last
+    }
+    __syncthreads();
+    const int i = blockIdx.y * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t key = keys[i];
+    const int dk = rt_key_depth(key);
+    int c = 0;
+#pragma unroll 8
+    for (int t = 0; t < RANK_TILE; ++t) c += (sd[t] < dk || (sd[t] == dk && sj[t] < key)) ? 1 : 0;
+    if (c) atomicAdd(rank + i, c);
+}
+
+__global__ void k_rank_scatter(const uint64_t* __restrict__ keys, const int* __restrict__ rank, int n,
+                               uint64_t* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[rank[i]] = keys[i];
+}
+
 __global__ void k_bitonic_global(uint64_t* keys, uint64_t n, uint64_t j, uint64_t k) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t p = i ^ j;
@@ -1307,7 +1341,7 @@ __device__ __forceinline__ bool coplanar64(const double* __restrict__ tri_n64, c
 // if another path of its receiver, of equal length, has pairwise coplanar
 // triangles, the same points (within 1e-9 diag) and a smaller triangle sequence.
 __global__ void k_dedup(int64_t P, int D, const int64_t* __restrict__ rx_offsets, const int32_t* __restrict__ path_rx,
-                        const int32_t* __restrict__ path_cand, const int32_t* __restrict__ depth,
+                        int32_t* __restrict__ path_cand, const int32_t* __restrict__ depth,
                         const int32_t* __restrict__ tri, const double* __restrict__ pts,
                         const int32_t* __restrict__ edge_flag, const double* __restrict__ tri_n64,
                         const float4* __restrict__ tri_v, double diag, uint32_t* bits, int64_t words,
@@ -1341,8 +1375,38 @@ __global__ void k_dedup(int64_t P, int D, const int64_t* __restrict__ rx_offsets
                 int64_t k = path_cand[i];
                 atomicAnd(bits + (int64_t)r * words + (k >> 5), ~(1u << (k & 31)));
                 atomicAdd(drops, 1ull);
+                path_cand[i] = -1;   // dropped (only this thread reads path_cand[i])
                 break;
             }
+        }
+    }
+}
+
+// Copies the paths the duplicate rule kept (path_cand >= 0) into fresh arrays,
+// one warp per receiver with a ballot prefix per 32 paths, so that the order
+// within a receiver is kept and no path is re-derived.
+__global__ void k_compact_paths(int R, int D, int64_t P, int64_t Pn, const int64_t* __restrict__ off,
+                                const int64_t* __restrict__ off_n, const int32_t* __restrict__ path_cand,
+                                const double* __restrict__ pts, const int32_t* __restrict__ depth,
+                                const int32_t* __restrict__ rx, const int32_t* __restrict__ tri, double* __restrict__ pts_n,
+                                int32_t* __restrict__ depth_n, int32_t* __restrict__ rx_n, int32_t* __restrict__ tri_n) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int64_t w = off_n[r];
+        const int64_t o1 = off[r + 1];
+        for (int64_t base = off[r]; base < o1; base += 32) {
+            const int64_t i = base + lane;
+            const bool keep = i < o1 && path_cand[i] >= 0;
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int64_t j = w + __popc(m & ((1u << lane) - 1u));
+                for (int e = 0; e < (D + 2) * 3; ++e) pts_n[j * (D + 2) * 3 + e] = pts[i * (D + 2) * 3 + e];
+                depth_n[j] = depth[i];
+                rx_n[j] = rx[i];
+                for (int b = 0; b < D; ++b) tri_n[(int64_t)b * Pn + j] = tri[(int64_t)b * P + i];
+            }
+            w += __popc(m);
         }
     }
 }
@@ -1516,9 +1580,27 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
             continue;
         }
         // ---------------- compact + sort (length, lexicographic)
+        d_sorted = sorted;
+        if (n_uniq <= RANK_SORT_MAX) {
+            // compact into the re-trace list's buffer (free once the re-trace has run:
+            // stream order), then rank and scatter into the sort buffer
+            uint64_t* unsorted = reinterpret_cast<uint64_t*>(redo);
+            int* rank = reinterpret_cast<int*>(unsorted + RANK_SORT_MAX);
+            RT_CK(ctx, cudaMemsetAsync(rank, 0, (size_t)RANK_SORT_MAX * 4, st));
+            k_table_compact<<<grid_for(ctx, cap, 256, 16), 256, 0, st>>>(table, cap, unsorted, counters + 3);
+            RT_COUNT(ctx);
+            if (n_uniq > 0) {
+                const int n = (int)n_uniq;
+                k_rank_count<<<dim3((n + RANK_TILE - 1) / RANK_TILE, (n + 255) / 256), 256, 0, st>>>(unsorted, n, rank);
+                RT_COUNT(ctx);
+                k_rank_scatter<<<grid_for(ctx, n, 256), 256, 0, st>>>(unsorted, rank, n, d_sorted);
+                RT_COUNT(ctx);
+            }
+            RT_CK_LAUNCH(ctx);
+            break;
+        }
         int64_t n_pad = SORT_BLOCK;
         while (n_pad < n_uniq) n_pad <<= 1;
-        d_sorted = sorted;
         k_fill_u64<<<grid_for(ctx, n_pad, 256), 256, 0, st>>>(d_sorted, n_pad, ~0ull); RT_COUNT(ctx);
         k_table_compact<<<grid_for(ctx, cap, 256, 16), 256, 0, st>>>(table, cap, d_sorted, counters + 3); RT_COUNT(ctx);
         RT_CK_LAUNCH(ctx);
@@ -1566,6 +1648,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
     unsigned long long* counters = nullptr;
     int32_t* flags = nullptr;
     int64_t* counts = nullptr;
+    int64_t n_emit = 0;
     for (int attempt = 0;; ++attempt) {
         size_t qcap = sc->queue_cap;
         size_t need = K * 4 + (size_t)D * K * 4 + (size_t)D * K * 24 + (size_t)D * K * 16 + qcap * 8 +
@@ -1638,22 +1721,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         k_segments<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st>>>(VA); RT_COUNT(ctx);
         mark(ctx, 4);
         TCK(cudaGetLastError());
-        int64_t* hp = ctx->h_pinned;
-        TCK(cudaMemcpyAsync(hp, flags, 4, cudaMemcpyDeviceToHost, st));
-        TCK(cudaStreamSynchronize(st));
-        if (*(int32_t*)hp) {
-            if (attempt >= 6) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "visibility queue overflow"));
-            sc->queue_cap *= 4;
-            continue;
-        }
-        break;
-    }
-
-    // ---------------- emission (repeated once more if the duplicate rule drops paths)
-    int32_t* path_rx = nullptr;
-    int32_t* path_cand = nullptr;
-    int32_t* edge = nullptr;
-    for (int pass = 0;; ++pass) {
+        // per-receiver path counts and offsets before the overflow check, so that
+        // one round trip returns both the queue flag and the number of paths
         k_row_count<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, counts); RT_COUNT(ctx);
         TCK(cudaGetLastError());
         if (!p->d_rx_offsets) TCK(cudaMallocAsync((void**)&p->d_rx_offsets, (size_t)(n_rx + 1) * 8, st));
@@ -1661,17 +1730,25 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         TCK(cudaGetLastError());
         int64_t* hp = ctx->h_pinned;
         TCK(cudaMemcpyAsync(hp, p->d_rx_offsets + n_rx, 8, cudaMemcpyDeviceToHost, st));
+        TCK(cudaMemcpyAsync(hp + 1, flags, 4, cudaMemcpyDeviceToHost, st));
         TCK(cudaStreamSynchronize(st));
-        const int64_t P = hp[0];
-        p->P = P;
-        if (pass > 0) {
-            cudaFreeAsync(p->d_pts, st);
-            cudaFreeAsync(p->d_depth, st);
-            cudaFreeAsync(p->d_rx, st);
-            cudaFreeAsync(p->d_tri, st);
-            cudaFreeAsync(path_cand, st);
-            cudaFreeAsync(edge, st);
+        if (*(int32_t*)(hp + 1)) {
+            if (attempt >= 6) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "visibility queue overflow"));
+            sc->queue_cap *= 4;
+            continue;
         }
+        n_emit = hp[0];
+        break;
+    }
+
+    // ---------------- emission, then the duplicate rule (kept paths compacted)
+    int32_t* path_rx = nullptr;
+    int32_t* path_cand = nullptr;
+    int32_t* edge = nullptr;
+    {
+        int64_t* hp = ctx->h_pinned;
+        const int64_t P = n_emit;
+        p->P = P;
         const size_t Pa = std::max<int64_t>(P, 1);
         TCK(cudaMallocAsync((void**)&p->d_pts, Pa * (D + 2) * 3 * 8, st));
         TCK(cudaMallocAsync((void**)&p->d_depth, Pa * 4, st));
@@ -1690,15 +1767,47 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
                                                              p->d_depth, p->d_rx, p->d_tri, edge, status); RT_COUNT(ctx);
             TCK(cudaGetLastError());
         }
-        if (pass > 0 || P == 0) break;
-        TCK(cudaMemsetAsync(counters + 4, 0, 8, st));
-        k_dedup<<<grid_for(ctx, P, 256), 256, 0, st>>>(P, D, p->d_rx_offsets, path_rx, path_cand, p->d_depth,
-                                                       p->d_tri, p->d_pts, edge, sc->d_tri_n64, sc->d_tri_v, sc->diag, bits, words,
-                                                       counters + 4); RT_COUNT(ctx);
-        TCK(cudaGetLastError());
-        TCK(cudaMemcpyAsync(hp, counters + 4, 8, cudaMemcpyDeviceToHost, st));
-        TCK(cudaStreamSynchronize(st));
-        if (hp[0] == 0) break;
+        if (P > 0) {
+            TCK(cudaMemsetAsync(counters + 4, 0, 8, st));
+            k_dedup<<<grid_for(ctx, P, 256), 256, 0, st>>>(P, D, p->d_rx_offsets, path_rx, path_cand, p->d_depth,
+                                                           p->d_tri, p->d_pts, edge, sc->d_tri_n64, sc->d_tri_v, sc->diag,
+                                                           bits, words, counters + 4); RT_COUNT(ctx);
+            TCK(cudaGetLastError());
+            TCK(cudaMemcpyAsync(hp, counters + 4, 8, cudaMemcpyDeviceToHost, st));
+            TCK(cudaStreamSynchronize(st));
+            const int64_t dropped = hp[0];
+            if (dropped > 0) {
+                // the kept paths, compacted per receiver (offsets from the cleared bits)
+                const int64_t Pn = P - dropped;
+                const size_t Pna = std::max<int64_t>(Pn, 1);
+                int64_t* off_n = nullptr;
+                double* pts_n = nullptr;
+                int32_t *depth_n = nullptr, *rx_n = nullptr, *tri_n = nullptr;
+                TCK(cudaMallocAsync((void**)&off_n, (size_t)(n_rx + 1) * 8, st));
+                TCK(cudaMallocAsync((void**)&pts_n, Pna * (D + 2) * 3 * 8, st));
+                TCK(cudaMallocAsync((void**)&depth_n, Pna * 4, st));
+                TCK(cudaMallocAsync((void**)&rx_n, Pna * 4, st));
+                TCK(cudaMallocAsync((void**)&tri_n, Pna * D * 4, st));
+                k_row_count<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, counts);
+                RT_COUNT(ctx);
+                k_scan<<<1, 1024, 0, st>>>(counts, n_rx, off_n); RT_COUNT(ctx);
+                k_compact_paths<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(
+                    n_rx, D, P, Pn, p->d_rx_offsets, off_n, path_cand, p->d_pts, p->d_depth, p->d_rx, p->d_tri, pts_n,
+                    depth_n, rx_n, tri_n); RT_COUNT(ctx);
+                TCK(cudaGetLastError());
+                cudaFreeAsync(p->d_rx_offsets, st);
+                cudaFreeAsync(p->d_pts, st);
+                cudaFreeAsync(p->d_depth, st);
+                cudaFreeAsync(p->d_rx, st);
+                cudaFreeAsync(p->d_tri, st);
+                p->d_rx_offsets = off_n;
+                p->d_pts = pts_n;
+                p->d_depth = depth_n;
+                p->d_rx = rx_n;
+                p->d_tri = tri_n;
+                p->P = Pn;
+            }
+        }
     }
     cudaFreeAsync(path_cand, st);
     cudaFreeAsync(edge, st);
