@@ -156,6 +156,46 @@ __device__ __forceinline__ int tri_test32(const WRay<float>& r, float4 p0, float
     return 2;
 }
 
+// tri_test32 for a launch ray: the FP64 ray of the final decision has the same
+// (canonical FP32) direction, and its origin differs from the FP32 one only by
+// the rounding of the transmitter, so the signs of the edge functions need only
+// cover this test's FP32 rounding.  With u = 2^-24, the translated and sheared
+// coordinates carry errors below 3u (Mv + Mo), Mv = max over the vertices of
+// |X_kx| + |X_ky| + |X_kz| (|Sx| + |Sy|) and Mo the same of the origin, so
+// |dU| <= u (4 L^2 + 12 (Mv + Mo) L) with L = max |sheared x, y|.  The margin is
+// twice that plus the FP64 test's growth TRI_TOL (|U| + |V| + |W|) (doubled):
+// usually far below the relative band of tri_test32, and rigorous where that
+// band is not (small, distant triangles).
+__device__ __forceinline__ int tri_test32_launch(const WRay<float>& r, float4 p0, float4 p1, float4 p2,
+                                                 float& t_out) {
+    const V3<float> A = from4<float>(p0) - r.o, B = from4<float>(p1) - r.o, C = from4<float>(p2) - r.o;
+    const float Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
+    const float Akx = comp(A, r.kx), Aky = comp(A, r.ky), Bkx = comp(B, r.kx), Bky = comp(B, r.ky);
+    const float Ckx = comp(C, r.kx), Cky = comp(C, r.ky);
+    const float Ax = Akx - r.Sx * Akz, Ay = Aky - r.Sy * Akz;
+    const float Bx = Bkx - r.Sx * Bkz, By = Bky - r.Sy * Bkz;
+    const float Cx = Ckx - r.Sx * Ckz, Cy = Cky - r.Sy * Ckz;
+    const float U = Cx * By - Cy * Bx, V = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
+    const float Sab = fabsf(r.Sx) + fabsf(r.Sy);
+    const float Mv = fmaxf(fmaxf(fabsf(Akx) + fabsf(Aky) + fabsf(Akz) * Sab, fabsf(Bkx) + fabsf(Bky) + fabsf(Bkz) * Sab),
+                           fabsf(Ckx) + fabsf(Cky) + fabsf(Ckz) * Sab);
+    const float Mo = fabsf(comp(r.o, r.kx)) + fabsf(comp(r.o, r.ky)) + fabsf(comp(r.o, r.kz)) * Sab;
+    const float L = fmaxf(fmaxf(fmaxf(fabsf(Ax), fabsf(Ay)), fmaxf(fabsf(Bx), fabsf(By))), fmaxf(fabsf(Cx), fabsf(Cy)));
+    const float sum = fabsf(U) + fabsf(V) + fabsf(W);
+    const float m = 2.0f * 5.9604645e-8f * (4.0f * L * L + 12.0f * (Mv + Mo) * L) + 2.0f * (float)TRI_TOL * sum;
+    const bool pos = U > m && V > m && W > m;
+    const bool neg = U < -m && V < -m && W < -m;
+    const float det = U + V + W;
+    const float Tn = (U * Akz + V * Bkz + W * Ckz) * r.Sz;
+    if (pos || neg) {
+        t_out = Tn / det;
+        return 1;
+    }
+    if ((U < -m || V < -m || W < -m) && (U > m || V > m || W > m)) return 0;
+    t_out = det != 0.0f ? Tn / det : 0.0f;
+    return 2;
+}
+
 // FP64 final decision: the triangle grown by TRI_TOL; a ray in its plane misses.
 // On a hit returns true with det > 0 and t = Tn / det (not divided here).
 __device__ __forceinline__ bool tri_test64(const WRay<double>& r, float4 p0, float4 p1, float4 p2, double& Tn,
@@ -252,7 +292,8 @@ __device__ __forceinline__ void traverse(const BvhNode* __restrict__ nodes, cons
 // triangle index; `und` is set if any decision that could matter was marginal.
 __device__ __forceinline__ int closest32(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris,
                                          const WRay<float>& r, float tmin, int skip, int* stack, float& t_out,
-                                         bool& und, int32_t* status, unsigned& nvis, unsigned& ntri) {
+                                         bool& und, int32_t* status, unsigned& nvis, unsigned& ntri,
+                                         bool launch_ray = false) {
     float tb = INFINITY, thi = INFINITY;
     int best = -1;
     traverse(nodes, r, tmin * 0.5f, thi, stack, status, nvis, [&](int first, int count) {
@@ -262,7 +303,7 @@ __device__ __forceinline__ int closest32(const BvhNode* __restrict__ nodes, cons
             if (id == skip) continue;
             ntri++;
             float th;
-            int cls = tri_test32(r, p0, p1, p2, th);
+            int cls = launch_ray ? tri_test32_launch(r, p0, p1, p2, th) : tri_test32(r, p0, p1, p2, th);
             if (cls == 0) continue;
             if (cls == 2) {
                 if (th > tmin * 0.5f && th < tb * 1.00001f) und = true;
@@ -662,7 +703,8 @@ struct SbrArgs {
     unsigned long long uniq_limit;
     int32_t* overflow;
     unsigned long long* next_ray;
-    int64_t* redo;
+    int64_t* redo;                  // re-trace list: ray | (undecided bounce << 32)
+    uint64_t* redo_key;             // key of the robust prefix of each listed ray
     unsigned long long* redo_count;
     int64_t redo_cap;
     int32_t* status;
@@ -730,14 +772,18 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
         float th;
         bool und = false;
         unsigned nv = 0, nt = 0;
-        int id = closest32(A.nodes, A.tris, r, eps, prev, stack, th, und, A.status, nv, nt);
+        int id = closest32(A.nodes, A.tris, r, eps, prev, stack, th, und, A.status, nv, nt, bounce == 0);
         c_vis += nv;
         c_tri += nt;
         c_q++;
         if (und) {
             unsigned long long slot = atomicAdd(A.redo_count, 1ull);
-            if ((int64_t)slot < A.redo_cap) A.redo[slot] = ray;
-            else atomicExch(A.overflow, 2);
+            if ((int64_t)slot < A.redo_cap) {
+                A.redo[slot] = ray | ((int64_t)bounce << 32);
+                A.redo_key[slot] = key;
+            } else {
+                atomicExch(A.overflow, 2);
+            }
             ray = -1;
             continue;
         }
@@ -770,7 +816,16 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
 // FP64 re-trace of the rays whose FP32 decisions were marginal (same rules,
 // final decisions).  One warp per block spreads the few rays over all SMs.
 // Inserts every prefix again; duplicates are harmless.
-__global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const double* __restrict__ tri_n64) {
+// Re-trace of a listed ray in FP64: the bounces before the one the FP32 pass
+// left undecided were decided robustly, so their triangles (in the stored key)
+// are replayed with one FP64 ray/triangle test each; the BVH search in
+// mixed precision (closest64) starts at the undecided bounce.
+__device__ __forceinline__ uint64_t key_prefix(uint64_t key, int b) {   // the fields of bounces < b
+    return b <= 0 ? 0ull : key & (~0ull << (48 - 16 * (b - 1)));
+}
+
+__global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const double* __restrict__ tri_n64,
+                                                           const float4* __restrict__ tri_v) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
     int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
@@ -786,24 +841,40 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const doub
     const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (lane >= rpw) return;
     for (unsigned long long w = warp * rpw + lane; w < n; w += W * rpw) {
-        int64_t ray = A.redo[w];
+        const int64_t e = A.redo[w];
+        const int64_t ray = e & 0xffffffffll;
+        int b0 = (int)(e >> 32);
+        uint64_t key = A.redo_key[w];
         float3 df = launch_dir(ray, __ldg(A.sched.z + ray));
         WRay<double> r;
         WRay<float> rf;
         r.o = mk(A.tx, A.ty, A.tz);
         r.d = mk((double)df.x, (double)df.y, (double)df.z);
         int prev = -1;
-        uint64_t key = 0;
         for (int b = 0; b < A.depth; ++b) {
             wray_init(r);
-            rf.o = mk((float)r.o.x, (float)r.o.y, (float)r.o.z);
-            rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
-            wray_init(rf);
             double th;
-            int id = closest64(A.nodes, A.tris, r, rf, A.eps, prev, stack, cand, cand_t, th, A.status);
-            if (id < 0) break;
-            key = rt_key_push(key, b, id);
-            hash_insert(A.table, A.mask, key, A.uniq, A.uniq_limit, A.overflow);
+            int id = -1;
+            if (b < b0) {   // robust prefix: its triangle, one FP64 test
+                id = rt_key_tri(key, b);
+                double Tn, det;
+                if (tri_test64(r, __ldg(tri_v + 3 * id), __ldg(tri_v + 3 * id + 1), __ldg(tri_v + 3 * id + 2), Tn, det) &&
+                    Tn > A.eps * det) {
+                    th = Tn * rcp64(det);
+                } else {   // not expected: search from here on
+                    b0 = b;
+                    key = key_prefix(key, b);
+                }
+            }
+            if (b >= b0) {
+                rf.o = mk((float)r.o.x, (float)r.o.y, (float)r.o.z);
+                rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
+                wray_init(rf);
+                id = closest64(A.nodes, A.tris, r, rf, A.eps, prev, stack, cand, cand_t, th, A.status);
+                if (id < 0) break;
+                key = rt_key_push(key_prefix(key, b), b, id);
+                hash_insert(A.table, A.mask, key, A.uniq, A.uniq_limit, A.overflow);
+            }
             V3<double> nn = mk(tri_n64[4 * id], tri_n64[4 * id + 1], tri_n64[4 * id + 2]);
             V3<double> p = r.o + th * r.d;
             r.d = r.d - (2.0 * dot(r.d, nn)) * nn;
@@ -1517,7 +1588,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
     for (int attempt = 0;; ++attempt) {
         size_t cap = sc->hash_cap;
         const size_t sort_cap = std::max<size_t>(SORT_BLOCK, cap / 2);
-        size_t need = cap * 8 + sort_cap * 8 + 256 * 8 + redo_cap * 8 + 4096;
+        size_t need = cap * 8 + sort_cap * 8 + 256 * 8 + redo_cap * 16 + 4096 + 256;
         void* base;
         rt_status s = rt_scratch(ctx, need, &base);
         if (s != RT_OK) return s;
@@ -1526,6 +1597,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         unsigned long long* counters = ar.take<unsigned long long>(8);   // uniq, next_ray, redo_count, compact
         int32_t* flags = ar.take<int32_t>(8);
         int64_t* redo = ar.take<int64_t>(redo_cap);
+        uint64_t* redo_key = ar.take<uint64_t>(redo_cap);
         uint64_t* sorted = ar.take<uint64_t>(sort_cap);
         mark(ctx, 0);
         RT_CK(ctx, cudaMemsetAsync(table, 0, cap * 8, st));
@@ -1548,6 +1620,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         A.overflow = flags;
         A.next_ray = counters + 1;
         A.redo = redo;
+        A.redo_key = redo_key;
         A.redo_count = counters + 2;
         A.redo_cap = redo_cap;
         A.status = status;
@@ -1562,7 +1635,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         mark(ctx, 7);
         RT_CK_LAUNCH(ctx);
         k_sbr_redo<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 2 * CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(
-            A, sc->d_tri_n64);
+            A, sc->d_tri_n64, sc->d_tri_v);
         RT_COUNT(ctx);
         mark(ctx, 1);
         RT_CK_LAUNCH(ctx);
@@ -1883,7 +1956,8 @@ struct BatchSbr {
     unsigned long long uniq_limit;
     int32_t* overflow;
     unsigned long long* next_ray;
-    int64_t* redo;
+    int64_t* redo;                  // global ray | (undecided bounce << 32)
+    uint64_t* redo_key;             // key of the robust prefix
     unsigned long long* redo_count;
     int64_t redo_cap;
     int32_t* status;
@@ -1951,14 +2025,18 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
         float th;
         bool und = false;
         unsigned nv = 0, nt = 0;
-        int id = closest32(nodes, bvh_tris, r, eps, prev, stack, th, und, A.status, nv, nt);
+        int id = closest32(nodes, bvh_tris, r, eps, prev, stack, th, und, A.status, nv, nt, bounce == 0);
         c_vis += nv;
         c_tri += nt;
         c_q++;
         if (und) {
             unsigned long long slot = atomicAdd(A.redo_count, 1ull);
-            if ((int64_t)slot < A.redo_cap) A.redo[slot] = ray;
-            else atomicExch(A.overflow, 2);
+            if ((int64_t)slot < A.redo_cap) {
+                A.redo[slot] = ray | ((int64_t)bounce << 32);
+                A.redo_key[slot] = key;
+            } else {
+                atomicExch(A.overflow, 2);
+            }
             ray = -1;
             continue;
         }
@@ -2004,7 +2082,10 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo_batch(BatchSbr A) {
     const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (lane >= rpw) return;
     for (unsigned long long w = warp * rpw + lane; w < n; w += W * rpw) {
-        int64_t ray = A.redo[w];
+        const int64_t e = A.redo[w];
+        const int64_t ray = e & 0xffffffffll;
+        int b0 = (int)(e >> 32);
+        uint64_t key = A.redo_key[w];
         int s = find_seg(A.ray_off, A.n + 1, ray);
         const SceneDev& d = A.sd[s];
         float3 df = launch_dir(ray - A.ray_off[s], __ldg(A.sched.z + (ray - A.ray_off[s])));
@@ -2013,17 +2094,31 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo_batch(BatchSbr A) {
         r.o = mk(d.tx, d.ty, d.tz);
         r.d = mk((double)df.x, (double)df.y, (double)df.z);
         int prev = -1;
-        uint64_t key = 0;
         for (int b = 0; b < A.depth; ++b) {
             wray_init(r);
-            rf.o = mk((float)r.o.x, (float)r.o.y, (float)r.o.z);
-            rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
-            wray_init(rf);
             double th;
-            int id = closest64(d.nodes, d.bvh_tris, r, rf, d.eps, prev, stack, cand, cand_t, th, A.status);
-            if (id < 0) break;
-            key = rt_key_push(key, b, id);
-            hash_insert(A.tables + (uint64_t)s * A.cap, A.cap - 1, key, A.uniq + s, A.uniq_limit, A.overflow);
+            int id = -1;
+            if (b < b0) {   // robust prefix: its triangle, one FP64 test (as k_sbr_redo)
+                id = rt_key_tri(key, b);
+                double Tn, det;
+                if (tri_test64(r, __ldg(d.tri_v + 3 * id), __ldg(d.tri_v + 3 * id + 1), __ldg(d.tri_v + 3 * id + 2),
+                               Tn, det) &&
+                    Tn > d.eps * det) {
+                    th = Tn * rcp64(det);
+                } else {
+                    b0 = b;
+                    key = key_prefix(key, b);
+                }
+            }
+            if (b >= b0) {
+                rf.o = mk((float)r.o.x, (float)r.o.y, (float)r.o.z);
+                rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
+                wray_init(rf);
+                id = closest64(d.nodes, d.bvh_tris, r, rf, d.eps, prev, stack, cand, cand_t, th, A.status);
+                if (id < 0) break;
+                key = rt_key_push(key_prefix(key, b), b, id);
+                hash_insert(A.tables + (uint64_t)s * A.cap, A.cap - 1, key, A.uniq + s, A.uniq_limit, A.overflow);
+            }
             V3<double> nn = mk(d.tri_n64[4 * id], d.tri_n64[4 * id + 1], d.tri_n64[4 * id + 2]);
             V3<double> p = r.o + th * r.d;
             r.d = r.d - (2.0 * dot(r.d, nn)) * nn;
@@ -2448,7 +2543,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
     size_t sort_cap = 0;
     for (int attempt = 0;; ++attempt) {
         sort_cap = std::max<size_t>(SORT_BLOCK, cap / 2);
-        size_t need = (size_t)n * cap * 8 + (size_t)n * sort_cap * 8 + (size_t)(2 * n + 8) * 8 + redo_cap * 8 + 16 * 256;
+        size_t need = (size_t)n * cap * 8 + (size_t)n * sort_cap * 8 + (size_t)(2 * n + 8) * 8 + redo_cap * 16 + 17 * 256;
         void* base;
         rt_status s0 = rt_scratch(ctx, need, &base);
         if (s0 != RT_OK) return fail(s0);
@@ -2457,6 +2552,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         unsigned long long* counters = ar.take<unsigned long long>(2 * n + 8);   // uniq[n], compact[n], next, redo
         int32_t* flags = ar.take<int32_t>(8);
         int64_t* redo = ar.take<int64_t>(redo_cap);
+        uint64_t* redo_key = ar.take<uint64_t>(redo_cap);
         sorted = ar.take<uint64_t>((size_t)n * sort_cap);
         BCK(cudaMemsetAsync(tables, 0, (size_t)n * cap * 8, st));
         BCK(cudaMemsetAsync(counters, 0, (2 * n + 8) * 8, st));
@@ -2473,6 +2569,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         A.overflow = flags;
         A.next_ray = counters + 2 * n;
         A.redo = redo;
+        A.redo_key = redo_key;
         A.redo_count = counters + 2 * n + 1;
         A.redo_cap = redo_cap;
         A.status = status;
