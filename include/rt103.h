@@ -253,6 +253,35 @@ rt_status rt_cfr_power_mse_fused(rt_ctx* ctx, const int64_t* rx_offsets_dev, int
  * out sets RT_ERR_TIMEOUT in the status word. */
 rt_status rt_set_cfr_tensor_cores(rt_ctx* ctx, int32_t enable);
 
+/* ------------------------------------------------------------------ antenna patterns */
+
+/* Trainable antenna patterns (Sec. III-B, Eq. polarization_model with zeta = 0):
+ * the directional gain is a mixture of M spherical Gaussians,
+ *   G(r) = 4 pi eta sum_m w_m exp(lambda_m mu_m . r) / a_m,
+ *   a_m = (2 pi / lambda_m) (exp(lambda_m) - exp(-lambda_m)),
+ * whose integral over the sphere is 4 pi eta (the factor 4 pi is the reading
+ * that matches the paper's normalisation), and a path's coefficient scales by
+ * sqrt(G_T(k_1) G_R(-k_{q+1})) with k_1 its departure direction and -k_{q+1}
+ * its arrival direction seen from the receiver (from the path records).
+ *   *_pattern_dev  1 + 5 M floats {eta, then per lobe w, lambda (> 0), mu_x, mu_y,
+ *                  mu_z (unit)}, or NULL for a unit gain on that side; 1 <= M <= 8
+ *   a_dev          complex64 per path (e.g. from rt_eval_fields with unit gains)
+ *   a_out_dev      complex64 per path, a sqrt(G_T G_R) (may alias a_dev)
+ *   gain_*_dev     per-path G_T and G_R (float32; may be NULL when not needed) */
+rt_status rt_antenna_apply(rt_ctx* ctx, const rt_paths* paths, const float* tx_pattern_dev, int32_t tx_lobes,
+                           const float* rx_pattern_dev, int32_t rx_lobes, const void* a_dev, void* a_out_dev,
+                           float* gain_tx_dev, float* gain_rx_dev);
+/* Adjoint of rt_antenna_apply given dL/da_out (PyTorch convention):
+ *   grad_a_dev    dL/da = sqrt(G_T G_R) dL/da_out (overwritten; may be NULL)
+ *   grad_*_dev    dL/d(eta, w, lambda, mu) of each given pattern, same packing,
+ *                 ACCUMULATED (+=); mu is treated as a free 3-vector.
+ * a_out_dev and gain_*_dev are the outputs of the forward call. */
+rt_status rt_antenna_apply_backward(rt_ctx* ctx, const rt_paths* paths, const float* tx_pattern_dev,
+                                    int32_t tx_lobes, const float* rx_pattern_dev, int32_t rx_lobes,
+                                    const void* a_out_dev, const float* gain_tx_dev, const float* gain_rx_dev,
+                                    const void* grad_out_dev, void* grad_a_dev, float* grad_tx_dev,
+                                    float* grad_rx_dev);
+
 /* ------------------------------------------------------------------ CIR, loss and metrics */
 
 /* CIR by N-point IDFT (Sec. II-A): h[r, l + N/2] = N^-1/2 sum_n H[r, n + N/2]

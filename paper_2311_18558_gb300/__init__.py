@@ -3,9 +3,11 @@ radio ray tracing (Hoydis et al., arXiv 2311.18558): specular path tracing,
 per-path field computation, CFR synthesis, their adjoints, behind the C ABI of
 include/rt103.h.  The Python layer only marshals arguments."""
 from ._lib import LIB_PATH, RtError, load  # noqa: F401
-from .api import (MLP_NB, MLP_NW, Context, Paths, Scene, autotune_trace, cfr, cfr_backward,  # noqa: F401
+from .api import (MLP_NB, MLP_NW, Context, Paths, Scene, antenna_apply, antenna_apply_backward,  # noqa: F401
+                  autotune_trace, cfr, cfr_backward,
                   cfr_power_mse_fused, cir, cir_metrics, cir_stats, delay_spread_power_loss, eval_fields,
                   eval_fields_backward, import_paths, mlp_backward, mlp_forward, pack_mlp, power_scale_ema,
                   set_cfr_tensor_cores, set_tuning, trace_batch, trace_paths)
-from .autograd import (Cfr, CfrPowerMSE, DelaySpreadPowerLoss, EvalFields, LogMaterials, NeuralMaterials,  # noqa: F401
-                       NeuralMaterialsFn, calibration_loss, paper_calibration_loss)
+from .autograd import (AntennaApply, AntennaPattern, Cfr, CfrPowerMSE, DelaySpreadPowerLoss,  # noqa: F401
+                       EvalFields, LogMaterials, NeuralMaterials, NeuralMaterialsFn, calibration_loss,
+                       paper_calibration_loss)

@@ -43,6 +43,8 @@ SIGNATURES = {
     "rt_paths_batch_info": (I32, [P, ctypes.POINTER(I32), P, P]),
     "rt_set_tuning": (I32, [P, I32, I32, I32]),
     "rt_set_cfr_tensor_cores": (I32, [P, I32]),
+    "rt_antenna_apply": (I32, [P, P, P, I32, P, I32, P, P, P, P]),
+    "rt_antenna_apply_backward": (I32, [P, P, P, I32, P, I32, P, P, P, P, P, P, P]),
     "rt_cir": (I32, [P, P, I32, I32, P]),
     "rt_cir_stats": (I32, [P, P, I32, I32, F64, P, P]),
     "rt_power_scale_ema": (I32, [P, P, P, I32, F32, P]),

@@ -267,6 +267,39 @@ def cfr_power_mse_fused(ctx: Context, rx_offsets, a, tau, f_center_hz, delta_f_h
     return loss, grad_a, H
 
 
+# ----------------------------------------------------------------------------- antenna patterns
+
+def _lobes(pat):
+    return 0 if pat is None else (int(pat.shape[0]) - 1) // 5
+
+
+def antenna_apply(ctx: Context, paths: Paths, a: torch.Tensor, tx_pattern=None, rx_pattern=None, out=None):
+    """a sqrt(G_T G_R) with mixture-of-lobes patterns (rt_antenna_apply); returns (a_out, G_T, G_R)."""
+    P = paths.n_paths
+    dev = a.device
+    a_out = out if out is not None else torch.empty_like(a)
+    gt = torch.empty(max(P, 1), dtype=torch.float32, device=dev)[:P] if tx_pattern is not None else None
+    gr = torch.empty(max(P, 1), dtype=torch.float32, device=dev)[:P] if rx_pattern is not None else None
+    ctx._stream()
+    ctx.check(ctx.lib.rt_antenna_apply(ctx.h, paths.h, _ptr(tx_pattern), _lobes(tx_pattern), _ptr(rx_pattern),
+                                       _lobes(rx_pattern), _ptr(a.contiguous()), _ptr(a_out), _ptr(gt), _ptr(gr)),
+              "rt_antenna_apply")
+    return a_out, gt, gr
+
+
+def antenna_apply_backward(ctx: Context, paths: Paths, a_out, gt, gr, grad_out, tx_pattern=None, rx_pattern=None):
+    """Adjoint of antenna_apply: (dL/da, dL/d tx pattern, dL/d rx pattern)."""
+    grad_a = torch.empty_like(a_out)
+    g_tx = torch.zeros_like(tx_pattern) if tx_pattern is not None else None
+    g_rx = torch.zeros_like(rx_pattern) if rx_pattern is not None else None
+    ctx._stream()
+    ctx.check(ctx.lib.rt_antenna_apply_backward(ctx.h, paths.h, _ptr(tx_pattern), _lobes(tx_pattern),
+                                                _ptr(rx_pattern), _lobes(rx_pattern), _ptr(a_out), _ptr(gt), _ptr(gr),
+                                                _ptr(grad_out.contiguous()), _ptr(grad_a), _ptr(g_tx), _ptr(g_rx)),
+              "rt_antenna_apply_backward")
+    return grad_a, g_tx, g_rx
+
+
 # ----------------------------------------------------------------------------- CIR, loss and metrics
 
 def cir(ctx: Context, H: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:

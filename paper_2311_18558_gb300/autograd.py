@@ -97,6 +97,55 @@ def paper_calibration_loss(ctx, paths, eps_r, sigma, P_meas, tau_meas, alpha_sta
     return DelaySpreadPowerLoss.apply(H, P_meas, tau_meas, alpha_state, ctx, delta_f_hz)
 
 
+class AntennaApply(torch.autograd.Function):
+    """a sqrt(G_T(departure) G_R(arrival)) with packed mixture-of-lobes patterns
+    (either may be None for a unit gain), rt_antenna_apply_backward as backward."""
+
+    @staticmethod
+    def forward(fctx, a, tx_pattern, rx_pattern, ctx, paths):
+        tx = tx_pattern.contiguous() if tx_pattern is not None else None
+        rx = rx_pattern.contiguous() if rx_pattern is not None else None
+        a_out, gt, gr = api.antenna_apply(ctx, paths, a, tx, rx)
+        fctx.save_for_backward(a_out, *(t for t in (gt, gr, tx, rx) if t is not None))
+        fctx.flags = (gt is not None, gr is not None)
+        fctx.args = (ctx, paths)
+        return a_out
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        saved = list(fctx.saved_tensors)
+        a_out = saved.pop(0)
+        has_t, has_r = fctx.flags
+        gt = saved.pop(0) if has_t else None
+        gr = saved.pop(0) if has_r else None
+        tx = saved.pop(0) if has_t else None
+        rx = saved.pop(0) if has_r else None
+        ctx, paths = fctx.args
+        ga, gtx, grx = api.antenna_apply_backward(ctx, paths, a_out, gt, gr, grad_out, tx, rx)
+        return ga, gtx, grx, None, None
+
+
+class AntennaPattern(torch.nn.Module):
+    """Trainable pattern of Sec. III-B: weights by a softmax, concentrations by an
+    exponential, mean directions normalised, radiation efficiency by a sigmoid;
+    forward() returns the packed physical parameters of rt_antenna_apply."""
+
+    def __init__(self, n_lobes=3, lam_init=2.0, eta_init=0.9, seed=0):
+        super().__init__()
+        g = torch.Generator().manual_seed(seed)
+        self.w_logit = torch.nn.Parameter(torch.zeros(n_lobes))
+        self.log_lam = torch.nn.Parameter(torch.full((n_lobes,), float(torch.log(torch.tensor(lam_init)))))
+        self.mu_raw = torch.nn.Parameter(torch.randn(n_lobes, 3, generator=g))
+        self.eta_logit = torch.nn.Parameter(torch.logit(torch.tensor(float(eta_init))))
+
+    def forward(self):
+        w = torch.softmax(self.w_logit, 0)
+        lam = torch.exp(self.log_lam)
+        mu = torch.nn.functional.normalize(self.mu_raw, dim=1)
+        lobes = torch.cat([w[:, None], lam[:, None], mu], 1).reshape(-1)
+        return torch.cat([torch.sigmoid(self.eta_logit)[None], lobes])
+
+
 class LogMaterials(torch.nn.Module):
     """Per-material parameters in the log domain of Eq. trainable_materials_1/2:
     sigma = exp(w_sigma), eps_r = 1 + exp(w_eps) (read-out vector v = 1, L = 1)."""

@@ -545,7 +545,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_paths_free(rt_pat
     if (!p) return RT_ERR_INVALID_ARG;
     cudaStream_t st = p->stream;
     void* ptrs[] = {p->d_rx_offsets, p->d_rx, p->d_depth, p->d_tri,  p->d_tau, p->d_len,
-                    p->d_mc,         p->d_Dm, p->d_pts,   p->d_cand};
+                    p->d_mc,         p->d_Dm, p->d_pts,   p->d_cand, p->d_dir};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, st);
     if (p->owned_scene) {

@@ -50,7 +50,7 @@ __device__ __forceinline__ void sph_basis(D3 k, D3* th, D3* ph) {
 __global__ void k_records(int64_t P, int D, const double* __restrict__ pts, const int32_t* __restrict__ depth,
                           const int32_t* __restrict__ tri, const double* __restrict__ tri_n64,
                           const int32_t* __restrict__ tri_material, const uint8_t* __restrict__ is_pec, double* tau,
-                          float* len, int2* mc, float4* Dm) {
+                          float* len, int2* mc, float4* Dm, float4* dir) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         const int q = depth[i];
         const double* pp = pts + (int64_t)i * (D + 2) * 3;
@@ -95,6 +95,9 @@ __global__ void k_records(int64_t P, int D, const double* __restrict__ pts, cons
         sph_basis(scl(-1.0, k[q + 1]), &rp, &rq);
         Dm[(int64_t)q * P + i] = make_float4((float)dotd(rp, out_p), (float)dotd(rp, out_q), (float)dotd(rq, out_p),
                                              (float)dotd(rq, out_q));
+        // departure and arrival directions, for direction-dependent antenna gains
+        dir[i] = make_float4((float)k[1].x, (float)k[1].y, (float)k[1].z, 0.0f);
+        dir[P + i] = make_float4((float)-k[q + 1].x, (float)-k[q + 1].y, (float)-k[q + 1].z, 0.0f);
     }
 }
 
@@ -414,11 +417,12 @@ rt_status rt_launch_paths_records(rt_ctx* ctx, rt_paths* p) {
     RT_CK(ctx, cudaMallocAsync((void**)&p->d_len, Pa * 4, st));
     RT_CK(ctx, cudaMallocAsync((void**)&p->d_mc, Pa * p->D * 8, st));
     RT_CK(ctx, cudaMallocAsync((void**)&p->d_Dm, Pa * (p->D + 1) * 16, st));
+    RT_CK(ctx, cudaMallocAsync((void**)&p->d_dir, Pa * 2 * 16, st));
     if (p->P == 0) return RT_OK;
     k_records<<<grid_for(ctx, p->P, 128, 16), 128, 0, st>>>(p->P, p->D, p->d_pts, p->d_depth, p->d_tri,
                                                            p->scene->d_tri_n64, p->scene->d_tri_material,
                                                            p->scene->d_is_pec, p->d_tau, p->d_len, p->d_mc,
-                                                           p->d_Dm); RT_COUNT(ctx);
+                                                           p->d_Dm, p->d_dir); RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;
 }

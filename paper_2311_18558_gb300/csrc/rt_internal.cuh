@@ -97,6 +97,7 @@ struct rt_paths {
     int2* d_mc = nullptr;              // D x P per bounce j: .x material (bit 30 set for a PEC
                                        // material), .y the bits of cos(theta_i) as float
     float4* d_Dm = nullptr;            // (D + 1) x P basis changes D_1 .. D_{q+1} (row major 2x2)
+    float4* d_dir = nullptr;           // 2 x P: departure direction k_1, arrival direction -k_{q+1} (unit, .w = 0)
     double* d_pts = nullptr;           // P x (D + 2) x 3
     uint64_t* d_cand = nullptr;        // K packed candidate keys
     rt_scene* owned_scene = nullptr;   // batch output: combined triangle tables, freed with the paths
