@@ -9,5 +9,5 @@ from .api import (MLP_NB, MLP_NW, Context, Paths, Scene, antenna_apply, antenna_
                   eval_fields_backward, import_paths, mlp_backward, mlp_forward, pack_mlp, power_scale_ema,
                   set_cfr_tensor_cores, set_tuning, trace_batch, trace_paths)
 from .autograd import (AntennaApply, AntennaPattern, Cfr, CfrPowerMSE, DelaySpreadPowerLoss,  # noqa: F401
-                       EvalFields, LogMaterials, NeuralMaterials, NeuralMaterialsFn, calibration_loss,
+                       EvalFields, LogMaterials, MaterialEmbeddings, NeuralMaterials, NeuralMaterialsFn, calibration_loss,
                        paper_calibration_loss)

@@ -161,6 +161,33 @@ class LogMaterials(torch.nn.Module):
         return 1.0 + torch.exp(self.w_eps), torch.exp(self.w_sigma)
 
 
+class MaterialEmbeddings(torch.nn.Module):
+    """The over-parametrised materials of Eq. trainable_materials_1/2: per material
+    two embeddings w_1, w_2 in L dimensions and one read-out vector v shared by all
+    materials, sigma = exp(v . w_1), eps_r = 1 + exp(v . w_2).  Initialised so that
+    v . w reproduces the given starting values (v = 1 / sqrt(L), w = v value * sqrt(L)
+    / L plus a small seeded spread that leaves v . w unchanged)."""
+
+    def __init__(self, eps_r_init, sigma_init, L=30, seed=0, spread=0.1):
+        super().__init__()
+        eps_r_init = torch.as_tensor(eps_r_init, dtype=torch.float32)
+        sigma_init = torch.as_tensor(sigma_init, dtype=torch.float32)
+        M = eps_r_init.shape[0]
+        g = torch.Generator().manual_seed(seed)
+        v = torch.full((L,), L ** -0.5)
+        # noise orthogonal to v, so that v . w starts at the requested value
+        n1 = torch.randn(M, L, generator=g) * spread
+        n2 = torch.randn(M, L, generator=g) * spread
+        n1 -= (n1 @ v)[:, None] * v[None, :]
+        n2 -= (n2 @ v)[:, None] * v[None, :]
+        self.v = torch.nn.Parameter(v)
+        self.w_sigma = torch.nn.Parameter(torch.log(sigma_init)[:, None] * v[None, :] + n1)
+        self.w_eps = torch.nn.Parameter(torch.log(eps_r_init - 1.0)[:, None] * v[None, :] + n2)
+
+    def forward(self):
+        return 1.0 + torch.exp(self.w_eps @ self.v), torch.exp(self.w_sigma @ self.v)
+
+
 def calibration_loss(ctx, paths, eps_r, sigma, target_power, rx_weight, freq_hz, f_center_hz, delta_f_hz, n_sub,
                      gain_tx=1.0, gain_rx=1.0, per_triangle=False):
     """One forward pass of Algorithm 1's inner loop: RT(p; Omega) -> CFR -> loss."""
