@@ -65,6 +65,8 @@ def _load():
             "orc_paths_count": (i64, [P]),
             "orc_paths_get": (None, [P, P, P, P, P, P]),
             "orc_paths_free": (None, [P]),
+            "orc_diffuse_paths": (P, [P, P, P, i32, i64, i32]),
+            "orc_paths_rays": (None, [P, P]),
             "orc_fields": (None, [P, i64, i32, P, P, P, P, P, P, P, i32, f64, f64, f64, i32, P]),
             "orc_fields_grad": (None, [P, i64, i32, P, P, P, P, P, P, P, i32, f64, f64, f64, P, P, P, P]),
             "orc_cfr": (None, [i64, P, P, P, i32, f64, f64, i32, P]),
@@ -169,6 +171,29 @@ class OracleScene:
         out["rx_offsets"] = np.cumsum(offs)
         out["candidates"] = cands
         out["max_depth"] = depth
+        return out
+
+    def diffuse_paths(self, n_rays, depth, rx=None, tx=None):
+        """Diffuse paths by next-event estimation (Sec. II-F): for every hit s_j of every
+        launch ray, the path Tx -> s_1..s_{j-1} (specular) -> s_j (diffuse) -> Rx when Rx
+        is on the incidence side of t_j and sees s_j.  Same dict layout as :meth:`trace`
+        plus ``ray`` (the launch ray of each path); ordered by (receiver, ray, j)."""
+        lib = _load()
+        tx = _c(self.scene.tx if tx is None else tx, np.float64)
+        rx = _c(self.scene.rx if rx is None else rx, np.float64).reshape(-1, 3)
+        ph = lib.orc_diffuse_paths(self.h, _p(tx), _p(rx), rx.shape[0], int(n_rays), int(depth))
+        P = lib.orc_paths_count(ph)
+        out = dict(rx=np.empty(P, np.int32), depth=np.empty(P, np.int32),
+                   seq=np.empty((P, depth), np.int32), pts=np.empty((P, depth + 2, 3), np.float64),
+                   tau=np.empty(P, np.float64), ray=np.empty(P, np.int32))
+        lib.orc_paths_get(ph, _p(out["rx"]), _p(out["depth"]), _p(out["seq"]), _p(out["pts"]), _p(out["tau"]))
+        lib.orc_paths_rays(ph, _p(out["ray"]))
+        lib.orc_paths_free(ph)
+        offs = np.zeros(rx.shape[0] + 1, np.int64)
+        np.add.at(offs, out["rx"] + 1, 1)
+        out["rx_offsets"] = np.cumsum(offs)
+        out["max_depth"] = depth
+        out["n_rays"] = int(n_rays)
         return out
 
     def fields(self, paths, eps_r=None, sigma=None, freq=None, gain_tx=1.0, gain_rx=1.0, ni_mode=0):

@@ -572,6 +572,7 @@ struct Paths {
     std::vector<int32_t> rx, depth, seq;  // seq: P x Dmax, -1 padded
     std::vector<double> pts;              // P x (Dmax+2) x 3
     std::vector<double> tau;
+    std::vector<int32_t> ray;             // diffuse paths: the launch ray that found the path
 };
 
 static bool seq_less(const int* a, const int* b, int q) {
@@ -776,6 +777,96 @@ void* orc_image_method(void* h, const double* tx, const double* rx, int n_rx, vo
         all->tau.insert(all->tau.end(), pr.tau.begin(), pr.tau.end());
     }
     return all;
+}
+
+// Diffuse reflection found by next-event estimation (Sec. II-F; the diffuse
+// reflection of Sec. II-D).  Every launch ray (the canonical FP32 Fibonacci
+// direction) bounces specularly as in sbr_ray, with its hit points
+// s_b = o_b + t_b d_b and reflected directions kept in FP64.  At each of its hits
+// s_j (j = 1..D) it is scattered diffusely towards every receiver that s_j sees,
+// giving the path Tx -> s_1 .. s_{j-1} (specular) -> s_j (diffuse) -> Rx.  The
+// receiver must lie strictly on the side of the plane of t_j from which the ray
+// came (the side of s_{j-1}, or of the transmitter for j = 1), be farther than
+// eps from s_j, and the segment s_j -> Rx must be free of every triangle but t_j
+// for t in (eps, len - eps).  Paths are grouped by receiver and ordered by
+// (ray, j) within a receiver; tau = (d_1 + .. + d_j + |Rx - s_j|) / c.
+void* orc_diffuse_paths(void* h, const double* tx, const double* rx, int n_rx, int64_t n_rays, int D) {
+    const Scene& s = *(Scene*)h;
+    const double eps = 1e-6 * s.diag;
+    const Vec3 txv = v3(tx[0], tx[1], tx[2]);
+    std::vector<int32_t> seq((size_t)n_rays * D, -1);
+    std::vector<Vec3> hit((size_t)n_rays * D);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n_rays; ++i) {
+        float f[3];
+        fibonacci_dir(i, n_rays, f);
+        Vec3 o = txv, d = v3(f[0], f[1], f[2]);
+        int prev = -1;
+        for (int b = 0; b < D; ++b) {
+            double th;
+            int t = closest_hit(s, o, d, eps, prev, true, &th);
+            if (t < 0) break;
+            Vec3 p = o + th * d;
+            seq[(size_t)D * i + b] = t;
+            hit[(size_t)D * i + b] = p;
+            Vec3 nn = s.n[t];
+            d = d - (2.0 * dot(d, nn)) * nn;
+            o = p;
+            prev = t;
+        }
+    }
+    std::vector<Paths> per_rx(n_rx);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int r = 0; r < n_rx; ++r) {
+        const Vec3 rxv = v3(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+        Paths& pr = per_rx[r];
+        for (int64_t i = 0; i < n_rays; ++i) {
+            double ell = 0.0;
+            Vec3 prev_pt = txv;
+            for (int j = 1; j <= D; ++j) {
+                const int t = seq[(size_t)D * i + j - 1];
+                if (t < 0) break;
+                const Vec3 p = hit[(size_t)D * i + j - 1];
+                ell += norm(p - prev_pt);
+                const Vec3 nn = s.n[t];
+                const double side_in = dot(prev_pt - p, nn), side_rx = dot(rxv - p, nn);
+                const Vec3 seg = rxv - p;
+                const double len = norm(seg);
+                const bool same_side = (side_in > 0.0 && side_rx > 0.0) || (side_in < 0.0 && side_rx < 0.0);
+                if (same_side && len > eps && !any_hit(s, p, seg, eps / len, 1.0 - eps / len, t, -1)) {
+                    pr.rx.push_back(r);
+                    pr.ray.push_back((int32_t)i);
+                    pr.depth.push_back(j);
+                    for (int b = 0; b < D; ++b) pr.seq.push_back(b < j ? seq[(size_t)D * i + b] : -1);
+                    for (int k = 0; k < D + 2; ++k) {
+                        Vec3 q = k == 0 ? txv : (k <= j ? hit[(size_t)D * i + k - 1] : (k == j + 1 ? rxv : v3(0, 0, 0)));
+                        pr.pts.push_back(q.x);
+                        pr.pts.push_back(q.y);
+                        pr.pts.push_back(q.z);
+                    }
+                    pr.tau.push_back((ell + len) / kC0);
+                }
+                prev_pt = p;
+            }
+        }
+    }
+    Paths* all = new Paths();
+    all->Dmax = D;
+    for (int r = 0; r < n_rx; ++r) {
+        Paths& pr = per_rx[r];
+        all->rx.insert(all->rx.end(), pr.rx.begin(), pr.rx.end());
+        all->ray.insert(all->ray.end(), pr.ray.begin(), pr.ray.end());
+        all->depth.insert(all->depth.end(), pr.depth.begin(), pr.depth.end());
+        all->seq.insert(all->seq.end(), pr.seq.begin(), pr.seq.end());
+        all->pts.insert(all->pts.end(), pr.pts.begin(), pr.pts.end());
+        all->tau.insert(all->tau.end(), pr.tau.begin(), pr.tau.end());
+    }
+    return all;
+}
+
+void orc_paths_rays(void* p, int32_t* ray) {
+    Paths& P = *(Paths*)p;
+    std::memcpy(ray, P.ray.data(), sizeof(int32_t) * P.ray.size());
 }
 
 int64_t orc_paths_count(void* p) { return (int64_t)((Paths*)p)->depth.size(); }

@@ -32,7 +32,8 @@ import numpy as np
 
 __all__ = [
     "Scene", "tiny_box", "street_canyon", "indoor_diff", "room_corridor", "city_batch",
-    "box_faces", "random_cfr_inputs", "random_fields_inputs", "random_mlp_params",
+    "box_faces", "random_cfr_inputs", "random_fields_inputs", "random_mlp_params", "random_scattering",
+    "ground_plane",
     "CONCRETE", "GLASS", "GROUND", "SPEED_OF_LIGHT", "VACUUM_PERMITTIVITY",
 ]
 
@@ -430,6 +431,31 @@ def random_fields_inputs(seed: int, n_materials: int):
     eps = rng.uniform(1.5, 12.0, n_materials).astype(np.float32)
     sig = (10.0 ** rng.uniform(-3.0, 0.5, n_materials)).astype(np.float32)
     return eps, sig
+
+
+def random_scattering(seed: int, n_materials: int) -> np.ndarray:
+    """Seeded per-material diffuse-reflection parameters (M x 8 float32):
+    [S, K_x, w_1, w_2, w_3, lambda_2, lambda_3, 0] with S ~ U(0.2, 0.7),
+    K_x ~ U(0.05, 0.5), (w_1, w_2, w_3) ~ Dirichlet(2, 2, 2), lambda ~ U(2, 15)."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((n_materials, 8), np.float32)
+    out[:, 0] = rng.uniform(0.2, 0.7, n_materials)
+    out[:, 1] = rng.uniform(0.05, 0.5, n_materials)
+    out[:, 2:5] = rng.dirichlet([2.0, 2.0, 2.0], n_materials)
+    out[:, 5:7] = rng.uniform(2.0, 15.0, (n_materials, 2))
+    return out
+
+
+def ground_plane(half: float = 200.0, tx=(0.0, 0.0, 10.0), rx=((25.0, 5.0, 2.0),)) -> Scene:
+    """One square ground plane (2 triangles, normal +z, material GROUND) of side
+    2 * half centred at the origin, a transmitter and receivers above it."""
+    v = np.array([[-half, -half, 0.0], [half, -half, 0.0], [half, half, 0.0], [-half, half, 0.0]], np.float32)
+    t = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    return Scene(name="ground_plane", verts=v, tris=t, tri_material=np.zeros(2, np.int32),
+                 eps_r=np.array([GROUND[0]], np.float32), sigma=np.array([GROUND[1]], np.float32),
+                 is_pec=np.zeros(1, np.uint8), tx=_f32(tx), rx=_f32(np.asarray(rx, np.float64)),
+                 n_rays=100_000, max_depth=1, freq_hz=3.5e9, f_center_hz=3.5e9,
+                 delta_f_hz=50e6 / 1024, n_sub=1024, seed=0)
 
 
 def random_mlp_params(seed: int, d_in: int = 39, width: int = 128, depth: int = 3, d_out: int = 2):
