@@ -282,6 +282,78 @@ rt_status rt_antenna_apply_backward(rt_ctx* ctx, const rt_paths* paths, const fl
                                     const void* grad_out_dev, void* grad_a_dev, float* grad_tx_dev,
                                     float* grad_rx_dev);
 
+/* ------------------------------------------------------------------ diffuse reflection */
+
+/* Diffuse reflection found by next-event estimation (Sec. II-F; the diffuse
+ * reflection model of Sec. II-D, Eq. scattered_field).  n_rays rays leave the
+ * transmitter along the same Fibonacci lattice as rt_trace_paths and bounce
+ * specularly up to max_depth times (closest hits decided in FP64); at each hit
+ * s_j the ray is scattered towards every receiver strictly on the side of t_j's
+ * plane it came from that sees s_j (nothing but t_j on the segment for
+ * t in (eps, len - eps), eps = 1e-6 scene diagonal), giving the path
+ * Tx -> s_1 .. s_{j-1} (specular) -> s_j (diffuse) -> Rx of depth j.
+ *   tx_host  3 doubles;  rx_dev  n_rx x 3 doubles [m]
+ *   1 <= max_depth <= 4, 1 <= n_rays, n_rays * max_depth < 2^31, 1 <= n_rx <= 2^24,
+ *   and n_rx * n_rays * max_depth / 32 <= 2^31 (the visibility bitmask)
+ * *out receives a paths object of the diffuse kind, grouped by receiver and
+ * ordered by (launch ray, j) within a receiver; rt_paths_count,
+ * rt_paths_rx_offsets, rt_paths_export (points Tx, s_1..s_j, Rx; tau =
+ * path length / c), rt_antenna_apply and rt_paths_free accept it; rt_eval_fields
+ * rejects it.  Synchronises (the path count sizes the outputs). */
+rt_status rt_trace_diffuse(rt_ctx* ctx, const rt_scene* scene, const double* tx_host, const double* rx_dev,
+                           int32_t n_rx, int64_t n_rays, int32_t max_depth, rt_paths** out);
+
+/* Coefficients of diffuse paths (Eq. scattered_field with chi_1 = chi_2 = 0):
+ * the specular prefix as rt_eval_fields with R = sqrt(1 - S^2) per bounce
+ * (Eq. specular_reflection), then at s_j
+ *   |E_s| = sqrt(4 pi / n_rays) S sqrt(f_s) |diag(r_perp, r_par) v|
+ * (v the incident field in the incidence basis without the spreading 1/l_j,
+ * which cancels against cos(theta_i) dA = 4 pi l_j^2 / n_rays: each launch ray
+ * samples the solid angle 4 pi / n_rays), the polarisation [sqrt(1 - K_x),
+ * sqrt(K_x)] in the basis e_perp = k_s x n / |k_s x n|, e_par = e_perp x k_s, and
+ *   a = lambda / (4 pi) sqrt(g_T g_R) |E_s| / d_last (D_last row 0 . pol),
+ * which is real.  f_s is the trainable scattering pattern of Sec. III-C:
+ *   f_s = w_1 / pi (k_s . n) + w_2 g(lambda_2, -k_i . k_s) + w_3 g(lambda_3, k_r . k_s),
+ *   g(lambda, c) = exp(lambda c) / a(lambda, cos theta_i), a = s U + (1 - s) L
+ * with U = 2 pi / lambda (e^lambda - 1), L = 2 pi / lambda (1 - e^-lambda) and the
+ * smooth step s(t(lambda), cos theta_i) of Sec. III-C.
+ *   eps_r_dev, sigma_dev  float32 per material (n_materials)
+ *   scat_dev              n_materials x 8 float32: S, K_x, w_1, w_2, w_3, lambda_2,
+ *                         lambda_3, unused; 0 <= S <= 1, 0 <= K_x <= 1, lambda > 0
+ *   a_dev                 n_paths complex64 output;  tau_dev  n_paths double (may be NULL) */
+rt_status rt_eval_fields_diffuse(rt_ctx* ctx, const rt_paths* paths, const float* eps_r_dev, const float* sigma_dev,
+                                 const float* scat_dev, double freq_hz, float gain_tx, float gain_rx, void* a_dev,
+                                 double* tau_dev);
+/* Adjoint of rt_eval_fields_diffuse, geometry held fixed: given grad_a (complex64),
+ * ACCUMULATES (+=) dL/d eps_r, dL/d sigma (per material) and dL/d scat
+ * (n_materials x 8, the last column untouched).  Gradient pointers may be NULL. */
+rt_status rt_eval_fields_diffuse_backward(rt_ctx* ctx, const rt_paths* paths, const float* eps_r_dev,
+                                          const float* sigma_dev, const float* scat_dev, double freq_hz,
+                                          float gain_tx, float gain_rx, const void* grad_a_dev,
+                                          float* grad_eps_r_dev, float* grad_sigma_dev, float* grad_scat_dev);
+
+/* Specular share of the reflected energy (Sec. II-D, Eq. specular_reflection):
+ * a_out[i] = a[i] prod_b sqrt(1 - S_b^2) over the bounces of specular path i,
+ * S_b = scat_dev[8 m_b] of the bounce's material.  a_out may alias a. */
+rt_status rt_specular_reduction(rt_ctx* ctx, const rt_paths* paths, const float* scat_dev, const void* a_dev,
+                                void* a_out_dev);
+/* Adjoint: grad_a = prod_b R_b grad_out (may be NULL); ACCUMULATES
+ * dL/dS_m = sum Re(conj(g) a_out) sum_{b: m_b = m} (-S_m / (1 - S_m^2)) into
+ * grad_scat_dev[8 m] (may be NULL; needs a_out_dev). */
+rt_status rt_specular_reduction_backward(rt_ctx* ctx, const rt_paths* paths, const float* scat_dev,
+                                         const void* a_out_dev, const void* grad_out_dev, void* grad_a_dev,
+                                         float* grad_scat_dev);
+
+/* Per-receiver concatenation of two path lists (8-byte elements: complex64
+ * coefficients or double delays), so that specular and diffuse paths go through
+ * one CFR: dst holds receiver r's elements of src1 ([off1[r], off1[r+1])) followed
+ * by its elements of src2; off_out (n_rx + 1 int64, may be NULL) = off1 + off2.
+ * rt_rx_split is its adjoint (either destination may be NULL). */
+rt_status rt_rx_merge(rt_ctx* ctx, int32_t n_rx, const int64_t* off1_dev, const int64_t* off2_dev,
+                      const void* src1_dev, const void* src2_dev, void* dst_dev, int64_t* off_out_dev);
+rt_status rt_rx_split(rt_ctx* ctx, int32_t n_rx, const int64_t* off1_dev, const int64_t* off2_dev,
+                      const void* src_dev, void* dst1_dev, void* dst2_dev);
+
 /* ------------------------------------------------------------------ CIR, loss and metrics */
 
 /* CIR by N-point IDFT (Sec. II-A): h[r, l + N/2] = N^-1/2 sum_n H[r, n + N/2]

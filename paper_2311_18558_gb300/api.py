@@ -300,6 +300,93 @@ def antenna_apply_backward(ctx: Context, paths: Paths, a_out, gt, gr, grad_out, 
     return grad_a, g_tx, g_rx
 
 
+# ----------------------------------------------------------------------------- diffuse reflection
+
+def trace_diffuse(ctx: Context, scene: Scene, tx, rx: torch.Tensor, n_rays: int, max_depth: int) -> Paths:
+    """Diffuse paths by next-event estimation from every SBR hit (rt_trace_diffuse)."""
+    rx = rx.to(device=torch.device("cuda", ctx.device), dtype=torch.float64).contiguous()
+    txa = (_c.c_double * 3)(*[float(v) for v in tx])
+    h = _c.c_void_p()
+    ctx._stream()
+    ctx.check(ctx.lib.rt_trace_diffuse(ctx.h, scene.h, txa, _ptr(rx), rx.shape[0], int(n_rays), int(max_depth),
+                                       _c.byref(h)), "rt_trace_diffuse")
+    return Paths(ctx, scene, h, rx.shape[0], max_depth)
+
+
+def eval_fields_diffuse(ctx: Context, paths: Paths, eps_r, sigma, scat, freq_hz: float, gain_tx: float = 1.0,
+                        gain_rx: float = 1.0, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Coefficients of diffuse paths (rt_eval_fields_diffuse); scat is (M, 8) float32."""
+    dev = torch.device("cuda", ctx.device)
+    a = out if out is not None else torch.empty(paths.n_paths, dtype=torch.complex64, device=dev)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_eval_fields_diffuse(ctx.h, paths.h, _ptr(eps_r), _ptr(sigma), _ptr(scat), float(freq_hz),
+                                             float(gain_tx), float(gain_rx), _ptr(a), None), "rt_eval_fields_diffuse")
+    return a
+
+
+def eval_fields_diffuse_backward(ctx: Context, paths: Paths, eps_r, sigma, scat, freq_hz, grad_a, grad_eps=None,
+                                 grad_sigma=None, grad_scat=None, gain_tx=1.0, gain_rx=1.0):
+    """Accumulates dL/deps_r, dL/dsigma and dL/dscat given dL/da (rt_eval_fields_diffuse_backward)."""
+    grad_eps = torch.zeros_like(eps_r, dtype=torch.float32) if grad_eps is None else grad_eps
+    grad_sigma = torch.zeros_like(sigma, dtype=torch.float32) if grad_sigma is None else grad_sigma
+    grad_scat = torch.zeros_like(scat, dtype=torch.float32) if grad_scat is None else grad_scat
+    ctx._stream()
+    ctx.check(ctx.lib.rt_eval_fields_diffuse_backward(ctx.h, paths.h, _ptr(eps_r), _ptr(sigma), _ptr(scat),
+                                                      float(freq_hz), float(gain_tx), float(gain_rx),
+                                                      _ptr(grad_a.contiguous()), _ptr(grad_eps), _ptr(grad_sigma),
+                                                      _ptr(grad_scat)), "rt_eval_fields_diffuse_backward")
+    return grad_eps, grad_sigma, grad_scat
+
+
+def specular_reduction(ctx: Context, paths: Paths, scat, a, out=None):
+    """a prod_b sqrt(1 - S_b^2) over the bounces of each specular path (rt_specular_reduction)."""
+    out = out if out is not None else torch.empty_like(a)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_specular_reduction(ctx.h, paths.h, _ptr(scat), _ptr(a.contiguous()), _ptr(out)),
+              "rt_specular_reduction")
+    return out
+
+
+def specular_reduction_backward(ctx: Context, paths: Paths, scat, a_out, grad_out, grad_scat=None):
+    """Adjoint of specular_reduction: (dL/da, dL/dscat accumulated into grad_scat)."""
+    grad_a = torch.empty_like(grad_out)
+    grad_scat = torch.zeros_like(scat, dtype=torch.float32) if grad_scat is None else grad_scat
+    ctx._stream()
+    ctx.check(ctx.lib.rt_specular_reduction_backward(ctx.h, paths.h, _ptr(scat), _ptr(a_out),
+                                                     _ptr(grad_out.contiguous()), _ptr(grad_a), _ptr(grad_scat)),
+              "rt_specular_reduction_backward")
+    return grad_a, grad_scat
+
+
+def rx_merge(ctx: Context, off1, off2, x1, x2, off_out=None):
+    """Per-receiver concatenation [x1 of r | x2 of r] (rt_rx_merge); 8-byte dtypes.  Returns (x, offsets)."""
+    if x1.element_size() != 8 or x2.dtype != x1.dtype:
+        raise ValueError("rx_merge takes two tensors of one 8-byte dtype (complex64 or float64)")
+    R = off1.shape[0] - 1
+    out = torch.empty(x1.shape[0] + x2.shape[0], dtype=x1.dtype, device=x1.device)
+    off_out = off_out if off_out is not None else torch.empty(R + 1, dtype=torch.int64, device=x1.device)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_rx_merge(ctx.h, R, _ptr(off1), _ptr(off2), _ptr(x1.contiguous()), _ptr(x2.contiguous()),
+                                  _ptr(out), _ptr(off_out)), "rt_rx_merge")
+    return out, off_out
+
+
+def rx_split(ctx: Context, off1, off2, x, n1=None, n2=None):
+    """Adjoint of rx_merge: the two per-receiver parts of x (rt_rx_split); n1, n2 are
+    the part sizes (read from the offsets when not given)."""
+    if x.element_size() != 8:
+        raise ValueError("rx_split takes an 8-byte dtype (complex64 or float64)")
+    n1 = int(off1[-1].item()) if n1 is None else int(n1)
+    n2 = int(off2[-1].item()) if n2 is None else int(n2)
+    d1 = torch.empty(n1, dtype=x.dtype, device=x.device)
+    d2 = torch.empty(n2, dtype=x.dtype, device=x.device)
+    R = off1.shape[0] - 1
+    ctx._stream()
+    ctx.check(ctx.lib.rt_rx_split(ctx.h, R, _ptr(off1), _ptr(off2), _ptr(x.contiguous()), _ptr(d1), _ptr(d2)),
+              "rt_rx_split")
+    return d1, d2
+
+
 # ----------------------------------------------------------------------------- CIR, loss and metrics
 
 def cir(ctx: Context, H: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:

@@ -168,24 +168,112 @@ class MaterialEmbeddings(torch.nn.Module):
     v . w reproduces the given starting values (v = 1 / sqrt(L), w = v value * sqrt(L)
     / L plus a small seeded spread that leaves v . w unchanged)."""
 
-    def __init__(self, eps_r_init, sigma_init, L=30, seed=0, spread=0.1):
+    def __init__(self, eps_r_init, sigma_init, L=30, seed=0, spread=0.1, S_init=None, K_x_init=None):
         super().__init__()
         eps_r_init = torch.as_tensor(eps_r_init, dtype=torch.float32)
         sigma_init = torch.as_tensor(sigma_init, dtype=torch.float32)
         M = eps_r_init.shape[0]
         g = torch.Generator().manual_seed(seed)
         v = torch.full((L,), L ** -0.5)
-        # noise orthogonal to v, so that v . w starts at the requested value
-        n1 = torch.randn(M, L, generator=g) * spread
-        n2 = torch.randn(M, L, generator=g) * spread
-        n1 -= (n1 @ v)[:, None] * v[None, :]
-        n2 -= (n2 @ v)[:, None] * v[None, :]
+
+        def embed(value):
+            # noise orthogonal to v, so that v . w starts at the requested value
+            n = torch.randn(M, L, generator=g) * spread
+            n -= (n @ v)[:, None] * v[None, :]
+            return torch.nn.Parameter(value[:, None] * v[None, :] + n)
         self.v = torch.nn.Parameter(v)
-        self.w_sigma = torch.nn.Parameter(torch.log(sigma_init)[:, None] * v[None, :] + n1)
-        self.w_eps = torch.nn.Parameter(torch.log(eps_r_init - 1.0)[:, None] * v[None, :] + n2)
+        self.w_sigma = embed(torch.log(sigma_init))
+        self.w_eps = embed(torch.log(eps_r_init - 1.0))
+        # S = sigmoid(v . w_3), K_x = sigmoid(v . w_4) (Eq. trainable_materials_4), when asked for
+        self.w_S = embed(torch.logit(torch.as_tensor(S_init, dtype=torch.float32))) if S_init is not None else None
+        self.w_Kx = (embed(torch.logit(torch.as_tensor(K_x_init, dtype=torch.float32)))
+                     if K_x_init is not None else None)
 
     def forward(self):
         return 1.0 + torch.exp(self.w_eps @ self.v), torch.exp(self.w_sigma @ self.v)
+
+    def scattering(self):
+        """(S, K_x) per material, sigmoid(v . w_3) and sigmoid(v . w_4)."""
+        return torch.sigmoid(self.w_S @ self.v), torch.sigmoid(self.w_Kx @ self.v)
+
+
+class EvalFieldsDiffuse(torch.autograd.Function):
+    """a = eval_fields_diffuse(eps_r, sigma, scat) for diffuse paths, with
+    rt_eval_fields_diffuse_backward as backward (scat is the (M, 8) table)."""
+
+    @staticmethod
+    def forward(fctx, eps_r, sigma, scat, ctx, paths, freq_hz, gain_tx=1.0, gain_rx=1.0):
+        eps_r, sigma, scat = eps_r.contiguous(), sigma.contiguous(), scat.contiguous()
+        a = api.eval_fields_diffuse(ctx, paths, eps_r, sigma, scat, freq_hz, gain_tx, gain_rx)
+        fctx.save_for_backward(eps_r, sigma, scat)
+        fctx.args = (ctx, paths, freq_hz, gain_tx, gain_rx)
+        return a
+
+    @staticmethod
+    def backward(fctx, grad_a):
+        eps_r, sigma, scat = fctx.saved_tensors
+        ctx, paths, freq_hz, gain_tx, gain_rx = fctx.args
+        ge, gs, gc = api.eval_fields_diffuse_backward(ctx, paths, eps_r, sigma, scat, freq_hz, grad_a.contiguous(),
+                                                      gain_tx=gain_tx, gain_rx=gain_rx)
+        return ge, gs, gc, None, None, None, None, None
+
+
+class SpecularReduction(torch.autograd.Function):
+    """a prod_b sqrt(1 - S_b^2) for specular paths (Eq. specular_reflection)."""
+
+    @staticmethod
+    def forward(fctx, a, scat, ctx, paths):
+        scat = scat.contiguous()
+        out = api.specular_reduction(ctx, paths, scat, a.contiguous())
+        fctx.save_for_backward(out, scat)
+        fctx.args = (ctx, paths)
+        return out
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        out, scat = fctx.saved_tensors
+        ctx, paths = fctx.args
+        ga, gc = api.specular_reduction_backward(ctx, paths, scat, out, grad_out.contiguous())
+        return ga, gc, None, None
+
+
+class RxMerge(torch.autograd.Function):
+    """Per-receiver concatenation of two coefficient lists (rt_rx_merge), with
+    rt_rx_split as backward."""
+
+    @staticmethod
+    def forward(fctx, x1, x2, off1, off2, ctx):
+        out, _ = api.rx_merge(ctx, off1, off2, x1, x2)
+        fctx.args = (ctx, off1, off2, x1.shape[0], x2.shape[0])
+        return out
+
+    @staticmethod
+    def backward(fctx, g):
+        ctx, off1, off2, n1, n2 = fctx.args
+        g1, g2 = api.rx_split(ctx, off1, off2, g.contiguous(), n1, n2)
+        return g1, g2, None, None, None
+
+
+class ScatteringPattern(torch.nn.Module):
+    """Per-material trainable scattering pattern of Sec. III-C: mixture weights
+    (w_1, w_2, w_3) by a softmax and concentrations lambda_2, lambda_3 by an
+    exponential; forward() returns (w (M, 3), lambda (M, 2))."""
+
+    def __init__(self, n_materials, lam_init=5.0, w_init=(1 / 3, 1 / 3, 1 / 3)):
+        super().__init__()
+        w0 = torch.log(torch.as_tensor(w_init, dtype=torch.float32))
+        self.w_logit = torch.nn.Parameter(w0.repeat(n_materials, 1))
+        self.log_lam = torch.nn.Parameter(torch.full((n_materials, 2), float(torch.log(torch.tensor(lam_init)))))
+
+    def forward(self):
+        return torch.softmax(self.w_logit, 1), torch.exp(self.log_lam)
+
+
+def pack_scattering(S, K_x, w, lam):
+    """The (M, 8) float32 table of rt_eval_fields_diffuse: S, K_x, w_1..w_3, lambda_2, lambda_3, 0."""
+    M = S.shape[0]
+    return torch.cat([S[:, None], K_x[:, None], w, lam, torch.zeros(M, 1, dtype=S.dtype, device=S.device)],
+                     1).float().contiguous()
 
 
 def calibration_loss(ctx, paths, eps_r, sigma, target_power, rx_weight, freq_hz, f_center_hz, delta_f_hz, n_sub,

@@ -545,7 +545,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_paths_free(rt_pat
     if (!p) return RT_ERR_INVALID_ARG;
     cudaStream_t st = p->stream;
     void* ptrs[] = {p->d_rx_offsets, p->d_rx, p->d_depth, p->d_tri,  p->d_tau, p->d_len,
-                    p->d_mc,         p->d_Dm, p->d_pts,   p->d_cand, p->d_dir};
+                    p->d_mc,         p->d_Dm, p->d_pts,   p->d_cand, p->d_dir, p->d_scat};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, st);
     if (p->owned_scene) {
@@ -676,6 +676,7 @@ static rt_status check_fields(rt_ctx* ctx, const rt_paths* p, const float* eps, 
                               double freq, float gtx, float grx) {
     if (!ctx) return RT_ERR_INVALID_ARG;
     if (!p || !eps || !sig) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument");
+    if (p->kind != 0) return rt_fail(ctx, RT_ERR_INVALID_ARG, "diffuse paths: use rt_eval_fields_diffuse");
     if (per_tri != 0 && per_tri != 1) return rt_fail(ctx, RT_ERR_INVALID_ARG, "per_triangle must be 0 or 1");
     if (!(freq > 0.0) || !std::isfinite(freq)) return rt_fail(ctx, RT_ERR_INVALID_ARG, "freq_hz must be > 0");
     if (!(gtx > 0.0f) || !(grx > 0.0f) || !std::isfinite(gtx) || !std::isfinite(grx))

@@ -1,0 +1,1094 @@
+// Diffuse reflection (arXiv 2311.18558, Sec. II-D "Diffuse reflection",
+// Eq. scattered_field), found by next-event estimation during shoot-and-bounce
+// (Sec. II-F), with the trainable scattering pattern of Sec. III-C
+// (Eq. trainable_scattering_pattern) and the specular share R = sqrt(1 - S^2)
+// of Eq. specular_reflection.
+//
+// Tracing (once per geometry):
+//   1. k_df_rays: every launch ray (canonical FP32 Fibonacci direction) bounces
+//      specularly up to D times; closest hits are decided in FP64 (watertight
+//      test, triangles grown by TRI_TOL, lowest index among hits within TIE_TOL),
+//      and hit points and reflected directions are carried in FP64.  Every hit
+//      s_j of ray i is a diffuse source with index i * D + (j - 1).
+//   2. k_df_nee: one thread per (source, receiver): the receiver must be strictly
+//      on the side of t_j's plane the ray came from and see s_j (FP64 any-hit
+//      over (eps, len - eps), t_j excluded); visible pairs set a bit of a
+//      (receiver x source) mask.
+//   3. per-receiver popcounts, scans and an ordered expansion give the paths
+//      grouped by receiver and ordered by (ray, j); k_df_records turns each
+//      into FP32 records for the field kernels.
+// Fields (every calibration step): the specular prefix as in the specular
+// kernels (with R per bounce), then the diffuse bounce
+//   |E_s| = sqrt(4 pi / N) S sqrt(f_s) |diag(r_perp, r_par) v|,
+//   a = lambda / (4 pi) sqrt(g_T g_R) |E_s| / d_last (D_last[0,0] sqrt(1 - K_x)
+//       + D_last[0,1] sqrt(K_x)),
+// where v is the incident field at s_j in its incidence basis without the
+// spherical spreading 1 / l_j, which cancels against cos(theta_i) dA = 4 pi l_j^2 / N
+// (each ray samples the solid angle 4 pi / N).  The scattered polarisation
+// [sqrt(1 - K_x), sqrt(K_x)] (chi_1 = chi_2 = 0) is taken in the basis
+// e_perp = k_s x n / |k_s x n|, e_par = e_perp x k_s of the scattered direction.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "fresnel.cuh"
+#include "launch_dir.cuh"
+#include "rt_internal.cuh"
+
+namespace {
+
+constexpr double DF_TRI_TOL = 1e-9;    // relative growth of every triangle (as the specular tracer)
+constexpr double DF_TIE_TOL = 1e-12;   // relative t-difference treated as a tie
+constexpr int DF_STACK = 64;
+constexpr int DF_MAX_VISITS = 1 << 20;
+constexpr int DF_THREADS = 128;
+constexpr int MAT_PEC = 1 << 30;       // PEC flag in the per-bounce material word (as the specular records)
+constexpr float DF_PI = 3.14159265358979323846f;
+
+int grid_of(const rt_ctx* ctx, int64_t n, int threads, int per_sm) {
+    int64_t g = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)ctx->num_sms * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// ------------------------------------------------------------------ FP64 rays
+struct Ray64 {
+    double o[3], d[3];
+    int kx, ky, kz;
+    double Sx, Sy, Sz;
+    float3 of, inv;   // FP32 origin and reciprocal direction for the box tests
+};
+
+__device__ __forceinline__ void ray64_init(Ray64& r) {
+    const double ax = fabs(r.d[0]), ay = fabs(r.d[1]), az = fabs(r.d[2]);
+    int kz = 0;
+    if (ay > ax) kz = 1;
+    if (az > (kz == 0 ? ax : ay)) kz = 2;
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    if (r.d[kz] < 0.0) {
+        const int s = kx;
+        kx = ky;
+        ky = s;
+    }
+    r.kx = kx;
+    r.ky = ky;
+    r.kz = kz;
+    r.Sx = r.d[kx] / r.d[kz];
+    r.Sy = r.d[ky] / r.d[kz];
+    r.Sz = 1.0 / r.d[kz];
+    r.of = make_float3((float)r.o[0], (float)r.o[1], (float)r.o[2]);
+    float inv[3];
+    for (int k = 0; k < 3; ++k) {
+        const float dk = (float)r.d[k];
+        inv[k] = 1.0f / (fabsf(dk) < 1e-30f ? copysignf(1e-30f, dk) : dk);
+    }
+    r.inv = make_float3(inv[0], inv[1], inv[2]);
+}
+
+// Watertight ray/triangle test in FP64 (Woop, Benthin and Wald, JCGT 2013) with
+// the scaled barycentrics allowed down to -DF_TRI_TOL (|U| + |V| + |W|); a ray in
+// the triangle's plane misses.  On a hit returns true and t = T / det.
+__device__ __forceinline__ bool tri_hit64(const Ray64& r, float4 p0, float4 p1, float4 p2, double& t) {
+    const double A[3] = {(double)p0.x - r.o[0], (double)p0.y - r.o[1], (double)p0.z - r.o[2]};
+    const double B[3] = {(double)p1.x - r.o[0], (double)p1.y - r.o[1], (double)p1.z - r.o[2]};
+    const double C[3] = {(double)p2.x - r.o[0], (double)p2.y - r.o[1], (double)p2.z - r.o[2]};
+    const double Ax = A[r.kx] - r.Sx * A[r.kz], Ay = A[r.ky] - r.Sy * A[r.kz];
+    const double Bx = B[r.kx] - r.Sx * B[r.kz], By = B[r.ky] - r.Sy * B[r.kz];
+    const double Cx = C[r.kx] - r.Sx * C[r.kz], Cy = C[r.ky] - r.Sy * C[r.kz];
+    const double U = Cx * By - Cy * Bx, V = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
+    const double m = DF_TRI_TOL * (fabs(U) + fabs(V) + fabs(W));
+    if ((U < -m || V < -m || W < -m) && (U > m || V > m || W > m)) return false;
+    const double det = U + V + W;
+    if (!(fabs(det) > 3.0 * m)) return false;
+    const double T = U * (r.Sz * A[r.kz]) + V * (r.Sz * B[r.kz]) + W * (r.Sz * C[r.kz]);
+    t = T / det;
+    return true;
+}
+
+// FP32 slab test of one child box over [tlo, thi] (boxes carry a 4e-6 diag pad,
+// far above the rounding of the FP32 ray).
+__device__ __forceinline__ bool box32(const Ray64& r, float lx, float ly, float lz, float hx, float hy, float hz,
+                                      float tlo, float thi) {
+    const float tx0 = (lx - r.of.x) * r.inv.x, tx1 = (hx - r.of.x) * r.inv.x;
+    const float ty0 = (ly - r.of.y) * r.inv.y, ty1 = (hy - r.of.y) * r.inv.y;
+    const float tz0 = (lz - r.of.z) * r.inv.z, tz1 = (hz - r.of.z) * r.inv.z;
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tlo));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), thi));
+    return tn <= tf;
+}
+
+// BVH walk with a per-thread stack; leaf(first, count) returns true to stop.
+// `thi` may be lowered by the leaf callback.  Visits are bounded.
+template <typename Leaf>
+__device__ __forceinline__ void walk(const BvhNode* __restrict__ nodes, const Ray64& r, float tlo, const float& thi,
+                                     int32_t* status, Leaf&& leaf) {
+    int stack[DF_STACK];
+    int sp = 0, ref = 0, visits = 0;
+    for (;;) {
+        if (++visits > DF_MAX_VISITS) {
+            rt_set_status(status, RT_ERR_ITER_LIMIT);
+            return;
+        }
+        if (ref >= 0) {
+            const float4* np = reinterpret_cast<const float4*>(nodes + ref);
+            const float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
+            const int4 d = __ldg(reinterpret_cast<const int4*>(np + 3));
+            const bool h0 = box32(r, a.x, a.y, a.z, a.w, b.x, b.y, tlo, thi);
+            const bool h1 = box32(r, b.z, b.w, c.x, c.y, c.z, c.w, tlo, thi);
+            if (h0 && h1) {
+                if (sp >= DF_STACK) {
+                    rt_set_status(status, RT_ERR_STACK_OVERFLOW);
+                    return;
+                }
+                stack[sp++] = d.y;
+                ref = d.x;
+                continue;
+            }
+            if (h0 || h1) {
+                ref = h0 ? d.x : d.y;
+                continue;
+            }
+        } else {
+            const int e = ~ref;
+            if (leaf(e >> 3, (e & 7) + 1)) return;
+        }
+        if (sp == 0) return;
+        ref = stack[--sp];
+    }
+}
+
+// FP32 upper end of a box interval that covers the FP64 parameter t.
+__device__ __forceinline__ float up32(double t) { return __double2float_ru(t) * (1.0f + 1e-6f) + 1e-30f; }
+
+// Closest hit with t > tmin, skipping triangle `skip` (original ids): the
+// smallest t, then among hits within DF_TIE_TOL of it the lowest triangle id.
+__device__ int closest_hit64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const Ray64& r,
+                             double tmin, int skip, double& t_out, int32_t* status) {
+    double bt = INFINITY;
+    float thi = INFINITY;
+    walk(nodes, r, (float)tmin * 0.5f, thi, status, [&](int first, int count) {
+        for (int k = first; k < first + count; ++k) {
+            const float4 p0 = __ldg(tris + 3 * k);
+            if (__float_as_int(p0.w) == skip) continue;
+            double t;
+            if (!tri_hit64(r, p0, __ldg(tris + 3 * k + 1), __ldg(tris + 3 * k + 2), t)) continue;
+            if (t > tmin && t < bt) {
+                bt = t;
+                thi = up32(bt + DF_TIE_TOL * bt);
+            }
+        }
+        return false;
+    });
+    t_out = bt;
+    if (!(bt < INFINITY)) return -1;
+    const double tmax = bt + DF_TIE_TOL * bt;
+    const float thi2 = up32(tmax);
+    int best = -1;
+    walk(nodes, r, (float)tmin * 0.5f, thi2, status, [&](int first, int count) {
+        for (int k = first; k < first + count; ++k) {
+            const float4 p0 = __ldg(tris + 3 * k);
+            const int id = __float_as_int(p0.w);
+            if (id == skip || (best >= 0 && id >= best)) continue;
+            double t;
+            if (!tri_hit64(r, p0, __ldg(tris + 3 * k + 1), __ldg(tris + 3 * k + 2), t)) continue;
+            if (t > tmin && t <= tmax) best = id;
+        }
+        return false;
+    });
+    return best;
+}
+
+// Any hit with tlo < t < thi, skipping triangle `skip`.
+__device__ bool any_hit64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const Ray64& r,
+                          double tlo, double thi, int skip, int32_t* status) {
+    bool hit = false;
+    const float fhi = up32(thi);
+    walk(nodes, r, (float)tlo * 0.5f, fhi, status, [&](int first, int count) {
+        for (int k = first; k < first + count; ++k) {
+            const float4 p0 = __ldg(tris + 3 * k);
+            if (__float_as_int(p0.w) == skip) continue;
+            double t;
+            if (!tri_hit64(r, p0, __ldg(tris + 3 * k + 1), __ldg(tris + 3 * k + 2), t)) continue;
+            if (t > tlo && t < thi) {
+                hit = true;
+                return true;
+            }
+        }
+        return false;
+    });
+    return hit;
+}
+
+struct Scn {
+    const BvhNode* nodes;
+    const float4* tris;      // BVH order, original id in v0.w
+    const double* n64;       // 4 per triangle: unit normal, n.v0
+    double eps;
+};
+
+__device__ __forceinline__ void load_n(const double* n64, int t, double n[3]) {
+    n[0] = __ldg(n64 + 4 * t);
+    n[1] = __ldg(n64 + 4 * t + 1);
+    n[2] = __ldg(n64 + 4 * t + 2);
+}
+
+// ------------------------------------------------------------------ 1. rays
+// Hits of ray i at bounce b: tri[b * N + i] (-1 after the ray escaped) and the
+// FP64 point pt[(b * N + i) * 3 + c].  The point and the reflected direction use
+// uncontracted FP64 operations, as the definition writes them.
+__global__ void __launch_bounds__(DF_THREADS) k_df_rays(int64_t N, int D, double tx0, double tx1, double tx2,
+                                                        const float* __restrict__ z, Scn S, int32_t* __restrict__ tri,
+                                                        double* __restrict__ pt, int32_t* status) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const float3 f = launch_dir(i, __ldg(z + i));
+        Ray64 r;
+        r.o[0] = tx0;
+        r.o[1] = tx1;
+        r.o[2] = tx2;
+        r.d[0] = f.x;
+        r.d[1] = f.y;
+        r.d[2] = f.z;
+        int prev = -1;
+        int b = 0;
+        for (; b < D; ++b) {
+            ray64_init(r);
+            double th;
+            const int t = closest_hit64(S.nodes, S.tris, r, S.eps, prev, th, status);
+            if (t < 0) break;
+            double p[3], n[3];
+            for (int c = 0; c < 3; ++c) p[c] = __dadd_rn(r.o[c], __dmul_rn(th, r.d[c]));
+            tri[(int64_t)b * N + i] = t;
+            for (int c = 0; c < 3; ++c) pt[((int64_t)b * N + i) * 3 + c] = p[c];
+            load_n(S.n64, t, n);
+            const double dn = __dadd_rn(__dadd_rn(__dmul_rn(r.d[0], n[0]), __dmul_rn(r.d[1], n[1])),
+                                        __dmul_rn(r.d[2], n[2]));
+            const double dn2 = __dmul_rn(2.0, dn);
+            for (int c = 0; c < 3; ++c) {
+                r.d[c] = __dsub_rn(r.d[c], __dmul_rn(dn2, n[c]));
+                r.o[c] = p[c];
+            }
+            prev = t;
+        }
+        for (; b < D; ++b) tri[(int64_t)b * N + i] = -1;
+    }
+}
+
+// ------------------------------------------------------------------ 2. next-event estimation
+// Pair index q = s * R + r (receivers fastest, so a warp shares its origin).
+__global__ void __launch_bounds__(DF_THREADS) k_df_nee(int64_t N, int D, int R, double tx0, double tx1, double tx2,
+                                                       const double* __restrict__ rx, const int32_t* __restrict__ tri,
+                                                       const double* __restrict__ pt, Scn S, uint32_t* __restrict__ mask,
+                                                       int64_t W, int32_t* status) {
+    const int64_t total = N * D * (int64_t)R;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(q % R);
+        const int64_t s = q / R;
+        const int64_t i = s / D;
+        const int b = (int)(s - i * D);
+        const int t = __ldg(tri + (int64_t)b * N + i);
+        if (t < 0) continue;
+        double p[3], pv[3], n[3], x[3];
+        for (int c = 0; c < 3; ++c) {
+            p[c] = __ldg(pt + ((int64_t)b * N + i) * 3 + c);
+            x[c] = __ldg(rx + 3 * (int64_t)r + c);
+        }
+        if (b == 0) {
+            pv[0] = tx0;
+            pv[1] = tx1;
+            pv[2] = tx2;
+        } else {
+            for (int c = 0; c < 3; ++c) pv[c] = __ldg(pt + ((int64_t)(b - 1) * N + i) * 3 + c);
+        }
+        load_n(S.n64, t, n);
+        const double side_in = (pv[0] - p[0]) * n[0] + (pv[1] - p[1]) * n[1] + (pv[2] - p[2]) * n[2];
+        const double side_rx = (x[0] - p[0]) * n[0] + (x[1] - p[1]) * n[1] + (x[2] - p[2]) * n[2];
+        if (!((side_in > 0.0 && side_rx > 0.0) || (side_in < 0.0 && side_rx < 0.0))) continue;
+        Ray64 ray;
+        for (int c = 0; c < 3; ++c) {
+            ray.o[c] = p[c];
+            ray.d[c] = x[c] - p[c];
+        }
+        const double len = sqrt(ray.d[0] * ray.d[0] + ray.d[1] * ray.d[1] + ray.d[2] * ray.d[2]);
+        if (!(len > S.eps)) continue;
+        ray64_init(ray);
+        if (any_hit64(S.nodes, S.tris, ray, S.eps / len, 1.0 - S.eps / len, t, status)) continue;
+        atomicOr(mask + (int64_t)r * W + (s >> 5), 1u << (s & 31));
+    }
+}
+
+// ------------------------------------------------------------------ 3. ordered emission
+// One block per receiver: exclusive prefix of the word popcounts within the row
+// (word_off) and the row total (cnt).
+__global__ void k_df_row_scan(int64_t W, const uint32_t* __restrict__ mask, int32_t* __restrict__ word_off,
+                              int64_t* __restrict__ cnt) {
+    __shared__ int32_t warp_sum[32];
+    __shared__ int64_t carry;
+    const int r = blockIdx.x;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t base = 0; base < W; base += blockDim.x) {
+        const int64_t w = base + threadIdx.x;
+        const int v = w < W ? __popc(__ldg(mask + (int64_t)r * W + w)) : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int ws = lane < nw ? warp_sum[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, ws, o);
+                if (lane >= o) ws += y;
+            }
+            if (lane < nw) warp_sum[lane] = ws;
+        }
+        __syncthreads();
+        const int before = (wid > 0 ? warp_sum[wid - 1] : 0) + x - v;
+        if (w < W) word_off[(int64_t)r * W + w] = (int32_t)(carry + before);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_sum[nw - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cnt[r] = carry;
+}
+
+// Single block: rx_off[0] = 0, rx_off[r + 1] = rx_off[r] + cnt[r].
+__global__ void k_df_offsets(int R, const int64_t* __restrict__ cnt, int64_t* __restrict__ off) {
+    __shared__ int64_t warp_sum[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        off[0] = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = 0; base < R; base += blockDim.x) {
+        const int r = base + threadIdx.x;
+        const int64_t v = r < R ? cnt[r] : 0;
+        int64_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int64_t ws = lane < nw ? warp_sum[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, ws, o);
+                if (lane >= o) ws += y;
+            }
+            if (lane < nw) warp_sum[lane] = ws;
+        }
+        __syncthreads();
+        const int64_t incl = (wid > 0 ? warp_sum[wid - 1] : 0) + x;
+        if (r < R) off[r + 1] = carry + incl;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_sum[nw - 1];
+        __syncthreads();
+    }
+}
+
+__global__ void k_df_expand(int R, int64_t W, const uint32_t* __restrict__ mask, const int32_t* __restrict__ word_off,
+                            const int64_t* __restrict__ rx_off, int32_t* __restrict__ out_rx,
+                            int64_t* __restrict__ out_src) {
+    const int64_t total = (int64_t)R * W;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t bits = __ldg(mask + q);
+        if (!bits) continue;
+        const int r = (int)(q / W);
+        const int64_t w = q - (int64_t)r * W;
+        int64_t o = __ldg(rx_off + r) + __ldg(word_off + q);
+        while (bits) {
+            const int k = __ffs(bits) - 1;
+            bits &= bits - 1;
+            out_rx[o] = r;
+            out_src[o] = w * 32 + k;
+            ++o;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ records
+struct D3 {
+    double x, y, z;
+};
+__device__ __forceinline__ D3 d3(double x, double y, double z) { return D3{x, y, z}; }
+__device__ __forceinline__ D3 sub(D3 a, D3 b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ D3 scl(double s, D3 a) { return d3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ double dotd(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ D3 crossd(D3 a, D3 b) {
+    return d3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ D3 unitd(D3 a) { return scl(1.0 / sqrt(dotd(a, a)), a); }
+
+// theta_hat, phi_hat of unit direction k (phi = 0 for a vertical direction).
+__device__ __forceinline__ void sph_basis(D3 k, D3* th, D3* ph) {
+    const double st = sqrt(k.x * k.x + k.y * k.y);
+    double cp = 1.0, sp = 0.0;
+    if (st > 0.0) {
+        cp = k.x / st;
+        sp = k.y / st;
+    }
+    *th = d3(k.z * cp, k.z * sp, -st);
+    *ph = d3(-sp, cp, 0.0);
+}
+
+// unit(k x n), or where k is (numerically) along n, `fb` made orthogonal to k.
+__device__ __forceinline__ D3 perp_or(D3 k, D3 n, D3 fb) {
+    const D3 c = crossd(k, n);
+    if (sqrt(dotd(c, c)) > 1e-12) return unitd(c);
+    return unitd(sub(fb, scl(dotd(fb, k), k)));
+}
+
+struct RecOut {
+    int32_t* depth;
+    int32_t* tri;      // D x P
+    double* pts;       // P x (D + 2) x 3
+    double* tau;
+    float* len;        // d_last
+    int2* mc;          // D x P
+    float4* Dm;        // (D + 1) x P
+    float4* dir;       // 2 x P
+    float4* scat;      // P
+};
+
+__global__ void k_df_records(int64_t P, int64_t N, int D, double tx0, double tx1, double tx2,
+                             const double* __restrict__ rx, const int32_t* __restrict__ prx,
+                             const int64_t* __restrict__ src, const int32_t* __restrict__ hit_tri,
+                             const double* __restrict__ hit_pt, const double* __restrict__ n64,
+                             const int32_t* __restrict__ tri_material, const uint8_t* __restrict__ is_pec,
+                             RecOut O) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = src[i];
+        const int64_t ray = s / D;
+        const int j = (int)(s - ray * D) + 1;
+        const int r = prx[i];
+        D3 pts[RT_MAX_DEPTH + 2];
+        pts[0] = d3(tx0, tx1, tx2);
+        for (int b = 1; b <= j; ++b) {
+            const double* q = hit_pt + ((int64_t)(b - 1) * N + ray) * 3;
+            pts[b] = d3(q[0], q[1], q[2]);
+        }
+        pts[j + 1] = d3(rx[3 * (int64_t)r], rx[3 * (int64_t)r + 1], rx[3 * (int64_t)r + 2]);
+        double* po = O.pts + i * (D + 2) * 3;
+        for (int b = 0; b < D + 2; ++b) {
+            const D3 q = b <= j + 1 ? pts[b] : d3(0.0, 0.0, 0.0);
+            po[3 * b] = q.x;
+            po[3 * b + 1] = q.y;
+            po[3 * b + 2] = q.z;
+        }
+        O.depth[i] = j;
+        int tt[RT_MAX_DEPTH];
+        for (int b = 0; b < D; ++b) {
+            tt[b] = b < j ? hit_tri[(int64_t)b * N + ray] : -1;
+            O.tri[(int64_t)b * P + i] = tt[b];
+        }
+        D3 k[RT_MAX_DEPTH + 2];
+        double ell = 0.0, dl = 0.0;
+        for (int b = 1; b <= j + 1; ++b) {
+            const D3 dv = sub(pts[b], pts[b - 1]);
+            const double db = sqrt(dotd(dv, dv));
+            k[b] = scl(1.0 / db, dv);
+            if (b <= j) ell += db;
+            else dl = db;
+        }
+        O.tau[i] = (ell + dl) / RT_C0;
+        O.len[i] = (float)dl;
+        D3 out_p, out_q;
+        sph_basis(k[1], &out_p, &out_q);
+        for (int b = 1; b <= j; ++b) {
+            const int t = tt[b - 1];
+            D3 n = d3(n64[4 * t], n64[4 * t + 1], n64[4 * t + 2]);
+            if (dotd(k[b], n) > 0.0) n = scl(-1.0, n);       // facing the incident wave
+            const double cos_i = -dotd(k[b], n);
+            const D3 e_perp = perp_or(k[b], n, out_p);
+            const D3 in_q = crossd(e_perp, k[b]);
+            O.Dm[(int64_t)(b - 1) * P + i] = make_float4((float)dotd(e_perp, out_p), (float)dotd(e_perp, out_q),
+                                                         (float)dotd(in_q, out_p), (float)dotd(in_q, out_q));
+            const int mt = tri_material[t];
+            O.mc[(int64_t)(b - 1) * P + i] = make_int2(mt | (is_pec[mt] ? MAT_PEC : 0), __float_as_int((float)cos_i));
+            if (b < j) {
+                out_p = e_perp;
+                out_q = crossd(e_perp, k[b + 1]);
+                continue;
+            }
+            // diffuse bounce: pattern cosines and the scattered basis
+            const D3 ks = k[j + 1];
+            const D3 kr = sub(k[j], scl(2.0 * dotd(k[j], n), n));
+            O.scat[i] = make_float4((float)dotd(ks, n), (float)(-dotd(k[j], ks)), (float)dotd(kr, ks),
+                                    (float)(1.0 / dl));
+            const D3 sp = perp_or(ks, n, e_perp);
+            const D3 sq = crossd(sp, ks);
+            D3 th, ph;
+            sph_basis(scl(-1.0, ks), &th, &ph);
+            O.Dm[(int64_t)j * P + i] = make_float4((float)dotd(th, sp), (float)dotd(th, sq), (float)dotd(ph, sp),
+                                                   (float)dotd(ph, sq));
+        }
+        for (int b = j; b < D; ++b) O.mc[(int64_t)b * P + i] = make_int2(0, 0);
+        O.dir[i] = make_float4((float)k[1].x, (float)k[1].y, (float)k[1].z, 0.0f);
+        O.dir[P + i] = make_float4((float)-k[j + 1].x, (float)-k[j + 1].y, (float)-k[j + 1].z, 0.0f);
+    }
+}
+
+// ------------------------------------------------------------------ scattering pattern
+// One lobe exp(lambda c) / a(lambda, cos theta_i) evaluated as
+// exp(lambda (c - 1)) / (a e^-lambda) so that nothing overflows; a is the smooth
+// step s(t, cos theta_i) between the hemispherical integrals with the axis on the
+// normal (U) and opposite it (L).  With dlog != nullptr also returns
+// d log g / d lambda.
+__device__ __forceinline__ float lobe(float lam, float c, float ci, float* dlog) {
+    const float q = expf(-lam);
+    const float em = -expm1f(-lam);                       // 1 - e^-lambda
+    const float k2 = 2.0f * DF_PI / lam;
+    const float Uh = k2 * em;                              // U e^-lambda
+    const float Lh = Uh * q;                               // L e^-lambda
+    const float nn = (1.6988f * lam + 10.8438f) * lam;
+    const float dn = (lam + 6.2201f) * lam + 10.2415f;
+    const float t = sqrtf(lam) * nn / dn;
+    const float e1 = expm1f(t * (1.0f + ci));
+    const float e2 = expm1f(t);
+    const float e3 = expf(t * ci);
+    const float Dd = e2 * (e3 + 1.0f);
+    const float s = e1 / Dd;
+    const float ah = s * Uh + (1.0f - s) * Lh;
+    const float g = expf(lam * (c - 1.0f)) / ah;
+    if (dlog) {
+        const float dUh = -Uh / lam + k2 * q;
+        const float dLh = -Lh / lam + k2 * (2.0f * q * q - q);
+        const float dt = t * (0.5f / lam + (3.3976f * lam + 10.8438f) / nn - (2.0f * lam + 6.2201f) / dn);
+        const float dN = (1.0f + ci) * (e1 + 1.0f);
+        const float dD = (e2 + 1.0f) * (e3 + 1.0f) + e2 * ci * e3;
+        const float ds = (dN - s * dD) / Dd;
+        const float dah = s * dUh + (1.0f - s) * dLh + (Uh - Lh) * ds * dt;
+        *dlog = (c - 1.0f) - dah / ah;
+    }
+    return g;
+}
+
+// f_s of Eq. trainable_scattering_pattern; pr = [S, K_x, w_1, w_2, w_3, lambda_2,
+// lambda_3, -]; with df != nullptr also df/dw_1, df/dw_2, df/dw_3, df/dlambda_2,
+// df/dlambda_3.
+__device__ __forceinline__ float pattern(const float* pr, float4 geo, float ci, float* df) {
+    float dl2, dl3;
+    const float g2 = lobe(pr[5], geo.y, ci, df ? &dl2 : nullptr);
+    const float g3 = lobe(pr[6], geo.z, ci, df ? &dl3 : nullptr);
+    if (df) {
+        df[0] = geo.x * (1.0f / DF_PI);
+        df[1] = g2;
+        df[2] = g3;
+        df[3] = pr[3] * g2 * dl2;
+        df[4] = pr[4] * g3 * dl3;
+    }
+    return pr[2] * (1.0f / DF_PI) * geo.x + pr[3] * g2 + pr[4] * g3;
+}
+
+// ------------------------------------------------------------------ fields
+struct DfArgs {
+    int64_t P;
+    const int32_t* depth;
+    const int2* mc;
+    const float4* Dm;
+    const float4* geo;       // (k_s.n, -k_i.k_s, k_r.k_s, 1/d_last)
+    const float* eps;
+    const float* sig;
+    const float* scat;       // M x 8
+    float inv_eps0w;
+    float amp;               // lambda / (4 pi) sqrt(g_T g_R) sqrt(4 pi / N)
+};
+
+__device__ __forceinline__ void mat_params(const DfArgs& A, int2 m, float2& eta, bool& pec, int& mat, float& c) {
+    pec = (m.x & MAT_PEC) != 0;
+    mat = m.x & ~MAT_PEC;
+    c = __int_as_float(m.y);
+    eta = make_float2(__ldg(A.eps + mat), -__ldg(A.sig + mat) * A.inv_eps0w);
+}
+
+__device__ __forceinline__ float r_spec(float S) { return sqrtf(fmaxf(0.0f, 1.0f - S * S)); }
+
+__global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, float2* __restrict__ a, const double* __restrict__ tau_in,
+                                                double* __restrict__ tau_out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.P; i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = A.depth[i];
+        float2 E0 = make_float2(1.0f, 0.0f), E1 = make_float2(0.0f, 0.0f);
+        float2 u0 = E0, u1 = E1;
+        int mat = 0;
+        float ci = 1.0f;
+        for (int b = 0; b < j; ++b) {
+            const float4 D = __ldg(A.Dm + (int64_t)b * A.P + i);
+            const float2 v0 = cadd(cscale(D.x, E0), cscale(D.y, E1));
+            const float2 v1 = cadd(cscale(D.z, E0), cscale(D.w, E1));
+            float2 eta, rp, rl, d0, d1;
+            bool pec;
+            mat_params(A, __ldg(A.mc + (int64_t)b * A.P + i), eta, pec, mat, ci);
+            if (pec) {
+                rp = make_float2(-1.0f, 0.0f);
+                rl = make_float2(1.0f, 0.0f);
+            } else {
+                fresnel<false>(eta, ci, rp, rl, d0, d1);
+            }
+            u0 = cmul(rp, v0);
+            u1 = cmul(rl, v1);
+            if (b + 1 < j) {
+                const float R = r_spec(__ldg(A.scat + 8 * mat));
+                E0 = cscale(R, u0);
+                E1 = cscale(R, u1);
+            }
+        }
+        const float nu = sqrtf(u0.x * u0.x + u0.y * u0.y + u1.x * u1.x + u1.y * u1.y);
+        const float* pr = A.scat + 8 * mat;
+        float prm[8];
+        for (int c = 0; c < 8; ++c) prm[c] = __ldg(pr + c);
+        const float4 geo = __ldg(A.geo + i);
+        const float f = pattern(prm, geo, ci, nullptr);
+        const float4 Dl = __ldg(A.Dm + (int64_t)j * A.P + i);
+        const float Kx = prm[1];
+        const float pol = Dl.x * sqrtf(fmaxf(0.0f, 1.0f - Kx)) + Dl.y * sqrtf(fmaxf(0.0f, Kx));
+        a[i] = make_float2(A.amp * prm[0] * sqrtf(fmaxf(f, 0.0f)) * nu * pol * geo.w, 0.0f);
+        if (tau_out) tau_out[i] = tau_in[i];
+    }
+}
+
+// Adjoint: every quantity is real-valued in a (chi = 0), so dL/dtheta =
+// Re(g) da/dtheta.  The field magnitude nu = |u| depends on eta of every bounce:
+// with the row vector l = conj(u)^T / nu walked backwards through the chain,
+// dnu/d eta_b = R_b l . diag(dr_perp, dr_par) v_b (holomorphic in eta), so
+// dnu/d eps_r = Re(.) and dnu/d sigma = Im(.) / (eps0 omega).
+// Per-material sums go to shared memory (MAXM > 0) or straight to global atomics.
+template <int MAXM>
+__global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restrict__ ga, float* __restrict__ geps,
+                                                float* __restrict__ gsig, float* __restrict__ gscat, int n_mat) {
+    __shared__ float acc[MAXM > 0 ? MAXM * 9 : 1];
+    if (MAXM > 0) {
+        for (int k = threadIdx.x; k < n_mat * 9; k += blockDim.x) acc[k] = 0.0f;
+        __syncthreads();
+    }
+    auto add = [&](int m, int c, float v) {
+        if (v == 0.0f) return;
+        if (MAXM > 0) {
+            atomicAdd(&acc[m * 9 + c], v);
+        } else if (c == 0) {
+            if (geps) atomicAdd(geps + m, v);
+        } else if (c == 1) {
+            if (gsig) atomicAdd(gsig + m, v);
+        } else if (gscat) {
+            atomicAdd(gscat + 8 * m + (c - 2), v);
+        }
+    };
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.P; i += (int64_t)gridDim.x * blockDim.x) {
+        const float g = ga[i].x;
+        if (g == 0.0f) continue;
+        const int j = A.depth[i];
+        float2 v0s[RT_MAX_DEPTH], v1s[RT_MAX_DEPTH], rps[RT_MAX_DEPTH], rls[RT_MAX_DEPTH];
+        float4 Ds[RT_MAX_DEPTH];
+        int mats[RT_MAX_DEPTH];
+        bool pecs[RT_MAX_DEPTH];
+        float cis[RT_MAX_DEPTH], Rs[RT_MAX_DEPTH];
+        float2 E0 = make_float2(1.0f, 0.0f), E1 = make_float2(0.0f, 0.0f), u0 = E0, u1 = E1;
+#pragma unroll
+        for (int b = 0; b < RT_MAX_DEPTH; ++b) {
+            if (b >= j) break;
+            const float4 D = __ldg(A.Dm + (int64_t)b * A.P + i);
+            Ds[b] = D;
+            const float2 v0 = cadd(cscale(D.x, E0), cscale(D.y, E1));
+            const float2 v1 = cadd(cscale(D.z, E0), cscale(D.w, E1));
+            float2 eta, rp, rl, d0, d1;
+            mat_params(A, __ldg(A.mc + (int64_t)b * A.P + i), eta, pecs[b], mats[b], cis[b]);
+            if (pecs[b]) {
+                rp = make_float2(-1.0f, 0.0f);
+                rl = make_float2(1.0f, 0.0f);
+            } else {
+                fresnel<false>(eta, cis[b], rp, rl, d0, d1);
+            }
+            v0s[b] = v0;
+            v1s[b] = v1;
+            rps[b] = rp;
+            rls[b] = rl;
+            u0 = cmul(rp, v0);
+            u1 = cmul(rl, v1);
+            Rs[b] = b + 1 < j ? r_spec(__ldg(A.scat + 8 * mats[b])) : 1.0f;
+            E0 = cscale(Rs[b], u0);
+            E1 = cscale(Rs[b], u1);
+        }
+        const int md = mats[j - 1];
+        float prm[8];
+        for (int c = 0; c < 8; ++c) prm[c] = __ldg(A.scat + 8 * md + c);
+        const float nu = sqrtf(u0.x * u0.x + u0.y * u0.y + u1.x * u1.x + u1.y * u1.y);
+        const float4 geo = __ldg(A.geo + i);
+        float df[5];
+        const float f = pattern(prm, geo, cis[j - 1], df);
+        const float sf = sqrtf(fmaxf(f, 0.0f));
+        const float4 Dl = __ldg(A.Dm + (int64_t)j * A.P + i);
+        const float Kx = fminf(fmaxf(prm[1], 1e-12f), 1.0f - 1e-7f);
+        const float sq1 = sqrtf(1.0f - Kx), sq2 = sqrtf(Kx);
+        const float pol = Dl.x * sq1 + Dl.y * sq2;
+        const float C = A.amp * geo.w;
+        const float S = prm[0];
+        // diffuse material: S, K_x, pattern
+        add(md, 2, g * C * sf * nu * pol);
+        add(md, 3, g * C * S * sf * nu * (-0.5f * Dl.x / sq1 + 0.5f * Dl.y / sq2));
+        if (f > 0.0f) {
+            const float dAdf = g * C * S * nu * pol * 0.5f / sf;
+            for (int c = 0; c < 5; ++c) add(md, 4 + c, dAdf * df[c]);
+        }
+        if (!(nu > 0.0f)) continue;
+        // reverse walk for d nu / d eta_b and d nu / d R_b
+        const float dAnu = g * C * S * sf * pol / nu;
+        float2 l0 = make_float2(u0.x * dAnu, -u0.y * dAnu), l1 = make_float2(u1.x * dAnu, -u1.y * dAnu);
+        for (int b = j - 1; b >= 0; --b) {
+            const float R = Rs[b];
+            if (!pecs[b]) {
+                float2 eta, rp, rl, d0, d1;
+                bool pec;
+                int mt;
+                float c;
+                mat_params(A, __ldg(A.mc + (int64_t)b * A.P + i), eta, pec, mt, c);
+                fresnel<true>(eta, c, rp, rl, d0, d1);
+                const float2 w = cscale(R, cadd(cmul(l0, cmul(d0, v0s[b])), cmul(l1, cmul(d1, v1s[b]))));
+                add(mats[b], 0, w.x);
+                add(mats[b], 1, w.y * A.inv_eps0w);
+            }
+            if (b + 1 < j) {
+                const float2 h = cadd(cmul(l0, cmul(rps[b], v0s[b])), cmul(l1, cmul(rls[b], v1s[b])));
+                const float S_b = __ldg(A.scat + 8 * mats[b]);
+                if (R > 0.0f) add(mats[b], 2, h.x * (-S_b / R));
+            }
+            const float2 m0 = cscale(R, cmul(l0, rps[b])), m1 = cscale(R, cmul(l1, rls[b]));
+            const float4 D = Ds[b];
+            l0 = cadd(cscale(D.x, m0), cscale(D.z, m1));
+            l1 = cadd(cscale(D.y, m0), cscale(D.w, m1));
+        }
+    }
+    if (MAXM > 0) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < n_mat * 9; k += blockDim.x) {
+            const float v = acc[k];
+            if (v == 0.0f) continue;
+            const int m = k / 9, c = k - 9 * m;
+            if (c == 0) {
+                if (geps) atomicAdd(geps + m, v);
+            } else if (c == 1) {
+                if (gsig) atomicAdd(gsig + m, v);
+            } else if (gscat) {
+                atomicAdd(gscat + 8 * m + (c - 2), v);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ specular share
+__global__ void k_spec_reduce(int64_t P, const int32_t* __restrict__ depth, const int2* __restrict__ mc,
+                              const float* __restrict__ scat, const float2* __restrict__ a, float2* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        const int q = depth[i];
+        float fac = 1.0f;
+        for (int b = 0; b < q; ++b) fac *= r_spec(__ldg(scat + 8 * (__ldg(mc + (int64_t)b * P + i).x & ~MAT_PEC)));
+        const float2 v = a[i];
+        out[i] = make_float2(fac * v.x, fac * v.y);
+    }
+}
+
+template <int MAXM>
+__global__ void __launch_bounds__(256) k_spec_reduce_bwd(int64_t P, const int32_t* __restrict__ depth,
+                                                         const int2* __restrict__ mc, const float* __restrict__ scat,
+                                                         const float2* __restrict__ a_out, const float2* __restrict__ g,
+                                                         float2* __restrict__ ga, float* __restrict__ gscat, int n_mat) {
+    __shared__ float acc[MAXM > 0 ? MAXM : 1];
+    if (MAXM > 0) {
+        for (int k = threadIdx.x; k < n_mat; k += blockDim.x) acc[k] = 0.0f;
+        __syncthreads();
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        const int q = depth[i];
+        float fac = 1.0f;
+        for (int b = 0; b < q; ++b) fac *= r_spec(__ldg(scat + 8 * (__ldg(mc + (int64_t)b * P + i).x & ~MAT_PEC)));
+        const float2 gi = g[i];
+        if (ga) ga[i] = make_float2(fac * gi.x, fac * gi.y);
+        if (!gscat) continue;
+        const float2 ao = a_out[i];
+        const float h = gi.x * ao.x + gi.y * ao.y;   // Re(conj(g) a_out) = fac dL/dfac
+        if (h == 0.0f) continue;
+        for (int b = 0; b < q; ++b) {
+            const int m = __ldg(mc + (int64_t)b * P + i).x & ~MAT_PEC;
+            const float S = __ldg(scat + 8 * m);
+            const float R2 = fmaxf(1.0f - S * S, 1e-30f);
+            const float v = h * (-S / R2);
+            if (MAXM > 0) atomicAdd(&acc[m], v);
+            else atomicAdd(gscat + 8 * m, v);
+        }
+    }
+    if (MAXM > 0 && gscat) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < n_mat; k += blockDim.x)
+            if (acc[k] != 0.0f) atomicAdd(gscat + 8 * k, acc[k]);
+    }
+}
+
+// ------------------------------------------------------------------ per-receiver merge / split
+// One warp per receiver: dst holds receiver r's elements of src1 followed by its
+// elements of src2 (8-byte elements), and off_out[r] = off1[r] + off2[r].
+__global__ void k_rx_merge(int R, const int64_t* __restrict__ off1, const int64_t* __restrict__ off2,
+                           const uint64_t* __restrict__ s1, const uint64_t* __restrict__ s2, uint64_t* __restrict__ dst,
+                           int64_t* __restrict__ off_out) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t a0 = off1[r], a1 = off1[r + 1], b0 = off2[r], b1 = off2[r + 1];
+        const int64_t o = a0 + b0;
+        if (lane == 0) {
+            if (off_out) off_out[r] = o;
+            if (off_out && r == R - 1) off_out[R] = a1 + b1;
+        }
+        for (int64_t k = lane; k < a1 - a0; k += 32) dst[o + k] = s1[a0 + k];
+        for (int64_t k = lane; k < b1 - b0; k += 32) dst[o + (a1 - a0) + k] = s2[b0 + k];
+    }
+}
+
+__global__ void k_rx_split(int R, const int64_t* __restrict__ off1, const int64_t* __restrict__ off2,
+                           const uint64_t* __restrict__ src, uint64_t* __restrict__ d1, uint64_t* __restrict__ d2) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t a0 = off1[r], a1 = off1[r + 1], b0 = off2[r], b1 = off2[r + 1];
+        const int64_t o = a0 + b0;
+        if (d1)
+            for (int64_t k = lane; k < a1 - a0; k += 32) d1[a0 + k] = src[o + k];
+        if (d2)
+            for (int64_t k = lane; k < b1 - b0; k += 32) d2[b0 + k] = src[o + (a1 - a0) + k];
+    }
+}
+
+DfArgs make_df_args(const rt_paths* p, const float* eps, const float* sig, const float* scat, double freq,
+                    float gtx, float grx) {
+    DfArgs A;
+    A.P = p->P;
+    A.depth = p->d_depth;
+    A.mc = p->d_mc;
+    A.Dm = p->d_Dm;
+    A.geo = p->d_scat;
+    A.eps = eps;
+    A.sig = sig;
+    A.scat = scat;
+    A.inv_eps0w = (float)(1.0 / (RT_EPS0 * 2.0 * RT_PI * freq));
+    A.amp = (float)(RT_C0 / freq / (4.0 * RT_PI) * std::sqrt((double)gtx * (double)grx) *
+                    std::sqrt(4.0 * RT_PI / (double)p->n_rays));
+    return A;
+}
+
+rt_status check_diffuse(rt_ctx* ctx, const rt_paths* p, const float* eps, const float* sig, const float* scat,
+                        double freq, float gtx, float grx) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (!p || !eps || !sig || !scat) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument");
+    if (p->kind != 1) return rt_fail(ctx, RT_ERR_INVALID_ARG, "not a diffuse paths object (rt_trace_diffuse)");
+    if (!(freq > 0.0) || !std::isfinite(freq)) return rt_fail(ctx, RT_ERR_INVALID_ARG, "freq_hz must be > 0");
+    if (!(gtx > 0.0f) || !(grx > 0.0f) || !std::isfinite(gtx) || !std::isfinite(grx))
+        return rt_fail(ctx, RT_ERR_INVALID_ARG, "antenna gains must be > 0");
+    return RT_OK;
+}
+
+}  // namespace
+
+#define RT_EXPORT extern "C" __attribute__((visibility("default")))
+
+RT_EXPORT rt_status rt_trace_diffuse(rt_ctx* ctx, const rt_scene* scene, const double* tx_host, const double* rx_dev,
+                                     int32_t n_rx, int64_t n_rays, int32_t max_depth, rt_paths** out) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (!scene || !tx_host || !rx_dev || !out) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument");
+    if (scene->owns_tables_only) return rt_fail(ctx, RT_ERR_INVALID_ARG, "scene has no BVH (batch tables)");
+    if (n_rays < 1 || n_rays * max_depth > 2147483647LL || max_depth < 1 || max_depth > RT_MAX_DEPTH || n_rx < 1 ||
+        n_rx > (1 << 24))
+        return rt_fail(ctx, RT_ERR_INVALID_ARG, "bad sizes");
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(tx_host[c])) return rt_fail(ctx, RT_ERR_INVALID_ARG, "transmitter not finite");
+    const int64_t N = n_rays, D = max_depth, R = n_rx;
+    const int64_t W = (N * D + 31) / 32;
+    if (R * W > (int64_t)1 << 31)
+        return rt_fail(ctx, RT_ERR_INVALID_ARG, "n_rx x n_rays x max_depth too large for the visibility mask");
+    *out = nullptr;
+    cudaStream_t st = ctx->stream;
+    int32_t* status = rt_status_ptr(ctx);
+    // launch z table (one FP64 division and subtraction per ray, rounded to FP32)
+    std::vector<float> zh(N);
+    for (int64_t i = 0; i < N; ++i) zh[i] = (float)(1.0 - (double)(2 * i + 1) / (double)N);
+    float* z = nullptr;
+    int32_t* hit_tri = nullptr;
+    double* hit_pt = nullptr;
+    uint32_t* mask = nullptr;
+    int32_t* word_off = nullptr;
+    int64_t* cnt = nullptr;
+    int64_t* src = nullptr;
+    rt_paths* p = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** d, size_t b) {
+        if (e == cudaSuccess) e = cudaMallocAsync(d, b, st);
+    };
+    auto cleanup = [&]() {
+        void* tmp[] = {z, hit_tri, hit_pt, mask, word_off, cnt, src};
+        for (void* q : tmp)
+            if (q) cudaFreeAsync(q, st);
+    };
+    A((void**)&z, N * 4);
+    A((void**)&hit_tri, N * D * 4);
+    A((void**)&hit_pt, N * D * 3 * 8);
+    A((void**)&mask, R * W * 4);
+    A((void**)&word_off, R * W * 4);
+    A((void**)&cnt, R * 8);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(z, zh.data(), N * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mask, 0, R * W * 4, st);
+    if (e != cudaSuccess) {
+        cleanup();
+        return rt_cuda_fail(ctx, e, "diffuse trace buffers");
+    }
+    const Scn S{scene->d_nodes, scene->d_bvh_tris, scene->d_tri_n64, scene->eps};
+    k_df_rays<<<grid_of(ctx, N, DF_THREADS, 16), DF_THREADS, 0, st>>>(N, (int)D, tx_host[0], tx_host[1], tx_host[2],
+                                                                      z, S, hit_tri, hit_pt, status); RT_COUNT(ctx);
+    k_df_nee<<<grid_of(ctx, N * D * R, DF_THREADS, 16), DF_THREADS, 0, st>>>(
+        N, (int)D, (int)R, tx_host[0], tx_host[1], tx_host[2], rx_dev, hit_tri, hit_pt, S, mask, W, status); RT_COUNT(ctx);
+    k_df_row_scan<<<(int)R, 256, 0, st>>>(W, mask, word_off, cnt); RT_COUNT(ctx);
+    p = new rt_paths();
+    p->scene = scene;
+    p->stream = st;
+    p->D = (int)D;
+    p->R = (int)R;
+    p->kind = 1;
+    p->n_rays = N;
+    A((void**)&p->d_rx_offsets, (R + 1) * 8);
+    if (e == cudaSuccess) {
+        k_df_offsets<<<1, 1024, 0, st>>>((int)R, cnt, p->d_rx_offsets); RT_COUNT(ctx);
+        e = cudaGetLastError();
+    }
+    int64_t P = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned, p->d_rx_offsets + R, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) P = *ctx->h_pinned;
+    p->P = P;
+    const size_t Pa = P > 0 ? (size_t)P : 1;
+    A((void**)&src, Pa * 8);
+    A((void**)&p->d_rx, Pa * 4);
+    A((void**)&p->d_depth, Pa * 4);
+    A((void**)&p->d_tri, Pa * D * 4);
+    A((void**)&p->d_pts, Pa * (D + 2) * 3 * 8);
+    A((void**)&p->d_tau, Pa * 8);
+    A((void**)&p->d_len, Pa * 4);
+    A((void**)&p->d_mc, Pa * D * 8);
+    A((void**)&p->d_Dm, Pa * (D + 1) * 16);
+    A((void**)&p->d_dir, Pa * 2 * 16);
+    A((void**)&p->d_scat, Pa * 16);
+    if (e == cudaSuccess && P > 0) {
+        k_df_expand<<<grid_of(ctx, R * W, 256, 8), 256, 0, st>>>((int)R, W, mask, word_off, p->d_rx_offsets, p->d_rx,
+                                                                  src); RT_COUNT(ctx);
+        RecOut O{p->d_depth, p->d_tri, p->d_pts, p->d_tau, p->d_len, p->d_mc, p->d_Dm, p->d_dir, p->d_scat};
+        k_df_records<<<grid_of(ctx, P, 128, 16), 128, 0, st>>>(P, N, (int)D, tx_host[0], tx_host[1], tx_host[2], rx_dev,
+                                                               p->d_rx, src, hit_tri, hit_pt, scene->d_tri_n64,
+                                                               scene->d_tri_material, scene->d_is_pec, O); RT_COUNT(ctx);
+        e = cudaGetLastError();
+    }
+    cleanup();
+    if (e != cudaSuccess) {
+        rt_paths_free(p);
+        return rt_cuda_fail(ctx, e, "diffuse trace");
+    }
+    *out = p;
+    return RT_OK;
+}
+
+RT_EXPORT rt_status rt_eval_fields_diffuse(rt_ctx* ctx, const rt_paths* paths, const float* eps_r_dev,
+                                           const float* sigma_dev, const float* scat_dev, double freq_hz,
+                                           float gain_tx, float gain_rx, void* a_dev, double* tau_dev) {
+    rt_status s = check_diffuse(ctx, paths, eps_r_dev, sigma_dev, scat_dev, freq_hz, gain_tx, gain_rx);
+    if (s != RT_OK) return s;
+    if (!a_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null a_dev");
+    if (paths->P == 0) return RT_OK;
+    const DfArgs A = make_df_args(paths, eps_r_dev, sigma_dev, scat_dev, freq_hz, gain_tx, gain_rx);
+    k_df_fwd<<<grid_of(ctx, paths->P, 256, 8), 256, 0, ctx->stream>>>(A, (float2*)a_dev, paths->d_tau, tau_dev);
+    RT_COUNT(ctx);
+    RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}
+
+RT_EXPORT rt_status rt_eval_fields_diffuse_backward(rt_ctx* ctx, const rt_paths* paths, const float* eps_r_dev,
+                                                    const float* sigma_dev, const float* scat_dev, double freq_hz,
+                                                    float gain_tx, float gain_rx, const void* grad_a_dev,
+                                                    float* grad_eps_r_dev, float* grad_sigma_dev,
+                                                    float* grad_scat_dev) {
+    rt_status s = check_diffuse(ctx, paths, eps_r_dev, sigma_dev, scat_dev, freq_hz, gain_tx, gain_rx);
+    if (s != RT_OK) return s;
+    if (!grad_a_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null grad_a_dev");
+    if (paths->P == 0) return RT_OK;
+    const DfArgs A = make_df_args(paths, eps_r_dev, sigma_dev, scat_dev, freq_hz, gain_tx, gain_rx);
+    const int n_mat = paths->scene->n_materials;
+    const int grid = grid_of(ctx, paths->P, 256, 8);
+    const float2* ga = (const float2*)grad_a_dev;
+    if (n_mat <= 64)
+        k_df_bwd<64><<<grid, 256, 0, ctx->stream>>>(A, ga, grad_eps_r_dev, grad_sigma_dev, grad_scat_dev, n_mat);
+    else
+        k_df_bwd<0><<<grid, 256, 0, ctx->stream>>>(A, ga, grad_eps_r_dev, grad_sigma_dev, grad_scat_dev, n_mat);
+    RT_COUNT(ctx);
+    RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}
+
+RT_EXPORT rt_status rt_specular_reduction(rt_ctx* ctx, const rt_paths* paths, const float* scat_dev, const void* a_dev,
+                                          void* a_out_dev) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (!paths || !scat_dev || !a_dev || !a_out_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument");
+    if (paths->kind != 0) return rt_fail(ctx, RT_ERR_INVALID_ARG, "not a specular paths object");
+    if (paths->P == 0) return RT_OK;
+    k_spec_reduce<<<grid_of(ctx, paths->P, 256, 8), 256, 0, ctx->stream>>>(
+        paths->P, paths->d_depth, paths->d_mc, scat_dev, (const float2*)a_dev, (float2*)a_out_dev); RT_COUNT(ctx);
+    RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}
+
+RT_EXPORT rt_status rt_specular_reduction_backward(rt_ctx* ctx, const rt_paths* paths, const float* scat_dev,
+                                                   const void* a_out_dev, const void* grad_out_dev, void* grad_a_dev,
+                                                   float* grad_scat_dev) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (!paths || !scat_dev || !grad_out_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument");
+    if (grad_scat_dev && !a_out_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "grad_scat_dev needs a_out_dev");
+    if (paths->kind != 0) return rt_fail(ctx, RT_ERR_INVALID_ARG, "not a specular paths object");
+    if (paths->P == 0) return RT_OK;
+    const int n_mat = paths->scene->n_materials;
+    const int grid = grid_of(ctx, paths->P, 256, 8);
+    if (n_mat <= 1024)
+        k_spec_reduce_bwd<1024><<<grid, 256, 0, ctx->stream>>>(paths->P, paths->d_depth, paths->d_mc, scat_dev,
+                                                               (const float2*)a_out_dev, (const float2*)grad_out_dev,
+                                                               (float2*)grad_a_dev, grad_scat_dev, n_mat);
+    else
+        k_spec_reduce_bwd<0><<<grid, 256, 0, ctx->stream>>>(paths->P, paths->d_depth, paths->d_mc, scat_dev,
+                                                            (const float2*)a_out_dev, (const float2*)grad_out_dev,
+                                                            (float2*)grad_a_dev, grad_scat_dev, n_mat);
+    RT_COUNT(ctx);
+    RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}
+
+RT_EXPORT rt_status rt_rx_merge(rt_ctx* ctx, int32_t n_rx, const int64_t* off1_dev, const int64_t* off2_dev,
+                                const void* src1_dev, const void* src2_dev, void* dst_dev, int64_t* off_out_dev) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (n_rx < 1 || !off1_dev || !off2_dev || !src1_dev || !src2_dev || !dst_dev)
+        return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument or n_rx < 1");
+    const int grid = grid_of(ctx, (int64_t)n_rx * 32, 256, 16);
+    k_rx_merge<<<grid, 256, 0, ctx->stream>>>(n_rx, off1_dev, off2_dev, (const uint64_t*)src1_dev,
+                                              (const uint64_t*)src2_dev, (uint64_t*)dst_dev, off_out_dev); RT_COUNT(ctx);
+    RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}
+
+RT_EXPORT rt_status rt_rx_split(rt_ctx* ctx, int32_t n_rx, const int64_t* off1_dev, const int64_t* off2_dev,
+                                const void* src_dev, void* dst1_dev, void* dst2_dev) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (n_rx < 1 || !off1_dev || !off2_dev || !src_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument or n_rx < 1");
+    const int grid = grid_of(ctx, (int64_t)n_rx * 32, 256, 16);
+    k_rx_split<<<grid, 256, 0, ctx->stream>>>(n_rx, off1_dev, off2_dev, (const uint64_t*)src_dev, (uint64_t*)dst1_dev,
+                                              (uint64_t*)dst2_dev); RT_COUNT(ctx);
+    RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}

@@ -104,6 +104,10 @@ struct rt_paths {
     int32_t n_scenes = 1;              // batch output: number of traced scenes
     int64_t* h_scene_rx_off = nullptr; // batch output: receiver offset of each scene (n_scenes + 1)
     int64_t* h_scene_tri_off = nullptr;// batch output: triangle-id offset of each scene (n_scenes + 1)
+    int32_t kind = 0;                  // 0: specular chains; 1: diffuse paths (last bounce diffuse)
+    int64_t n_rays = 0;                // diffuse paths: launch rays that sampled the surfaces
+    float4* d_scat = nullptr;          // diffuse paths, P: (k_s.n, -k_i.k_s, k_r.k_s, 1/d_last) at the
+                                       // diffuse point (n facing the incident wave)
 };
 
 // ---------------------------------------------------------------- error helpers
