@@ -356,6 +356,9 @@ def run_ours(args):
     # ---------------- eval_fields / adjoint at an HBM-bound size
     fields_hbm = time_fields_hbm(rt, ctx, scene, sc, flush)
 
+    # ---------------- diffuse reflection: trace, calibration step, field kernels
+    diffuse = time_diffuse(rt, ctx, flush, args)
+
     # ---------------- learned form (neural materials) vs the plain per-object form
     learned = time_learned(rt, ctx, args)
 
@@ -388,6 +391,7 @@ def run_ours(args):
             "calibration_ms": {k: round(v, 4) for k, v in cal.items()},
             "calibration_indoor": calib_indoor,
             "fields_hbm": fields_hbm,
+            "diffuse": diffuse,
             "learned": learned,
             "batch": batch,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
@@ -733,6 +737,122 @@ def time_fields_hbm(rt, ctx, scene, sc, flush, reps=10, copies=1000):
             "peak_source": src}
 
 
+def time_diffuse(rt, ctx, flush, args, n_rx_step=4, n_rays_diffuse=20_000):
+    """Diffuse reflection on the indoor scene (256 receivers): the diffuse trace
+    (next-event estimation from every shoot-and-bounce hit), the calibration step
+    over specular + diffuse paths captured in one CUDA graph (eval_fields ->
+    specular share, eval_fields_diffuse -> per-receiver merge -> CFR + power MSE +
+    CFR adjoint -> split -> adjoints of both), and the diffuse field kernels alone
+    with their HBM roofline.  Algorithmic bytes per diffuse path of depth j:
+    forward 4 (depth) + 8 j (material, cos) + 16 (j + 1) (basis changes) + 16
+    (pattern cosines, 1/d) + 8 (a out) = 44 + 24 j; the adjoint reads the same
+    records and dL/da instead of writing a."""
+    import torch
+
+    import scenegen
+    sc = scenegen.indoor_diff()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    scene = rt.Scene.from_synthetic(ctx, sc)
+    rx = torch.tensor(sc.rx[::n_rx_step], dtype=torch.float64, device=dev)
+    R = rx.shape[0]
+    stream = torch.cuda.current_stream()
+
+    def ev_time(fn, reps):
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            fn()
+            e0.record(stream)
+            e0.synchronize()
+            out.append(s0.elapsed_time(e0))
+        return float(np.median(out))
+    ps = rt.trace_paths(ctx, scene, sc.tx, rx, sc.n_rays, sc.max_depth)
+    pd = rt.trace_diffuse(ctx, scene, sc.tx, rx, n_rays_diffuse, sc.max_depth)
+    trace_ms = ev_time(lambda: rt.trace_diffuse(ctx, scene, sc.tx, rx, n_rays_diffuse, sc.max_depth), 3)
+    fc, df, N = sc.f_center_hz, sc.delta_f_hz, sc.n_sub
+    eps = torch.tensor(sc.eps_r, device=dev)
+    sig = torch.tensor(sc.sigma, device=dev)
+    hidden = torch.tensor(scenegen.random_scattering(21, sc.n_materials), device=dev)
+    tau, off = rt.rx_merge(ctx, ps.rx_offsets, pd.rx_offsets, ps.tau, pd.tau)
+    a_s = rt.specular_reduction(ctx, ps, hidden, rt.eval_fields(ctx, ps, eps, sig, sc.freq_hz))
+    a_d = rt.eval_fields_diffuse(ctx, pd, eps, sig, hidden, sc.freq_hz)
+    a_m, _ = rt.rx_merge(ctx, ps.rx_offsets, pd.rx_offsets, a_s, a_d)
+    T = (rt.cfr(ctx, off, a_m, tau, fc, df, N).abs() ** 2).float().contiguous()
+    m = T.mean(1)
+    w = torch.where(m > 0, 1.0 / torch.where(m > 0, m, torch.ones_like(m)), torch.zeros_like(m)).float().contiguous()
+    scat = hidden.clone()
+    scat[:, 0] *= 0.7
+    scat[:, 1] = 0.25
+    M = sc.n_materials
+    ge, gs, gg = torch.zeros(M, device=dev), torch.zeros(M, device=dev), torch.zeros(2, device=dev)
+    gc = torch.zeros_like(scat)
+    loss = torch.zeros(1, device=dev)
+    a_sp = torch.empty_like(a_s)
+    a_sr = torch.empty_like(a_s)
+    a_df = torch.empty_like(a_d)
+    ga_m = torch.empty_like(a_m)
+    Ps, Pd = ps.n_paths, pd.n_paths
+
+    def cal_step():
+        rt.eval_fields(ctx, ps, eps, sig, sc.freq_hz, out=a_sp)
+        rt.specular_reduction(ctx, ps, scat, a_sp, out=a_sr)
+        rt.eval_fields_diffuse(ctx, pd, eps, sig, scat, sc.freq_hz, out=a_df)
+        am, _ = rt.rx_merge(ctx, ps.rx_offsets, pd.rx_offsets, a_sr, a_df)
+        rt.cfr_power_mse_fused(ctx, off, am, tau, fc, df, N, T, w, loss=loss, grad_a=ga_m)
+        g_s, g_d = rt.rx_split(ctx, ps.rx_offsets, pd.rx_offsets, ga_m, Ps, Pd)
+        ge.zero_()
+        gs.zero_()
+        gg.zero_()
+        gc.zero_()
+        g_sp, _ = rt.specular_reduction_backward(ctx, ps, scat, a_sr, g_s, grad_scat=gc)
+        rt.eval_fields_backward(ctx, ps, eps, sig, sc.freq_hz, g_sp, ge, gs, gg)
+        rt.eval_fields_diffuse_backward(ctx, pd, eps, sig, scat, sc.freq_hz, g_d, ge, gs, gc)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            cal_step()
+    stream.wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        cal_step()
+    for _ in range(5):
+        g.replay()
+    n = max(args.steps, 20)
+    step_ms = ev_time(g.replay, n)
+    cfr_ms = ev_time(lambda: rt.cfr_power_mse_fused(ctx, off, a_m, tau, fc, df, N, T, w, loss=loss, grad_a=ga_m), 10)
+    rt.set_cfr_tensor_cores(ctx, False)
+    cfr_simt_ms = ev_time(lambda: rt.cfr_power_mse_fused(ctx, off, a_m, tau, fc, df, N, T, w, loss=loss,
+                                                         grad_a=ga_m), 10)
+    rt.set_cfr_tensor_cores(ctx, True)
+    roof_cfr = roofline_cfr(cfr_ms, Ps + Pd, N)
+    roof_cfr["traffic"] = None   # the committed DRAM counters are those of the indoor workload
+    t_f = ev_time(lambda: rt.eval_fields_diffuse(ctx, pd, eps, sig, scat, sc.freq_hz, out=a_df), 20)
+    gd = (a_df * 0.5).contiguous()
+    t_b = ev_time(lambda: rt.eval_fields_diffuse_backward(ctx, pd, eps, sig, scat, sc.freq_hz, gd, ge, gs, gc), 20)
+    j = pd.export()["depth"].double()
+    fwd_bytes = float((44.0 + 24.0 * j).sum().item())
+    peaks, src = load_peaks()
+    hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+    gf, gb = fwd_bytes / (t_f * 1e-3) / 1e9, fwd_bytes / (t_b * 1e-3) / 1e9
+    return {"workload": "indoor_diff, 256 receivers, specular 1e6 rays + diffuse 2e4 rays, depth 3",
+            "n_rx": R, "n_rays_diffuse": n_rays_diffuse, "n_paths_specular": Ps, "n_paths_diffuse": Pd,
+            "nee_pairs": n_rays_diffuse * sc.max_depth * R,
+            "trace_diffuse_ms": trace_ms, "nee_pairs_per_s": n_rays_diffuse * sc.max_depth * R / (trace_ms * 1e-3),
+            "calibration_step_ms": step_ms, "graph": True, "n_sub": N, "cfr_fused_ms": cfr_ms,
+            "cfr_fused_simt_ms": cfr_simt_ms, "roofline_cfr": roof_cfr,
+            "l2": "flushed: 256 MiB written between timed runs",
+            "roofline_fields_diffuse": {"kernel": "k_df_fwd", "bound": "hbm", "achieved": gf, "peak": hbm,
+                                        "unit": "GB/s", "frac": gf / hbm, "ms": t_f, "bytes": fwd_bytes,
+                                        "peak_source": src},
+            "roofline_fields_diffuse_bwd": {"kernel": "k_df_bwd", "bound": "hbm", "achieved": gb, "peak": hbm,
+                                            "unit": "GB/s", "frac": gb / hbm, "ms": t_b, "bytes": fwd_bytes,
+                                            "peak_source": src}}
+
+
 def time_paper_loss_step(rt, ctx, p, sc, eps, sig, flush, n):
     """Calibration step of Algorithm 1 with the paper's loss on traced paths:
     eval_fields -> CFR -> CIR statistics -> power scale (moving average) -> SMAPE
@@ -1067,7 +1187,8 @@ def run_case(args):
     benchmark line): street_step = the street-canyon step (trace + fields +
     fused CFR loss + adjoints); indoor_calibration = the indoor calibration step
     (graph replays); fields_hbm = eval_fields and its adjoint on the tiled
-    street-canyon paths; city_batch = one batched trace of the 16 cities."""
+    street-canyon paths; diffuse = the diffuse trace, calibration step and field
+    kernels on the indoor scene; city_batch = one batched trace of the 16 cities."""
     import torch
 
     import paper_2311_18558_gb300 as rt
@@ -1101,6 +1222,9 @@ def run_case(args):
         sc = scenegen.street_canyon()
         scene = rt.Scene.from_synthetic(ctx, sc)
         out.update(time_fields_hbm(rt, ctx, scene, sc, flush, reps=max(args.steps, 1)))
+    elif args.case == "diffuse":
+        args.steps = max(args.steps, 1)
+        out.update(time_diffuse(rt, ctx, flush, args))
     elif args.case == "city_batch":
         cities = scenegen.city_batch()
         scenes = [rt.Scene.from_synthetic(ctx, c) for c in cities]
@@ -1122,7 +1246,8 @@ def main():
     ap.add_argument("--n-sub", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 16-city batched measurement")
-    ap.add_argument("--case", choices=["street_step", "indoor_calibration", "fields_hbm", "city_batch"], default=None,
+    ap.add_argument("--case", choices=["street_step", "indoor_calibration", "fields_hbm", "diffuse", "city_batch"],
+                    default=None,
                     help="run one workload alone (for profiler captures) instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -202,17 +202,95 @@ __device__ int closest_hit64(const BvhNode* __restrict__ nodes, const float4* __
     return best;
 }
 
-// Any hit with tlo < t < thi, skipping triangle `skip`.
-__device__ bool any_hit64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const Ray64& r,
-                          double tlo, double thi, int skip, int32_t* status) {
+// FP32 copy of a ray for the prefilter of the any-hit queries.
+struct Ray32 {
+    float o[3], d[3];
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ void ray32_from(const Ray64& r, Ray32& q) {
+    for (int c = 0; c < 3; ++c) {
+        q.o[c] = (float)r.o[c];
+        q.d[c] = (float)r.d[c];
+    }
+    const float ax = fabsf(q.d[0]), ay = fabsf(q.d[1]), az = fabsf(q.d[2]);
+    int kz = 0;
+    if (ay > ax) kz = 1;
+    if (az > (kz == 0 ? ax : ay)) kz = 2;
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    if (q.d[kz] < 0.0f) {
+        const int s = kx;
+        kx = ky;
+        ky = s;
+    }
+    q.kx = kx;
+    q.ky = ky;
+    q.kz = kz;
+    q.Sx = q.d[kx] / q.d[kz];
+    q.Sy = q.d[ky] / q.d[kz];
+    q.Sz = 1.0f / q.d[kz];
+}
+
+// FP32 watertight test of a segment query: 0 = a miss of the FP64 test for
+// certain, 1 = a hit of the FP64 test with tlo < t < thi for certain, 2 =
+// undecided.  The FP32 ray differs from the FP64 one by the rounding of its
+// origin and direction; with u = 2^-24 the sheared coordinates carry errors below
+// 4u (M_v + M_o) (M_v = max over the vertices of |X_kx| + |X_ky| + |X_kz| (|S_x| + |S_y|),
+// M_o the same of the origin), so the edge functions are off by less than
+// 2u (4 L^2 + 16 (M_v + M_o) L) (L the largest sheared coordinate); the margin is
+// that plus twice the FP64 test's growth DF_TRI_TOL (|U| + |V| + |W|).  The
+// parameter t is trusted to 64u (M_v + M_o) / |d_kz| plus 1e-6.
+__device__ __forceinline__ int tri_seg32(const Ray32& r, float4 p0, float4 p1, float4 p2, float tlo, float thi) {
+    const float A[3] = {p0.x - r.o[0], p0.y - r.o[1], p0.z - r.o[2]};
+    const float B[3] = {p1.x - r.o[0], p1.y - r.o[1], p1.z - r.o[2]};
+    const float C[3] = {p2.x - r.o[0], p2.y - r.o[1], p2.z - r.o[2]};
+    const float Akz = A[r.kz], Bkz = B[r.kz], Ckz = C[r.kz];
+    const float Ax = A[r.kx] - r.Sx * Akz, Ay = A[r.ky] - r.Sy * Akz;
+    const float Bx = B[r.kx] - r.Sx * Bkz, By = B[r.ky] - r.Sy * Bkz;
+    const float Cx = C[r.kx] - r.Sx * Ckz, Cy = C[r.ky] - r.Sy * Ckz;
+    const float U = Cx * By - Cy * Bx, V = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
+    const float Sab = fabsf(r.Sx) + fabsf(r.Sy);
+    const float Mv = fmaxf(fmaxf(fabsf(A[r.kx]) + fabsf(A[r.ky]) + fabsf(Akz) * Sab,
+                                 fabsf(B[r.kx]) + fabsf(B[r.ky]) + fabsf(Bkz) * Sab),
+                           fabsf(C[r.kx]) + fabsf(C[r.ky]) + fabsf(Ckz) * Sab);
+    const float Mo = fabsf(r.o[r.kx]) + fabsf(r.o[r.ky]) + fabsf(r.o[r.kz]) * Sab;
+    const float L = fmaxf(fmaxf(fmaxf(fabsf(Ax), fabsf(Ay)), fmaxf(fabsf(Bx), fabsf(By))), fmaxf(fabsf(Cx), fabsf(Cy)));
+    const float sum = fabsf(U) + fabsf(V) + fabsf(W);
+    const float u = 5.9604645e-8f;
+    const float m = 2.0f * u * (4.0f * L * L + 16.0f * (Mv + Mo) * L) + 2.0f * (float)DF_TRI_TOL * sum;
+    if ((U < -m || V < -m || W < -m) && (U > m || V > m || W > m)) return 0;
+    const bool pos = U > m && V > m && W > m, neg = U < -m && V < -m && W < -m;
+    if (!pos && !neg) return 2;
+    const float t = (U * Akz + V * Bkz + W * Ckz) * r.Sz / (U + V + W);
+    const float tt = 64.0f * u * (Mv + Mo) * fabsf(r.Sz) + 1e-6f;
+    if (t > tlo + tt && t < thi - tt) return 1;
+    if (t < tlo - tt || t > thi + tt) return 0;
+    return 2;
+}
+
+// Any hit with tlo < t < thi, skipping triangle `skip`: FP32 prefilter, FP64
+// test only where the prefilter is undecided.
+__device__ bool any_hit_seg(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const Ray64& r,
+                            double tlo, double thi, int skip, int32_t* status) {
+    Ray32 q;
+    ray32_from(r, q);
     bool hit = false;
-    const float fhi = up32(thi);
-    walk(nodes, r, (float)tlo * 0.5f, fhi, status, [&](int first, int count) {
+    const float fhi = up32(thi), flo = (float)tlo, fthi = (float)thi;
+    walk(nodes, r, flo * 0.5f, fhi, status, [&](int first, int count) {
         for (int k = first; k < first + count; ++k) {
             const float4 p0 = __ldg(tris + 3 * k);
             if (__float_as_int(p0.w) == skip) continue;
+            const float4 p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+            const int c = tri_seg32(q, p0, p1, p2, flo, fthi);
+            if (c == 0) continue;
+            if (c == 1) {
+                hit = true;
+                return true;
+            }
             double t;
-            if (!tri_hit64(r, p0, __ldg(tris + 3 * k + 1), __ldg(tris + 3 * k + 2), t)) continue;
+            if (!tri_hit64(r, p0, p1, p2, t)) continue;
             if (t > tlo && t < thi) {
                 hit = true;
                 return true;
@@ -315,7 +393,7 @@ __global__ void __launch_bounds__(DF_THREADS) k_df_nee(int64_t N, int D, int R, 
         const double len = sqrt(ray.d[0] * ray.d[0] + ray.d[1] * ray.d[1] + ray.d[2] * ray.d[2]);
         if (!(len > S.eps)) continue;
         ray64_init(ray);
-        if (any_hit64(S.nodes, S.tris, ray, S.eps / len, 1.0 - S.eps / len, t, status)) continue;
+        if (any_hit_seg(S.nodes, S.tris, ray, S.eps / len, 1.0 - S.eps / len, t, status)) continue;
         atomicOr(mask + (int64_t)r * W + (s >> 5), 1u << (s & 31));
     }
 }
@@ -661,18 +739,25 @@ __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, float2* __restrict__ a
 // with the row vector l = conj(u)^T / nu walked backwards through the chain,
 // dnu/d eta_b = R_b l . diag(dr_perp, dr_par) v_b (holomorphic in eta), so
 // dnu/d eps_r = Re(.) and dnu/d sigma = Im(.) / (eps0 omega).
-// Per-material sums go to shared memory (MAXM > 0) or straight to global atomics.
-template <int MAXM>
+// Per-material sums: with COLS > 0 (at most MAXM <= 8 materials, blocks of COLS
+// threads) every thread owns a column of 9 x MAXM shared-memory accumulators
+// (no atomics in the path loop; one block reduction at the end); otherwise
+// shared-memory atomics (MAXM > 0) or global atomics.
+template <int MAXM, int COLS>
 __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restrict__ ga, float* __restrict__ geps,
                                                 float* __restrict__ gsig, float* __restrict__ gscat, int n_mat) {
-    __shared__ float acc[MAXM > 0 ? MAXM * 9 : 1];
-    if (MAXM > 0) {
+    __shared__ float acc[COLS > 0 ? 9 * MAXM * COLS : (MAXM > 0 ? MAXM * 9 : 1)];
+    if (COLS > 0) {
+        for (int k = 0; k < 9 * MAXM; ++k) acc[k * COLS + threadIdx.x] = 0.0f;
+    } else if (MAXM > 0) {
         for (int k = threadIdx.x; k < n_mat * 9; k += blockDim.x) acc[k] = 0.0f;
         __syncthreads();
     }
     auto add = [&](int m, int c, float v) {
         if (v == 0.0f) return;
-        if (MAXM > 0) {
+        if (COLS > 0) {
+            acc[(c * MAXM + m) * COLS + threadIdx.x] += v;
+        } else if (MAXM > 0) {
             atomicAdd(&acc[m * 9 + c], v);
         } else if (c == 0) {
             if (geps) atomicAdd(geps + m, v);
@@ -692,6 +777,8 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restri
         bool pecs[RT_MAX_DEPTH];
         float cis[RT_MAX_DEPTH], Rs[RT_MAX_DEPTH];
         float2 E0 = make_float2(1.0f, 0.0f), E1 = make_float2(0.0f, 0.0f), u0 = E0, u1 = E1;
+        int md = 0;
+        float ci_d = 1.0f;
 #pragma unroll
         for (int b = 0; b < RT_MAX_DEPTH; ++b) {
             if (b >= j) break;
@@ -716,14 +803,17 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restri
             Rs[b] = b + 1 < j ? r_spec(__ldg(A.scat + 8 * mats[b])) : 1.0f;
             E0 = cscale(Rs[b], u0);
             E1 = cscale(Rs[b], u1);
+            if (b == j - 1) {
+                md = mats[b];
+                ci_d = cis[b];
+            }
         }
-        const int md = mats[j - 1];
         float prm[8];
         for (int c = 0; c < 8; ++c) prm[c] = __ldg(A.scat + 8 * md + c);
         const float nu = sqrtf(u0.x * u0.x + u0.y * u0.y + u1.x * u1.x + u1.y * u1.y);
         const float4 geo = __ldg(A.geo + i);
         float df[5];
-        const float f = pattern(prm, geo, cis[j - 1], df);
+        const float f = pattern(prm, geo, ci_d, df);
         const float sf = sqrtf(fmaxf(f, 0.0f));
         const float4 Dl = __ldg(A.Dm + (int64_t)j * A.P + i);
         const float Kx = fminf(fmaxf(prm[1], 1e-12f), 1.0f - 1e-7f);
@@ -742,7 +832,9 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restri
         // reverse walk for d nu / d eta_b and d nu / d R_b
         const float dAnu = g * C * S * sf * pol / nu;
         float2 l0 = make_float2(u0.x * dAnu, -u0.y * dAnu), l1 = make_float2(u1.x * dAnu, -u1.y * dAnu);
-        for (int b = j - 1; b >= 0; --b) {
+#pragma unroll
+        for (int b = RT_MAX_DEPTH - 1; b >= 0; --b) {
+            if (b > j - 1) continue;
             const float R = Rs[b];
             if (!pecs[b]) {
                 float2 eta, rp, rl, d0, d1;
@@ -766,7 +858,25 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restri
             l1 = cadd(cscale(D.y, m0), cscale(D.w, m1));
         }
     }
-    if (MAXM > 0) {
+    if (COLS > 0) {
+        __syncthreads();
+        const int lane = threadIdx.x & 31;
+        for (int k = threadIdx.x >> 5; k < 9 * MAXM; k += COLS / 32) {
+            const int c = k / MAXM, m = k - c * MAXM;
+            if (m >= n_mat) continue;
+            float v = 0.0f;
+            for (int t = lane; t < COLS; t += 32) v += acc[k * COLS + t];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane != 0 || v == 0.0f) continue;
+            if (c == 0) {
+                if (geps) atomicAdd(geps + m, v);
+            } else if (c == 1) {
+                if (gsig) atomicAdd(gsig + m, v);
+            } else if (gscat) {
+                atomicAdd(gscat + 8 * m + (c - 2), v);
+            }
+        }
+    } else if (MAXM > 0) {
         __syncthreads();
         for (int k = threadIdx.x; k < n_mat * 9; k += blockDim.x) {
             const float v = acc[k];
@@ -1024,12 +1134,17 @@ RT_EXPORT rt_status rt_eval_fields_diffuse_backward(rt_ctx* ctx, const rt_paths*
     if (paths->P == 0) return RT_OK;
     const DfArgs A = make_df_args(paths, eps_r_dev, sigma_dev, scat_dev, freq_hz, gain_tx, gain_rx);
     const int n_mat = paths->scene->n_materials;
-    const int grid = grid_of(ctx, paths->P, 256, 8);
     const float2* ga = (const float2*)grad_a_dev;
-    if (n_mat <= 64)
-        k_df_bwd<64><<<grid, 256, 0, ctx->stream>>>(A, ga, grad_eps_r_dev, grad_sigma_dev, grad_scat_dev, n_mat);
+    if (n_mat <= 8)
+        k_df_bwd<8, 128><<<grid_of(ctx, paths->P, 128, 12), 128, 0, ctx->stream>>>(A, ga, grad_eps_r_dev,
+                                                                                   grad_sigma_dev, grad_scat_dev,
+                                                                                   n_mat);
+    else if (n_mat <= 64)
+        k_df_bwd<64, 0><<<grid_of(ctx, paths->P, 256, 8), 256, 0, ctx->stream>>>(A, ga, grad_eps_r_dev,
+                                                                                 grad_sigma_dev, grad_scat_dev, n_mat);
     else
-        k_df_bwd<0><<<grid, 256, 0, ctx->stream>>>(A, ga, grad_eps_r_dev, grad_sigma_dev, grad_scat_dev, n_mat);
+        k_df_bwd<0, 0><<<grid_of(ctx, paths->P, 256, 8), 256, 0, ctx->stream>>>(A, ga, grad_eps_r_dev,
+                                                                                grad_sigma_dev, grad_scat_dev, n_mat);
     RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;
