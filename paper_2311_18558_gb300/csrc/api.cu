@@ -50,6 +50,10 @@ struct LossScratch {
     double* part = nullptr;
     unsigned int* done = nullptr;
     int cap = 0;
+    int* split_ints = nullptr;     // heavy-slot tables of the split fused CFR (6 per slot)
+    int split_cap = 0;
+    void* split_acc = nullptr;     // heavy-receiver H / dL/dH rows
+    size_t split_acc_bytes = 0;
 };
 static std::vector<std::pair<rt_ctx*, LossScratch>>& loss_table() {
     static std::vector<std::pair<rt_ctx*, LossScratch>> t;
@@ -71,12 +75,41 @@ rt_status rt_cfr_fused_scratch(rt_ctx* ctx, int R, double** part, unsigned int**
         ls->done = nullptr;
         int cap = std::max(R, 1024);
         RT_CK(ctx, cudaMalloc((void**)&ls->part, (size_t)cap * sizeof(double)));
-        RT_CK(ctx, cudaMalloc((void**)&ls->done, 4 * sizeof(unsigned int)));
-        RT_CK(ctx, cudaMemset(ls->done, 0, 4 * sizeof(unsigned int)));
+        RT_CK(ctx, cudaMalloc((void**)&ls->done, 16 * sizeof(unsigned int)));
+        RT_CK(ctx, cudaMemset(ls->done, 0, 16 * sizeof(unsigned int)));
         ls->cap = cap;
     }
     *part = ls->part;
     *done = ls->done;
+    return RT_OK;
+}
+
+// Tables of the heavy-receiver split of the tensor-core fused CFR (grow-only,
+// like the loss partials): 8 counters and 6 R ints (R heavy slots), zeroed when
+// allocated, and acc_bytes for the slots' rows.
+rt_status rt_cfr_split_scratch(rt_ctx* ctx, int R, size_t acc_bytes, int** ints, void** acc) {
+    LossScratch* ls = nullptr;
+    for (auto& e : loss_table())
+        if (e.first == ctx) ls = &e.second;
+    if (!ls) {
+        loss_table().push_back({ctx, LossScratch()});
+        ls = &loss_table().back().second;
+    }
+    if (R > ls->split_cap) {
+        if (ls->split_ints) RT_CK(ctx, cudaFree(ls->split_ints));
+        ls->split_ints = nullptr;
+        RT_CK(ctx, cudaMalloc((void**)&ls->split_ints, (6 * (size_t)R + 8) * sizeof(int)));
+        RT_CK(ctx, cudaMemset(ls->split_ints, 0, (6 * (size_t)R + 8) * sizeof(int)));
+        ls->split_cap = R;
+    }
+    if (acc_bytes > ls->split_acc_bytes) {
+        if (ls->split_acc) RT_CK(ctx, cudaFree(ls->split_acc));
+        ls->split_acc = nullptr;
+        RT_CK(ctx, cudaMalloc(&ls->split_acc, acc_bytes));
+        ls->split_acc_bytes = acc_bytes;
+    }
+    *ints = ls->split_ints;
+    *acc = ls->split_acc;
     return RT_OK;
 }
 
@@ -86,6 +119,8 @@ static void loss_scratch_release(rt_ctx* ctx) {
         if (t[i].first == ctx) {
             if (t[i].second.part) cudaFree(t[i].second.part);
             if (t[i].second.done) cudaFree(t[i].second.done);
+            if (t[i].second.split_ints) cudaFree(t[i].second.split_ints);
+            if (t[i].second.split_acc) cudaFree(t[i].second.split_acc);
             t.erase(t.begin() + i);
             return;
         }

@@ -26,6 +26,9 @@
 // Loss partials and the two counters (completed CTAs, next receiver) of the
 // fused and tensor-core kernels (api.cu); the counters are zero between launches.
 rt_status rt_cfr_fused_scratch(rt_ctx* ctx, int R, double** part, unsigned int** done);
+// Counters (8 ints) and heavy-slot tables (6 ints per slot) of the split fused
+// kernel, zeroed when first allocated, and the slots' rows (api.cu).
+rt_status rt_cfr_split_scratch(rt_ctx* ctx, int R, size_t acc_bytes, int** ints, void** acc);
 
 namespace {
 
@@ -508,12 +511,55 @@ __device__ __forceinline__ float2 tc_A(const float2* tF, int nf, int ii, int m) 
     return cmul(tF[ii * nf + (m >> 3)], tF[ii * nf + 16 + (m & 7)]);
 }
 
+// Receivers with many paths are split over CTAs (mode 3, the fused loss).  CTAs
+// take receivers from a counter; a receiver of at most TC_SPLIT paths is
+// processed whole, as in mode 2.  A receiver with more paths (the first
+// TC_HEAVY_CAP of them met in a call; later ones stay whole) is deferred: the
+// CTA that meets it clears its row of `acc` and its counters, then publishes it
+// (pub = epoch + 1).  Every receiver counts as classified as soon as it is taken
+// (a deferred one once published).  CTAs that find no receiver left work through
+// the heavy list in segments of TC_SEG paths: they claim forward segments
+// (per-receiver counter, cursor over the list); a forward segment adds its
+// partial H to the row with float atomics (so H of a split receiver is summed in
+// no fixed order); the CTA that finishes a receiver's last forward segment turns
+// the row into dL/dH, writes the receiver's loss partial and raises `ready`.
+// When every receiver is classified and every forward segment claimed, CTAs
+// claim adjoint segments the same way and wait for `ready`.  Each wait (for
+// classification, publication or `ready`) depends only on work that a running
+// CTA took before, so it ends; all are bounded.  The last CTA sums the loss over
+// all receivers in receiver order and advances the epoch.
+constexpr int TC_SPLIT = 4096;
+constexpr int TC_SEG = 1024;
+constexpr int TC_HEAVY_CAP = 4096;
+
+struct TcSplit {
+    unsigned int* cnt = nullptr;       // [0] heavy receivers met, [1] forward cursor, [2] adjoint cursor,
+                                       // [3] receivers classified, [4] call epoch (never reset)
+    unsigned int* pub = nullptr;       // TC_HEAVY_CAP: epoch + 1 once the slot is published
+    int* list = nullptr;               // TC_HEAVY_CAP: receiver of heavy slot h
+    unsigned int* seg_next = nullptr;  // TC_HEAVY_CAP: next forward segment to claim
+    unsigned int* adj_next = nullptr;  // TC_HEAVY_CAP: next adjoint segment to claim
+    unsigned int* fwd_done = nullptr;  // TC_HEAVY_CAP: finished forward segments
+    unsigned int* ready = nullptr;     // TC_HEAVY_CAP: dL/dH of the receiver is in acc
+    float2* acc = nullptr;             // TC_HEAVY_CAP x N
+};
+
+// Bounded wait of one thread until *flag reaches `want`; false on time-out.
+__device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int want) {
+    for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
+        if (*(volatile const unsigned int*)flag >= want) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
 // Receivers with at most TC_DIRECT paths skip the MMAs: each thread evaluates its
 // row directly (N2 x n complex products), which is cheaper than building 128-row
 // operand tiles for so few paths.
 constexpr int TC_DIRECT = 8;
 
-// MODE 0: forward (H out); 1: adjoint from g_H; 2: forward + power MSE + adjoint.
+// MODE 0: forward (H out); 1: adjoint from g_H; 2: forward + power MSE + adjoint;
+// 3: as 2 with receivers of many paths split over CTAs (TcSplit).
 template <int N2, int MODE>
 __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t* __restrict__ offs, int R,
                                                        const float2* __restrict__ a, const double* __restrict__ tau,
@@ -521,9 +567,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                                                        const float2* __restrict__ gH, float* __restrict__ loss,
                                                        float2* __restrict__ ga, float2* __restrict__ H,
                                                        double* __restrict__ part, unsigned int* __restrict__ ctr,
-                                                       int32_t* __restrict__ status) {
+                                                       int32_t* __restrict__ status, TcSplit sp) {
     using T = TcDims<N2>;
     constexpr bool FWD = MODE != 1, BWD = MODE != 0;
+    constexpr bool LOSS = MODE == 2 || MODE == 3;   // loss epilogue of whole receivers
     extern __shared__ float4 smem4[];
     float* A_hi = reinterpret_cast<float*>(smem4);
     float* A_lo = A_hi + T::A_FLOATS;
@@ -539,10 +586,18 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
     __shared__ int s_r;
     __shared__ double s_red[TC_THREADS / 32];
     __shared__ bool s_last;
+    __shared__ int s_kind, s_slot, s_nseg;
+    __shared__ int64_t s_i0, s_i1;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t mb = smem_u32(&mbar);
+    // mode 4: number of heavy receivers (fixed once mode 3 has finished); with
+    // none, the CTA takes no TMEM and only joins the completion count
     if (tid == 0) mbar_init(mb, 1);
+    __syncthreads();
+    // mode 3: this call's epoch (only the last CTA advances it, at the very end)
+    const unsigned int epoch = MODE == 3 ? __ldcg(sp.cnt + 4) : 0u;
+    int phase = 0;   // mode 3, thread 0: 0 receivers, 1 heavy forward segments, 2 heavy adjoint segments
     if (warp == 0) tmem_alloc(smem_u32(&tmem_sh), TC_TMEM_COLS);
     tc_fence_before();
     __syncthreads();
@@ -571,19 +626,114 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
 
     for (;;) {
         __syncthreads();   // every thread has read s_r (and finished the previous receiver)
-        if (tid == 0) s_r = (int)atomicAdd(ctr + 1, 1u);
+        if (tid == 0) {
+            int kind = 0, slot = -1, nseg = 1, rr = R;
+            int64_t a0 = 0, a1 = 0;
+            if (MODE == 3 && phase == 0) {
+                rr = (int)atomicAdd(ctr + 1, 1u);
+                if (rr < R) {
+                    a0 = offs[rr];
+                    a1 = offs[rr + 1];
+                    bool defer = false;
+                    if (ok && a1 - a0 > TC_SPLIT) {
+                        const int h = (int)atomicAdd(sp.cnt, 1u);
+                        if (h < TC_HEAVY_CAP) {
+                            kind = 3;   // deferred: published below, split later
+                            slot = h;
+                            defer = true;
+                        }
+                    }
+                    if (!defer) atomicAdd(sp.cnt + 3, 1u);   // classified
+                } else {
+                    phase = 1;
+                }
+            }
+            if (MODE == 3 && phase > 0) {
+                // heavy receivers: claim a forward segment; once the heavy list is final
+                // and every forward segment claimed, an adjoint segment
+                rr = R;
+                for (int it = 0; it < TC_WAIT_LIMIT && rr == R && phase <= 2; ++it) {
+                    unsigned int* cur = sp.cnt + phase;
+                    unsigned int* next = phase == 1 ? sp.seg_next : sp.adj_next;
+                    const int h = (int)*(volatile unsigned int*)cur;
+                    const int n_met = (int)min(*(volatile unsigned int*)sp.cnt, (unsigned int)TC_HEAVY_CAP);
+                    if (h >= n_met) {
+                        if (phase == 1 && *(volatile unsigned int*)(sp.cnt + 3) < (unsigned int)R) {
+                            __nanosleep(64);   // receivers still being classified: more may come
+                            continue;
+                        }
+                        if (phase == 1 && (int)min(*(volatile unsigned int*)sp.cnt, (unsigned int)TC_HEAVY_CAP) > h)
+                            continue;   // appended while we looked
+                        ++phase;
+                        continue;
+                    }
+                    if (*(volatile unsigned int*)(sp.pub + h) != epoch + 1u) {
+                        __nanosleep(64);   // being published by the CTA that met it
+                        continue;
+                    }
+                    __threadfence();
+                    const int rh = sp.list[h];
+                    const int64_t b0 = offs[rh], b1 = offs[rh + 1];
+                    const int g = (int)((b1 - b0 + TC_SEG - 1) / TC_SEG);
+                    const int sg = (int)atomicAdd(next + h, 1u);
+                    if (sg < g) {
+                        rr = rh;
+                        kind = phase;
+                        slot = h;
+                        nseg = g;
+                        a0 = b0 + (int64_t)sg * TC_SEG;
+                        a1 = min(b1, a0 + TC_SEG);
+                        break;
+                    }
+                    atomicCAS(cur, (unsigned int)h, (unsigned int)h + 1u);
+                }
+                if (rr == R && phase <= 2) rt_set_status(status, RT_ERR_TIMEOUT);
+            } else if (MODE != 3) {
+                rr = (int)atomicAdd(ctr + 1, 1u);
+                if (rr < R) {
+                    a0 = offs[rr];
+                    a1 = offs[rr + 1];
+                }
+            }
+            s_r = rr;
+            s_kind = kind;
+            s_slot = slot;
+            s_nseg = nseg;
+            s_i0 = a0;
+            s_i1 = a1;
+        }
         __syncthreads();
         const int r = s_r;
         if (r >= R || !ok) break;
-        const int64_t i0 = offs[r], i1 = offs[r + 1];
+        const int kind = s_kind, slot = s_slot;
+        const int64_t i0 = s_i0, i1 = s_i1;
         const int P = (int)(i1 - i0);
+        if (MODE == 3 && kind == 3) {
+            // a heavy receiver: clear its row and counters, then publish it
+            for (int c = tid; c < S.N; c += TC_THREADS) sp.acc[(int64_t)slot * S.N + c] = make_float2(0.0f, 0.0f);
+            if (tid == 0) {
+                sp.list[slot] = r;
+                sp.seg_next[slot] = 0u;
+                sp.adj_next[slot] = 0u;
+                sp.fwd_done[slot] = 0u;
+                sp.ready[slot] = 0u;
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                atomicExch(sp.pub + slot, epoch + 1u);
+                atomicAdd(sp.cnt + 3, 1u);   // classified
+            }
+            continue;
+        }
+        const bool do_fwd = FWD && kind != 2;
         const bool direct = P <= TC_DIRECT;
         const int nch = (P + TC_CP - 1) / TC_CP;
         float hre[N2], him[N2];
 #pragma unroll
         for (int c2 = 0; c2 < N2; ++c2) hre[c2] = him[c2] = 0.0f;
 
-        if (FWD && direct && P > 0) {
+        if (do_fwd && direct && P > 0) {
             tc_tables<N2>(S, i0, P, P, a, tau, tP, tC, tF, tFc);
             for (int ii = 0; ii < P; ++ii) {
                 const float2 ac = cmul(tFc[ii * TC_NFC + (m >> 3)], tF[ii * T::NF + 16 + (m & 7)]);
@@ -595,7 +745,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                     him[c2] = fmaf(ac.x, b.y, fmaf(ac.y, b.x, him[c2]));
                 }
             }
-        } else if (FWD && P > 0) {
+        } else if (do_fwd && P > 0) {
             bool first = true;
             for (int ch = 0; ch < nch && ok; ++ch) {
                 const int64_t base = i0 + (int64_t)ch * TC_CP;
@@ -666,7 +816,61 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
             continue;
         }
         float gre[N2], gim[N2];
-        if (MODE == 2) {
+        if (MODE == 3 && kind == 1) {
+            // forward segment of a split receiver: add the partial H to its row
+            float2* row = sp.acc + (int64_t)slot * S.N + (int64_t)m * N2;
+#pragma unroll
+            for (int c2 = 0; c2 < N2; ++c2) {
+                atomicAdd(&row[c2].x, hre[c2]);
+                atomicAdd(&row[c2].y, him[c2]);
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) s_last = atomicAdd(sp.fwd_done + slot, 1u) == (unsigned int)(s_nseg - 1);
+            __syncthreads();
+            if (!s_last) continue;
+            // the last segment: H complete; loss partial and dL/dH in place of H
+            __threadfence();
+            const float wr = w[r];
+            double lsum = 0.0;
+#pragma unroll
+            for (int c2 = 0; c2 < N2; ++c2) {
+                const float2 h = __ldcg(row + c2);
+                const float e = h.x * h.x + h.y * h.y - target[hrow + c2];
+                const float we = wr * e;
+                lsum += (double)(we * we);
+                const float sc = 4.0f * wr * wr * e * inv_rn;
+                row[c2] = make_float2(sc * h.x, sc * h.y);
+                if (H) H[hrow + c2] = h;
+            }
+            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+            if (lane == 0) s_red[warp] = lsum;
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                part[r] = s_red[0] + s_red[1] + s_red[2] + s_red[3];
+                __threadfence();
+                atomicExch(sp.ready + slot, 1u);
+            }
+            continue;
+        }
+        if (MODE == 3 && kind == 2) {
+            // adjoint segment of a split receiver: dL/dH from its row once ready
+            if (tid == 0) s_last = wait_flag(sp.ready + slot, 1u);
+            __syncthreads();
+            if (!s_last) {
+                ok = false;
+                break;
+            }
+            __threadfence();
+            const float2* row = sp.acc + (int64_t)slot * S.N + (int64_t)m * N2;
+#pragma unroll
+            for (int c2 = 0; c2 < N2; ++c2) {
+                const float2 g = __ldcg(row + c2);
+                gre[c2] = g.x;
+                gim[c2] = g.y;
+            }
+        } else if (LOSS) {
             const float wr = w[r];
             double lsum = 0.0;
 #pragma unroll
@@ -696,7 +900,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
             const int64_t base = i0 + (int64_t)ch * TC_CP;
             const int n = min(TC_CP, P - ch * TC_CP);
             const int n_pad = direct ? n : (n + 7) & ~7;
-            if (!FWD || ch != nch - 1) tc_tables<N2>(S, base, n, n_pad, nullptr, tau, tP, tC, tF, tFc);
+            if (!do_fwd || ch != nch - 1) tc_tables<N2>(S, base, n, n_pad, nullptr, tau, tP, tC, tF, tFc);
             float vr[32], vi[32];
             if (direct) {
 #pragma unroll
@@ -807,7 +1011,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                 ga[base + lane] = cmulc(s, base_phasor(tP[lane]));
             }
         }
-        if (MODE == 2) {
+        if ((MODE == 2 || MODE == 3) && kind == 0) {
             __syncthreads();
             if (tid == 0) part[r] = s_red[0] + s_red[1] + s_red[2] + s_red[3];
         }
@@ -820,7 +1024,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
-    // completion: the last CTA resets the receiver counter (and sums the loss)
+    // completion: the last CTA resets the counters and sums the loss over all
+    // receivers in receiver order (mode 3: only if no receiver was deferred; mode 4
+    // then does it)
     if (tid == 0) {
         __threadfence();
         const unsigned int prev = atomicAdd(ctr, 1u);
@@ -829,7 +1035,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
     __syncthreads();
     if (s_last) {
         __threadfence();
-        if (MODE == 2) {
+        if (MODE == 2 || MODE == 3) {
             double s = 0.0;
             for (int k = tid; k < R; k += TC_THREADS) s += ((volatile double*)part)[k];
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -840,6 +1046,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
         if (tid == 0) {
             ctr[0] = 0u;
             ctr[1] = 0u;
+            if (MODE == 3) {
+                sp.cnt[0] = 0u;
+                sp.cnt[1] = 0u;
+                sp.cnt[2] = 0u;
+                sp.cnt[3] = 0u;
+                sp.cnt[4] = epoch + 1u;
+            }
         }
     }
 }
@@ -848,7 +1061,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
 template <int MODE>
 rt_status launch_tc(rt_ctx* ctx, const CfrShape& S, const int64_t* offs, int R, const float2* a, const double* tau,
                     const float* target, const float* w, const float2* gH, float* loss, float2* ga, float2* H,
-                    double* part, unsigned int* ctr) {
+                    double* part, unsigned int* ctr, TcSplit sp = TcSplit()) {
     auto go = [&](auto n2) -> rt_status {
         constexpr int N2 = decltype(n2)::value;
         auto kern = k_cfr_tc<N2, MODE>;
@@ -862,9 +1075,9 @@ rt_status launch_tc(rt_ctx* ctx, const CfrShape& S, const int64_t* offs, int R, 
         RT_CK(ctx, cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device));
         int per_sm = smem_sm / (int)(smem + 64 + (size_t)reserved);
         per_sm = std::max(1, std::min(per_sm, (int)(512 / TC_TMEM_COLS)));
-        const int grid = std::max(1, std::min(R, ctx->num_sms * per_sm));
+        const int grid = std::max(1, MODE == 3 ? ctx->num_sms * per_sm : std::min(R, ctx->num_sms * per_sm));
         kern<<<grid, TC_THREADS, smem, ctx->stream>>>(S, offs, R, a, tau, target, w, gH, loss, ga, H, part, ctr,
-                                                       ctx->d_status);
+                                                       ctx->d_status, sp);
         RT_COUNT(ctx);
         RT_CK_LAUNCH(ctx);
         return RT_OK;
@@ -998,9 +1211,24 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fus
     unsigned int* done;
     s = rt_cfr_fused_scratch(ctx, n_rx, &part, &done);
     if (s != RT_OK) return s;
-    if (tc_supported(ctx, n_sub))
-        return launch_tc<2>(ctx, S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, target_power_dev,
-                            rx_weight_dev, nullptr, loss_dev, (float2*)grad_a_dev, (float2*)H_dev, part, done);
+    if (tc_supported(ctx, n_sub)) {
+        // receivers with many paths are deferred and split over CTAs (mode 3)
+        int* ints = nullptr;
+        void* acc = nullptr;
+        s = rt_cfr_split_scratch(ctx, TC_HEAVY_CAP, (size_t)TC_HEAVY_CAP * (size_t)n_sub * sizeof(float2), &ints, &acc);
+        if (s != RT_OK) return s;
+        TcSplit sp;
+        sp.cnt = reinterpret_cast<unsigned int*>(ints);   // zeroed with the tables, once per context
+        sp.list = ints + 8;
+        sp.seg_next = reinterpret_cast<unsigned int*>(sp.list + TC_HEAVY_CAP);
+        sp.adj_next = sp.seg_next + TC_HEAVY_CAP;
+        sp.fwd_done = sp.adj_next + TC_HEAVY_CAP;
+        sp.ready = sp.fwd_done + TC_HEAVY_CAP;
+        sp.pub = sp.ready + TC_HEAVY_CAP;
+        sp.acc = static_cast<float2*>(acc);
+        return launch_tc<3>(ctx, S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, target_power_dev,
+                            rx_weight_dev, nullptr, loss_dev, (float2*)grad_a_dev, (float2*)H_dev, part, done, sp);
+    }
     const size_t smem = fwd_smem(S) + (size_t)S.N * 8;
     return dispatch_opt(ctx, S.N, [&](auto opt) -> rt_status {
         constexpr int O = decltype(opt)::value;

@@ -99,3 +99,70 @@ def test_cfr_tensor_cores(rt, ctx, n_sub):
     nz = den > 0
     assert (num[nz] / den[nz]).max() <= 2e-4
     assert abs(results[True][2] - results[False][2]) <= 2e-4 * abs(L_ref)
+
+
+# receivers above 4096 paths are split over CTAs in the fused kernel (segments of
+# 1024 paths); 4096 itself stays whole
+SPLIT_COUNTS = np.array([3, 4096, 4097, 9000, 0, 40000, 17, 5000], np.int64)
+
+
+@pytest.mark.parametrize("n_sub", [256, 1024])
+def test_fused_split_receivers(rt, ctx, n_sub):
+    rng = np.random.default_rng(7 + n_sub)
+    offs = np.zeros(len(SPLIT_COUNTS) + 1, np.int64)
+    offs[1:] = np.cumsum(SPLIT_COUNTS)
+    P = int(offs[-1])
+    a = (10.0 ** rng.uniform(-5, -2, P) * np.exp(1j * rng.uniform(0, 2 * np.pi, P))).astype(np.complex64)
+    tau = rng.uniform(1e-9, 1.5e-6, P)
+    fc, df = 1.272e9, 50e6 / n_sub
+    Href = oracle.cfr(a.astype(np.complex128), tau, offs, fc, df, n_sub)
+    T = (np.abs(Href) ** 2 * rng.uniform(0.5, 1.5, Href.shape)).astype(np.float32)
+    w = oracle.power_weights(T).astype(np.float32)
+    L_ref, _ = oracle.power_mse(Href, T, w)
+    o, ad, td = _dev(offs, torch.int64), _dev(a, torch.complex64), _dev(tau, torch.float64)
+    Hf = torch.empty((len(offs) - 1, n_sub), dtype=torch.complex64, device="cuda")
+    for _ in range(2):   # twice: counters, flags and rows must be reset by each call
+        loss, gaf, _ = rt.cfr_power_mse_fused(ctx, o, ad, td, fc, df, n_sub, _dev(T, torch.float32),
+                                              _dev(w, torch.float32), H=Hf)
+        loss, gaf, H = loss.item(), gaf.cpu().numpy(), Hf.cpu().numpy()
+        assert abs(loss - L_ref) <= 1e-4 * abs(L_ref), (loss, L_ref)
+        num, den = normwise_rows(H, Href)
+        assert (num[den > 0] / den[den > 0]).max() <= 1e-4
+        assert np.all(H[SPLIT_COUNTS == 0] == 0)
+        _, gH_at = oracle.power_mse(H.astype(np.complex128), T, w)
+        ga_at = oracle.cfr_grad(tau, offs, fc, df, n_sub, gH_at)
+        for r in range(len(SPLIT_COUNTS)):   # per receiver, so a split one cannot hide behind the others
+            s = slice(offs[r], offs[r + 1])
+            if offs[r + 1] > offs[r]:
+                assert np.linalg.norm(gaf[s] - ga_at[s]) <= 1e-4 * np.linalg.norm(ga_at[s]), r
+    assert ctx.status_word() == 0
+
+
+def test_fused_split_beyond_heavy_cap(rt, ctx):
+    # 4100 receivers of 4097 paths: the first 4096 are split, the rest stay whole.
+    # Receivers on both sides of the cap are checked against the FP64 oracle one
+    # by one (a receiver's H and dL/da depend only on its own paths and target,
+    # with the loss normalised by R N of the whole call)
+    R, n_sub, Pr = 4100, 256, 4097
+    rng = np.random.default_rng(11)
+    P = R * Pr
+    a_h = (10.0 ** rng.uniform(-5, -2, P) * np.exp(1j * rng.uniform(0, 2 * np.pi, P))).astype(np.complex64)
+    tau_h = rng.uniform(1e-9, 1.5e-6, P)
+    offs = torch.arange(R + 1, dtype=torch.int64, device="cuda") * Pr
+    a, tau = _dev(a_h, torch.complex64), _dev(tau_h, torch.float64)
+    fc, df = 1.272e9, 50e6 / n_sub
+    T = (rt.cfr(ctx, offs, a, tau, fc, df, n_sub).abs() ** 2 * 1.3).float().contiguous()
+    w = torch.ones(R, device="cuda")
+    H = torch.empty((R, n_sub), dtype=torch.complex64, device="cuda")
+    loss, ga, _ = rt.cfr_power_mse_fused(ctx, offs, a, tau, fc, df, n_sub, T, w, H=H)
+    H, ga, T = H.cpu().numpy(), ga.cpu().numpy(), T.cpu().numpy()
+    one = np.array([0, Pr], np.int64)
+    for r in (0, 4095, 4096, 4099):
+        s = slice(r * Pr, (r + 1) * Pr)
+        Href = oracle.cfr(a_h[s].astype(np.complex128), tau_h[s], one, fc, df, n_sub)
+        assert np.linalg.norm(H[r] - Href[0]) <= 1e-4 * np.linalg.norm(Href[0]), r
+        _, gH_at = oracle.power_mse(H[r:r + 1].astype(np.complex128), T[r:r + 1], np.ones(1))
+        ga_at = oracle.cfr_grad(tau_h[s], one, fc, df, n_sub, gH_at / R)
+        err = np.linalg.norm(ga[s] - ga_at) / np.linalg.norm(ga_at)
+        assert err <= 1e-4, (r, err)
+    assert ctx.status_word() == 0
