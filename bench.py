@@ -1157,7 +1157,7 @@ def roofline_cfr(ms, n_paths, N):
     peaks, src = load_peaks()
     tf32 = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]) * (1.1 / 2.25)
     ach = 3 * 16.0 * N * n_paths / (ms * 1e-3) / 1e12
-    return {"kernel": "k_cfr_tc<8,2>", "bound": "tensor", "achieved": ach, "peak": tf32, "unit": "TFLOP/s",
+    return {"kernel": "k_cfr_tc<8,3>", "bound": "tensor", "achieved": ach, "peak": tf32, "unit": "TFLOP/s",
             "frac": ach / tf32, "traffic": ncu_traffic("k_cfr_tc"), "kernel_ms": ms,
             "peak_source": f"{src} bf16 x 1.1/2.25 (TF32)",
             "algorithmic": "3 x 16 N P TF32 flops (3xTF32 split of 8 N P complex MAC flops, forward and adjoint)"}

@@ -62,7 +62,19 @@ struct Ray64 {
     float3 of, inv;   // FP32 origin and reciprocal direction for the box tests
 };
 
-__device__ __forceinline__ void ray64_init(Ray64& r) {
+// FP32 origin and reciprocal direction of the box tests.
+__device__ __forceinline__ void ray64_init_box(Ray64& r) {
+    r.of = make_float3((float)r.o[0], (float)r.o[1], (float)r.o[2]);
+    float inv[3];
+    for (int k = 0; k < 3; ++k) {
+        const float dk = (float)r.d[k];
+        inv[k] = 1.0f / (fabsf(dk) < 1e-30f ? copysignf(1e-30f, dk) : dk);
+    }
+    r.inv = make_float3(inv[0], inv[1], inv[2]);
+}
+
+// Axis permutation and shear of the FP64 watertight test.
+__device__ __forceinline__ void ray64_init_shear(Ray64& r) {
     const double ax = fabs(r.d[0]), ay = fabs(r.d[1]), az = fabs(r.d[2]);
     int kz = 0;
     if (ay > ax) kz = 1;
@@ -80,13 +92,11 @@ __device__ __forceinline__ void ray64_init(Ray64& r) {
     r.Sx = r.d[kx] / r.d[kz];
     r.Sy = r.d[ky] / r.d[kz];
     r.Sz = 1.0 / r.d[kz];
-    r.of = make_float3((float)r.o[0], (float)r.o[1], (float)r.o[2]);
-    float inv[3];
-    for (int k = 0; k < 3; ++k) {
-        const float dk = (float)r.d[k];
-        inv[k] = 1.0f / (fabsf(dk) < 1e-30f ? copysignf(1e-30f, dk) : dk);
-    }
-    r.inv = make_float3(inv[0], inv[1], inv[2]);
+}
+
+__device__ __forceinline__ void ray64_init(Ray64& r) {
+    ray64_init_shear(r);
+    ray64_init_box(r);
 }
 
 // Watertight ray/triangle test in FP64 (Woop, Benthin and Wald, JCGT 2013) with
@@ -272,12 +282,18 @@ __device__ __forceinline__ int tri_seg32(const Ray32& r, float4 p0, float4 p1, f
 
 // Any hit with tlo < t < thi, skipping triangle `skip`: FP32 prefilter, FP64
 // test only where the prefilter is undecided.
-__device__ bool any_hit_seg(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const Ray64& r,
-                            double tlo, double thi, int skip, int32_t* status) {
+// The segment is origin + t d, t in (eps / |d|, 1 - eps / |d|), |d|^2 = len2;
+// only r.o and r.d need to be set: the FP64 shear and bounds are formed the first
+// time a triangle is undecided (most queries never need them).
+__device__ bool any_hit_seg(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, Ray64& r,
+                            double len2, double eps, int skip, int32_t* status) {
+    ray64_init_box(r);
     Ray32 q;
     ray32_from(r, q);
-    bool hit = false;
-    const float fhi = up32(thi), flo = (float)tlo, fthi = (float)thi;
+    bool hit = false, fp64_ready = false;
+    double tlo = 0.0, thi = 0.0;
+    const float flo = (float)eps * rsqrtf((float)len2), fthi = 1.0f - flo;
+    const float fhi = fthi * (1.0f + 1e-6f) + 1e-30f;
     walk(nodes, r, flo * 0.5f, fhi, status, [&](int first, int count) {
         for (int k = first; k < first + count; ++k) {
             const float4 p0 = __ldg(tris + 3 * k);
@@ -288,6 +304,13 @@ __device__ bool any_hit_seg(const BvhNode* __restrict__ nodes, const float4* __r
             if (c == 1) {
                 hit = true;
                 return true;
+            }
+            if (!fp64_ready) {
+                ray64_init_shear(r);
+                const double len = sqrt(len2);
+                tlo = eps / len;
+                thi = 1.0 - tlo;
+                fp64_ready = true;
             }
             double t;
             if (!tri_hit64(r, p0, p1, p2, t)) continue;
@@ -390,10 +413,9 @@ __global__ void __launch_bounds__(DF_THREADS) k_df_nee(int64_t N, int D, int R, 
             ray.o[c] = p[c];
             ray.d[c] = x[c] - p[c];
         }
-        const double len = sqrt(ray.d[0] * ray.d[0] + ray.d[1] * ray.d[1] + ray.d[2] * ray.d[2]);
-        if (!(len > S.eps)) continue;
-        ray64_init(ray);
-        if (any_hit_seg(S.nodes, S.tris, ray, S.eps / len, 1.0 - S.eps / len, t, status)) continue;
+        const double len2 = ray.d[0] * ray.d[0] + ray.d[1] * ray.d[1] + ray.d[2] * ray.d[2];
+        if (!(len2 > S.eps * S.eps)) continue;
+        if (any_hit_seg(S.nodes, S.tris, ray, len2, S.eps, t, status)) continue;
         atomicOr(mask + (int64_t)r * W + (s >> 5), 1u << (s & 31));
     }
 }
@@ -942,36 +964,49 @@ __global__ void __launch_bounds__(256) k_spec_reduce_bwd(int64_t P, const int32_
 }
 
 // ------------------------------------------------------------------ per-receiver merge / split
-// One warp per receiver: dst holds receiver r's elements of src1 followed by its
-// elements of src2 (8-byte elements), and off_out[r] = off1[r] + off2[r].
-__global__ void k_rx_merge(int R, const int64_t* __restrict__ off1, const int64_t* __restrict__ off2,
-                           const uint64_t* __restrict__ s1, const uint64_t* __restrict__ s2, uint64_t* __restrict__ dst,
-                           int64_t* __restrict__ off_out) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R;
-         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const int64_t a0 = off1[r], a1 = off1[r + 1], b0 = off2[r], b1 = off2[r + 1];
-        const int64_t o = a0 + b0;
-        if (lane == 0) {
-            if (off_out) off_out[r] = o;
-            if (off_out && r == R - 1) off_out[R] = a1 + b1;
-        }
-        for (int64_t k = lane; k < a1 - a0; k += 32) dst[o + k] = s1[a0 + k];
-        for (int64_t k = lane; k < b1 - b0; k += 32) dst[o + (a1 - a0) + k] = s2[b0 + k];
+// The merged list holds receiver r's elements of list 1 then its elements of
+// list 2, starting at S(r) = off1[r] + off2[r].  One thread per merged element
+// (lanes on consecutive elements, so loads and stores coalesce); a thread finds
+// the receiver of its first element by bisection on S and walks forward from
+// there for its later ones (a grid stride later).
+__device__ __forceinline__ int rx_of(int64_t i, int R, const int64_t* __restrict__ off1,
+                                     const int64_t* __restrict__ off2) {
+    int lo = 0, hi = R;   // S(lo) <= i < S(hi)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(off1 + mid) + __ldg(off2 + mid) <= i) lo = mid;
+        else hi = mid;
     }
+    return lo;
 }
 
-__global__ void k_rx_split(int R, const int64_t* __restrict__ off1, const int64_t* __restrict__ off2,
-                           const uint64_t* __restrict__ src, uint64_t* __restrict__ d1, uint64_t* __restrict__ d2) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R;
-         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const int64_t a0 = off1[r], a1 = off1[r + 1], b0 = off2[r], b1 = off2[r + 1];
-        const int64_t o = a0 + b0;
-        if (d1)
-            for (int64_t k = lane; k < a1 - a0; k += 32) d1[a0 + k] = src[o + k];
-        if (d2)
-            for (int64_t k = lane; k < b1 - b0; k += 32) d2[b0 + k] = src[o + (a1 - a0) + k];
+template <bool MERGE>
+__global__ void __launch_bounds__(256) k_rx_perm(int R, const int64_t* __restrict__ off1,
+                                                 const int64_t* __restrict__ off2, const uint64_t* __restrict__ a,
+                                                 const uint64_t* __restrict__ b, uint64_t* __restrict__ x,
+                                                 uint64_t* __restrict__ ya, uint64_t* __restrict__ yb,
+                                                 int64_t* __restrict__ off_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (MERGE && off_out)
+        for (int64_t q = g; q <= R; q += stride) off_out[q] = __ldg(off1 + q) + __ldg(off2 + q);
+    const int64_t total = __ldg(off1 + R) + __ldg(off2 + R);
+    if (g >= total) return;
+    int r = rx_of(g, R, off1, off2);
+    for (int64_t i = g; i < total; i += stride) {
+        while (r + 1 < R && __ldg(off1 + r + 1) + __ldg(off2 + r + 1) <= i) ++r;
+        const int64_t a0 = __ldg(off1 + r), b0 = __ldg(off2 + r);
+        const int64_t k = i - (a0 + b0), n1 = __ldg(off1 + r + 1) - a0;
+        if (MERGE) {
+            x[i] = k < n1 ? a[a0 + k] : b[b0 + (k - n1)];
+        } else {
+            const uint64_t v = a[i];
+            if (k < n1) {
+                if (ya) ya[a0 + k] = v;
+            } else if (yb) {
+                yb[b0 + (k - n1)] = v;
+            }
+        }
     }
 }
 
@@ -1190,9 +1225,9 @@ RT_EXPORT rt_status rt_rx_merge(rt_ctx* ctx, int32_t n_rx, const int64_t* off1_d
     if (!ctx) return RT_ERR_INVALID_ARG;
     if (n_rx < 1 || !off1_dev || !off2_dev || !src1_dev || !src2_dev || !dst_dev)
         return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument or n_rx < 1");
-    const int grid = grid_of(ctx, (int64_t)n_rx * 32, 256, 16);
-    k_rx_merge<<<grid, 256, 0, ctx->stream>>>(n_rx, off1_dev, off2_dev, (const uint64_t*)src1_dev,
-                                              (const uint64_t*)src2_dev, (uint64_t*)dst_dev, off_out_dev); RT_COUNT(ctx);
+    k_rx_perm<true><<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(n_rx, off1_dev, off2_dev, (const uint64_t*)src1_dev,
+                                                               (const uint64_t*)src2_dev, (uint64_t*)dst_dev, nullptr,
+                                                               nullptr, off_out_dev); RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;
 }
@@ -1201,9 +1236,9 @@ RT_EXPORT rt_status rt_rx_split(rt_ctx* ctx, int32_t n_rx, const int64_t* off1_d
                                 const void* src_dev, void* dst1_dev, void* dst2_dev) {
     if (!ctx) return RT_ERR_INVALID_ARG;
     if (n_rx < 1 || !off1_dev || !off2_dev || !src_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument or n_rx < 1");
-    const int grid = grid_of(ctx, (int64_t)n_rx * 32, 256, 16);
-    k_rx_split<<<grid, 256, 0, ctx->stream>>>(n_rx, off1_dev, off2_dev, (const uint64_t*)src_dev, (uint64_t*)dst1_dev,
-                                              (uint64_t*)dst2_dev); RT_COUNT(ctx);
+    k_rx_perm<false><<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(n_rx, off1_dev, off2_dev, (const uint64_t*)src_dev,
+                                                                nullptr, nullptr, (uint64_t*)dst1_dev,
+                                                                (uint64_t*)dst2_dev, nullptr); RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;
 }
