@@ -52,8 +52,10 @@ struct LossScratch {
     int cap = 0;
     int* split_ints = nullptr;     // heavy-slot tables of the split fused CFR (6 per slot)
     int split_cap = 0;
-    void* split_acc = nullptr;     // heavy-receiver H / dL/dH rows
+    void* split_acc = nullptr;     // heavy-receiver grid rows
     size_t split_acc_bytes = 0;
+    float* split_deconv = nullptr; // 4096 floats: per-column factors of the split receivers' transform
+    int split_deconv_n = 0;        // n_sub the factors were made for (0: none yet)
 };
 static std::vector<std::pair<rt_ctx*, LossScratch>>& loss_table() {
     static std::vector<std::pair<rt_ctx*, LossScratch>> t;
@@ -87,7 +89,8 @@ rt_status rt_cfr_fused_scratch(rt_ctx* ctx, int R, double** part, unsigned int**
 // Tables of the heavy-receiver split of the tensor-core fused CFR (grow-only,
 // like the loss partials): 8 counters and 6 R ints (R heavy slots), zeroed when
 // allocated, and acc_bytes for the slots' rows.
-rt_status rt_cfr_split_scratch(rt_ctx* ctx, int R, size_t acc_bytes, int** ints, void** acc) {
+rt_status rt_cfr_split_scratch(rt_ctx* ctx, int R, size_t acc_bytes, int** ints, void** acc, float** deconv,
+                               int** deconv_n) {
     LossScratch* ls = nullptr;
     for (auto& e : loss_table())
         if (e.first == ctx) ls = &e.second;
@@ -108,8 +111,11 @@ rt_status rt_cfr_split_scratch(rt_ctx* ctx, int R, size_t acc_bytes, int** ints,
         RT_CK(ctx, cudaMalloc(&ls->split_acc, acc_bytes));
         ls->split_acc_bytes = acc_bytes;
     }
+    if (!ls->split_deconv) RT_CK(ctx, cudaMalloc((void**)&ls->split_deconv, 4096 * sizeof(float)));
     *ints = ls->split_ints;
     *acc = ls->split_acc;
+    *deconv = ls->split_deconv;
+    *deconv_n = &ls->split_deconv_n;
     return RT_OK;
 }
 
@@ -121,6 +127,7 @@ static void loss_scratch_release(rt_ctx* ctx) {
             if (t[i].second.done) cudaFree(t[i].second.done);
             if (t[i].second.split_ints) cudaFree(t[i].second.split_ints);
             if (t[i].second.split_acc) cudaFree(t[i].second.split_acc);
+            if (t[i].second.split_deconv) cudaFree(t[i].second.split_deconv);
             t.erase(t.begin() + i);
             return;
         }

@@ -20,6 +20,7 @@
 #include <cmath>
 #include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "rt_internal.cuh"
 
@@ -28,7 +29,8 @@
 rt_status rt_cfr_fused_scratch(rt_ctx* ctx, int R, double** part, unsigned int** done);
 // Counters (8 ints) and heavy-slot tables (6 ints per slot) of the split fused
 // kernel, zeroed when first allocated, and the slots' rows (api.cu).
-rt_status rt_cfr_split_scratch(rt_ctx* ctx, int R, size_t acc_bytes, int** ints, void** acc);
+rt_status rt_cfr_split_scratch(rt_ctx* ctx, int R, size_t acc_bytes, int** ints, void** acc, float** deconv,
+                               int** deconv_n);
 
 namespace {
 
@@ -541,8 +543,77 @@ struct TcSplit {
     unsigned int* adj_next = nullptr;  // TC_HEAVY_CAP: next adjoint segment to claim
     unsigned int* fwd_done = nullptr;  // TC_HEAVY_CAP: finished forward segments
     unsigned int* ready = nullptr;     // TC_HEAVY_CAP: dL/dH of the receiver is in acc
-    float2* acc = nullptr;             // TC_HEAVY_CAP x N
+    float2* acc = nullptr;             // TC_HEAVY_CAP x 2N: oversampled grid of each heavy receiver
+    const float* dec = nullptr;        // N: 1 / (M phi_hat(n)) per column (see below)
 };
+
+// Heavy receivers use a non-uniform FFT instead of the dense product (the
+// method of Barnett, Magland and af Klinteberg, "A parallel non-uniform fast
+// Fourier transform library based on an exponential of semicircle kernel",
+// SIAM J. Sci. Comput. 2019, written here from its mathematics):
+//   H[c] = sum_i c'_i exp(-j 2 pi n x_i),  n = c - N/2,  c'_i = a_i exp(-j 2 pi f_c tau_i),
+//   x_i = frac(df tau_i).
+// Spreading: b[l] = sum_i c'_i phi((l - M x_i) 2 / W), l mod M, on a grid of
+// M = 2N cells with phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on |z| <= 1 (W cells
+// wide); then B = FFT_-(b) and H[c] = B[n mod M] / (M phi_hat(n)) with
+// M phi_hat(n) = W/2 int_{-1}^{1} phi(z) cos(pi n W z / M) dz (host quadrature).
+// The adjoint is the transposed chain: g'[n] = g_H[c] / (M phi_hat(n)) placed at
+// n mod M (zero elsewhere), b' = FFT_+(g'), and dL/dc'_i = sum_l phi(.) b'[l],
+// dL/da_i = conj(exp(-j 2 pi f_c tau_i)) dL/dc'_i.  With W = 8 and beta = 2.3 W
+// the kernel's aliasing error is ~1e-7 relative to sum |c'_i|.
+constexpr int NU_W = 8;
+constexpr float NU_BETA = 2.30f * NU_W;
+constexpr double NU_BETA_D = 2.30 * NU_W;
+
+__device__ __forceinline__ float es_phi(float z) {
+    const float q = 1.0f - z * z;
+    return q > 0.0f ? expf(NU_BETA * (sqrtf(q) - 1.0f)) : 0.0f;
+}
+
+// Path i in grid coordinates: the first cell l0 of its W-cell support, the FP32
+// offset d0 = l0 - M x (in [-W/2, -W/2 + 1)), and the carrier phasor
+// exp(-j 2 pi f_c tau).  The cell position is formed in FP64, so the phase error
+// of any mode stays ~1e-7 rad.
+__device__ __forceinline__ void nu_place(double tau, double fc, double df, int M, int& l0, float& d0, float2& e) {
+    const double pc = fc * tau;
+    const float fr = (float)(pc - floor(pc));
+    float sn, cs;
+    sincospif(-2.0f * fr, &sn, &cs);
+    e = make_float2(cs, sn);
+    const double xd = df * tau;
+    const double xm = (xd - floor(xd)) * (double)M;
+    const double l0d = ceil(xm - 0.5 * NU_W);
+    l0 = (int)l0d;
+    d0 = (float)(l0d - xm);
+}
+
+// In-place radix-2 FFT of M = 2^logM complex values in shared memory by a CTA of
+// TC_THREADS threads: X[k] = sum_l x[l] exp(sign j 2 pi k l / M).
+__device__ void fft_smem(float2* x, int M, int logM, float sign) {
+    for (int i = threadIdx.x; i < M; i += TC_THREADS) {
+        const int j = (int)(__brev((unsigned)i) >> (32 - logM));
+        if (i < j) {
+            const float2 t = x[i];
+            x[i] = x[j];
+            x[j] = t;
+        }
+    }
+    __syncthreads();
+    for (int st = 1; st <= logM; ++st) {
+        const int half = 1 << (st - 1);
+        for (int b = threadIdx.x; b < M / 2; b += TC_THREADS) {
+            const int pos = b & (half - 1);
+            const int i0 = ((b >> (st - 1)) << st) + pos, i1 = i0 + half;
+            float sn, cs;
+            sincospif(sign * (float)pos / (float)half, &sn, &cs);
+            const float2 v = x[i1], u = x[i0];
+            const float2 t = make_float2(cs * v.x - sn * v.y, cs * v.y + sn * v.x);
+            x[i0] = make_float2(u.x + t.x, u.y + t.y);
+            x[i1] = make_float2(u.x - t.x, u.y - t.y);
+        }
+        __syncthreads();
+    }
+}
 
 // Bounded wait of one thread until *flag reaches `want`; false on time-out.
 __device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int want) {
@@ -710,7 +781,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
         const int P = (int)(i1 - i0);
         if (MODE == 3 && kind == 3) {
             // a heavy receiver: clear its row and counters, then publish it
-            for (int c = tid; c < S.N; c += TC_THREADS) sp.acc[(int64_t)slot * S.N + c] = make_float2(0.0f, 0.0f);
+            for (int c = tid; c < 2 * S.N; c += TC_THREADS) sp.acc[(int64_t)slot * 2 * S.N + c] = make_float2(0.0f, 0.0f);
             if (tid == 0) {
                 sp.list[slot] = r;
                 sp.seg_next[slot] = 0u;
@@ -726,7 +797,102 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
             }
             continue;
         }
-        const bool do_fwd = FWD && kind != 2;
+        if (MODE == 3 && (kind == 1 || kind == 2)) {
+            // a segment of a split receiver: non-uniform FFT on its grid row
+            const int M = 2 * S.N, logM = 31 - __clz(M);
+            const double fc = S.f0 + 0.5 * (double)S.N * S.df;
+            float2* grid = reinterpret_cast<float2*>(A_hi);   // M values (fits in the operand tiles)
+            float2* row = sp.acc + (int64_t)slot * M;
+            if (kind == 1) {
+                for (int l = tid; l < M; l += TC_THREADS) grid[l] = make_float2(0.0f, 0.0f);
+                __syncthreads();
+                for (int64_t i = i0 + tid; i < i1; i += TC_THREADS) {
+                    int l0;
+                    float d0;
+                    float2 e;
+                    nu_place(tau[i], fc, S.df, M, l0, d0, e);
+                    const float2 cp = cmul(a[i], e);
+#pragma unroll
+                    for (int k = 0; k < NU_W; ++k) {
+                        const float wk = es_phi((d0 + (float)k) * (2.0f / NU_W));
+                        float2* gp = grid + ((l0 + k) & (M - 1));
+                        atomicAdd(&gp->x, wk * cp.x);
+                        atomicAdd(&gp->y, wk * cp.y);
+                    }
+                }
+                __syncthreads();
+                for (int l = tid; l < M; l += TC_THREADS) {
+                    const float2 v = grid[l];
+                    if (v.x != 0.0f) atomicAdd(&row[l].x, v.x);
+                    if (v.y != 0.0f) atomicAdd(&row[l].y, v.y);
+                }
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) s_last = atomicAdd(sp.fwd_done + slot, 1u) == (unsigned int)(s_nseg - 1);
+                __syncthreads();
+                if (!s_last) continue;
+                // the last segment: H, the loss partial, then the adjoint grid b'
+                __threadfence();
+                for (int l = tid; l < M; l += TC_THREADS) grid[l] = __ldcg(row + l);
+                __syncthreads();
+                fft_smem(grid, M, logM, -1.0f);
+                const float wr = w[r];
+                double lsum = 0.0;
+                for (int c = tid; c < S.N; c += TC_THREADS) {
+                    const int idx = (c - S.N / 2) & (M - 1);
+                    const float dv = sp.dec[c];
+                    const float2 h = make_float2(grid[idx].x * dv, grid[idx].y * dv);
+                    const float e = h.x * h.x + h.y * h.y - target[(int64_t)r * S.N + c];
+                    const float we = wr * e;
+                    lsum += (double)(we * we);
+                    const float sc = 4.0f * wr * wr * e * inv_rn * dv;
+                    if (H) H[(int64_t)r * S.N + c] = h;
+                    grid[idx] = make_float2(sc * h.x, sc * h.y);
+                }
+                for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+                if (lane == 0) s_red[warp] = lsum;
+                __syncthreads();
+                for (int l = S.N / 2 + tid; l < M - S.N / 2; l += TC_THREADS) grid[l] = make_float2(0.0f, 0.0f);
+                __syncthreads();
+                fft_smem(grid, M, logM, 1.0f);
+                for (int l = tid; l < M; l += TC_THREADS) row[l] = grid[l];
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) {
+                    part[r] = s_red[0] + s_red[1] + s_red[2] + s_red[3];
+                    __threadfence();
+                    atomicExch(sp.ready + slot, 1u);
+                }
+                continue;
+            }
+            // kind 2: dL/da of the segment's paths once the adjoint grid is ready
+            if (tid == 0) s_last = wait_flag(sp.ready + slot, 1u);
+            __syncthreads();
+            if (!s_last) {
+                ok = false;
+                break;
+            }
+            __threadfence();
+            for (int l = tid; l < M; l += TC_THREADS) grid[l] = __ldcg(row + l);
+            __syncthreads();
+            for (int64_t i = i0 + tid; i < i1; i += TC_THREADS) {
+                int l0;
+                float d0;
+                float2 e;
+                nu_place(tau[i], fc, S.df, M, l0, d0, e);
+                float2 gc = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int k = 0; k < NU_W; ++k) {
+                    const float wk = es_phi((d0 + (float)k) * (2.0f / NU_W));
+                    const float2 v = grid[(l0 + k) & (M - 1)];
+                    gc.x = fmaf(wk, v.x, gc.x);
+                    gc.y = fmaf(wk, v.y, gc.y);
+                }
+                ga[i] = cmulc(gc, e);
+            }
+            continue;
+        }
+        const bool do_fwd = FWD;
         const bool direct = P <= TC_DIRECT;
         const int nch = (P + TC_CP - 1) / TC_CP;
         float hre[N2], him[N2];
@@ -816,61 +982,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
             continue;
         }
         float gre[N2], gim[N2];
-        if (MODE == 3 && kind == 1) {
-            // forward segment of a split receiver: add the partial H to its row
-            float2* row = sp.acc + (int64_t)slot * S.N + (int64_t)m * N2;
-#pragma unroll
-            for (int c2 = 0; c2 < N2; ++c2) {
-                atomicAdd(&row[c2].x, hre[c2]);
-                atomicAdd(&row[c2].y, him[c2]);
-            }
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) s_last = atomicAdd(sp.fwd_done + slot, 1u) == (unsigned int)(s_nseg - 1);
-            __syncthreads();
-            if (!s_last) continue;
-            // the last segment: H complete; loss partial and dL/dH in place of H
-            __threadfence();
-            const float wr = w[r];
-            double lsum = 0.0;
-#pragma unroll
-            for (int c2 = 0; c2 < N2; ++c2) {
-                const float2 h = __ldcg(row + c2);
-                const float e = h.x * h.x + h.y * h.y - target[hrow + c2];
-                const float we = wr * e;
-                lsum += (double)(we * we);
-                const float sc = 4.0f * wr * wr * e * inv_rn;
-                row[c2] = make_float2(sc * h.x, sc * h.y);
-                if (H) H[hrow + c2] = h;
-            }
-            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
-            if (lane == 0) s_red[warp] = lsum;
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) {
-                part[r] = s_red[0] + s_red[1] + s_red[2] + s_red[3];
-                __threadfence();
-                atomicExch(sp.ready + slot, 1u);
-            }
-            continue;
-        }
-        if (MODE == 3 && kind == 2) {
-            // adjoint segment of a split receiver: dL/dH from its row once ready
-            if (tid == 0) s_last = wait_flag(sp.ready + slot, 1u);
-            __syncthreads();
-            if (!s_last) {
-                ok = false;
-                break;
-            }
-            __threadfence();
-            const float2* row = sp.acc + (int64_t)slot * S.N + (int64_t)m * N2;
-#pragma unroll
-            for (int c2 = 0; c2 < N2; ++c2) {
-                const float2 g = __ldcg(row + c2);
-                gre[c2] = g.x;
-                gim[c2] = g.y;
-            }
-        } else if (LOSS) {
+        if (LOSS) {
             const float wr = w[r];
             double lsum = 0.0;
 #pragma unroll
@@ -1215,8 +1327,46 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fus
         // receivers with many paths are deferred and split over CTAs (mode 3)
         int* ints = nullptr;
         void* acc = nullptr;
-        s = rt_cfr_split_scratch(ctx, TC_HEAVY_CAP, (size_t)TC_HEAVY_CAP * (size_t)n_sub * sizeof(float2), &ints, &acc);
+        float* dec = nullptr;
+        int* dec_n = nullptr;
+        s = rt_cfr_split_scratch(ctx, TC_HEAVY_CAP, (size_t)TC_HEAVY_CAP * 2 * (size_t)n_sub * sizeof(float2), &ints,
+                                 &acc, &dec, &dec_n);
         if (s != RT_OK) return s;
+        if (*dec_n != n_sub) {
+            // 1 / (M phi_hat(n)), M phi_hat(n) = W/2 int_{-1}^{1} phi(z) cos(pi n W z / M) dz
+            // (Gauss-Legendre, 256 nodes by Newton iteration on P_256)
+            const int Q = 256;
+            std::vector<double> zq(Q), wq(Q);
+            for (int i = 0; i < Q; ++i) {
+                double z = std::cos(RT_PI * (i + 0.75) / (Q + 0.5)), dp = 1.0;
+                for (int it = 0; it < 100; ++it) {
+                    double p0 = 1.0, p1 = z;
+                    for (int k = 2; k <= Q; ++k) {
+                        const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                        p0 = p1;
+                        p1 = p2;
+                    }
+                    dp = Q * (z * p1 - p0) / (z * z - 1.0);
+                    const double dz = p1 / dp;
+                    z -= dz;
+                    if (std::fabs(dz) < 1e-15) break;
+                }
+                zq[i] = z;
+                wq[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+            }
+            const int M = 2 * n_sub;
+            std::vector<float> hd(n_sub);
+            for (int c = 0; c < n_sub; ++c) {
+                const double n = (double)(c - n_sub / 2);
+                double acc_q = 0.0;
+                for (int i = 0; i < Q; ++i)
+                    acc_q += wq[i] * std::exp(NU_BETA_D * (std::sqrt(1.0 - zq[i] * zq[i]) - 1.0)) *
+                             std::cos(RT_PI * n * NU_W * zq[i] / M);
+                hd[c] = (float)(1.0 / (0.5 * NU_W * acc_q));
+            }
+            RT_CK(ctx, cudaMemcpy(dec, hd.data(), n_sub * sizeof(float), cudaMemcpyHostToDevice));
+            *dec_n = n_sub;
+        }
         TcSplit sp;
         sp.cnt = reinterpret_cast<unsigned int*>(ints);   // zeroed with the tables, once per context
         sp.list = ints + 8;
@@ -1226,6 +1376,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fus
         sp.ready = sp.fwd_done + TC_HEAVY_CAP;
         sp.pub = sp.ready + TC_HEAVY_CAP;
         sp.acc = static_cast<float2*>(acc);
+        sp.dec = dec;
         return launch_tc<3>(ctx, S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, target_power_dev,
                             rx_weight_dev, nullptr, loss_dev, (float2*)grad_a_dev, (float2*)H_dev, part, done, sp);
     }
