@@ -379,44 +379,67 @@ __global__ void __launch_bounds__(DF_THREADS) k_df_rays(int64_t N, int D, double
 }
 
 // ------------------------------------------------------------------ 2. next-event estimation
+// One (source, receiver) pair of the next-event estimation: source s = i D + b is
+// hit b of launch ray i.
+__device__ __forceinline__ void nee_pair(int64_t N, int b, int i, int s, int r, double tx0, double tx1, double tx2,
+                                     const double* __restrict__ rx, const int32_t* __restrict__ tri,
+                                     const double* __restrict__ pt, const Scn& S, uint32_t* __restrict__ mask,
+                                     int64_t W, int32_t* status) {
+    const int t = __ldg(tri + (int64_t)b * N + i);
+    if (t < 0) return;
+    double p[3], pv[3], n[3], x[3];
+    for (int c = 0; c < 3; ++c) {
+        p[c] = __ldg(pt + ((int64_t)b * N + i) * 3 + c);
+        x[c] = __ldg(rx + 3 * (int64_t)r + c);
+    }
+    if (b == 0) {
+        pv[0] = tx0;
+        pv[1] = tx1;
+        pv[2] = tx2;
+    } else {
+        for (int c = 0; c < 3; ++c) pv[c] = __ldg(pt + ((int64_t)(b - 1) * N + i) * 3 + c);
+    }
+    load_n(S.n64, t, n);
+    const double side_in = (pv[0] - p[0]) * n[0] + (pv[1] - p[1]) * n[1] + (pv[2] - p[2]) * n[2];
+    const double side_rx = (x[0] - p[0]) * n[0] + (x[1] - p[1]) * n[1] + (x[2] - p[2]) * n[2];
+    if (!((side_in > 0.0 && side_rx > 0.0) || (side_in < 0.0 && side_rx < 0.0))) return;
+    Ray64 ray;
+    for (int c = 0; c < 3; ++c) {
+        ray.o[c] = p[c];
+        ray.d[c] = x[c] - p[c];
+    }
+    const double len2 = ray.d[0] * ray.d[0] + ray.d[1] * ray.d[1] + ray.d[2] * ray.d[2];
+    if (!(len2 > S.eps * S.eps)) return;
+    if (any_hit_seg(S.nodes, S.tris, ray, len2, S.eps, t, status)) return;
+    atomicOr(mask + (int64_t)r * W + (s >> 5), 1u << (s & 31));
+}
+
 // Pair index q = s * R + r (receivers fastest, so a warp shares its origin).
 __global__ void __launch_bounds__(DF_THREADS) k_df_nee(int64_t N, int D, int R, double tx0, double tx1, double tx2,
                                                        const double* __restrict__ rx, const int32_t* __restrict__ tri,
                                                        const double* __restrict__ pt, Scn S, uint32_t* __restrict__ mask,
                                                        int64_t W, int32_t* status) {
+    // q = s R + r, advanced by the grid stride without a 64-bit division per pair
+    // (s = i D + b < 2^31: n_rays max_depth < 2^31 is checked on the host)
     const int64_t total = N * D * (int64_t)R;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(q % R);
-        const int64_t s = q / R;
-        const int64_t i = s / D;
-        const int b = (int)(s - i * D);
-        const int t = __ldg(tri + (int64_t)b * N + i);
-        if (t < 0) continue;
-        double p[3], pv[3], n[3], x[3];
-        for (int c = 0; c < 3; ++c) {
-            p[c] = __ldg(pt + ((int64_t)b * N + i) * 3 + c);
-            x[c] = __ldg(rx + 3 * (int64_t)r + c);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t q0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q0 >= total) return;
+    int r = (int)(q0 % R);
+    int64_t s = q0 / R;
+    const int64_t ds = stride / R;
+    const int dr = (int)(stride % R);
+    for (int64_t q = q0; q < total; q += stride) {
+        const int si = (int)s;
+        const int i = si / D;
+        const int b = si - i * D;
+        nee_pair(N, b, i, si, r, tx0, tx1, tx2, rx, tri, pt, S, mask, W, status);
+        s += ds;
+        r += dr;
+        if (r >= R) {
+            r -= R;
+            ++s;
         }
-        if (b == 0) {
-            pv[0] = tx0;
-            pv[1] = tx1;
-            pv[2] = tx2;
-        } else {
-            for (int c = 0; c < 3; ++c) pv[c] = __ldg(pt + ((int64_t)(b - 1) * N + i) * 3 + c);
-        }
-        load_n(S.n64, t, n);
-        const double side_in = (pv[0] - p[0]) * n[0] + (pv[1] - p[1]) * n[1] + (pv[2] - p[2]) * n[2];
-        const double side_rx = (x[0] - p[0]) * n[0] + (x[1] - p[1]) * n[1] + (x[2] - p[2]) * n[2];
-        if (!((side_in > 0.0 && side_rx > 0.0) || (side_in < 0.0 && side_rx < 0.0))) continue;
-        Ray64 ray;
-        for (int c = 0; c < 3; ++c) {
-            ray.o[c] = p[c];
-            ray.d[c] = x[c] - p[c];
-        }
-        const double len2 = ray.d[0] * ray.d[0] + ray.d[1] * ray.d[1] + ray.d[2] * ray.d[2];
-        if (!(len2 > S.eps * S.eps)) continue;
-        if (any_hit_seg(S.nodes, S.tris, ray, len2, S.eps, t, status)) continue;
-        atomicOr(mask + (int64_t)r * W + (s >> 5), 1u << (s & 31));
     }
 }
 
@@ -522,30 +545,38 @@ struct D3 {
 };
 __device__ __forceinline__ D3 d3(double x, double y, double z) { return D3{x, y, z}; }
 __device__ __forceinline__ D3 sub(D3 a, D3 b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ D3 scl(double s, D3 a) { return d3(s * a.x, s * a.y, s * a.z); }
 __device__ __forceinline__ double dotd(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ D3 crossd(D3 a, D3 b) {
-    return d3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ D3 unitd(D3 a) { return scl(1.0 / sqrt(dotd(a, a)), a); }
 
-// theta_hat, phi_hat of unit direction k (phi = 0 for a vertical direction).
-__device__ __forceinline__ void sph_basis(D3 k, D3* th, D3* ph) {
-    const double st = sqrt(k.x * k.x + k.y * k.y);
-    double cp = 1.0, sp = 0.0;
-    if (st > 0.0) {
+// FP32 counterparts for the bases of the records.
+struct F3 {
+    float x, y, z;
+};
+__device__ __forceinline__ F3 f3(float x, float y, float z) { return F3{x, y, z}; }
+__device__ __forceinline__ F3 fsub(F3 a, F3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ F3 fscl(float s, F3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float fdot(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ F3 fcross(F3 a, F3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ F3 funit(F3 a) { return fscl(1.0f / sqrtf(fdot(a, a)), a); }
+
+__device__ __forceinline__ void sph_basis_f(F3 k, F3* th, F3* ph) {
+    const float st = sqrtf(k.x * k.x + k.y * k.y);
+    float cp = 1.0f, sp = 0.0f;
+    if (st > 0.0f) {
         cp = k.x / st;
         sp = k.y / st;
     }
-    *th = d3(k.z * cp, k.z * sp, -st);
-    *ph = d3(-sp, cp, 0.0);
+    *th = f3(k.z * cp, k.z * sp, -st);
+    *ph = f3(-sp, cp, 0.0f);
 }
 
-// unit(k x n), or where k is (numerically) along n, `fb` made orthogonal to k.
-__device__ __forceinline__ D3 perp_or(D3 k, D3 n, D3 fb) {
-    const D3 c = crossd(k, n);
-    if (sqrt(dotd(c, c)) > 1e-12) return unitd(c);
-    return unitd(sub(fb, scl(dotd(fb, k), k)));
+// unit(k x n), or where k is (numerically) along n, `fb` made orthogonal to k
+// (at such incidences every transverse basis gives the same field magnitude).
+__device__ __forceinline__ F3 perp_or_f(F3 k, F3 n, F3 fb) {
+    const F3 c = fcross(k, n);
+    if (fdot(c, c) > 1e-12f) return funit(c);
+    return funit(fsub(fb, fscl(fdot(fb, k), k)));
 }
 
 struct RecOut {
@@ -567,9 +598,9 @@ __global__ void k_df_records(int64_t P, int64_t N, int D, double tx0, double tx1
                              const int32_t* __restrict__ tri_material, const uint8_t* __restrict__ is_pec,
                              RecOut O) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = src[i];
-        const int64_t ray = s / D;
-        const int j = (int)(s - ray * D) + 1;
+        const int s = (int)src[i];   // < n_rays max_depth < 2^31
+        const int ray = s / D;
+        const int j = s - ray * D + 1;
         const int r = prx[i];
         D3 pts[RT_MAX_DEPTH + 2];
         pts[0] = d3(tx0, tx1, tx2);
@@ -591,50 +622,51 @@ __global__ void k_df_records(int64_t P, int64_t N, int D, double tx0, double tx1
             tt[b] = b < j ? hit_tri[(int64_t)b * N + ray] : -1;
             O.tri[(int64_t)b * P + i] = tt[b];
         }
-        D3 k[RT_MAX_DEPTH + 2];
+        // lengths and delay in FP64; directions and every basis in FP32 (the records
+        // are stored in FP32)
+        F3 k[RT_MAX_DEPTH + 2];
         double ell = 0.0, dl = 0.0;
         for (int b = 1; b <= j + 1; ++b) {
             const D3 dv = sub(pts[b], pts[b - 1]);
             const double db = sqrt(dotd(dv, dv));
-            k[b] = scl(1.0 / db, dv);
+            const float inv = 1.0f / (float)db;
+            k[b] = f3((float)dv.x * inv, (float)dv.y * inv, (float)dv.z * inv);
             if (b <= j) ell += db;
             else dl = db;
         }
         O.tau[i] = (ell + dl) / RT_C0;
         O.len[i] = (float)dl;
-        D3 out_p, out_q;
-        sph_basis(k[1], &out_p, &out_q);
+        F3 out_p, out_q;
+        sph_basis_f(k[1], &out_p, &out_q);
         for (int b = 1; b <= j; ++b) {
             const int t = tt[b - 1];
-            D3 n = d3(n64[4 * t], n64[4 * t + 1], n64[4 * t + 2]);
-            if (dotd(k[b], n) > 0.0) n = scl(-1.0, n);       // facing the incident wave
-            const double cos_i = -dotd(k[b], n);
-            const D3 e_perp = perp_or(k[b], n, out_p);
-            const D3 in_q = crossd(e_perp, k[b]);
-            O.Dm[(int64_t)(b - 1) * P + i] = make_float4((float)dotd(e_perp, out_p), (float)dotd(e_perp, out_q),
-                                                         (float)dotd(in_q, out_p), (float)dotd(in_q, out_q));
+            F3 n = f3((float)n64[4 * t], (float)n64[4 * t + 1], (float)n64[4 * t + 2]);
+            if (fdot(k[b], n) > 0.0f) n = fscl(-1.0f, n);       // facing the incident wave
+            const float cos_i = -fdot(k[b], n);
+            const F3 e_perp = perp_or_f(k[b], n, out_p);
+            const F3 in_q = fcross(e_perp, k[b]);
+            O.Dm[(int64_t)(b - 1) * P + i] =
+                make_float4(fdot(e_perp, out_p), fdot(e_perp, out_q), fdot(in_q, out_p), fdot(in_q, out_q));
             const int mt = tri_material[t];
-            O.mc[(int64_t)(b - 1) * P + i] = make_int2(mt | (is_pec[mt] ? MAT_PEC : 0), __float_as_int((float)cos_i));
+            O.mc[(int64_t)(b - 1) * P + i] = make_int2(mt | (is_pec[mt] ? MAT_PEC : 0), __float_as_int(cos_i));
             if (b < j) {
                 out_p = e_perp;
-                out_q = crossd(e_perp, k[b + 1]);
+                out_q = fcross(e_perp, k[b + 1]);
                 continue;
             }
             // diffuse bounce: pattern cosines and the scattered basis
-            const D3 ks = k[j + 1];
-            const D3 kr = sub(k[j], scl(2.0 * dotd(k[j], n), n));
-            O.scat[i] = make_float4((float)dotd(ks, n), (float)(-dotd(k[j], ks)), (float)dotd(kr, ks),
-                                    (float)(1.0 / dl));
-            const D3 sp = perp_or(ks, n, e_perp);
-            const D3 sq = crossd(sp, ks);
-            D3 th, ph;
-            sph_basis(scl(-1.0, ks), &th, &ph);
-            O.Dm[(int64_t)j * P + i] = make_float4((float)dotd(th, sp), (float)dotd(th, sq), (float)dotd(ph, sp),
-                                                   (float)dotd(ph, sq));
+            const F3 ks = k[j + 1];
+            const F3 kr = fsub(k[j], fscl(2.0f * fdot(k[j], n), n));
+            O.scat[i] = make_float4(fdot(ks, n), -fdot(k[j], ks), fdot(kr, ks), (float)(1.0 / dl));
+            const F3 sp = perp_or_f(ks, n, e_perp);
+            const F3 sq = fcross(sp, ks);
+            F3 th, ph;
+            sph_basis_f(fscl(-1.0f, ks), &th, &ph);
+            O.Dm[(int64_t)j * P + i] = make_float4(fdot(th, sp), fdot(th, sq), fdot(ph, sp), fdot(ph, sq));
         }
         for (int b = j; b < D; ++b) O.mc[(int64_t)b * P + i] = make_int2(0, 0);
-        O.dir[i] = make_float4((float)k[1].x, (float)k[1].y, (float)k[1].z, 0.0f);
-        O.dir[P + i] = make_float4((float)-k[j + 1].x, (float)-k[j + 1].y, (float)-k[j + 1].z, 0.0f);
+        O.dir[i] = make_float4(k[1].x, k[1].y, k[1].z, 0.0f);
+        O.dir[P + i] = make_float4(-k[j + 1].x, -k[j + 1].y, -k[j + 1].z, 0.0f);
     }
 }
 
