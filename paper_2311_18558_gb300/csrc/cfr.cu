@@ -630,7 +630,7 @@ __device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int
 constexpr int TC_DIRECT = 8;
 
 // MODE 0: forward (H out); 1: adjoint from g_H; 2: forward + power MSE + adjoint;
-// 3: as 2 with receivers of many paths split over CTAs (TcSplit).
+// 3, 4, 5: as 2, 0, 1 with receivers of many paths split over CTAs (TcSplit).
 template <int N2, int MODE>
 __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t* __restrict__ offs, int R,
                                                        const float2* __restrict__ a, const double* __restrict__ tau,
@@ -640,8 +640,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                                                        double* __restrict__ part, unsigned int* __restrict__ ctr,
                                                        int32_t* __restrict__ status, TcSplit sp) {
     using T = TcDims<N2>;
-    constexpr bool FWD = MODE != 1, BWD = MODE != 0;
+    constexpr bool SPLIT = MODE >= 3;                  // receivers of many paths split over CTAs
+    constexpr bool FWD = MODE != 1 && MODE != 5, BWD = MODE != 0 && MODE != 4;
     constexpr bool LOSS = MODE == 2 || MODE == 3;   // loss epilogue of whole receivers
+    constexpr int LAST_PHASE = MODE == 4 ? 1 : 2;   // split work: 1 forward segments, 2 adjoint segments
     extern __shared__ float4 smem4[];
     float* A_hi = reinterpret_cast<float*>(smem4);
     float* A_lo = A_hi + T::A_FLOATS;
@@ -667,7 +669,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
     if (tid == 0) mbar_init(mb, 1);
     __syncthreads();
     // mode 3: this call's epoch (only the last CTA advances it, at the very end)
-    const unsigned int epoch = MODE == 3 ? __ldcg(sp.cnt + 4) : 0u;
+    const unsigned int epoch = SPLIT ? __ldcg(sp.cnt + 4) : 0u;
     int phase = 0;   // mode 3, thread 0: 0 receivers, 1 heavy forward segments, 2 heavy adjoint segments
     if (warp == 0) tmem_alloc(smem_u32(&tmem_sh), TC_TMEM_COLS);
     tc_fence_before();
@@ -700,7 +702,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
         if (tid == 0) {
             int kind = 0, slot = -1, nseg = 1, rr = R;
             int64_t a0 = 0, a1 = 0;
-            if (MODE == 3 && phase == 0) {
+            if (SPLIT && phase == 0) {
                 rr = (int)atomicAdd(ctr + 1, 1u);
                 if (rr < R) {
                     a0 = offs[rr];
@@ -716,24 +718,24 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                     }
                     if (!defer) atomicAdd(sp.cnt + 3, 1u);   // classified
                 } else {
-                    phase = 1;
+                    phase = MODE == 5 ? 2 : 1;
                 }
             }
-            if (MODE == 3 && phase > 0) {
+            if (SPLIT && phase > 0) {
                 // heavy receivers: claim a forward segment; once the heavy list is final
                 // and every forward segment claimed, an adjoint segment
                 rr = R;
-                for (int it = 0; it < TC_WAIT_LIMIT && rr == R && phase <= 2; ++it) {
+                for (int it = 0; it < TC_WAIT_LIMIT && rr == R && phase <= LAST_PHASE; ++it) {
                     unsigned int* cur = sp.cnt + phase;
                     unsigned int* next = phase == 1 ? sp.seg_next : sp.adj_next;
                     const int h = (int)*(volatile unsigned int*)cur;
                     const int n_met = (int)min(*(volatile unsigned int*)sp.cnt, (unsigned int)TC_HEAVY_CAP);
                     if (h >= n_met) {
-                        if (phase == 1 && *(volatile unsigned int*)(sp.cnt + 3) < (unsigned int)R) {
+                        if (*(volatile unsigned int*)(sp.cnt + 3) < (unsigned int)R) {
                             __nanosleep(64);   // receivers still being classified: more may come
                             continue;
                         }
-                        if (phase == 1 && (int)min(*(volatile unsigned int*)sp.cnt, (unsigned int)TC_HEAVY_CAP) > h)
+                        if ((int)min(*(volatile unsigned int*)sp.cnt, (unsigned int)TC_HEAVY_CAP) > h)
                             continue;   // appended while we looked
                         ++phase;
                         continue;
@@ -758,8 +760,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                     }
                     atomicCAS(cur, (unsigned int)h, (unsigned int)h + 1u);
                 }
-                if (rr == R && phase <= 2) rt_set_status(status, RT_ERR_TIMEOUT);
-            } else if (MODE != 3) {
+                if (rr == R && phase <= LAST_PHASE) rt_set_status(status, RT_ERR_TIMEOUT);
+            } else if (!SPLIT) {
                 rr = (int)atomicAdd(ctr + 1, 1u);
                 if (rr < R) {
                     a0 = offs[rr];
@@ -779,15 +781,32 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
         const int kind = s_kind, slot = s_slot;
         const int64_t i0 = s_i0, i1 = s_i1;
         const int P = (int)(i1 - i0);
-        if (MODE == 3 && kind == 3) {
-            // a heavy receiver: clear its row and counters, then publish it
-            for (int c = tid; c < 2 * S.N; c += TC_THREADS) sp.acc[(int64_t)slot * 2 * S.N + c] = make_float2(0.0f, 0.0f);
+        if (SPLIT && kind == 3) {
+            // a heavy receiver: clear its row and counters (mode 5: put the transformed
+            // dL/dH in the row at once), then publish it
+            const int M = 2 * S.N;
+            float2* row = sp.acc + (int64_t)slot * M;
+            if (MODE == 5) {
+                float2* grid = reinterpret_cast<float2*>(A_hi);
+                for (int l = tid; l < M; l += TC_THREADS) grid[l] = make_float2(0.0f, 0.0f);
+                __syncthreads();
+                for (int c = tid; c < S.N; c += TC_THREADS) {
+                    const float2 g = gH[(int64_t)r * S.N + c];
+                    const float dv = sp.dec[c];
+                    grid[(c - S.N / 2) & (M - 1)] = make_float2(g.x * dv, g.y * dv);
+                }
+                __syncthreads();
+                fft_smem(grid, M, 31 - __clz(M), 1.0f);
+                for (int l = tid; l < M; l += TC_THREADS) row[l] = grid[l];
+            } else {
+                for (int l = tid; l < M; l += TC_THREADS) row[l] = make_float2(0.0f, 0.0f);
+            }
             if (tid == 0) {
                 sp.list[slot] = r;
                 sp.seg_next[slot] = 0u;
                 sp.adj_next[slot] = 0u;
                 sp.fwd_done[slot] = 0u;
-                sp.ready[slot] = 0u;
+                sp.ready[slot] = MODE == 5 ? 1u : 0u;
             }
             __threadfence();
             __syncthreads();
@@ -797,7 +816,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
             }
             continue;
         }
-        if (MODE == 3 && (kind == 1 || kind == 2)) {
+        if (SPLIT && (kind == 1 || kind == 2)) {
             // a segment of a split receiver: non-uniform FFT on its grid row
             const int M = 2 * S.N, logM = 31 - __clz(M);
             const double fc = S.f0 + 0.5 * (double)S.N * S.df;
@@ -836,6 +855,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                 for (int l = tid; l < M; l += TC_THREADS) grid[l] = __ldcg(row + l);
                 __syncthreads();
                 fft_smem(grid, M, logM, -1.0f);
+                if (MODE == 4) {
+                    for (int c = tid; c < S.N; c += TC_THREADS) {
+                        const int idx = (c - S.N / 2) & (M - 1);
+                        const float dv = sp.dec[c];
+                        H[(int64_t)r * S.N + c] = make_float2(grid[idx].x * dv, grid[idx].y * dv);
+                    }
+                    continue;
+                }
                 const float wr = w[r];
                 double lsum = 0.0;
                 for (int c = tid; c < S.N; c += TC_THREADS) {
@@ -976,7 +1003,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
 
         // ---- epilogue: H out, loss, g_H
         const int64_t hrow = (int64_t)r * S.N + (int64_t)m * N2;
-        if (MODE == 0) {
+        if (MODE == 0 || MODE == 4) {
 #pragma unroll
             for (int c2 = 0; c2 < N2; ++c2) H[hrow + c2] = make_float2(hre[c2], him[c2]);
             continue;
@@ -1158,7 +1185,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
         if (tid == 0) {
             ctr[0] = 0u;
             ctr[1] = 0u;
-            if (MODE == 3) {
+            if (SPLIT) {
                 sp.cnt[0] = 0u;
                 sp.cnt[1] = 0u;
                 sp.cnt[2] = 0u;
@@ -1187,7 +1214,7 @@ rt_status launch_tc(rt_ctx* ctx, const CfrShape& S, const int64_t* offs, int R, 
         RT_CK(ctx, cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device));
         int per_sm = smem_sm / (int)(smem + 64 + (size_t)reserved);
         per_sm = std::max(1, std::min(per_sm, (int)(512 / TC_TMEM_COLS)));
-        const int grid = std::max(1, MODE == 3 ? ctx->num_sms * per_sm : std::min(R, ctx->num_sms * per_sm));
+        const int grid = std::max(1, MODE >= 3 ? ctx->num_sms * per_sm : std::min(R, ctx->num_sms * per_sm));
         kern<<<grid, TC_THREADS, smem, ctx->stream>>>(S, offs, R, a, tau, target, w, gH, loss, ga, H, part, ctr,
                                                        ctx->d_status, sp);
         RT_COUNT(ctx);
@@ -1257,6 +1284,63 @@ static rt_status set_smem(rt_ctx* ctx, K kernel, size_t bytes) {
     return RT_OK;
 }
 
+// Scratch of the heavy-receiver split (modes 3 to 5) and the per-column factors
+// 1 / (M phi_hat(n)) of its non-uniform FFT (made on the host when n_sub changes).
+static rt_status split_setup(rt_ctx* ctx, int n_sub, TcSplit* sp) {
+    int* ints = nullptr;
+    void* acc = nullptr;
+    float* dec = nullptr;
+    int* dec_n = nullptr;
+    rt_status s = rt_cfr_split_scratch(ctx, TC_HEAVY_CAP, (size_t)TC_HEAVY_CAP * 2 * (size_t)n_sub * sizeof(float2), &ints,
+                             &acc, &dec, &dec_n);
+    if (s != RT_OK) return s;
+    if (*dec_n != n_sub) {
+        // 1 / (M phi_hat(n)), M phi_hat(n) = W/2 int_{-1}^{1} phi(z) cos(pi n W z / M) dz
+        // (Gauss-Legendre, 256 nodes by Newton iteration on P_256)
+        const int Q = 256;
+        std::vector<double> zq(Q), wq(Q);
+        for (int i = 0; i < Q; ++i) {
+            double z = std::cos(RT_PI * (i + 0.75) / (Q + 0.5)), dp = 1.0;
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1.0, p1 = z;
+                for (int k = 2; k <= Q; ++k) {
+                    const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                dp = Q * (z * p1 - p0) / (z * z - 1.0);
+                const double dz = p1 / dp;
+                z -= dz;
+                if (std::fabs(dz) < 1e-15) break;
+            }
+            zq[i] = z;
+            wq[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        }
+        const int M = 2 * n_sub;
+        std::vector<float> hd(n_sub);
+        for (int c = 0; c < n_sub; ++c) {
+            const double n = (double)(c - n_sub / 2);
+            double acc_q = 0.0;
+            for (int i = 0; i < Q; ++i)
+                acc_q += wq[i] * std::exp(NU_BETA_D * (std::sqrt(1.0 - zq[i] * zq[i]) - 1.0)) *
+                         std::cos(RT_PI * n * NU_W * zq[i] / M);
+            hd[c] = (float)(1.0 / (0.5 * NU_W * acc_q));
+        }
+        RT_CK(ctx, cudaMemcpy(dec, hd.data(), n_sub * sizeof(float), cudaMemcpyHostToDevice));
+        *dec_n = n_sub;
+    }
+    sp->cnt = reinterpret_cast<unsigned int*>(ints);   // zeroed with the tables, once per context
+    sp->list = ints + 8;
+    sp->seg_next = reinterpret_cast<unsigned int*>(sp->list + TC_HEAVY_CAP);
+    sp->adj_next = sp->seg_next + TC_HEAVY_CAP;
+    sp->fwd_done = sp->adj_next + TC_HEAVY_CAP;
+    sp->ready = sp->fwd_done + TC_HEAVY_CAP;
+    sp->pub = sp->ready + TC_HEAVY_CAP;
+    sp->acc = static_cast<float2*>(acc);
+    sp->dec = dec;
+    return RT_OK;
+}
+
 extern "C" __attribute__((visibility("default"))) rt_status rt_cfr(rt_ctx* ctx, const int64_t* rx_offsets_dev, int32_t n_rx, const void* a_dev,
                             const double* tau_dev, double f_center_hz, double delta_f_hz, int32_t n_sub, void* H_dev) {
     CfrShape S;
@@ -1268,8 +1352,11 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr(rt_ctx* ctx, 
         unsigned int* ctr;
         s = rt_cfr_fused_scratch(ctx, n_rx, &part, &ctr);
         if (s != RT_OK) return s;
-        return launch_tc<0>(ctx, S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, nullptr, nullptr, nullptr,
-                            nullptr, nullptr, (float2*)H_dev, part, ctr);
+        TcSplit sp;
+        s = split_setup(ctx, n_sub, &sp);
+        if (s != RT_OK) return s;
+        return launch_tc<4>(ctx, S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, nullptr, nullptr, nullptr,
+                            nullptr, nullptr, (float2*)H_dev, part, ctr, sp);
     }
     const size_t smem = fwd_smem(S);
     return dispatch_opt(ctx, S.N, [&](auto opt) -> rt_status {
@@ -1295,8 +1382,11 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_backward(rt_c
         unsigned int* ctr;
         s = rt_cfr_fused_scratch(ctx, n_rx, &part, &ctr);
         if (s != RT_OK) return s;
-        return launch_tc<1>(ctx, S, rx_offsets_dev, n_rx, nullptr, tau_dev, nullptr, nullptr,
-                            (const float2*)grad_H_dev, nullptr, (float2*)grad_a_dev, nullptr, part, ctr);
+        TcSplit sp;
+        s = split_setup(ctx, n_sub, &sp);
+        if (s != RT_OK) return s;
+        return launch_tc<5>(ctx, S, rx_offsets_dev, n_rx, nullptr, tau_dev, nullptr, nullptr,
+                            (const float2*)grad_H_dev, nullptr, (float2*)grad_a_dev, nullptr, part, ctr, sp);
     }
     const size_t smem = fwd_smem(S) + (size_t)S.N * 8;
     s = set_smem(ctx, k_cfr_bwd, smem);
@@ -1325,58 +1415,9 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fus
     if (s != RT_OK) return s;
     if (tc_supported(ctx, n_sub)) {
         // receivers with many paths are deferred and split over CTAs (mode 3)
-        int* ints = nullptr;
-        void* acc = nullptr;
-        float* dec = nullptr;
-        int* dec_n = nullptr;
-        s = rt_cfr_split_scratch(ctx, TC_HEAVY_CAP, (size_t)TC_HEAVY_CAP * 2 * (size_t)n_sub * sizeof(float2), &ints,
-                                 &acc, &dec, &dec_n);
-        if (s != RT_OK) return s;
-        if (*dec_n != n_sub) {
-            // 1 / (M phi_hat(n)), M phi_hat(n) = W/2 int_{-1}^{1} phi(z) cos(pi n W z / M) dz
-            // (Gauss-Legendre, 256 nodes by Newton iteration on P_256)
-            const int Q = 256;
-            std::vector<double> zq(Q), wq(Q);
-            for (int i = 0; i < Q; ++i) {
-                double z = std::cos(RT_PI * (i + 0.75) / (Q + 0.5)), dp = 1.0;
-                for (int it = 0; it < 100; ++it) {
-                    double p0 = 1.0, p1 = z;
-                    for (int k = 2; k <= Q; ++k) {
-                        const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
-                        p0 = p1;
-                        p1 = p2;
-                    }
-                    dp = Q * (z * p1 - p0) / (z * z - 1.0);
-                    const double dz = p1 / dp;
-                    z -= dz;
-                    if (std::fabs(dz) < 1e-15) break;
-                }
-                zq[i] = z;
-                wq[i] = 2.0 / ((1.0 - z * z) * dp * dp);
-            }
-            const int M = 2 * n_sub;
-            std::vector<float> hd(n_sub);
-            for (int c = 0; c < n_sub; ++c) {
-                const double n = (double)(c - n_sub / 2);
-                double acc_q = 0.0;
-                for (int i = 0; i < Q; ++i)
-                    acc_q += wq[i] * std::exp(NU_BETA_D * (std::sqrt(1.0 - zq[i] * zq[i]) - 1.0)) *
-                             std::cos(RT_PI * n * NU_W * zq[i] / M);
-                hd[c] = (float)(1.0 / (0.5 * NU_W * acc_q));
-            }
-            RT_CK(ctx, cudaMemcpy(dec, hd.data(), n_sub * sizeof(float), cudaMemcpyHostToDevice));
-            *dec_n = n_sub;
-        }
         TcSplit sp;
-        sp.cnt = reinterpret_cast<unsigned int*>(ints);   // zeroed with the tables, once per context
-        sp.list = ints + 8;
-        sp.seg_next = reinterpret_cast<unsigned int*>(sp.list + TC_HEAVY_CAP);
-        sp.adj_next = sp.seg_next + TC_HEAVY_CAP;
-        sp.fwd_done = sp.adj_next + TC_HEAVY_CAP;
-        sp.ready = sp.fwd_done + TC_HEAVY_CAP;
-        sp.pub = sp.ready + TC_HEAVY_CAP;
-        sp.acc = static_cast<float2*>(acc);
-        sp.dec = dec;
+        s = split_setup(ctx, n_sub, &sp);
+        if (s != RT_OK) return s;
         return launch_tc<3>(ctx, S, rx_offsets_dev, n_rx, (const float2*)a_dev, tau_dev, target_power_dev,
                             rx_weight_dev, nullptr, loss_dev, (float2*)grad_a_dev, (float2*)H_dev, part, done, sp);
     }

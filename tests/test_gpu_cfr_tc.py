@@ -101,8 +101,9 @@ def test_cfr_tensor_cores(rt, ctx, n_sub):
     assert abs(results[True][2] - results[False][2]) <= 2e-4 * abs(L_ref)
 
 
-# receivers above 4096 paths are split over CTAs in the fused kernel (segments of
-# 1024 paths); 4096 itself stays whole
+# receivers above 4096 paths are split over CTAs (segments of 1024 paths) and
+# evaluated by a non-uniform FFT, in the fused loss, the plain CFR and its
+# adjoint; 4096 itself stays whole
 SPLIT_COUNTS = np.array([3, 4096, 4097, 9000, 0, 40000, 17, 5000], np.int64)
 
 
@@ -120,6 +121,19 @@ def test_fused_split_receivers(rt, ctx, n_sub):
     w = oracle.power_weights(T).astype(np.float32)
     L_ref, _ = oracle.power_mse(Href, T, w)
     o, ad, td = _dev(offs, torch.int64), _dev(a, torch.complex64), _dev(tau, torch.float64)
+    # the plain CFR and its adjoint split the same receivers
+    gH = (rng.normal(size=Href.shape) + 1j * rng.normal(size=Href.shape)).astype(np.complex64)
+    ga_ref = oracle.cfr_grad(tau, offs, fc, df, n_sub, gH.astype(np.complex128))
+    for _ in range(2):
+        Hc = rt.cfr(ctx, o, ad, td, fc, df, n_sub).cpu().numpy()
+        num, den = normwise_rows(Hc, Href)
+        assert (num[den > 0] / den[den > 0]).max() <= 1e-4
+        assert np.all(Hc[SPLIT_COUNTS == 0] == 0)
+        gab = rt.cfr_backward(ctx, o, td, fc, df, n_sub, _dev(gH, torch.complex64)).cpu().numpy()
+        for r in range(len(SPLIT_COUNTS)):
+            s = slice(offs[r], offs[r + 1])
+            if offs[r + 1] > offs[r]:
+                assert np.linalg.norm(gab[s] - ga_ref[s]) <= 1e-4 * np.linalg.norm(ga_ref[s]), r
     Hf = torch.empty((len(offs) - 1, n_sub), dtype=torch.complex64, device="cuda")
     for _ in range(2):   # twice: counters, flags and rows must be reset by each call
         loss, gaf, _ = rt.cfr_power_mse_fused(ctx, o, ad, td, fc, df, n_sub, _dev(T, torch.float32),
