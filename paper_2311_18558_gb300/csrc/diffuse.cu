@@ -219,11 +219,13 @@ struct Ray32 {
     float Sx, Sy, Sz;
 };
 
-__device__ __forceinline__ void ray32_from(const Ray64& r, Ray32& q) {
-    for (int c = 0; c < 3; ++c) {
-        q.o[c] = (float)r.o[c];
-        q.d[c] = (float)r.d[c];
-    }
+__device__ __forceinline__ void ray32_set(float3 o, float3 d, Ray32& q) {
+    q.o[0] = o.x;
+    q.o[1] = o.y;
+    q.o[2] = o.z;
+    q.d[0] = d.x;
+    q.d[1] = d.y;
+    q.d[2] = d.z;
     const float ax = fabsf(q.d[0]), ay = fabsf(q.d[1]), az = fabsf(q.d[2]);
     int kz = 0;
     if (ay > ax) kz = 1;
@@ -286,10 +288,16 @@ __device__ __forceinline__ int tri_seg32(const Ray32& r, float4 p0, float4 p1, f
 // only r.o and r.d need to be set: the FP64 shear and bounds are formed the first
 // time a triangle is undecided (most queries never need them).
 __device__ bool any_hit_seg(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, Ray64& r,
-                            double len2, double eps, int skip, int32_t* status) {
-    ray64_init_box(r);
+                            float3 o32, float3 d32, double len2, double eps, int skip, int32_t* status) {
+    r.of = o32;
+    {
+        const float dk[3] = {d32.x, d32.y, d32.z};
+        float inv[3];
+        for (int k = 0; k < 3; ++k) inv[k] = 1.0f / (fabsf(dk[k]) < 1e-30f ? copysignf(1e-30f, dk[k]) : dk[k]);
+        r.inv = make_float3(inv[0], inv[1], inv[2]);
+    }
     Ray32 q;
-    ray32_from(r, q);
+    ray32_set(o32, d32, q);
     bool hit = false, fp64_ready = false;
     double tlo = 0.0, thi = 0.0;
     const float flo = (float)eps * rsqrtf((float)len2), fthi = 1.0f - flo;
@@ -328,6 +336,7 @@ struct Scn {
     const BvhNode* nodes;
     const float4* tris;      // BVH order, original id in v0.w
     const double* n64;       // 4 per triangle: unit normal, n.v0
+    const float4* plane32;   // 3 per triangle, the first = (unit normal, n.v0) in FP32
     double eps;
 };
 
@@ -343,7 +352,11 @@ __device__ __forceinline__ void load_n(const double* n64, int t, double n[3]) {
 // uncontracted FP64 operations, as the definition writes them.
 __global__ void __launch_bounds__(DF_THREADS) k_df_rays(int64_t N, int D, double tx0, double tx1, double tx2,
                                                         const float* __restrict__ z, Scn S, int32_t* __restrict__ tri,
-                                                        double* __restrict__ pt, int32_t* status) {
+                                                        double* __restrict__ pt, float4* __restrict__ pt32, int R,
+                                                        const double* __restrict__ rx, float4* __restrict__ rx32,
+                                                        int32_t* status) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < R; q += (int64_t)gridDim.x * blockDim.x)
+        rx32[q] = make_float4((float)rx[3 * q], (float)rx[3 * q + 1], (float)rx[3 * q + 2], 0.0f);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const float3 f = launch_dir(i, __ldg(z + i));
         Ray64 r;
@@ -364,6 +377,7 @@ __global__ void __launch_bounds__(DF_THREADS) k_df_rays(int64_t N, int D, double
             for (int c = 0; c < 3; ++c) p[c] = __dadd_rn(r.o[c], __dmul_rn(th, r.d[c]));
             tri[(int64_t)b * N + i] = t;
             for (int c = 0; c < 3; ++c) pt[((int64_t)b * N + i) * 3 + c] = p[c];
+            pt32[(int64_t)b * N + i] = make_float4((float)p[0], (float)p[1], (float)p[2], 0.0f);
             load_n(S.n64, t, n);
             const double dn = __dadd_rn(__dadd_rn(__dmul_rn(r.d[0], n[0]), __dmul_rn(r.d[1], n[1])),
                                         __dmul_rn(r.d[2], n[2]));
@@ -382,27 +396,46 @@ __global__ void __launch_bounds__(DF_THREADS) k_df_rays(int64_t N, int D, double
 // One (source, receiver) pair of the next-event estimation: source s = i D + b is
 // hit b of launch ray i.
 __device__ __forceinline__ void nee_pair(int64_t N, int b, int i, int s, int r, double tx0, double tx1, double tx2,
-                                     const double* __restrict__ rx, const int32_t* __restrict__ tri,
-                                     const double* __restrict__ pt, const Scn& S, uint32_t* __restrict__ mask,
-                                     int64_t W, int32_t* status) {
+                                         const double* __restrict__ rx, const float4* __restrict__ rx32,
+                                         const int32_t* __restrict__ tri, const double* __restrict__ pt,
+                                         const float4* __restrict__ pt32, const Scn& S, uint32_t* __restrict__ mask,
+                                         int64_t W, int32_t* status) {
     const int t = __ldg(tri + (int64_t)b * N + i);
     if (t < 0) return;
-    double p[3], pv[3], n[3], x[3];
+    // sides of the plane in FP32 (the FP32 copies are the rounded FP64 values; the
+    // sign is certain when |side| exceeds 1e-6 (|x|_1 + |p|_1), far above the
+    // rounding of the copies, the normal and the dot product), else in FP64
+    const float4 pf = __ldg(pt32 + (int64_t)b * N + i);
+    const float4 xf = __ldg(rx32 + r);
+    const float4 vf = b == 0 ? make_float4((float)tx0, (float)tx1, (float)tx2, 0.0f)
+                             : __ldg(pt32 + (int64_t)(b - 1) * N + i);
+    const float4 nf = __ldg(S.plane32 + 3 * t);
+    const float sr = (xf.x - pf.x) * nf.x + (xf.y - pf.y) * nf.y + (xf.z - pf.z) * nf.z;
+    const float si = (vf.x - pf.x) * nf.x + (vf.y - pf.y) * nf.y + (vf.z - pf.z) * nf.z;
+    const float ap = fabsf(pf.x) + fabsf(pf.y) + fabsf(pf.z);
+    const float br = 1e-6f * (fabsf(xf.x) + fabsf(xf.y) + fabsf(xf.z) + ap);
+    const float bi = 1e-6f * (fabsf(vf.x) + fabsf(vf.y) + fabsf(vf.z) + ap);
+    double p[3], x[3];
     for (int c = 0; c < 3; ++c) {
         p[c] = __ldg(pt + ((int64_t)b * N + i) * 3 + c);
         x[c] = __ldg(rx + 3 * (int64_t)r + c);
     }
-    if (b == 0) {
-        pv[0] = tx0;
-        pv[1] = tx1;
-        pv[2] = tx2;
+    if (fabsf(sr) > br && fabsf(si) > bi) {
+        if ((sr > 0.0f) != (si > 0.0f)) return;
     } else {
-        for (int c = 0; c < 3; ++c) pv[c] = __ldg(pt + ((int64_t)(b - 1) * N + i) * 3 + c);
+        double pv[3], n[3];
+        if (b == 0) {
+            pv[0] = tx0;
+            pv[1] = tx1;
+            pv[2] = tx2;
+        } else {
+            for (int c = 0; c < 3; ++c) pv[c] = __ldg(pt + ((int64_t)(b - 1) * N + i) * 3 + c);
+        }
+        load_n(S.n64, t, n);
+        const double side_in = (pv[0] - p[0]) * n[0] + (pv[1] - p[1]) * n[1] + (pv[2] - p[2]) * n[2];
+        const double side_rx = (x[0] - p[0]) * n[0] + (x[1] - p[1]) * n[1] + (x[2] - p[2]) * n[2];
+        if (!((side_in > 0.0 && side_rx > 0.0) || (side_in < 0.0 && side_rx < 0.0))) return;
     }
-    load_n(S.n64, t, n);
-    const double side_in = (pv[0] - p[0]) * n[0] + (pv[1] - p[1]) * n[1] + (pv[2] - p[2]) * n[2];
-    const double side_rx = (x[0] - p[0]) * n[0] + (x[1] - p[1]) * n[1] + (x[2] - p[2]) * n[2];
-    if (!((side_in > 0.0 && side_rx > 0.0) || (side_in < 0.0 && side_rx < 0.0))) return;
     Ray64 ray;
     for (int c = 0; c < 3; ++c) {
         ray.o[c] = p[c];
@@ -410,15 +443,18 @@ __device__ __forceinline__ void nee_pair(int64_t N, int b, int i, int s, int r, 
     }
     const double len2 = ray.d[0] * ray.d[0] + ray.d[1] * ray.d[1] + ray.d[2] * ray.d[2];
     if (!(len2 > S.eps * S.eps)) return;
-    if (any_hit_seg(S.nodes, S.tris, ray, len2, S.eps, t, status)) return;
+    const float3 o32 = make_float3(pf.x, pf.y, pf.z);
+    const float3 d32 = make_float3((float)ray.d[0], (float)ray.d[1], (float)ray.d[2]);
+    if (any_hit_seg(S.nodes, S.tris, ray, o32, d32, len2, S.eps, t, status)) return;
     atomicOr(mask + (int64_t)r * W + (s >> 5), 1u << (s & 31));
 }
 
 // Pair index q = s * R + r (receivers fastest, so a warp shares its origin).
 __global__ void __launch_bounds__(DF_THREADS) k_df_nee(int64_t N, int D, int R, double tx0, double tx1, double tx2,
-                                                       const double* __restrict__ rx, const int32_t* __restrict__ tri,
-                                                       const double* __restrict__ pt, Scn S, uint32_t* __restrict__ mask,
-                                                       int64_t W, int32_t* status) {
+                                                       const double* __restrict__ rx, const float4* __restrict__ rx32,
+                                                       const int32_t* __restrict__ tri, const double* __restrict__ pt,
+                                                       const float4* __restrict__ pt32, Scn S,
+                                                       uint32_t* __restrict__ mask, int64_t W, int32_t* status) {
     // q = s R + r, advanced by the grid stride without a 64-bit division per pair
     // (s = i D + b < 2^31: n_rays max_depth < 2^31 is checked on the host)
     const int64_t total = N * D * (int64_t)R;
@@ -433,7 +469,7 @@ __global__ void __launch_bounds__(DF_THREADS) k_df_nee(int64_t N, int D, int R, 
         const int si = (int)s;
         const int i = si / D;
         const int b = si - i * D;
-        nee_pair(N, b, i, si, r, tx0, tx1, tx2, rx, tri, pt, S, mask, W, status);
+        nee_pair(N, b, i, si, r, tx0, tx1, tx2, rx, rx32, tri, pt, pt32, S, mask, W, status);
         s += ds;
         r += dr;
         if (r >= R) {
@@ -674,44 +710,57 @@ __global__ void k_df_records(int64_t P, int64_t N, int D, double tx0, double tx1
 // One lobe exp(lambda c) / a(lambda, cos theta_i) evaluated as
 // exp(lambda (c - 1)) / (a e^-lambda) so that nothing overflows; a is the smooth
 // step s(t, cos theta_i) between the hemispherical integrals with the axis on the
-// normal (U) and opposite it (L).  With dlog != nullptr also returns
-// d log g / d lambda.
-__device__ __forceinline__ float lobe(float lam, float c, float ci, float* dlog) {
+// normal (U) and opposite it (L).  The parts that depend on lambda alone (t(lambda),
+// e^t - 1, U e^-lambda, L e^-lambda and their derivatives) are formed once per
+// material (LobeK); a path then needs three exponentials per lobe.
+struct LobeK {
+    float lam, t, e2, Uh, Lh, dt, dUh, dLh;
+};
+
+__device__ __forceinline__ LobeK lobe_prep(float lam) {
+    LobeK k;
     const float q = expf(-lam);
     const float em = -expm1f(-lam);                       // 1 - e^-lambda
     const float k2 = 2.0f * DF_PI / lam;
-    const float Uh = k2 * em;                              // U e^-lambda
-    const float Lh = Uh * q;                               // L e^-lambda
     const float nn = (1.6988f * lam + 10.8438f) * lam;
     const float dn = (lam + 6.2201f) * lam + 10.2415f;
-    const float t = sqrtf(lam) * nn / dn;
-    const float e1 = expm1f(t * (1.0f + ci));
-    const float e2 = expm1f(t);
-    const float e3 = expf(t * ci);
-    const float Dd = e2 * (e3 + 1.0f);
+    k.lam = lam;
+    k.t = sqrtf(lam) * nn / dn;
+    k.e2 = expm1f(k.t);
+    k.Uh = k2 * em;                                        // U e^-lambda
+    k.Lh = k.Uh * q;                                       // L e^-lambda
+    k.dt = k.t * (0.5f / lam + (3.3976f * lam + 10.8438f) / nn - (2.0f * lam + 6.2201f) / dn);
+    k.dUh = -k.Uh / lam + k2 * q;
+    k.dLh = -k.Lh / lam + k2 * (2.0f * q * q - q);
+    return k;
+}
+
+// g = exp(lambda c) / a(lambda, ci); with dlog != nullptr also d log g / d lambda.
+__device__ __forceinline__ float lobe_eval(const LobeK& k, float c, float ci, float* dlog) {
+    const float e1 = expm1f(k.t * (1.0f + ci));
+    const float e3 = expf(k.t * ci);
+    const float Dd = k.e2 * (e3 + 1.0f);
     const float s = e1 / Dd;
-    const float ah = s * Uh + (1.0f - s) * Lh;
-    const float g = expf(lam * (c - 1.0f)) / ah;
+    const float ah = s * k.Uh + (1.0f - s) * k.Lh;
+    const float g = expf(k.lam * (c - 1.0f)) / ah;
     if (dlog) {
-        const float dUh = -Uh / lam + k2 * q;
-        const float dLh = -Lh / lam + k2 * (2.0f * q * q - q);
-        const float dt = t * (0.5f / lam + (3.3976f * lam + 10.8438f) / nn - (2.0f * lam + 6.2201f) / dn);
         const float dN = (1.0f + ci) * (e1 + 1.0f);
-        const float dD = (e2 + 1.0f) * (e3 + 1.0f) + e2 * ci * e3;
+        const float dD = (k.e2 + 1.0f) * (e3 + 1.0f) + k.e2 * ci * e3;
         const float ds = (dN - s * dD) / Dd;
-        const float dah = s * dUh + (1.0f - s) * dLh + (Uh - Lh) * ds * dt;
+        const float dah = s * k.dUh + (1.0f - s) * k.dLh + (k.Uh - k.Lh) * ds * k.dt;
         *dlog = (c - 1.0f) - dah / ah;
     }
     return g;
 }
 
 // f_s of Eq. trainable_scattering_pattern; pr = [S, K_x, w_1, w_2, w_3, lambda_2,
-// lambda_3, -]; with df != nullptr also df/dw_1, df/dw_2, df/dw_3, df/dlambda_2,
-// df/dlambda_3.
-__device__ __forceinline__ float pattern(const float* pr, float4 geo, float ci, float* df) {
+// lambda_3, -], k2 / k3 the lambda-only parts of its two lobes; with df != nullptr
+// also df/dw_1, df/dw_2, df/dw_3, df/dlambda_2, df/dlambda_3.
+__device__ __forceinline__ float pattern(const float* pr, const LobeK& k2, const LobeK& k3, float4 geo, float ci,
+                                         float* df) {
     float dl2, dl3;
-    const float g2 = lobe(pr[5], geo.y, ci, df ? &dl2 : nullptr);
-    const float g3 = lobe(pr[6], geo.z, ci, df ? &dl3 : nullptr);
+    const float g2 = lobe_eval(k2, geo.y, ci, df ? &dl2 : nullptr);
+    const float g3 = lobe_eval(k3, geo.z, ci, df ? &dl3 : nullptr);
     if (df) {
         df[0] = geo.x * (1.0f / DF_PI);
         df[1] = g2;
@@ -720,6 +769,26 @@ __device__ __forceinline__ float pattern(const float* pr, float4 geo, float ci, 
         df[4] = pr[4] * g3 * dl3;
     }
     return pr[2] * (1.0f / DF_PI) * geo.x + pr[3] * g2 + pr[4] * g3;
+}
+
+// Per-material lobe table in shared memory (materials < DF_LOBE_TAB), else per path.
+constexpr int DF_LOBE_TAB = 64;
+
+__device__ __forceinline__ void lobe_table(LobeK (*tab)[2], const float* scat, int n_mat) {
+    if (n_mat <= DF_LOBE_TAB) {
+        for (int k = threadIdx.x; k < 2 * n_mat; k += blockDim.x) tab[k >> 1][k & 1] = lobe_prep(__ldg(scat + 8 * (k >> 1) + 5 + (k & 1)));
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void lobes_of(LobeK (*tab)[2], const float* prm, int mat, int n_mat, LobeK& k2, LobeK& k3) {
+    if (n_mat <= DF_LOBE_TAB) {
+        k2 = tab[mat][0];
+        k3 = tab[mat][1];
+    } else {
+        k2 = lobe_prep(prm[5]);
+        k3 = lobe_prep(prm[6]);
+    }
 }
 
 // ------------------------------------------------------------------ fields
@@ -732,6 +801,7 @@ struct DfArgs {
     const float* eps;
     const float* sig;
     const float* scat;       // M x 8
+    int n_mat;
     float inv_eps0w;
     float amp;               // lambda / (4 pi) sqrt(g_T g_R) sqrt(4 pi / N)
 };
@@ -747,6 +817,8 @@ __device__ __forceinline__ float r_spec(float S) { return sqrtf(fmaxf(0.0f, 1.0f
 
 __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, float2* __restrict__ a, const double* __restrict__ tau_in,
                                                 double* __restrict__ tau_out) {
+    __shared__ LobeK s_lk[DF_LOBE_TAB][2];
+    lobe_table(s_lk, A.scat, A.n_mat);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.P; i += (int64_t)gridDim.x * blockDim.x) {
         const int j = A.depth[i];
         float2 E0 = make_float2(1.0f, 0.0f), E1 = make_float2(0.0f, 0.0f);
@@ -779,7 +851,9 @@ __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, float2* __restrict__ a
         float prm[8];
         for (int c = 0; c < 8; ++c) prm[c] = __ldg(pr + c);
         const float4 geo = __ldg(A.geo + i);
-        const float f = pattern(prm, geo, ci, nullptr);
+        LobeK k2, k3;
+        lobes_of(s_lk, prm, mat, A.n_mat, k2, k3);
+        const float f = pattern(prm, k2, k3, geo, ci, nullptr);
         const float4 Dl = __ldg(A.Dm + (int64_t)j * A.P + i);
         const float Kx = prm[1];
         const float pol = Dl.x * sqrtf(fmaxf(0.0f, 1.0f - Kx)) + Dl.y * sqrtf(fmaxf(0.0f, Kx));
@@ -801,6 +875,8 @@ template <int MAXM, int COLS>
 __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restrict__ ga, float* __restrict__ geps,
                                                 float* __restrict__ gsig, float* __restrict__ gscat, int n_mat) {
     __shared__ float acc[COLS > 0 ? 9 * MAXM * COLS : (MAXM > 0 ? MAXM * 9 : 1)];
+    __shared__ LobeK s_lk[DF_LOBE_TAB][2];
+    lobe_table(s_lk, A.scat, A.n_mat);
     if (COLS > 0) {
         for (int k = 0; k < 9 * MAXM; ++k) acc[k * COLS + threadIdx.x] = 0.0f;
     } else if (MAXM > 0) {
@@ -867,7 +943,9 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restri
         const float nu = sqrtf(u0.x * u0.x + u0.y * u0.y + u1.x * u1.x + u1.y * u1.y);
         const float4 geo = __ldg(A.geo + i);
         float df[5];
-        const float f = pattern(prm, geo, ci_d, df);
+        LobeK k2, k3;
+        lobes_of(s_lk, prm, md, A.n_mat, k2, k3);
+        const float f = pattern(prm, k2, k3, geo, ci_d, df);
         const float sf = sqrtf(fmaxf(f, 0.0f));
         const float4 Dl = __ldg(A.Dm + (int64_t)j * A.P + i);
         const float Kx = fminf(fmaxf(prm[1], 1e-12f), 1.0f - 1e-7f);
@@ -1053,6 +1131,7 @@ DfArgs make_df_args(const rt_paths* p, const float* eps, const float* sig, const
     A.eps = eps;
     A.sig = sig;
     A.scat = scat;
+    A.n_mat = p->scene->n_materials;
     A.inv_eps0w = (float)(1.0 / (RT_EPS0 * 2.0 * RT_PI * freq));
     A.amp = (float)(RT_C0 / freq / (4.0 * RT_PI) * std::sqrt((double)gtx * (double)grx) *
                     std::sqrt(4.0 * RT_PI / (double)p->n_rays));
@@ -1097,6 +1176,8 @@ RT_EXPORT rt_status rt_trace_diffuse(rt_ctx* ctx, const rt_scene* scene, const d
     float* z = nullptr;
     int32_t* hit_tri = nullptr;
     double* hit_pt = nullptr;
+    float4* hit_pt32 = nullptr;
+    float4* rx32 = nullptr;
     uint32_t* mask = nullptr;
     int32_t* word_off = nullptr;
     int64_t* cnt = nullptr;
@@ -1107,13 +1188,15 @@ RT_EXPORT rt_status rt_trace_diffuse(rt_ctx* ctx, const rt_scene* scene, const d
         if (e == cudaSuccess) e = cudaMallocAsync(d, b, st);
     };
     auto cleanup = [&]() {
-        void* tmp[] = {z, hit_tri, hit_pt, mask, word_off, cnt, src};
+        void* tmp[] = {z, hit_tri, hit_pt, hit_pt32, rx32, mask, word_off, cnt, src};
         for (void* q : tmp)
             if (q) cudaFreeAsync(q, st);
     };
     A((void**)&z, N * 4);
     A((void**)&hit_tri, N * D * 4);
     A((void**)&hit_pt, N * D * 3 * 8);
+    A((void**)&hit_pt32, N * D * 16);
+    A((void**)&rx32, R * 16);
     A((void**)&mask, R * W * 4);
     A((void**)&word_off, R * W * 4);
     A((void**)&cnt, R * 8);
@@ -1123,11 +1206,13 @@ RT_EXPORT rt_status rt_trace_diffuse(rt_ctx* ctx, const rt_scene* scene, const d
         cleanup();
         return rt_cuda_fail(ctx, e, "diffuse trace buffers");
     }
-    const Scn S{scene->d_nodes, scene->d_bvh_tris, scene->d_tri_n64, scene->eps};
-    k_df_rays<<<grid_of(ctx, N, DF_THREADS, 16), DF_THREADS, 0, st>>>(N, (int)D, tx_host[0], tx_host[1], tx_host[2],
-                                                                      z, S, hit_tri, hit_pt, status); RT_COUNT(ctx);
+    const Scn S{scene->d_nodes, scene->d_bvh_tris, scene->d_tri_n64, scene->d_tri_bary, scene->eps};
+    k_df_rays<<<grid_of(ctx, std::max<int64_t>(N, R), DF_THREADS, 16), DF_THREADS, 0, st>>>(
+        N, (int)D, tx_host[0], tx_host[1], tx_host[2], z, S, hit_tri, hit_pt, hit_pt32, (int)R, rx_dev, rx32,
+        status); RT_COUNT(ctx);
     k_df_nee<<<grid_of(ctx, N * D * R, DF_THREADS, 16), DF_THREADS, 0, st>>>(
-        N, (int)D, (int)R, tx_host[0], tx_host[1], tx_host[2], rx_dev, hit_tri, hit_pt, S, mask, W, status); RT_COUNT(ctx);
+        N, (int)D, (int)R, tx_host[0], tx_host[1], tx_host[2], rx_dev, rx32, hit_tri, hit_pt, hit_pt32, S, mask, W,
+        status); RT_COUNT(ctx);
     k_df_row_scan<<<(int)R, 256, 0, st>>>(W, mask, word_off, cnt); RT_COUNT(ctx);
     p = new rt_paths();
     p->scene = scene;
