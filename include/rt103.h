@@ -153,6 +153,11 @@ rt_status rt_paths_export(const rt_paths* paths, int32_t* tri_seq_dev, int32_t* 
 /* Copies the candidate list, n_candidates x max_depth int32 (-1 padded), in
  * (length, lexicographic) order; candidate 0 is the empty sequence. */
 rt_status rt_paths_candidates(const rt_paths* paths, int32_t* seq_dev);
+/* Read-only device views of the paths' own arrays, without a copy: rx_offsets
+ * (n_rx + 1 int64) and tau (n_paths double [s]).  They stay valid until
+ * rt_paths_free; the caller must not write through them.  Either output may
+ * be NULL. */
+rt_status rt_paths_device_views(const rt_paths* paths, const int64_t** rx_offsets_dev, const double** tau_dev);
 rt_status rt_paths_free(rt_paths* paths);
 
 /* Batched tracing of n_scenes scenes (Sec. II-F, as rt_trace_paths for each

@@ -38,6 +38,7 @@ SIGNATURES = {
     "rt_paths_rx_offsets": (I32, [P, P]),
     "rt_paths_export": (I32, [P, P, P, P, P, P]),
     "rt_paths_candidates": (I32, [P, P]),
+    "rt_paths_device_views": (I32, [P, PP, PP]),
     "rt_paths_free": (I32, [P]),
     "rt_trace_batch": (I32, [P, P, I32, P, P, P, I64, I32, PP]),
     "rt_paths_batch_info": (I32, [P, ctypes.POINTER(I32), P, P]),

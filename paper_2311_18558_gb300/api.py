@@ -121,22 +121,55 @@ class Scene:
             pass
 
 
+class _PathsHandle:
+    """Owns one library paths object; frees it when the last reference (the Paths
+    object or a device view of its arrays) goes, or on close()."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.rt_paths_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        # at interpreter exit the process releases everything; calling into CUDA
+        # while Python and the runtime tear down is not safe
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceView:
+    """A library-owned device array exposed through __cuda_array_interface__ (no
+    copy); it keeps the owning paths handle alive.  Read it only."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, owner: _PathsHandle):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3}
+        self._owner = owner
+
+
 class Paths:
-    """Traced (or imported) paths with their frozen geometry records."""
+    """Traced (or imported) paths with their frozen geometry records.  ``rx_offsets``
+    and ``tau`` are read-only views of the library's arrays (valid while the object
+    is open)."""
 
     def __init__(self, ctx: Context, scene: Scene, h, n_rx: int, max_depth: int):
         self.ctx, self.scene, self.h = ctx, scene, h
+        self._handle = _PathsHandle(ctx, h)
         self.n_rx, self.max_depth = int(n_rx), int(max_depth)
         p, k = _c.c_int64(), _c.c_int64()
         ctx.lib.rt_paths_count(h, _c.byref(p), _c.byref(k))
         self.n_paths, self.n_candidates = int(p.value), int(k.value)
+        off, tau = _c.c_void_p(), _c.c_void_p()
+        ctx.check(ctx.lib.rt_paths_device_views(h, _c.byref(off), _c.byref(tau)), "rt_paths_device_views")
         dev = torch.device("cuda", ctx.device)
-        self.rx_offsets = torch.empty(self.n_rx + 1, dtype=torch.int64, device=dev)
-        ctx._stream()
-        ctx.check(ctx.lib.rt_paths_rx_offsets(h, _ptr(self.rx_offsets)), "rt_paths_rx_offsets")
-        self.tau = torch.empty(max(self.n_paths, 1), dtype=torch.float64, device=dev)[: self.n_paths]
-        if self.n_paths:
-            ctx.check(ctx.lib.rt_paths_export(h, None, None, None, _ptr(self.tau), None), "rt_paths_export")
+        self.rx_offsets = torch.as_tensor(_DeviceView(off.value, self.n_rx + 1, "<i8", self._handle), device=dev)
+        self.tau = torch.as_tensor(_DeviceView(tau.value, self.n_paths, "<f8", self._handle), device=dev)
 
     def export(self):
         """Triangle sequences, depths, receivers, delays and points as device tensors."""
@@ -162,19 +195,10 @@ class Paths:
         return out[: self.n_candidates]
 
     def close(self):
-        if getattr(self, "h", None):
-            self.ctx.lib.rt_paths_free(self.h)
-            self.h = None
-
-    def __del__(self):
-        # at interpreter exit the process releases everything; calling into CUDA
-        # while Python and the runtime tear down is not safe
-        if sys.is_finalizing():
-            return
-        try:
-            self.close()
-        except Exception:
-            pass
+        """Frees the library's paths now (the rx_offsets and tau views die with them)."""
+        if getattr(self, "_handle", None) is not None:
+            self._handle.close()
+        self.h = None
 
 
 def trace_paths(ctx: Context, scene: Scene, tx, rx: torch.Tensor, n_rays: int, max_depth: int) -> Paths:

@@ -643,6 +643,15 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_paths_export(cons
     return RT_OK;
 }
 
+extern "C" __attribute__((visibility("default"))) rt_status rt_paths_device_views(const rt_paths* p,
+                                                                                  const int64_t** rx_offsets,
+                                                                                  const double** tau) {
+    if (!p) return RT_ERR_INVALID_ARG;
+    if (rx_offsets) *rx_offsets = p->d_rx_offsets;
+    if (tau) *tau = p->d_tau;
+    return RT_OK;
+}
+
 extern "C" __attribute__((visibility("default"))) rt_status rt_paths_candidates(const rt_paths* p, int32_t* seq) {
     if (!p || !seq) return RT_ERR_INVALID_ARG;
     rt_ctx* ctx = p->scene->ctx;

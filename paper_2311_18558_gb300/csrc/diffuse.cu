@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "fresnel.cuh"
+#include "vec3f.cuh"
 #include "launch_dir.cuh"
 #include "rt_internal.cuh"
 
@@ -582,38 +583,6 @@ struct D3 {
 __device__ __forceinline__ D3 d3(double x, double y, double z) { return D3{x, y, z}; }
 __device__ __forceinline__ D3 sub(D3 a, D3 b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ double dotd(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-
-// FP32 counterparts for the bases of the records.
-struct F3 {
-    float x, y, z;
-};
-__device__ __forceinline__ F3 f3(float x, float y, float z) { return F3{x, y, z}; }
-__device__ __forceinline__ F3 fsub(F3 a, F3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ F3 fscl(float s, F3 a) { return f3(s * a.x, s * a.y, s * a.z); }
-__device__ __forceinline__ float fdot(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ F3 fcross(F3 a, F3 b) {
-    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ F3 funit(F3 a) { return fscl(1.0f / sqrtf(fdot(a, a)), a); }
-
-__device__ __forceinline__ void sph_basis_f(F3 k, F3* th, F3* ph) {
-    const float st = sqrtf(k.x * k.x + k.y * k.y);
-    float cp = 1.0f, sp = 0.0f;
-    if (st > 0.0f) {
-        cp = k.x / st;
-        sp = k.y / st;
-    }
-    *th = f3(k.z * cp, k.z * sp, -st);
-    *ph = f3(-sp, cp, 0.0f);
-}
-
-// unit(k x n), or where k is (numerically) along n, `fb` made orthogonal to k
-// (at such incidences every transverse basis gives the same field magnitude).
-__device__ __forceinline__ F3 perp_or_f(F3 k, F3 n, F3 fb) {
-    const F3 c = fcross(k, n);
-    if (fdot(c, c) > 1e-12f) return funit(c);
-    return funit(fsub(fb, fscl(fdot(fb, k), k)));
-}
 
 struct RecOut {
     int32_t* depth;

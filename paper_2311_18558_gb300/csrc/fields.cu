@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "fresnel.cuh"
+#include "vec3f.cuh"
 #include "rt_internal.cuh"
 
 namespace {
@@ -27,26 +28,7 @@ struct D3 {
 };
 __device__ __forceinline__ D3 d3(double x, double y, double z) { return D3{x, y, z}; }
 __device__ __forceinline__ D3 sub(D3 a, D3 b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ D3 scl(double s, D3 a) { return d3(s * a.x, s * a.y, s * a.z); }
 __device__ __forceinline__ double dotd(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ D3 crossd(D3 a, D3 b) {
-    return d3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ D3 unitd(D3 a) { return scl(1.0 / sqrt(dotd(a, a)), a); }
-
-// theta_hat, phi_hat of direction k (unit), written without trigonometry:
-// cos(theta) = k_z, sin(theta) = |k_xy|, (cos phi, sin phi) = k_xy / |k_xy|,
-// phi = 0 for a vertical direction.
-__device__ __forceinline__ void sph_basis(D3 k, D3* th, D3* ph) {
-    double st = sqrt(k.x * k.x + k.y * k.y);
-    double cp = 1.0, sp = 0.0;
-    if (st > 0.0) {
-        cp = k.x / st;
-        sp = k.y / st;
-    }
-    *th = d3(k.z * cp, k.z * sp, -st);
-    *ph = d3(-sp, cp, 0.0);
-}
 
 __global__ void k_records(int64_t P, int D, const double* __restrict__ pts, const int32_t* __restrict__ depth,
                           const int32_t* __restrict__ tri, const double* __restrict__ tri_n64,
@@ -56,49 +38,45 @@ __global__ void k_records(int64_t P, int D, const double* __restrict__ pts, cons
         const int q = depth[i];
         const double* pp = pts + (int64_t)i * (D + 2) * 3;
         D3 prev = d3(pp[0], pp[1], pp[2]);
-        D3 k[RT_MAX_DEPTH + 2];
+        // lengths and delay in FP64; directions and every basis in FP32 (the records
+        // are stored in FP32)
+        F3 k[RT_MAX_DEPTH + 2];
         double L = 0.0;
         for (int j = 1; j <= q + 1; ++j) {
             D3 cur = d3(pp[3 * j], pp[3 * j + 1], pp[3 * j + 2]);
             D3 dv = sub(cur, prev);
-            double dj = sqrt(dotd(dv, dv));
-            k[j] = scl(1.0 / dj, dv);
+            const double dj = sqrt(dotd(dv, dv));
+            const float inv = 1.0f / (float)dj;
+            k[j] = f3((float)dv.x * inv, (float)dv.y * inv, (float)dv.z * inv);
             L += dj;
             prev = cur;
         }
         tau[i] = L / RT_C0;
         len[i] = (float)L;
-        D3 out_p, out_q;
-        sph_basis(k[1], &out_p, &out_q);
+        F3 out_p, out_q;
+        sph_basis_f(k[1], &out_p, &out_q);
         for (int j = 1; j <= q; ++j) {
             int t = tri[(int64_t)(j - 1) * P + i];
-            D3 n = d3(tri_n64[4 * t], tri_n64[4 * t + 1], tri_n64[4 * t + 2]);
-            if (dotd(k[j], n) > 0.0) n = scl(-1.0, n);
-            double cos_i = -dotd(k[j], n);
-            D3 cr = crossd(k[j], n);
-            D3 e_perp;
-            if (sqrt(dotd(cr, cr)) > 1e-12) {
-                e_perp = unitd(cr);
-            } else {
-                // normal incidence: any transverse unit vector serves; continue the
-                // previous outgoing p-vector
-                e_perp = unitd(sub(out_p, scl(dotd(out_p, k[j]), k[j])));
-            }
-            D3 in_q = crossd(e_perp, k[j]);
-            Dm[(int64_t)(j - 1) * P + i] = make_float4((float)dotd(e_perp, out_p), (float)dotd(e_perp, out_q),
-                                                       (float)dotd(in_q, out_p), (float)dotd(in_q, out_q));
+            F3 n = f3((float)tri_n64[4 * t], (float)tri_n64[4 * t + 1], (float)tri_n64[4 * t + 2]);
+            if (fdot(k[j], n) > 0.0f) n = fscl(-1.0f, n);
+            const float cos_i = -fdot(k[j], n);
+            // at (numerically) normal incidence any transverse unit vector serves; the
+            // previous outgoing p-vector is continued
+            const F3 e_perp = perp_or_f(k[j], n, out_p);
+            const F3 in_q = fcross(e_perp, k[j]);
+            Dm[(int64_t)(j - 1) * P + i] =
+                make_float4(fdot(e_perp, out_p), fdot(e_perp, out_q), fdot(in_q, out_p), fdot(in_q, out_q));
             const int mt = tri_material[t];
-            mc[(int64_t)(j - 1) * P + i] = make_int2(mt | (is_pec[mt] ? MAT_PEC : 0), __float_as_int((float)cos_i));
+            mc[(int64_t)(j - 1) * P + i] = make_int2(mt | (is_pec[mt] ? MAT_PEC : 0), __float_as_int(cos_i));
             out_p = e_perp;
-            out_q = crossd(e_perp, k[j + 1]);
+            out_q = fcross(e_perp, k[j + 1]);
         }
-        D3 rp, rq;
-        sph_basis(scl(-1.0, k[q + 1]), &rp, &rq);
-        Dm[(int64_t)q * P + i] = make_float4((float)dotd(rp, out_p), (float)dotd(rp, out_q), (float)dotd(rq, out_p),
-                                             (float)dotd(rq, out_q));
+        F3 rp, rq;
+        sph_basis_f(fscl(-1.0f, k[q + 1]), &rp, &rq);
+        Dm[(int64_t)q * P + i] = make_float4(fdot(rp, out_p), fdot(rp, out_q), fdot(rq, out_p), fdot(rq, out_q));
         // departure and arrival directions, for direction-dependent antenna gains
-        dir[i] = make_float4((float)k[1].x, (float)k[1].y, (float)k[1].z, 0.0f);
-        dir[P + i] = make_float4((float)-k[q + 1].x, (float)-k[q + 1].y, (float)-k[q + 1].z, 0.0f);
+        dir[i] = make_float4(k[1].x, k[1].y, k[1].z, 0.0f);
+        dir[P + i] = make_float4(-k[q + 1].x, -k[q + 1].y, -k[q + 1].z, 0.0f);
     }
 }
 
