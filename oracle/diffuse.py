@@ -24,10 +24,11 @@ Model of one diffuse path Tx -> s_1 .. s_{j-1} (specular) -> s_j (diffuse) -> Rx
   solid angle 4 pi / N, so the surface element it samples at s_j is
   dA = 4 pi l_j^2 / (N cos theta_i) and cos(theta_i) dA = 4 pi l_j^2 / N.  Hence
   |E_s| = sqrt(4 pi / N) S sqrt(f_s) |diag(r_perp, r_par) v|.
-  Reading of the polarisation vector (chi_1 = chi_2 = 0, as the paper's synthetic
-  data): [sqrt(1 - K_x), sqrt(K_x)] is expressed in the basis of the scattered
-  direction k_s and the normal: e_perp,s = k_s x n / |k_s x n|,
-  e_par,s = e_perp,s x k_s.
+  Reading of the polarisation vector: [sqrt(1 - K_x) e^{j chi_1}, sqrt(K_x) e^{j chi_2}]
+  is expressed in the basis of the scattered direction k_s and the normal:
+  e_perp,s = k_s x n / |k_s x n|, e_par,s = e_perp,s x k_s.  The random phases
+  chi are inputs (per path); without them chi_1 = chi_2 = 0, as the paper's
+  synthetic data.
 * Propagation to Rx: 1 / d_{j+1}, basis change D_{j+1} into the theta/phi basis
   of the arrival direction -k_s, projection on C_R = [sqrt(g_R), 0], times
   lambda / (4 pi).  The propagation phase is left to the CFR through
@@ -144,11 +145,12 @@ def _tri_normals(scene):
 
 # ----------------------------------------------------------------------------- fields
 
-def fields(scene, paths, eps_r, sigma, scat, freq, n_rays, gain_tx=1.0, gain_rx=1.0):
+def fields(scene, paths, eps_r, sigma, scat, freq, n_rays, gain_tx=1.0, gain_rx=1.0, chi=None):
     """Coefficients a_i (complex128 tensor) of the diffuse paths from
     OracleScene.diffuse_paths.  eps_r, sigma: per material; scat: per material
-    [S, K_x, w_1, w_2, w_3, lambda_2, lambda_3] (M x 7 or more columns).  Any of
-    them may be tensors with requires_grad."""
+    [S, K_x, w_1, w_2, w_3, lambda_2, lambda_3] (M x 7 or more columns); chi:
+    optional per-path phases (P x 2, radians) of Eq. scattered_field.  Any of them
+    may be tensors with requires_grad."""
     eps_r, sigma, scat = _t(eps_r), _t(sigma), _t(scat)
     lam_w = C0 / freq
     omega = 2.0 * math.pi * freq
@@ -199,12 +201,15 @@ def fields(scene, paths, eps_r, sigma, scat, freq, n_rays, gain_tx=1.0, gain_rx=
             nu = torch.sqrt((u.real ** 2 + u.imag ** 2).sum(-1))
             amp = math.sqrt(4.0 * math.pi / n_rays) * S * torch.sqrt(f) * nu / seg[:, j]
             Kx = scat[m, 1].to(DT)
-            pol = torch.stack([torch.sqrt(1.0 - Kx), torch.sqrt(Kx)], -1)
+            pol = torch.stack([torch.sqrt(1.0 - Kx), torch.sqrt(Kx)], -1).to(torch.complex128)
+            if chi is not None:
+                ch = torch.as_tensor(np.asarray(chi, np.float64)[idx])
+                pol = pol * torch.exp(1j * ch)
             sp = _perp(ks, n, e_perp)
             sq = torch.cross(sp, ks, dim=-1)
             th, ph = _sph_basis(-ks)
             Dl = _basis_change(th, ph, sp, sq)
-            er = Dl[:, 0, 0] * pol[:, 0] + Dl[:, 0, 1] * pol[:, 1]
+            er = Dl[:, 0, 0].to(torch.complex128) * pol[:, 0] + Dl[:, 0, 1].to(torch.complex128) * pol[:, 1]
             a_j = lam_w / (4.0 * math.pi) * math.sqrt(gain_rx) * amp * er
             a = a.index_put((torch.as_tensor(idx),), a_j.to(torch.complex128))
     return a

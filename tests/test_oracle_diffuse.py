@@ -242,3 +242,18 @@ def test_specular_reduction():
     scat[0, 0] = 0.6
     out = od.specular_reduction(sc, tr, scat, a).numpy()
     np.testing.assert_allclose(np.abs(out) ** 2, np.abs(a) ** 2 * 0.64 ** tr["depth"], rtol=1e-13)
+
+
+def test_random_phases_rotate_each_polarisation():
+    # K_x = 0 keeps only the first polarisation component: the phases turn a by
+    # exp(j chi_1) and leave |a|; K_x = 1 keeps only the second: exp(j chi_2)
+    sc = scenegen.tiny_box()
+    o = oracle.OracleScene(sc)
+    d = o.diffuse_paths(200, 2)
+    rng = np.random.default_rng(9)
+    chi = rng.uniform(0, 2 * np.pi, (len(d["rx"]), 2))
+    for kx, col in ((0.0, 0), (1.0, 1)):
+        scat = np.array([[0.5, kx, 0.4, 0.3, 0.3, 3.0, 6.0]])
+        a0 = od.fields(sc, d, sc.eps_r, sc.sigma, scat, sc.freq_hz, 200).numpy()
+        a1 = od.fields(sc, d, sc.eps_r, sc.sigma, scat, sc.freq_hz, 200, chi=chi).numpy()
+        np.testing.assert_allclose(a1, a0 * np.exp(1j * chi[:, col]), rtol=1e-12, atol=1e-25)
