@@ -308,16 +308,18 @@ rt_status rt_antenna_apply_backward(rt_ctx* ctx, const rt_paths* paths, const fl
 rt_status rt_trace_diffuse(rt_ctx* ctx, const rt_scene* scene, const double* tx_host, const double* rx_dev,
                            int32_t n_rx, int64_t n_rays, int32_t max_depth, rt_paths** out);
 
-/* Coefficients of diffuse paths (Eq. scattered_field with chi_1 = chi_2 = 0):
+/* Coefficients of diffuse paths (Eq. scattered_field; chi_1 = chi_2 = 0 unless
+ * phases were attached with rt_set_diffuse_phases):
  * the specular prefix as rt_eval_fields with R = sqrt(1 - S^2) per bounce
  * (Eq. specular_reflection), then at s_j
  *   |E_s| = sqrt(4 pi / n_rays) S sqrt(f_s) |diag(r_perp, r_par) v|
  * (v the incident field in the incidence basis without the spreading 1/l_j,
  * which cancels against cos(theta_i) dA = 4 pi l_j^2 / n_rays: each launch ray
- * samples the solid angle 4 pi / n_rays), the polarisation [sqrt(1 - K_x),
- * sqrt(K_x)] in the basis e_perp = k_s x n / |k_s x n|, e_par = e_perp x k_s, and
+ * samples the solid angle 4 pi / n_rays), the polarisation [sqrt(1 - K_x) e^{j chi_1},
+ * sqrt(K_x) e^{j chi_2}] in the basis e_perp = k_s x n / |k_s x n|,
+ * e_par = e_perp x k_s, and
  *   a = lambda / (4 pi) sqrt(g_T g_R) |E_s| / d_last (D_last row 0 . pol),
- * which is real.  f_s is the trainable scattering pattern of Sec. III-C:
+ * which is real when chi = 0.  f_s is the trainable scattering pattern of Sec. III-C:
  *   f_s = w_1 / pi (k_s . n) + w_2 g(lambda_2, -k_i . k_s) + w_3 g(lambda_3, k_r . k_s),
  *   g(lambda, c) = exp(lambda c) / a(lambda, cos theta_i), a = s U + (1 - s) L
  * with U = 2 pi / lambda (e^lambda - 1), L = 2 pi / lambda (1 - e^-lambda) and the
@@ -336,6 +338,13 @@ rt_status rt_eval_fields_diffuse_backward(rt_ctx* ctx, const rt_paths* paths, co
                                           const float* sigma_dev, const float* scat_dev, double freq_hz,
                                           float gain_tx, float gain_rx, const void* grad_a_dev,
                                           float* grad_eps_r_dev, float* grad_sigma_dev, float* grad_scat_dev);
+
+/* Attaches the random phases chi_1, chi_2 of Eq. scattered_field to a diffuse
+ * paths object: chi_dev holds n_paths x 2 float32 (radians, in path order) and
+ * stays owned by the caller, who keeps it alive and unchanged while the paths
+ * are evaluated; NULL restores chi = 0.  rt_eval_fields_diffuse and its adjoint
+ * read it. */
+rt_status rt_set_diffuse_phases(rt_ctx* ctx, rt_paths* paths, const float* chi_dev);
 
 /* Specular share of the reflected energy (Sec. II-D, Eq. specular_reflection):
  * a_out[i] = a[i] prod_b sqrt(1 - S_b^2) over the bounces of specular path i,

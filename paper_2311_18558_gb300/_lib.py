@@ -47,6 +47,7 @@ SIGNATURES = {
     "rt_trace_diffuse": (I32, [P, P, P, P, I32, I64, I32, PP]),
     "rt_eval_fields_diffuse": (I32, [P, P, P, P, P, F64, F32, F32, P, P]),
     "rt_eval_fields_diffuse_backward": (I32, [P, P, P, P, P, F64, F32, F32, P, P, P, P]),
+    "rt_set_diffuse_phases": (I32, [P, P, P]),
     "rt_specular_reduction": (I32, [P, P, P, P, P]),
     "rt_specular_reduction_backward": (I32, [P, P, P, P, P, P, P]),
     "rt_rx_merge": (I32, [P, I32, P, P, P, P, P, P]),

@@ -362,6 +362,18 @@ def eval_fields_diffuse_backward(ctx: Context, paths: Paths, eps_r, sigma, scat,
     return grad_eps, grad_sigma, grad_scat
 
 
+def set_diffuse_phases(ctx: Context, paths: Paths, chi=None):
+    """Attaches per-path random phases (n_paths x 2 float32, radians) of Eq.
+    scattered_field to diffuse paths, or clears them (rt_set_diffuse_phases).  The
+    tensor is kept referenced by the paths object."""
+    if chi is not None:
+        chi = chi.to(device=torch.device("cuda", ctx.device), dtype=torch.float32).contiguous()
+        if chi.shape != (paths.n_paths, 2):
+            raise ValueError("chi must have shape (n_paths, 2)")
+    ctx.check(ctx.lib.rt_set_diffuse_phases(ctx.h, paths.h, _ptr(chi)), "rt_set_diffuse_phases")
+    paths.chi = chi
+
+
 def specular_reduction(ctx: Context, paths: Paths, scat, a, out=None):
     """a prod_b sqrt(1 - S_b^2) over the bounces of each specular path (rt_specular_reduction)."""
     out = out if out is not None else torch.empty_like(a)

@@ -770,6 +770,7 @@ struct DfArgs {
     const float* eps;
     const float* sig;
     const float* scat;       // M x 8
+    const float2* chi;       // per-path random phases (chi_1, chi_2), or null
     int n_mat;
     float inv_eps0w;
     float amp;               // lambda / (4 pi) sqrt(g_T g_R) sqrt(4 pi / N)
@@ -783,6 +784,17 @@ __device__ __forceinline__ void mat_params(const DfArgs& A, int2 m, float2& eta,
 }
 
 __device__ __forceinline__ float r_spec(float S) { return sqrtf(fmaxf(0.0f, 1.0f - S * S)); }
+
+// Receiver projection of the scattered polarisation [c1 e^{j chi_1}, c2 e^{j chi_2}]
+// through row 0 of D_last (chi = 0 without per-path phases).
+__device__ __forceinline__ float2 pol_of(float4 Dl, float c1, float c2, const float2* __restrict__ chi, int64_t i) {
+    if (!chi) return make_float2(Dl.x * c1 + Dl.y * c2, 0.0f);
+    const float2 ch = __ldg(chi + i);
+    float s1, k1, s2, k2;
+    sincosf(ch.x, &s1, &k1);
+    sincosf(ch.y, &s2, &k2);
+    return make_float2(Dl.x * c1 * k1 + Dl.y * c2 * k2, Dl.x * c1 * s1 + Dl.y * c2 * s2);
+}
 
 __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, float2* __restrict__ a, const double* __restrict__ tau_in,
                                                 double* __restrict__ tau_out) {
@@ -825,8 +837,9 @@ __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, float2* __restrict__ a
         const float f = pattern(prm, k2, k3, geo, ci, nullptr);
         const float4 Dl = __ldg(A.Dm + (int64_t)j * A.P + i);
         const float Kx = prm[1];
-        const float pol = Dl.x * sqrtf(fmaxf(0.0f, 1.0f - Kx)) + Dl.y * sqrtf(fmaxf(0.0f, Kx));
-        a[i] = make_float2(A.amp * prm[0] * sqrtf(fmaxf(f, 0.0f)) * nu * pol * geo.w, 0.0f);
+        const float2 pol = pol_of(Dl, sqrtf(fmaxf(0.0f, 1.0f - Kx)), sqrtf(fmaxf(0.0f, Kx)), A.chi, i);
+        const float K = A.amp * prm[0] * sqrtf(fmaxf(f, 0.0f)) * nu * geo.w;
+        a[i] = make_float2(K * pol.x, K * pol.y);
         if (tau_out) tau_out[i] = tau_in[i];
     }
 }
@@ -867,8 +880,8 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restri
         }
     };
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.P; i += (int64_t)gridDim.x * blockDim.x) {
-        const float g = ga[i].x;
-        if (g == 0.0f) continue;
+        const float2 gc = ga[i];
+        if (gc.x == 0.0f && gc.y == 0.0f) continue;
         const int j = A.depth[i];
         float2 v0s[RT_MAX_DEPTH], v1s[RT_MAX_DEPTH], rps[RT_MAX_DEPTH], rls[RT_MAX_DEPTH];
         float4 Ds[RT_MAX_DEPTH];
@@ -919,19 +932,24 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restri
         const float4 Dl = __ldg(A.Dm + (int64_t)j * A.P + i);
         const float Kx = fminf(fmaxf(prm[1], 1e-12f), 1.0f - 1e-7f);
         const float sq1 = sqrtf(1.0f - Kx), sq2 = sqrtf(Kx);
-        const float pol = Dl.x * sq1 + Dl.y * sq2;
+        // a = K pol with K real: dL/dtheta = dK/dtheta Re(conj(g) pol) for every
+        // parameter but K_x, whose derivative goes through pol
+        const float2 pol = pol_of(Dl, sq1, sq2, A.chi, i);
+        const float2 dpol = pol_of(Dl, -0.5f / sq1, 0.5f / sq2, A.chi, i);
+        const float gpol = gc.x * pol.x + gc.y * pol.y;
+        const float gdpol = gc.x * dpol.x + gc.y * dpol.y;
         const float C = A.amp * geo.w;
         const float S = prm[0];
         // diffuse material: S, K_x, pattern
-        add(md, 2, g * C * sf * nu * pol);
-        add(md, 3, g * C * S * sf * nu * (-0.5f * Dl.x / sq1 + 0.5f * Dl.y / sq2));
+        add(md, 2, gpol * C * sf * nu);
+        add(md, 3, gdpol * C * S * sf * nu);
         if (f > 0.0f) {
-            const float dAdf = g * C * S * nu * pol * 0.5f / sf;
+            const float dAdf = gpol * C * S * nu * 0.5f / sf;
             for (int c = 0; c < 5; ++c) add(md, 4 + c, dAdf * df[c]);
         }
         if (!(nu > 0.0f)) continue;
         // reverse walk for d nu / d eta_b and d nu / d R_b
-        const float dAnu = g * C * S * sf * pol / nu;
+        const float dAnu = gpol * C * S * sf / nu;
         float2 l0 = make_float2(u0.x * dAnu, -u0.y * dAnu), l1 = make_float2(u1.x * dAnu, -u1.y * dAnu);
 #pragma unroll
         for (int b = RT_MAX_DEPTH - 1; b >= 0; --b) {
@@ -1100,6 +1118,7 @@ DfArgs make_df_args(const rt_paths* p, const float* eps, const float* sig, const
     A.eps = eps;
     A.sig = sig;
     A.scat = scat;
+    A.chi = p->d_chi;
     A.n_mat = p->scene->n_materials;
     A.inv_eps0w = (float)(1.0 / (RT_EPS0 * 2.0 * RT_PI * freq));
     A.amp = (float)(RT_C0 / freq / (4.0 * RT_PI) * std::sqrt((double)gtx * (double)grx) *
@@ -1131,7 +1150,7 @@ RT_EXPORT rt_status rt_trace_diffuse(rt_ctx* ctx, const rt_scene* scene, const d
         n_rx > (1 << 24))
         return rt_fail(ctx, RT_ERR_INVALID_ARG, "bad sizes");
     for (int c = 0; c < 3; ++c)
-        if (!std::isfinite(tx_host[c])) return rt_fail(ctx, RT_ERR_INVALID_ARG, "transmitter not finite");
+        if (!std::isfinite(tx_host[c])) return rt_fail(ctx, RT_ERR_NUMERIC, "transmitter not finite");
     const int64_t N = n_rays, D = max_depth, R = n_rx;
     const int64_t W = (N * D + 31) / 32;
     if (R * W > (int64_t)1 << 31)
@@ -1268,6 +1287,14 @@ RT_EXPORT rt_status rt_eval_fields_diffuse_backward(rt_ctx* ctx, const rt_paths*
                                                                                 grad_sigma_dev, grad_scat_dev, n_mat);
     RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}
+
+RT_EXPORT rt_status rt_set_diffuse_phases(rt_ctx* ctx, rt_paths* paths, const float* chi_dev) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (!paths) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null paths");
+    if (paths->kind != 1) return rt_fail(ctx, RT_ERR_INVALID_ARG, "not a diffuse paths object (rt_trace_diffuse)");
+    paths->d_chi = reinterpret_cast<const float2*>(chi_dev);
     return RT_OK;
 }
 

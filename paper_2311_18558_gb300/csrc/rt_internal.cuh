@@ -106,6 +106,7 @@ struct rt_paths {
     int64_t* h_scene_tri_off = nullptr;// batch output: triangle-id offset of each scene (n_scenes + 1)
     int32_t kind = 0;                  // 0: specular chains; 1: diffuse paths (last bounce diffuse)
     int64_t n_rays = 0;                // diffuse paths: launch rays that sampled the surfaces
+    const float2* d_chi = nullptr;     // diffuse paths: caller-owned per-path phases (chi_1, chi_2), or none
     float4* d_scat = nullptr;          // diffuse paths, P: (k_s.n, -k_i.k_s, k_r.k_s, 1/d_last) at the
                                        // diffuse point (n facing the incident wave)
 };

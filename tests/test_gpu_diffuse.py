@@ -229,3 +229,73 @@ def test_scattering_calibration(rt, ctx):
         losses.append(L.item())
     assert losses[-1] < 0.1 * losses[0], losses[::15]
     assert ctx.status_word() == 0
+
+
+def test_diffuse_rejects_bad_arguments(rt, ctx):
+    # host-side validation: nothing is launched, the status word stays clear
+    sc = scenegen.tiny_box()
+    scene = rt.Scene.from_synthetic(ctx, sc)
+    rxt = torch.tensor(sc.rx, dtype=torch.float64, device="cuda")
+    with pytest.raises(rt.RtError, match="INVALID_ARG"):
+        rt.trace_diffuse(ctx, scene, sc.tx, rxt, 1000, 5)
+    with pytest.raises(rt.RtError, match="INVALID_ARG"):
+        rt.trace_diffuse(ctx, scene, sc.tx, rxt, 0, 2)
+    with pytest.raises(rt.RtError, match="NUMERIC"):
+        rt.trace_diffuse(ctx, scene, (float("nan"), 0.0, 0.0), rxt, 10, 2)
+    pd = rt.trace_diffuse(ctx, scene, sc.tx, rxt, 100, 2)
+    ps = rt.trace_paths(ctx, scene, sc.tx, rxt, 1000, 2)
+    eps = torch.tensor(sc.eps_r, device="cuda")
+    sig = torch.tensor(sc.sigma, device="cuda")
+    scat = torch.tensor(_scat(1, sc.n_materials), device="cuda")
+    a = torch.zeros(ps.n_paths, dtype=torch.complex64, device="cuda")
+    with pytest.raises(rt.RtError, match="INVALID_ARG"):
+        rt.eval_fields(ctx, pd, eps, sig, sc.freq_hz)            # diffuse paths in the specular kernel
+    with pytest.raises(rt.RtError, match="INVALID_ARG"):
+        rt.eval_fields_diffuse(ctx, ps, eps, sig, scat, sc.freq_hz)   # and the reverse
+    with pytest.raises(rt.RtError, match="INVALID_ARG"):
+        rt.specular_reduction(ctx, pd, scat, torch.zeros(pd.n_paths, dtype=torch.complex64, device="cuda"))
+    with pytest.raises(rt.RtError, match="INVALID_ARG"):
+        rt.eval_fields_diffuse(ctx, pd, eps, sig, scat, -1.0)
+    with pytest.raises(rt.RtError, match="INVALID_ARG"):
+        rt.eval_fields_diffuse(ctx, pd, eps, sig, scat, sc.freq_hz, gain_tx=0.0)
+    with pytest.raises(ValueError):
+        rt.rx_merge(ctx, ps.rx_offsets, pd.rx_offsets, a, torch.zeros(pd.n_paths, device="cuda"))
+    assert ctx.status_word() == 0
+
+
+def test_random_phases(rt, ctx, indoor):
+    # per-path random phases of Eq. scattered_field (inputs): coefficients and the
+    # adjoint against the oracle with the same phases, then cleared again
+    sc, scene, p, tr = indoor
+    scat = _scat(13, sc.n_materials)
+    rng = np.random.default_rng(17)
+    chi = rng.uniform(0, 2 * np.pi, (p.n_paths, 2)).astype(np.float32)
+    rt.set_diffuse_phases(ctx, p, torch.tensor(chi, device="cuda"))
+    try:
+        eps_d, sig_d = torch.tensor(sc.eps_r, device="cuda"), torch.tensor(sc.sigma, device="cuda")
+        scat_d = torch.tensor(scat, device="cuda")
+        a = rt.eval_fields_diffuse(ctx, p, eps_d, sig_d, scat_d, sc.freq_hz).cpu().numpy()
+        ref = od.fields(sc, tr, sc.eps_r.astype(np.float64), sc.sigma.astype(np.float64), scat.astype(np.float64),
+                        sc.freq_hz, 3000, chi=chi.astype(np.float64)).numpy()
+        np.testing.assert_allclose(a, ref, rtol=2e-5, atol=1e-6 * np.abs(ref).max())
+        g = (rng.normal(size=p.n_paths) + 1j * rng.normal(size=p.n_paths)).astype(np.complex64)
+        ge, gs, gcat = rt.eval_fields_diffuse_backward(ctx, p, eps_d, sig_d, scat_d, sc.freq_hz,
+                                                        torch.tensor(g, device="cuda"))
+        e = torch.tensor(sc.eps_r.astype(np.float64), requires_grad=True)
+        s = torch.tensor(sc.sigma.astype(np.float64), requires_grad=True)
+        c = torch.tensor(scat[:, :7].astype(np.float64), requires_grad=True)
+        af = od.fields(sc, tr, e, s, c, sc.freq_hz, 3000, chi=chi.astype(np.float64))
+        (torch.as_tensor(g.astype(np.complex128)).conj() * af).real.sum().backward()
+        for got, ref_g in ((ge, e.grad), (gs, s.grad)):
+            got, ref_g = got.cpu().numpy(), ref_g.numpy()
+            assert np.linalg.norm(got - ref_g) <= 1e-4 * np.linalg.norm(ref_g)
+        gcat = gcat.cpu().numpy()
+        for col in range(7):
+            ref_c = c.grad[:, col].numpy()
+            assert np.linalg.norm(gcat[:, col] - ref_c) <= 1e-4 * np.linalg.norm(ref_c), col
+    finally:
+        rt.set_diffuse_phases(ctx, p, None)
+    a0 = rt.eval_fields_diffuse(ctx, p, torch.tensor(sc.eps_r, device="cuda"), torch.tensor(sc.sigma, device="cuda"),
+                                torch.tensor(scat, device="cuda"), sc.freq_hz)
+    assert torch.all(a0.imag == 0)
+    assert ctx.status_word() == 0
