@@ -72,13 +72,16 @@ rt_status rt_status_word(rt_ctx* ctx, int32_t* device_error);
 const char* rt_version(void);
 
 /* Instrumentation (no counterpart in the paper; used by the benchmark).
- * flags bit 0: time the stages of rt_trace_paths with CUDA events;
+ * flags bit 0: time the stages of rt_trace_paths with CUDA events (recorded on
+ * the stream; the trace does not wait for them, rt_profile_read does);
  * flags bit 1: count BVH node visits and triangle tests in the tracing kernels
  * (adds atomics; leave off when timing). */
 rt_status rt_set_profiling(rt_ctx* ctx, int32_t flags);
 /* Reads the instrumentation of ctx (any pointer may be NULL):
  *   launches      number of kernels this context launched so far
- *   stage_ms[8]   last trace: SBR, dedup+sort, image method, visibility,
+ *   stage_ms[8]   last trace (waits for its last stage event if not read yet;
+ *                 a trace not read before the next one starts is dropped):
+ *                 SBR, dedup+sort, image method, visibility,
  *                 emission+records, total, then within SBR the shoot-and-bounce
  *                 kernel alone and the FP64 re-trace (bit 0 set, else zeros)
  *   counters[8]   since the last rt_set_profiling: SBR node visits, SBR triangle

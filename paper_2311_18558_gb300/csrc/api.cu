@@ -178,7 +178,27 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_set_profiling(rt_
         ctx->h_counters[k] = 0;
         ctx->stage_ms[k] = 0.0;
     }
+    ctx->stage_pending = 0;
     ctx->profile = flags;
+    return RT_OK;
+}
+
+rt_status rt_collect_stage_times(rt_ctx* ctx) {
+    if (!ctx->stage_pending) return RT_OK;
+    ctx->stage_pending = 0;
+    RT_CK(ctx, cudaEventSynchronize(ctx->ev[5]));
+    float ms = 0.f;
+    // stages: SBR, dedup + sort (incl. candidate setup), image method, visibility, emission
+    for (int k = 0; k < 5; ++k) {
+        RT_CK(ctx, cudaEventElapsedTime(&ms, ctx->ev[k], ctx->ev[k + 1]));
+        ctx->stage_ms[k] = ms;
+    }
+    RT_CK(ctx, cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]));
+    ctx->stage_ms[5] = ms;
+    RT_CK(ctx, cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[7]));   // the SBR kernel alone
+    ctx->stage_ms[6] = ms;
+    RT_CK(ctx, cudaEventElapsedTime(&ms, ctx->ev[7], ctx->ev[1]));   // the FP64 re-trace
+    ctx->stage_ms[7] = ms;
     return RT_OK;
 }
 
@@ -186,8 +206,11 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_profile_read(rt_c
                                                                             double* stage_ms, int64_t* counters) {
     if (!ctx) return RT_ERR_INVALID_ARG;
     if (launches) *launches = ctx->launches;
-    if (stage_ms)
+    if (stage_ms) {
+        rt_status s = rt_collect_stage_times(ctx);
+        if (s != RT_OK) return s;
         for (int k = 0; k < 8; ++k) stage_ms[k] = ctx->stage_ms[k];
+    }
     if (counters) {
         unsigned long long d[8] = {0};
         if (ctx->d_counters) {

@@ -15,8 +15,11 @@
 //      over (eps, len - eps), t_j excluded); visible pairs set a bit of a
 //      (receiver x source) mask.
 //   3. per-receiver popcounts, scans and an ordered expansion give the paths
-//      grouped by receiver and ordered by (ray, j); k_df_records turns each
-//      into FP32 records for the field kernels.
+//      grouped by receiver and ordered by (ray, j).
+//   4. k_df_prefix forms, once per (ray, j), what all paths from s_j share (the
+//      FP64 length up to s_j, the reflection bases of bounces 1..j);
+//      k_df_records adds each path's last segment and scattered basis and writes
+//      the FP32 records for the field kernels.
 // Fields (every calibration step): the specular prefix as in the specular
 // kernels (with R per bounce), then the diffuse bounce
 //   |E_s| = sqrt(4 pi / N) S sqrt(f_s) |diag(r_perp, r_par) v|,
@@ -25,7 +28,8 @@
 // where v is the incident field at s_j in its incidence basis without the
 // spherical spreading 1 / l_j, which cancels against cos(theta_i) dA = 4 pi l_j^2 / N
 // (each ray samples the solid angle 4 pi / N).  The scattered polarisation
-// [sqrt(1 - K_x), sqrt(K_x)] (chi_1 = chi_2 = 0) is taken in the basis
+// [sqrt(1 - K_x) e^{j chi_1}, sqrt(K_x) e^{j chi_2}] (the phases per path, zero
+// unless rt_set_diffuse_phases gave them) is taken in the basis
 // e_perp = k_s x n / |k_s x n|, e_par = e_perp x k_s of the scattered direction.
 #include <cuda_runtime.h>
 
@@ -596,82 +600,155 @@ struct RecOut {
     float4* scat;      // P
 };
 
-__global__ void k_df_records(int64_t P, int64_t N, int D, double tx0, double tx1, double tx2,
-                             const double* __restrict__ rx, const int32_t* __restrict__ prx,
-                             const int64_t* __restrict__ src, const int32_t* __restrict__ hit_tri,
-                             const double* __restrict__ hit_pt, const double* __restrict__ n64,
-                             const int32_t* __restrict__ tri_material, const uint8_t* __restrict__ is_pec,
-                             RecOut O) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
-        const int s = (int)src[i];   // < n_rays max_depth < 2^31
-        const int ray = s / D;
-        const int j = s - ray * D + 1;
-        const int r = prx[i];
-        D3 pts[RT_MAX_DEPTH + 2];
+// What every diffuse path of one (ray, diffuse bounce j) shares: the path up to the
+// diffuse point is the ray's own, only the last segment goes to the receiver.
+// Index s = ray * D + j - 1 (the source index of the emission).
+struct __align__(16) DfPre {
+    double ell;    // length of the j segments up to the diffuse point (FP64)
+    double pad;
+    float4 kin;    // direction of incidence at the diffuse point
+    float4 n;      // unit normal there, facing the incident wave
+    float4 ep;     // e_perp of the last reflection basis (the fallback of the scattered basis)
+    float4 d0;     // direction of departure
+};
+
+// One thread per (ray, bounce): lengths in FP64, directions and the reflection bases
+// of bounces 1..j in FP32 (the records are stored in FP32).  Dm and mc of bounce b
+// go to pre_Dm / pre_mc[s * D + b - 1].
+__global__ void k_df_prefix(int64_t N, int D, double tx0, double tx1, double tx2,
+                            const int32_t* __restrict__ hit_tri, const double* __restrict__ hit_pt,
+                            const double* __restrict__ n64, const int32_t* __restrict__ tri_material,
+                            const uint8_t* __restrict__ is_pec, DfPre* __restrict__ pre,
+                            float4* __restrict__ pre_Dm, int2* __restrict__ pre_mc) {
+    const int64_t M = N * D;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < M; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ray = s / D;
+        const int j = (int)(s - ray * D) + 1;
+        if (hit_tri[(int64_t)(j - 1) * N + ray] < 0) continue;   // the ray escaped before bounce j
+        D3 pts[RT_MAX_DEPTH + 1];
         pts[0] = d3(tx0, tx1, tx2);
         for (int b = 1; b <= j; ++b) {
             const double* q = hit_pt + ((int64_t)(b - 1) * N + ray) * 3;
             pts[b] = d3(q[0], q[1], q[2]);
         }
-        pts[j + 1] = d3(rx[3 * (int64_t)r], rx[3 * (int64_t)r + 1], rx[3 * (int64_t)r + 2]);
-        double* po = O.pts + i * (D + 2) * 3;
-        for (int b = 0; b < D + 2; ++b) {
-            const D3 q = b <= j + 1 ? pts[b] : d3(0.0, 0.0, 0.0);
-            po[3 * b] = q.x;
-            po[3 * b + 1] = q.y;
-            po[3 * b + 2] = q.z;
-        }
-        O.depth[i] = j;
-        int tt[RT_MAX_DEPTH];
-        for (int b = 0; b < D; ++b) {
-            tt[b] = b < j ? hit_tri[(int64_t)b * N + ray] : -1;
-            O.tri[(int64_t)b * P + i] = tt[b];
-        }
-        // lengths and delay in FP64; directions and every basis in FP32 (the records
-        // are stored in FP32)
-        F3 k[RT_MAX_DEPTH + 2];
-        double ell = 0.0, dl = 0.0;
-        for (int b = 1; b <= j + 1; ++b) {
+        F3 k[RT_MAX_DEPTH + 1];
+        double ell = 0.0;
+        for (int b = 1; b <= j; ++b) {
             const D3 dv = sub(pts[b], pts[b - 1]);
             const double db = sqrt(dotd(dv, dv));
             const float inv = 1.0f / (float)db;
             k[b] = f3((float)dv.x * inv, (float)dv.y * inv, (float)dv.z * inv);
-            if (b <= j) ell += db;
-            else dl = db;
+            ell += db;
         }
-        O.tau[i] = (ell + dl) / RT_C0;
-        O.len[i] = (float)dl;
         F3 out_p, out_q;
         sph_basis_f(k[1], &out_p, &out_q);
+        F3 n = f3(0.0f, 0.0f, 0.0f), e_perp = n;
         for (int b = 1; b <= j; ++b) {
-            const int t = tt[b - 1];
-            F3 n = f3((float)n64[4 * t], (float)n64[4 * t + 1], (float)n64[4 * t + 2]);
+            const int t = hit_tri[(int64_t)(b - 1) * N + ray];
+            n = f3((float)n64[4 * t], (float)n64[4 * t + 1], (float)n64[4 * t + 2]);
             if (fdot(k[b], n) > 0.0f) n = fscl(-1.0f, n);       // facing the incident wave
             const float cos_i = -fdot(k[b], n);
-            const F3 e_perp = perp_or_f(k[b], n, out_p);
+            e_perp = perp_or_f(k[b], n, out_p);
             const F3 in_q = fcross(e_perp, k[b]);
-            O.Dm[(int64_t)(b - 1) * P + i] =
+            pre_Dm[s * D + b - 1] =
                 make_float4(fdot(e_perp, out_p), fdot(e_perp, out_q), fdot(in_q, out_p), fdot(in_q, out_q));
             const int mt = tri_material[t];
-            O.mc[(int64_t)(b - 1) * P + i] = make_int2(mt | (is_pec[mt] ? MAT_PEC : 0), __float_as_int(cos_i));
+            pre_mc[s * D + b - 1] = make_int2(mt | (is_pec[mt] ? MAT_PEC : 0), __float_as_int(cos_i));
             if (b < j) {
                 out_p = e_perp;
                 out_q = fcross(e_perp, k[b + 1]);
-                continue;
             }
+        }
+        DfPre P;
+        P.ell = ell;
+        P.pad = 0.0;
+        P.kin = make_float4(k[j].x, k[j].y, k[j].z, 0.0f);
+        P.n = make_float4(n.x, n.y, n.z, 0.0f);
+        P.ep = make_float4(e_perp.x, e_perp.y, e_perp.z, 0.0f);
+        P.d0 = make_float4(k[1].x, k[1].y, k[1].z, 0.0f);
+        pre[s] = P;
+    }
+}
+
+// One thread per diffuse path: the shared part from its (ray, bounce) prefix, the
+// last segment (diffuse point -> receiver) in FP64, the scattered basis in FP32.
+// Blocks of DF_REC_THREADS take tiles of as many consecutive paths; the FP64 points
+// of a tile (one row of (D + 2) x 3 per path) are staged in shared memory and
+// written out as one contiguous, coalesced range.
+constexpr int DF_REC_THREADS = 128;
+__global__ void __launch_bounds__(DF_REC_THREADS) k_df_records(int64_t P, int64_t N, int D, double tx0, double tx1,
+                                                               double tx2, const double* __restrict__ rx,
+                                                               const int32_t* __restrict__ prx,
+                                                               const int64_t* __restrict__ src,
+                                                               const int32_t* __restrict__ hit_tri,
+                                                               const double* __restrict__ hit_pt,
+                                                               const DfPre* __restrict__ pre,
+                                                               const float4* __restrict__ pre_Dm,
+                                                               const int2* __restrict__ pre_mc, RecOut O) {
+    constexpr double INV_C0 = 1.0 / RT_C0;
+    __shared__ __align__(16) double sp[DF_REC_THREADS * (RT_MAX_DEPTH + 2) * 3];
+    const int row = (D + 2) * 3;
+    double* po = sp + threadIdx.x * row;
+    for (int64_t i0 = (int64_t)blockIdx.x * DF_REC_THREADS; i0 < P; i0 += (int64_t)gridDim.x * DF_REC_THREADS) {
+        const int64_t i = i0 + threadIdx.x;
+        if (i < P) {
+            const int s32 = (int)src[i];   // < n_rays max_depth < 2^31
+            const int ray = s32 / D;
+            const int j = s32 - ray * D + 1;
+            const int64_t s = s32;
+            const int r = prx[i];
+            const DfPre Q = pre[s];
+            po[0] = tx0;
+            po[1] = tx1;
+            po[2] = tx2;
+            D3 last = d3(0.0, 0.0, 0.0);
+            for (int b = 1; b <= j; ++b) {
+                const double* q = hit_pt + ((int64_t)(b - 1) * N + ray) * 3;
+                last = d3(q[0], q[1], q[2]);
+                po[3 * b] = last.x;
+                po[3 * b + 1] = last.y;
+                po[3 * b + 2] = last.z;
+            }
+            const D3 pr = d3(rx[3 * (int64_t)r], rx[3 * (int64_t)r + 1], rx[3 * (int64_t)r + 2]);
+            po[3 * (j + 1)] = pr.x;
+            po[3 * (j + 1) + 1] = pr.y;
+            po[3 * (j + 1) + 2] = pr.z;
+            for (int c = 3 * (j + 2); c < row; ++c) po[c] = 0.0;
+            O.depth[i] = j;
+            for (int b = 0; b < D; ++b) O.tri[(int64_t)b * P + i] = b < j ? hit_tri[(int64_t)b * N + ray] : -1;
+            const D3 dv = sub(pr, last);
+            const double dl = sqrt(dotd(dv, dv));
+            const float inv = 1.0f / (float)dl;
+            const F3 ks = f3((float)dv.x * inv, (float)dv.y * inv, (float)dv.z * inv);
+            O.tau[i] = (Q.ell + dl) * INV_C0;
+            O.len[i] = (float)dl;
+            for (int b = 0; b < j; ++b) {
+                O.Dm[(int64_t)b * P + i] = pre_Dm[s * D + b];
+                O.mc[(int64_t)b * P + i] = pre_mc[s * D + b];
+            }
+            for (int b = j; b < D; ++b) O.mc[(int64_t)b * P + i] = make_int2(0, 0);
             // diffuse bounce: pattern cosines and the scattered basis
-            const F3 ks = k[j + 1];
-            const F3 kr = fsub(k[j], fscl(2.0f * fdot(k[j], n), n));
-            O.scat[i] = make_float4(fdot(ks, n), -fdot(k[j], ks), fdot(kr, ks), (float)(1.0 / dl));
-            const F3 sp = perp_or_f(ks, n, e_perp);
-            const F3 sq = fcross(sp, ks);
+            const F3 kin = f3(Q.kin.x, Q.kin.y, Q.kin.z);
+            const F3 n = f3(Q.n.x, Q.n.y, Q.n.z);
+            const F3 kr = fsub(kin, fscl(2.0f * fdot(kin, n), n));
+            O.scat[i] = make_float4(fdot(ks, n), -fdot(kin, ks), fdot(kr, ks), (float)(1.0 / dl));
+            const F3 sp_ = perp_or_f(ks, n, f3(Q.ep.x, Q.ep.y, Q.ep.z));
+            const F3 sq = fcross(sp_, ks);
             F3 th, ph;
             sph_basis_f(fscl(-1.0f, ks), &th, &ph);
-            O.Dm[(int64_t)j * P + i] = make_float4(fdot(th, sp), fdot(th, sq), fdot(ph, sp), fdot(ph, sq));
+            O.Dm[(int64_t)j * P + i] = make_float4(fdot(th, sp_), fdot(th, sq), fdot(ph, sp_), fdot(ph, sq));
+            O.dir[i] = Q.d0;
+            O.dir[P + i] = make_float4(-ks.x, -ks.y, -ks.z, 0.0f);
         }
-        for (int b = j; b < D; ++b) O.mc[(int64_t)b * P + i] = make_int2(0, 0);
-        O.dir[i] = make_float4(k[1].x, k[1].y, k[1].z, 0.0f);
-        O.dir[P + i] = make_float4(-k[j + 1].x, -k[j + 1].y, -k[j + 1].z, 0.0f);
+        __syncthreads();
+        // the tile's points: rows of consecutive paths are contiguous in O.pts too;
+        // i0 row doubles start on a 16-byte boundary (i0 is a multiple of 128)
+        const int cnt = (int)(P - i0 < DF_REC_THREADS ? P - i0 : DF_REC_THREADS) * row;
+        double2* dst = reinterpret_cast<double2*>(O.pts + i0 * row);
+        const double2* s2 = reinterpret_cast<const double2*>(sp);
+        for (int k = threadIdx.x; k < cnt / 2; k += DF_REC_THREADS) dst[k] = s2[k];
+        if ((cnt & 1) && threadIdx.x == 0) O.pts[i0 * row + cnt - 1] = sp[cnt - 1];
+        __syncthreads();
     }
 }
 
@@ -1170,13 +1247,16 @@ RT_EXPORT rt_status rt_trace_diffuse(rt_ctx* ctx, const rt_scene* scene, const d
     int32_t* word_off = nullptr;
     int64_t* cnt = nullptr;
     int64_t* src = nullptr;
+    DfPre* pre = nullptr;
+    float4* pre_Dm = nullptr;
+    int2* pre_mc = nullptr;
     rt_paths* p = nullptr;
     cudaError_t e = cudaSuccess;
     auto A = [&](void** d, size_t b) {
         if (e == cudaSuccess) e = cudaMallocAsync(d, b, st);
     };
     auto cleanup = [&]() {
-        void* tmp[] = {z, hit_tri, hit_pt, hit_pt32, rx32, mask, word_off, cnt, src};
+        void* tmp[] = {z, hit_tri, hit_pt, hit_pt32, rx32, mask, word_off, cnt, src, pre, pre_Dm, pre_mc};
         for (void* q : tmp)
             if (q) cudaFreeAsync(q, st);
     };
@@ -1231,13 +1311,22 @@ RT_EXPORT rt_status rt_trace_diffuse(rt_ctx* ctx, const rt_scene* scene, const d
     A((void**)&p->d_Dm, Pa * (D + 1) * 16);
     A((void**)&p->d_dir, Pa * 2 * 16);
     A((void**)&p->d_scat, Pa * 16);
+    if (P > 0) {
+        A((void**)&pre, N * D * sizeof(DfPre));
+        A((void**)&pre_Dm, N * D * D * 16);
+        A((void**)&pre_mc, N * D * D * 8);
+    }
     if (e == cudaSuccess && P > 0) {
         k_df_expand<<<grid_of(ctx, R * W, 256, 8), 256, 0, st>>>((int)R, W, mask, word_off, p->d_rx_offsets, p->d_rx,
                                                                   src); RT_COUNT(ctx);
         RecOut O{p->d_depth, p->d_tri, p->d_pts, p->d_tau, p->d_len, p->d_mc, p->d_Dm, p->d_dir, p->d_scat};
-        k_df_records<<<grid_of(ctx, P, 128, 16), 128, 0, st>>>(P, N, (int)D, tx_host[0], tx_host[1], tx_host[2], rx_dev,
-                                                               p->d_rx, src, hit_tri, hit_pt, scene->d_tri_n64,
-                                                               scene->d_tri_material, scene->d_is_pec, O); RT_COUNT(ctx);
+        k_df_prefix<<<grid_of(ctx, N * D, 128, 16), 128, 0, st>>>(N, (int)D, tx_host[0], tx_host[1], tx_host[2], hit_tri,
+                                                                  hit_pt, scene->d_tri_n64, scene->d_tri_material,
+                                                                  scene->d_is_pec, pre, pre_Dm, pre_mc); RT_COUNT(ctx);
+        k_df_records<<<grid_of(ctx, P, DF_REC_THREADS, 12), DF_REC_THREADS, 0, st>>>(
+            P, N, (int)D, tx_host[0], tx_host[1], tx_host[2], rx_dev, p->d_rx, src, hit_tri, hit_pt, pre, pre_Dm, pre_mc,
+            O);
+        RT_COUNT(ctx);
         e = cudaGetLastError();
     }
     cleanup();

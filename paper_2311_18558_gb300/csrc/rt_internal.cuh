@@ -36,6 +36,7 @@ struct rt_ctx {
     unsigned long long* d_counters = nullptr;   // 8 device counters (bit 1)
     int64_t h_counters[8] = {0};                // host-side counts of the same slots
     cudaEvent_t ev[8] = {};                     // trace stage events (bit 0)
+    int32_t stage_pending = 0;                  // the last trace's events are recorded, not yet read
     // coherent processing order of the launch directions, per ray count (see trace.cu)
     int64_t sched_n = 0, sched_band = 0, sched_full = 0;
     int32_t* d_sched_order = nullptr;   // sched_band entries
@@ -117,6 +118,9 @@ rt_status rt_cuda_fail(rt_ctx* ctx, cudaError_t e, const char* what);
 // Grow the context scratch arena to at least `bytes`; returns its base.
 rt_status rt_scratch(rt_ctx* ctx, size_t bytes, void** base);
 int32_t* rt_status_ptr(rt_ctx* ctx);
+// Stage times of the last trace (profiling bit 0): waits for its last stage
+// event and fills ctx->stage_ms; a no-op when nothing is pending.
+rt_status rt_collect_stage_times(rt_ctx* ctx);
 
 #define RT_CK(ctx, call)                                              \
     do {                                                              \

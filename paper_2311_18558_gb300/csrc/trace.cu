@@ -1495,6 +1495,7 @@ static rt_status ray_schedule(rt_ctx* ctx, int64_t n, RaySched* out) {
 }
 
 static void mark(rt_ctx* ctx, int k) {
+    if (k == 0) ctx->stage_pending = 0;   // a new trace: unread stage times of the last one are dropped
     if (ctx->profile & 1) cudaEventRecord(ctx->ev[k], ctx->stream);
 }
 
@@ -1833,21 +1834,9 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
     rt_status s = rt_launch_paths_records(ctx, p);
     if (s != RT_OK) return fail(s);
     if (ctx->profile & 1) {
-        cudaEventRecord(ctx->ev[5], st);
-        TCK(cudaEventSynchronize(ctx->ev[5]));
-        float ms;
-        // stages: SBR, dedup + sort (incl. candidate setup), image method, visibility, emission
-        const int a[5] = {0, 1, 2, 3, 4}, b[5] = {1, 2, 3, 4, 5};
-        for (int k = 0; k < 5; ++k) {
-            cudaEventElapsedTime(&ms, ctx->ev[a[k]], ctx->ev[b[k]]);
-            ctx->stage_ms[k] = ms;
-        }
-        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
-        ctx->stage_ms[5] = ms;
-        cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[7]);   // the SBR kernel alone
-        ctx->stage_ms[6] = ms;
-        cudaEventElapsedTime(&ms, ctx->ev[7], ctx->ev[1]);   // the FP64 re-trace
-        ctx->stage_ms[7] = ms;
+        // read out by rt_collect_stage_times: the trace itself does not wait
+        TCK(cudaEventRecord(ctx->ev[5], st));
+        ctx->stage_pending = 1;
     }
 #undef TCK
     *out = p;
@@ -2779,20 +2768,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
     rt_status s1 = rt_launch_paths_records(ctx, p);
     if (s1 != RT_OK) return fail(s1);
     if (ctx->profile & 1) {
-        cudaEventRecord(ctx->ev[5], st);
-        BCK(cudaEventSynchronize(ctx->ev[5]));
-        float ms;
-        const int a[5] = {0, 1, 2, 3, 4}, b[5] = {1, 2, 3, 4, 5};
-        for (int k = 0; k < 5; ++k) {
-            cudaEventElapsedTime(&ms, ctx->ev[a[k]], ctx->ev[b[k]]);
-            ctx->stage_ms[k] = ms;
-        }
-        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
-        ctx->stage_ms[5] = ms;
-        cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[7]);   // the SBR kernel alone
-        ctx->stage_ms[6] = ms;
-        cudaEventElapsedTime(&ms, ctx->ev[7], ctx->ev[1]);   // the FP64 re-trace
-        ctx->stage_ms[7] = ms;
+        BCK(cudaEventRecord(ctx->ev[5], st));
+        ctx->stage_pending = 1;
     }
 #undef BCK
     *out = p;
@@ -2857,6 +2834,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_autotune_trace(
             rt_status s = rt_trace_paths(ctx, scene, tx_host, rx_dev, n_rx, n_rays, max_depth, &p);
             if (s != RT_OK) return s;
             rt_paths_free(p);
+            s = rt_collect_stage_times(ctx);
+            if (s != RT_OK) return s;
             best = std::min(best, ctx->stage_ms[stage]);
         }
         *ms_out = best;
