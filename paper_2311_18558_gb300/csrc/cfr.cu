@@ -587,6 +587,28 @@ __device__ __forceinline__ void nu_place(double tau, double fc, double df, int M
     d0 = (float)(l0d - xm);
 }
 
+// Bitonic sort of one value per lane across a full warp, ascending in key, the
+// payload (d, c) travelling with its key.
+__device__ __forceinline__ void warp_sort_by_key(int& key, float& d, float2& c, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int ok = __shfl_xor_sync(0xffffffffu, key, j);
+            const float od = __shfl_xor_sync(0xffffffffu, d, j);
+            const float ox = __shfl_xor_sync(0xffffffffu, c.x, j);
+            const float oy = __shfl_xor_sync(0xffffffffu, c.y, j);
+            // the lower lane of a pair keeps the smaller key in an ascending block
+            const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+            if (keep_min ? ok < key : ok > key) {
+                key = ok;
+                d = od;
+                c = make_float2(ox, oy);
+            }
+        }
+    }
+}
+
 // In-place radix-2 FFT of M = 2^logM complex values in shared memory by a CTA of
 // TC_THREADS threads: X[k] = sum_l x[l] exp(sign j 2 pi k l / M).
 __device__ void fft_smem(float2* x, int M, int logM, float sign) {
@@ -825,18 +847,49 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
             if (kind == 1) {
                 for (int l = tid; l < M; l += TC_THREADS) grid[l] = make_float2(0.0f, 0.0f);
                 __syncthreads();
-                for (int64_t i = i0 + tid; i < i1; i += TC_THREADS) {
-                    int l0;
-                    float d0;
-                    float2 e;
-                    nu_place(tau[i], fc, S.df, M, l0, d0, e);
-                    const float2 cp = cmul(a[i], e);
+                // Delays cluster on a few cells of the grid, so per-path atomics
+                // collide.  Each warp takes 32 consecutive paths, sorts them by
+                // first cell l0 across its lanes, sums each run of equal l0 per
+                // tap, and the run's first lane adds the 8 sums: the atomics of one
+                // instruction then go to distinct cells.
+                for (int64_t base = i0 + (tid & ~31); base < i1; base += TC_THREADS) {
+                    const int64_t i = base + lane;
+                    int key = 0x7fffffff;   // lanes past the segment sort last, add nothing
+                    float d0 = 0.0f;
+                    float2 cp = make_float2(0.0f, 0.0f);
+                    if (i < i1) {
+                        float2 e;
+                        nu_place(tau[i], fc, S.df, M, key, d0, e);
+                        cp = cmul(a[i], e);
+                    }
+                    warp_sort_by_key(key, d0, cp, lane);
+                    // same[s]: lane + s holds the same l0 (runs are contiguous)
+                    unsigned same = 0u;
+#pragma unroll
+                    for (int b = 0; b < 5; ++b) {
+                        const int ok = __shfl_down_sync(0xffffffffu, key, 1 << b);
+                        if (lane + (1 << b) < 32 && ok == key) same |= 1u << b;
+                    }
+                    const int kp = __shfl_up_sync(0xffffffffu, key, 1);
+                    const bool head = key != 0x7fffffff && (lane == 0 || kp != key);
 #pragma unroll
                     for (int k = 0; k < NU_W; ++k) {
                         const float wk = es_phi((d0 + (float)k) * (2.0f / NU_W));
-                        float2* gp = grid + ((l0 + k) & (M - 1));
-                        atomicAdd(&gp->x, wk * cp.x);
-                        atomicAdd(&gp->y, wk * cp.y);
+                        float vx = wk * cp.x, vy = wk * cp.y;
+#pragma unroll
+                        for (int b = 0; b < 5; ++b) {
+                            const float ox = __shfl_down_sync(0xffffffffu, vx, 1 << b);
+                            const float oy = __shfl_down_sync(0xffffffffu, vy, 1 << b);
+                            if (same & (1u << b)) {
+                                vx += ox;
+                                vy += oy;
+                            }
+                        }
+                        if (head) {
+                            float2* gp = grid + ((key + k) & (M - 1));
+                            atomicAdd(&gp->x, vx);
+                            atomicAdd(&gp->y, vy);
+                        }
                     }
                 }
                 __syncthreads();
