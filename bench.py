@@ -193,9 +193,16 @@ def max_over_ranks(world, x):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_step, steps, world, slowest_s):
+    """Weak scaling: every rank processes units_per_step per step; the job's rate is
+    all units of all ranks over the slowest rank's time."""
+    return units_per_step * steps * world / slowest_s
 
 
 # --------------------------------------------------------------------------- oracle (CPU)
@@ -333,7 +340,7 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in ev]
     total_s = max_over_ranks(world, sum(step_ms) / 1e3)
     ms_per_step = 1e3 * total_s / args.steps
-    value = sc.n_rays * args.steps * world / total_s
+    value = whole_job_rate(sc.n_rays, args.steps, world, total_s)
     gpu_launches = launches1 - launches0
     stage_mean = stage_acc / args.steps
 
