@@ -1258,26 +1258,38 @@ __global__ void k_row_count(const uint32_t* __restrict__ bits, int R, int64_t wo
 
 // Exclusive scan of n int64 counts into offsets[0..n] (single block).
 __global__ void k_scan(const int64_t* __restrict__ counts, int n, int64_t* offsets) {
-    __shared__ int64_t part[1024];
-    const int T = blockDim.x;
+    __shared__ int64_t wsum[32];
+    const int T = blockDim.x;   // a multiple of 32, at most 1024
     const int per = (n + T - 1) / T;
     const int lo = threadIdx.x * per, hi = min(n, lo + per);
     int64_t s = 0;
     for (int i = lo; i < hi; ++i) s += counts[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < T; o <<= 1) {
-        int64_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    // inclusive scan of the per-thread sums: within each warp by shuffles, then
+    // over the warp totals by the first warp
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
     }
-    int64_t run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int64_t v = lane < (T >> 5) ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(FULL, v, o);
+            if (lane >= o) v += y;
+        }
+        __syncwarp();
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int64_t run = x - s + (w > 0 ? wsum[w - 1] : 0);
     for (int i = lo; i < hi; ++i) {
         offsets[i] = run;
         run += counts[i];
     }
-    if (threadIdx.x == T - 1) offsets[n] = part[T - 1];
+    if (threadIdx.x == T - 1) offsets[n] = run;
 }
 
 // Expansion of the bitmask into (receiver, candidate) pairs at their final
