@@ -962,21 +962,32 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restri
         const int j = A.depth[i];
         float2 v0s[RT_MAX_DEPTH], v1s[RT_MAX_DEPTH], rps[RT_MAX_DEPTH], rls[RT_MAX_DEPTH];
         float4 Ds[RT_MAX_DEPTH];
+        int2 mcs[RT_MAX_DEPTH];
         int mats[RT_MAX_DEPTH];
         bool pecs[RT_MAX_DEPTH];
         float cis[RT_MAX_DEPTH], Rs[RT_MAX_DEPTH];
+        // every record of the path first (independent loads in flight together),
+        // then the chain
+#pragma unroll
+        for (int b = 0; b < RT_MAX_DEPTH; ++b) {
+            if (b < j) {
+                Ds[b] = __ldg(A.Dm + (int64_t)b * A.P + i);
+                mcs[b] = __ldg(A.mc + (int64_t)b * A.P + i);
+            }
+        }
+        const float4 geo = __ldg(A.geo + i);
+        const float4 Dl = __ldg(A.Dm + (int64_t)j * A.P + i);
         float2 E0 = make_float2(1.0f, 0.0f), E1 = make_float2(0.0f, 0.0f), u0 = E0, u1 = E1;
         int md = 0;
         float ci_d = 1.0f;
 #pragma unroll
         for (int b = 0; b < RT_MAX_DEPTH; ++b) {
             if (b >= j) break;
-            const float4 D = __ldg(A.Dm + (int64_t)b * A.P + i);
-            Ds[b] = D;
+            const float4 D = Ds[b];
             const float2 v0 = cadd(cscale(D.x, E0), cscale(D.y, E1));
             const float2 v1 = cadd(cscale(D.z, E0), cscale(D.w, E1));
             float2 eta, rp, rl, d0, d1;
-            mat_params(A, __ldg(A.mc + (int64_t)b * A.P + i), eta, pecs[b], mats[b], cis[b]);
+            mat_params(A, mcs[b], eta, pecs[b], mats[b], cis[b]);
             if (pecs[b]) {
                 rp = make_float2(-1.0f, 0.0f);
                 rl = make_float2(1.0f, 0.0f);
@@ -1000,13 +1011,11 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restri
         float prm[8];
         for (int c = 0; c < 8; ++c) prm[c] = __ldg(A.scat + 8 * md + c);
         const float nu = sqrtf(u0.x * u0.x + u0.y * u0.y + u1.x * u1.x + u1.y * u1.y);
-        const float4 geo = __ldg(A.geo + i);
         float df[5];
         LobeK k2, k3;
         lobes_of(s_lk, prm, md, A.n_mat, k2, k3);
         const float f = pattern(prm, k2, k3, geo, ci_d, df);
         const float sf = sqrtf(fmaxf(f, 0.0f));
-        const float4 Dl = __ldg(A.Dm + (int64_t)j * A.P + i);
         const float Kx = fminf(fmaxf(prm[1], 1e-12f), 1.0f - 1e-7f);
         const float sq1 = sqrtf(1.0f - Kx), sq2 = sqrtf(Kx);
         // a = K pol with K real: dL/dtheta = dK/dtheta Re(conj(g) pol) for every
@@ -1037,7 +1046,7 @@ __global__ void __launch_bounds__(256) k_df_bwd(DfArgs A, const float2* __restri
                 bool pec;
                 int mt;
                 float c;
-                mat_params(A, __ldg(A.mc + (int64_t)b * A.P + i), eta, pec, mt, c);
+                mat_params(A, mcs[b], eta, pec, mt, c);
                 fresnel<true>(eta, c, rp, rl, d0, d1);
                 const float2 w = cscale(R, cadd(cmul(l0, cmul(d0, v0s[b])), cmul(l1, cmul(d1, v1s[b]))));
                 add(mats[b], 0, w.x);
