@@ -873,23 +873,37 @@ __device__ __forceinline__ float2 pol_of(float4 Dl, float c1, float c2, const fl
     return make_float2(Dl.x * c1 * k1 + Dl.y * c2 * k2, Dl.x * c1 * s1 + Dl.y * c2 * s2);
 }
 
-__global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, float2* __restrict__ a, const double* __restrict__ tau_in,
+__global__ void __launch_bounds__(256, 4) k_df_fwd(DfArgs A, float2* __restrict__ a, const double* __restrict__ tau_in,
                                                 double* __restrict__ tau_out) {
     __shared__ LobeK s_lk[DF_LOBE_TAB][2];
     lobe_table(s_lk, A.scat, A.n_mat);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.P; i += (int64_t)gridDim.x * blockDim.x) {
         const int j = A.depth[i];
+        // the path's records first (independent loads in flight together)
+        float4 Ds[RT_MAX_DEPTH];
+        int2 mcs[RT_MAX_DEPTH];
+#pragma unroll
+        for (int b = 0; b < RT_MAX_DEPTH; ++b) {
+            if (b < j) {
+                Ds[b] = __ldg(A.Dm + (int64_t)b * A.P + i);
+                mcs[b] = __ldg(A.mc + (int64_t)b * A.P + i);
+            }
+        }
+        const float4 geo = __ldg(A.geo + i);
+        const float4 Dl = __ldg(A.Dm + (int64_t)j * A.P + i);
         float2 E0 = make_float2(1.0f, 0.0f), E1 = make_float2(0.0f, 0.0f);
         float2 u0 = E0, u1 = E1;
         int mat = 0;
         float ci = 1.0f;
-        for (int b = 0; b < j; ++b) {
-            const float4 D = __ldg(A.Dm + (int64_t)b * A.P + i);
+#pragma unroll
+        for (int b = 0; b < RT_MAX_DEPTH; ++b) {
+            if (b >= j) break;
+            const float4 D = Ds[b];
             const float2 v0 = cadd(cscale(D.x, E0), cscale(D.y, E1));
             const float2 v1 = cadd(cscale(D.z, E0), cscale(D.w, E1));
             float2 eta, rp, rl, d0, d1;
             bool pec;
-            mat_params(A, __ldg(A.mc + (int64_t)b * A.P + i), eta, pec, mat, ci);
+            mat_params(A, mcs[b], eta, pec, mat, ci);
             if (pec) {
                 rp = make_float2(-1.0f, 0.0f);
                 rl = make_float2(1.0f, 0.0f);
@@ -908,11 +922,9 @@ __global__ void __launch_bounds__(256) k_df_fwd(DfArgs A, float2* __restrict__ a
         const float* pr = A.scat + 8 * mat;
         float prm[8];
         for (int c = 0; c < 8; ++c) prm[c] = __ldg(pr + c);
-        const float4 geo = __ldg(A.geo + i);
         LobeK k2, k3;
         lobes_of(s_lk, prm, mat, A.n_mat, k2, k3);
         const float f = pattern(prm, k2, k3, geo, ci, nullptr);
-        const float4 Dl = __ldg(A.Dm + (int64_t)j * A.P + i);
         const float Kx = prm[1];
         const float2 pol = pol_of(Dl, sqrtf(fmaxf(0.0f, 1.0f - Kx)), sqrtf(fmaxf(0.0f, Kx)), A.chi, i);
         const float K = A.amp * prm[0] * sqrtf(fmaxf(f, 0.0f)) * nu * geo.w;
