@@ -179,44 +179,6 @@ __device__ __forceinline__ void walk(const BvhNode* __restrict__ nodes, const Ra
 // FP32 upper end of a box interval that covers the FP64 parameter t.
 __device__ __forceinline__ float up32(double t) { return __double2float_ru(t) * (1.0f + 1e-6f) + 1e-30f; }
 
-// Closest hit with t > tmin, skipping triangle `skip` (original ids): the
-// smallest t, then among hits within DF_TIE_TOL of it the lowest triangle id.
-__device__ int closest_hit64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const Ray64& r,
-                             double tmin, int skip, double& t_out, int32_t* status) {
-    double bt = INFINITY;
-    float thi = INFINITY;
-    walk(nodes, r, (float)tmin * 0.5f, thi, status, [&](int first, int count) {
-        for (int k = first; k < first + count; ++k) {
-            const float4 p0 = __ldg(tris + 3 * k);
-            if (__float_as_int(p0.w) == skip) continue;
-            double t;
-            if (!tri_hit64(r, p0, __ldg(tris + 3 * k + 1), __ldg(tris + 3 * k + 2), t)) continue;
-            if (t > tmin && t < bt) {
-                bt = t;
-                thi = up32(bt + DF_TIE_TOL * bt);
-            }
-        }
-        return false;
-    });
-    t_out = bt;
-    if (!(bt < INFINITY)) return -1;
-    const double tmax = bt + DF_TIE_TOL * bt;
-    const float thi2 = up32(tmax);
-    int best = -1;
-    walk(nodes, r, (float)tmin * 0.5f, thi2, status, [&](int first, int count) {
-        for (int k = first; k < first + count; ++k) {
-            const float4 p0 = __ldg(tris + 3 * k);
-            const int id = __float_as_int(p0.w);
-            if (id == skip || (best >= 0 && id >= best)) continue;
-            double t;
-            if (!tri_hit64(r, p0, __ldg(tris + 3 * k + 1), __ldg(tris + 3 * k + 2), t)) continue;
-            if (t > tmin && t <= tmax) best = id;
-        }
-        return false;
-    });
-    return best;
-}
-
 // FP32 copy of a ray for the prefilter of the any-hit queries.
 struct Ray32 {
     float o[3], d[3];
@@ -259,32 +221,99 @@ __device__ __forceinline__ void ray32_set(float3 o, float3 d, Ray32& q) {
 // 2u (4 L^2 + 16 (M_v + M_o) L) (L the largest sheared coordinate); the margin is
 // that plus twice the FP64 test's growth DF_TRI_TOL (|U| + |V| + |W|).  The
 // parameter t is trusted to 64u (M_v + M_o) / |d_kz| plus 1e-6.
-__device__ __forceinline__ int tri_seg32(const Ray32& r, float4 p0, float4 p1, float4 p2, float tlo, float thi) {
+struct Edge32 {
+    float U, V, W, m;   // edge functions and their error margin
+    float Akz, Bkz, Ckz, Mv, Mo;
+};
+
+__device__ __forceinline__ Edge32 edges32(const Ray32& r, float4 p0, float4 p1, float4 p2) {
     const float A[3] = {p0.x - r.o[0], p0.y - r.o[1], p0.z - r.o[2]};
     const float B[3] = {p1.x - r.o[0], p1.y - r.o[1], p1.z - r.o[2]};
     const float C[3] = {p2.x - r.o[0], p2.y - r.o[1], p2.z - r.o[2]};
-    const float Akz = A[r.kz], Bkz = B[r.kz], Ckz = C[r.kz];
-    const float Ax = A[r.kx] - r.Sx * Akz, Ay = A[r.ky] - r.Sy * Akz;
-    const float Bx = B[r.kx] - r.Sx * Bkz, By = B[r.ky] - r.Sy * Bkz;
-    const float Cx = C[r.kx] - r.Sx * Ckz, Cy = C[r.ky] - r.Sy * Ckz;
-    const float U = Cx * By - Cy * Bx, V = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
+    Edge32 e;
+    e.Akz = A[r.kz];
+    e.Bkz = B[r.kz];
+    e.Ckz = C[r.kz];
+    const float Ax = A[r.kx] - r.Sx * e.Akz, Ay = A[r.ky] - r.Sy * e.Akz;
+    const float Bx = B[r.kx] - r.Sx * e.Bkz, By = B[r.ky] - r.Sy * e.Bkz;
+    const float Cx = C[r.kx] - r.Sx * e.Ckz, Cy = C[r.ky] - r.Sy * e.Ckz;
+    e.U = Cx * By - Cy * Bx;
+    e.V = Ax * Cy - Ay * Cx;
+    e.W = Bx * Ay - By * Ax;
     const float Sab = fabsf(r.Sx) + fabsf(r.Sy);
-    const float Mv = fmaxf(fmaxf(fabsf(A[r.kx]) + fabsf(A[r.ky]) + fabsf(Akz) * Sab,
-                                 fabsf(B[r.kx]) + fabsf(B[r.ky]) + fabsf(Bkz) * Sab),
-                           fabsf(C[r.kx]) + fabsf(C[r.ky]) + fabsf(Ckz) * Sab);
-    const float Mo = fabsf(r.o[r.kx]) + fabsf(r.o[r.ky]) + fabsf(r.o[r.kz]) * Sab;
+    e.Mv = fmaxf(fmaxf(fabsf(A[r.kx]) + fabsf(A[r.ky]) + fabsf(e.Akz) * Sab,
+                       fabsf(B[r.kx]) + fabsf(B[r.ky]) + fabsf(e.Bkz) * Sab),
+                 fabsf(C[r.kx]) + fabsf(C[r.ky]) + fabsf(e.Ckz) * Sab);
+    e.Mo = fabsf(r.o[r.kx]) + fabsf(r.o[r.ky]) + fabsf(r.o[r.kz]) * Sab;
     const float L = fmaxf(fmaxf(fmaxf(fabsf(Ax), fabsf(Ay)), fmaxf(fabsf(Bx), fabsf(By))), fmaxf(fabsf(Cx), fabsf(Cy)));
-    const float sum = fabsf(U) + fabsf(V) + fabsf(W);
+    const float sum = fabsf(e.U) + fabsf(e.V) + fabsf(e.W);
     const float u = 5.9604645e-8f;
-    const float m = 2.0f * u * (4.0f * L * L + 16.0f * (Mv + Mo) * L) + 2.0f * (float)DF_TRI_TOL * sum;
-    if ((U < -m || V < -m || W < -m) && (U > m || V > m || W > m)) return 0;
-    const bool pos = U > m && V > m && W > m, neg = U < -m && V < -m && W < -m;
+    e.m = 2.0f * u * (4.0f * L * L + 16.0f * (e.Mv + e.Mo) * L) + 2.0f * (float)DF_TRI_TOL * sum;
+    return e;
+}
+
+// The line of the ray passes outside the triangle for certain (edge functions of
+// both signs beyond the margin): the FP64 test misses too.
+__device__ __forceinline__ bool certain_miss32(const Edge32& e) {
+    return (e.U < -e.m || e.V < -e.m || e.W < -e.m) && (e.U > e.m || e.V > e.m || e.W > e.m);
+}
+
+__device__ __forceinline__ int tri_seg32(const Ray32& r, float4 p0, float4 p1, float4 p2, float tlo, float thi) {
+    const Edge32 e = edges32(r, p0, p1, p2);
+    if (certain_miss32(e)) return 0;
+    const float m = e.m;
+    const bool pos = e.U > m && e.V > m && e.W > m, neg = e.U < -m && e.V < -m && e.W < -m;
     if (!pos && !neg) return 2;
-    const float t = (U * Akz + V * Bkz + W * Ckz) * r.Sz / (U + V + W);
-    const float tt = 64.0f * u * (Mv + Mo) * fabsf(r.Sz) + 1e-6f;
+    const float u = 5.9604645e-8f;
+    const float t = (e.U * e.Akz + e.V * e.Bkz + e.W * e.Ckz) * r.Sz / (e.U + e.V + e.W);
+    const float tt = 64.0f * u * (e.Mv + e.Mo) * fabsf(r.Sz) + 1e-6f;
     if (t > tlo + tt && t < thi - tt) return 1;
     if (t < tlo - tt || t > thi + tt) return 0;
     return 2;
+}
+
+// Closest hit with t > tmin, skipping triangle `skip` (original ids): the
+// smallest t, then among hits within DF_TIE_TOL of it the lowest triangle id.
+// The FP64 test runs only on triangles that the FP32 edge test (q: the ray's
+// FP32 copy) does not place outside for certain.
+__device__ int closest_hit64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const Ray64& r,
+                             const Ray32& q, double tmin, int skip, double& t_out, int32_t* status) {
+    double bt = INFINITY;
+    float thi = INFINITY;
+    walk(nodes, r, (float)tmin * 0.5f, thi, status, [&](int first, int count) {
+        for (int k = first; k < first + count; ++k) {
+            const float4 p0 = __ldg(tris + 3 * k);
+            if (__float_as_int(p0.w) == skip) continue;
+            const float4 p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+            if (certain_miss32(edges32(q, p0, p1, p2))) continue;
+            double t;
+            if (!tri_hit64(r, p0, p1, p2, t)) continue;
+            if (t > tmin && t < bt) {
+                bt = t;
+                thi = up32(bt + DF_TIE_TOL * bt);
+            }
+        }
+        return false;
+    });
+    t_out = bt;
+    if (!(bt < INFINITY)) return -1;
+    const double tmax = bt + DF_TIE_TOL * bt;
+    const float thi2 = up32(tmax);
+    int best = -1;
+    walk(nodes, r, (float)tmin * 0.5f, thi2, status, [&](int first, int count) {
+        for (int k = first; k < first + count; ++k) {
+            const float4 p0 = __ldg(tris + 3 * k);
+            const int id = __float_as_int(p0.w);
+            if (id == skip || (best >= 0 && id >= best)) continue;
+            const float4 p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+            if (certain_miss32(edges32(q, p0, p1, p2))) continue;
+            double t;
+            if (!tri_hit64(r, p0, p1, p2, t)) continue;
+            if (t > tmin && t <= tmax) best = id;
+        }
+        return false;
+    });
+    return best;
 }
 
 // Any hit with tlo < t < thi, skipping triangle `skip`: FP32 prefilter, FP64
@@ -375,8 +404,11 @@ __global__ void __launch_bounds__(DF_THREADS) k_df_rays(int64_t N, int D, double
         int b = 0;
         for (; b < D; ++b) {
             ray64_init(r);
+            Ray32 q;
+            ray32_set(make_float3((float)r.o[0], (float)r.o[1], (float)r.o[2]),
+                      make_float3((float)r.d[0], (float)r.d[1], (float)r.d[2]), q);
             double th;
-            const int t = closest_hit64(S.nodes, S.tris, r, S.eps, prev, th, status);
+            const int t = closest_hit64(S.nodes, S.tris, r, q, S.eps, prev, th, status);
             if (t < 0) break;
             double p[3], n[3];
             for (int c = 0; c < 3; ++c) p[c] = __dadd_rn(r.o[c], __dmul_rn(th, r.d[c]));
