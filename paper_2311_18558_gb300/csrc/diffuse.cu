@@ -318,11 +318,12 @@ __device__ int closest_hit64(const BvhNode* __restrict__ nodes, const float4* __
 
 // Any hit with tlo < t < thi, skipping triangle `skip`: FP32 prefilter, FP64
 // test only where the prefilter is undecided.
-// The segment is origin + t d, t in (eps / |d|, 1 - eps / |d|), |d|^2 = len2;
+// The segment is origin + t d, t in (eps / |d|, 1 - eps / |d|); len2f is |d|^2
+// from the FP32 direction (the FP32 bounds only), the FP64 |d| is formed from r.d;
 // only r.o and r.d need to be set: the FP64 shear and bounds are formed the first
 // time a triangle is undecided (most queries never need them).
 __device__ bool any_hit_seg(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, Ray64& r,
-                            float3 o32, float3 d32, double len2, double eps, int skip, int32_t* status) {
+                            float3 o32, float3 d32, float len2f, double eps, int skip, int32_t* status) {
     r.of = o32;
     {
         const float dk[3] = {d32.x, d32.y, d32.z};
@@ -334,7 +335,7 @@ __device__ bool any_hit_seg(const BvhNode* __restrict__ nodes, const float4* __r
     ray32_set(o32, d32, q);
     bool hit = false, fp64_ready = false;
     double tlo = 0.0, thi = 0.0;
-    const float flo = (float)eps * rsqrtf((float)len2), fthi = 1.0f - flo;
+    const float flo = (float)eps * rsqrtf(len2f), fthi = 1.0f - flo;
     const float fhi = fthi * (1.0f + 1e-6f) + 1e-30f;
     walk(nodes, r, flo * 0.5f, fhi, status, [&](int first, int count) {
         for (int k = first; k < first + count; ++k) {
@@ -349,7 +350,7 @@ __device__ bool any_hit_seg(const BvhNode* __restrict__ nodes, const float4* __r
             }
             if (!fp64_ready) {
                 ray64_init_shear(r);
-                const double len = sqrt(len2);
+                const double len = sqrt(r.d[0] * r.d[0] + r.d[1] * r.d[1] + r.d[2] * r.d[2]);
                 tlo = eps / len;
                 thi = 1.0 - tlo;
                 fp64_ready = true;
@@ -478,11 +479,18 @@ __device__ __forceinline__ void nee_pair(int64_t N, int b, int i, int s, int r, 
         ray.o[c] = p[c];
         ray.d[c] = x[c] - p[c];
     }
-    const double len2 = ray.d[0] * ray.d[0] + ray.d[1] * ray.d[1] + ray.d[2] * ray.d[2];
-    if (!(len2 > S.eps * S.eps)) return;
     const float3 o32 = make_float3(pf.x, pf.y, pf.z);
     const float3 d32 = make_float3((float)ray.d[0], (float)ray.d[1], (float)ray.d[2]);
-    if (any_hit_seg(S.nodes, S.tris, ray, o32, d32, len2, S.eps, t, status)) return;
+    // |d| > eps decided in FP32 where the FP32 length (relative error below 1e-6)
+    // is clear of eps^2 by 1e-5, else in FP64
+    const float len2f = d32.x * d32.x + d32.y * d32.y + d32.z * d32.z;
+    const float e2f = (float)(S.eps * S.eps);
+    if (len2f < e2f * 0.99999f) return;
+    if (!(len2f > e2f * 1.00001f)) {
+        const double len2 = ray.d[0] * ray.d[0] + ray.d[1] * ray.d[1] + ray.d[2] * ray.d[2];
+        if (!(len2 > S.eps * S.eps)) return;
+    }
+    if (any_hit_seg(S.nodes, S.tris, ray, o32, d32, len2f, S.eps, t, status)) return;
     atomicOr(mask + (int64_t)r * W + (s >> 5), 1u << (s & 31));
 }
 
