@@ -910,24 +910,28 @@ __global__ void k_bitonic_merge_local(uint64_t* keys, uint64_t k) {
 constexpr int RANK_SORT_MAX = 8192;
 constexpr int RANK_TILE = 512;
 
-// The order is key_less: depth first, then the key (left-aligned fields).
+// The order is key_less: depth first, then the key (left-aligned fields).  With
+// every used field >= 1 (triangle id + 1), the key shifted right by its empty
+// fields, v = key >> 16 (4 - depth), orders the same way as one unsigned number:
+// a depth-q value is at least 2^(16 (q - 1)), above every depth-(q - 1) value, and
+// within a depth the shift keeps the order.
+__device__ __forceinline__ uint64_t rank_value(uint64_t key) {
+    const int q = rt_key_depth(key);
+    return q == 0 ? 0ull : key >> (16 * (4 - q));
+}
+
 __global__ void k_rank_count(const uint64_t* __restrict__ keys, int n, int* __restrict__ rank) {
     __shared__ uint64_t sj[RANK_TILE];
-    __shared__ int sd[RANK_TILE];
     const int j0 = blockIdx.x * RANK_TILE;
-    for (int t = threadIdx.x; t < RANK_TILE; t += blockDim.x) {
-        const bool in = j0 + t < n;
-        sj[t] = in ? keys[j0 + t] : ~0ull;
-        sd[t] = in ? rt_key_depth(sj[t]) : RT_MAX_DEPTH + 1;   // padding sorts last
-    }
+    for (int t = threadIdx.x; t < RANK_TILE; t += blockDim.x)
+        sj[t] = j0 + t < n ? rank_value(keys[j0 + t]) : ~0ull;   // padding never counts as smaller
     __syncthreads();
     const int i = blockIdx.y * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint64_t key = keys[i];
-    const int dk = rt_key_depth(key);
+    const uint64_t v = rank_value(keys[i]);
     int c = 0;
 #pragma unroll 8
-    for (int t = 0; t < RANK_TILE; ++t) c += (sd[t] < dk || (sd[t] == dk && sj[t] < key)) ? 1 : 0;
+    for (int t = 0; t < RANK_TILE; ++t) c += sj[t] < v ? 1 : 0;
     if (c) atomicAdd(rank + i, c);
 }
 
