@@ -609,6 +609,21 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_info(const 
 extern "C" __attribute__((visibility("default"))) rt_status rt_paths_free(rt_paths* p) {
     if (!p) return RT_ERR_INVALID_ARG;
     cudaStream_t st = p->stream;
+    if (p->d_block_geo) {
+        cudaFreeAsync(p->d_block_geo, st);
+        p->d_rx = nullptr;
+        p->d_depth = nullptr;
+        p->d_tri = nullptr;
+        p->d_pts = nullptr;
+    }
+    if (p->d_block_rec) {
+        cudaFreeAsync(p->d_block_rec, st);
+        p->d_tau = nullptr;
+        p->d_len = nullptr;
+        p->d_mc = nullptr;
+        p->d_Dm = nullptr;
+        p->d_dir = nullptr;
+    }
     void* ptrs[] = {p->d_rx_offsets, p->d_rx, p->d_depth, p->d_tri,  p->d_tau, p->d_len,
                     p->d_mc,         p->d_Dm, p->d_pts,   p->d_cand, p->d_dir, p->d_scat};
     for (void* q : ptrs)

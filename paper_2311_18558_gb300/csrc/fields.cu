@@ -346,12 +346,19 @@ int grid_for(const rt_ctx* ctx, int64_t n, int threads, int per_sm) {
 
 rt_status rt_launch_paths_records(rt_ctx* ctx, rt_paths* p) {
     cudaStream_t st = ctx->stream;
-    const int64_t Pa = p->P > 0 ? p->P : 1;
-    RT_CK(ctx, cudaMallocAsync((void**)&p->d_tau, Pa * 8, st));
-    RT_CK(ctx, cudaMallocAsync((void**)&p->d_len, Pa * 4, st));
-    RT_CK(ctx, cudaMallocAsync((void**)&p->d_mc, Pa * p->D * 8, st));
-    RT_CK(ctx, cudaMallocAsync((void**)&p->d_Dm, Pa * (p->D + 1) * 16, st));
-    RT_CK(ctx, cudaMallocAsync((void**)&p->d_dir, Pa * 2 * 16, st));
+    const size_t Pa = p->P > 0 ? (size_t)p->P : 1;
+    // one allocation for the five record arrays
+    RtCarve c;
+    const size_t o_tau = c.take(Pa * 8), o_len = c.take(Pa * 4), o_mc = c.take(Pa * p->D * 8),
+                 o_Dm = c.take(Pa * (p->D + 1) * 16), o_dir = c.take(Pa * 2 * 16);
+    char* b = nullptr;
+    RT_CK(ctx, cudaMallocAsync((void**)&b, c.off, st));
+    p->d_block_rec = b;
+    p->d_tau = reinterpret_cast<double*>(b + o_tau);
+    p->d_len = reinterpret_cast<float*>(b + o_len);
+    p->d_mc = reinterpret_cast<int2*>(b + o_mc);
+    p->d_Dm = reinterpret_cast<float4*>(b + o_Dm);
+    p->d_dir = reinterpret_cast<float4*>(b + o_dir);
     if (p->P == 0) return RT_OK;
     k_records<<<grid_for(ctx, p->P, 128, 16), 128, 0, st>>>(p->P, p->D, p->d_pts, p->d_depth, p->d_tri,
                                                            p->scene->d_tri_n64, p->scene->d_tri_material,

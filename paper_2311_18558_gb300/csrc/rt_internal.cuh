@@ -110,6 +110,19 @@ struct rt_paths {
     const float2* d_chi = nullptr;     // diffuse paths: caller-owned per-path phases (chi_1, chi_2), or none
     float4* d_scat = nullptr;          // diffuse paths, P: (k_s.n, -k_i.k_s, k_r.k_s, 1/d_last) at the
                                        // diffuse point (n facing the incident wave)
+    // single allocations carved into several arrays (freed as a whole), or null
+    void* d_block_geo = nullptr;       // d_rx, d_depth, d_tri, d_pts
+    void* d_block_rec = nullptr;       // d_tau, d_len, d_mc, d_Dm, d_dir
+};
+
+// Offsets of arrays carved from one allocation, each on a 256-byte boundary.
+struct RtCarve {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    }
 };
 
 // ---------------------------------------------------------------- error helpers

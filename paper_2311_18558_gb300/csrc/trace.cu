@@ -1786,10 +1786,19 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         const int64_t P = n_emit;
         p->P = P;
         const size_t Pa = std::max<int64_t>(P, 1);
-        TCK(cudaMallocAsync((void**)&p->d_pts, Pa * (D + 2) * 3 * 8, st));
-        TCK(cudaMallocAsync((void**)&p->d_depth, Pa * 4, st));
-        TCK(cudaMallocAsync((void**)&p->d_rx, Pa * 4, st));
-        TCK(cudaMallocAsync((void**)&p->d_tri, Pa * D * 4, st));
+        {
+            // one allocation for the four path arrays
+            RtCarve c;
+            const size_t o_pts = c.take(Pa * (D + 2) * 3 * 8), o_depth = c.take(Pa * 4), o_rx = c.take(Pa * 4),
+                         o_tri = c.take(Pa * D * 4);
+            char* b = nullptr;
+            TCK(cudaMallocAsync((void**)&b, c.off, st));
+            p->d_block_geo = b;
+            p->d_pts = reinterpret_cast<double*>(b + o_pts);
+            p->d_depth = reinterpret_cast<int32_t*>(b + o_depth);
+            p->d_rx = reinterpret_cast<int32_t*>(b + o_rx);
+            p->d_tri = reinterpret_cast<int32_t*>(b + o_tri);
+        }
         TCK(cudaMallocAsync((void**)&path_cand, Pa * 4, st));
         TCK(cudaMallocAsync((void**)&edge, Pa * 4, st));
         path_rx = p->d_rx;
@@ -1817,13 +1826,16 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
                 const int64_t Pn = P - dropped;
                 const size_t Pna = std::max<int64_t>(Pn, 1);
                 int64_t* off_n = nullptr;
-                double* pts_n = nullptr;
-                int32_t *depth_n = nullptr, *rx_n = nullptr, *tri_n = nullptr;
                 TCK(cudaMallocAsync((void**)&off_n, (size_t)(n_rx + 1) * 8, st));
-                TCK(cudaMallocAsync((void**)&pts_n, Pna * (D + 2) * 3 * 8, st));
-                TCK(cudaMallocAsync((void**)&depth_n, Pna * 4, st));
-                TCK(cudaMallocAsync((void**)&rx_n, Pna * 4, st));
-                TCK(cudaMallocAsync((void**)&tri_n, Pna * D * 4, st));
+                RtCarve c;
+                const size_t o_pts = c.take(Pna * (D + 2) * 3 * 8), o_depth = c.take(Pna * 4),
+                             o_rx = c.take(Pna * 4), o_tri = c.take(Pna * D * 4);
+                char* blk = nullptr;
+                TCK(cudaMallocAsync((void**)&blk, c.off, st));
+                double* pts_n = reinterpret_cast<double*>(blk + o_pts);
+                int32_t* depth_n = reinterpret_cast<int32_t*>(blk + o_depth);
+                int32_t* rx_n = reinterpret_cast<int32_t*>(blk + o_rx);
+                int32_t* tri_n = reinterpret_cast<int32_t*>(blk + o_tri);
                 k_row_count<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, counts);
                 RT_COUNT(ctx);
                 k_scan<<<1, 1024, 0, st>>>(counts, n_rx, off_n); RT_COUNT(ctx);
@@ -1832,10 +1844,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
                     depth_n, rx_n, tri_n); RT_COUNT(ctx);
                 TCK(cudaGetLastError());
                 cudaFreeAsync(p->d_rx_offsets, st);
-                cudaFreeAsync(p->d_pts, st);
-                cudaFreeAsync(p->d_depth, st);
-                cudaFreeAsync(p->d_rx, st);
-                cudaFreeAsync(p->d_tri, st);
+                cudaFreeAsync(p->d_block_geo, st);
+                p->d_block_geo = blk;
                 p->d_rx_offsets = off_n;
                 p->d_pts = pts_n;
                 p->d_depth = depth_n;
