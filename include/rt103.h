@@ -225,6 +225,15 @@ rt_status rt_eval_fields_backward(rt_ctx* ctx, const rt_paths* paths, const floa
                                   float* grad_gain_dev);
 
 /* ------------------------------------------------------------------ CFR */
+/* Arithmetic of the CFR calls: FP32 throughout, phases reduced per path in FP64.
+ * With N in {256, 512, 1024, 2048, 4096} and the tensor cores selected (the
+ * default, rt_set_cfr_tensor_cores), the products run as three TF32 products
+ * on tcgen05.  A receiver with more than 4096 paths (up to 4096 such receivers
+ * per call) is then evaluated by a non-uniform FFT instead: an exponential-of-
+ * semicircle kernel 8 cells wide on a 2N-cell grid, deconvolved per subcarrier.
+ * Its approximation error is about 1e-7 of sum_i |a_i| per entry, on top of FP32
+ * rounding.  Its segments add into the grid with float atomics, so the rounding
+ * of those receivers (not their value) may differ between runs. */
 
 /* Discrete CFR (Sec. II-A): H[r, n] = sum_{i in r} a_i exp(-j 2 pi (f_c + n df) tau_i),
  * n = -N/2 .. N/2-1, written to column n + N/2 of row r.
