@@ -1132,10 +1132,41 @@ def time_learned(rt, ctx, args, train_steps=100):
             "mlp_bwd_tflops": 2 * flops_fwd / (ms_bwd * 1e-3) / 1e12}
 
 
+def code_sha256(path):
+    """SHA-256 of a C/C++/CUDA source with its comments and layout removed: a
+    change to the code changes it, a change to a comment or to whitespace does
+    not.  String and character literals are kept as they are."""
+    import hashlib
+    with open(path, encoding="utf-8") as f:
+        src = f.read()
+    out = []
+    i, n = 0, len(src)
+    while i < n:
+        ch = src[i]
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif ch in "\"'":
+            j = i + 1
+            while j < n and src[j] != ch:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(ch)
+            i += 1
+    tokens = "".join(out).split()
+    return hashlib.sha256(" ".join(tokens).encode()).hexdigest()
+
+
 def ncu_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when the kernel's source file changed since the counters were taken."""
-    import hashlib
+    when the code of the kernel's source file changed since the counters were
+    taken (comments aside)."""
     p = os.path.join(ROOT, "profiles", "ncu_counters.json")
     if not os.path.exists(p):
         return None
@@ -1146,9 +1177,8 @@ def ncu_traffic(kernel):
     src = os.path.join(ROOT, d["source"])
     if not os.path.exists(src):
         return None
-    with open(src, "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != d["source_sha256"]:
-            return None
+    if code_sha256(src) != d["code_sha256"]:
+        return None
     return d["dram_bytes_per_launch"] * d.get("scale_to_bench", 1.0)
 
 

@@ -231,7 +231,8 @@ rt_status rt_eval_fields_backward(rt_ctx* ctx, const rt_paths* paths, const floa
  * on tcgen05.  A receiver with more than 4096 paths (up to 4096 such receivers
  * per call) is then evaluated by a non-uniform FFT instead: an exponential-of-
  * semicircle kernel 8 cells wide on a 2N-cell grid, deconvolved per subcarrier.
- * Its approximation error is about 1e-7 of sum_i |a_i| per entry, on top of FP32
+ * Its approximation error per entry is at most about 4e-7 of sum_i |a_i| (a
+ * lone path; far less when many paths' errors average), on top of FP32
  * rounding.  Its segments add into the grid with float atomics, so the rounding
  * of those receivers (not their value) may differ between runs. */
 
