@@ -37,3 +37,15 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_counter_validity_follows_the_code_not_the_comments(tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+    src = "int f(int x) { // twice\n  return 2 * x; /* doubled */ }\nconst char* s = \"a // b\";\n"
+    a, b, c = tmp_path / "a.cu", tmp_path / "b.cu", tmp_path / "c.cu"
+    a.write_text(src)
+    b.write_text(src.replace("// twice", "// two times").replace("  return", "\treturn"))
+    c.write_text(src.replace("a // b", "a // c"))
+    assert bench.code_sha256(str(a)) == bench.code_sha256(str(b))   # comments and layout only
+    assert bench.code_sha256(str(a)) != bench.code_sha256(str(c))   # a string literal is code
