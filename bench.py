@@ -53,6 +53,60 @@ def load_peaks():
     return dict(PEAKS_FALLBACK), "fallback"
 
 
+_MEASURED = {}
+
+
+def measure_peaks(dev):
+    """Peaks that MEASURED_PEAKS.json does not hold, measured here with cuBLAS through
+    torch (best of 5 CUDA-event-timed products, after one untimed one):
+      tf32_tflops  float32 matmul with TF32 tensor cores allowed (8192^3);
+      fp32_tflops  float32 matmul with TF32 off, i.e. FP32 FMA on the SIMT units (8192^3);
+      fp64_tflops  float64 matmul (4096^3).
+    Each is 2 n^3 flops over the fastest run.  Measured once per process."""
+    import torch
+    if _MEASURED:
+        return dict(_MEASURED)
+    stream = torch.cuda.current_stream()
+
+    def best(fn, flops, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            fn()
+            e.record(stream)
+            e.synchronize()
+            ts.append(s.elapsed_time(e))
+        return flops / (min(ts) * 1e-3) / 1e12
+
+    old_tf32 = torch.backends.cuda.matmul.allow_tf32
+    try:
+        n = 8192
+        g = torch.Generator(device=dev).manual_seed(0)
+        a = torch.randn((n, n), device=dev, generator=g)
+        b = torch.randn((n, n), device=dev, generator=g)
+        c = torch.empty((n, n), device=dev)
+        torch.backends.cuda.matmul.allow_tf32 = True
+        _MEASURED["tf32_tflops"] = best(lambda: torch.mm(a, b, out=c), 2.0 * n ** 3)
+        torch.backends.cuda.matmul.allow_tf32 = False
+        _MEASURED["fp32_tflops"] = best(lambda: torch.mm(a, b, out=c), 2.0 * n ** 3)
+        del a, b, c
+        n = 4096
+        a = torch.randn((n, n), device=dev, dtype=torch.float64, generator=g)
+        b = torch.randn((n, n), device=dev, dtype=torch.float64, generator=g)
+        c = torch.empty((n, n), device=dev, dtype=torch.float64)
+        _MEASURED["fp64_tflops"] = best(lambda: torch.mm(a, b, out=c), 2.0 * n ** 3, reps=3)
+        del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old_tf32
+    torch.cuda.empty_cache()
+    _MEASURED["how"] = ("cuBLAS via torch.mm, best of 5 CUDA-event-timed runs: float32 8192^3 with TF32 "
+                        "allowed (tf32) and not allowed (fp32, SIMT FMA), float64 4096^3 (3 runs)")
+    return dict(_MEASURED)
+
+
 class ClockSampler:
     """SM clocks and clock-event (throttle) reasons sampled during the timed region.
 
@@ -248,12 +302,16 @@ def run_reference(args):
         "impl": "reference", "metric": "rays/s traced", "value": value, "unit": "rays/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(sc, args.n_sub, "host"),
+        # the same config as the GPU arm, so the two lines compare like for like
+        "config": workload_config(sc, args.n_sub, L2_NOTE),
         "cpu_baseline": {"value": value, "unit": "rays/s", "cores": omp_threads(), "kind": "oracle",
                          "sample": "full street-canyon step per timed step (trace, fields, CFR, loss, adjoints)"},
         "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+L2_NOTE = "flushed: 256 MiB written between timed steps"
 
 
 def workload_config(sc, n_sub, l2):
@@ -273,6 +331,7 @@ def run_ours(args):
     world, rank, local = dist_setup(args.gpus)
     dev = torch.device("cuda", torch.cuda.current_device())
     peaks, peak_src = load_peaks()
+    peaks.update(measure_peaks(dev))
     sc = scenegen.street_canyon()
     N = args.n_sub
     fc, df = sc.f_center_hz, sc.delta_f_hz
@@ -394,7 +453,14 @@ def run_ours(args):
             "metric": "rays/s traced", "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(sc, N, "flushed: 256 MiB written between timed steps"),
+            "config": workload_config(sc, N, L2_NOTE),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clock_info,
+            # the metric's second half: the indoor calibration step (eval_fields, CFR, loss,
+            # CFR adjoint, eval_fields adjoint; one CUDA graph), and the same math as plain
+            # PyTorch complex64 ops on this GPU
+            "calibration_step_ms": calib_indoor["ms_per_step_median"],
+            "calibration_plain_ms": calib_indoor.get("plain_pytorch", {}).get("ms_per_step_median"),
             "paths_per_step": n_paths, "paths_per_s": n_paths * args.steps * world / total_s,
             "step_ms_spread": {"min": round(min(step_ms), 4), "median": round(float(np.median(step_ms)), 4),
                                "max": round(max(step_ms), 4)},
@@ -405,16 +471,44 @@ def run_ours(args):
             "diffuse": diffuse,
             "learned": learned,
             "batch": batch,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-            "clocks": clock_info,
+            "peaks_measured": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in measure_peaks(dev).items()},
             "counters": {"sbr_node_visits": counters[0], "sbr_tri_tests": counters[1], "sbr_queries": counters[2],
                          "fp64_retraced_rays": counters[3], "vis_node_visits": counters[4],
                          "vis_tri_tests": counters[5], "vis_segments": counters[6], "pairs_tested": counters[7]},
         }
+        line["summary"] = summary(line)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def summary(line):
+    """The headline figures of the nested records, repeated last on the line so that
+    a reader of its end sees them."""
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return round(d, 4) if isinstance(d, float) else d
+    ci, df_, fh, lr, bt = (line.get(k) for k in ("calibration_indoor", "diffuse", "fields_hbm", "learned", "batch"))
+    return {
+        "rays_per_s": g(line, "value"), "ms_per_step": g(line, "ms_per_step"), "e2e_rays_per_s": g(line, "e2e", "value"),
+        "calibration_step_ms": g(line, "calibration_step_ms"), "calibration_plain_ms": g(line, "calibration_plain_ms"),
+        "frac": {"k_sbr": g(line, "roofline", "frac"), "k_cfr_tc": g(ci, "roofline_cfr", "frac"),
+                 "k_fields_fwd": g(fh, "fields_fwd", "frac"), "k_fields_bwd": g(fh, "fields_bwd", "frac"),
+                 "k_df_fwd": g(df_, "roofline_fields_diffuse", "frac"),
+                 "k_df_bwd": g(df_, "roofline_fields_diffuse_bwd", "frac")},
+        "learned": {"train_rx": g(lr, "train_rx"), "neural_step_ms": g(lr, "neural_step_ms"),
+                    "plain_step_ms": g(lr, "plain_step_ms"), "heldout_loss_neural": g(lr, "heldout_loss_neural"),
+                    "heldout_loss_plain": g(lr, "heldout_loss_plain"),
+                    "eps_r_err_neural": g(lr, "per_triangle_error", "neural", "seen", "eps_r_mean_rel"),
+                    "eps_r_err_plain": g(lr, "per_triangle_error", "plain", "seen", "eps_r_mean_rel")},
+        "batch": {"trace_batched_ms": g(bt, "trace_batched_ms"), "trace_loop_ms": g(bt, "trace_loop_ms"),
+                  "calibration_graph_ms": g(bt, "calibration_graph_ms"),
+                  "calibration_loop_ms": g(bt, "calibration_loop_ms")},
+    }
 
 
 def time_calibration(rt, ctx, p, eps, sig, target, weight, freq, fc, df, N, flush, steps):
@@ -1041,20 +1135,26 @@ def time_batch(rt, ctx, args, reps=3):
             "autotune_stage_ms": tune_ms}
 
 
-def time_learned(rt, ctx, args, train_steps=100):
-    """Room-and-corridor scene (19,626 triangles, per-triangle ground truth):
-    MLP forward/backward kernel times, one training step of the neural form
-    (MLP -> fields -> CFR loss -> adjoints -> Adam) and of the plain per-object
-    form, and both held-out losses after the same number of Adam steps."""
+def time_learned(rt, ctx, args, train_steps=150, timed_steps=20, warm_steps=3):
+    """Room-and-corridor scene (19,626 triangles, per-triangle ground truth) at its
+    stated size: 10^5 receivers at 256 subcarriers, 90,000 for training and 10,000
+    held out, 10^6 rays at depth 3.  Both forms run full-batch Adam steps over all
+    training receivers (one step = one epoch): the neural form (MLP -> per-triangle
+    fields -> CFR loss -> adjoints -> MLP adjoint) and the plain per-object form
+    (4 objects).  Both are warmed for the same steps, then the same number of steps
+    of each is timed.  Reported: the step times, the held-out losses after the same
+    number of steps, and the per-triangle eps_r / sigma errors of both against the
+    hidden ground truth."""
     import torch
 
     import scenegen
-    sc = scenegen.room_corridor(n_rx=1536)
+    sc = scenegen.room_corridor()
+    n_tr = 90_000
     dev = torch.device("cuda", torch.cuda.current_device())
     scene_tri = rt.Scene.from_synthetic(ctx, sc)
     scene_obj = rt.Scene(ctx, sc.verts, sc.tris, sc.tri_object, np.zeros(4, np.uint8))
-    rx_tr = torch.tensor(sc.rx[:1280], device=dev)
-    rx_te = torch.tensor(sc.rx[1280:], device=dev)
+    rx_tr = torch.tensor(sc.rx[:n_tr], device=dev)
+    rx_te = torch.tensor(sc.rx[n_tr:], device=dev)
     fc, df, N, f = sc.f_center_hz, sc.delta_f_hz, sc.n_sub, sc.freq_hz
     eg, sg = torch.tensor(sc.eps_r, device=dev), torch.tensor(sc.sigma, device=dev)
 
@@ -1065,12 +1165,17 @@ def time_learned(rt, ctx, args, train_steps=100):
         w = torch.where(m > 0, 1 / torch.where(m > 0, m, torch.ones_like(m)), torch.zeros_like(m)).float()
         return T, w.contiguous()
 
+    t0 = time.perf_counter()
     tri_tr = rt.trace_paths(ctx, scene_tri, sc.tx, rx_tr, sc.n_rays, sc.max_depth)
+    torch.cuda.synchronize()
+    trace_s = time.perf_counter() - t0
     tri_te = rt.trace_paths(ctx, scene_tri, sc.tx, rx_te, sc.n_rays, sc.max_depth)
     obj_tr = rt.trace_paths(ctx, scene_obj, sc.tx, rx_tr, sc.n_rays, sc.max_depth)
     obj_te = rt.trace_paths(ctx, scene_obj, sc.tx, rx_te, sc.n_rays, sc.max_depth)
     Ttr, wtr = target(tri_tr)
     Tte, wte = target(tri_te)
+    seen = torch.unique(tri_tr.export()["seq"])
+    seen = seen[seen >= 0]
     plain = rt.LogMaterials(np.full(4, 4.0), np.full(4, 0.05)).cuda()
     opt_p = torch.optim.Adam(plain.parameters(), lr=0.05)
     Ws, bs = scenegen.random_mlp_params(11)
@@ -1108,11 +1213,33 @@ def time_learned(rt, ctx, args, train_steps=100):
         e0.synchronize()
         return s0.elapsed_time(e0) / n
 
-    ms_plain = timed(lambda: plain_step(obj_tr, Ttr, wtr), train_steps)
-    ms_neural = timed(lambda: neural_step(tri_tr, Ttr, wtr), train_steps)
+    run_p = lambda: plain_step(obj_tr, Ttr, wtr)     # noqa: E731
+    run_n = lambda: neural_step(tri_tr, Ttr, wtr)    # noqa: E731
+    for _ in range(warm_steps):
+        run_p()
+        run_n()
+    torch.cuda.synchronize()
+    ms_plain = timed(run_p, timed_steps)
+    ms_neural = timed(run_n, timed_steps)
+    for _ in range(train_steps - warm_steps - timed_steps):
+        run_p()
+        run_n()
     with torch.no_grad():
         held_plain = plain_step(obj_te, Tte, wte, train=False).item()
         held_neural = neural_step(tri_te, Tte, wte, train=False).item()
+        e_n, s_n = neural(ctx, scene_tri)
+        e_o, s_o = plain()
+        tob = torch.as_tensor(sc.tri_object, device=dev, dtype=torch.int64)
+        e_p, s_p = e_o[tob], s_o[tob]
+
+        def tri_err(e, s, idx):
+            re = ((e[idx] - eg[idx]).abs() / eg[idx]).mean().item()
+            ls = (torch.log10(s[idx]) - torch.log10(sg[idx])).abs().mean().item()
+            return {"eps_r_mean_rel": re, "sigma_mean_abs_log10": ls}
+        every = torch.arange(sc.n_tris, device=dev)
+        errors = {"neural": {"seen": tri_err(e_n, s_n, seen), "all": tri_err(e_n, s_n, every)},
+                  "plain": {"seen": tri_err(e_p, s_p, seen), "all": tri_err(e_p, s_p, every)},
+                  "triangles_seen": int(seen.numel())}
     # MLP kernels alone (the a12 roofline inputs)
     w16 = neural.w.detach().to(torch.bfloat16)
     b = neural.b.detach()
@@ -1124,12 +1251,20 @@ def time_learned(rt, ctx, args, train_steps=100):
     dz = torch.empty((sc.n_tris, 384), device=dev)
     ms_bwd = timed(lambda: rt.mlp_backward(ctx, scene_tri, w16, act, eps, sig, g1, g1, gw, gb, dz), 20)
     flops_fwd = 2.0 * sc.n_tris * (40 * 128 + 2 * 128 * 128 + 128 * 2)
-    return {"workload": "room_corridor", "n_tris": sc.n_tris, "train_rx": 1280, "heldout_rx": 256,
-            "adam_steps": train_steps, "neural_step_ms": ms_neural, "plain_step_ms": ms_plain,
-            "heldout_loss_neural": held_neural, "heldout_loss_plain": held_plain,
-            "mlp_fwd_ms": ms_fwd, "mlp_bwd_ms": ms_bwd,
-            "mlp_fwd_tflops": flops_fwd / (ms_fwd * 1e-3) / 1e12,
-            "mlp_bwd_tflops": 2 * flops_fwd / (ms_bwd * 1e-3) / 1e12}
+    res = {"workload": "room_corridor", "n_tris": sc.n_tris, "train_rx": n_tr, "heldout_rx": sc.n_rx - n_tr,
+           "n_sub": N, "n_rays": sc.n_rays, "train_paths": tri_tr.n_paths, "heldout_paths": tri_te.n_paths,
+           "trace_train_s": trace_s, "adam_steps": train_steps,
+           "step": "full batch over the training receivers (one Adam step = one epoch)",
+           "warmup_steps_each": warm_steps, "timed_steps_each": timed_steps,
+           "neural_step_ms": ms_neural, "plain_step_ms": ms_plain,
+           "heldout_loss_neural": held_neural, "heldout_loss_plain": held_plain,
+           "per_triangle_error": errors,
+           "mlp_fwd_ms": ms_fwd, "mlp_bwd_ms": ms_bwd,
+           "mlp_fwd_tflops": flops_fwd / (ms_fwd * 1e-3) / 1e12,
+           "mlp_bwd_tflops": 2 * flops_fwd / (ms_bwd * 1e-3) / 1e12}
+    del tri_tr, tri_te, obj_tr, obj_te, Ttr, Tte
+    torch.cuda.empty_cache()
+    return res
 
 
 def code_sha256(path):
@@ -1182,21 +1317,28 @@ def ncu_traffic(kernel):
     return d["dram_bytes_per_launch"] * d.get("scale_to_bench", 1.0)
 
 
+def fp32_peak(peaks):
+    """FP32 SIMT peak: the measured SGEMM rate when present, else unit counts x clock."""
+    if peaks.get("fp32_tflops"):
+        return peaks["fp32_tflops"], "measured: cuBLAS float32 matmul with TF32 off (SIMT FMA), 8192^3"
+    return FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+
+
 def roofline_for(name, ms, counters, cal, n_paths, sc, N, peaks, peak_src):
     hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+    fp32, fp32_src = fp32_peak(peaks)
     if name == "sbr":
         flops = FLOPS_PER_NODE_VISIT * counters[0] + FLOPS_PER_TRI_TEST * counters[1]
         ach = flops / (ms * 1e-3) / 1e12
-        return {"kernel": "k_sbr", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": ncu_traffic("k_sbr"),
-                "kernel_ms": ms, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+        return {"kernel": "k_sbr", "bound": "alu", "achieved": ach, "peak": fp32,
+                "unit": "TFLOP/s", "frac": ach / fp32, "traffic": ncu_traffic("k_sbr"),
+                "kernel_ms": ms, "peak_source": fp32_src, "frac_of_derived": ach / FP32_PEAK_TFLOPS,
                 "algorithmic": f"{FLOPS_PER_NODE_VISIT} flops/node visit + {FLOPS_PER_TRI_TEST} flops/triangle test"}
     if name == "visibility":
         flops = FLOPS_PER_NODE_VISIT * counters[4] + FLOPS_PER_TRI_TEST * counters[5]
         ach = flops / (ms * 1e-3) / 1e12
-        return {"kernel": "k_visibility", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+        return {"kernel": "k_visibility", "bound": "alu", "achieved": ach, "peak": fp32,
+                "unit": "TFLOP/s", "frac": ach / fp32, "traffic": None, "peak_source": fp32_src}
     if name in ("fields_fwd", "fields_bwd"):
         # bytes per path of depth q: 4 (depth) + 4 (L) + 4q (tri) + 4q (cos) + 16(q+1) (D) + 8 (a)
         q = 2.0
@@ -1205,21 +1347,26 @@ def roofline_for(name, ms, counters, cal, n_paths, sc, N, peaks, peak_src):
         return {"kernel": "k_" + name, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                 "frac": gbs / hbm, "traffic": None, "peak_source": peak_src}
     # stage without a dedicated counter model: report time only against HBM with its bytes unknown
-    return {"kernel": name, "bound": "alu", "achieved": None, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+    return {"kernel": name, "bound": "alu", "achieved": None, "peak": fp32, "unit": "TFLOP/s",
             "frac": None, "traffic": None, "ms": ms}
 
 
 def roofline_cfr(ms, n_paths, N):
     """Fused CFR + loss + adjoint on the tensor cores: 16 N P algorithmic FP32
     flops (8 per complex multiply-add, forward and adjoint), executed as three
-    TF32 products each (hi.hi + hi.lo + lo.hi); peak = the measured BF16 dense
-    peak x the nominal TF32 / BF16 ratio (1.1 / 2.25)."""
+    TF32 products each (hi.hi + hi.lo + lo.hi); peak = the TF32 dense rate measured
+    with cuBLAS in this process (else the measured BF16 peak x the nominal TF32 /
+    BF16 ratio 1.1 / 2.25)."""
     peaks, src = load_peaks()
-    tf32 = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]) * (1.1 / 2.25)
+    if _MEASURED.get("tf32_tflops"):
+        tf32, psrc = _MEASURED["tf32_tflops"], "measured: cuBLAS float32 matmul with TF32 allowed, 8192^3"
+    else:
+        tf32 = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]) * (1.1 / 2.25)
+        psrc = f"{src} bf16 x 1.1/2.25 (TF32)"
     ach = 3 * 16.0 * N * n_paths / (ms * 1e-3) / 1e12
     return {"kernel": "k_cfr_tc<8,3>", "bound": "tensor", "achieved": ach, "peak": tf32, "unit": "TFLOP/s",
             "frac": ach / tf32, "traffic": ncu_traffic("k_cfr_tc"), "kernel_ms": ms,
-            "peak_source": f"{src} bf16 x 1.1/2.25 (TF32)",
+            "peak_source": psrc,
             "algorithmic": "3 x 16 N P TF32 flops (3xTF32 split of 8 N P complex MAC flops, forward and adjoint)"}
 
 

@@ -270,6 +270,17 @@ rt_status rt_cfr_power_mse_fused(rt_ctx* ctx, const int64_t* rx_offsets_dev, int
  * compute the same quantities to FP32 accuracy.  A bounded device wait that runs
  * out sets RT_ERR_TIMEOUT in the status word. */
 rt_status rt_set_cfr_tensor_cores(rt_ctx* ctx, int32_t enable);
+/* Poll limit of the waits in which one CTA of the CFR calls waits for work of
+ * another (the receivers of more than 4096 paths, split over CTAs: waits for
+ * their classification, publication and finished forward sums).  polls = 0
+ * restores the default, 2^22 polls; 1 <= polls <= 2^22 sets it.  A wait that
+ * runs out sets RT_ERR_TIMEOUT in the status word, the kernel finishes without
+ * the work it waited for (outputs of that call are then undefined) and later
+ * calls are unaffected.  The waits of a CTA on its own tensor-core products keep
+ * their fixed bound.  The paper has no counterpart: this exists so that the
+ * time-out path can be exercised with a short limit.  polls outside [0, 2^22]
+ * returns RT_ERR_INVALID_ARG. */
+rt_status rt_set_wait_limit(rt_ctx* ctx, int32_t polls);
 
 /* ------------------------------------------------------------------ antenna patterns */
 
@@ -447,18 +458,27 @@ rt_status rt_mlp_backward(rt_ctx* ctx, const rt_scene* scene, const uint16_t* we
                           const float* grad_eps_r_dev, const float* grad_sigma_dev, float* dz_work_dev,
                           float* grad_weights_dev, float* grad_bias_dev);
 
-/* Same computation, inputs, outputs and errors as rt_cfr_power_mse_fused, for
- * callers that cannot allocate device memory during the call (for example a
- * loop that reserved its whole memory budget in advance, or a host program whose
- * own memory manager forbids other code from calling the CUDA allocator).  The
- * paper has no counterpart: this is a property of the library, not of the method.
+/* The loss, its gradient and H of rt_cfr_power_mse_fused (same inputs, outputs
+ * and errors), for callers that cannot allocate device memory during the call
+ * (for example a loop that reserved its whole memory budget in advance, or a host
+ * program whose own memory manager forbids other code from calling the CUDA
+ * allocator).  The paper has no counterpart: this is a property of the library,
+ * not of the method.
+ *   - A receiver of more than 4096 paths is summed exactly, by one CTA, where
+ *     rt_cfr_power_mse_fused splits it over CTAs and uses the non-uniform FFT of
+ *     its approximation (at most ~4e-7 of sum |a_i| per entry of H).  Results for
+ *     such receivers therefore differ from the regular call within that error,
+ *     and they take longer (the whole P x N sum on one CTA).  Other receivers get
+ *     the same arithmetic as the regular call.
  *   - Allocates nothing: its working memory is one fixed array inside the
  *     library (512 KiB + 256 B) that every GPU loading the library keeps until
  *     the process exits.
  *   - n_rx must be <= 65536; larger values return RT_ERR_INVALID_ARG with a
  *     message, nothing launched.
  *   - The first call on a device looks up that array's device address; make the
- *     first call on each device before any stream capture.
+ *     first call on each device before any stream capture (a first call inside a
+ *     capture returns RT_ERR_INVALID_ARG).  Later calls outside a capture look
+ *     it up again.
  *   - All calls share the array: sequential calls are independent (the call
  *     resets what must start at zero), but calls that overlap on the GPU, e.g. on
  *     two streams at once, race on it. */

@@ -44,6 +44,7 @@ SIGNATURES = {
     "rt_paths_batch_info": (I32, [P, ctypes.POINTER(I32), P, P]),
     "rt_set_tuning": (I32, [P, I32, I32, I32]),
     "rt_set_cfr_tensor_cores": (I32, [P, I32]),
+    "rt_set_wait_limit": (I32, [P, I32]),
     "rt_trace_diffuse": (I32, [P, P, P, P, I32, I64, I32, PP]),
     "rt_eval_fields_diffuse": (I32, [P, P, P, P, P, F64, F32, F32, P, P]),
     "rt_eval_fields_diffuse_backward": (I32, [P, P, P, P, P, F64, F32, F32, P, P, P, P]),

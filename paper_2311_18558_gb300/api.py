@@ -562,6 +562,11 @@ def set_cfr_tensor_cores(ctx: Context, enable: bool):
     ctx.check(ctx.lib.rt_set_cfr_tensor_cores(ctx.h, int(bool(enable))), "rt_set_cfr_tensor_cores")
 
 
+def set_wait_limit(ctx: Context, polls: int):
+    """Poll limit of the CFR kernels' waits on other CTAs; 0 restores the default (rt_set_wait_limit)."""
+    ctx.check(ctx.lib.rt_set_wait_limit(ctx.h, int(polls)), "rt_set_wait_limit")
+
+
 def set_tuning(ctx: Context, sbr: int, pairs: int, vis: int):
     ctx.check(ctx.lib.rt_set_tuning(ctx.h, int(sbr), int(pairs), int(vis)), "rt_set_tuning")
 

@@ -545,6 +545,7 @@ struct TcSplit {
     unsigned int* ready = nullptr;     // TC_HEAVY_CAP: dL/dH of the receiver is in acc
     float2* acc = nullptr;             // TC_HEAVY_CAP x 2N: oversampled grid of each heavy receiver
     const float* dec = nullptr;        // N: 1 / (M phi_hat(n)) per column (see below)
+    int wait_limit = 1 << 22;          // polls of a wait on another CTA (rt_set_wait_limit)
 };
 
 // Heavy receivers use a non-uniform FFT instead of the dense product (the
@@ -638,9 +639,9 @@ __device__ void fft_smem(float2* x, int M, int logM, float sign) {
     }
 }
 
-// Bounded wait of one thread until *flag reaches `want`; false on time-out.
-__device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int want) {
-    for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
+// Bounded wait of one thread until *flag reaches `want`; false after `limit` polls.
+__device__ __forceinline__ bool wait_flag(const unsigned int* flag, unsigned int want, int limit) {
+    for (int it = 0; it < limit; ++it) {
         if (*(volatile const unsigned int*)flag >= want) return true;
         __nanosleep(64);
     }
@@ -748,7 +749,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                 // heavy receivers: claim a forward segment; once the heavy list is final
                 // and every forward segment claimed, an adjoint segment
                 rr = R;
-                for (int it = 0; it < TC_WAIT_LIMIT && rr == R && phase <= LAST_PHASE; ++it) {
+                for (int it = 0; it < sp.wait_limit && rr == R && phase <= LAST_PHASE; ++it) {
                     unsigned int* cur = sp.cnt + phase;
                     unsigned int* next = phase == 1 ? sp.seg_next : sp.adj_next;
                     const int h = (int)*(volatile unsigned int*)cur;
@@ -947,7 +948,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                 continue;
             }
             // kind 2: dL/da of the segment's paths once the adjoint grid is ready
-            if (tid == 0) s_last = wait_flag(sp.ready + slot, 1u);
+            if (tid == 0) s_last = wait_flag(sp.ready + slot, 1u, sp.wait_limit);
             __syncthreads();
             if (!s_last) {
                 ok = false;
@@ -1392,6 +1393,7 @@ static rt_status split_setup(rt_ctx* ctx, int n_sub, TcSplit* sp) {
     sp->pub = sp->ready + TC_HEAVY_CAP;
     sp->acc = static_cast<float2*>(acc);
     sp->dec = dec;
+    sp->wait_limit = ctx->wait_limit > 0 ? ctx->wait_limit : TC_WAIT_LIMIT;
     return RT_OK;
 }
 
@@ -1512,14 +1514,23 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[RT_NOALLOC_MAX_
 
 // Device address of g_noalloc_scratch per device.  In host code the array's
 // name only stands in for the symbol; its address on a device comes from
-// cudaGetSymbolAddress, asked once per device with that device current.
+// cudaGetSymbolAddress, asked with that device current.  It is asked again on
+// every call made outside a stream capture, so an address cached before a device
+// reset (after which the array may live elsewhere) is never used; inside a
+// capture the address of the last call outside one is used, and a first call
+// inside a capture is refused.
 static void* g_noalloc_addr[64];
 static std::mutex g_noalloc_mu;
 
 static rt_status noalloc_scratch_address(rt_ctx* ctx, unsigned char** base) {
     if (ctx->device < 0 || ctx->device >= 64) return rt_fail(ctx, RT_ERR_UNSUPPORTED, "device index >= 64");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    RT_CK(ctx, cudaStreamIsCapturing(ctx->stream, &cap));
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[ctx->device]) {
+    if (cap != cudaStreamCaptureStatusNone && !g_noalloc_addr[ctx->device])
+        return rt_fail(ctx, RT_ERR_INVALID_ARG,
+                       "the first allocation-free call on a device must come before any stream capture");
+    if (cap == cudaStreamCaptureStatusNone) {
         int cur = -1;
         RT_CK(ctx, cudaGetDevice(&cur));
         if (cur != ctx->device) RT_CK(ctx, cudaSetDevice(ctx->device));
@@ -1566,6 +1577,14 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_cfr_power_mse_fus
         RT_CK_LAUNCH(ctx);
         return RT_OK;
     });
+}
+
+extern "C" __attribute__((visibility("default"))) rt_status rt_set_wait_limit(rt_ctx* ctx, int32_t polls) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (polls < 0 || polls > TC_WAIT_LIMIT)
+        return rt_fail(ctx, RT_ERR_INVALID_ARG, "polls = %d outside [0, %d]", polls, TC_WAIT_LIMIT);
+    ctx->wait_limit = polls;
+    return RT_OK;
 }
 
 extern "C" __attribute__((visibility("default"))) rt_status rt_set_cfr_tensor_cores(rt_ctx* ctx, int32_t enable) {

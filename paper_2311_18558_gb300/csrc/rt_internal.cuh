@@ -47,6 +47,7 @@ struct rt_ctx {
     int tune_pairs_blocks_per_sm = 16;
     int tune_vis_blocks_per_sm = 8;
     int cfr_tensor_cores = 1;   // CFR on tcgen05 (3xTF32) where n_sub allows, else SIMT
+    int32_t wait_limit = 0;     // polls of the CFR waits on other CTAs (0: the default 2^22)
 };
 
 // Count one kernel launch of `ctx` (every launch site calls this).

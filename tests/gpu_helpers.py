@@ -55,3 +55,15 @@ def normwise_rows(x, ref):
     num = np.linalg.norm(np.asarray(x) - np.asarray(ref), axis=-1)
     den = np.linalg.norm(np.asarray(ref), axis=-1)
     return num, den
+
+
+def assert_grad_close(got, ref, rtol=1e-4, floor=1e-3, what=""):
+    """Gradient parity: normwise within rtol, and every entry whose magnitude exceeds
+    floor * max|ref| within rtol relative on its own, so that a small entry (a material
+    with few paths) cannot be wrong under the cover of a large one."""
+    got = np.asarray(got, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    assert np.linalg.norm(got - ref) <= rtol * np.linalg.norm(ref), (what, got, ref)
+    big = np.abs(ref) > floor * np.abs(ref).max()
+    rel = np.abs(got[big] - ref[big]) / np.abs(ref[big])
+    assert rel.size == 0 or rel.max() <= rtol, (what, np.flatnonzero(big)[np.argmax(rel)], rel.max(), got, ref)

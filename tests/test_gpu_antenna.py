@@ -9,7 +9,7 @@ import torch
 
 import oracle
 import scenegen
-from gpu_helpers import assert_same_paths, gpu_trace, oracle_trace
+from gpu_helpers import assert_grad_close, assert_same_paths, gpu_trace, oracle_trace
 from oracle import antenna as oa
 
 pytestmark = pytest.mark.gpu
@@ -101,8 +101,7 @@ def test_backward_matches_oracle(rt, ctx, indoor):
         dw, dlam, dmu = oa.gain_grad(dirs, w, lam, mu, eta, d)
         deta = float((d * oa.gain(dirs, w, lam, mu, eta)).sum() / eta)
         ref = np.concatenate([[deta], np.concatenate([dw[:, None], dlam[:, None], dmu], 1).reshape(-1)])
-        got = got.cpu().numpy()
-        assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref), (got, ref)
+        assert_grad_close(got.cpu().numpy(), ref)
 
 
 def test_pattern_recovery(rt, ctx, indoor):

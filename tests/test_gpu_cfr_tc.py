@@ -152,6 +152,45 @@ def test_fused_split_receivers(rt, ctx, n_sub):
     assert ctx.status_word() == 0
 
 
+RT_ERR_TIMEOUT = 7
+
+
+def test_wait_timeout_sets_status(rt, ctx):
+    # With a limit of one poll, a CTA that has to move from the forward segments of
+    # the split receivers to their adjoint segments (which takes one poll of its
+    # own) runs out: every call of this shape sets RT_ERR_TIMEOUT.  The kernel must
+    # return, the status word must say so, and the next call with the default limit
+    # must be correct (nothing left behind by the cut-short call).
+    counts = np.array([5000, 3, 9000, 0, 60], np.int64)
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    rng = np.random.default_rng(21)
+    P = int(offs[-1])
+    a = (10.0 ** rng.uniform(-5, -2, P) * np.exp(1j * rng.uniform(0, 2 * np.pi, P))).astype(np.complex64)
+    tau = rng.uniform(1e-9, 1.5e-6, P)
+    n_sub = 256
+    fc, df = 1.272e9, 50e6 / n_sub
+    Href = oracle.cfr(a.astype(np.complex128), tau, offs, fc, df, n_sub)
+    T = (np.abs(Href) ** 2 * rng.uniform(0.5, 1.5, Href.shape)).astype(np.float32)
+    w = oracle.power_weights(T).astype(np.float32)
+    L_ref, _ = oracle.power_mse(Href, T, w)
+    args = (_dev(offs, torch.int64), _dev(a, torch.complex64), _dev(tau, torch.float64), fc, df, n_sub,
+            _dev(T, torch.float32), _dev(w, torch.float32))
+    assert ctx.status_word() == 0
+    with pytest.raises(Exception):
+        rt.set_wait_limit(ctx, -1)
+    rt.set_wait_limit(ctx, 1)
+    try:
+        rt.cfr_power_mse_fused(ctx, *args)
+        torch.cuda.synchronize()
+        assert ctx.status_word() == RT_ERR_TIMEOUT
+    finally:
+        rt.set_wait_limit(ctx, 0)
+    for _ in range(2):
+        loss, ga, _ = rt.cfr_power_mse_fused(ctx, *args)
+        assert abs(loss.item() - L_ref) <= 1e-4 * abs(L_ref)
+    assert ctx.status_word() == 0
+
+
 def test_fused_split_beyond_heavy_cap(rt, ctx):
     # 4100 receivers of 4097 paths: the first 4096 are split, the rest stay whole.
     # Receivers on both sides of the cap are checked against the FP64 oracle one

@@ -13,7 +13,7 @@ import torch
 
 import oracle
 import scenegen
-from gpu_helpers import gpu_trace, normwise_rows, oracle_trace
+from gpu_helpers import assert_grad_close, gpu_trace, normwise_rows, oracle_trace
 from oracle import cir as oc
 
 pytestmark = pytest.mark.gpu
@@ -151,8 +151,8 @@ def test_paper_loss_gradient_end_to_end(rt, ctx):
     got_s = params.w_sigma.grad.cpu().numpy()
     g_weps = ge * (eps0 - 1.0)
     g_wsig = gs * sig0
-    assert np.linalg.norm(got_e - g_weps) <= 1e-4 * np.linalg.norm(g_weps)
-    assert np.linalg.norm(got_s - g_wsig) <= 1e-4 * np.linalg.norm(g_wsig)
+    assert_grad_close(got_e, g_weps, what="eps_r")
+    assert_grad_close(got_s, g_wsig, what="sigma")
 
 
 @pytest.mark.parametrize("param", ["log", "embeddings"])

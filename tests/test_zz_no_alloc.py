@@ -5,7 +5,10 @@ memory while they run the loss (for example a loop that reserved its memory
 budget in advance, or a host program whose memory manager forbids other code
 from calling the CUDA allocator).  It keeps its working memory in a fixed array
 inside the library.  Both entry points are called through the C ABI on the same
-inputs; two calls in a row must both agree with the regular entry point.
+inputs; two calls in a row must both agree with the regular entry point, on the
+tensor cores and on the SIMT units.  A receiver of more than 4096 paths is summed
+exactly by the allocation-free call (the regular call uses its non-uniform FFT
+approximation there), so that case is also checked against the FP64 oracle.
 """
 import ctypes
 
@@ -13,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import scenegen
 
 pytestmark = pytest.mark.gpu
@@ -38,11 +42,13 @@ def _call(lib, fn, ctx, offs, a, tau, fc, df, N, T, w):
     return loss.cpu().numpy()[0], ga.cpu().numpy(), H.cpu().numpy()
 
 
+@pytest.mark.parametrize("tensor_cores", [1, 0])
 @pytest.mark.parametrize("N", [256, 1024])
-def test_noalloc_matches_regular_entry_point(N):
+def test_noalloc_matches_regular_entry_point(N, tensor_cores):
     import paper_2311_18558_gb300 as rt
     ctx = rt.Context(0)
     lib = ctx.lib
+    rt.set_cfr_tensor_cores(ctx, tensor_cores)
     a, tau, offs = scenegen.random_cfr_inputs(77 + N, 96, 60, empty_every=11)
     fc, df = 1.272e9, 50e6 / N
     rng = np.random.default_rng(N)
@@ -57,6 +63,45 @@ def test_noalloc_matches_regular_entry_point(N):
         assert abs(L - L_ref) <= 1e-4 * abs(L_ref)
         assert np.linalg.norm(ga - ga_ref) <= 1e-4 * np.linalg.norm(ga_ref)
         assert np.linalg.norm(H - H_ref) <= 1e-4 * np.linalg.norm(H_ref)
+    assert ctx.status_word() == 0
+
+
+def test_noalloc_heavy_receiver():
+    # 5000 paths on one receiver: exact sum here, non-uniform FFT in the regular call.
+    # H and the loss are compared with the regular call and H with the oracle.  dL/da
+    # = adjoint(4 w^2 (|H|^2 - P*) H / (R N)) magnifies any difference in H where |H|^2
+    # is close to P*, so it is checked, per receiver, against the oracle's adjoint of
+    # the loss derivative at the H this call returned (as the other fused-loss tests do).
+    import paper_2311_18558_gb300 as rt
+    ctx = rt.Context(0)
+    lib = ctx.lib
+    N = 256
+    counts = np.array([5000, 3, 0, 40], np.int64)
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    rng = np.random.default_rng(5)
+    P = int(offs[-1])
+    a = (10.0 ** rng.uniform(-5, -2, P) * np.exp(1j * rng.uniform(0, 2 * np.pi, P))).astype(np.complex64)
+    tau = rng.uniform(1e-9, 1.5e-6, P)
+    fc, df = 1.272e9, 50e6 / N
+    Href = oracle.cfr(a.astype(np.complex128), tau, offs, fc, df, N)
+    T = (np.abs(Href) ** 2 * rng.uniform(0.5, 1.5, Href.shape)).astype(np.float32)
+    w = oracle.power_weights(T).astype(np.float32)
+    args = (_dev(offs, torch.int64), _dev(a, torch.complex64), _dev(tau, torch.float64), fc, df, N,
+            _dev(T, torch.float32), _dev(w, torch.float32))
+    L_reg, ga_reg, H_reg = _call(lib, "rt_cfr_power_mse_fused", ctx, *args)
+    for _ in range(2):
+        L, ga, H = _call(lib, "rt_cfr_power_mse_fused_noalloc", ctx, *args)
+        assert abs(L - L_reg) <= 1e-4 * abs(L_reg)
+        _, gH_at = oracle.power_mse(H.astype(np.complex128), T, w)
+        ga_at = oracle.cfr_grad(tau, offs, fc, df, N, gH_at)
+        for r in range(len(counts)):
+            s = slice(offs[r], offs[r + 1])
+            if counts[r]:
+                assert np.linalg.norm(H[r] - H_reg[r]) <= 1e-4 * np.linalg.norm(H_reg[r]), r
+                assert np.linalg.norm(H[r] - Href[r]) <= 1e-4 * np.linalg.norm(Href[r]), r
+                assert np.linalg.norm(ga[s] - ga_at[s]) <= 1e-4 * np.linalg.norm(ga_at[s]), r
+            else:
+                assert np.all(H[r] == 0)
     assert ctx.status_word() == 0
 
 
