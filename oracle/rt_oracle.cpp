@@ -21,10 +21,12 @@
 // over independent rays or receivers.
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <set>
 #include <vector>
 
@@ -974,6 +976,206 @@ void orc_cfr_grad(int64_t P, const double* tau, const int64_t* rx_offsets, int n
             grad_a[2 * i + 1] = acc.imag();
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// First-order diffraction (Sec. II-D, Eq. diffraction; candidates and the point of
+// diffraction, Sec. II-F).  The paper models edges as infinitely long wedges
+// whose two faces may carry different materials, takes candidate edges from the
+// shoot-and-bouncing rays and finds the point of diffraction by Keller's
+// principle of the shortest path.  Readings (the paper is silent on them):
+//  * Wedges.  Triangles share an edge when two of their vertices coincide in
+//    position.  An edge shared by exactly two triangles is a wedge when its exterior
+//    angle n pi (measured outside the solid, between the two faces, from the
+//    triangles' winding normals taken as outward) has 1 < n <= 2; n = 2 is a
+//    screen (two coincident faces back to back).  A flat pair (n = 1), a concave
+//    pair (n < 1), a border edge (one triangle), an edge of three or more triangles
+//    and a pair with inconsistent winding are not wedges.  The geometry is taken
+//    literally (a box standing on a ground plane keeps its base edges).
+//  * Canonical frame of a wedge: face 0 is the lower triangle index, t0 the unit
+//    vector from the edge into face 0, n0 its normal, e = t0 x n0 the edge
+//    direction, so that angles about e grow from face 0 into the exterior; the
+//    edge runs from its start vertex E_s to E_s + l e.
+//  * Candidate wedges: those with a face among the triangles that the launch rays
+//    hit first (the depth-1 candidates of the specular trace).
+//  * Point of diffraction Q: on the edge line, the point minimising |Tx - Q| +
+//    |Q - Rx| (Keller), x_Q = (x_T b + x_R a) / (a + b) along e from E_s, with a, b
+//    the distances of Tx and Rx from the line and x_T, x_R their abscissae.  Valid
+//    when a, b > eps, 0 <= x_Q < l (half-open, so a point shared by collinear edge
+//    pieces belongs to one of them), Tx and Rx lie strictly in the exterior
+//    (0 < phi', phi < n pi), |Q - Tx|, |Rx - Q| > eps, and both segments are free
+//    of triangles other than the two faces for t in (eps, len - eps).
+//  * Incidence face (Luebbers' R_0): the face on the transmitter's side, i.e. the
+//    labels are swapped when the transmitter's angle phi' exceeds n pi / 2.
+struct Wedge {
+    int f0, fn;          // canonical: f0 < fn
+    Vec3 es, e, t0, n0;  // start vertex, edge direction, face-0 frame
+    double len, n;
+};
+
+static bool vless(Vec3 a, Vec3 b) {
+    if (a.x != b.x) return a.x < b.x;
+    if (a.y != b.y) return a.y < b.y;
+    return a.z < b.z;
+}
+
+static std::vector<Wedge> build_wedges(const Scene& s) {
+    std::map<std::array<double, 6>, std::vector<int>> edges;
+    for (int t = 0; t < s.T; ++t) {
+        Vec3 v[3] = {s.a[t], s.b[t], s.c[t]};
+        for (int k = 0; k < 3; ++k) {
+            Vec3 p = v[k], q = v[(k + 1) % 3];
+            if (vless(q, p)) std::swap(p, q);
+            edges[{p.x, p.y, p.z, q.x, q.y, q.z}].push_back(t);
+        }
+    }
+    std::vector<Wedge> out;
+    for (auto& kv : edges) {
+        if (kv.second.size() != 2) continue;
+        int f0 = std::min(kv.second[0], kv.second[1]), f1 = std::max(kv.second[0], kv.second[1]);
+        if (f0 == f1) continue;
+        Vec3 A = v3(kv.first[0], kv.first[1], kv.first[2]), B = v3(kv.first[3], kv.first[4], kv.first[5]);
+        Vec3 er = unit(B - A);
+        auto inward = [&](int t) {   // unit vector from the edge into triangle t, normal to the edge
+            Vec3 v[3] = {s.a[t], s.b[t], s.c[t]};
+            Vec3 c = v[0];
+            for (int k = 0; k < 3; ++k)
+                if (!((v[k].x == A.x && v[k].y == A.y && v[k].z == A.z) || (v[k].x == B.x && v[k].y == B.y && v[k].z == B.z)))
+                    c = v[k];
+            Vec3 w = c - A;
+            return unit(w - dot(w, er) * er);
+        };
+        Vec3 t0 = inward(f0), t1 = inward(f1);
+        Vec3 n0 = s.n[f0], n1 = s.n[f1];
+        Vec3 e = dot(cross(er, t0), n0) >= 0.0 ? er : -1.0 * er;
+        // face n must face the exterior too: its normal is -(e x t1)
+        if (dot(-1.0 * cross(e, t1), n1) <= 0.5) continue;
+        double psi = std::atan2(dot(t1, n0), dot(t1, t0));
+        if (psi < 0.0) psi += 2.0 * kPi;
+        if (psi < 1e-12) psi = 2.0 * kPi;   // coincident faces back to back: a screen
+        double n = psi / kPi;
+        if (!(n > 1.0 + 1e-9)) continue;
+        Wedge w;
+        w.f0 = f0;
+        w.fn = f1;
+        w.e = e;
+        w.t0 = t0;
+        w.n0 = n0;
+        w.len = norm(B - A);
+        w.es = dot(B - A, e) > 0.0 ? A : B;
+        w.n = n;
+        out.push_back(w);
+    }
+    std::sort(out.begin(), out.end(), [](const Wedge& x, const Wedge& y) {
+        return x.f0 != y.f0 ? x.f0 < y.f0 : x.fn < y.fn;
+    });
+    return out;
+}
+
+// angle of direction d about the wedge's edge, from face 0 towards the exterior, in [0, 2 pi)
+static double wedge_angle(const Wedge& w, Vec3 d) {
+    Vec3 p = d - dot(d, w.e) * w.e;
+    double a = std::atan2(dot(p, w.n0), dot(p, w.t0));
+    return a < 0.0 ? a + 2.0 * kPi : a;
+}
+
+struct WedgeTable {
+    std::vector<Wedge> w;
+};
+
+void* orc_wedges(void* h) {
+    WedgeTable* t = new WedgeTable();
+    t->w = build_wedges(*(Scene*)h);
+    return t;
+}
+
+int64_t orc_wedges_count(void* wt) { return (int64_t)((WedgeTable*)wt)->w.size(); }
+
+// per wedge: faces (f0, fn), start vertex, edge direction, t0, n0 (3 each), length, n
+void orc_wedges_get(void* wt, int32_t* faces, double* geo) {
+    const std::vector<Wedge>& W = ((WedgeTable*)wt)->w;
+    for (size_t i = 0; i < W.size(); ++i) {
+        faces[2 * i] = W[i].f0;
+        faces[2 * i + 1] = W[i].fn;
+        double* g = geo + 14 * i;
+        Vec3 v[4] = {W[i].es, W[i].e, W[i].t0, W[i].n0};
+        for (int k = 0; k < 4; ++k) {
+            g[3 * k] = v[k].x;
+            g[3 * k + 1] = v[k].y;
+            g[3 * k + 2] = v[k].z;
+        }
+        g[12] = W[i].len;
+        g[13] = W[i].n;
+    }
+}
+
+void orc_wedges_free(void* wt) { delete (WedgeTable*)wt; }
+
+// Diffraction paths Tx -> Q -> Rx for every (candidate wedge, receiver).  Output
+// (Paths, Dmax = 2, depth 1): seq = (incidence face, other face), pts = Tx, Q, Rx,
+// plus `ray` = the wedge's index in the wedge table; grouped by receiver, by wedge
+// within a receiver.
+void* orc_diffraction_paths(void* h, void* wt, const double* tx, const double* rx, int n_rx, void* cand_h) {
+    const Scene& s = *(Scene*)h;
+    const std::vector<Wedge>& W = ((WedgeTable*)wt)->w;
+    std::vector<int32_t>& cv = *(std::vector<int32_t>*)cand_h;
+    const int D = cv[0];
+    const int64_t K = cv[1];
+    std::vector<char> first(s.T, 0);
+    for (int64_t k = 0; k < K; ++k) {
+        const int32_t* sq = cv.data() + 2 + (size_t)D * k;
+        if (sq[0] >= 0 && (D == 1 || sq[1] < 0)) first[sq[0]] = 1;
+    }
+    std::vector<int> cw;
+    for (size_t i = 0; i < W.size(); ++i)
+        if (first[W[i].f0] || first[W[i].fn]) cw.push_back((int)i);
+    const double eps = 1e-6 * s.diag;
+    const Vec3 T = v3(tx[0], tx[1], tx[2]);
+    std::vector<Paths> per(n_rx);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int r = 0; r < n_rx; ++r) {
+        const Vec3 R = v3(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
+        Paths& pr = per[r];
+        for (int wi : cw) {
+            const Wedge& w = W[wi];
+            double xT = dot(T - w.es, w.e), xR = dot(R - w.es, w.e);
+            double a = norm(T - w.es - xT * w.e), b = norm(R - w.es - xR * w.e);
+            if (!(a > eps && b > eps)) continue;
+            double xQ = (xT * b + xR * a) / (a + b);
+            if (!(xQ >= 0.0 && xQ < w.len)) continue;
+            Vec3 Q = w.es + xQ * w.e;
+            double php = wedge_angle(w, T - Q), ph = wedge_angle(w, R - Q);
+            double lim = w.n * kPi;
+            if (!(php > 0.0 && php < lim && ph > 0.0 && ph < lim)) continue;
+            double sp = norm(Q - T), sd = norm(R - Q);
+            if (!(sp > eps && sd > eps)) continue;
+            if (any_hit(s, T, Q - T, eps / sp, 1.0 - eps / sp, w.f0, w.fn)) continue;
+            if (any_hit(s, Q, R - Q, eps / sd, 1.0 - eps / sd, w.f0, w.fn)) continue;
+            bool swap = php > 0.5 * lim;
+            pr.depth.push_back(1);
+            pr.seq.push_back(swap ? w.fn : w.f0);
+            pr.seq.push_back(swap ? w.f0 : w.fn);
+            for (Vec3 p : {T, Q, R, v3(0, 0, 0)}) {
+                pr.pts.push_back(p.x);
+                pr.pts.push_back(p.y);
+                pr.pts.push_back(p.z);
+            }
+            pr.tau.push_back((sp + sd) / kC0);
+            pr.ray.push_back(wi);
+        }
+    }
+    Paths* all = new Paths();
+    all->Dmax = 2;
+    for (int r = 0; r < n_rx; ++r) {
+        Paths& pr = per[r];
+        for (size_t i = 0; i < pr.depth.size(); ++i) all->rx.push_back(r);
+        all->depth.insert(all->depth.end(), pr.depth.begin(), pr.depth.end());
+        all->seq.insert(all->seq.end(), pr.seq.begin(), pr.seq.end());
+        all->pts.insert(all->pts.end(), pr.pts.begin(), pr.pts.end());
+        all->tau.insert(all->tau.end(), pr.tau.begin(), pr.tau.end());
+        all->ray.insert(all->ray.end(), pr.ray.begin(), pr.ray.end());
+    }
+    return all;
 }
 
 void orc_fresnel(double eps_r, double sigma, double freq, double cos_i, double* out) {
