@@ -382,6 +382,78 @@ rt_status rt_specular_reduction_backward(rt_ctx* ctx, const rt_paths* paths, con
                                          const void* a_out_dev, const void* grad_out_dev, void* grad_a_dev,
                                          float* grad_scat_dev);
 
+/* ------------------------------------------------------------------ diffraction */
+
+/* Wedges of the scene's mesh for first-order diffraction (Sec. II-D Eq.
+ * diffraction: infinitely long wedges whose two faces may have different
+ * materials).  Two triangles sharing two vertex positions form an edge; the edge
+ * is a wedge when its exterior angle n pi, measured outside the solid with the
+ * triangles' winding normals taken as outward, has 1 < n <= 2 (n = 2: two
+ * coincident faces back to back, a screen).  Flat pairs, concave pairs (n < 1),
+ * border edges, edges of three or more triangles and pairs of inconsistent
+ * winding are not wedges.  The table is built on the host at the first call that
+ * needs it (one copy of the triangles to the host) and kept with the scene.
+ *   n_wedges    out: number of wedges
+ *   faces_host  2 x n_wedges int32 (face 0 < face n, ordered by (face 0, face n)), or NULL
+ *   n_host      n_wedges double, n of each wedge, or NULL */
+rt_status rt_scene_wedges(rt_ctx* ctx, const rt_scene* scene, int32_t* n_wedges, int32_t* faces_host,
+                          double* n_host);
+
+/* First-order diffraction paths Tx -> Q -> Rx (Sec. II-D Eq. diffraction;
+ * Sec. II-F: candidate edges identified during shoot-and-bounce, the point of
+ * diffraction by Keller's principle of the shortest path).
+ *   specular  a specular trace (rt_trace_paths) of the same scene and transmitter:
+ *             the wedges with a face among its depth-1 candidates (the triangles
+ *             the launch rays hit first) are the candidate wedges.
+ * For every (candidate wedge, receiver): Q is the point of the edge line that
+ * minimises |Tx - Q| + |Q - Rx| (FP64); the path is valid when Tx and Rx are off
+ * the edge line by more than 1e-6 of the scene diagonal (eps), Q lies on the edge
+ * piece (half-open: 0 <= x < length from its start vertex), Tx and Rx are strictly
+ * in the wedge's exterior, both segments are longer than eps and no triangle other
+ * than the two faces cuts them for t in (eps, len - eps).  Output: a paths object
+ * of the diffraction kind, grouped by receiver and ordered by wedge within a
+ * receiver; rt_paths_export gives depth 1, the two faces as the triangle
+ * sequence (the incidence face, i.e. the face on the transmitter's side, first),
+ * the points Tx, Q, Rx, (0, 0, 0) and tau = (|Q - Tx| + |Rx - Q|) / c.
+ * rt_eval_fields_diffraction, rt_antenna_apply, rt_paths_rx_offsets and
+ * rt_paths_free accept it; rt_eval_fields rejects it.  Synchronises twice (the
+ * candidate and path counts size the outputs). */
+rt_status rt_trace_diffraction(rt_ctx* ctx, const rt_scene* scene, const rt_paths* specular, const double* tx_host,
+                               const double* rx_dev, int32_t n_rx, rt_paths** out);
+
+/* Coefficients of diffraction paths: the uniform theory of diffraction
+ * (Kouyoumjian and Pathak, Proc. IEEE 1974) with Luebbers' face coefficients
+ * (IEEE Trans. AP 1984), the model the paper names for Q, in the edge-fixed frame:
+ *   D_{s,h} = -e^{-j pi/4} / (2 n sqrt(2 pi k) sin beta_0) [T1 + T2 + R_0 T3 + R_n T4],
+ *   T_i = cot(eps_i / 2n) F(2 k L sin^2(eps_i / 2)) for the reduced angles eps_i of
+ *   pi + (phi - phi'), pi - (phi - phi'), pi - (phi + phi'), pi + (phi + phi'),
+ *   F(X) = 2 j sqrt(X) e^{jX} int_{sqrt X}^inf e^{-j t^2} dt,
+ *   R_0, R_n the Fresnel coefficients (Eq. fresnel-1/2; r_perp for D_s, r_par for
+ *   D_h, -1 / +1 for a perfect conductor) of the incidence face at
+ *   cos theta = |sin beta_0 sin phi'| and of the other face at
+ *   |sin beta_0 sin(n pi - phi)|,
+ *   a = lambda / (4 pi) sqrt(g_T g_R) sqrt(s' / (s (s + s'))) / s'
+ *       (D_s b_in b_out + D_h p_in p_out),   L = s s' sin^2 beta_0 / (s + s'),
+ * with phi', phi the angles of Tx and Rx about the edge from the incidence face,
+ * beta_0 the angle between the edge and the incident ray, s' = |Q - Tx|,
+ * s = |Rx - Q|, and b_in, p_in (b_out, p_out) the projections of the transmit
+ * (receive) polarisation theta_hat on the edge-fixed bases (beta', phi') of the
+ * incident and (beta, phi) of the diffracted ray.  Arguments as rt_eval_fields:
+ * per_triangle = 0 indexes eps_r_dev / sigma_dev by material, 1 by triangle
+ * (perfect conductors are flagged per material in both cases).
+ *   a_dev  n_paths complex64 output;  tau_dev  n_paths double (may be NULL) */
+rt_status rt_eval_fields_diffraction(rt_ctx* ctx, const rt_paths* paths, const float* eps_r_dev,
+                                     const float* sigma_dev, int32_t per_triangle, double freq_hz, float gain_tx,
+                                     float gain_rx, void* a_dev, double* tau_dev);
+/* Adjoint of rt_eval_fields_diffraction with the geometry held fixed: given
+ * grad_a (complex64), ACCUMULATES (+=) dL/d eps_r and dL/d sigma of both faces'
+ * materials (dL/dx = Re(conj(g) da/dx), da/dsigma = -j/(eps0 omega) da/deta) and
+ * dL/d(g_T, g_R) into grad_gain_dev (2 floats, may be NULL). */
+rt_status rt_eval_fields_diffraction_backward(rt_ctx* ctx, const rt_paths* paths, const float* eps_r_dev,
+                                              const float* sigma_dev, int32_t per_triangle, double freq_hz,
+                                              float gain_tx, float gain_rx, const void* grad_a_dev,
+                                              float* grad_eps_r_dev, float* grad_sigma_dev, float* grad_gain_dev);
+
 /* Per-receiver concatenation of two path lists (8-byte elements: complex64
  * coefficients or double delays), so that specular and diffuse paths go through
  * one CFR: dst holds receiver r's elements of src1 ([off1[r], off1[r+1])) followed

@@ -232,9 +232,9 @@ def fields(sc, dp, eps_r, sigma, freq=None, gain_tx=1.0, gain_rx=1.0):
     f0, fn = dp["faces"][:, 0], dp["faces"][:, 1]
     m0 = f0 if sc.per_triangle else sc.tri_material[f0]
     mn = fn if sc.per_triangle else sc.tri_material[fn]
+    # perfect conductors are flagged per material id of the triangle, in both modes
     pec = np.asarray(sc.is_pec).astype(bool)
-    pec0 = np.zeros(len(f0), bool) if sc.per_triangle else pec[m0]
-    pecn = np.zeros(len(fn), bool) if sc.per_triangle else pec[mn]
+    pec0, pecn = pec[sc.tri_material[f0]], pec[sc.tri_material[fn]]
     w = 2.0 * math.pi * freq
     eta0 = eps_r[m0] - 1j * sigma[m0] / (EPS0 * w)
     etan = eps_r[mn] - 1j * sigma[mn] / (EPS0 * w)

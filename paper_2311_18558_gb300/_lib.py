@@ -51,6 +51,10 @@ SIGNATURES = {
     "rt_set_diffuse_phases": (I32, [P, P, P]),
     "rt_specular_reduction": (I32, [P, P, P, P, P]),
     "rt_specular_reduction_backward": (I32, [P, P, P, P, P, P, P]),
+    "rt_scene_wedges": (I32, [P, P, ctypes.POINTER(I32), P, P]),
+    "rt_trace_diffraction": (I32, [P, P, P, P, P, I32, PP]),
+    "rt_eval_fields_diffraction": (I32, [P, P, P, P, I32, F64, F32, F32, P, P]),
+    "rt_eval_fields_diffraction_backward": (I32, [P, P, P, P, I32, F64, F32, F32, P, P, P, P]),
     "rt_rx_merge": (I32, [P, I32, P, P, P, P, P, P]),
     "rt_rx_split": (I32, [P, I32, P, P, P, P, P]),
     "rt_antenna_apply": (I32, [P, P, P, I32, P, I32, P, P, P, P]),

@@ -362,6 +362,60 @@ def eval_fields_diffuse_backward(ctx: Context, paths: Paths, eps_r, sigma, scat,
     return grad_eps, grad_sigma, grad_scat
 
 
+def scene_wedges(ctx: Context, scene: Scene):
+    """Wedges of the scene's mesh (rt_scene_wedges): faces (W, 2) int32 and n (W,) float64."""
+    n = _c.c_int32()
+    ctx._stream()
+    ctx.check(ctx.lib.rt_scene_wedges(ctx.h, scene.h, _c.byref(n), None, None), "rt_scene_wedges")
+    faces = np.zeros((max(n.value, 1), 2), np.int32)
+    nn = np.zeros(max(n.value, 1), np.float64)
+    ctx.check(ctx.lib.rt_scene_wedges(ctx.h, scene.h, _c.byref(n), faces.ctypes.data_as(_c.c_void_p),
+                                      nn.ctypes.data_as(_c.c_void_p)), "rt_scene_wedges")
+    return faces[: n.value], nn[: n.value]
+
+
+def trace_diffraction(ctx: Context, scene: Scene, specular: Paths, tx, rx: torch.Tensor) -> Paths:
+    """First-order diffraction paths Tx -> edge -> Rx (rt_trace_diffraction); the candidate
+    wedges come from the first hits of `specular`, a trace of the same scene and Tx."""
+    rx = rx.to(device=torch.device("cuda", ctx.device), dtype=torch.float64).contiguous()
+    txa = (_c.c_double * 3)(*[float(v) for v in tx])
+    h = _c.c_void_p()
+    ctx._stream()
+    ctx.check(ctx.lib.rt_trace_diffraction(ctx.h, scene.h, specular.h, txa, _ptr(rx), rx.shape[0], _c.byref(h)),
+              "rt_trace_diffraction")
+    return Paths(ctx, scene, h, rx.shape[0], 2)
+
+
+def eval_fields_diffraction(ctx: Context, paths: Paths, eps_r, sigma, freq_hz: float, gain_tx: float = 1.0,
+                            gain_rx: float = 1.0, per_triangle: bool = False,
+                            out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Coefficients of diffraction paths (rt_eval_fields_diffraction)."""
+    dev = torch.device("cuda", ctx.device)
+    a = out if out is not None else torch.empty(paths.n_paths, dtype=torch.complex64, device=dev)
+    ctx._stream()
+    ctx.check(ctx.lib.rt_eval_fields_diffraction(ctx.h, paths.h, _ptr(eps_r), _ptr(sigma), int(per_triangle),
+                                                 float(freq_hz), float(gain_tx), float(gain_rx), _ptr(a), None),
+              "rt_eval_fields_diffraction")
+    return a
+
+
+def eval_fields_diffraction_backward(ctx: Context, paths: Paths, eps_r, sigma, freq_hz, grad_a, grad_eps=None,
+                                     grad_sigma=None, grad_gain=None, gain_tx=1.0, gain_rx=1.0,
+                                     per_triangle: bool = False):
+    """Accumulates dL/deps_r, dL/dsigma and dL/d(g_T, g_R) given dL/da
+    (rt_eval_fields_diffraction_backward)."""
+    grad_eps = torch.zeros_like(eps_r, dtype=torch.float32) if grad_eps is None else grad_eps
+    grad_sigma = torch.zeros_like(sigma, dtype=torch.float32) if grad_sigma is None else grad_sigma
+    grad_gain = torch.zeros(2, dtype=torch.float32, device=eps_r.device) if grad_gain is None else grad_gain
+    ctx._stream()
+    ctx.check(ctx.lib.rt_eval_fields_diffraction_backward(ctx.h, paths.h, _ptr(eps_r), _ptr(sigma), int(per_triangle),
+                                                          float(freq_hz), float(gain_tx), float(gain_rx),
+                                                          _ptr(grad_a.contiguous()), _ptr(grad_eps),
+                                                          _ptr(grad_sigma), _ptr(grad_gain)),
+              "rt_eval_fields_diffraction_backward")
+    return grad_eps, grad_sigma, grad_gain
+
+
 def set_diffuse_phases(ctx: Context, paths: Paths, chi=None):
     """Attaches per-path random phases (n_paths x 2 float32, radians) of Eq.
     scattered_field to diffuse paths, or clears them (rt_set_diffuse_phases).  The

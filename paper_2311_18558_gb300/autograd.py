@@ -218,6 +218,28 @@ class EvalFieldsDiffuse(torch.autograd.Function):
         return ge, gs, gc, None, None, None, None, None
 
 
+class EvalFieldsDiffraction(torch.autograd.Function):
+    """a = eval_fields_diffraction(eps_r, sigma) for diffraction paths (Sec. II-D Eq.
+    diffraction), with rt_eval_fields_diffraction_backward as backward."""
+
+    @staticmethod
+    def forward(fctx, eps_r, sigma, ctx, paths, freq_hz, gain_tx=1.0, gain_rx=1.0, per_triangle=False):
+        eps_r, sigma = eps_r.contiguous(), sigma.contiguous()
+        a = api.eval_fields_diffraction(ctx, paths, eps_r, sigma, freq_hz, gain_tx, gain_rx, per_triangle)
+        fctx.save_for_backward(eps_r, sigma)
+        fctx.args = (ctx, paths, freq_hz, gain_tx, gain_rx, per_triangle)
+        return a
+
+    @staticmethod
+    def backward(fctx, grad_a):
+        eps_r, sigma = fctx.saved_tensors
+        ctx, paths, freq_hz, gain_tx, gain_rx, per_triangle = fctx.args
+        ge, gs, _ = api.eval_fields_diffraction_backward(ctx, paths, eps_r, sigma, freq_hz, grad_a.contiguous(),
+                                                         gain_tx=gain_tx, gain_rx=gain_rx,
+                                                         per_triangle=per_triangle)
+        return ge, gs, None, None, None, None, None, None
+
+
 class SpecularReduction(torch.autograd.Function):
     """a prod_b sqrt(1 - S_b^2) for specular paths (Eq. specular_reflection)."""
 

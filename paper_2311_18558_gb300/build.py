@@ -14,7 +14,10 @@ LIB = os.path.join(HERE, "librt103.so")
 INCLUDE = os.path.join(ROOT, "include")
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code without floating-point contraction, so that host-side geometry (the
+# wedge table) rounds alike on x86 and on Arm
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+         "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
 

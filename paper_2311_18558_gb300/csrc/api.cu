@@ -591,7 +591,12 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_free(rt_sce
     cudaFree(sc->d_tri_bary64);
     cudaFree(sc->d_tri_material);
     cudaFree(sc->d_is_pec);
+    cudaFree(sc->d_wedge);
+    cudaFree(sc->d_wedge_faces);
+    cudaFree(sc->d_tri_wedges);
     delete[] sc->h_is_pec;
+    delete[] sc->h_wedge_faces;
+    delete[] sc->h_wedge_n;
     delete sc;
     return RT_OK;
 }
@@ -765,7 +770,9 @@ static rt_status check_fields(rt_ctx* ctx, const rt_paths* p, const float* eps, 
                               double freq, float gtx, float grx) {
     if (!ctx) return RT_ERR_INVALID_ARG;
     if (!p || !eps || !sig) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument");
-    if (p->kind != 0) return rt_fail(ctx, RT_ERR_INVALID_ARG, "diffuse paths: use rt_eval_fields_diffuse");
+    if (p->kind != 0)
+        return rt_fail(ctx, RT_ERR_INVALID_ARG,
+                       "not a specular paths object (diffuse: rt_eval_fields_diffuse, diffraction: rt_eval_fields_diffraction)");
     if (per_tri != 0 && per_tri != 1) return rt_fail(ctx, RT_ERR_INVALID_ARG, "per_triangle must be 0 or 1");
     if (!(freq > 0.0) || !std::isfinite(freq)) return rt_fail(ctx, RT_ERR_INVALID_ARG, "freq_hz must be > 0");
     if (!(gtx > 0.0f) || !(grx > 0.0f) || !std::isfinite(gtx) || !std::isfinite(grx))

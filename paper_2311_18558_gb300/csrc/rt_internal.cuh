@@ -83,6 +83,13 @@ struct rt_scene {
     size_t queue_cap = 1u << 20;       // learned visibility-queue capacity
     uint8_t* h_is_pec = nullptr;       // host copy of the material PEC flags (batch checks)
     bool owns_tables_only = false;     // combined batch scene: no BVH, tables owned here
+    // wedges for diffraction, built at the first rt_trace_diffraction / rt_scene_wedges
+    int32_t n_wedges = -1;             // -1: not built yet
+    double* d_wedge = nullptr;         // 14 doubles per wedge: start vertex, e, t0, n0 (3 each), length, n
+    int2* d_wedge_faces = nullptr;     // per wedge (face 0, face n), face 0 < face n
+    int32_t* d_tri_wedges = nullptr;   // 3 per triangle: wedges with the triangle as a face, -1 none
+    int32_t* h_wedge_faces = nullptr;  // host copy of d_wedge_faces
+    double* h_wedge_n = nullptr;       // host copy of n per wedge
 };
 
 struct rt_paths {
@@ -106,11 +113,14 @@ struct rt_paths {
     int32_t n_scenes = 1;              // batch output: number of traced scenes
     int64_t* h_scene_rx_off = nullptr; // batch output: receiver offset of each scene (n_scenes + 1)
     int64_t* h_scene_tri_off = nullptr;// batch output: triangle-id offset of each scene (n_scenes + 1)
-    int32_t kind = 0;                  // 0: specular chains; 1: diffuse paths (last bounce diffuse)
+    int32_t kind = 0;                  // 0: specular chains; 1: diffuse paths (last bounce diffuse);
+                                       // 2: first-order diffraction paths
     int64_t n_rays = 0;                // diffuse paths: launch rays that sampled the surfaces
     const float2* d_chi = nullptr;     // diffuse paths: caller-owned per-path phases (chi_1, chi_2), or none
     float4* d_scat = nullptr;          // diffuse paths, P: (k_s.n, -k_i.k_s, k_r.k_s, 1/d_last) at the
                                        // diffuse point (n facing the incident wave)
+    float* d_dif = nullptr;            // diffraction paths: DIF_REC x P records (in d_block_rec)
+    int2* d_dif_faces = nullptr;       // diffraction paths: (incidence face, other face) per path
     // single allocations carved into several arrays (freed as a whole), or null
     void* d_block_geo = nullptr;       // d_rx, d_depth, d_tri, d_pts
     void* d_block_rec = nullptr;       // d_tau, d_len, d_mc, d_Dm, d_dir
