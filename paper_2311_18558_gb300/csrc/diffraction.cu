@@ -442,6 +442,7 @@ struct RecArgs {
     const int32_t* prx;
     const int32_t* pk;
     float* rec;          // DIF_REC x P
+    double* eps64;       // 4 x P: the reduced angles eps_1..eps_4 in FP64
     int2* faces;         // P: (incidence face, other face)
     double* tau;
     double* pts;         // P x 4 x 3: Tx, Q, Rx, 0
@@ -490,10 +491,12 @@ __global__ void k_dif_records(RecArgs A) {
         rec[8 * P + i] = (float)fabs(sinb * sin(php));
         rec[9 * P + i] = (float)fabs(sinb * sin(lim - phi));
         const double d = phi - php, s = phi + php;
-        rec[10 * P + i] = (float)reduce_angle(DIF_PI + d, w.n);
-        rec[11 * P + i] = (float)reduce_angle(DIF_PI - d, w.n);
-        rec[12 * P + i] = (float)reduce_angle(DIF_PI - s, w.n);
-        rec[13 * P + i] = (float)reduce_angle(DIF_PI + s, w.n);
+        const double ep[4] = {reduce_angle(DIF_PI + d, w.n), reduce_angle(DIF_PI - d, w.n),
+                              reduce_angle(DIF_PI - s, w.n), reduce_angle(DIF_PI + s, w.n)};
+        for (int k = 0; k < 4; ++k) {
+            rec[(10 + k) * P + i] = (float)ep[k];
+            A.eps64[k * P + i] = ep[k];
+        }
         const int fi = swap ? f.y : f.x, fo = swap ? f.x : f.y;
         A.faces[i] = make_int2(fi, fo);
         A.tri[i] = fi;
@@ -572,9 +575,81 @@ __device__ __forceinline__ float2 utd_term(float eps, float n, float kL) {
     return make_float2(F.x * ct, F.y * ct);
 }
 
+// FP64 versions for the paths whose bracket cancels (below): the series up to
+// X = 4 (30 terms), the continued fraction from depth 60 above; both within
+// ~1e-12 of the exact value.
+struct C64 {
+    double x, y;
+};
+__device__ __forceinline__ C64 zmul(C64 a, C64 b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ C64 zadd(C64 a, C64 b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ C64 zdiv(C64 a, C64 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return {(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+__device__ __forceinline__ C64 zsqrt(C64 z) {   // principal root, as csqrt
+    const double r = sqrt(z.x * z.x + z.y * z.y);
+    if (z.x >= 0.0) {
+        const double t = sqrt(0.5 * (r + z.x));
+        return {t, t > 0.0 ? z.y / (2.0 * t) : 0.0};
+    }
+    const double t = sqrt(0.5 * (r - z.x));
+    return {fabs(z.y) / (2.0 * t), copysign(t, z.y)};
+}
+
+__device__ C64 transition_fn64(double X) {
+    const double u = sqrt(X);
+    if (X < 4.0) {
+        double sr = 0.0, si = 0.0, tr = 1.0, ti = 0.0;
+        for (int k = 0; k < 30; ++k) {
+            const double inv = 1.0 / (double)(2 * k + 1);
+            sr += tr * inv;
+            si += ti * inv;
+            const double f = X / (double)(k + 1);
+            const double nr = ti * f, ni = -tr * f;
+            tr = nr;
+            ti = ni;
+        }
+        const double q = 0.62665706865775012560;   // sqrt(pi) / 2 * cos(pi / 4)
+        const double Ir = q - u * sr, Ii = -q - u * si;
+        const double sx = sin(X), cx = cos(X);
+        const double er = cx * Ir - sx * Ii, ei = cx * Ii + sx * Ir;
+        return {-2.0 * u * ei, 2.0 * u * er};
+    }
+    const double zr = u * 0.70710678118654752440, zi = zr;
+    double tr = zr, ti = zi;
+    for (int k = 60; k >= 1; --k) {
+        const double inv = 0.5 * (double)k / (tr * tr + ti * ti);
+        const double nr = zr + tr * inv, ni = zi - ti * inv;
+        tr = nr;
+        ti = ni;
+    }
+    return zdiv(C64{zr, zi}, C64{tr, ti});
+}
+
+__device__ C64 utd_term64(double eps, double n, double kL) {
+    if (fabs(eps) < 1e-12) {
+        const double a = sqrt(2.0 * DIF_PI * kL) * (eps < 0.0 ? -1.0 : 1.0), c = 0.70710678118654752440;
+        return {n * a * c, n * (a * c - 2.0 * kL * eps)};
+    }
+    const double s = sin(0.5 * eps);
+    const C64 F = transition_fn64(2.0 * kL * s * s);
+    const double ct = cos(eps / (2.0 * n)) / sin(eps / (2.0 * n));
+    return {F.x * ct, F.y * ct};
+}
+
+__device__ void fresnel64(C64 eta, double c, C64& rp, C64& rl) {
+    const double s2 = fmax(0.0, 1.0 - c * c);
+    const C64 s = zsqrt(C64{eta.x - s2, eta.y});
+    rp = zdiv(C64{c - s.x, -s.y}, C64{c + s.x, s.y});
+    const C64 ec{c * eta.x, c * eta.y};
+    rl = zdiv(C64{ec.x - s.x, ec.y - s.y}, C64{ec.x + s.x, ec.y + s.y});
+}
+
 struct DifField {
     int64_t P;
     const float* rec;
+    const double* eps64;
     const int2* faces;
     const int32_t* tri_material;
     const uint8_t* is_pec;
@@ -582,6 +657,7 @@ struct DifField {
     const float* sig;
     int per_tri;
     float k, lam, w_eps0;   // wave number, wavelength, eps0 omega
+    double k64, w_eps0_64;
     float gtx, grx;
 };
 
@@ -624,6 +700,36 @@ __device__ __forceinline__ float2 eta_of(const DifField& F, int m) {
     return make_float2(__ldg(F.eps + m), -__ldg(F.sig + m) / F.w_eps0);
 }
 
+// v = b_in b_out [T1 + T2 + R_0s T3 + R_ns T4] + p_in p_out [T1 + T2 + R_0h T3 + R_nh T4].
+// Where the brackets cancel (|v| below 1e-3 of the sum of the magnitudes of its
+// terms: grazing incidence on, or grazing observation along, a face, where the
+// field is nearly cancelled by its reflection), the FP32 terms' rounding would
+// dominate the result, so v is formed again in FP64 from the FP64 reduced angles
+// and FP64 Fresnel coefficients.  Such paths are rare.
+__device__ __forceinline__ float2 dif_bracket(const DifField& F, const DifPath& d, int64_t i, float2 R0s, float2 R0h,
+                                              float2 Rns, float2 Rnh) {
+    const float2 bs = cadd(cadd(d.T12, cmul(R0s, d.T3)), cmul(Rns, d.T4));
+    const float2 bh = cadd(cadd(d.T12, cmul(R0h, d.T3)), cmul(Rnh, d.T4));
+    const float2 v = cadd(cscale(d.bb, bs), cscale(d.pp, bh));
+    const float t3 = hypotf(d.T3.x, d.T3.y), t4 = hypotf(d.T4.x, d.T4.y), t12 = hypotf(d.T12.x, d.T12.y);
+    const float mag = fabsf(d.bb) * (t12 + hypotf(R0s.x, R0s.y) * t3 + hypotf(Rns.x, Rns.y) * t4) +
+                      fabsf(d.pp) * (t12 + hypotf(R0h.x, R0h.y) * t3 + hypotf(Rnh.x, Rnh.y) * t4);
+    if (hypotf(v.x, v.y) >= 1e-3f * mag) return v;
+    const int64_t P = F.P;
+    const double n = __ldg(F.rec + i), kL = F.k64 * (double)__ldg(F.rec + 2 * P + i);
+    C64 T[4];
+    for (int k = 0; k < 4; ++k) T[k] = utd_term64(F.eps64[k * P + i], n, kL);
+    C64 r0s{-1.0, 0.0}, r0h{1.0, 0.0}, rns{-1.0, 0.0}, rnh{1.0, 0.0};
+    if (!d.pec0)
+        fresnel64(C64{(double)__ldg(F.eps + d.m0), -(double)__ldg(F.sig + d.m0) / F.w_eps0_64}, (double)d.c0, r0s, r0h);
+    if (!d.pecn)
+        fresnel64(C64{(double)__ldg(F.eps + d.mn), -(double)__ldg(F.sig + d.mn) / F.w_eps0_64}, (double)d.cn, rns, rnh);
+    const C64 u12 = zadd(T[0], T[1]);
+    const C64 s = zadd(zadd(u12, zmul(r0s, T[2])), zmul(rns, T[3]));
+    const C64 h = zadd(zadd(u12, zmul(r0h, T[2])), zmul(rnh, T[3]));
+    return make_float2((float)(d.bb * s.x + d.pp * h.x), (float)(d.bb * s.y + d.pp * h.y));
+}
+
 __global__ void k_dif_fwd(DifField F, float2* __restrict__ a, double* __restrict__ tau_out,
                           const double* __restrict__ tau) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < F.P; i += (int64_t)gridDim.x * blockDim.x) {
@@ -631,9 +737,7 @@ __global__ void k_dif_fwd(DifField F, float2* __restrict__ a, double* __restrict
         float2 R0s = make_float2(-1.0f, 0.0f), R0h = make_float2(1.0f, 0.0f), Rns = R0s, Rnh = R0h, u0, u1;
         if (!d.pec0) fresnel<false>(eta_of(F, d.m0), d.c0, R0s, R0h, u0, u1);
         if (!d.pecn) fresnel<false>(eta_of(F, d.mn), d.cn, Rns, Rnh, u0, u1);
-        const float2 bs = cadd(cadd(d.T12, cmul(R0s, d.T3)), cmul(Rns, d.T4));
-        const float2 bh = cadd(cadd(d.T12, cmul(R0h, d.T3)), cmul(Rnh, d.T4));
-        const float2 v = cadd(cscale(d.bb, bs), cscale(d.pp, bh));
+        const float2 v = dif_bracket(F, d, i, R0s, R0h, Rns, Rnh);
         a[i] = cscale(d.K, cmul(d.pre, v));
         if (tau_out) tau_out[i] = tau[i];
     }
@@ -660,9 +764,7 @@ __global__ void k_dif_bwd(DifField F, const float2* __restrict__ ga, float* __re
         float2 d0s = make_float2(0.0f, 0.0f), d0h = d0s, dns = d0s, dnh = d0s;
         if (!d.pec0) fresnel<true>(eta_of(F, d.m0), d.c0, R0s, R0h, d0s, d0h);
         if (!d.pecn) fresnel<true>(eta_of(F, d.mn), d.cn, Rns, Rnh, dns, dnh);
-        const float2 bs = cadd(cadd(d.T12, cmul(R0s, d.T3)), cmul(Rns, d.T4));
-        const float2 bh = cadd(cadd(d.T12, cmul(R0h, d.T3)), cmul(Rnh, d.T4));
-        const float2 a = cscale(d.K, cmul(d.pre, cadd(cscale(d.bb, bs), cscale(d.pp, bh))));
+        const float2 a = cscale(d.K, cmul(d.pre, dif_bracket(F, d, i, R0s, R0h, Rns, Rnh)));
         const float ra = g.x * a.x + g.y * a.y;   // Re(conj(g) a)
         gt += ra;
         gr += ra;
@@ -821,12 +923,13 @@ RT_EXPORT rt_status rt_trace_diffraction(rt_ctx* ctx, const rt_scene* scene, con
     {
         RtCarve c;
         const size_t o_tau = c.take(Pa * 8), o_rec = c.take(Pa * DIF_REC * 4), o_f = c.take(Pa * sizeof(int2)),
-                     o_dir = c.take(Pa * 2 * sizeof(float4));
+                     o_dir = c.take(Pa * 2 * sizeof(float4)), o_e64 = c.take(Pa * 4 * 8);
         char* b = nullptr;
         DCK(cudaMallocAsync((void**)&b, c.off, st));
         p->d_block_rec = b;
         p->d_tau = reinterpret_cast<double*>(b + o_tau);
         p->d_dir = reinterpret_cast<float4*>(b + o_dir);
+        p->d_dif64 = reinterpret_cast<double*>(b + o_e64);
         p->d_dif = reinterpret_cast<float*>(b + o_rec);
         p->d_dif_faces = reinterpret_cast<int2*>(b + o_f);
     }
@@ -846,6 +949,7 @@ RT_EXPORT rt_status rt_trace_diffraction(rt_ctx* ctx, const rt_scene* scene, con
         RA.prx = p->d_rx;
         RA.pk = pk;
         RA.rec = p->d_dif;
+        RA.eps64 = p->d_dif64;
         RA.faces = p->d_dif_faces;
         RA.tau = p->d_tau;
         RA.pts = p->d_pts;
@@ -876,6 +980,9 @@ static rt_status dif_field_args(rt_ctx* ctx, const rt_paths* paths, const float*
     if (!(gtx > 0.0f) || !(grx > 0.0f)) return rt_fail(ctx, RT_ERR_INVALID_ARG, "antenna gains must be > 0");
     F.P = paths->P;
     F.rec = paths->d_dif;
+    F.eps64 = paths->d_dif64;
+    F.k64 = 2.0 * RT_PI * freq_hz / RT_C0;
+    F.w_eps0_64 = RT_EPS0 * 2.0 * RT_PI * freq_hz;
     F.faces = paths->d_dif_faces;
     F.tri_material = paths->scene->d_tri_material;
     F.is_pec = paths->scene->d_is_pec;
