@@ -409,6 +409,9 @@ def run_ours(args):
     a = rt.eval_fields(ctx, p, eps, sig, sc.freq_hz)
     cal = time_calibration(rt, ctx, p, eps, sig, target, weight, sc.freq_hz, fc, df, N, flush, args.steps)
 
+    # ---------------- first-order diffraction on the same workload
+    diffraction = time_diffraction(rt, ctx, scene, sc, p, rx_dev, eps, sig, flush, args.steps, peaks, peak_src)
+
     # ---------------- traversal counters (separate, untimed pass)
     ctx.set_profiling(2)
     rt.trace_paths(ctx, scene, sc.tx, rx_dev, sc.n_rays, sc.max_depth)
@@ -470,6 +473,7 @@ def run_ours(args):
             "fields_hbm": fields_hbm,
             "diffuse": diffuse,
             "learned": learned,
+            "diffraction": diffraction,
             "batch": batch,
             "peaks_measured": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in measure_peaks(dev).items()},
             "counters": {"sbr_node_visits": counters[0], "sbr_tri_tests": counters[1], "sbr_queries": counters[2],
@@ -499,16 +503,76 @@ def summary(line):
         "frac": {"k_sbr": g(line, "roofline", "frac"), "k_cfr_tc": g(ci, "roofline_cfr", "frac"),
                  "k_fields_fwd": g(fh, "fields_fwd", "frac"), "k_fields_bwd": g(fh, "fields_bwd", "frac"),
                  "k_df_fwd": g(df_, "roofline_fields_diffuse", "frac"),
-                 "k_df_bwd": g(df_, "roofline_fields_diffuse_bwd", "frac")},
+                 "k_df_bwd": g(df_, "roofline_fields_diffuse_bwd", "frac"),
+                 "k_dif_fwd": g(line.get("diffraction"), "roofline_fields_diffraction", "frac"),
+                 "k_dif_bwd": g(line.get("diffraction"), "roofline_fields_diffraction_bwd", "frac")},
         "learned": {"train_rx": g(lr, "train_rx"), "neural_step_ms": g(lr, "neural_step_ms"),
                     "plain_step_ms": g(lr, "plain_step_ms"), "heldout_loss_neural": g(lr, "heldout_loss_neural"),
                     "heldout_loss_plain": g(lr, "heldout_loss_plain"),
                     "eps_r_err_neural": g(lr, "per_triangle_error", "neural", "seen", "eps_r_mean_rel"),
                     "eps_r_err_plain": g(lr, "per_triangle_error", "plain", "seen", "eps_r_mean_rel")},
+        "diffraction": {"n_paths": g(line.get("diffraction"), "n_paths"),
+                        "trace_ms": g(line.get("diffraction"), "trace_ms"),
+                        "fields_fwd_ms": g(line.get("diffraction"), "fields_fwd_ms"),
+                        "fields_bwd_ms": g(line.get("diffraction"), "fields_bwd_ms")},
         "batch": {"trace_batched_ms": g(bt, "trace_batched_ms"), "trace_loop_ms": g(bt, "trace_loop_ms"),
                   "calibration_graph_ms": g(bt, "calibration_graph_ms"),
                   "calibration_loop_ms": g(bt, "calibration_loop_ms")},
     }
+
+
+# algorithmic bytes per diffraction path: 14 FP32 records + the two faces (int2) +
+# a out (complex64); the adjoint reads dL/da instead of writing a
+DIF_BYTES_FWD = 14 * 4 + 8 + 8
+DIF_BYTES_BWD = 14 * 4 + 8 + 8
+
+
+def time_diffraction(rt, ctx, scene, sc, p_spec, rx_dev, eps, sig, flush, steps, peaks, peak_src):
+    """First-order diffraction on the street canyon (every receiver; candidate
+    wedges from the specular trace's first hits): the trace (wall time on the
+    stream, host read-backs included), and the field kernel and its adjoint with
+    their HBM roofline."""
+    import torch
+    stream = torch.cuda.current_stream()
+    hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+
+    def timed(fn, n):
+        ts = []
+        for _ in range(n):
+            flush.zero_()
+            s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            fn()
+            e0.record(stream)
+            e0.synchronize()
+            ts.append(s0.elapsed_time(e0))
+        return float(np.median(ts))
+
+    for _ in range(3):
+        d = rt.trace_diffraction(ctx, scene, p_spec, sc.tx, rx_dev)
+    t_trace = timed(lambda: rt.trace_diffraction(ctx, scene, p_spec, sc.tx, rx_dev), max(steps, 10))
+    d = rt.trace_diffraction(ctx, scene, p_spec, sc.tx, rx_dev)
+    P = d.n_paths
+    a = rt.eval_fields_diffraction(ctx, d, eps, sig, sc.freq_hz)
+    g = torch.ones_like(a)
+    ge = torch.zeros_like(eps)
+    gs = torch.zeros_like(sig)
+    t_f = timed(lambda: rt.eval_fields_diffraction(ctx, d, eps, sig, sc.freq_hz, out=a), max(steps, 20))
+    t_b = timed(lambda: rt.eval_fields_diffraction_backward(ctx, d, eps, sig, sc.freq_hz, g, ge, gs), max(steps, 20))
+    faces, n = rt.scene_wedges(ctx, scene)
+    gf = DIF_BYTES_FWD * P / (t_f * 1e-3) / 1e9
+    gb = DIF_BYTES_BWD * P / (t_b * 1e-3) / 1e9
+    return {"workload": "street_canyon", "n_rx": sc.n_rx, "n_rays": sc.n_rays, "n_wedges": int(len(n)),
+            "n_paths": P, "trace_ms": t_trace, "paths_per_s": P / (t_trace * 1e-3),
+            "fields_fwd_ms": t_f, "fields_bwd_ms": t_b,
+            "roofline_fields_diffraction": {"kernel": "k_dif_fwd", "bound": "hbm", "achieved": gf, "peak": hbm,
+                                            "unit": "GB/s", "frac": gf / hbm, "traffic": None,
+                                            "peak_source": peak_src,
+                                            "algorithmic": f"{DIF_BYTES_FWD} B/path"},
+            "roofline_fields_diffraction_bwd": {"kernel": "k_dif_bwd", "bound": "hbm", "achieved": gb, "peak": hbm,
+                                                "unit": "GB/s", "frac": gb / hbm, "traffic": None,
+                                                "peak_source": peak_src, "algorithmic": f"{DIF_BYTES_BWD} B/path"},
+            "l2": "flushed: 256 MiB written between timed runs"}
 
 
 def time_calibration(rt, ctx, p, eps, sig, target, weight, freq, fc, df, N, flush, steps):

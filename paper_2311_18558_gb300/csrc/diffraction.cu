@@ -521,7 +521,9 @@ __global__ void k_dif_records(RecArgs A) {
 // z = e^{j pi/4} u, int_u^inf e^{-j t^2} dt = e^{-j pi/4} sqrt(pi)/2 erfc(z), and
 // the Laplace continued fraction erfc(z) = e^{-z^2} / sqrt(pi) / (z + 1/2 / (z +
 // 1 / (z + 3/2 / (z + ...)))) gives F = z / (z + 1/2 / (z + 1 / (z + ...))),
-// evaluated bottom-up from depth 40.  Both stay within ~1e-6 of the exact value.
+// evaluated bottom-up from depth ceil(4 + 90 / X) (its truncation error is below
+// 2e-8 at every X >= 2, measured against a 30-digit evaluation).  Both stay within
+// ~1e-6 of the exact value in FP32.
 __device__ __forceinline__ float2 transition_fn(float X) {
     const float u = sqrtf(X);
     if (X < 2.0f) {
@@ -545,8 +547,8 @@ __device__ __forceinline__ float2 transition_fn(float X) {
     }
     const float zr = u * 0.70710678118654752f, zi = zr;
     float tr = zr, ti = zi;
-#pragma unroll 4
-    for (int k = 40; k >= 1; --k) {
+    const int depth = (int)ceilf(4.0f + 90.0f / X);
+    for (int k = depth; k >= 1; --k) {
         const float h = 0.5f * (float)k;
         const float inv = h / (tr * tr + ti * ti);
         const float nr = zr + tr * inv, ni = zi - ti * inv;   // t = z + h / t
@@ -575,9 +577,9 @@ __device__ __forceinline__ float2 utd_term(float eps, float n, float kL) {
     return make_float2(F.x * ct, F.y * ct);
 }
 
-// FP64 versions for the paths whose bracket cancels (below): the series up to
-// X = 4 (30 terms), the continued fraction from depth 60 above; both within
-// ~1e-12 of the exact value.
+// FP64 versions for the paths whose bracket cancels (below): the series below
+// X = 6 (40 terms), the continued fraction above from depth ceil(5 + 260 / X)
+// (measured against a 30-digit evaluation: within 3e-14 for every X >= 6).
 struct C64 {
     double x, y;
 };
@@ -599,9 +601,9 @@ __device__ __forceinline__ C64 zsqrt(C64 z) {   // principal root, as csqrt
 
 __device__ C64 transition_fn64(double X) {
     const double u = sqrt(X);
-    if (X < 4.0) {
+    if (X < 6.0) {
         double sr = 0.0, si = 0.0, tr = 1.0, ti = 0.0;
-        for (int k = 0; k < 30; ++k) {
+        for (int k = 0; k < 40; ++k) {
             const double inv = 1.0 / (double)(2 * k + 1);
             sr += tr * inv;
             si += ti * inv;
@@ -618,7 +620,8 @@ __device__ C64 transition_fn64(double X) {
     }
     const double zr = u * 0.70710678118654752440, zi = zr;
     double tr = zr, ti = zi;
-    for (int k = 60; k >= 1; --k) {
+    const int depth = (int)ceil(5.0 + 260.0 / X);
+    for (int k = depth; k >= 1; --k) {
         const double inv = 0.5 * (double)k / (tr * tr + ti * ti);
         const double nr = zr + tr * inv, ni = zi - ti * inv;
         tr = nr;
@@ -634,7 +637,9 @@ __device__ C64 utd_term64(double eps, double n, double kL) {
     }
     const double s = sin(0.5 * eps);
     const C64 F = transition_fn64(2.0 * kL * s * s);
-    const double ct = cos(eps / (2.0 * n)) / sin(eps / (2.0 * n));
+    double sn, cs;
+    sincos(eps / (2.0 * n), &sn, &cs);
+    const double ct = cs / sn;
     return {F.x * ct, F.y * ct};
 }
 
@@ -700,21 +705,26 @@ __device__ __forceinline__ float2 eta_of(const DifField& F, int m) {
     return make_float2(__ldg(F.eps + m), -__ldg(F.sig + m) / F.w_eps0);
 }
 
-// v = b_in b_out [T1 + T2 + R_0s T3 + R_ns T4] + p_in p_out [T1 + T2 + R_0h T3 + R_nh T4].
-// Where the brackets cancel (|v| below 1e-3 of the sum of the magnitudes of its
-// terms: grazing incidence on, or grazing observation along, a face, where the
-// field is nearly cancelled by its reflection), the FP32 terms' rounding would
-// dominate the result, so v is formed again in FP64 from the FP64 reduced angles
-// and FP64 Fresnel coefficients.  Such paths are rare.
-__device__ __forceinline__ float2 dif_bracket(const DifField& F, const DifPath& d, int64_t i, float2 R0s, float2 R0h,
-                                              float2 Rns, float2 Rnh) {
+// v = b_in b_out [T1 + T2 + R_0s T3 + R_ns T4] + p_in p_out [T1 + T2 + R_0h T3 + R_nh T4]
+// in FP32; `cancels` is set where |v| is below 1e-3 of the sum of the magnitudes
+// of its terms (grazing incidence on, or grazing observation along, a face, where
+// the field is nearly cancelled by its reflection): there the terms' FP32
+// rounding (~1e-7 of each) would exceed 1e-4 of v, and the forward pass forms v
+// again in FP64 (dif_bracket64).  About 0.5 % of the street canyon's paths.
+__device__ __forceinline__ float2 dif_bracket(const DifPath& d, float2 R0s, float2 R0h, float2 Rns, float2 Rnh,
+                                              bool& cancels) {
     const float2 bs = cadd(cadd(d.T12, cmul(R0s, d.T3)), cmul(Rns, d.T4));
     const float2 bh = cadd(cadd(d.T12, cmul(R0h, d.T3)), cmul(Rnh, d.T4));
     const float2 v = cadd(cscale(d.bb, bs), cscale(d.pp, bh));
     const float t3 = hypotf(d.T3.x, d.T3.y), t4 = hypotf(d.T4.x, d.T4.y), t12 = hypotf(d.T12.x, d.T12.y);
     const float mag = fabsf(d.bb) * (t12 + hypotf(R0s.x, R0s.y) * t3 + hypotf(Rns.x, Rns.y) * t4) +
                       fabsf(d.pp) * (t12 + hypotf(R0h.x, R0h.y) * t3 + hypotf(Rnh.x, Rnh.y) * t4);
-    if (hypotf(v.x, v.y) >= 1e-3f * mag) return v;
+    cancels = hypotf(v.x, v.y) < 1e-3f * mag;
+    return v;
+}
+
+// v of dif_bracket in FP64 from the FP64 reduced angles and FP64 Fresnel coefficients.
+__device__ float2 dif_bracket64(const DifField& F, const DifPath& d, int64_t i) {
     const int64_t P = F.P;
     const double n = __ldg(F.rec + i), kL = F.k64 * (double)__ldg(F.rec + 2 * P + i);
     C64 T[4];
@@ -730,16 +740,43 @@ __device__ __forceinline__ float2 dif_bracket(const DifField& F, const DifPath& 
     return make_float2((float)(d.bb * s.x + d.pp * h.x), (float)(d.bb * s.y + d.pp * h.y));
 }
 
+// Forward in FP32; paths whose bracket cancels are appended to fb (fb[0] the
+// count, reset before the launch, the list from fb + 4) for k_dif_fix.
 __global__ void k_dif_fwd(DifField F, float2* __restrict__ a, double* __restrict__ tau_out,
-                          const double* __restrict__ tau) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < F.P; i += (int64_t)gridDim.x * blockDim.x) {
+                          const double* __restrict__ tau, int32_t* __restrict__ fb) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < F.P; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        bool cancels = false;
+        if (i < F.P) {
+            const DifPath d = dif_path(F, i);
+            float2 R0s = make_float2(-1.0f, 0.0f), R0h = make_float2(1.0f, 0.0f), Rns = R0s, Rnh = R0h, u0, u1;
+            if (!d.pec0) fresnel<false>(eta_of(F, d.m0), d.c0, R0s, R0h, u0, u1);
+            if (!d.pecn) fresnel<false>(eta_of(F, d.mn), d.cn, Rns, Rnh, u0, u1);
+            const float2 v = dif_bracket(d, R0s, R0h, Rns, Rnh, cancels);
+            a[i] = cscale(d.K, cmul(d.pre, v));
+            if (tau_out) tau_out[i] = tau[i];
+        }
+        // warp-aggregated append of the cancelling paths
+        const unsigned m = __ballot_sync(0xffffffffu, cancels);
+        if (m) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(fb, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (cancels) fb[4 + base + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
+        }
+    }
+}
+
+// The listed paths again, with the bracket in FP64.  Item j goes to block
+// j mod gridDim.x first, so that the few listed paths spread over all SMs (the
+// FP64 pipe of one SM is the limit, not the lanes of a warp).
+__global__ void k_dif_fix(DifField F, float2* __restrict__ a, const int32_t* __restrict__ fb) {
+    const int n = *(volatile const int32_t*)fb;
+    for (int j = threadIdx.x * gridDim.x + blockIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int64_t i = fb[4 + j];
         const DifPath d = dif_path(F, i);
-        float2 R0s = make_float2(-1.0f, 0.0f), R0h = make_float2(1.0f, 0.0f), Rns = R0s, Rnh = R0h, u0, u1;
-        if (!d.pec0) fresnel<false>(eta_of(F, d.m0), d.c0, R0s, R0h, u0, u1);
-        if (!d.pecn) fresnel<false>(eta_of(F, d.mn), d.cn, Rns, Rnh, u0, u1);
-        const float2 v = dif_bracket(F, d, i, R0s, R0h, Rns, Rnh);
-        a[i] = cscale(d.K, cmul(d.pre, v));
-        if (tau_out) tau_out[i] = tau[i];
+        a[i] = cscale(d.K, cmul(d.pre, dif_bracket64(F, d, i)));
     }
 }
 
@@ -764,7 +801,10 @@ __global__ void k_dif_bwd(DifField F, const float2* __restrict__ ga, float* __re
         float2 d0s = make_float2(0.0f, 0.0f), d0h = d0s, dns = d0s, dnh = d0s;
         if (!d.pec0) fresnel<true>(eta_of(F, d.m0), d.c0, R0s, R0h, d0s, d0h);
         if (!d.pecn) fresnel<true>(eta_of(F, d.mn), d.cn, Rns, Rnh, dns, dnh);
-        const float2 a = cscale(d.K, cmul(d.pre, dif_bracket(F, d, i, R0s, R0h, Rns, Rnh)));
+        // a enters only the gain gradients, a sum over all paths: the FP32 bracket
+        // suffices (the material terms below are products, free of cancellation)
+        bool cancels;
+        const float2 a = cscale(d.K, cmul(d.pre, dif_bracket(d, R0s, R0h, Rns, Rnh, cancels)));
         const float ra = g.x * a.x + g.y * a.y;   // Re(conj(g) a)
         gt += ra;
         gr += ra;
@@ -923,13 +963,15 @@ RT_EXPORT rt_status rt_trace_diffraction(rt_ctx* ctx, const rt_scene* scene, con
     {
         RtCarve c;
         const size_t o_tau = c.take(Pa * 8), o_rec = c.take(Pa * DIF_REC * 4), o_f = c.take(Pa * sizeof(int2)),
-                     o_dir = c.take(Pa * 2 * sizeof(float4)), o_e64 = c.take(Pa * 4 * 8);
+                     o_dir = c.take(Pa * 2 * sizeof(float4)), o_e64 = c.take(Pa * 4 * 8),
+                     o_fb = c.take((Pa + 4) * 4);
         char* b = nullptr;
         DCK(cudaMallocAsync((void**)&b, c.off, st));
         p->d_block_rec = b;
         p->d_tau = reinterpret_cast<double*>(b + o_tau);
         p->d_dir = reinterpret_cast<float4*>(b + o_dir);
         p->d_dif64 = reinterpret_cast<double*>(b + o_e64);
+        p->d_dif_fb = reinterpret_cast<int32_t*>(b + o_fb);
         p->d_dif = reinterpret_cast<float*>(b + o_rec);
         p->d_dif_faces = reinterpret_cast<int2*>(b + o_f);
     }
@@ -1005,7 +1047,11 @@ RT_EXPORT rt_status rt_eval_fields_diffraction(rt_ctx* ctx, const rt_paths* path
     if (s != RT_OK) return s;
     if (!a_dev && paths->P > 0) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null output");
     if (paths->P == 0) return RT_OK;
-    k_dif_fwd<<<dif_grid(ctx, paths->P, 256, 16), 256, 0, ctx->stream>>>(F, (float2*)a_dev, tau_dev, paths->d_tau);
+    RT_CK(ctx, cudaMemsetAsync(paths->d_dif_fb, 0, 4, ctx->stream));
+    k_dif_fwd<<<dif_grid(ctx, paths->P, 256, 16), 256, 0, ctx->stream>>>(F, (float2*)a_dev, tau_dev, paths->d_tau,
+                                                                         paths->d_dif_fb);
+    RT_COUNT(ctx);
+    k_dif_fix<<<ctx->num_sms, 64, 0, ctx->stream>>>(F, (float2*)a_dev, paths->d_dif_fb);
     RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;

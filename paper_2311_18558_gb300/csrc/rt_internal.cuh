@@ -121,6 +121,7 @@ struct rt_paths {
                                        // diffuse point (n facing the incident wave)
     float* d_dif = nullptr;            // diffraction paths: DIF_REC x P records (in d_block_rec)
     double* d_dif64 = nullptr;         // diffraction paths: 4 x P reduced angles in FP64 (in d_block_rec)
+    int32_t* d_dif_fb = nullptr;       // diffraction paths: count + list of paths re-evaluated in FP64
     int2* d_dif_faces = nullptr;       // diffraction paths: (incidence face, other face) per path
     // single allocations carved into several arrays (freed as a whole), or null
     void* d_block_geo = nullptr;       // d_rx, d_depth, d_tri, d_pts

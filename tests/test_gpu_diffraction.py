@@ -195,3 +195,65 @@ def test_empty_and_rejected(rt, ctx):
     with pytest.raises(rt.RtError):
         rt.eval_fields(ctx, dif2, _dev(sc2.eps_r), _dev(sc2.sigma), sc2.freq_hz)
     assert ctx.status_word() == 0
+
+
+def test_calibration_gradient_with_diffraction(rt, ctx):
+    # specular and diffraction paths of each receiver merged into one CFR, power MSE,
+    # autograd through the library back to eps_r and sigma, against the oracle's
+    # FP64 chain (CFR adjoint, split, specular adjoint + diffraction autograd)
+    sc = scenegen.street_canyon()
+    step, n_rays = 127, 200_000
+    rx = sc.rx[::step]
+    scene, spec, dif, ex = _trace(rt, ctx, sc, n_rays, rx)
+    sco = sc.subset_rx(np.arange(0, sc.n_rx, step))
+    o = oracle.OracleScene(sco)
+    tr = o.trace(n_rays=n_rays)
+    dp = od.paths(o, n_rays=n_rays)
+    fc, df, N, f = sc.f_center_hz, sc.delta_f_hz * 4, 256, sc.freq_hz
+    R = len(rx)
+
+    def merge(x1, o1, x2, o2):
+        out, off = [], [0]
+        for r in range(R):
+            out += [x1[o1[r]:o1[r + 1]], x2[o2[r]:o2[r + 1]]]
+            off.append(off[-1] + (o1[r + 1] - o1[r]) + (o2[r + 1] - o2[r]))
+        return np.concatenate(out), np.array(off, np.int64)
+
+    def oracle_a(eps, sig):
+        a_s = o.fields(tr, eps_r=eps, sigma=sig)
+        a_d = od.fields(sco, dp, eps, sig).detach().numpy()
+        return a_s, a_d
+
+    tau_m, off_m = merge(tr["tau"], tr["rx_offsets"], dp["tau"], dp["rx_offsets"])
+    a_s, a_d = oracle_a(sc.eps_r.astype(np.float64), sc.sigma.astype(np.float64))
+    T = np.abs(oracle.cfr(merge(a_s, tr["rx_offsets"], a_d, dp["rx_offsets"])[0], tau_m, off_m, fc, df, N)) ** 2
+    w = oracle.power_weights(T)
+    eps0 = (sc.eps_r * 1.3).astype(np.float32)
+    sig0 = (sc.sigma * 0.6).astype(np.float32)
+    # oracle chain
+    a_s, a_d = oracle_a(eps0.astype(np.float64), sig0.astype(np.float64))
+    a_m = merge(a_s, tr["rx_offsets"], a_d, dp["rx_offsets"])[0]
+    L_ref, gH = oracle.power_mse(oracle.cfr(a_m, tau_m, off_m, fc, df, N), T, w)
+    ga = oracle.cfr_grad(tau_m, off_m, fc, df, N, gH)
+    ga_s = np.concatenate([ga[off_m[r]:off_m[r] + tr["rx_offsets"][r + 1] - tr["rx_offsets"][r]] for r in range(R)])
+    ga_d = np.concatenate([ga[off_m[r + 1] - (dp["rx_offsets"][r + 1] - dp["rx_offsets"][r]):off_m[r + 1]]
+                           for r in range(R)])
+    ge_s, gs_s, _ = o.fields_grad(tr, ga_s, eps_r=eps0, sigma=sig0)
+    e = torch.tensor(eps0.astype(np.float64), requires_grad=True)
+    s = torch.tensor(sig0.astype(np.float64), requires_grad=True)
+    (torch.as_tensor(ga_d).conj() * od.fields(sco, dp, e, s)).real.sum().backward()
+    ge_ref, gs_ref = ge_s + e.grad.numpy(), gs_s + s.grad.numpy()
+    # library
+    ep = _dev(eps0).requires_grad_(True)
+    sp = _dev(sig0).requires_grad_(True)
+    a1 = rt.EvalFields.apply(ep, sp, ctx, spec, f, 1.0, 1.0, False)
+    a2 = rt.EvalFieldsDiffraction.apply(ep, sp, ctx, dif, f)
+    am = rt.RxMerge.apply(a1, a2, spec.rx_offsets, dif.rx_offsets, ctx)
+    taum, offm = rt.rx_merge(ctx, spec.rx_offsets, dif.rx_offsets, spec.tau, dif.tau)
+    assert np.array_equal(offm.cpu().numpy(), off_m)
+    loss = rt.CfrPowerMSE.apply(am, taum, offm, _dev(T), _dev(w), ctx, fc, df, N)
+    loss.backward()
+    assert abs(loss.item() - L_ref) <= 1e-4 * L_ref
+    assert_grad_close(ep.grad.cpu().numpy(), ge_ref, what="eps_r")
+    assert_grad_close(sp.grad.cpu().numpy(), gs_ref, what="sigma")
+    assert ctx.status_word() == 0
