@@ -262,6 +262,25 @@ rt_status rt_cfr_power_mse_fused(rt_ctx* ctx, const int64_t* rx_offsets_dev, int
                                  double delta_f_hz, int32_t n_sub, const float* target_power_dev,
                                  const float* rx_weight_dev, float* loss_dev, void* grad_a_dev,
                                  void* H_dev);
+/* With enable = 1, rt_trace_paths returns without waiting for the GPU: its
+ * buffers are sized from the counts of the scene's last trace that did wait (the
+ * scene's first trace waits in any case), every stage reads the previous stage's
+ * counts on the device, and the paths object holds as many slots as were sized:
+ * rt_paths_count gives the slots and the receiver offsets give the real layout.
+ * rt_eval_fields, rt_eval_fields_backward, the CFR calls and
+ * rt_paths_device_views / rt_paths_rx_offsets accept such paths;
+ * rt_paths_export, rt_paths_candidates, rt_antenna_apply*, rt_specular_reduction*
+ * and rt_trace_diffraction need rt_paths_resolve first.  A capacity that
+ * overflowed sets RT_ERR_CAPACITY in the status word (the results of that trace
+ * are then invalid; trace again with enable = 0).  With enable = 0 (the default)
+ * rt_trace_paths waits once, at its end, and retries with more room on overflow.
+ * The paper has no counterpart: this is a property of the library. */
+rt_status rt_set_trace_async(rt_ctx* ctx, int32_t enable);
+/* Waits for a trace that returned without waiting and fixes its path count on
+ * the host (rt_paths_count then gives the paths); RT_ERR_CAPACITY if one of its
+ * capacities overflowed.  A no-op on other paths. */
+rt_status rt_paths_resolve(rt_paths* paths);
+
 /* Arithmetic of rt_cfr, rt_cfr_backward and rt_cfr_power_mse_fused (and its
  * allocation-free variant): with enable = 1 (the default) and n_sub in {256, 512,
  * 1024, 2048, 4096} the contraction over the paths runs on the tensor cores

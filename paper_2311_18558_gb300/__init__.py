@@ -9,7 +9,7 @@ from .api import (MLP_NB, MLP_NW, Context, Paths, Scene, antenna_apply, antenna_
                   delay_spread_power_loss, eval_fields, eval_fields_backward, eval_fields_diffraction,
                   eval_fields_diffraction_backward, eval_fields_diffuse, eval_fields_diffuse_backward,
                   import_paths, mlp_backward, mlp_forward, pack_mlp, power_scale_ema, rx_merge, rx_split,
-                  scene_wedges, set_cfr_tensor_cores, set_diffuse_phases, set_tuning, set_wait_limit,
+                  scene_wedges, set_cfr_tensor_cores, set_diffuse_phases, set_trace_async, set_tuning, set_wait_limit,
                   specular_reduction, specular_reduction_backward, trace_batch, trace_diffraction,
                   trace_diffuse, trace_paths)
 from .autograd import (AntennaApply, AntennaPattern, Cfr, CfrPowerMSE, DelaySpreadPowerLoss,  # noqa: F401

@@ -45,6 +45,8 @@ SIGNATURES = {
     "rt_set_tuning": (I32, [P, I32, I32, I32]),
     "rt_set_cfr_tensor_cores": (I32, [P, I32]),
     "rt_set_wait_limit": (I32, [P, I32]),
+    "rt_set_trace_async": (I32, [P, I32]),
+    "rt_paths_resolve": (I32, [P]),
     "rt_trace_diffuse": (I32, [P, P, P, P, I32, I64, I32, PP]),
     "rt_eval_fields_diffuse": (I32, [P, P, P, P, P, F64, F32, F32, P, P]),
     "rt_eval_fields_diffuse_backward": (I32, [P, P, P, P, P, F64, F32, F32, P, P, P, P]),

@@ -171,8 +171,21 @@ class Paths:
         self.rx_offsets = torch.as_tensor(_DeviceView(off.value, self.n_rx + 1, "<i8", self._handle), device=dev)
         self.tau = torch.as_tensor(_DeviceView(tau.value, self.n_paths, "<f8", self._handle), device=dev)
 
+    def resolve(self):
+        """Waits for a trace that returned without waiting (rt_set_trace_async) and
+        fixes n_paths to the paths it found (rt_paths_resolve); a no-op otherwise."""
+        self.ctx._stream()
+        self.ctx.check(self.ctx.lib.rt_paths_resolve(self.h), "rt_paths_resolve")
+        p, k = _c.c_int64(), _c.c_int64()
+        self.ctx.lib.rt_paths_count(self.h, _c.byref(p), _c.byref(k))
+        if int(p.value) != self.n_paths:
+            self.n_paths, self.n_candidates = int(p.value), int(k.value)
+            self.tau = self.tau[: self.n_paths]
+        return self
+
     def export(self):
         """Triangle sequences, depths, receivers, delays and points as device tensors."""
+        self.resolve()
         dev = torch.device("cuda", self.ctx.device)
         P, D = self.n_paths, self.max_depth
         out = dict(seq=torch.empty((P, D), dtype=torch.int32, device=dev),
@@ -614,6 +627,12 @@ def trace_batch(ctx: Context, scenes, txs, rxs, n_rays: int, max_depth: int) -> 
 def set_cfr_tensor_cores(ctx: Context, enable: bool):
     """CFR contraction on the tensor cores (default) or on the SIMT units (rt_set_cfr_tensor_cores)."""
     ctx.check(ctx.lib.rt_set_cfr_tensor_cores(ctx.h, int(bool(enable))), "rt_set_cfr_tensor_cores")
+
+
+def set_trace_async(ctx: Context, enable: bool):
+    """trace_paths returns without waiting for the GPU (rt_set_trace_async); its paths then
+    hold slots until Paths.resolve()."""
+    ctx.check(ctx.lib.rt_set_trace_async(ctx.h, int(bool(enable))), "rt_set_trace_async")
 
 
 def set_wait_limit(ctx: Context, polls: int):

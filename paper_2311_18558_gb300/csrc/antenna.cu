@@ -175,6 +175,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_antenna_apply(
     int32_t rx_lobes, const void* a_dev, void* a_out_dev, float* gain_tx_dev, float* gain_rx_dev) {
     if (!ctx) return RT_ERR_INVALID_ARG;
     if (!paths || !a_dev || !a_out_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument");
+    RT_REQUIRE_RESOLVED(ctx, paths);
     rt_status s = check_pattern(ctx, tx_pattern_dev, tx_lobes);
     if (s != RT_OK) return s;
     s = check_pattern(ctx, rx_pattern_dev, rx_lobes);
@@ -194,6 +195,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_antenna_apply_bac
     const void* grad_out_dev, void* grad_a_dev, float* grad_tx_dev, float* grad_rx_dev) {
     if (!ctx) return RT_ERR_INVALID_ARG;
     if (!paths || !a_out_dev || !grad_out_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument");
+    RT_REQUIRE_RESOLVED(ctx, paths);
     if ((tx_pattern_dev && !gain_tx_dev) || (rx_pattern_dev && !gain_rx_dev))
         return rt_fail(ctx, RT_ERR_INVALID_ARG, "the forward gains of every given pattern are required");
     rt_status s = check_pattern(ctx, tx_pattern_dev, tx_lobes);

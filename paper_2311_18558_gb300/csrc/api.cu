@@ -159,7 +159,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_create(int device
     ctx->num_sms = prop.multiProcessorCount;
     if (cudaMalloc((void**)&ctx->d_status, sizeof(int32_t)) != cudaSuccess ||
         cudaMemset(ctx->d_status, 0, sizeof(int32_t)) != cudaSuccess ||
-        cudaMallocHost((void**)&ctx->h_pinned, 64) != cudaSuccess) {
+        cudaMallocHost((void**)&ctx->h_pinned, 64 * 8) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_trace_words, 64 * 8) != cudaSuccess) {
         delete ctx;
         return RT_ERR_OOM;
     }
@@ -234,6 +235,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_destroy(rt_ctx* c
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->d_trace_words) cudaFree(ctx->d_trace_words);
     loss_scratch_release(ctx);
     delete ctx;
     return RT_OK;
@@ -672,6 +674,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_paths_export(cons
                                      double* points) {
     if (!p) return RT_ERR_INVALID_ARG;
     rt_ctx* ctx = p->scene->ctx;
+    RT_REQUIRE_RESOLVED(ctx, p);
     cudaStream_t st = ctx->stream;
     if (p->P == 0) return RT_OK;
     if (tri_seq)
@@ -698,6 +701,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_paths_device_view
 extern "C" __attribute__((visibility("default"))) rt_status rt_paths_candidates(const rt_paths* p, int32_t* seq) {
     if (!p || !seq) return RT_ERR_INVALID_ARG;
     rt_ctx* ctx = p->scene->ctx;
+    RT_REQUIRE_RESOLVED(ctx, p);
     if (p->K == 0) return RT_OK;
     std::vector<uint64_t> keys(p->K);
     RT_CK(ctx, cudaMemcpyAsync(keys.data(), p->d_cand, p->K * 8, cudaMemcpyDeviceToHost, ctx->stream));

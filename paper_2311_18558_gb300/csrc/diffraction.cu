@@ -869,6 +869,7 @@ RT_EXPORT rt_status rt_trace_diffraction(rt_ctx* ctx, const rt_scene* scene, con
     if (n_rx < 1 || !rx_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "n_rx must be >= 1 with a receiver array");
     if (specular->kind != 0 || specular->scene != scene || !specular->d_cand)
         return rt_fail(ctx, RT_ERR_INVALID_ARG, "specular must be a specular trace of this scene");
+    RT_REQUIRE_RESOLVED(ctx, specular);
     for (int c = 0; c < 3; ++c)
         if (!std::isfinite(tx[c])) return rt_fail(ctx, RT_ERR_INVALID_ARG, "non-finite transmitter");
     rt_status s = ensure_wedges(ctx, scene);

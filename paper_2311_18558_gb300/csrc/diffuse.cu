@@ -1142,6 +1142,7 @@ RT_EXPORT rt_status rt_specular_reduction(rt_ctx* ctx, const rt_paths* paths, co
     if (!ctx) return RT_ERR_INVALID_ARG;
     if (!paths || !scat_dev || !a_dev || !a_out_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument");
     if (paths->kind != 0) return rt_fail(ctx, RT_ERR_INVALID_ARG, "not a specular paths object");
+    RT_REQUIRE_RESOLVED(ctx, paths);
     if (paths->P == 0) return RT_OK;
     k_spec_reduce<<<grid_of(ctx, paths->P, 256, 8), 256, 0, ctx->stream>>>(
         paths->P, paths->d_depth, paths->d_mc, scat_dev, (const float2*)a_dev, (float2*)a_out_dev); RT_COUNT(ctx);
@@ -1156,6 +1157,7 @@ RT_EXPORT rt_status rt_specular_reduction_backward(rt_ctx* ctx, const rt_paths* 
     if (!paths || !scat_dev || !grad_out_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "null argument");
     if (grad_scat_dev && !a_out_dev) return rt_fail(ctx, RT_ERR_INVALID_ARG, "grad_scat_dev needs a_out_dev");
     if (paths->kind != 0) return rt_fail(ctx, RT_ERR_INVALID_ARG, "not a specular paths object");
+    RT_REQUIRE_RESOLVED(ctx, paths);
     if (paths->P == 0) return RT_OK;
     const int n_mat = paths->scene->n_materials;
     const int grid = grid_of(ctx, paths->P, 256, 8);

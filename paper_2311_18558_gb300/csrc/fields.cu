@@ -30,10 +30,14 @@ __device__ __forceinline__ D3 d3(double x, double y, double z) { return D3{x, y,
 __device__ __forceinline__ D3 sub(D3 a, D3 b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ double dotd(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-__global__ void k_records(int64_t P, int D, const double* __restrict__ pts, const int32_t* __restrict__ depth,
-                          const int32_t* __restrict__ tri, const double* __restrict__ tri_n64,
-                          const int32_t* __restrict__ tri_material, const uint8_t* __restrict__ is_pec, double* tau,
-                          float* len, int2* mc, float4* Dm, float4* dir) {
+// P paths (or *P_dev of them, at most P, when P_dev is given: the count of a trace
+// that has not been read back); P is also the slot stride of tri, mc, Dm and dir.
+__global__ void k_records(int64_t P, const int64_t* __restrict__ P_dev, int D, const double* __restrict__ pts,
+                          const int32_t* __restrict__ depth, const int32_t* __restrict__ tri,
+                          const double* __restrict__ tri_n64, const int32_t* __restrict__ tri_material,
+                          const uint8_t* __restrict__ is_pec, double* tau, float* len, int2* mc, float4* Dm,
+                          float4* dir) {
+    if (P_dev) P = min(*P_dev, P);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         const int q = depth[i];
         const double* pp = pts + (int64_t)i * (D + 2) * 3;
@@ -84,6 +88,7 @@ __global__ void k_records(int64_t P, int D, const double* __restrict__ pts, cons
 
 struct FieldArgs {
     int64_t P;
+    const int64_t* Pd;         // the count of paths of a trace that did not wait (at most P), or null
     int D;
     int n_mat;                 // entries of eps / sig (materials, or triangles when per_tri)
     const int32_t* depth;
@@ -114,6 +119,7 @@ __device__ __forceinline__ float2 eta_of(const FieldArgs& A, const float2* s_eta
 // material and cos, basis changes) are in flight together; the material gather
 // of the step is a shared-memory table (or an L2-resident per-triangle array).
 __global__ void __launch_bounds__(256, 6) k_fields_fwd(FieldArgs A, float2* __restrict__ a_out, double* __restrict__ tau_out) {
+    if (A.Pd) A.P = min(*A.Pd, A.P);   // slots of a trace that did not wait: its count (and stride)
     __shared__ float2 s_tab[ETA_SMEM];
     const bool smem_eta = !A.per_tri && A.n_mat <= ETA_SMEM;
     if (smem_eta) {
@@ -189,6 +195,7 @@ __global__ void __launch_bounds__(256, 4) k_fields_bwd(FieldArgs A, const float2
                                                        float* __restrict__ geps, float* __restrict__ gsig,
                                                        float* __restrict__ ggain, float inv_gtx, float inv_grx,
                                                        int n_mat) {
+    if (A.Pd) A.P = min(*A.Pd, A.P);   // slots of a trace that did not wait: its count (and stride)
     __shared__ float s_eps[MAXM > 0 ? MAXM : 1], s_sig[MAXM > 0 ? MAXM : 1], s_gain[2];
     __shared__ float2 s_tab[ETA_SMEM];
     if (MAXM > 0)
@@ -315,6 +322,7 @@ FieldArgs make_args(const rt_paths* p, const float* eps, const float* sig, int p
                     float grx) {
     FieldArgs A;
     A.P = p->P;
+    A.Pd = p->d_count;
     A.D = p->D;
     A.depth = p->d_depth;
     A.tri = p->d_tri;
@@ -344,7 +352,7 @@ int grid_for(const rt_ctx* ctx, int64_t n, int threads, int per_sm) {
 
 }  // namespace
 
-rt_status rt_launch_paths_records(rt_ctx* ctx, rt_paths* p) {
+rt_status rt_launch_paths_records(rt_ctx* ctx, rt_paths* p, const int64_t* P_dev) {
     cudaStream_t st = ctx->stream;
     const size_t Pa = p->P > 0 ? (size_t)p->P : 1;
     // one allocation for the five record arrays
@@ -360,7 +368,7 @@ rt_status rt_launch_paths_records(rt_ctx* ctx, rt_paths* p) {
     p->d_Dm = reinterpret_cast<float4*>(b + o_Dm);
     p->d_dir = reinterpret_cast<float4*>(b + o_dir);
     if (p->P == 0) return RT_OK;
-    k_records<<<grid_for(ctx, p->P, 128, 16), 128, 0, st>>>(p->P, p->D, p->d_pts, p->d_depth, p->d_tri,
+    k_records<<<grid_for(ctx, p->P, 128, 16), 128, 0, st>>>(p->P, P_dev, p->D, p->d_pts, p->d_depth, p->d_tri,
                                                            p->scene->d_tri_n64, p->scene->d_tri_material,
                                                            p->scene->d_is_pec, p->d_tau, p->d_len, p->d_mc,
                                                            p->d_Dm, p->d_dir); RT_COUNT(ctx);

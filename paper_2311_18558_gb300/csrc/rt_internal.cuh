@@ -27,8 +27,10 @@ struct rt_ctx {
     // reusable scratch arena (grown on demand, freed with the context)
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
-    // pinned host word for small readbacks
+    // pinned host words for small readbacks (64 words)
     int64_t* h_pinned = nullptr;
+    // device words of one trace (64): stage counters and capacity flags, read back once at its end
+    unsigned long long* d_trace_words = nullptr;
     // instrumentation
     int64_t launches = 0;              // kernels launched through this context
     int32_t profile = 0;               // bit 0: trace stage events, bit 1: traversal counters
@@ -48,6 +50,7 @@ struct rt_ctx {
     int tune_vis_blocks_per_sm = 8;
     int cfr_tensor_cores = 1;   // CFR on tcgen05 (3xTF32) where n_sub allows, else SIMT
     int32_t wait_limit = 0;     // polls of the CFR waits on other CTAs (0: the default 2^22)
+    int32_t trace_async = 0;    // rt_trace_paths returns without waiting (paths counted on the device)
 };
 
 // Count one kernel launch of `ctx` (every launch site calls this).
@@ -81,6 +84,8 @@ struct rt_scene {
     uint8_t* d_is_pec = nullptr;
     size_t hash_cap = 1u << 20;        // learned dedup table capacity
     size_t queue_cap = 1u << 20;       // learned visibility-queue capacity
+    int64_t uniq_hint = 0;             // unique candidate keys of the last trace (0: none yet)
+    int64_t paths_hint = 0;            // emitted paths of the last trace (0: none yet)
     uint8_t* h_is_pec = nullptr;       // host copy of the material PEC flags (batch checks)
     bool owns_tables_only = false;     // combined batch scene: no BVH, tables owned here
     // wedges for diffraction, built at the first rt_trace_diffraction / rt_scene_wedges
@@ -98,6 +103,10 @@ struct rt_paths {
     int64_t P = 0, K = 0;
     int D = 0, R = 0;
     int64_t* d_rx_offsets = nullptr;   // R + 1
+    // a trace that returned without waiting: P is the number of slots, the count
+    // is d_count[0] (K in d_count[1], a capacity overflow flag in d_count[2]) until
+    // rt_paths_resolve reads it
+    int64_t* d_count = nullptr;
     int32_t* d_rx = nullptr;           // P
     int32_t* d_depth = nullptr;        // P
     int32_t* d_tri = nullptr;          // D x P (slot-major), -1 padded
@@ -139,6 +148,14 @@ struct RtCarve {
 };
 
 // ---------------------------------------------------------------- error helpers
+// Entry points that need the path count on the host refuse paths of a trace that
+// returned without waiting (rt_paths_resolve first).
+#define RT_REQUIRE_RESOLVED(ctx, p)                                                                     \
+    do {                                                                                                \
+        if ((p) && (p)->d_count)                                                                        \
+            return rt_fail((ctx), RT_ERR_INVALID_ARG, "paths not resolved: call rt_paths_resolve first"); \
+    } while (0)
+
 rt_status rt_fail(rt_ctx* ctx, rt_status st, const char* fmt, ...);
 rt_status rt_cuda_fail(rt_ctx* ctx, cudaError_t e, const char* what);
 // Grow the context scratch arena to at least `bytes`; returns its base.
@@ -183,4 +200,6 @@ rt_status rt_launch_fields_bwd(rt_ctx* ctx, const rt_paths* p, const float* eps,
                                float* geps, float* gsig, float* ggain);
 // Geometry records (delay, length, cos(theta_i), basis changes) of every path
 // from its points and triangles (d_pts, d_tri, d_depth must be filled).
-rt_status rt_launch_paths_records(rt_ctx* ctx, rt_paths* p);
+// With P_dev, the paths are counted on the device (at most p->P, which then gives
+// only the slots allocated): the records use that count as their stride.
+rt_status rt_launch_paths_records(rt_ctx* ctx, rt_paths* p, const int64_t* P_dev = nullptr);

@@ -831,8 +831,10 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const doub
 }
 
 // ------------------------------------------------------------------ compaction + sort
+// Non-zero table entries into out (at most out_cap of them; the count keeps
+// counting past it, which the host reads as an overflow).
 __global__ void k_table_compact(const unsigned long long* __restrict__ table, uint64_t cap, uint64_t* out,
-                                unsigned long long* count) {
+                                unsigned long long* count, uint64_t out_cap) {
     const int lane = threadIdx.x & 31;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i - lane < cap;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -843,7 +845,8 @@ __global__ void k_table_compact(const unsigned long long* __restrict__ table, ui
         int leader = __ffs(m) - 1;
         if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
         base = __shfl_sync(FULL, base, leader);
-        if (k) out[base + __popc(m & ((1u << lane) - 1))] = k;
+        const unsigned long long slot = base + __popc(m & ((1u << lane) - 1));
+        if (k && slot < out_cap) out[slot] = k;
     }
 }
 
@@ -920,9 +923,13 @@ __device__ __forceinline__ uint64_t rank_value(uint64_t key) {
     return q == 0 ? 0ull : key >> (16 * (4 - q));
 }
 
-__global__ void k_rank_count(const uint64_t* __restrict__ keys, int n, int* __restrict__ rank) {
+// n: the number of keys, read from the compaction count (at most cap).
+__global__ void k_rank_count(const uint64_t* __restrict__ keys, const unsigned long long* __restrict__ n_dev, int cap,
+                             int* __restrict__ rank) {
     __shared__ uint64_t sj[RANK_TILE];
+    const int n = (int)min(*n_dev, (unsigned long long)cap);
     const int j0 = blockIdx.x * RANK_TILE;
+    if (j0 >= n) return;
     for (int t = threadIdx.x; t < RANK_TILE; t += blockDim.x)
         sj[t] = j0 + t < n ? rank_value(keys[j0 + t]) : ~0ull;   // padding never counts as smaller
     __syncthreads();
@@ -935,8 +942,9 @@ __global__ void k_rank_count(const uint64_t* __restrict__ keys, int n, int* __re
     if (c) atomicAdd(rank + i, c);
 }
 
-__global__ void k_rank_scatter(const uint64_t* __restrict__ keys, const int* __restrict__ rank, int n,
-                               uint64_t* __restrict__ out) {
+__global__ void k_rank_scatter(const uint64_t* __restrict__ keys, const int* __restrict__ rank,
+                               const unsigned long long* __restrict__ n_dev, int cap, uint64_t* __restrict__ out) {
+    const int n = (int)min(*n_dev, (unsigned long long)cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[rank[i]] = keys[i];
 }
 
@@ -960,29 +968,48 @@ __global__ void k_fill_u64(uint64_t* p, uint64_t n, uint64_t v) {
 }
 
 // ------------------------------------------------------------------ candidates
+// The candidate list: the line of sight (key 0), then the sorted unique keys
+// (n of them, read from the compaction count, at most cap); K = n + 1 is stored
+// for the later kernels and the host.
+__global__ void k_cand_keys(const uint64_t* __restrict__ sorted, const unsigned long long* __restrict__ n_dev,
+                            int64_t cap, uint64_t* __restrict__ cand, int64_t* __restrict__ K_dev) {
+    const int64_t n = (int64_t)min(*n_dev, (unsigned long long)cap);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
+        cand[i] = i == 0 ? 0ull : sorted[i - 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *K_dev = n + 1;
+}
+
 // Per candidate: length q, triangles, and the image sources I_1..I_q of the
 // transmitter (I_j = I_{j-1} - 2 ((I_{j-1} - a_j).n_j) n_j), FP64 and FP32.
-__global__ void k_candidates(const uint64_t* __restrict__ keys, int64_t K, int D, double tx, double ty, double tz,
-                             const float4* __restrict__ tri_v, const double* __restrict__ tri_n64, int32_t* cand_depth,
-                             int32_t* cand_tri, double* img64, float4* img32) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
+// The arrays hold Kc slots (slot-major, stride Kc); the slots from *K_dev on are
+// marked empty (depth -1) and produce no pairs.
+__global__ void k_candidates(const uint64_t* __restrict__ keys, int64_t Kc, const int64_t* __restrict__ K_dev, int D,
+                             double tx, double ty, double tz, const float4* __restrict__ tri_v,
+                             const double* __restrict__ tri_n64, int32_t* cand_depth, int32_t* cand_tri, double* img64,
+                             float4* img32) {
+    const int64_t K = *K_dev;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Kc; k += (int64_t)gridDim.x * blockDim.x) {
+        if (k >= K) {
+            cand_depth[k] = -1;
+            continue;
+        }
         uint64_t key = keys[k];
         int q = rt_key_depth(key);
         cand_depth[k] = q;
         V3<double> I = mk(tx, ty, tz);
         for (int j = 0; j < D; ++j) {
             int t = j < q ? rt_key_tri(key, j) : -1;
-            cand_tri[(int64_t)j * K + k] = t;
+            cand_tri[(int64_t)j * Kc + k] = t;
             if (t >= 0) {
                 V3<double> n = mk(tri_n64[4 * t], tri_n64[4 * t + 1], tri_n64[4 * t + 2]);
                 V3<double> a = from4<double>(__ldg(tri_v + 3 * t));
                 I = I - (2.0 * dot(I - a, n)) * n;
             }
-            double* o = img64 + ((int64_t)j * K + k) * 3;
+            double* o = img64 + ((int64_t)j * Kc + k) * 3;
             o[0] = I.x;
             o[1] = I.y;
             o[2] = I.z;
-            img32[(int64_t)j * K + k] = make_float4((float)I.x, (float)I.y, (float)I.z, 0.0f);
+            img32[(int64_t)j * Kc + k] = make_float4((float)I.x, (float)I.y, (float)I.z, 0.0f);
         }
     }
 }
@@ -1083,7 +1110,7 @@ __device__ __forceinline__ void pairs_tile(const CandView& C, int64_t k0, int64_
     const int lane = threadIdx.x & 31;
     for (int64_t k = k0; k < k1; ++k) {
         const int q = C.depth[k];
-        const bool ok = r_ok && (q == 0 || prefilter32(C, k, q, rxf, tri_bary));
+        const bool ok = r_ok && q >= 0 && (q == 0 || prefilter32(C, k, q, rxf, tri_bary));
         const unsigned m = __ballot_sync(FULL, ok);
         if (m) {
             unsigned long long base = 0;
@@ -1298,8 +1325,10 @@ __global__ void k_scan(const int64_t* __restrict__ counts, int n, int64_t* offse
 
 // Expansion of the bitmask into (receiver, candidate) pairs at their final
 // positions, candidates in increasing order within a receiver (one warp each).
+// Paths at or beyond cap are not written (the host reads offsets[R] > cap as an
+// overflow and traces again with more room).
 __global__ void k_expand(const uint32_t* __restrict__ bits, int R, int64_t words, const int64_t* __restrict__ offsets,
-                         int32_t* path_rx, int32_t* path_cand) {
+                         int32_t* path_rx, int32_t* path_cand, int64_t cap) {
     const int lane = threadIdx.x & 31;
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R;
          r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -1317,8 +1346,10 @@ __global__ void k_expand(const uint32_t* __restrict__ bits, int R, int64_t words
             while (b) {
                 int bit = __ffs(b) - 1;
                 b &= b - 1;
-                path_rx[my] = (int32_t)r;
-                path_cand[my] = (int32_t)(w * 32 + bit);
+                if (my < cap) {
+                    path_rx[my] = (int32_t)r;
+                    path_cand[my] = (int32_t)(w * 32 + bit);
+                }
                 my++;
             }
             pos += __shfl_sync(FULL, incl, 31);
@@ -1328,11 +1359,14 @@ __global__ void k_expand(const uint32_t* __restrict__ bits, int R, int64_t words
 
 // FP64 points of every emitted path, its triangle slots, and whether any
 // reflection point lies on a triangle edge (input of the duplicate rule).
-__global__ void k_points(CandView C, int64_t P, int D, const int32_t* __restrict__ path_rx,
+// P: the number of emitted paths (*P_dev, at most cap), also the slot stride of tri_out.
+__global__ void k_points(CandView C, const int64_t* __restrict__ P_dev, int64_t cap, int D,
+                         const int32_t* __restrict__ path_rx,
                          const int32_t* __restrict__ path_cand, const double* __restrict__ rx, double tx, double ty,
                          double tz, const float4* __restrict__ tri_v, const double* __restrict__ tri_n64,
                          const double* __restrict__ bary64, double eps, double* pts_out, int32_t* depth_out,
                          int32_t* rx_out, int32_t* tri_out, int32_t* edge_flag, int32_t* status) {
+    const int64_t P = min(*P_dev, cap);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t k = path_cand[i];
         int r = path_rx[i];
@@ -1373,18 +1407,20 @@ __device__ __forceinline__ bool coplanar64(const double* __restrict__ tri_n64, c
 // Coplanar-duplicate rule: a path with a reflection point on an edge is dropped
 // if another path of its receiver, of equal length, has pairwise coplanar
 // triangles, the same points (within 1e-9 diag) and a smaller triangle sequence.
-__global__ void k_dedup(int64_t P, int D, const int64_t* __restrict__ rx_offsets, const int32_t* __restrict__ path_rx,
+__global__ void k_dedup(const int64_t* __restrict__ P_dev, int64_t cap, int D, const int64_t* __restrict__ rx_offsets,
+                        const int32_t* __restrict__ path_rx,
                         int32_t* __restrict__ path_cand, const int32_t* __restrict__ depth,
                         const int32_t* __restrict__ tri, const double* __restrict__ pts,
                         const int32_t* __restrict__ edge_flag, const double* __restrict__ tri_n64,
                         const float4* __restrict__ tri_v, double diag, uint32_t* bits, int64_t words,
                         unsigned long long* drops) {
+    const int64_t P = min(*P_dev, cap);
     const double tol2 = (1e-9 * diag) * (1e-9 * diag);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         if (!edge_flag[i]) continue;
         int r = path_rx[i];
         int q = depth[i];
-        for (int64_t j = rx_offsets[r]; j < rx_offsets[r + 1]; ++j) {
+        for (int64_t j = rx_offsets[r]; j < rx_offsets[r + 1] && j < P; ++j) {
             if (j == i || !edge_flag[j] || depth[j] != q) continue;
             bool same = true;
             for (int b = 0; b < q && same; ++b)
@@ -1418,22 +1454,25 @@ __global__ void k_dedup(int64_t P, int D, const int64_t* __restrict__ rx_offsets
 // Copies the paths the duplicate rule kept (path_cand >= 0) into fresh arrays,
 // one warp per receiver with a ballot prefix per 32 paths, so that the order
 // within a receiver is kept and no path is re-derived.
-__global__ void k_compact_paths(int R, int D, int64_t P, int64_t Pn, const int64_t* __restrict__ off,
+// P = off[R] (the emitted paths, stride of tri) and Pn = off_n[R] (the kept ones,
+// stride of tri_n) are read from device memory, both at most cap.
+__global__ void k_compact_paths(int R, int D, int64_t cap, const int64_t* __restrict__ off,
                                 const int64_t* __restrict__ off_n, const int32_t* __restrict__ path_cand,
                                 const double* __restrict__ pts, const int32_t* __restrict__ depth,
                                 const int32_t* __restrict__ rx, const int32_t* __restrict__ tri, double* __restrict__ pts_n,
                                 int32_t* __restrict__ depth_n, int32_t* __restrict__ rx_n, int32_t* __restrict__ tri_n) {
     const int lane = threadIdx.x & 31;
+    const int64_t P = min(off[R], cap), Pn = min(off_n[R], cap);
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R;
          r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         int64_t w = off_n[r];
         const int64_t o1 = off[r + 1];
         for (int64_t base = off[r]; base < o1; base += 32) {
             const int64_t i = base + lane;
-            const bool keep = i < o1 && path_cand[i] >= 0;
+            const bool keep = i < o1 && i < P && path_cand[i] >= 0;
             const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                const int64_t j = w + __popc(m & ((1u << lane) - 1u));
+            const int64_t j = w + __popc(m & ((1u << lane) - 1u));
+            if (keep && j < Pn) {
                 for (int e = 0; e < (D + 2) * 3; ++e) pts_n[j * (D + 2) * 3 + e] = pts[i * (D + 2) * 3 + e];
                 depth_n[j] = depth[i];
                 rx_n[j] = rx[i];
@@ -1442,6 +1481,33 @@ __global__ void k_compact_paths(int R, int D, int64_t P, int64_t Pn, const int64
             w += __popc(m);
         }
     }
+}
+
+// The counts and capacity flags of a pass, checked on the device before its
+// records are formed.  meta = {kept paths (0 after an overflow, so that nothing
+// reads the slots a cut-short pass may have left unwritten), candidates, overflow
+// (0, 1, or 2 for the re-trace list)}.  In a trace that does not wait, an overflow
+// also sets RT_ERR_CAPACITY in the status word.
+__global__ void k_trace_check(const unsigned long long* __restrict__ tw, const int64_t* __restrict__ P_emit,
+                              const int64_t* __restrict__ P_kept, int64_t ucap, int64_t pcap, int64_t* meta,
+                              int32_t* status, int report) {
+    if (threadIdx.x != 0) return;
+    const int32_t f1 = reinterpret_cast<const int32_t*>(tw + 8)[0];
+    const int32_t f2 = reinterpret_cast<const int32_t*>(tw + 24)[0];
+    const int64_t keys = (int64_t)tw[3];
+    const bool ovf = f1 != 0 || f2 != 0 || keys > ucap || *P_emit > pcap;
+    meta[0] = ovf ? 0 : min(*P_kept, pcap);
+    meta[1] = min(keys, ucap) + 1;
+    meta[2] = f1 == 2 ? 2 : (ovf ? 1 : 0);
+    if (ovf && report) rt_set_status(status, RT_ERR_CAPACITY);
+}
+
+// After an overflowed pass (meta[2] != 0) the receiver offsets may point past the
+// slots: every receiver is emptied, so that no later kernel reads beyond them.
+__global__ void k_trace_guard(const int64_t* __restrict__ meta, int64_t* offsets, int R) {
+    if (meta[2] == 0) return;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= R; r += (int64_t)gridDim.x * blockDim.x)
+        offsets[r] = 0;
 }
 
 inline int grid_for(rt_ctx* ctx, int64_t n, int threads, int per_sm = 8) {
@@ -1527,6 +1593,28 @@ struct Arena {
     }
 };
 
+extern "C" __attribute__((visibility("default"))) rt_status rt_set_trace_async(rt_ctx* ctx, int32_t enable) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (enable != 0 && enable != 1) return rt_fail(ctx, RT_ERR_INVALID_ARG, "enable must be 0 or 1");
+    ctx->trace_async = enable;
+    return RT_OK;
+}
+
+extern "C" __attribute__((visibility("default"))) rt_status rt_paths_resolve(rt_paths* p) {
+    if (!p) return RT_ERR_INVALID_ARG;
+    if (!p->d_count) return RT_OK;
+    rt_ctx* ctx = p->scene->ctx;
+    int64_t* hp = ctx->h_pinned;
+    RT_CK(ctx, cudaMemcpyAsync(hp, p->d_count, 3 * 8, cudaMemcpyDeviceToHost, p->stream));
+    RT_CK(ctx, cudaStreamSynchronize(p->stream));
+    if (hp[2] == 2) return rt_fail(ctx, RT_ERR_CAPACITY, "FP64 re-trace list overflow");
+    if (hp[2]) return rt_fail(ctx, RT_ERR_CAPACITY, "a trace capacity overflowed: trace again with waiting on");
+    p->P = hp[0];
+    p->K = hp[1];
+    p->d_count = nullptr;
+    return RT_OK;
+}
+
 extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ctx* ctx, const rt_scene* scene, const double* tx_host, const double* rx_dev,
                                     int32_t n_rx, int64_t n_rays, int32_t max_depth, rt_paths** out) {
     if (!ctx) return RT_ERR_INVALID_ARG;
@@ -1544,28 +1632,46 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
     const size_t stack_bytes = (size_t)RT_STACK * TRACE_THREADS * sizeof(int);
     const size_t vis_bytes = (size_t)(RT_STACK + VIS_CAND_CAP) * TRACE_THREADS * sizeof(int);
 
-    // ---------------- 1-2: SBR into the hash set (grow and retry on overflow)
+    // One pass of the whole pipeline with buffers sized from capacities (the hash
+    // table, the unique candidates, the visibility queue and the paths: the scene
+    // remembers the last counts), the counts of each stage read on the device by
+    // the next; a single read-back at the end checks every capacity, and a pass
+    // that overflowed one is run again with more room.
     const int64_t redo_cap = std::max<int64_t>(1 << 16, n_rays / 16);
-    uint64_t* d_sorted = nullptr;
-    int64_t n_uniq = 0;
+    unsigned long long* tw = ctx->d_trace_words;   // 64 words, see rt_ctx
+    unsigned long long* c1 = tw;                    // SBR: uniq, next_ray, redo_count, compacted keys
+    int32_t* f1 = reinterpret_cast<int32_t*>(tw + 8);   // SBR flags: hash overflow (1), re-trace list (2)
+    unsigned long long* c2 = tw + 16;               // visibility queue count, .., [4] duplicates dropped
+    int32_t* f2 = reinterpret_cast<int32_t*>(tw + 24);  // queue overflow
+    int64_t* K_dev = reinterpret_cast<int64_t*>(tw + 28);
     for (int attempt = 0;; ++attempt) {
-        size_t cap = sc->hash_cap;
-        const size_t sort_cap = std::max<size_t>(SORT_BLOCK, cap / 2);
-        size_t need = cap * 8 + sort_cap * 8 + 256 * 8 + redo_cap * 16 + 4096 + 256;
+        if (attempt >= 8) return rt_fail(ctx, RT_ERR_CAPACITY, "trace capacities did not converge");
+        const size_t cap = sc->hash_cap;
+        // unique keys: the last count with room, at most the table's limit
+        int64_t ucap = std::max<int64_t>(1024, sc->uniq_hint + sc->uniq_hint / 4 + 256);
+        ucap = std::min<int64_t>(ucap, (int64_t)(cap / 2));
+        const bool rank_sort = ucap <= RANK_SORT_MAX;
+        int64_t n_pad = SORT_BLOCK;
+        while (n_pad < ucap) n_pad <<= 1;
+        const int64_t Kc = ucap + 1;
+        const int64_t words = (Kc + 31) / 32;
+        const size_t qcap = sc->queue_cap;
+
+        // ---------------- 1-2: SBR into the hash set
+        const size_t need1 = cap * 8 + (size_t)n_pad * 8 + redo_cap * 16 + (size_t)RANK_SORT_MAX * 12 + 4096;
         void* base;
-        rt_status s = rt_scratch(ctx, need, &base);
+        rt_status s = rt_scratch(ctx, need1, &base);
         if (s != RT_OK) return s;
         Arena ar{(char*)base};
         unsigned long long* table = ar.take<unsigned long long>(cap);
-        unsigned long long* counters = ar.take<unsigned long long>(8);   // uniq, next_ray, redo_count, compact
-        int32_t* flags = ar.take<int32_t>(8);
         int64_t* redo = ar.take<int64_t>(redo_cap);
         uint64_t* redo_key = ar.take<uint64_t>(redo_cap);
-        uint64_t* sorted = ar.take<uint64_t>(sort_cap);
+        uint64_t* sorted = ar.take<uint64_t>(n_pad);
+        uint64_t* unsorted = ar.take<uint64_t>(RANK_SORT_MAX);
+        int* rank = ar.take<int>(RANK_SORT_MAX);
         mark(ctx, 0);
         RT_CK(ctx, cudaMemsetAsync(table, 0, cap * 8, st));
-        RT_CK(ctx, cudaMemsetAsync(counters, 0, 8 * 8, st));
-        RT_CK(ctx, cudaMemsetAsync(flags, 0, 8 * 4, st));
+        RT_CK(ctx, cudaMemsetAsync(tw, 0, 64 * 8, st));
         SbrArgs A;
         A.nodes = sc->d_nodes;
         A.tris = sc->d_bvh_tris;
@@ -1578,13 +1684,13 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         A.eps = sc->eps;
         A.table = table;
         A.mask = cap - 1;
-        A.uniq = counters + 0;
+        A.uniq = c1 + 0;
         A.uniq_limit = cap / 2;
-        A.overflow = flags;
-        A.next_ray = counters + 1;
+        A.overflow = f1;
+        A.next_ray = c1 + 1;
         A.redo = redo;
         A.redo_key = redo_key;
-        A.redo_count = counters + 2;
+        A.redo_count = c1 + 2;
         A.redo_cap = redo_cap;
         A.status = status;
         A.counters = (ctx->profile & 2) ? ctx->d_counters : nullptr;
@@ -1602,128 +1708,93 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         RT_COUNT(ctx);
         mark(ctx, 1);
         RT_CK_LAUNCH(ctx);
-        int64_t* hp = ctx->h_pinned;
-        RT_CK(ctx, cudaMemcpyAsync(hp, counters, 8, cudaMemcpyDeviceToHost, st));
-        RT_CK(ctx, cudaMemcpyAsync(hp + 1, flags, 4, cudaMemcpyDeviceToHost, st));
-        RT_CK(ctx, cudaStreamSynchronize(st));
-        n_uniq = hp[0];
-        int32_t ovf = *(int32_t*)(hp + 1);
-        if (ovf == 2) return rt_fail(ctx, RT_ERR_CAPACITY, "FP64 re-trace list overflow");
-        if (ovf) {
-            if (attempt >= 6 || sc->hash_cap >= ((size_t)1 << 31))
-                return rt_fail(ctx, RT_ERR_CAPACITY, "candidate hash table overflow");
-            sc->hash_cap *= 4;
-            continue;
+        if (sc->uniq_hint == 0) {
+            // the scene's first trace: learn the number of unique keys (later traces
+            // size from the last count and do not wait here)
+            RT_CK(ctx, cudaMemcpyAsync(ctx->h_pinned, c1, 8, cudaMemcpyDeviceToHost, st));
+            RT_CK(ctx, cudaStreamSynchronize(st));
+            sc->uniq_hint = std::max<int64_t>(1, ctx->h_pinned[0]);
+            if (sc->uniq_hint > ucap && ucap < (int64_t)(cap / 2)) continue;
         }
-        // ---------------- compact + sort (length, lexicographic)
-        d_sorted = sorted;
-        if (n_uniq <= RANK_SORT_MAX) {
-            // compact into the re-trace list's buffer (free once the re-trace has run:
-            // stream order), then rank and scatter into the sort buffer
-            uint64_t* unsorted = reinterpret_cast<uint64_t*>(redo);
-            int* rank = reinterpret_cast<int*>(unsorted + RANK_SORT_MAX);
+        // ---------------- compact + sort (length, lexicographic), at most ucap keys
+        if (rank_sort) {
             RT_CK(ctx, cudaMemsetAsync(rank, 0, (size_t)RANK_SORT_MAX * 4, st));
-            k_table_compact<<<grid_for(ctx, cap, 256, 16), 256, 0, st>>>(table, cap, unsorted, counters + 3);
+            k_table_compact<<<grid_for(ctx, cap, 256, 16), 256, 0, st>>>(table, cap, unsorted, c1 + 3, (uint64_t)ucap);
             RT_COUNT(ctx);
-            if (n_uniq > 0) {
-                const int n = (int)n_uniq;
-                k_rank_count<<<dim3((n + RANK_TILE - 1) / RANK_TILE, (n + 255) / 256), 256, 0, st>>>(unsorted, n, rank);
-                RT_COUNT(ctx);
-                k_rank_scatter<<<grid_for(ctx, n, 256), 256, 0, st>>>(unsorted, rank, n, d_sorted);
-                RT_COUNT(ctx);
+            const int n = (int)ucap;
+            k_rank_count<<<dim3((n + RANK_TILE - 1) / RANK_TILE, (n + 255) / 256), 256, 0, st>>>(unsorted, c1 + 3, n,
+                                                                                                 rank);
+            RT_COUNT(ctx);
+            k_rank_scatter<<<grid_for(ctx, n, 256), 256, 0, st>>>(unsorted, rank, c1 + 3, n, sorted);
+            RT_COUNT(ctx);
+        } else {
+            k_fill_u64<<<grid_for(ctx, n_pad, 256), 256, 0, st>>>(sorted, n_pad, ~0ull); RT_COUNT(ctx);
+            k_table_compact<<<grid_for(ctx, cap, 256, 16), 256, 0, st>>>(table, cap, sorted, c1 + 3, (uint64_t)ucap);
+            RT_COUNT(ctx);
+            k_bitonic_local<<<(unsigned)(n_pad / SORT_BLOCK), 1024, 0, st>>>(sorted); RT_COUNT(ctx);
+            for (uint64_t k = 2 * SORT_BLOCK; k <= (uint64_t)n_pad; k <<= 1) {
+                for (uint64_t j = k >> 1; j >= (uint64_t)SORT_BLOCK; j >>= 1) {
+                    k_bitonic_global<<<grid_for(ctx, n_pad, 256, 16), 256, 0, st>>>(sorted, n_pad, j, k);
+                    RT_COUNT(ctx);
+                }
+                k_bitonic_merge_local<<<(unsigned)(n_pad / SORT_BLOCK), 1024, 0, st>>>(sorted, k); RT_COUNT(ctx);
             }
-            RT_CK_LAUNCH(ctx);
-            break;
-        }
-        int64_t n_pad = SORT_BLOCK;
-        while (n_pad < n_uniq) n_pad <<= 1;
-        k_fill_u64<<<grid_for(ctx, n_pad, 256), 256, 0, st>>>(d_sorted, n_pad, ~0ull); RT_COUNT(ctx);
-        k_table_compact<<<grid_for(ctx, cap, 256, 16), 256, 0, st>>>(table, cap, d_sorted, counters + 3); RT_COUNT(ctx);
-        RT_CK_LAUNCH(ctx);
-        k_bitonic_local<<<(unsigned)(n_pad / SORT_BLOCK), 1024, 0, st>>>(d_sorted); RT_COUNT(ctx);
-        for (uint64_t k = 2 * SORT_BLOCK; k <= (uint64_t)n_pad; k <<= 1) {
-            for (uint64_t j = k >> 1; j >= (uint64_t)SORT_BLOCK; j >>= 1) {
-                k_bitonic_global<<<grid_for(ctx, n_pad, 256, 16), 256, 0, st>>>(d_sorted, n_pad, j, k);
-                RT_COUNT(ctx);
-            }
-            k_bitonic_merge_local<<<(unsigned)(n_pad / SORT_BLOCK), 1024, 0, st>>>(d_sorted, k); RT_COUNT(ctx);
         }
         RT_CK_LAUNCH(ctx);
-        break;
-    }
 
-    // ---------------- candidates (LoS first)
-    const int64_t K = n_uniq + 1;
-    rt_paths* p = new rt_paths();
-    p->scene = scene;
-    p->stream = st;
-    p->D = D;
-    p->R = n_rx;
-    p->K = K;
-    auto fail = [&](rt_status s) {
-        rt_paths_free(p);
-        return s;
-    };
+        // ---------------- candidates (LoS first), Kc slots
+        rt_paths* p = new rt_paths();
+        p->scene = scene;
+        p->stream = st;
+        p->D = D;
+        p->R = n_rx;
+        auto fail = [&](rt_status e) {
+            rt_paths_free(p);
+            return e;
+        };
 #define TCK(call)                                                         \
     do {                                                                  \
         cudaError_t _e = (call);                                          \
         if (_e != cudaSuccess) return fail(rt_cuda_fail(ctx, _e, #call)); \
     } while (0)
-    TCK(cudaMallocAsync((void**)&p->d_cand, K * 8, st));
-    TCK(cudaMemsetAsync(p->d_cand, 0, 8, st));
-    if (n_uniq > 0) TCK(cudaMemcpyAsync(p->d_cand + 1, d_sorted, n_uniq * 8, cudaMemcpyDeviceToDevice, st));
+        TCK(cudaMallocAsync((void**)&p->d_cand, Kc * 8, st));
+        k_cand_keys<<<grid_for(ctx, Kc, 256), 256, 0, st>>>(sorted, c1 + 3, ucap, p->d_cand, K_dev); RT_COUNT(ctx);
+        TCK(cudaGetLastError());
 
-    // candidate arrays + visibility queue + bitmask: a fresh scratch layout
-    const int64_t words = (K + 31) / 32;
-    int32_t* cand_depth = nullptr;
-    int32_t* cand_tri = nullptr;
-    double* img64 = nullptr;
-    float4* img32 = nullptr;
-    uint2* queue = nullptr;
-    uint32_t* bits = nullptr;
-    unsigned long long* counters = nullptr;
-    int32_t* flags = nullptr;
-    int64_t* counts = nullptr;
-    int64_t n_emit = 0;
-    for (int attempt = 0;; ++attempt) {
-        size_t qcap = sc->queue_cap;
-        size_t need = K * 4 + (size_t)D * K * 4 + (size_t)D * K * 24 + (size_t)D * K * 16 + qcap * 8 +
-                      (size_t)n_rx * words * 4 + 64 * 8 + (size_t)(n_rx + 1) * 8 * 2 + qcap * 4 +
-                      2 * (size_t)(D + 1) * qcap * 16 + 20 * 256;
-        void* base;
-        rt_status s = rt_scratch(ctx, need, &base);
+        // candidate arrays + visibility queue + bitmask: a fresh scratch layout (the
+        // sorted keys above are consumed first, in stream order)
+        const size_t need2 = Kc * 4 + (size_t)D * Kc * 4 + (size_t)D * Kc * 24 + (size_t)D * Kc * 16 + qcap * 8 +
+                             (size_t)n_rx * words * 4 + (size_t)(n_rx + 1) * 8 * 2 + qcap * 4 +
+                             2 * (size_t)(D + 1) * qcap * 16 + 20 * 256;
+        s = rt_scratch(ctx, need2, &base);
         if (s != RT_OK) return fail(s);
-        Arena ar{(char*)base};
-        cand_depth = ar.take<int32_t>(K);
-        cand_tri = ar.take<int32_t>((size_t)D * K);
-        img64 = ar.take<double>((size_t)D * K * 3);
-        img32 = ar.take<float4>((size_t)D * K);
-        queue = ar.take<uint2>(qcap);
-        bits = ar.take<uint32_t>((size_t)n_rx * words);
-        counters = ar.take<unsigned long long>(8);
-        flags = ar.take<int32_t>(8);
-        counts = ar.take<int64_t>(n_rx + 1);
-        int32_t* seg_q = ar.take<int32_t>(qcap);
-        float4* seg_o = ar.take<float4>((size_t)(D + 1) * qcap);
-        float4* seg_d = ar.take<float4>((size_t)(D + 1) * qcap);
-        TCK(cudaMemsetAsync(counters, 0, 64, st));
-        TCK(cudaMemsetAsync(flags, 0, 32, st));
+        Arena ar2{(char*)base};
+        int32_t* cand_depth = ar2.take<int32_t>(Kc);
+        int32_t* cand_tri = ar2.take<int32_t>((size_t)D * Kc);
+        double* img64 = ar2.take<double>((size_t)D * Kc * 3);
+        float4* img32 = ar2.take<float4>((size_t)D * Kc);
+        uint2* queue = ar2.take<uint2>(qcap);
+        uint32_t* bits = ar2.take<uint32_t>((size_t)n_rx * words);
+        int64_t* counts = ar2.take<int64_t>(n_rx + 1);
+        int32_t* seg_q = ar2.take<int32_t>(qcap);
+        float4* seg_o = ar2.take<float4>((size_t)(D + 1) * qcap);
+        float4* seg_d = ar2.take<float4>((size_t)(D + 1) * qcap);
         TCK(cudaMemsetAsync(bits, 0, (size_t)n_rx * words * 4, st));
-        k_candidates<<<grid_for(ctx, K, 256), 256, 0, st>>>(p->d_cand, K, D, tx_host[0], tx_host[1], tx_host[2],
-                                                            sc->d_tri_v, sc->d_tri_n64, cand_depth, cand_tri, img64,
-                                                            img32); RT_COUNT(ctx);
+        k_candidates<<<grid_for(ctx, Kc, 256), 256, 0, st>>>(p->d_cand, Kc, K_dev, D, tx_host[0], tx_host[1], tx_host[2],
+                                                             sc->d_tri_v, sc->d_tri_n64, cand_depth, cand_tri, img64,
+                                                             img32); RT_COUNT(ctx);
         TCK(cudaGetLastError());
         PairArgs PA;
-        PA.C = CandView{K, cand_depth, cand_tri, img64, img32};
+        PA.C = CandView{Kc, cand_depth, cand_tri, img64, img32};
         PA.R = n_rx;
         PA.rx = rx_dev;
         PA.tri_bary = sc->d_tri_bary;
         PA.queue = queue;
-        PA.qcount = counters;
+        PA.qcount = c2;
         PA.qcap = qcap;
-        PA.overflow = flags;
+        PA.overflow = f2;
         mark(ctx, 2);
-        k_pairs<<<grid_for(ctx, ((K + PAIR_CC - 1) / PAIR_CC) * ((n_rx + 31) / 32) * 32, 256,
+        k_pairs<<<grid_for(ctx, ((Kc + PAIR_CC - 1) / PAIR_CC) * ((n_rx + 31) / 32) * 32, 256,
                            ctx->tune_pairs_blocks_per_sm),
                   256, 0, st>>>(PA); RT_COUNT(ctx);
         mark(ctx, 3);
@@ -1741,7 +1812,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         VA.bary64 = sc->d_tri_bary64;
         VA.eps = sc->eps;
         VA.queue = queue;
-        VA.qcount = counters;
+        VA.qcount = c2;
         VA.qcap = qcap;
         VA.bits = bits;
         VA.words = words;
@@ -1751,46 +1822,45 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         VA.seg_q = seg_q;
         VA.seg_o = seg_o;
         VA.seg_d = seg_d;
-        ctx->h_counters[7] += K * (int64_t)n_rx;
         k_backtrace<<<ctx->num_sms * 8, TRACE_THREADS, 0, st>>>(VA); RT_COUNT(ctx);
         TCK(cudaGetLastError());
         k_segments<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st>>>(VA); RT_COUNT(ctx);
         mark(ctx, 4);
         TCK(cudaGetLastError());
-        // per-receiver path counts and offsets before the overflow check, so that
-        // one round trip returns both the queue flag and the number of paths
+        int64_t* off_e = nullptr;   // offsets of the emitted paths (before the duplicate rule)
+        TCK(cudaMallocAsync((void**)&off_e, (size_t)(n_rx + 1) * 8, st));
         k_row_count<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, counts); RT_COUNT(ctx);
+        k_scan<<<1, 1024, 0, st>>>(counts, n_rx, off_e); RT_COUNT(ctx);
         TCK(cudaGetLastError());
-        if (!p->d_rx_offsets) TCK(cudaMallocAsync((void**)&p->d_rx_offsets, (size_t)(n_rx + 1) * 8, st));
-        k_scan<<<1, 1024, 0, st>>>(counts, n_rx, p->d_rx_offsets); RT_COUNT(ctx);
-        TCK(cudaGetLastError());
-        int64_t* hp = ctx->h_pinned;
-        TCK(cudaMemcpyAsync(hp, p->d_rx_offsets + n_rx, 8, cudaMemcpyDeviceToHost, st));
-        TCK(cudaMemcpyAsync(hp + 1, flags, 4, cudaMemcpyDeviceToHost, st));
-        TCK(cudaStreamSynchronize(st));
-        if (*(int32_t*)(hp + 1)) {
-            if (attempt >= 6) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "visibility queue overflow"));
-            sc->queue_cap *= 4;
-            continue;
+        if (sc->paths_hint == 0) {
+            // the scene's first trace: learn the number of emitted paths
+            TCK(cudaMemcpyAsync(ctx->h_pinned, off_e + n_rx, 8, cudaMemcpyDeviceToHost, st));
+            TCK(cudaStreamSynchronize(st));
+            sc->paths_hint = std::max<int64_t>(1, ctx->h_pinned[0]);
         }
-        n_emit = hp[0];
-        break;
-    }
+        const int64_t pcap = std::max<int64_t>(1024, sc->paths_hint + sc->paths_hint / 4 + 1024);
 
-    // ---------------- emission, then the duplicate rule (kept paths compacted)
-    int32_t* path_rx = nullptr;
-    int32_t* path_cand = nullptr;
-    int32_t* edge = nullptr;
-    {
-        int64_t* hp = ctx->h_pinned;
-        const int64_t P = n_emit;
-        p->P = P;
-        const size_t Pa = std::max<int64_t>(P, 1);
+        // ---------------- emission (pcap slots), the duplicate rule, then the kept
+        // paths compacted into the final arrays
+        const size_t Pa = (size_t)pcap;
+        int32_t* path_cand = nullptr;
+        int32_t* edge = nullptr;
+        char* tmp = nullptr;   // emitted paths before the duplicate rule
+        RtCarve ct;
+        const size_t t_pts = ct.take(Pa * (D + 2) * 3 * 8), t_depth = ct.take(Pa * 4), t_rx = ct.take(Pa * 4),
+                     t_tri = ct.take(Pa * D * 4), t_cand = ct.take(Pa * 4), t_edge = ct.take(Pa * 4);
+        TCK(cudaMallocAsync((void**)&tmp, ct.off, st));
+        double* pts_e = reinterpret_cast<double*>(tmp + t_pts);
+        int32_t* depth_e = reinterpret_cast<int32_t*>(tmp + t_depth);
+        int32_t* rx_e = reinterpret_cast<int32_t*>(tmp + t_rx);
+        int32_t* tri_e = reinterpret_cast<int32_t*>(tmp + t_tri);
+        path_cand = reinterpret_cast<int32_t*>(tmp + t_cand);
+        edge = reinterpret_cast<int32_t*>(tmp + t_edge);
+        int64_t* meta = nullptr;
         {
-            // one allocation for the four path arrays
             RtCarve c;
             const size_t o_pts = c.take(Pa * (D + 2) * 3 * 8), o_depth = c.take(Pa * 4), o_rx = c.take(Pa * 4),
-                         o_tri = c.take(Pa * D * 4);
+                         o_tri = c.take(Pa * D * 4), o_meta = c.take(4 * 8);
             char* b = nullptr;
             TCK(cudaMallocAsync((void**)&b, c.off, st));
             p->d_block_geo = b;
@@ -1798,75 +1868,98 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
             p->d_depth = reinterpret_cast<int32_t*>(b + o_depth);
             p->d_rx = reinterpret_cast<int32_t*>(b + o_rx);
             p->d_tri = reinterpret_cast<int32_t*>(b + o_tri);
+            meta = reinterpret_cast<int64_t*>(b + o_meta);
         }
-        TCK(cudaMallocAsync((void**)&path_cand, Pa * 4, st));
-        TCK(cudaMallocAsync((void**)&edge, Pa * 4, st));
-        path_rx = p->d_rx;
-        if (P > 0) {
-            k_expand<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, p->d_rx_offsets,
-                                                                                 path_rx, path_cand); RT_COUNT(ctx);
-            TCK(cudaGetLastError());
-            CandView C{K, cand_depth, cand_tri, img64, img32};
-            k_points<<<grid_for(ctx, P, 256), 256, 0, st>>>(C, P, D, path_rx, path_cand, rx_dev, tx_host[0], tx_host[1],
-                                                             tx_host[2], sc->d_tri_v, sc->d_tri_n64, sc->d_tri_bary64, sc->eps, p->d_pts,
-                                                             p->d_depth, p->d_rx, p->d_tri, edge, status); RT_COUNT(ctx);
-            TCK(cudaGetLastError());
-        }
-        if (P > 0) {
-            TCK(cudaMemsetAsync(counters + 4, 0, 8, st));
-            k_dedup<<<grid_for(ctx, P, 256), 256, 0, st>>>(P, D, p->d_rx_offsets, path_rx, path_cand, p->d_depth,
-                                                           p->d_tri, p->d_pts, edge, sc->d_tri_n64, sc->d_tri_v, sc->diag,
-                                                           bits, words, counters + 4); RT_COUNT(ctx);
-            TCK(cudaGetLastError());
-            TCK(cudaMemcpyAsync(hp, counters + 4, 8, cudaMemcpyDeviceToHost, st));
-            TCK(cudaStreamSynchronize(st));
-            const int64_t dropped = hp[0];
-            if (dropped > 0) {
-                // the kept paths, compacted per receiver (offsets from the cleared bits)
-                const int64_t Pn = P - dropped;
-                const size_t Pna = std::max<int64_t>(Pn, 1);
-                int64_t* off_n = nullptr;
-                TCK(cudaMallocAsync((void**)&off_n, (size_t)(n_rx + 1) * 8, st));
-                RtCarve c;
-                const size_t o_pts = c.take(Pna * (D + 2) * 3 * 8), o_depth = c.take(Pna * 4),
-                             o_rx = c.take(Pna * 4), o_tri = c.take(Pna * D * 4);
-                char* blk = nullptr;
-                TCK(cudaMallocAsync((void**)&blk, c.off, st));
-                double* pts_n = reinterpret_cast<double*>(blk + o_pts);
-                int32_t* depth_n = reinterpret_cast<int32_t*>(blk + o_depth);
-                int32_t* rx_n = reinterpret_cast<int32_t*>(blk + o_rx);
-                int32_t* tri_n = reinterpret_cast<int32_t*>(blk + o_tri);
-                k_row_count<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, counts);
-                RT_COUNT(ctx);
-                k_scan<<<1, 1024, 0, st>>>(counts, n_rx, off_n); RT_COUNT(ctx);
-                k_compact_paths<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(
-                    n_rx, D, P, Pn, p->d_rx_offsets, off_n, path_cand, p->d_pts, p->d_depth, p->d_rx, p->d_tri, pts_n,
-                    depth_n, rx_n, tri_n); RT_COUNT(ctx);
-                TCK(cudaGetLastError());
-                cudaFreeAsync(p->d_rx_offsets, st);
-                cudaFreeAsync(p->d_block_geo, st);
-                p->d_block_geo = blk;
-                p->d_rx_offsets = off_n;
-                p->d_pts = pts_n;
-                p->d_depth = depth_n;
-                p->d_rx = rx_n;
-                p->d_tri = tri_n;
-                p->P = Pn;
+        TCK(cudaMallocAsync((void**)&p->d_rx_offsets, (size_t)(n_rx + 1) * 8, st));
+        const int64_t* P_e = off_e + n_rx;
+        k_expand<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, off_e, rx_e, path_cand,
+                                                                             pcap); RT_COUNT(ctx);
+        CandView C{Kc, cand_depth, cand_tri, img64, img32};
+        k_points<<<grid_for(ctx, pcap, 256), 256, 0, st>>>(C, P_e, pcap, D, rx_e, path_cand, rx_dev, tx_host[0],
+                                                           tx_host[1], tx_host[2], sc->d_tri_v, sc->d_tri_n64,
+                                                           sc->d_tri_bary64, sc->eps, pts_e, depth_e, rx_e, tri_e, edge,
+                                                           status); RT_COUNT(ctx);
+        k_dedup<<<grid_for(ctx, pcap, 256), 256, 0, st>>>(P_e, pcap, D, off_e, rx_e, path_cand, depth_e, tri_e, pts_e,
+                                                          edge, sc->d_tri_n64, sc->d_tri_v, sc->diag, bits, words,
+                                                          c2 + 4); RT_COUNT(ctx);
+        k_row_count<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, counts); RT_COUNT(ctx);
+        k_scan<<<1, 1024, 0, st>>>(counts, n_rx, p->d_rx_offsets); RT_COUNT(ctx);
+        k_compact_paths<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(
+            n_rx, D, pcap, off_e, p->d_rx_offsets, path_cand, pts_e, depth_e, rx_e, tri_e, p->d_pts, p->d_depth,
+            p->d_rx, p->d_tri); RT_COUNT(ctx);
+        TCK(cudaGetLastError());
+        k_trace_check<<<1, 32, 0, st>>>(tw, off_e + n_rx, p->d_rx_offsets + n_rx, ucap, pcap, meta, status,
+                                        ctx->trace_async);
+        RT_COUNT(ctx);
+        k_trace_guard<<<grid_for(ctx, n_rx + 1, 256), 256, 0, st>>>(meta, p->d_rx_offsets, n_rx);
+        RT_COUNT(ctx);
+        TCK(cudaGetLastError());
+        p->P = pcap;   // the slots of the record arrays; set to the count below
+        rt_status rs = rt_launch_paths_records(ctx, p, meta);
+        if (rs != RT_OK) return fail(rs);
+        cudaFreeAsync(tmp, st);
+        if (ctx->trace_async) {
+            // no read-back: the paths are counted on the device; the scene keeps its
+            // capacities from the last trace that was read back
+            cudaFreeAsync(off_e, st);
+            p->K = Kc;
+            p->d_count = meta;
+            if (ctx->profile & 1) {
+                TCK(cudaEventRecord(ctx->ev[5], st));
+                ctx->stage_pending = 1;
             }
+            *out = p;
+            return RT_OK;
         }
-    }
-    cudaFreeAsync(path_cand, st);
-    cudaFreeAsync(edge, st);
-    rt_status s = rt_launch_paths_records(ctx, p);
-    if (s != RT_OK) return fail(s);
-    if (ctx->profile & 1) {
-        // read out by rt_collect_stage_times: the trace itself does not wait
-        TCK(cudaEventRecord(ctx->ev[5], st));
-        ctx->stage_pending = 1;
-    }
+
+        // ---------------- the one read-back: every count and capacity flag
+        int64_t* hp = ctx->h_pinned;
+        TCK(cudaMemcpyAsync(hp, tw, 32 * 8, cudaMemcpyDeviceToHost, st));
+        TCK(cudaMemcpyAsync(hp + 32, off_e + n_rx, 8, cudaMemcpyDeviceToHost, st));
+        TCK(cudaMemcpyAsync(hp + 33, p->d_rx_offsets + n_rx, 8, cudaMemcpyDeviceToHost, st));
+        cudaFreeAsync(off_e, st);
+        TCK(cudaStreamSynchronize(st));
+        const int32_t ovf1 = reinterpret_cast<const int32_t*>(hp + 8)[0];
+        const int64_t n_keys = hp[3];
+        const int32_t ovf2 = reinterpret_cast<const int32_t*>(hp + 24)[0];
+        const int64_t P_emit = hp[32], P_kept = hp[33];
+        if (ovf1 == 2) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "FP64 re-trace list overflow"));
+        bool again = false;
+        if (ovf1) {
+            if (sc->hash_cap >= ((size_t)1 << 31)) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "candidate hash table overflow"));
+            sc->hash_cap *= 4;
+            again = true;
+        }
+        if (n_keys > ucap) {
+            sc->uniq_hint = n_keys;
+            again = true;
+        }
+        if (ovf2) {
+            sc->queue_cap *= 4;
+            again = true;
+        }
+        if (P_emit > pcap) {
+            sc->paths_hint = P_emit;
+            again = true;
+        }
+        if (again) {
+            rt_paths_free(p);
+            continue;
+        }
+        sc->uniq_hint = n_keys;
+        sc->paths_hint = P_emit;
+        ctx->h_counters[7] += (n_keys + 1) * (int64_t)n_rx;
+        p->K = n_keys + 1;
+        p->P = P_kept;
+        if (ctx->profile & 1) {
+            // read out by rt_collect_stage_times: the trace itself does not wait
+            TCK(cudaEventRecord(ctx->ev[5], st));
+            ctx->stage_pending = 1;
+        }
 #undef TCK
-    *out = p;
-    return RT_OK;
+        *out = p;
+        return RT_OK;
+    }
 }
 
 // ===========================================================================
