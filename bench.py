@@ -530,6 +530,11 @@ def summary(line):
                         "fields_fwd_ms": g(line.get("diffraction"), "fields_fwd_ms"),
                         "fields_bwd_ms": g(line.get("diffraction"), "fields_bwd_ms")},
         "batch": {"trace_batched_ms": g(bt, "trace_batched_ms"), "trace_loop_ms": g(bt, "trace_loop_ms"),
+                  "trace_cal_loop_ms": g(bt, "trace_and_calibration", "loop_ms"),
+                  "trace_cal_graph_ms": g(bt, "trace_and_calibration", "graph_ms"),
+                  "small_trace_cal_loop_ms": g(bt, "small_cities_trace_and_calibration", "loop_ms"),
+                  "small_trace_cal_batched_ms": g(bt, "small_cities_trace_and_calibration", "batched_ms"),
+                  "small_trace_cal_graph_ms": g(bt, "small_cities_trace_and_calibration", "graph_ms"),
                   "calibration_graph_ms": g(bt, "calibration_graph_ms"),
                   "calibration_loop_ms": g(bt, "calibration_loop_ms")},
     }
@@ -1202,6 +1207,15 @@ def time_batch(rt, ctx, args, reps=3):
             st()
     cal_graph = [timed(g.replay)[0] for _ in range(10)]
     cal_loop = [timed(lambda: [st() for st in steps_l])[0] for _ in range(10)]
+    del g, step_b, steps_l, pb, pl
+    # trace + calibration of every scene: a per-scene loop, one batched pipeline,
+    # and that pipeline replayed from one CUDA graph (the traces do not wait for
+    # the host in any of the three)
+    full = trace_calibration_forms(rt, ctx, scenes, txs, rxs, n_rays, depth, c0, dev, reps)
+    small_idx = [i for i, c in enumerate(cities) if c.n_tris < 3500]
+    small = trace_calibration_forms(rt, ctx, [scenes[i] for i in small_idx], [txs[i] for i in small_idx],
+                                    [rxs[i] for i in small_idx], 100_000, depth, c0, dev, 20)
+    small.update({"scenes": small_idx, "n_tris": [cities[i].n_tris for i in small_idx], "rays_per_scene": 100_000})
     return {"workload": "city_batch", "n_scenes": len(cities), "n_tris": [c.n_tris for c in cities],
             "n_rx": int(sum(c.n_rx for c in cities)), "rays_per_scene": n_rays, "max_depth": depth,
             "n_paths": pb.n_paths, "n_candidates": pb.n_candidates,
@@ -1209,8 +1223,93 @@ def time_batch(rt, ctx, args, reps=3):
             "rays_per_s_batched": total_rays / (np.median(t_batch) * 1e-3),
             "rays_per_s_loop": total_rays / (np.median(t_loop) * 1e-3),
             "calibration_graph_ms": float(np.median(cal_graph)), "calibration_loop_ms": float(np.median(cal_loop)),
+            "trace_and_calibration": full, "small_cities_trace_and_calibration": small,
             "autotuned_blocks_per_sm": {"sbr": tuned[0], "pairs": tuned[1], "visibility": tuned[2]},
             "autotune_stage_ms": tune_ms}
+
+
+def trace_calibration_forms(rt, ctx, scenes, txs, rxs, n_rays, depth, c0, dev, reps):
+    """Trace + calibration step (fields, fused CFR + power MSE + adjoint at 256
+    subcarriers, fields adjoint) of every scene, three ways: a loop of per-scene
+    rt_trace_paths and calibration calls, one rt_trace_batch pipeline with one
+    calibration over all receivers, and that pipeline captured in one CUDA graph
+    and replayed.  Traces do not wait for the host (rt_set_trace_async; inside the
+    graph they cannot); the median of `reps` timed runs on the stream, L2 not
+    flushed (the scenes and paths are the step's working set)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    fc, df, N, f = c0.f_center_hz, c0.delta_f_hz, c0.n_sub, c0.freq_hz
+    eps = torch.tensor(c0.eps_r, device=dev)
+    sig = torch.tensor(c0.sigma, device=dev)
+    eps_t, sig_t = (eps * 1.2).contiguous(), (sig * 0.7).contiguous()
+
+    def target(p):
+        a = rt.eval_fields(ctx, p, eps, sig, f)
+        T = (rt.cfr(ctx, p.rx_offsets, a, p.tau, fc, df, N).abs() ** 2).float().contiguous()
+        m = T.mean(1)
+        return T, torch.where(m > 0, 1 / torch.where(m > 0, m, torch.ones_like(m)), torch.zeros_like(m)).float()
+
+    pb = rt.trace_batch(ctx, scenes, txs, rxs, n_rays, depth)          # capacities, targets
+    Tb, wb = target(pb)
+    tl = [target(rt.trace_paths(ctx, scenes[i], txs[i], rxs[i], n_rays, depth)) for i in range(len(scenes))]
+    loss = torch.zeros(1, device=dev)
+    ge, gs, gg = torch.zeros_like(eps), torch.zeros_like(sig), torch.zeros(2, device=dev)
+
+    def calibrate(p, T, w):
+        a = rt.eval_fields(ctx, p, eps_t, sig_t, f)
+        _, ga, _ = rt.cfr_power_mse_fused(ctx, p.rx_offsets, a, p.tau, fc, df, N, T, w, loss=loss)
+        rt.eval_fields_backward(ctx, p, eps_t, sig_t, f, ga, ge, gs, gg)
+
+    def step_batch():
+        p = rt.trace_batch(ctx, scenes, txs, rxs, n_rays, depth)
+        calibrate(p, Tb, wb)
+        return p
+
+    def step_loop():
+        for i in range(len(scenes)):
+            calibrate(rt.trace_paths(ctx, scenes[i], txs[i], rxs[i], n_rays, depth), *tl[i])
+
+    def timed(fn, n):
+        ts = []
+        for _ in range(n):
+            torch.cuda.synchronize()
+            s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            fn()
+            e0.record(stream)
+            e0.synchronize()
+            ts.append(s0.elapsed_time(e0))
+        return float(np.median(ts))
+
+    rt.set_trace_async(ctx, True)
+    try:
+        for _ in range(2):
+            step_loop()
+            step_batch()
+        t_loop = timed(step_loop, reps)
+        t_batch = timed(step_batch, reps)
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            step_batch()
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            pg = step_batch()
+        g.replay()
+        t_graph = timed(g.replay, reps)
+    finally:
+        rt.set_trace_async(ctx, False)
+    torch.cuda.synchronize()
+    if ctx.status_word() != 0:
+        raise RuntimeError("device status set during the batched trace measurement")
+    pg.resolve()
+    if pg.n_paths != pb.n_paths:
+        raise RuntimeError("the graph-replayed batch found a different number of paths")
+    del g, pg
+    return {"n_scenes": len(scenes), "n_paths": pb.n_paths, "loop_ms": t_loop, "batched_ms": t_batch,
+            "graph_ms": t_graph, "reps": reps}
 
 
 def time_learned(rt, ctx, args, train_steps=150, timed_steps=20, warm_steps=3):

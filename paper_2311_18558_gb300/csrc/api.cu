@@ -2,6 +2,8 @@
 // field calls.  Tracing lives in trace.cu, CFR calls in cfr.cu.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -31,6 +33,10 @@ rt_status rt_cuda_fail(rt_ctx* ctx, cudaError_t e, const char* what) {
 
 rt_status rt_scratch(rt_ctx* ctx, size_t bytes, void** base) {
     if (bytes > ctx->scratch_bytes) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(ctx->stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            return rt_fail(ctx, RT_ERR_CAPACITY,
+                           "the scratch arena would grow inside a stream capture: run the call once before capturing");
         if (ctx->scratch) RT_CK(ctx, cudaFreeAsync(ctx->scratch, ctx->stream));
         ctx->scratch = nullptr;
         ctx->scratch_bytes = 0;
@@ -159,8 +165,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_create(int device
     ctx->num_sms = prop.multiProcessorCount;
     if (cudaMalloc((void**)&ctx->d_status, sizeof(int32_t)) != cudaSuccess ||
         cudaMemset(ctx->d_status, 0, sizeof(int32_t)) != cudaSuccess ||
-        cudaMallocHost((void**)&ctx->h_pinned, 64 * 8) != cudaSuccess ||
-        cudaMalloc((void**)&ctx->d_trace_words, 64 * 8) != cudaSuccess) {
+        cudaMallocHost((void**)&ctx->h_pinned, RT_TRACE_WORDS * 8) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->d_trace_words, RT_TRACE_WORDS * 8) != cudaSuccess) {
         delete ctx;
         return RT_ERR_OOM;
     }
@@ -236,6 +242,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_destroy(rt_ctx* c
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->d_trace_words) cudaFree(ctx->d_trace_words);
+    if (ctx->batch_comb && --ctx->batch_comb->refs == 0) rt_scene_free(ctx->batch_comb);
     loss_scratch_release(ctx);
     delete ctx;
     return RT_OK;
@@ -549,6 +556,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_upload(rt_c
     }
 
     rt_scene* sc = new rt_scene();
+    static std::atomic<uint64_t> serials{0};
+    sc->serial = ++serials;
     sc->ctx = ctx;
     sc->n_tris = n_tris;
     sc->n_nodes = (int)dn.size();
@@ -635,7 +644,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_paths_free(rt_pat
                     p->d_mc,         p->d_Dm, p->d_pts,   p->d_cand, p->d_dir, p->d_scat};
     for (void* q : ptrs)
         if (q) cudaFreeAsync(q, st);
-    if (p->owned_scene) {
+    if (p->owned_scene && --p->owned_scene->refs == 0) {
         cudaStreamSynchronize(st);
         rt_scene_free(p->owned_scene);
     }

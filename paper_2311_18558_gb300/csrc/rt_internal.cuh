@@ -6,6 +6,7 @@
 
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "rt103.h"
 
@@ -18,6 +19,8 @@
 #define RT_MAX_VISITS (1 << 20)        // node-visit bound of one traversal
 
 // ---------------------------------------------------------------- handles
+#define RT_TRACE_WORDS 1024   // device trace words and pinned host words per context
+
 struct rt_ctx {
     int device = 0;
     int num_sms = 0;
@@ -27,10 +30,14 @@ struct rt_ctx {
     // reusable scratch arena (grown on demand, freed with the context)
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
-    // pinned host words for small readbacks (64 words)
+    // pinned host words for small readbacks (RT_TRACE_WORDS)
     int64_t* h_pinned = nullptr;
-    // device words of one trace (64): stage counters and capacity flags, read back once at its end
+    // device words of one trace (RT_TRACE_WORDS): stage counters and capacity flags,
+    // read back once at its end (batched traces: per-scene counts from word 64 on)
     unsigned long long* d_trace_words = nullptr;
+    int64_t batch_paths_hint = 0;       // emitted paths of the last batched trace (0: none yet)
+    struct rt_scene* batch_comb = nullptr;   // combined triangle tables of the last batch (one reference)
+    std::vector<uint64_t> batch_key;    // serials of that batch's scenes
     // instrumentation
     int64_t launches = 0;              // kernels launched through this context
     int32_t profile = 0;               // bit 0: trace stage events, bit 1: traversal counters
@@ -88,6 +95,8 @@ struct rt_scene {
     int64_t paths_hint = 0;            // emitted paths of the last trace (0: none yet)
     uint8_t* h_is_pec = nullptr;       // host copy of the material PEC flags (batch checks)
     bool owns_tables_only = false;     // combined batch scene: no BVH, tables owned here
+    int32_t refs = 0;                  // combined batch scene: paths objects and the context cache using it
+    uint64_t serial = 0;               // unique per uploaded scene (keys the batch cache)
     // wedges for diffraction, built at the first rt_trace_diffraction / rt_scene_wedges
     int32_t n_wedges = -1;             // -1: not built yet
     double* d_wedge = nullptr;         // 14 doubles per wedge: start vertex, e, t0, n0 (3 each), length, n

@@ -1576,9 +1576,15 @@ static rt_status ray_schedule(rt_ctx* ctx, int64_t n, RaySched* out) {
     return RT_OK;
 }
 
+static bool stream_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// Stage events of the trace (profiling bit 0); none inside a stream capture.
 static void mark(rt_ctx* ctx, int k) {
     if (k == 0) ctx->stage_pending = 0;   // a new trace: unread stage times of the last one are dropped
-    if (ctx->profile & 1) cudaEventRecord(ctx->ev[k], ctx->stream);
+    if ((ctx->profile & 1) && !stream_capturing(ctx->stream)) cudaEventRecord(ctx->ev[k], ctx->stream);
 }
 
 struct Arena {
@@ -1631,6 +1637,12 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
     int32_t* status = rt_status_ptr(ctx);
     const size_t stack_bytes = (size_t)RT_STACK * TRACE_THREADS * sizeof(int);
     const size_t vis_bytes = (size_t)(RT_STACK + VIS_CAND_CAP) * TRACE_THREADS * sizeof(int);
+    // inside a stream capture (a CUDA graph) the trace does not wait: its capacities
+    // come from an earlier trace of the scene outside the capture
+    const bool in_capture = stream_capturing(st);
+    if (in_capture && (sc->uniq_hint == 0 || sc->paths_hint == 0))
+        return rt_fail(ctx, RT_ERR_INVALID_ARG, "a trace inside a stream capture needs an earlier trace of the scene");
+    const bool async = ctx->trace_async || in_capture;
 
     // One pass of the whole pipeline with buffers sized from capacities (the hash
     // table, the unique candidates, the visibility queue and the paths: the scene
@@ -1648,7 +1660,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         if (attempt >= 8) return rt_fail(ctx, RT_ERR_CAPACITY, "trace capacities did not converge");
         const size_t cap = sc->hash_cap;
         // unique keys: the last count with room, at most the table's limit
-        int64_t ucap = std::max<int64_t>(1024, sc->uniq_hint + sc->uniq_hint / 4 + 256);
+        int64_t ucap = std::max<int64_t>(1024, sc->uniq_hint + sc->uniq_hint / 8 + 256);
         ucap = std::min<int64_t>(ucap, (int64_t)(cap / 2));
         const bool rank_sort = ucap <= RANK_SORT_MAX;
         int64_t n_pad = SORT_BLOCK;
@@ -1838,7 +1850,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
             TCK(cudaStreamSynchronize(st));
             sc->paths_hint = std::max<int64_t>(1, ctx->h_pinned[0]);
         }
-        const int64_t pcap = std::max<int64_t>(1024, sc->paths_hint + sc->paths_hint / 4 + 1024);
+        const int64_t pcap = std::max<int64_t>(1024, sc->paths_hint + sc->paths_hint / 8 + 1024);
 
         // ---------------- emission (pcap slots), the duplicate rule, then the kept
         // paths compacted into the final arrays
@@ -1888,8 +1900,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
             n_rx, D, pcap, off_e, p->d_rx_offsets, path_cand, pts_e, depth_e, rx_e, tri_e, p->d_pts, p->d_depth,
             p->d_rx, p->d_tri); RT_COUNT(ctx);
         TCK(cudaGetLastError());
-        k_trace_check<<<1, 32, 0, st>>>(tw, off_e + n_rx, p->d_rx_offsets + n_rx, ucap, pcap, meta, status,
-                                        ctx->trace_async);
+        k_trace_check<<<1, 32, 0, st>>>(tw, off_e + n_rx, p->d_rx_offsets + n_rx, ucap, pcap, meta, status, async);
         RT_COUNT(ctx);
         k_trace_guard<<<grid_for(ctx, n_rx + 1, 256), 256, 0, st>>>(meta, p->d_rx_offsets, n_rx);
         RT_COUNT(ctx);
@@ -1898,13 +1909,13 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         rt_status rs = rt_launch_paths_records(ctx, p, meta);
         if (rs != RT_OK) return fail(rs);
         cudaFreeAsync(tmp, st);
-        if (ctx->trace_async) {
+        if (async) {
             // no read-back: the paths are counted on the device; the scene keeps its
             // capacities from the last trace that was read back
             cudaFreeAsync(off_e, st);
             p->K = Kc;
             p->d_count = meta;
-            if (ctx->profile & 1) {
+            if ((ctx->profile & 1) && !in_capture) {
                 TCK(cudaEventRecord(ctx->ev[5], st));
                 ctx->stage_pending = 1;
             }
@@ -2198,16 +2209,43 @@ __global__ void k_table_compact_batch(const unsigned long long* __restrict__ tab
         int leader = __ffs(m) - 1;
         if (lane == leader) base = atomicAdd(counts + s, (unsigned long long)__popc(m));
         base = __shfl_sync(FULL, base, leader);
-        if (k) out[s * out_stride + base + __popc(m & ((1u << lane) - 1))] = k;
+        const unsigned long long slot = base + __popc(m & ((1u << lane) - 1));
+        if (k && slot < out_stride) out[s * out_stride + slot] = k;   // beyond: counted, read as an overflow
     }
 }
 
-// Image sources of every candidate of every scene (global candidate index).
+// The candidate list of every scene: LoS, then its sorted keys (at most the
+// scene's slots minus one; the count comes from the compaction); K of each scene
+// is stored in K_dev.
+__global__ void k_cand_keys_batch(const uint64_t* __restrict__ sorted, uint64_t sort_stride,
+                                  const unsigned long long* __restrict__ counts, const int64_t* __restrict__ cand_off,
+                                  int n, uint64_t* __restrict__ cand, int64_t* __restrict__ K_dev) {
+    const int64_t KT = cand_off[n];
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < KT; k += (int64_t)gridDim.x * blockDim.x) {
+        const int s = find_seg(cand_off, n + 1, k);
+        const int64_t local = k - cand_off[s];
+        const int64_t ns = (int64_t)min(counts[s], (unsigned long long)(cand_off[s + 1] - cand_off[s] - 1));
+        if (local == 0) {
+            cand[k] = 0ull;
+            K_dev[s] = ns + 1;
+        } else if (local <= ns) {
+            cand[k] = sorted[(uint64_t)s * sort_stride + (uint64_t)(local - 1)];
+        }
+    }
+}
+
+// Image sources of every candidate of every scene (global candidate index); the
+// slots of a scene from its K_dev on are marked empty (depth -1).
 __global__ void k_candidates_batch(const uint64_t* __restrict__ keys, int64_t K, int D, const SceneDev* sd,
-                                   const int64_t* cand_off, int n, int32_t* cand_depth, int32_t* cand_tri,
-                                   double* img64, float4* img32) {
+                                   const int64_t* cand_off, int n, const int64_t* __restrict__ K_dev,
+                                   int32_t* cand_depth, int32_t* cand_tri, double* img64, float4* img32) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
-        const SceneDev& d = sd[find_seg(cand_off, n + 1, k)];
+        const int sc = find_seg(cand_off, n + 1, k);
+        if (k - cand_off[sc] >= K_dev[sc]) {
+            cand_depth[k] = -1;
+            continue;
+        }
+        const SceneDev& d = sd[sc];
         uint64_t key = keys[k];
         int q = rt_key_depth(key);
         cand_depth[k] = q;
@@ -2400,7 +2438,7 @@ __global__ void k_row_count_batch(const uint32_t* __restrict__ bits, const int64
 
 __global__ void k_expand_batch(const uint32_t* __restrict__ bits, const int64_t* rx_off, const int64_t* cand_off,
                                const int64_t* bits_off, int n, const int64_t* __restrict__ offsets, int32_t* path_rx,
-                               int32_t* path_cand) {
+                               int32_t* path_cand, int64_t cap) {
     const int lane = threadIdx.x & 31;
     const int64_t R = rx_off[n];
     for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < R;
@@ -2422,8 +2460,10 @@ __global__ void k_expand_batch(const uint32_t* __restrict__ bits, const int64_t*
             while (b) {
                 int bit = __ffs(b) - 1;
                 b &= b - 1;
-                path_rx[my] = (int32_t)g;
-                path_cand[my] = (int32_t)(cand_off[s] + w * 32 + bit);
+                if (my < cap) {
+                    path_rx[my] = (int32_t)g;
+                    path_cand[my] = (int32_t)(cand_off[s] + w * 32 + bit);
+                }
                 my++;
             }
             pos += __shfl_sync(FULL, incl, 31);
@@ -2432,10 +2472,12 @@ __global__ void k_expand_batch(const uint32_t* __restrict__ bits, const int64_t*
 }
 
 // FP64 points of every path; triangle slots carry global (offset) ids.
-__global__ void k_points_batch(CandView C, int64_t P, int D, const SceneDev* sd, const int64_t* cand_off, int n,
-                               const int32_t* __restrict__ path_rx, const int32_t* __restrict__ path_cand,
-                               const double* __restrict__ rx, double* pts_out, int32_t* depth_out, int32_t* rx_out,
-                               int32_t* tri_out, int32_t* edge_flag, int32_t* status) {
+__global__ void k_points_batch(CandView C, const int64_t* __restrict__ P_dev, int64_t cap, int D, const SceneDev* sd,
+                               const int64_t* cand_off, int n, const int32_t* __restrict__ path_rx,
+                               const int32_t* __restrict__ path_cand, const double* __restrict__ rx, double* pts_out,
+                               int32_t* depth_out, int32_t* rx_out, int32_t* tri_out, int32_t* edge_flag,
+                               int32_t* status) {
+    const int64_t P = min(*P_dev, cap);   // also the slot stride of tri_out
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t kg = path_cand[i];
         int r = path_rx[i];
@@ -2464,19 +2506,21 @@ __global__ void k_points_batch(CandView C, int64_t P, int D, const SceneDev* sd,
 
 // Duplicate rule over all scenes (global path, receiver, triangle and
 // candidate indices; bits cleared in the scene's own bitmask layout).
-__global__ void k_dedup_batch(int64_t P, int D, const int64_t* __restrict__ path_off, const int32_t* __restrict__ path_rx,
-                              const int32_t* __restrict__ path_cand, const int32_t* __restrict__ depth,
+__global__ void k_dedup_batch(const int64_t* __restrict__ P_dev, int64_t cap, int D,
+                              const int64_t* __restrict__ path_off, const int32_t* __restrict__ path_rx,
+                              int32_t* __restrict__ path_cand, const int32_t* __restrict__ depth,
                               const int32_t* __restrict__ tri, const double* __restrict__ pts,
                               const int32_t* __restrict__ edge_flag, const double* __restrict__ tri_n64,
                               const float4* __restrict__ tri_v, double diag, const int64_t* rx_off,
                               const int64_t* cand_off, const int64_t* bits_off, int n, uint32_t* bits,
                               unsigned long long* drops) {
+    const int64_t P = min(*P_dev, cap);
     const double tol2 = (1e-9 * diag) * (1e-9 * diag);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         if (!edge_flag[i]) continue;
         int r = path_rx[i];
         int q = depth[i];
-        for (int64_t j = path_off[r]; j < path_off[r + 1]; ++j) {
+        for (int64_t j = path_off[r]; j < path_off[r + 1] && j < P; ++j) {
             if (j == i || !edge_flag[j] || depth[j] != q) continue;
             bool same = true;
             for (int b = 0; b < q && same; ++b)
@@ -2502,15 +2546,138 @@ __global__ void k_dedup_batch(int64_t P, int D, const int64_t* __restrict__ path
                 const int64_t kl = path_cand[i] - cand_off[s];
                 atomicAnd(bits + bits_off[s] + (r - rx_off[s]) * words + (kl >> 5), ~(1u << (kl & 31)));
                 atomicAdd(drops, 1ull);
+                path_cand[i] = -1;   // dropped (only this thread reads path_cand[i])
                 break;
             }
         }
     }
 }
 
+// The counts and capacity flags of a batched pass (as k_trace_check): the scenes'
+// unique keys against their slots, the emitted paths against the path slots.
+__global__ void k_batch_check(const int32_t* __restrict__ f1, const int32_t* __restrict__ f2,
+                              const unsigned long long* __restrict__ counts, const int64_t* __restrict__ cand_off, int n,
+                              const int64_t* __restrict__ P_emit, const int64_t* __restrict__ P_kept, int64_t pcap,
+                              int64_t* meta, int32_t* status, int report) {
+    if (threadIdx.x != 0) return;
+    bool ovf = f1[0] != 0 || f2[0] != 0 || *P_emit > pcap;
+    int64_t K = 0;
+    for (int s = 0; s < n; ++s) {
+        const int64_t slots = cand_off[s + 1] - cand_off[s] - 1;
+        if ((int64_t)counts[s] > slots) ovf = true;
+        K += min((int64_t)counts[s], slots) + 1;
+    }
+    meta[0] = ovf ? 0 : min(*P_kept, pcap);
+    meta[1] = K;
+    meta[2] = f1[0] == 2 ? 2 : (ovf ? 1 : 0);
+    if (ovf && report) rt_set_status(status, RT_ERR_CAPACITY);
+}
+
 }  // namespace
 
-// Candidate cap per scene of one batch: hash tables of `cap` entries.
+// Per-call metadata of a batch (scene descriptors, prefix arrays) written by
+// kernels that carry it in their parameters, so that a captured batch keeps its
+// own copy (no host buffer has to outlive the graph).
+constexpr int META_SCENES = 16;
+struct SceneChunk {
+    int first, count;
+    SceneDev sd[META_SCENES];
+};
+__global__ void k_put_scenes(SceneChunk c, SceneDev* out) {
+    if ((int)threadIdx.x < c.count) out[c.first + threadIdx.x] = c.sd[threadIdx.x];
+}
+constexpr int META_I64 = 256;
+struct I64Chunk {
+    int first, count;
+    int64_t v[META_I64];
+};
+__global__ void k_put_i64(I64Chunk c, int64_t* out) {
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) out[c.first + i] = c.v[i];
+}
+
+static rt_status put_scenes(rt_ctx* ctx, const std::vector<SceneDev>& h, SceneDev* d) {
+    for (size_t f = 0; f < h.size(); f += META_SCENES) {
+        SceneChunk c;
+        c.first = (int)f;
+        c.count = (int)std::min<size_t>(META_SCENES, h.size() - f);
+        for (int i = 0; i < c.count; ++i) c.sd[i] = h[f + i];
+        k_put_scenes<<<1, META_SCENES, 0, ctx->stream>>>(c, d);
+        RT_COUNT(ctx);
+    }
+    RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}
+
+static rt_status put_i64(rt_ctx* ctx, const std::vector<int64_t>& h, int64_t* d) {
+    for (size_t f = 0; f < h.size(); f += META_I64) {
+        I64Chunk c;
+        c.first = (int)f;
+        c.count = (int)std::min<size_t>(META_I64, h.size() - f);
+        for (int i = 0; i < c.count; ++i) c.v[i] = h[f + i];
+        k_put_i64<<<1, 128, 0, ctx->stream>>>(c, d);
+        RT_COUNT(ctx);
+    }
+    RT_CK_LAUNCH(ctx);
+    return RT_OK;
+}
+
+// Combined triangle tables of a batch (triangle ids offset per scene), cached in
+// the context for its last list of scenes (by serial number) and shared by
+// reference with the paths objects that use them.
+static rt_status batch_tables(rt_ctx* ctx, const rt_scene* const* scenes, int n, const std::vector<int64_t>& tri_off,
+                              rt_scene** out) {
+    std::vector<uint64_t> key(n);
+    for (int s = 0; s < n; ++s) key[s] = scenes[s]->serial;
+    if (ctx->batch_comb && ctx->batch_key == key) {
+        *out = ctx->batch_comb;
+        return RT_OK;
+    }
+    cudaStream_t st = ctx->stream;
+    const int n_mat = scenes[0]->n_materials;
+    rt_scene* comb = new rt_scene();
+    comb->ctx = ctx;
+    comb->owns_tables_only = true;
+    comb->n_tris = (int)tri_off[n];
+    comb->n_materials = n_mat;
+    comb->diag = 0.0;
+    for (int s = 0; s < n; ++s) comb->diag = std::max(comb->diag, scenes[s]->diag);
+    comb->eps = 1e-6 * comb->diag;
+    comb->refs = 1;   // the context cache
+    cudaError_t e = cudaMalloc((void**)&comb->d_tri_n64, (size_t)tri_off[n] * 32);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&comb->d_tri_v, (size_t)tri_off[n] * 48);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&comb->d_tri_material, (size_t)tri_off[n] * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&comb->d_is_pec, (size_t)std::max(n_mat, 1));
+    for (int s = 0; s < n && e == cudaSuccess; ++s) {
+        const rt_scene* sc = scenes[s];
+        e = cudaMemcpyAsync(comb->d_tri_n64 + 4 * tri_off[s], sc->d_tri_n64, (size_t)sc->n_tris * 32,
+                            cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(comb->d_tri_v + 3 * tri_off[s], sc->d_tri_v, (size_t)sc->n_tris * 48,
+                                cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(comb->d_tri_material + tri_off[s], sc->d_tri_material, (size_t)sc->n_tris * 4,
+                                cudaMemcpyDeviceToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(comb->d_is_pec, scenes[0]->d_is_pec, n_mat, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+        rt_scene_free(comb);
+        return rt_cuda_fail(ctx, e, "batch triangle tables");
+    }
+    comb->h_is_pec = new uint8_t[std::max(n_mat, 1)];
+    std::memcpy(comb->h_is_pec, scenes[0]->h_is_pec, n_mat);
+    if (ctx->batch_comb && --ctx->batch_comb->refs == 0) {
+        cudaStreamSynchronize(st);
+        rt_scene_free(ctx->batch_comb);
+    }
+    ctx->batch_comb = comb;
+    ctx->batch_key = key;
+    *out = comb;
+    return RT_OK;
+}
+
+// Batched trace with the structure of rt_trace_paths: capacities per scene (its
+// last unique keys) and for the batch's paths (the last batch's count), counts
+// read on the device, one read-back at the end (or none with rt_set_trace_async).
 extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
     rt_ctx* ctx, const rt_scene* const* scenes, int32_t n_scenes, const double* tx_host, const double* rx_dev,
     const int32_t* rx_counts_host, int64_t n_rays, int32_t max_depth, rt_paths** out) {
@@ -2541,8 +2708,12 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
     int32_t* status = rt_status_ptr(ctx);
     const size_t stack_bytes = (size_t)RT_STACK * TRACE_THREADS * sizeof(int);
     const size_t vis_bytes = (size_t)(RT_STACK + VIS_CAND_CAP) * TRACE_THREADS * sizeof(int);
-
-    // per-scene descriptors and prefix arrays on the device (in the paths' own memory)
+    const int64_t RT = rx_off[n];
+    rt_scene* comb = nullptr;
+    {
+        rt_status sc0 = batch_tables(ctx, scenes, n, tri_off, &comb);
+        if (sc0 != RT_OK) return sc0;
+    }
     std::vector<SceneDev> hsd(n);
     for (int s = 0; s < n; ++s) {
         const rt_scene* sc = scenes[s];
@@ -2551,66 +2722,97 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
                           make_float3((float)tx_host[3 * s], (float)tx_host[3 * s + 1], (float)tx_host[3 * s + 2]),
                           n_rays, (int32_t)tri_off[s]};
     }
-    SceneDev* d_sd = nullptr;
-    int64_t* d_offs = nullptr;   // ray_off, rx_off, then cand_off, pair_off, bits_off (filled later)
-    rt_paths* p = new rt_paths();
-    p->stream = st;
-    p->D = D;
-    p->R = (int)rx_off[n];
-    p->n_scenes = n;
-    p->h_scene_rx_off = new int64_t[n + 1];
-    p->h_scene_tri_off = new int64_t[n + 1];
-    for (int s = 0; s <= n; ++s) {
-        p->h_scene_rx_off[s] = rx_off[s];
-        p->h_scene_tri_off[s] = tri_off[s];
+    unsigned long long* tw = ctx->d_trace_words;
+    int32_t* f1 = reinterpret_cast<int32_t*>(tw + 8);      // SBR: hash overflow (1), re-trace list (2)
+    unsigned long long* c2 = tw + 16;                       // visibility queue count, .., [4] duplicates
+    int32_t* f2 = reinterpret_cast<int32_t*>(tw + 24);     // queue overflow
+    unsigned long long* uniq_dev = tw + 64;                 // per scene: keys inserted
+    unsigned long long* keys_dev = tw + 320;                // per scene: keys compacted
+    int64_t* K_dev = reinterpret_cast<int64_t*>(tw + 576);  // per scene: candidates
+    const int64_t redo_cap = std::max<int64_t>(1 << 16, ray_off[n] / 16);
+    const bool in_capture = stream_capturing(st);
+    if (in_capture) {
+        bool known = ctx->batch_paths_hint > 0;
+        for (int s = 0; s < n; ++s) known &= scenes[s]->uniq_hint > 0;
+        if (!known) return rt_fail(ctx, RT_ERR_INVALID_ARG, "a batch trace inside a stream capture needs an earlier trace");
     }
-    void* meta = nullptr;
-    auto fail = [&](rt_status s) {
-        if (meta) cudaFreeAsync(meta, st);
-        rt_paths_free(p);
-        return s;
-    };
+    const bool async = ctx->trace_async || in_capture;
+    for (int attempt = 0;; ++attempt) {
+        if (attempt >= 8) return rt_fail(ctx, RT_ERR_CAPACITY, "batch trace capacities did not converge");
+        size_t cap = 1u << 16;
+        for (int s = 0; s < n; ++s) cap = std::max(cap, scenes[s]->hash_cap);
+        std::vector<int64_t> ucap(n), cand_off(n + 1, 0), pair_off(n + 1, 0), bits_off(n + 1, 0);
+        int64_t sort_cap = SORT_BLOCK;
+        bool first = false;
+        for (int s = 0; s < n; ++s) {
+            const int64_t hint = scenes[s]->uniq_hint;
+            first |= hint == 0;
+            ucap[s] = std::min<int64_t>(std::max<int64_t>(1024, hint + hint / 8 + 256), (int64_t)(cap / 2));
+            while (sort_cap < ucap[s]) sort_cap <<= 1;
+            const int64_t K = ucap[s] + 1;
+            cand_off[s + 1] = cand_off[s] + K;
+            pair_off[s + 1] = pair_off[s] + ((K + PAIR_CC - 1) / PAIR_CC) * ((rx_off[s + 1] - rx_off[s] + 31) / 32);
+            bits_off[s + 1] = bits_off[s] + ((K + 31) / 32) * (rx_off[s + 1] - rx_off[s]);
+        }
+        const int64_t KT = cand_off[n];
+        if (KT > 0x7fffffffLL) return rt_fail(ctx, RT_ERR_CAPACITY, "more than 2^31 candidate slots in a batch");
+        size_t qcap = 1u << 20;
+        for (int s = 0; s < n; ++s) qcap = std::max(qcap, scenes[s]->queue_cap);
+
+        rt_paths* p = new rt_paths();
+        p->stream = st;
+        p->D = D;
+        p->R = (int)RT;
+        p->n_scenes = n;
+        p->scene = comb;
+        p->owned_scene = comb;
+        comb->refs++;
+        p->h_scene_rx_off = new int64_t[n + 1];
+        p->h_scene_tri_off = new int64_t[n + 1];
+        for (int s = 0; s <= n; ++s) {
+            p->h_scene_rx_off[s] = rx_off[s];
+            p->h_scene_tri_off[s] = tri_off[s];
+        }
+        void* meta = nullptr;
+        auto fail = [&](rt_status e) {
+            if (meta) cudaFreeAsync(meta, st);
+            rt_paths_free(p);
+            return e;
+        };
 #define BCK(call)                                                         \
     do {                                                                  \
         cudaError_t _e = (call);                                          \
         if (_e != cudaSuccess) return fail(rt_cuda_fail(ctx, _e, #call)); \
     } while (0)
-    BCK(cudaMallocAsync(&meta, sizeof(SceneDev) * n + sizeof(int64_t) * 5 * (n + 1) + 256, st));
-    d_sd = reinterpret_cast<SceneDev*>(meta);
-    d_offs = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(meta) + align_up(sizeof(SceneDev) * n, 64));
-    int64_t* d_ray_off = d_offs;
-    int64_t* d_rx_off = d_offs + (n + 1);
-    int64_t* d_cand_off = d_offs + 2 * (n + 1);
-    int64_t* d_pair_off = d_offs + 3 * (n + 1);
-    int64_t* d_bits_off = d_offs + 4 * (n + 1);
-    BCK(cudaMemcpyAsync(d_sd, hsd.data(), sizeof(SceneDev) * n, cudaMemcpyHostToDevice, st));
-    BCK(cudaMemcpyAsync(d_ray_off, ray_off.data(), 8 * (n + 1), cudaMemcpyHostToDevice, st));
-    BCK(cudaMemcpyAsync(d_rx_off, rx_off.data(), 8 * (n + 1), cudaMemcpyHostToDevice, st));
+        // per-scene descriptors and the prefix arrays
+        BCK(cudaMallocAsync(&meta, align_up(sizeof(SceneDev) * n, 64) + sizeof(int64_t) * 5 * (n + 1) + 256, st));
+        SceneDev* d_sd = reinterpret_cast<SceneDev*>(meta);
+        int64_t* d_offs = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(meta) + align_up(sizeof(SceneDev) * n, 64));
+        int64_t* d_ray_off = d_offs;
+        int64_t* d_rx_off = d_offs + (n + 1);
+        int64_t* d_cand_off = d_offs + 2 * (n + 1);
+        int64_t* d_pair_off = d_offs + 3 * (n + 1);
+        int64_t* d_bits_off = d_offs + 4 * (n + 1);
+        {
+            rt_status sm = put_scenes(ctx, hsd, d_sd);
+            std::vector<int64_t> offs;
+            for (const auto* v : {&ray_off, &rx_off, &cand_off, &pair_off, &bits_off}) offs.insert(offs.end(), v->begin(), v->end());
+            if (sm == RT_OK) sm = put_i64(ctx, offs, d_offs);
+            if (sm != RT_OK) return fail(sm);
+        }
 
-    // ---------------- SBR over all scenes, one persistent launch (+ FP64 re-trace)
-    size_t cap = 1u << 16;
-    for (int s = 0; s < n; ++s) cap = std::max(cap, const_cast<rt_scene*>(scenes[s])->hash_cap);
-    const int64_t total_rays = ray_off[n];
-    const int64_t redo_cap = std::max<int64_t>(1 << 16, total_rays / 16);
-    std::vector<int64_t> uniq(n);
-    uint64_t* sorted = nullptr;
-    size_t sort_cap = 0;
-    for (int attempt = 0;; ++attempt) {
-        sort_cap = std::max<size_t>(SORT_BLOCK, cap / 2);
-        size_t need = (size_t)n * cap * 8 + (size_t)n * sort_cap * 8 + (size_t)(2 * n + 8) * 8 + redo_cap * 16 + 17 * 256;
+        // ---------------- SBR over all scenes, one persistent launch (+ FP64 re-trace)
+        size_t need1 = (size_t)n * cap * 8 + (size_t)n * sort_cap * 8 + redo_cap * 16 + 8 * 256;
         void* base;
-        rt_status s0 = rt_scratch(ctx, need, &base);
+        rt_status s0 = rt_scratch(ctx, need1, &base);
         if (s0 != RT_OK) return fail(s0);
         Arena ar{(char*)base};
         unsigned long long* tables = ar.take<unsigned long long>((size_t)n * cap);
-        unsigned long long* counters = ar.take<unsigned long long>(2 * n + 8);   // uniq[n], compact[n], next, redo
-        int32_t* flags = ar.take<int32_t>(8);
         int64_t* redo = ar.take<int64_t>(redo_cap);
         uint64_t* redo_key = ar.take<uint64_t>(redo_cap);
-        sorted = ar.take<uint64_t>((size_t)n * sort_cap);
+        uint64_t* sorted = ar.take<uint64_t>((size_t)n * sort_cap);
         BCK(cudaMemsetAsync(tables, 0, (size_t)n * cap * 8, st));
-        BCK(cudaMemsetAsync(counters, 0, (2 * n + 8) * 8, st));
-        BCK(cudaMemsetAsync(flags, 0, 32, st));
+        BCK(cudaMemsetAsync(tw, 0, RT_TRACE_WORDS * 8, st));
         BatchSbr A;
         A.sd = d_sd;
         A.ray_off = d_ray_off;
@@ -2618,13 +2820,13 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         A.depth = D;
         A.tables = tables;
         A.cap = cap;
-        A.uniq = counters;
+        A.uniq = uniq_dev;
         A.uniq_limit = cap / 2;
-        A.overflow = flags;
-        A.next_ray = counters + 2 * n;
+        A.overflow = f1;
+        A.next_ray = tw + 1;
         A.redo = redo;
         A.redo_key = redo_key;
-        A.redo_count = counters + 2 * n + 1;
+        A.redo_count = tw + 2;
         A.redo_cap = redo_cap;
         A.status = status;
         A.counters = (ctx->profile & 2) ? ctx->d_counters : nullptr;
@@ -2642,32 +2844,34 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
         mark(ctx, 1);
-        int64_t* hp = ctx->h_pinned;   // 64 bytes: read counters in pieces
-        std::vector<unsigned long long> hu(n);
-        BCK(cudaMemcpyAsync(hp, flags, 4, cudaMemcpyDeviceToHost, st));
-        BCK(cudaStreamSynchronize(st));
-        int32_t ovf = *(int32_t*)hp;
-        BCK(cudaMemcpy(hu.data(), counters, 8 * n, cudaMemcpyDeviceToHost));
-        if (ovf == 2) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "FP64 re-trace list overflow"));
-        if (ovf) {
-            if (attempt >= 6 || cap >= ((size_t)1 << 30)) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "hash overflow"));
-            cap *= 4;
-            continue;
+        if (first) {
+            // some scene is traced for the first time: learn its unique keys
+            int64_t* hp = ctx->h_pinned;
+            BCK(cudaMemcpyAsync(hp, uniq_dev, 8 * n, cudaMemcpyDeviceToHost, st));
+            BCK(cudaStreamSynchronize(st));
+            bool grow = false;
+            for (int s = 0; s < n; ++s) {
+                rt_scene* sc = const_cast<rt_scene*>(scenes[s]);
+                if (sc->uniq_hint == 0) sc->uniq_hint = std::max<int64_t>(1, hp[s]);
+                grow |= hp[s] > ucap[s] && ucap[s] < (int64_t)(cap / 2);
+            }
+            if (grow) {
+                cudaFreeAsync(meta, st);
+                meta = nullptr;
+                rt_paths_free(p);
+                continue;
+            }
         }
-        for (int s = 0; s < n; ++s) {
-            uniq[s] = (int64_t)hu[s];
-            const_cast<rt_scene*>(scenes[s])->hash_cap = std::max(scenes[s]->hash_cap, cap);
-        }
-        BCK(cudaMemsetAsync(counters + n, 0, 8 * n, st));
+        // ---------------- keys of each scene sorted (length, lexicographic), at most its slots
         k_fill_u64<<<grid_for(ctx, (int64_t)n * sort_cap, 256), 256, 0, st>>>(sorted, (uint64_t)n * sort_cap, ~0ull);
         RT_COUNT(ctx);
         k_table_compact_batch<<<grid_for(ctx, (int64_t)n * cap, 256, 16), 256, 0, st>>>(tables, n, cap, sorted,
-                                                                                        sort_cap, counters + n);
+                                                                                        sort_cap, keys_dev);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
-        for (int s = 0; s < n; ++s) {   // bitonic sort of each scene's keys
+        for (int s = 0; s < n; ++s) {
             int64_t n_pad = SORT_BLOCK;
-            while (n_pad < uniq[s]) n_pad <<= 1;
+            while (n_pad < ucap[s]) n_pad <<= 1;
             uint64_t* keys = sorted + (size_t)s * sort_cap;
             k_bitonic_local<<<(unsigned)(n_pad / SORT_BLOCK), 1024, 0, st>>>(keys);
             RT_COUNT(ctx);
@@ -2681,66 +2885,31 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
             }
         }
         BCK(cudaGetLastError());
-        break;
-    }
 
-    // ---------------- candidates of all scenes (LoS first in each scene)
-    std::vector<int64_t> cand_off(n + 1, 0), pair_off(n + 1, 0), bits_off(n + 1, 0);
-    for (int s = 0; s < n; ++s) {
-        const int64_t K = uniq[s] + 1;
-        cand_off[s + 1] = cand_off[s] + K;
-        pair_off[s + 1] = pair_off[s] + ((K + PAIR_CC - 1) / PAIR_CC) * ((rx_off[s + 1] - rx_off[s] + 31) / 32);
-        bits_off[s + 1] = bits_off[s] + ((K + 31) / 32) * (rx_off[s + 1] - rx_off[s]);
-        ctx->h_counters[7] += K * (rx_off[s + 1] - rx_off[s]);
-    }
-    const int64_t KT = cand_off[n];
-    if (KT > 0x7fffffffLL) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "more than 2^31 candidates in a batch"));
-    p->K = KT;
-    BCK(cudaMemcpyAsync(d_cand_off, cand_off.data(), 8 * (n + 1), cudaMemcpyHostToDevice, st));
-    BCK(cudaMemcpyAsync(d_pair_off, pair_off.data(), 8 * (n + 1), cudaMemcpyHostToDevice, st));
-    BCK(cudaMemcpyAsync(d_bits_off, bits_off.data(), 8 * (n + 1), cudaMemcpyHostToDevice, st));
-    BCK(cudaMallocAsync((void**)&p->d_cand, KT * 8, st));
-    for (int s = 0; s < n; ++s) {
-        BCK(cudaMemsetAsync(p->d_cand + cand_off[s], 0, 8, st));
-        if (uniq[s] > 0)
-            BCK(cudaMemcpyAsync(p->d_cand + cand_off[s] + 1, sorted + (size_t)s * sort_cap, uniq[s] * 8,
-                                cudaMemcpyDeviceToDevice, st));
-    }
-    int32_t *cand_depth = nullptr, *cand_tri = nullptr;
-    double* img64 = nullptr;
-    float4* img32 = nullptr;
-    uint2* queue = nullptr;
-    uint32_t* bits = nullptr;
-    unsigned long long* counters = nullptr;
-    int32_t* flags = nullptr;
-    int64_t* counts = nullptr;
-    size_t qcap = 1u << 20;
-    for (int s = 0; s < n; ++s) qcap = std::max(qcap, scenes[s]->queue_cap);
-    for (int attempt = 0;; ++attempt) {
-        size_t need = KT * 4 + (size_t)D * KT * 4 + (size_t)D * KT * 24 + (size_t)D * KT * 16 + qcap * 8 +
-                      (size_t)bits_off[n] * 4 + 64 * 8 + (size_t)(rx_off[n] + 1) * 8 * 2 + qcap * 4 +
-                      2 * (size_t)(D + 1) * qcap * 16 + 20 * 256;
-        void* base;
-        rt_status s0 = rt_scratch(ctx, need, &base);
+        // ---------------- candidates of all scenes (LoS first in each scene)
+        BCK(cudaMallocAsync((void**)&p->d_cand, KT * 8, st));
+        k_cand_keys_batch<<<grid_for(ctx, KT, 256), 256, 0, st>>>(sorted, (uint64_t)sort_cap, keys_dev, d_cand_off, n,
+                                                                   p->d_cand, K_dev);
+        RT_COUNT(ctx);
+        size_t need2 = KT * 4 + (size_t)D * KT * 4 + (size_t)D * KT * 24 + (size_t)D * KT * 16 + qcap * 8 +
+                       (size_t)bits_off[n] * 4 + (size_t)(RT + 1) * 8 * 2 + qcap * 4 +
+                       2 * (size_t)(D + 1) * qcap * 16 + 20 * 256;
+        s0 = rt_scratch(ctx, need2, &base);
         if (s0 != RT_OK) return fail(s0);
-        Arena ar{(char*)base};
-        cand_depth = ar.take<int32_t>(KT);
-        cand_tri = ar.take<int32_t>((size_t)D * KT);
-        img64 = ar.take<double>((size_t)D * KT * 3);
-        img32 = ar.take<float4>((size_t)D * KT);
-        queue = ar.take<uint2>(qcap);
-        bits = ar.take<uint32_t>((size_t)bits_off[n]);
-        counters = ar.take<unsigned long long>(8);
-        flags = ar.take<int32_t>(8);
-        counts = ar.take<int64_t>(rx_off[n] + 1);
-        int32_t* seg_q = ar.take<int32_t>(qcap);
-        float4* seg_o = ar.take<float4>((size_t)(D + 1) * qcap);
-        float4* seg_d = ar.take<float4>((size_t)(D + 1) * qcap);
-        BCK(cudaMemsetAsync(counters, 0, 64, st));
-        BCK(cudaMemsetAsync(flags, 0, 32, st));
+        Arena ar2{(char*)base};
+        int32_t* cand_depth = ar2.take<int32_t>(KT);
+        int32_t* cand_tri = ar2.take<int32_t>((size_t)D * KT);
+        double* img64 = ar2.take<double>((size_t)D * KT * 3);
+        float4* img32 = ar2.take<float4>((size_t)D * KT);
+        uint2* queue = ar2.take<uint2>(qcap);
+        uint32_t* bits = ar2.take<uint32_t>((size_t)bits_off[n]);
+        int64_t* counts = ar2.take<int64_t>(RT + 1);
+        int32_t* seg_q = ar2.take<int32_t>(qcap);
+        float4* seg_o = ar2.take<float4>((size_t)(D + 1) * qcap);
+        float4* seg_d = ar2.take<float4>((size_t)(D + 1) * qcap);
         BCK(cudaMemsetAsync(bits, 0, (size_t)bits_off[n] * 4, st));
-        k_candidates_batch<<<grid_for(ctx, KT, 256), 256, 0, st>>>(p->d_cand, KT, D, d_sd, d_cand_off, n, cand_depth,
-                                                                    cand_tri, img64, img32);
+        k_candidates_batch<<<grid_for(ctx, KT, 256), 256, 0, st>>>(p->d_cand, KT, D, d_sd, d_cand_off, n, K_dev,
+                                                                    cand_depth, cand_tri, img64, img32);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
         BatchPairs PA;
@@ -2752,9 +2921,9 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         PA.n = n;
         PA.rx = rx_dev;
         PA.queue = queue;
-        PA.qcount = counters;
+        PA.qcount = c2;
         PA.qcap = qcap;
-        PA.overflow = flags;
+        PA.overflow = f2;
         mark(ctx, 2);
         k_pairs_batch<<<grid_for(ctx, pair_off[n] * 32, 256, ctx->tune_pairs_blocks_per_sm), 256, 0, st>>>(PA);
         RT_COUNT(ctx);
@@ -2769,7 +2938,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         VA.n = n;
         VA.rx = rx_dev;
         VA.queue = queue;
-        VA.qcount = counters;
+        VA.qcount = c2;
         VA.qcap = qcap;
         VA.bits = bits;
         VA.status = status;
@@ -2785,114 +2954,143 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
         mark(ctx, 4);
-        int64_t* hp = ctx->h_pinned;
-        BCK(cudaMemcpyAsync(hp, flags, 4, cudaMemcpyDeviceToHost, st));
-        BCK(cudaStreamSynchronize(st));
-        if (*(int32_t*)hp) {
-            if (attempt >= 6) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "visibility queue overflow"));
-            qcap *= 4;
-            continue;
-        }
-        for (int s = 0; s < n; ++s) const_cast<rt_scene*>(scenes[s])->queue_cap = std::max(scenes[s]->queue_cap, qcap);
-        break;
-    }
 
-    // ---------------- combined triangle tables of the batch (global triangle ids)
-    rt_scene* comb = new rt_scene();
-    p->owned_scene = comb;
-    p->scene = comb;
-    comb->ctx = ctx;
-    comb->owns_tables_only = true;
-    comb->n_tris = (int)tri_off[n];
-    comb->n_materials = n_mat;
-    comb->diag = 0.0;
-    for (int s = 0; s < n; ++s) comb->diag = std::max(comb->diag, scenes[s]->diag);
-    comb->eps = 1e-6 * comb->diag;
-    BCK(cudaMalloc((void**)&comb->d_tri_n64, (size_t)tri_off[n] * 32));
-    BCK(cudaMalloc((void**)&comb->d_tri_v, (size_t)tri_off[n] * 48));
-    BCK(cudaMalloc((void**)&comb->d_tri_material, (size_t)tri_off[n] * 4));
-    BCK(cudaMalloc((void**)&comb->d_is_pec, (size_t)std::max(n_mat, 1)));
-    for (int s = 0; s < n; ++s) {
-        const rt_scene* sc = scenes[s];
-        BCK(cudaMemcpyAsync(comb->d_tri_n64 + 4 * tri_off[s], sc->d_tri_n64, (size_t)sc->n_tris * 32,
-                            cudaMemcpyDeviceToDevice, st));
-        BCK(cudaMemcpyAsync(comb->d_tri_v + 3 * tri_off[s], sc->d_tri_v, (size_t)sc->n_tris * 48,
-                            cudaMemcpyDeviceToDevice, st));
-        BCK(cudaMemcpyAsync(comb->d_tri_material + tri_off[s], sc->d_tri_material, (size_t)sc->n_tris * 4,
-                            cudaMemcpyDeviceToDevice, st));
-    }
-    BCK(cudaMemcpyAsync(comb->d_is_pec, scenes[0]->d_is_pec, n_mat, cudaMemcpyDeviceToDevice, st));
-    comb->h_is_pec = new uint8_t[std::max(n_mat, 1)];
-    std::memcpy(comb->h_is_pec, scenes[0]->h_is_pec, n_mat);
-
-    // ---------------- emission over all receivers of all scenes
-    const int64_t RT = rx_off[n];
-    int32_t* path_cand = nullptr;
-    int32_t* edge = nullptr;
-    for (int pass = 0;; ++pass) {
+        // ---------------- emission over all receivers of all scenes (pcap slots),
+        // the duplicate rule, the kept paths compacted
+        int64_t* off_e = nullptr;
+        BCK(cudaMallocAsync((void**)&off_e, (size_t)(RT + 1) * 8, st));
         k_row_count_batch<<<grid_for(ctx, RT * 32, 256, 16), 256, 0, st>>>(bits, d_rx_off, d_cand_off, d_bits_off, n,
                                                                           counts);
         RT_COUNT(ctx);
-        if (!p->d_rx_offsets) BCK(cudaMallocAsync((void**)&p->d_rx_offsets, (size_t)(RT + 1) * 8, st));
+        k_scan<<<1, 1024, 0, st>>>(counts, (int)RT, off_e);
+        RT_COUNT(ctx);
+        BCK(cudaGetLastError());
+        if (ctx->batch_paths_hint == 0) {
+            BCK(cudaMemcpyAsync(ctx->h_pinned, off_e + RT, 8, cudaMemcpyDeviceToHost, st));
+            BCK(cudaStreamSynchronize(st));
+            ctx->batch_paths_hint = std::max<int64_t>(1, ctx->h_pinned[0]);
+        }
+        const int64_t pcap = std::max<int64_t>(1024, ctx->batch_paths_hint + ctx->batch_paths_hint / 8 + 1024);
+        const size_t Pa = (size_t)pcap;
+        char* tmp = nullptr;
+        RtCarve ct;
+        const size_t t_pts = ct.take(Pa * (D + 2) * 3 * 8), t_depth = ct.take(Pa * 4), t_rx = ct.take(Pa * 4),
+                     t_tri = ct.take(Pa * D * 4), t_cand = ct.take(Pa * 4), t_edge = ct.take(Pa * 4);
+        BCK(cudaMallocAsync((void**)&tmp, ct.off, st));
+        double* pts_e = reinterpret_cast<double*>(tmp + t_pts);
+        int32_t* depth_e = reinterpret_cast<int32_t*>(tmp + t_depth);
+        int32_t* rx_e = reinterpret_cast<int32_t*>(tmp + t_rx);
+        int32_t* tri_e = reinterpret_cast<int32_t*>(tmp + t_tri);
+        int32_t* path_cand = reinterpret_cast<int32_t*>(tmp + t_cand);
+        int32_t* edge = reinterpret_cast<int32_t*>(tmp + t_edge);
+        int64_t* pmeta = nullptr;
+        {
+            RtCarve c;
+            const size_t o_pts = c.take(Pa * (D + 2) * 3 * 8), o_depth = c.take(Pa * 4), o_rx = c.take(Pa * 4),
+                         o_tri = c.take(Pa * D * 4), o_meta = c.take(4 * 8);
+            char* b = nullptr;
+            BCK(cudaMallocAsync((void**)&b, c.off, st));
+            p->d_block_geo = b;
+            p->d_pts = reinterpret_cast<double*>(b + o_pts);
+            p->d_depth = reinterpret_cast<int32_t*>(b + o_depth);
+            p->d_rx = reinterpret_cast<int32_t*>(b + o_rx);
+            p->d_tri = reinterpret_cast<int32_t*>(b + o_tri);
+            pmeta = reinterpret_cast<int64_t*>(b + o_meta);
+        }
+        BCK(cudaMallocAsync((void**)&p->d_rx_offsets, (size_t)(RT + 1) * 8, st));
+        const int64_t* P_e = off_e + RT;
+        k_expand_batch<<<grid_for(ctx, RT * 32, 256, 16), 256, 0, st>>>(bits, d_rx_off, d_cand_off, d_bits_off, n,
+                                                                        off_e, rx_e, path_cand, pcap);
+        RT_COUNT(ctx);
+        CandView C{KT, cand_depth, cand_tri, img64, img32};
+        k_points_batch<<<grid_for(ctx, pcap, 256), 256, 0, st>>>(C, P_e, pcap, D, d_sd, d_cand_off, n, rx_e, path_cand,
+                                                                 rx_dev, pts_e, depth_e, rx_e, tri_e, edge, status);
+        RT_COUNT(ctx);
+        k_dedup_batch<<<grid_for(ctx, pcap, 256), 256, 0, st>>>(P_e, pcap, D, off_e, rx_e, path_cand, depth_e, tri_e,
+                                                                pts_e, edge, comb->d_tri_n64, comb->d_tri_v, comb->diag,
+                                                                d_rx_off, d_cand_off, d_bits_off, n, bits, c2 + 4);
+        RT_COUNT(ctx);
+        k_row_count_batch<<<grid_for(ctx, RT * 32, 256, 16), 256, 0, st>>>(bits, d_rx_off, d_cand_off, d_bits_off, n,
+                                                                          counts);
+        RT_COUNT(ctx);
         k_scan<<<1, 1024, 0, st>>>(counts, (int)RT, p->d_rx_offsets);
         RT_COUNT(ctx);
-        BCK(cudaGetLastError());
-        int64_t* hp = ctx->h_pinned;
-        BCK(cudaMemcpyAsync(hp, p->d_rx_offsets + RT, 8, cudaMemcpyDeviceToHost, st));
-        BCK(cudaStreamSynchronize(st));
-        const int64_t P = hp[0];
-        p->P = P;
-        if (pass > 0) {
-            cudaFreeAsync(p->d_pts, st);
-            cudaFreeAsync(p->d_depth, st);
-            cudaFreeAsync(p->d_rx, st);
-            cudaFreeAsync(p->d_tri, st);
-            cudaFreeAsync(path_cand, st);
-            cudaFreeAsync(edge, st);
-        }
-        const size_t Pa = std::max<int64_t>(P, 1);
-        BCK(cudaMallocAsync((void**)&p->d_pts, Pa * (D + 2) * 3 * 8, st));
-        BCK(cudaMallocAsync((void**)&p->d_depth, Pa * 4, st));
-        BCK(cudaMallocAsync((void**)&p->d_rx, Pa * 4, st));
-        BCK(cudaMallocAsync((void**)&p->d_tri, Pa * D * 4, st));
-        BCK(cudaMallocAsync((void**)&path_cand, Pa * 4, st));
-        BCK(cudaMallocAsync((void**)&edge, Pa * 4, st));
-        if (P > 0) {
-            k_expand_batch<<<grid_for(ctx, RT * 32, 256, 16), 256, 0, st>>>(bits, d_rx_off, d_cand_off, d_bits_off, n,
-                                                                           p->d_rx_offsets, p->d_rx, path_cand);
-            RT_COUNT(ctx);
-            CandView C{KT, cand_depth, cand_tri, img64, img32};
-            k_points_batch<<<grid_for(ctx, P, 256), 256, 0, st>>>(C, P, D, d_sd, d_cand_off, n, p->d_rx, path_cand,
-                                                                   rx_dev, p->d_pts, p->d_depth, p->d_rx, p->d_tri,
-                                                                   edge, status);
-            RT_COUNT(ctx);
-            BCK(cudaGetLastError());
-        }
-        if (pass > 0 || P == 0) break;
-        BCK(cudaMemsetAsync(counters + 4, 0, 8, st));
-        k_dedup_batch<<<grid_for(ctx, P, 256), 256, 0, st>>>(P, D, p->d_rx_offsets, p->d_rx, path_cand, p->d_depth,
-                                                             p->d_tri, p->d_pts, edge, comb->d_tri_n64, comb->d_tri_v,
-                                                             comb->diag, d_rx_off, d_cand_off, d_bits_off, n, bits,
-                                                             counters + 4);
+        k_compact_paths<<<grid_for(ctx, RT * 32, 256, 16), 256, 0, st>>>((int)RT, D, pcap, off_e, p->d_rx_offsets,
+                                                                         path_cand, pts_e, depth_e, rx_e, tri_e,
+                                                                         p->d_pts, p->d_depth, p->d_rx, p->d_tri);
+        RT_COUNT(ctx);
+        k_batch_check<<<1, 32, 0, st>>>(f1, f2, keys_dev, d_cand_off, n, P_e, p->d_rx_offsets + RT, pcap, pmeta, status,
+                                        async);
+        RT_COUNT(ctx);
+        k_trace_guard<<<grid_for(ctx, RT + 1, 256), 256, 0, st>>>(pmeta, p->d_rx_offsets, (int)RT);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
-        BCK(cudaMemcpyAsync(hp, counters + 4, 8, cudaMemcpyDeviceToHost, st));
+        p->P = pcap;
+        rt_status s1 = rt_launch_paths_records(ctx, p, pmeta);
+        if (s1 != RT_OK) return fail(s1);
+        cudaFreeAsync(tmp, st);
+        cudaFreeAsync(meta, st);
+        meta = nullptr;
+        if (async) {
+            cudaFreeAsync(off_e, st);
+            p->K = KT;
+            p->d_count = pmeta;
+            if ((ctx->profile & 1) && !in_capture) {
+                BCK(cudaEventRecord(ctx->ev[5], st));
+                ctx->stage_pending = 1;
+            }
+            *out = p;
+            return RT_OK;
+        }
+        // ---------------- the one read-back
+        int64_t* hp = ctx->h_pinned;
+        BCK(cudaMemcpyAsync(hp, pmeta, 3 * 8, cudaMemcpyDeviceToHost, st));
+        BCK(cudaMemcpyAsync(hp + 4, off_e + RT, 8, cudaMemcpyDeviceToHost, st));
+        BCK(cudaMemcpyAsync(hp + 8, tw + 8, 8, cudaMemcpyDeviceToHost, st));
+        BCK(cudaMemcpyAsync(hp + 9, tw + 24, 8, cudaMemcpyDeviceToHost, st));
+        BCK(cudaMemcpyAsync(hp + 16, keys_dev, 8 * n, cudaMemcpyDeviceToHost, st));
+        cudaFreeAsync(off_e, st);
         BCK(cudaStreamSynchronize(st));
-        if (hp[0] == 0) break;
-    }
-    cudaFreeAsync(path_cand, st);
-    cudaFreeAsync(edge, st);
-    cudaFreeAsync(meta, st);
-    meta = nullptr;
-    rt_status s1 = rt_launch_paths_records(ctx, p);
-    if (s1 != RT_OK) return fail(s1);
-    if (ctx->profile & 1) {
-        BCK(cudaEventRecord(ctx->ev[5], st));
-        ctx->stage_pending = 1;
-    }
+        const int32_t ovf1 = reinterpret_cast<const int32_t*>(hp + 8)[0];
+        const int32_t ovf2 = reinterpret_cast<const int32_t*>(hp + 9)[0];
+        const int64_t P_emit = hp[4];
+        if (ovf1 == 2) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "FP64 re-trace list overflow"));
+        bool again = false;
+        if (ovf1) {
+            if (cap >= ((size_t)1 << 30)) return fail(rt_fail(ctx, RT_ERR_CAPACITY, "hash overflow"));
+            for (int s = 0; s < n; ++s) const_cast<rt_scene*>(scenes[s])->hash_cap = cap * 4;
+            again = true;
+        }
+        for (int s = 0; s < n; ++s) {
+            rt_scene* sc = const_cast<rt_scene*>(scenes[s]);
+            if (hp[16 + s] > ucap[s]) again = true;
+            sc->uniq_hint = std::max<int64_t>(1, hp[16 + s]);
+        }
+        if (ovf2) {
+            for (int s = 0; s < n; ++s) const_cast<rt_scene*>(scenes[s])->queue_cap = qcap * 4;
+            again = true;
+        }
+        if (P_emit > pcap) again = true;
+        ctx->batch_paths_hint = std::max<int64_t>(1, P_emit);
+        if (again) {
+            rt_paths_free(p);
+            continue;
+        }
+        int64_t Ktot = 0;
+        for (int s = 0; s < n; ++s) {
+            Ktot += hp[16 + s] + 1;
+            ctx->h_counters[7] += (hp[16 + s] + 1) * (rx_off[s + 1] - rx_off[s]);
+        }
+        p->K = Ktot;
+        p->P = hp[0];
+        if (ctx->profile & 1) {
+            BCK(cudaEventRecord(ctx->ev[5], st));
+            ctx->stage_pending = 1;
+        }
 #undef BCK
-    *out = p;
-    return RT_OK;
+        *out = p;
+        return RT_OK;
+    }
 }
 
 // ===========================================================================

@@ -88,3 +88,55 @@ def test_autotuner(rt, ctx):
     rt.set_tuning(ctx, 8, 16, 8)
     with pytest.raises(rt.RtError):
         rt.set_tuning(ctx, 0, 16, 8)
+
+
+def test_batch_and_calibration_in_one_cuda_graph(rt):
+    # the batched trace (which waits for nothing inside a capture) and the
+    # calibration step (fields, fused CFR + loss + adjoint, fields adjoint) of the
+    # small cities captured in one CUDA graph; every replay gives the results of
+    # the same calls made outside the graph
+    ctx = rt.Context(0)
+    cities = scenegen.city_batch()
+    pick = [i for i, c in enumerate(cities) if c.n_tris < 3500]
+    n_rays, depth, N = 100_000, 4, 256
+    small = [cities[i] for i in pick]
+    scenes = [rt.Scene.from_synthetic(ctx, c) for c in small]
+    rxs = [torch.tensor(c.rx, dtype=torch.float64, device="cuda") for c in small]
+    txs = [c.tx for c in small]
+    sc0 = small[0]
+    fc, df, f = sc0.f_center_hz, 50e6 / N, sc0.freq_hz
+    eps = torch.tensor(sc0.eps_r * 1.2, device="cuda")
+    sig = torch.tensor(sc0.sigma * 0.7, device="cuda")
+    p0 = rt.trace_batch(ctx, scenes, txs, rxs, n_rays, depth)       # learns the capacities
+    a0 = rt.eval_fields(ctx, p0, torch.tensor(sc0.eps_r, device="cuda"), torch.tensor(sc0.sigma, device="cuda"), f)
+    T = (rt.cfr(ctx, p0.rx_offsets, a0, p0.tau, fc, df, N).abs() ** 2).float().contiguous()
+    w = (1.0 / T.mean(1).clamp_min(1e-30)).float().contiguous()
+
+    def step():
+        p = rt.trace_batch(ctx, scenes, txs, rxs, n_rays, depth)
+        a = rt.eval_fields(ctx, p, eps, sig, f)
+        loss, ga, _ = rt.cfr_power_mse_fused(ctx, p.rx_offsets, a, p.tau, fc, df, N, T, w)
+        ge, gs, gg = rt.eval_fields_backward(ctx, p, eps, sig, f, ga)
+        return p, loss, ge, gs
+
+    _, L_ref, ge_ref, gs_ref = step()
+    L_ref, ge_ref, gs_ref = L_ref.item(), ge_ref.cpu().numpy(), gs_ref.cpu().numpy()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()                                  # sizes every scratch buffer on this stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        p, loss, ge, gs = step()
+    for _ in range(3):
+        g.replay()
+        torch.cuda.synchronize()
+        assert loss.item() == pytest.approx(L_ref, rel=1e-6)
+        np.testing.assert_allclose(ge.cpu().numpy(), ge_ref, rtol=1e-5, atol=1e-12)
+        np.testing.assert_allclose(gs.cpu().numpy(), gs_ref, rtol=1e-5, atol=1e-12)
+        assert torch.equal(p.rx_offsets, p0.rx_offsets)
+    assert ctx.status_word() == 0
+    p.resolve()
+    assert p.n_paths == p0.n_paths
