@@ -1207,6 +1207,7 @@ def time_batch(rt, ctx, args, reps=3):
             st()
     cal_graph = [timed(g.replay)[0] for _ in range(10)]
     cal_loop = [timed(lambda: [st() for st in steps_l])[0] for _ in range(10)]
+    n_paths_b, n_cand_b = pb.n_paths, pb.n_candidates
     del g, step_b, steps_l, pb, pl
     # trace + calibration of every scene: a per-scene loop, one batched pipeline,
     # and that pipeline replayed from one CUDA graph (the traces do not wait for
@@ -1218,7 +1219,7 @@ def time_batch(rt, ctx, args, reps=3):
     small.update({"scenes": small_idx, "n_tris": [cities[i].n_tris for i in small_idx], "rays_per_scene": 100_000})
     return {"workload": "city_batch", "n_scenes": len(cities), "n_tris": [c.n_tris for c in cities],
             "n_rx": int(sum(c.n_rx for c in cities)), "rays_per_scene": n_rays, "max_depth": depth,
-            "n_paths": pb.n_paths, "n_candidates": pb.n_candidates,
+            "n_paths": n_paths_b, "n_candidates": n_cand_b,
             "trace_batched_ms": float(np.median(t_batch)), "trace_loop_ms": float(np.median(t_loop)),
             "rays_per_s_batched": total_rays / (np.median(t_batch) * 1e-3),
             "rays_per_s_loop": total_rays / (np.median(t_loop) * 1e-3),
@@ -1609,6 +1610,19 @@ def run_case(args):
     elif args.case == "diffuse":
         args.steps = max(args.steps, 1)
         out.update(time_diffuse(rt, ctx, flush, args))
+    elif args.case == "diffraction":
+        sc = scenegen.street_canyon()
+        scene = rt.Scene.from_synthetic(ctx, sc)
+        rx = torch.tensor(sc.rx, dtype=torch.float64, device=dev)
+        eps = torch.tensor(sc.eps_r, device=dev)
+        sig = torch.tensor(sc.sigma, device=dev)
+        spec = rt.trace_paths(ctx, scene, sc.tx, rx, sc.n_rays, sc.max_depth)
+        for _ in range(args.warmup + args.steps):
+            flush.zero_()
+            d = rt.trace_diffraction(ctx, scene, spec, sc.tx, rx)
+            a = rt.eval_fields_diffraction(ctx, d, eps, sig, sc.freq_hz)
+            rt.eval_fields_diffraction_backward(ctx, d, eps, sig, sc.freq_hz, torch.ones_like(a))
+        out["n_paths"] = d.n_paths
     elif args.case == "city_batch":
         cities = scenegen.city_batch()
         scenes = [rt.Scene.from_synthetic(ctx, c) for c in cities]
@@ -1630,7 +1644,8 @@ def main():
     ap.add_argument("--n-sub", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 16-city batched measurement")
-    ap.add_argument("--case", choices=["street_step", "indoor_calibration", "fields_hbm", "diffuse", "city_batch"],
+    ap.add_argument("--case", choices=["street_step", "indoor_calibration", "fields_hbm", "diffuse", "diffraction",
+                                       "city_batch"],
                     default=None,
                     help="run one workload alone (for profiler captures) instead of the benchmark")
     args = ap.parse_args()
