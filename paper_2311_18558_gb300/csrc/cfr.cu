@@ -43,15 +43,41 @@ struct PathPhase {
     float ulo;
 };
 
+// frac(x tau) of two doubles as a signed fixed-point fraction in units of 2^-64
+// (value in [-1/2, 1/2)), from the exact 106-bit product of the significands:
+// x tau = m_x m_t 2^(e_x + e_t - 2150) with biased exponents e, so the fraction
+// scaled by 2^64 is the product shifted right by s = 2086 - e_x - e_t (left if s
+// is negative; bits above 2^64 are whole cycles and drop out).  Integer
+// arithmetic only: the FP64 units of this GPU issue at a small fraction of the
+// integer rate.  Zeros and subnormals give 0 (|x tau| < 2^-1000 for any delay).
+__device__ __forceinline__ int64_t frac_mul(double x, double tau) {
+    const uint64_t bx = (uint64_t)__double_as_longlong(x), bt = (uint64_t)__double_as_longlong(tau);
+    const int ex = (int)((bx >> 52) & 0x7ff), et = (int)((bt >> 52) & 0x7ff);
+    if (ex == 0 || et == 0) return 0;
+    const uint64_t frac_bits = (1ull << 52) - 1;
+    const uint64_t mx = (bx & frac_bits) | (1ull << 52), mt = (bt & frac_bits) | (1ull << 52);
+    const uint64_t lo = mx * mt, hi = __umul64hi(mx, mt);
+    const int s = 2086 - ex - et;
+    uint64_t f = 0;
+    if (s >= 128) f = 0;
+    else if (s >= 64) f = hi >> (s - 64);
+    else if (s > 0) f = (hi << (64 - s)) | (lo >> s);
+    else if (s > -64) f = lo << (-s);
+    if ((bx ^ bt) >> 63) f = 0ull - f;   // frac(-y) = -frac(y)
+    return (int64_t)f;
+}
+
+// fixed-point fraction (units 2^-64) to float, to FP32 precision
+__device__ __forceinline__ float frac_to_float(int64_t f) { return (float)(int)(f >> 32) * 0x1p-32f; }
+
 __device__ __forceinline__ PathPhase path_phase(double tau, double f0, double df) {
     PathPhase p;
-    double x = f0 * tau;
-    p.p0 = (float)(x - rint(x));
-    double u = df * tau;
-    double ur = u - rint(u);
-    double hi = rint(ur * 4096.0) * (1.0 / 4096.0);
-    p.uhi = (float)hi;
-    p.ulo = (float)(ur - hi);
+    p.p0 = frac_to_float(frac_mul(f0, tau));
+    // u = frac(df tau) = hi + lo with hi the nearest multiple of 2^-12
+    const int64_t u = frac_mul(df, tau);
+    const int64_t hi = (int64_t)(((uint64_t)u + (1ull << 51)) & ~((1ull << 52) - 1));
+    p.uhi = (float)(int)(hi >> 52) * 0x1p-12f;
+    p.ulo = (float)(int)((u - hi) >> 20) * 0x1p-44f;
     return p;
 }
 
@@ -62,6 +88,18 @@ __device__ __forceinline__ float2 phasor(const PathPhase& p, int m) {
     x = x + (float)m * p.ulo;
     float s, c;
     sincospif(2.0f * x, &s, &c);
+    return make_float2(c, -s);
+}
+
+// As phasor(), with the hardware sine and cosine (absolute error about 4e-7 for
+// arguments in [-pi, pi]): the tensor-core tables, whose operands are split
+// into TF32 pairs and accumulated in FP32, stay within FP32 accuracy of H.
+__device__ __forceinline__ float2 phasor_fast(const PathPhase& p, int m) {
+    float x = (float)m * p.uhi;
+    x = x - rintf(x);
+    x = x + (float)m * p.ulo;
+    float s, c;
+    __sincosf(6.28318530717958647692f * x, &s, &c);
     return make_float2(c, -s);
 }
 
@@ -357,8 +395,6 @@ __global__ void __launch_bounds__(CFR_THREADS) k_cfr_fused(CfrShape S, const int
 
 constexpr int TC_THREADS = 128;
 constexpr int TC_CP = 16;                 // paths per chunk (at most 32: one per lane in the adjoint reduction)
-constexpr uint32_t TC_TMEM_COLS = 128;    // D (fwd) at column 0, Y' at TC_Y_COL
-constexpr uint32_t TC_Y_COL = 64;
 constexpr int TC_WAIT_LIMIT = 1 << 22;    // bounded mbarrier waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -463,6 +499,11 @@ struct TcDims {
     static constexpr int B_FLOATS = (NB * KA > 2 * TC_CP * KG) ? NB * KA : 2 * TC_CP * KG;
     static constexpr int NAH = 16, NAL = 8;                // A_i[c1] = Ah[c1 / 8] Al[c1 % 8]
     static constexpr int NF = NAH + NAL + N2;              // factor phasors per path
+    // TMEM: the forward D at column 0 (NB columns), the adjoint's Y' (2 TC_CP
+    // columns) from column Y_COL (32-column aligned); the allocation is the next
+    // power of two, so that up to 512 / TMEM_COLS CTAs share an SM's TMEM
+    static constexpr uint32_t Y_COL = NB < 32 ? 32 : NB;
+    static constexpr uint32_t TMEM_COLS = Y_COL + 2 * TC_CP <= 64 ? 64 : 128;
 };
 
 // c_i A_i at c1 = 8k, per path (forward operand factors)
@@ -502,7 +543,7 @@ __device__ __forceinline__ void tc_tables(const CfrShape& S, int64_t base, int n
     for (int e = t; e < n_pad * T::NF; e += TC_THREADS) {
         const int ii = e / T::NF, k = e - ii * T::NF;
         const int m = k < T::NAH ? k * T::NAL * N2 : k < T::NAH + T::NAL ? (k - T::NAH) * N2 : k - T::NAH - T::NAL;
-        const float2 f = phasor(tP[ii], m);
+        const float2 f = phasor_fast(tP[ii], m);
         tF[e] = f;
         if (a && k < T::NAH) tFc[ii * TC_NFC + k] = cmul(tC[ii], f);
     }
@@ -576,17 +617,18 @@ __device__ __forceinline__ float es_phi(float z) {
 // offset d0 = l0 - M x (in [-W/2, -W/2 + 1)), and the carrier phasor
 // exp(-j 2 pi f_c tau).  The cell position is formed in FP64, so the phase error
 // of any mode stays ~1e-7 rad.
-__device__ __forceinline__ void nu_place(double tau, double fc, double df, int M, int& l0, float& d0, float2& e) {
-    const double pc = fc * tau;
-    const float fr = (float)(pc - floor(pc));
+__device__ __forceinline__ void nu_place(double tau, double fc, double df, int logM, int& l0, float& d0, float2& e) {
     float sn, cs;
-    sincospif(-2.0f * fr, &sn, &cs);
+    sincospif(-2.0f * frac_to_float(frac_mul(fc, tau)), &sn, &cs);
     e = make_float2(cs, sn);
-    const double xd = df * tau;
-    const double xm = (xd - floor(xd)) * (double)M;
-    const double l0d = ceil(xm - 0.5 * NU_W);
-    l0 = (int)l0d;
-    d0 = (float)(l0d - xm);
+    // x M = I + phi: I the cell (top logM bits of frac(df tau) in [0, 1)), phi the
+    // remainder in [0, 1); l0 = ceil(x M - W/2) = I - W/2 + [phi > 0]
+    const uint64_t x = (uint64_t)frac_mul(df, tau);
+    const int I = (int)(x >> (64 - logM));
+    const uint64_t phi = x << logM;
+    const float phif = (float)(unsigned)(phi >> 40) * 0x1p-24f;
+    l0 = I - NU_W / 2 + (phi != 0 ? 1 : 0);
+    d0 = (phi != 0 ? 1.0f : 0.0f) - (float)(NU_W / 2) - phif;
 }
 
 // Bitonic sort of one value per lane across a full warp, ascending in key, the
@@ -695,7 +737,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
     // mode 3: this call's epoch (only the last CTA advances it, at the very end)
     const unsigned int epoch = SPLIT ? __ldcg(sp.cnt + 4) : 0u;
     int phase = 0;   // mode 3, thread 0: 0 receivers, 1 heavy forward segments, 2 heavy adjoint segments
-    if (warp == 0) tmem_alloc(smem_u32(&tmem_sh), TC_TMEM_COLS);
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_sh), T::TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -861,7 +903,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                     float2 cp = make_float2(0.0f, 0.0f);
                     if (i < i1) {
                         float2 e;
-                        nu_place(tau[i], fc, S.df, M, key, d0, e);
+                        nu_place(tau[i], fc, S.df, logM, key, d0, e);
                         cp = cmul(a[i], e);
                     }
                     warp_sort_by_key(key, d0, cp, lane);
@@ -919,14 +961,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                     continue;
                 }
                 const float wr = w[r];
-                double lsum = 0.0;
+                float lsum = 0.0f;   // FP32 within a receiver, FP64 across receivers
                 for (int c = tid; c < S.N; c += TC_THREADS) {
                     const int idx = (c - S.N / 2) & (M - 1);
                     const float dv = sp.dec[c];
                     const float2 h = make_float2(grid[idx].x * dv, grid[idx].y * dv);
                     const float e = h.x * h.x + h.y * h.y - target[(int64_t)r * S.N + c];
                     const float we = wr * e;
-                    lsum += (double)(we * we);
+                    lsum = fmaf(we, we, lsum);
                     const float sc = 4.0f * wr * wr * e * inv_rn * dv;
                     if (H) H[(int64_t)r * S.N + c] = h;
                     grid[idx] = make_float2(sc * h.x, sc * h.y);
@@ -961,7 +1003,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                 int l0;
                 float d0;
                 float2 e;
-                nu_place(tau[i], fc, S.df, M, l0, d0, e);
+                nu_place(tau[i], fc, S.df, logM, l0, d0, e);
                 float2 gc = make_float2(0.0f, 0.0f);
 #pragma unroll
                 for (int k = 0; k < NU_W; ++k) {
@@ -1066,12 +1108,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
         float gre[N2], gim[N2];
         if (LOSS) {
             const float wr = w[r];
-            double lsum = 0.0;
+            float lsum = 0.0f;   // FP32 within a receiver, FP64 across receivers
 #pragma unroll
             for (int c2 = 0; c2 < N2; ++c2) {
                 const float e = hre[c2] * hre[c2] + him[c2] * him[c2] - target[hrow + c2];
                 const float we = wr * e;
-                lsum += (double)(we * we);
+                lsum = fmaf(we, we, lsum);
                 const float s = 4.0f * wr * wr * e * inv_rn;   // dL/dH = 4 w^2 (|H|^2 - P*) H / (R N)
                 gre[c2] = s * hre[c2];
                 gim[c2] = s * him[c2];
@@ -1149,7 +1191,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                     const uint32_t idesc = tc_idesc(128, 2 * TC_CP);
                     const uint32_t ah = smem_u32(A_hi), al = smem_u32(A_lo), bh = smem_u32(B_hi), bl = smem_u32(B_lo);
                     const uint32_t sbo = (T::KG / 4) * 128;
-                    const uint32_t d = tmem + TC_Y_COL;
+                    const uint32_t d = tmem + T::Y_COL;
                     for (int s = 0; s < T::KG / 8; ++s) {
                         const uint32_t off = (uint32_t)s * 256;
                         tc_mma(d, tc_sdesc(ah + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, s > 0 ? 1u : 0u);
@@ -1160,8 +1202,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                 if (!ok) break;
 #pragma unroll
                 for (int c = 0; c < TC_CP; c += 16) {
-                    tmem_ld16(lane_base + TC_Y_COL + c, vr + c);
-                    tmem_ld16(lane_base + TC_Y_COL + TC_CP + c, vi + c);
+                    tmem_ld16(lane_base + T::Y_COL + c, vr + c);
+                    tmem_ld16(lane_base + T::Y_COL + TC_CP + c, vi + c);
                 }
                 tmem_wait_ld();
                 tc_fence_before();
@@ -1217,7 +1259,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
+    if (warp == 0) tmem_dealloc(tmem, T::TMEM_COLS);
     // completion: the last CTA resets the counters and sums the loss over all
     // receivers in receiver order (mode 3: only if no receiver was deferred; mode 4
     // then does it)
@@ -1268,7 +1310,7 @@ rt_status launch_tc(rt_ctx* ctx, const CfrShape& S, const int64_t* offs, int R, 
         RT_CK(ctx, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
         RT_CK(ctx, cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device));
         int per_sm = smem_sm / (int)(smem + 64 + (size_t)reserved);
-        per_sm = std::max(1, std::min(per_sm, (int)(512 / TC_TMEM_COLS)));
+        per_sm = std::max(1, std::min(per_sm, (int)(512 / TcDims<N2>::TMEM_COLS)));
         const int grid = std::max(1, MODE >= 3 ? ctx->num_sms * per_sm : std::min(R, ctx->num_sms * per_sm));
         kern<<<grid, TC_THREADS, smem, ctx->stream>>>(S, offs, R, a, tau, target, w, gH, loss, ga, H, part, ctr,
                                                        ctx->d_status, sp);

@@ -106,7 +106,6 @@ struct FieldArgs {
     float amp;         // lambda / (4 pi) sqrt(g_T g_R)
 };
 
-constexpr int FWD_NP = 2;     // paths per thread and iteration (independent loads in flight)
 constexpr int ETA_SMEM = 64;  // per-material eta table in shared memory up to this many materials
 
 // eta = eps_r - j sigma / (eps0 omega) of material (or triangle) m
@@ -115,13 +114,66 @@ __device__ __forceinline__ float2 eta_of(const FieldArgs& A, const float2* s_eta
     return make_float2(__ldg(A.eps + m), -__ldg(A.sig + m) * A.inv_eps0w);
 }
 
-// FWD_NP paths per thread in lockstep, so that their record loads (depth, L,
-// material and cos, basis changes) are in flight together; the material gather
-// of the step is a shared-memory table (or an L2-resident per-triangle array).
-__global__ void __launch_bounds__(256, 6) k_fields_fwd(FieldArgs A, float2* __restrict__ a_out, double* __restrict__ tau_out) {
+// The records of one path, held in registers: depth q, total length L, the
+// q + 1 basis changes D_1 .. D_{q+1}, the q material words (material | PEC flag,
+// cos theta_i) and, for per-triangle materials, the q triangles.  Every load is
+// issued before any arithmetic, so that all of a path's loads are in flight at
+// once: the slot loads wait only for q.
+template <bool PER_TRI>
+struct PathRec {
+    int q;
+    float len;
+    float4 D[RT_MAX_DEPTH + 1];
+    int2 w[RT_MAX_DEPTH];
+    int t[PER_TRI ? RT_MAX_DEPTH : 1];
+};
+
+template <bool PER_TRI>
+__device__ __forceinline__ void rec_head(const FieldArgs& A, int64_t i, PathRec<PER_TRI>& r) {
+    r.q = __ldg(A.depth + i);
+    r.len = __ldg(A.len + i);
+    r.D[0] = __ldg(A.Dm + i);
+}
+
+template <bool PER_TRI>
+__device__ __forceinline__ void rec_slots(const FieldArgs& A, int64_t i, PathRec<PER_TRI>& r) {
+#pragma unroll
+    for (int j = 0; j < RT_MAX_DEPTH; ++j) {
+        if (j < r.q) {
+            const int64_t o = (int64_t)j * A.P + i;
+            r.w[j] = __ldg(A.mc + o);
+            if (PER_TRI) r.t[j] = __ldg(A.tri + o);
+            r.D[j + 1] = __ldg(A.Dm + o + A.P);
+        }
+    }
+}
+
+// Fresnel coefficients of bounce j (and their derivatives w.r.t. eta if GRAD);
+// returns the material (or triangle) index, -1 for a perfect conductor.
+template <bool GRAD, bool PER_TRI>
+__device__ __forceinline__ int bounce_coeffs(const FieldArgs& A, const float2* s_eta, const PathRec<PER_TRI>& r, int j,
+                                             float2& rp, float2& rl, float2& drp, float2& drl) {
+    if (r.w[j].x & MAT_PEC) {
+        rp = make_float2(-1.0f, 0.0f);
+        rl = make_float2(1.0f, 0.0f);
+        return -1;
+    }
+    const int m = PER_TRI ? r.t[j] : r.w[j].x;
+    fresnel<GRAD>(eta_of(A, s_eta, m), __int_as_float(r.w[j].y), rp, rl, drp, drl);
+    return m;
+}
+
+// FWD_NP paths per thread, their records loaded together; the material gather of
+// the step is a shared-memory table (or an L2-resident per-triangle array).
+// Launched with one path per thread at 5 blocks of 256 per SM: with every record
+// of a path in flight at once that keeps enough loads outstanding, while two
+// paths per thread need ~106 registers and ran 40 % slower.
+template <bool PER_TRI, int FWD_NP, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_fields_fwd(FieldArgs A, float2* __restrict__ a_out,
+                                                       double* __restrict__ tau_out) {
     if (A.Pd) A.P = min(*A.Pd, A.P);   // slots of a trace that did not wait: its count (and stride)
     __shared__ float2 s_tab[ETA_SMEM];
-    const bool smem_eta = !A.per_tri && A.n_mat <= ETA_SMEM;
+    const bool smem_eta = !PER_TRI && A.n_mat <= ETA_SMEM;
     if (smem_eta) {
         for (int m = threadIdx.x; m < A.n_mat; m += blockDim.x)
             s_tab[m] = make_float2(A.eps[m], -A.sig[m] * A.inv_eps0w);
@@ -130,68 +182,49 @@ __global__ void __launch_bounds__(256, 6) k_fields_fwd(FieldArgs A, float2* __re
     const float2* s_eta = smem_eta ? s_tab : nullptr;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < A.P; i0 += FWD_NP * stride) {
+        PathRec<PER_TRI> r[FWD_NP];
         int64_t idx[FWD_NP];
-        int q[FWD_NP];
-        float len[FWD_NP];
-        float2 v0[FWD_NP], v1[FWD_NP];
+        double tau[FWD_NP];
 #pragma unroll
         for (int k = 0; k < FWD_NP; ++k) {
             idx[k] = i0 + k * stride;
-            const bool ok = idx[k] < A.P;
-            q[k] = ok ? __ldg(A.depth + idx[k]) : -1;
-            len[k] = ok ? __ldg(A.len + idx[k]) : 1.0f;
-            // slot s of the record holds D_{s+1}; v = D_1 C_T with C_T = [1, 0]
-            const float4 d = ok ? __ldg(A.Dm + idx[k]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            v0[k] = make_float2(d.x, 0.0f);
-            v1[k] = make_float2(d.z, 0.0f);
-        }
-#pragma unroll
-        for (int j = 0; j < RT_MAX_DEPTH; ++j) {
-            int2 w[FWD_NP];
-            int t[FWD_NP];
-            float4 e[FWD_NP];
-#pragma unroll
-            for (int k = 0; k < FWD_NP; ++k) {
-                if (j < q[k]) {
-                    const int64_t o = (int64_t)j * A.P + idx[k];
-                    w[k] = __ldg(A.mc + o);
-                    t[k] = A.per_tri ? __ldg(A.tri + o) : 0;
-                    e[k] = __ldg(A.Dm + o + A.P);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < FWD_NP; ++k) {
-                if (j < q[k]) {
-                    float2 rp, rl, unused;
-                    if (w[k].x & MAT_PEC) {
-                        rp = make_float2(-1.0f, 0.0f);
-                        rl = make_float2(1.0f, 0.0f);
-                    } else {
-                        const int m = A.per_tri ? t[k] : w[k].x;
-                        fresnel<false>(eta_of(A, s_eta, m), __int_as_float(w[k].y), rp, rl, unused, unused);
-                    }
-                    const float2 g0 = cmul(rp, v0[k]), g1 = cmul(rl, v1[k]);
-                    v0[k] = cadd(cscale(e[k].x, g0), cscale(e[k].y, g1));
-                    v1[k] = cadd(cscale(e[k].z, g0), cscale(e[k].w, g1));
-                }
+            r[k].q = -1;
+            if (idx[k] < A.P) {
+                rec_head(A, idx[k], r[k]);
+                if (tau_out) tau[k] = __ldg(A.tau + idx[k]);
             }
         }
+#pragma unroll
+        for (int k = 0; k < FWD_NP; ++k) rec_slots(A, idx[k], r[k]);
 #pragma unroll
         for (int k = 0; k < FWD_NP; ++k) {
-            if (q[k] >= 0) {
-                a_out[idx[k]] = cscale(A.amp / len[k], v0[k]);
-                if (tau_out) tau_out[idx[k]] = A.tau[idx[k]];
+            if (r[k].q < 0) continue;
+            // v = D_1 C_T with C_T = [1, 0]; v <- D_{j+1} diag(r_perp, r_par) v
+            float2 v0 = make_float2(r[k].D[0].x, 0.0f), v1 = make_float2(r[k].D[0].z, 0.0f);
+#pragma unroll
+            for (int j = 0; j < RT_MAX_DEPTH; ++j) {
+                if (j < r[k].q) {
+                    float2 rp, rl, unused;
+                    bounce_coeffs<false>(A, s_eta, r[k], j, rp, rl, unused, unused);
+                    const float2 g0 = cmul(rp, v0), g1 = cmul(rl, v1);
+                    const float4 e = r[k].D[j + 1];
+                    v0 = cadd(cscale(e.x, g0), cscale(e.y, g1));
+                    v1 = cadd(cscale(e.z, g0), cscale(e.w, g1));
+                }
             }
+            a_out[idx[k]] = cscale(A.amp / r[k].len, v0);
+            if (tau_out) tau_out[idx[k]] = tau[k];
         }
     }
 }
 
-// Reduction of the per-material gradients: REGM > 0 keeps one register
-// accumulator per material (few materials: no shared-memory atomics on a handful
-// of hot addresses), MAXM > 0 accumulates in shared memory, otherwise global
-// atomics (per-triangle materials: scattered, little contention).
-template <int MAXM, int REGM>
-__global__ void __launch_bounds__(256, 4) k_fields_bwd(FieldArgs A, const float2* __restrict__ ga,
+// Reduction of the per-material gradients: REGM > 0 keeps one shared-memory
+// column per material and thread (few materials: no atomics on a handful of hot
+// addresses), MAXM > 0 accumulates with shared-memory atomics, otherwise global
+// atomics (per-triangle materials: scattered, little contention).  The records
+// of a path are loaded once, into registers, and serve both walks.
+template <int MAXM, int REGM, bool PER_TRI>
+__global__ void __launch_bounds__(256, 3) k_fields_bwd(FieldArgs A, const float2* __restrict__ ga,
                                                        float* __restrict__ geps, float* __restrict__ gsig,
                                                        float* __restrict__ ggain, float inv_gtx, float inv_grx,
                                                        int n_mat) {
@@ -201,7 +234,7 @@ __global__ void __launch_bounds__(256, 4) k_fields_bwd(FieldArgs A, const float2
     if (MAXM > 0)
         for (int m = threadIdx.x; m < n_mat; m += blockDim.x) s_eps[m] = s_sig[m] = 0.0f;
     if (threadIdx.x < 2) s_gain[threadIdx.x] = 0.0f;
-    const bool smem_eta = !A.per_tri && A.n_mat <= ETA_SMEM;
+    const bool smem_eta = !PER_TRI && A.n_mat <= ETA_SMEM;
     if (smem_eta)
         for (int m = threadIdx.x; m < A.n_mat; m += blockDim.x)
             s_tab[m] = make_float2(A.eps[m], -A.sig[m] * A.inv_eps0w);
@@ -215,56 +248,42 @@ __global__ void __launch_bounds__(256, 4) k_fields_bwd(FieldArgs A, const float2
     __syncthreads();
     float gain_acc = 0.0f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.P; i += (int64_t)gridDim.x * blockDim.x) {
-        const int q = __ldg(A.depth + i);
-        const float scale = A.amp / __ldg(A.len + i);
-        const float4 d = __ldg(A.Dm + i);
-        float2 v0 = make_float2(d.x, 0.0f), v1 = make_float2(d.z, 0.0f);
+        PathRec<PER_TRI> r;
+        rec_head(A, i, r);
+        const float2 g = __ldg(ga + i);
+        rec_slots(A, i, r);
+        const float scale = A.amp / r.len;
+        float2 v0 = make_float2(r.D[0].x, 0.0f), v1 = make_float2(r.D[0].z, 0.0f);
         // forward walk: keep only the field entering every bounce
         float2 in0[RT_MAX_DEPTH], in1[RT_MAX_DEPTH];
+        float4 last = r.D[0];   // D_{q+1}
 #pragma unroll
         for (int j = 0; j < RT_MAX_DEPTH; ++j) {
-            if (j < q) {
-                const int64_t o = (int64_t)j * A.P + i;
-                const int2 w = __ldg(A.mc + o);
+            if (j < r.q) {
                 float2 rp, rl, unused;
-                if (w.x & MAT_PEC) {
-                    rp = make_float2(-1.0f, 0.0f);
-                    rl = make_float2(1.0f, 0.0f);
-                } else {
-                    const int m = A.per_tri ? __ldg(A.tri + o) : w.x;
-                    fresnel<false>(eta_of(A, s_eta, m), __int_as_float(w.y), rp, rl, unused, unused);
-                }
+                bounce_coeffs<false>(A, s_eta, r, j, rp, rl, unused, unused);
                 in0[j] = v0;
                 in1[j] = v1;
                 const float2 g0 = cmul(rp, v0), g1 = cmul(rl, v1);
-                const float4 e = __ldg(A.Dm + o + A.P);
+                const float4 e = r.D[j + 1];
                 v0 = cadd(cscale(e.x, g0), cscale(e.y, g1));
                 v1 = cadd(cscale(e.z, g0), cscale(e.w, g1));
+                last = e;
             }
         }
-        const float4 last = __ldg(A.Dm + (int64_t)q * A.P + i);   // D_{q+1}
         const float2 a = cscale(scale, v0);
-        const float2 g = __ldg(ga + i);
         // Re(conj(g) a) / (2 g_T) and / (2 g_R) share Re(conj(g) a)
         gain_acc += g.x * a.x + g.y * a.y;
         // reverse walk: l = scale * (row 0 of D_{q+1}) . Gamma_q D_q ... is the row
         // vector after bounce j; da/dr_perp_j = l[0] in0_j, da/dr_par_j = l[1] in1_j.
-        // The bounce's record is read again (cache hit) and its Fresnel
-        // coefficients are recomputed with their derivatives.
+        // The bounce's Fresnel coefficients are recomputed with their derivatives.
         float2 l0 = make_float2(scale * last.x, 0.0f), l1 = make_float2(scale * last.y, 0.0f);
 #pragma unroll
         for (int j = RT_MAX_DEPTH - 1; j >= 0; --j) {
-            if (j < q) {
-                const int64_t o = (int64_t)j * A.P + i;
-                const int2 w = __ldg(A.mc + o);
-                float2 rp, rl;
-                if (w.x & MAT_PEC) {
-                    rp = make_float2(-1.0f, 0.0f);
-                    rl = make_float2(1.0f, 0.0f);
-                } else {
-                    const int m = A.per_tri ? __ldg(A.tri + o) : w.x;
-                    float2 drp, drl;
-                    fresnel<true>(eta_of(A, s_eta, m), __int_as_float(w.y), rp, rl, drp, drl);
+            if (j < r.q) {
+                float2 rp, rl, drp, drl;
+                const int m = bounce_coeffs<true>(A, s_eta, r, j, rp, rl, drp, drl);
+                if (m >= 0) {
                     const float2 da = cadd(cmul(cmul(l0, in0[j]), drp), cmul(cmul(l1, in1[j]), drl));
                     // Re(conj(g) da) and Im(conj(g) da)
                     const float re = g.x * da.x + g.y * da.y;
@@ -282,7 +301,7 @@ __global__ void __launch_bounds__(256, 4) k_fields_bwd(FieldArgs A, const float2
                     }
                 }
                 const float2 h0 = cmul(l0, rp), h1 = cmul(l1, rl);
-                const float4 e = j == 0 ? d : __ldg(A.Dm + o);
+                const float4 e = r.D[j];
                 l0 = cadd(cscale(e.x, h0), cscale(e.z, h1));
                 l1 = cadd(cscale(e.y, h0), cscale(e.w, h1));
             }
@@ -380,7 +399,10 @@ rt_status rt_launch_fields_fwd(rt_ctx* ctx, const rt_paths* p, const float* eps,
                                double freq, float gtx, float grx, float2* a, double* tau) {
     if (p->P == 0) return RT_OK;
     FieldArgs A = make_args(p, eps, sig, per_tri, freq, gtx, grx);
-    k_fields_fwd<<<grid_for(ctx, p->P, 256, 6), 256, 0, ctx->stream>>>(A, a, tau); RT_COUNT(ctx);
+    const int grid = grid_for(ctx, p->P, 256, 5);
+    if (per_tri) k_fields_fwd<true, 1, 5><<<grid, 256, 0, ctx->stream>>>(A, a, tau);
+    else k_fields_fwd<false, 1, 5><<<grid, 256, 0, ctx->stream>>>(A, a, tau);
+    RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;
 }
@@ -391,13 +413,19 @@ rt_status rt_launch_fields_bwd(rt_ctx* ctx, const rt_paths* p, const float* eps,
     if (p->P == 0) return RT_OK;
     FieldArgs A = make_args(p, eps, sig, per_tri, freq, gtx, grx);
     const int n_mat = per_tri ? p->scene->n_tris : p->scene->n_materials;
-    const int grid = grid_for(ctx, p->P, 256, 4);
+    const int grid = grid_for(ctx, p->P, 256, 3);
     if (!per_tri && n_mat <= 8)
-        k_fields_bwd<8, 8><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx, n_mat);
+        k_fields_bwd<8, 8, false><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx,
+                                                                 n_mat);
     else if (!per_tri && n_mat <= 64)
-        k_fields_bwd<64, 0><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx, n_mat);
+        k_fields_bwd<64, 0, false><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx,
+                                                                  n_mat);
+    else if (!per_tri)
+        k_fields_bwd<0, 0, false><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx,
+                                                                 n_mat);
     else
-        k_fields_bwd<0, 0><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx, n_mat);
+        k_fields_bwd<0, 0, true><<<grid, 256, 0, ctx->stream>>>(A, ga, geps, gsig, ggain, 1.0f / gtx, 1.0f / grx,
+                                                                n_mat);
     RT_COUNT(ctx);
     RT_CK_LAUNCH(ctx);
     return RT_OK;

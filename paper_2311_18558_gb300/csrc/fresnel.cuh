@@ -9,23 +9,38 @@ static __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 static __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 static __device__ __forceinline__ float2 cscale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+// The hardware's approximate reciprocal and square root (PTX rcp.approx.ftz,
+// sqrt.approx.ftz: a few units in the last place), several times cheaper than
+// the correctly rounded forms and well inside the FP32 accuracy of the field
+// chain.  Their arguments here are O(1e-3 .. 1e6), far from subnormals.
+static __device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+static __device__ __forceinline__ float sqrt_fast(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Principal square root from |z|: sqrt(z) = t + j y/(2t) with t = sqrt((|z| + x)/2)
 // for x >= 0, and the mirrored form for x < 0 (no cancellation either way).
 // |z| of eta - sin^2 is O(1..1e3), so sqrt(x^2 + y^2) needs no scaling.
 static __device__ __forceinline__ float2 csqrt(float2 z) {
-    const float r = sqrtf(z.x * z.x + z.y * z.y);
+    const float r = sqrt_fast(z.x * z.x + z.y * z.y);
     if (z.x >= 0.0f) {
-        const float t = sqrtf(0.5f * (r + z.x));
-        return make_float2(t, t > 0.0f ? z.y * __frcp_rn(2.0f * t) : 0.0f);
+        const float t = sqrt_fast(0.5f * (r + z.x));
+        return make_float2(t, t > 0.0f ? z.y * rcp_fast(2.0f * t) : 0.0f);
     }
-    const float t = sqrtf(0.5f * (r - z.x));
-    return make_float2(fabsf(z.y) * __frcp_rn(2.0f * t), copysignf(t, z.y));
+    const float t = sqrt_fast(0.5f * (r - z.x));
+    return make_float2(fabsf(z.y) * rcp_fast(2.0f * t), copysignf(t, z.y));
 }
 
-// 1 / z = conj(z) / |z|^2 with one correctly rounded reciprocal (|z|^2 of the
-// Fresnel denominators stays far from FP32 over- and underflow)
+// 1 / z = conj(z) / |z|^2 with one reciprocal (|z|^2 of the Fresnel denominators
+// stays far from FP32 over- and underflow)
 static __device__ __forceinline__ float2 crcp(float2 z) {
-    const float inv = __frcp_rn(z.x * z.x + z.y * z.y);
+    const float inv = rcp_fast(z.x * z.x + z.y * z.y);
     return make_float2(z.x * inv, -z.y * inv);
 }
 
