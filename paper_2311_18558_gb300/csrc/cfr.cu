@@ -509,43 +509,89 @@ struct TcDims {
 // c_i A_i at c1 = 8k, per path (forward operand factors)
 constexpr int TC_NFC = 16;
 
+// Phasor tables of one chunk of TC_CP paths (two sets, so that the next chunk's
+// tables are built while the current chunk's MMAs run).
+struct TcTab {
+    float2* tF;      // TC_CP x NF factor phasors
+    float2* tFc;     // TC_CP x TC_NFC: c_i A_i at c1 = 8k (forward only)
+    float2* tC;      // TC_CP: c_i = a_i exp(-j 2 pi f_0 tau_i) (forward only)
+    PathPhase* tP;   // TC_CP phase data
+};
+
+template <int N2>
+__host__ __device__ constexpr size_t tc_tab_bytes() {
+    return (size_t)TC_CP * (TcDims<N2>::NF + TC_NFC) * 8 + (size_t)TC_CP * 8 + (size_t)TC_CP * sizeof(PathPhase);
+}
+
+// Phase data and c_i of a whole receiver, formed once when it has at most this
+// many paths (one load latency per receiver instead of one per chunk).
+constexpr int TC_PH_CAP = 128;
+
 // Dynamic shared memory of the tensor-core kernel: A and B operand tiles (hi,
-// lo), then the phasor tables and a reduction buffer.
+// lo), two sets of phasor tables, a reduction buffer and the receiver's phases.
 template <int N2>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
     using T = TcDims<N2>;
-    return (size_t)(2 * T::A_FLOATS + 2 * T::B_FLOATS) * 4 + (size_t)TC_CP * (T::NF + TC_NFC) * 8 +
-           (size_t)TC_CP * 8 + (size_t)TC_CP * sizeof(PathPhase) + 4 * 32 * 8 + 64;
+    return (size_t)(2 * T::A_FLOATS + 2 * T::B_FLOATS) * 4 + 2 * tc_tab_bytes<N2>() + 4 * 32 * 8 +
+           (size_t)TC_PH_CAP * (sizeof(PathPhase) + 8) + 64;
 }
 
-// Phase data and factor phasors of paths [base, base + n), padded with zero
-// phases (phasor 1, c = 0) up to n_pad:
+template <int N2>
+__device__ __forceinline__ TcTab tc_tab(char* base) {
+    TcTab t;
+    t.tF = reinterpret_cast<float2*>(base);
+    t.tFc = t.tF + TC_CP * TcDims<N2>::NF;
+    t.tC = t.tFc + TC_CP * TC_NFC;
+    t.tP = reinterpret_cast<PathPhase*>(t.tC + TC_CP);
+    return t;
+}
+
+// Tables of chunk ch of a receiver's paths [i0, i0 + P): the chunk's paths
+// [base, base + n), padded with zero phases (phasor 1, c = 0) up to n_pad (n
+// itself for a direct receiver, else the next multiple of 8):
 //   tP[ii], tC[ii] = a_i exp(-j 2 pi f_0 tau_i) (if a), tF[ii][0..16) = A_i at
 //   c1 = 8k, tF[ii][16..24) = A_i at c1 = k, tF[ii][24..24+N2) = B_i[c2].
+// With cP (the receiver's phases and c_i, formed at its start) the chunk's phase
+// data come from there; else they are loaded and formed here.  The caller
+// guarantees that no thread still reads tb; ends with a barrier.
 template <int N2>
-__device__ __forceinline__ void tc_tables(const CfrShape& S, int64_t base, int n, int n_pad,
+__device__ __forceinline__ void tc_tables(const CfrShape& S, int64_t i0, int P, int ch, bool direct,
                                           const float2* __restrict__ a, const double* __restrict__ tau,
-                                          PathPhase* tP, float2* tC, float2* tF, float2* tFc) {
+                                          const TcTab& tb, const PathPhase* cP, const float2* cC) {
     using T = TcDims<N2>;
     const int t = threadIdx.x;
-    __syncthreads();
-    if (t < n_pad) {
-        if (t < n) {
-            PathPhase p = path_phase(tau[base + t], S.f0, S.df);
-            tP[t] = p;
-            tC[t] = a ? cmul(a[base + t], base_phasor(p)) : make_float2(0.0f, 0.0f);
-        } else {
-            tP[t] = PathPhase{0.0f, 0.0f, 0.0f};
-            tC[t] = make_float2(0.0f, 0.0f);
+    const int64_t base = i0 + (int64_t)ch * TC_CP;
+    const int n = min(TC_CP, P - ch * TC_CP);
+    const int n_pad = direct ? n : (n + 7) & ~7;
+    const PathPhase* srcP = tb.tP;
+    const float2* srcC = tb.tC;
+    if (cP) {
+        srcP = cP + ch * TC_CP;
+        srcC = cC + ch * TC_CP;
+        if (t < n_pad) {
+            tb.tP[t] = t < n ? srcP[t] : PathPhase{0.0f, 0.0f, 0.0f};
+            tb.tC[t] = t < n && a ? srcC[t] : make_float2(0.0f, 0.0f);
         }
+    } else {
+        if (t < n_pad) {
+            if (t < n) {
+                PathPhase p = path_phase(tau[base + t], S.f0, S.df);
+                tb.tP[t] = p;
+                tb.tC[t] = a ? cmul(a[base + t], base_phasor(p)) : make_float2(0.0f, 0.0f);
+            } else {
+                tb.tP[t] = PathPhase{0.0f, 0.0f, 0.0f};
+                tb.tC[t] = make_float2(0.0f, 0.0f);
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int e = t; e < n_pad * T::NF; e += TC_THREADS) {
         const int ii = e / T::NF, k = e - ii * T::NF;
         const int m = k < T::NAH ? k * T::NAL * N2 : k < T::NAH + T::NAL ? (k - T::NAH) * N2 : k - T::NAH - T::NAL;
-        const float2 f = phasor_fast(tP[ii], m);
-        tF[e] = f;
-        if (a && k < T::NAH) tFc[ii * TC_NFC + k] = cmul(tC[ii], f);
+        const PathPhase pp = ii < n ? srcP[ii] : PathPhase{0.0f, 0.0f, 0.0f};
+        const float2 f = phasor_fast(pp, m);
+        tb.tF[e] = f;
+        if (a && k < T::NAH) tb.tFc[ii * TC_NFC + k] = ii < n ? cmul(srcC[ii], f) : make_float2(0.0f, 0.0f);
     }
     __syncthreads();
 }
@@ -715,11 +761,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
     float* A_lo = A_hi + T::A_FLOATS;
     float* B_hi = A_lo + T::A_FLOATS;
     float* B_lo = B_hi + T::B_FLOATS;
-    float2* tF = reinterpret_cast<float2*>(B_lo + T::B_FLOATS);
-    float2* tFc = tF + TC_CP * T::NF;
-    float2* tC = tFc + TC_CP * TC_NFC;
-    float2* tRed = tC + TC_CP;
-    PathPhase* tP = reinterpret_cast<PathPhase*>(tRed + 4 * 32);
+    char* tab_base = reinterpret_cast<char*>(B_lo + T::B_FLOATS);
+    // table set k (k = chunk & 1), its pointers formed arithmetically
+    auto tabset = [&](int k) { return tc_tab<N2>(tab_base + (size_t)(k & 1) * tc_tab_bytes<N2>()); };
+    float2* tRed = reinterpret_cast<float2*>(tab_base + 2 * tc_tab_bytes<N2>());
+    float2* rcC = tRed + 4 * 32;                                  // TC_PH_CAP: c_i of the receiver
+    PathPhase* rcP = reinterpret_cast<PathPhase*>(rcC + TC_PH_CAP);   // TC_PH_CAP: its phase data
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_sh;
     __shared__ int s_r;
@@ -748,8 +795,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
     const float inv_rn = 1.0f / ((float)R * (float)S.N);
     const int m = tid;   // row c1 of this thread
 
-    // one batch of MMAs issued by thread 0, completion on the mbarrier
-    auto run_mma = [&](auto issue) -> bool {
+    // one batch of MMAs issued by thread 0 once the operand tiles are written;
+    // its completion arrives on the mbarrier, which mma_wait polls (bounded)
+    auto mma_issue = [&](auto issue) {
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {
@@ -757,6 +805,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
             issue();
             tc_commit(mb);
         }
+    };
+    auto mma_wait = [&]() -> bool {
         bool done = mbar_wait(mb, parity);
         parity ^= 1u;
         tc_fence_after();
@@ -1019,15 +1069,27 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
         const bool do_fwd = FWD;
         const bool direct = P <= TC_DIRECT;
         const int nch = (P + TC_CP - 1) / TC_CP;
+        // a receiver of at most TC_PH_CAP paths: its phases and c_i once, all loads at once
+        const bool cached = !direct && P <= TC_PH_CAP;
+        if (cached) {
+            for (int t = tid; t < P; t += TC_THREADS) {
+                const PathPhase pp = path_phase(tau[i0 + t], S.f0, S.df);
+                rcP[t] = pp;
+                rcC[t] = do_fwd ? cmul(a[i0 + t], base_phasor(pp)) : make_float2(0.0f, 0.0f);
+            }
+            __syncthreads();
+        }
+        const PathPhase* cP = cached ? rcP : nullptr;
         float hre[N2], him[N2];
 #pragma unroll
         for (int c2 = 0; c2 < N2; ++c2) hre[c2] = him[c2] = 0.0f;
 
         if (do_fwd && direct && P > 0) {
-            tc_tables<N2>(S, i0, P, P, a, tau, tP, tC, tF, tFc);
+            const TcTab tb = tabset(0);
+            tc_tables<N2>(S, i0, P, 0, true, a, tau, tb, cP, rcC);
             for (int ii = 0; ii < P; ++ii) {
-                const float2 ac = cmul(tFc[ii * TC_NFC + (m >> 3)], tF[ii * T::NF + 16 + (m & 7)]);
-                const float2* B = tF + ii * T::NF + T::NAH + T::NAL;
+                const float2 ac = cmul(tb.tFc[ii * TC_NFC + (m >> 3)], tb.tF[ii * T::NF + 16 + (m & 7)]);
+                const float2* B = tb.tF + ii * T::NF + T::NAH + T::NAL;
 #pragma unroll
                 for (int c2 = 0; c2 < N2; ++c2) {
                     const float2 b = B[c2];
@@ -1036,19 +1098,23 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                 }
             }
         } else if (do_fwd && P > 0) {
+            // Chunks in a software pipeline: the tables of chunk ch + 1 (with the
+            // loads of its delays and coefficients) are built in the other table set
+            // while the MMAs of chunk ch run; the operand tiles are rewritten only
+            // after those MMAs have completed.
+            tc_tables<N2>(S, i0, P, 0, false, a, tau, tabset(0), cP, rcC);
             bool first = true;
             for (int ch = 0; ch < nch && ok; ++ch) {
-                const int64_t base = i0 + (int64_t)ch * TC_CP;
+                const TcTab tb = tabset(ch);
                 const int n = min(TC_CP, P - ch * TC_CP);
                 const int n_pad = (n + 7) & ~7;   // the K steps issued cover paths [0, n_pad)
-                tc_tables<N2>(S, base, n, n_pad, a, tau, tP, tC, tF, tFc);
                 // A' row m: k = i (Re Ac), k = CP + i (Im Ac)
                 for (int i4 = 0; i4 < n_pad / 4; ++i4) {
                     float re[4], im[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int ii = 4 * i4 + q;
-                        float2 v = cmul(tFc[ii * TC_NFC + (m >> 3)], tF[ii * T::NF + 16 + (m & 7)]);
+                        float2 v = cmul(tb.tFc[ii * TC_NFC + (m >> 3)], tb.tF[ii * T::NF + 16 + (m & 7)]);
                         re[q] = v.x;
                         im[q] = v.y;
                     }
@@ -1065,24 +1131,28 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                     float x[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float2 b = tF[(i0p + q) * T::NF + T::NAH + T::NAL + (row % N2)];
+                        const float2 b = tb.tF[(i0p + q) * T::NF + T::NAH + T::NAL + (row % N2)];
                         x[q] = row < N2 ? (imhalf ? -b.y : b.x) : (imhalf ? b.x : b.y);
                     }
                     put4(B_hi, B_lo, (T::KA / 4) * 32, row, kb, x[0], x[1], x[2], x[3]);
                 }
-                ok = run_mma([&]() {
+                const bool acc0 = first;
+                mma_issue([&]() {
                     const uint32_t idesc = tc_idesc(128, T::NB);
                     const uint32_t ah = smem_u32(A_hi), al = smem_u32(A_lo), bh = smem_u32(B_hi), bl = smem_u32(B_lo);
                     const uint32_t sbo = (T::KA / 4) * 128;
+                    bool fst = acc0;
                     for (int s = 0; s < T::KA / 8; ++s) {
                         if (8 * (s % (TC_CP / 8)) >= n) continue;   // all-zero K step
                         const uint32_t off = (uint32_t)s * 256;
-                        tc_mma(tmem, tc_sdesc(ah + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, first ? 0u : 1u);
+                        tc_mma(tmem, tc_sdesc(ah + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, fst ? 0u : 1u);
                         tc_mma(tmem, tc_sdesc(ah + off, 128, sbo), tc_sdesc(bl + off, 128, sbo), idesc, 1u);
                         tc_mma(tmem, tc_sdesc(al + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, 1u);
-                        first = false;
+                        fst = false;
                     }
                 });
+                if (ch + 1 < nch) tc_tables<N2>(S, i0, P, ch + 1, false, a, tau, tabset(ch + 1), cP, rcC);
+                ok = mma_wait();
                 first = false;
             }
             if (!ok) break;
@@ -1097,7 +1167,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                 him[c2] = v[N2 + c2];
             }
         }
-
         // ---- epilogue: H out, loss, g_H
         const int64_t hrow = (int64_t)r * S.N + (int64_t)m * N2;
         if (MODE == 0 || MODE == 4) {
@@ -1130,20 +1199,24 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
             }
         }
 
-        // ---- adjoint: Y[m][i] = sum_c2 g[m][c2] conj(B_i[c2]), then conj(A_i[m]) Y, reduced over m
-        // last chunk first: its tables are still in place from the forward
+        // ---- adjoint: Y[m][i] = sum_c2 g[m][c2] conj(B_i[c2]), then conj(A_i[m]) Y, reduced over m.
+        // Chunks in reverse order.  After a forward the tables of the last two
+        // chunks are still in place (chunk ch in set ch & 1); the tables of chunk
+        // ch - 1 are built while the MMAs of chunk ch run.
         for (int ch = nch - 1; ch >= 0 && ok; --ch) {
+            const TcTab tb = tabset(ch);
             const int64_t base = i0 + (int64_t)ch * TC_CP;
             const int n = min(TC_CP, P - ch * TC_CP);
-            const int n_pad = direct ? n : (n + 7) & ~7;
-            if (!do_fwd || ch != nch - 1) tc_tables<N2>(S, base, n, n_pad, nullptr, tau, tP, tC, tF, tFc);
+            if (ch == nch - 1 && !do_fwd) tc_tables<N2>(S, i0, P, ch, direct, nullptr, tau, tb, cP, rcC);
+            // the tables of chunk ch - 1 still in place from the forward
+            const bool prev_kept = do_fwd && ch - 1 >= nch - 2;
             float vr[32], vi[32];
             if (direct) {
 #pragma unroll
                 for (int ii = 0; ii < 32; ++ii) {
                     float yr = 0.0f, yi = 0.0f;
                     if (ii < n) {
-                        const float2* B = tF + ii * T::NF + T::NAH + T::NAL;
+                        const float2* B = tb.tF + ii * T::NF + T::NAH + T::NAL;
 #pragma unroll
                         for (int c2 = 0; c2 < N2; ++c2) {   // g conj(B)
                             const float2 b = B[c2];
@@ -1155,6 +1228,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                     vi[ii] = yi;
                 }
             } else {
+                const int n_pad = (n + 7) & ~7;
                 if (ch == nch - 1) {
                     // G' (128 x KG), written once per receiver into the A tiles
 #pragma unroll
@@ -1180,14 +1254,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                         const int k = 4 * kb + q;
                         float v = 0.0f;
                         if (k < 2 * N2) {
-                            const float2 b = tF[ii * T::NF + T::NAH + T::NAL + (k % N2)];
+                            const float2 b = tb.tF[ii * T::NF + T::NAH + T::NAL + (k % N2)];
                             v = k < N2 ? (imrow ? -b.y : b.x) : (imrow ? b.x : b.y);
                         }
                         x[q] = v;
                     }
                     put4(B_hi, B_lo, (T::KG / 4) * 32, row, kb, x[0], x[1], x[2], x[3]);
                 }
-                ok = run_mma([&]() {
+                mma_issue([&]() {
                     const uint32_t idesc = tc_idesc(128, 2 * TC_CP);
                     const uint32_t ah = smem_u32(A_hi), al = smem_u32(A_lo), bh = smem_u32(B_hi), bl = smem_u32(B_lo);
                     const uint32_t sbo = (T::KG / 4) * 128;
@@ -1199,6 +1273,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                         tc_mma(d, tc_sdesc(al + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, 1u);
                     }
                 });
+                if (ch >= 1 && !prev_kept) tc_tables<N2>(S, i0, P, ch - 1, false, nullptr, tau, tabset(ch - 1), cP, rcC);
+                ok = mma_wait();
                 if (!ok) break;
 #pragma unroll
                 for (int c = 0; c < TC_CP; c += 16) {
@@ -1213,7 +1289,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
 #pragma unroll
             for (int ii = 0; ii < 32; ++ii) {   // conj(A_i[m]) Y[m][i]
                 float2 p = make_float2(0.0f, 0.0f);
-                if (ii < n) p = cmulc(make_float2(vr[ii], vi[ii]), tc_A(tF, T::NF, ii, m));
+                if (ii < n) p = cmulc(make_float2(vr[ii], vi[ii]), tc_A(tb.tF, T::NF, ii, m));
                 vr[ii] = p.x;
                 vi[ii] = p.y;
             }
@@ -1244,7 +1320,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                     s.x += tRed[k * 32 + lane].x;
                     s.y += tRed[k * 32 + lane].y;
                 }
-                ga[base + lane] = cmulc(s, base_phasor(tP[lane]));
+                ga[base + lane] = cmulc(s, base_phasor(tb.tP[lane]));
             }
         }
         if ((MODE == 2 || MODE == 3) && kind == 0) {

@@ -766,6 +766,21 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
 // left undecided were decided robustly, so their triangles (in the stored key)
 // are replayed with one FP64 ray/triangle test each; the BVH search in
 // mixed precision (closest64) starts at the undecided bounce.
+// The hit of a robust prefix bounce, whose triangle the FP32 pass decided with
+// margin: t where the FP64 ray meets the triangle's FP64 plane n.x = c,
+// t = (c - n.o) / (n.d), a dozen FP64 operations instead of the full
+// ray/triangle test (the FP64 pipe bounds this kernel).  False if the ray is
+// (nearly) parallel to the plane or t <= tmin, which the caller treats as
+// undecided.
+__device__ __forceinline__ bool replay_plane(const double* __restrict__ tri_n64, int id, const WRay<double>& r,
+                                             double tmin, double& t_out) {
+    const double nx = tri_n64[4 * id], ny = tri_n64[4 * id + 1], nz = tri_n64[4 * id + 2], c = tri_n64[4 * id + 3];
+    const double nd = nx * r.d.x + ny * r.d.y + nz * r.d.z;
+    if (!(fabs(nd) > 1e-9)) return false;
+    t_out = (c - (nx * r.o.x + ny * r.o.y + nz * r.o.z)) * rcp64(nd);
+    return t_out > tmin;
+}
+
 __device__ __forceinline__ uint64_t key_prefix(uint64_t key, int b) {   // the fields of bounces < b
     return b <= 0 ? 0ull : key & (~0ull << (48 - 16 * (b - 1)));
 }
@@ -798,21 +813,17 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const doub
         r.d = mk((double)df.x, (double)df.y, (double)df.z);
         int prev = -1;
         for (int b = 0; b < A.depth; ++b) {
-            wray_init(r);
             double th;
             int id = -1;
-            if (b < b0) {   // robust prefix: its triangle, one FP64 test
+            if (b < b0) {   // robust prefix: its triangle is known, t from its plane in FP64
                 id = rt_key_tri(key, b);
-                double Tn, det;
-                if (tri_test64(r, __ldg(tri_v + 3 * id), __ldg(tri_v + 3 * id + 1), __ldg(tri_v + 3 * id + 2), Tn, det) &&
-                    Tn > A.eps * det) {
-                    th = Tn * rcp64(det);
-                } else {   // not expected: search from here on
+                if (!replay_plane(tri_n64, id, r, A.eps, th)) {   // not expected: search from here on
                     b0 = b;
                     key = key_prefix(key, b);
                 }
             }
             if (b >= b0) {
+                wray_init(r);
                 rf.o = mk((float)r.o.x, (float)r.o.y, (float)r.o.z);
                 rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
                 wray_init(rf);
@@ -2160,22 +2171,17 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo_batch(BatchSbr A) {
         r.d = mk((double)df.x, (double)df.y, (double)df.z);
         int prev = -1;
         for (int b = 0; b < A.depth; ++b) {
-            wray_init(r);
             double th;
             int id = -1;
-            if (b < b0) {   // robust prefix: its triangle, one FP64 test (as k_sbr_redo)
+            if (b < b0) {   // robust prefix (as k_sbr_redo)
                 id = rt_key_tri(key, b);
-                double Tn, det;
-                if (tri_test64(r, __ldg(d.tri_v + 3 * id), __ldg(d.tri_v + 3 * id + 1), __ldg(d.tri_v + 3 * id + 2),
-                               Tn, det) &&
-                    Tn > d.eps * det) {
-                    th = Tn * rcp64(det);
-                } else {
+                if (!replay_plane(d.tri_n64, id, r, d.eps, th)) {
                     b0 = b;
                     key = key_prefix(key, b);
                 }
             }
             if (b >= b0) {
+                wray_init(r);
                 rf.o = mk((float)r.o.x, (float)r.o.y, (float)r.o.z);
                 rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
                 wray_init(rf);
