@@ -1617,12 +1617,21 @@ def run_case(args):
         eps = torch.tensor(sc.eps_r, device=dev)
         sig = torch.tensor(sc.sigma, device=dev)
         spec = rt.trace_paths(ctx, scene, sc.tx, rx, sc.n_rays, sc.max_depth)
-        for _ in range(args.warmup + args.steps):
+        stream = torch.cuda.current_stream()
+        tt = []
+        for it in range(args.warmup + args.steps):
             flush.zero_()
+            s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
             d = rt.trace_diffraction(ctx, scene, spec, sc.tx, rx)
+            e0.record(stream)
             a = rt.eval_fields_diffraction(ctx, d, eps, sig, sc.freq_hz)
             rt.eval_fields_diffraction_backward(ctx, d, eps, sig, sc.freq_hz, torch.ones_like(a))
+            e0.synchronize()
+            if it >= args.warmup:
+                tt.append(s0.elapsed_time(e0))
         out["n_paths"] = d.n_paths
+        out["trace_ms"] = float(np.median(tt))
     elif args.case == "city_batch":
         cities = scenegen.city_batch()
         scenes = [rt.Scene.from_synthetic(ctx, c) for c in cities]

@@ -1139,15 +1139,18 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                 const bool acc0 = first;
                 mma_issue([&]() {
                     const uint32_t idesc = tc_idesc(128, T::NB);
-                    const uint32_t ah = smem_u32(A_hi), al = smem_u32(A_lo), bh = smem_u32(B_hi), bl = smem_u32(B_lo);
                     const uint32_t sbo = (T::KA / 4) * 128;
+                    // K step s starts 256 bytes further: its descriptors are the base ones
+                    // plus 16 s in the start-address field (addresses stay below 256 KB)
+                    const uint64_t dah = tc_sdesc(smem_u32(A_hi), 128, sbo), dal = tc_sdesc(smem_u32(A_lo), 128, sbo);
+                    const uint64_t dbh = tc_sdesc(smem_u32(B_hi), 128, sbo), dbl = tc_sdesc(smem_u32(B_lo), 128, sbo);
                     bool fst = acc0;
                     for (int s = 0; s < T::KA / 8; ++s) {
                         if (8 * (s % (TC_CP / 8)) >= n) continue;   // all-zero K step
-                        const uint32_t off = (uint32_t)s * 256;
-                        tc_mma(tmem, tc_sdesc(ah + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, fst ? 0u : 1u);
-                        tc_mma(tmem, tc_sdesc(ah + off, 128, sbo), tc_sdesc(bl + off, 128, sbo), idesc, 1u);
-                        tc_mma(tmem, tc_sdesc(al + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, 1u);
+                        const uint64_t o = (uint64_t)(16 * s);
+                        tc_mma(tmem, dah + o, dbh + o, idesc, fst ? 0u : 1u);
+                        tc_mma(tmem, dah + o, dbl + o, idesc, 1u);
+                        tc_mma(tmem, dal + o, dbh + o, idesc, 1u);
                         fst = false;
                     }
                 });
@@ -1263,14 +1266,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                 }
                 mma_issue([&]() {
                     const uint32_t idesc = tc_idesc(128, 2 * TC_CP);
-                    const uint32_t ah = smem_u32(A_hi), al = smem_u32(A_lo), bh = smem_u32(B_hi), bl = smem_u32(B_lo);
                     const uint32_t sbo = (T::KG / 4) * 128;
+                    const uint64_t dah = tc_sdesc(smem_u32(A_hi), 128, sbo), dal = tc_sdesc(smem_u32(A_lo), 128, sbo);
+                    const uint64_t dbh = tc_sdesc(smem_u32(B_hi), 128, sbo), dbl = tc_sdesc(smem_u32(B_lo), 128, sbo);
                     const uint32_t d = tmem + T::Y_COL;
                     for (int s = 0; s < T::KG / 8; ++s) {
-                        const uint32_t off = (uint32_t)s * 256;
-                        tc_mma(d, tc_sdesc(ah + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, s > 0 ? 1u : 0u);
-                        tc_mma(d, tc_sdesc(ah + off, 128, sbo), tc_sdesc(bl + off, 128, sbo), idesc, 1u);
-                        tc_mma(d, tc_sdesc(al + off, 128, sbo), tc_sdesc(bh + off, 128, sbo), idesc, 1u);
+                        const uint64_t o = (uint64_t)(16 * s);
+                        tc_mma(d, dah + o, dbh + o, idesc, s > 0 ? 1u : 0u);
+                        tc_mma(d, dah + o, dbl + o, idesc, 1u);
+                        tc_mma(d, dal + o, dbh + o, idesc, 1u);
                     }
                 });
                 if (ch >= 1 && !prev_kept) tc_tables<N2>(S, i0, P, ch - 1, false, nullptr, tau, tabset(ch - 1), cP, rcC);

@@ -319,7 +319,65 @@ __global__ void k_dif_compact(const uint8_t* __restrict__ flag, int W, int32_t* 
     if (threadIdx.x == 0) *count = s_base;
 }
 
+// FP32 copy of a candidate wedge for the prefilter of k_dif_pairs: edge start s,
+// e, t0, n0, (sin n pi, cos n pi) (the other face's outward normal is
+// sin(n pi) t0 - cos(n pi) n0), length, and the transmitter's abscissa xT and
+// distance a from the edge line.
+struct WedgeF {
+    float4 a;   // s.x, s.y, s.z, len
+    float4 b;   // e.x, e.y, e.z, xT
+    float4 c;   // t0.x, t0.y, t0.z, a
+    float4 d;   // n0.x, n0.y, n0.z, sin(n pi)
+    float cn;   // cos(n pi)
+};
+
+__global__ void k_dif_prep(const double* __restrict__ wedge, const int32_t* __restrict__ cw, int Kw, D3 T,
+                           float4* __restrict__ out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Kw; k += gridDim.x * blockDim.x) {
+        const WedgeDev w = load_wedge(wedge, cw[k]);
+        const D3 dT = d3sub(T, w.s);
+        const double xT = d3dot(dT, w.e);
+        const double a = d3norm(d3sub(dT, d3mul(xT, w.e)));
+        double sn, cn;
+        sincospi(w.n, &sn, &cn);
+        float4* o = out + 5 * (size_t)k;
+        o[0] = make_float4((float)w.s.x, (float)w.s.y, (float)w.s.z, (float)w.len);
+        o[1] = make_float4((float)w.e.x, (float)w.e.y, (float)w.e.z, (float)xT);
+        o[2] = make_float4((float)w.t0.x, (float)w.t0.y, (float)w.t0.z, (float)a);
+        o[3] = make_float4((float)w.n0.x, (float)w.n0.y, (float)w.n0.z, (float)sn);
+        o[4] = make_float4((float)cn, 0.0f, 0.0f, 0.0f);
+    }
+}
+
+// FP32 prefilter of a (receiver, wedge) pair: false only where the FP64 tests of
+// keller() certainly fail for the receiver, i.e. the receiver lies inside the
+// wedge (behind both faces), closer to the edge line than eps, or Keller's
+// abscissa lies outside [0, len), each by more than the margin m.  The FP32
+// quantities carry errors of a few 1e-7 of the scene size (the records rounded
+// from FP64 and a handful of FP32 operations), and m is 16 eps = 1.6e-5 of the
+// scene diagonal.  The abscissa test is skipped when a + b is small, where the
+// division would magnify those errors.
+__device__ __forceinline__ bool dif_maybe(const float4* __restrict__ wf, float rx, float ry, float rz, float eps,
+                                          float m) {
+    const float4 A = __ldg(wf), B = __ldg(wf + 1), C = __ldg(wf + 2), Dd = __ldg(wf + 3);
+    const float cn = __ldg(reinterpret_cast<const float*>(wf + 4));
+    const float dx = rx - A.x, dy = ry - A.y, dz = rz - A.z;
+    const float xR = dx * B.x + dy * B.y + dz * B.z;
+    const float x0 = dx * C.x + dy * C.y + dz * C.z;
+    const float y0 = dx * Dd.x + dy * Dd.y + dz * Dd.z;
+    if (y0 < -m && x0 * Dd.w - y0 * cn < -m) return false;   // inside the wedge
+    const float b = sqrtf(x0 * x0 + y0 * y0);
+    if (b < eps - m) return false;
+    const float a = C.w;
+    if (a + b > 1000.0f * eps) {
+        const float xQ = (B.w * b + xR * a) / (a + b);
+        if (xQ < -m || xQ > A.w + m) return false;
+    }
+    return true;
+}
+
 struct DifArgs {
+    const float4* wf;   // Kw x 5: WedgeF of the candidates
     const double* wedge;
     const int2* wfaces;
     const int32_t* cw;   // candidate wedge ids (ascending)
@@ -341,9 +399,11 @@ __global__ void __launch_bounds__(DIF_THREADS) k_dif_pairs(DifArgs A) {
     const int64_t n = (int64_t)A.R * A.Kw;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(i / A.Kw), k = (int)(i - (int64_t)r * A.Kw);
+        const D3 R{A.rx[3 * r], A.rx[3 * r + 1], A.rx[3 * r + 2]};
+        if (!dif_maybe(A.wf + 5 * (size_t)k, (float)R.x, (float)R.y, (float)R.z, (float)A.eps, 16.0f * (float)A.eps))
+            continue;
         const int wi = __ldg(A.cw + k);
         const WedgeDev w = load_wedge(A.wedge, wi);
-        const D3 R{A.rx[3 * r], A.rx[3 * r + 1], A.rx[3 * r + 2]};
         Keller kp;
         if (!keller(w, A.tx, R, A.eps, kp)) continue;
         const int2 f = __ldg(A.wfaces + wi);
@@ -882,7 +942,20 @@ RT_EXPORT rt_status rt_trace_diffraction(rt_ctx* ctx, const rt_scene* scene, con
     p->D = 2;
     p->R = n_rx;
     p->kind = 2;
+    // temporaries of the call (freed on every exit)
+    uint8_t* flag = nullptr;
+    int32_t* list = nullptr;
+    int32_t* count = nullptr;
+    float4* wf = nullptr;
+    uint32_t* bits = nullptr;
+    int64_t* counts = nullptr;
+    int32_t* pk = nullptr;
+    auto release = [&]() {
+        for (void* q : {(void*)flag, (void*)list, (void*)wf, (void*)bits, (void*)counts, (void*)pk})
+            if (q) cudaFreeAsync(q, st);
+    };
     auto fail = [&](rt_status e) {
+        release();
         rt_paths_free(p);
         return e;
     };
@@ -893,9 +966,6 @@ RT_EXPORT rt_status rt_trace_diffraction(rt_ctx* ctx, const rt_scene* scene, con
     } while (0)
     DCK(cudaMallocAsync((void**)&p->d_rx_offsets, (size_t)(n_rx + 1) * 8, st));
     // candidate wedges
-    uint8_t* flag = nullptr;
-    int32_t* list = nullptr;
-    int32_t* count = nullptr;
     const size_t Wa = std::max(W, 1);
     DCK(cudaMallocAsync((void**)&flag, Wa, st));
     DCK(cudaMallocAsync((void**)&list, Wa * 4 + 64, st));
@@ -915,13 +985,15 @@ RT_EXPORT rt_status rt_trace_diffraction(rt_ctx* ctx, const rt_scene* scene, con
     const int Kw = *(int32_t*)hp;   // p->K stays 0: a diffraction paths object has no candidate keys
     // valid (receiver, wedge) pairs
     const int64_t words = std::max<int64_t>(1, ((int64_t)Kw + 31) / 32);
-    uint32_t* bits = nullptr;
-    int64_t* counts = nullptr;
     DCK(cudaMallocAsync((void**)&bits, (size_t)n_rx * words * 4, st));
     DCK(cudaMallocAsync((void**)&counts, (size_t)n_rx * 8, st));
     DCK(cudaMemsetAsync(bits, 0, (size_t)n_rx * words * 4, st));
     if (Kw > 0) {
+        DCK(cudaMallocAsync((void**)&wf, (size_t)Kw * 5 * sizeof(float4), st));
+        k_dif_prep<<<dif_grid(ctx, Kw, 128, 4), 128, 0, st>>>(scene->d_wedge, list, Kw, D3{tx[0], tx[1], tx[2]}, wf);
+        RT_COUNT(ctx);
         DifArgs A;
+        A.wf = wf;
         A.wedge = scene->d_wedge;
         A.wfaces = scene->d_wedge_faces;
         A.cw = list;
@@ -977,7 +1049,6 @@ RT_EXPORT rt_status rt_trace_diffraction(rt_ctx* ctx, const rt_scene* scene, con
         p->d_dif_faces = reinterpret_cast<int2*>(b + o_f);
     }
     if (P > 0) {
-        int32_t* pk = nullptr;
         DCK(cudaMallocAsync((void**)&pk, Pa * 4, st));
         k_dif_expand<<<dif_grid(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, p->d_rx_offsets,
                                                                                    p->d_rx, pk);
@@ -1002,12 +1073,8 @@ RT_EXPORT rt_status rt_trace_diffraction(rt_ctx* ctx, const rt_scene* scene, con
         k_dif_records<<<dif_grid(ctx, P, 128, 16), 128, 0, st>>>(RA);
         RT_COUNT(ctx);
         DCK(cudaGetLastError());
-        cudaFreeAsync(pk, st);
     }
-    cudaFreeAsync(bits, st);
-    cudaFreeAsync(counts, st);
-    cudaFreeAsync(flag, st);
-    cudaFreeAsync(list, st);
+    release();
 #undef DCK
     *out = p;
     return RT_OK;
