@@ -927,9 +927,20 @@ def time_fields_hbm(rt, ctx, scene, sc, flush, reps=10, copies=1000):
     peaks, src = load_peaks()
     hbm = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
     gf, gb = fwd_bytes / (t_f * 1e-3) / 1e9, bwd_bytes / (t_b * 1e-3) / 1e9
+
+    def line(ms, nbytes, g, kernel):
+        # traffic: DRAM bytes per launch from the committed ncu counters (null once the
+        # kernel's code changed); the records of a warp's paths have mixed depths, so a
+        # slot's sectors are partly unused and DRAM traffic exceeds the algorithmic bytes
+        tr = ncu_traffic(kernel) if copies == 1000 else None
+        out = {"ms": ms, "bytes": nbytes, "achieved_gbs": g, "peak_gbs": hbm, "frac": g / hbm, "traffic": tr}
+        if tr:
+            out["dram_gbs"] = tr / (ms * 1e-3) / 1e9
+            out["dram_frac"] = out["dram_gbs"] / hbm
+        return out
     return {"workload": f"street_canyon paths x {copies} (rt_paths_import)", "n_paths": p.n_paths,
-            "fields_fwd": {"ms": t_f, "bytes": fwd_bytes, "achieved_gbs": gf, "peak_gbs": hbm, "frac": gf / hbm},
-            "fields_bwd": {"ms": t_b, "bytes": bwd_bytes, "achieved_gbs": gb, "peak_gbs": hbm, "frac": gb / hbm},
+            "fields_fwd": line(t_f, fwd_bytes, gf, "k_fields_fwd"),
+            "fields_bwd": line(t_b, bwd_bytes, gb, "k_fields_bwd"),
             "peak_source": src}
 
 

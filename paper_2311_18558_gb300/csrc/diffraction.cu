@@ -407,8 +407,11 @@ __global__ void __launch_bounds__(DIF_THREADS) k_dif_pairs(DifArgs A) {
         Keller kp;
         if (!keller(w, A.tx, R, A.eps, kp)) continue;
         const int2 f = __ldg(A.wfaces + wi);
-        if (!seg_clear(A.nodes, A.tris, A.tx, kp.Q, A.eps, f.x, f.y, A.status)) continue;
+        // the receiver's segment first: it rejects more pairs than the transmitter's
+        // (measured on the street canyon: 25 % of the Keller-valid pairs see the
+        // receiver, 64 % the transmitter), so fewer long segments are queried
         if (!seg_clear(A.nodes, A.tris, kp.Q, R, A.eps, f.x, f.y, A.status)) continue;
+        if (!seg_clear(A.nodes, A.tris, A.tx, kp.Q, A.eps, f.x, f.y, A.status)) continue;
         atomicOr(A.bits + (int64_t)r * A.words + (k >> 5), 1u << (k & 31));
     }
 }
