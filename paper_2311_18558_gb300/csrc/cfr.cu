@@ -1069,6 +1069,17 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
         const bool do_fwd = FWD;
         const bool direct = P <= TC_DIRECT;
         const int nch = (P + TC_CP - 1) / TC_CP;
+        // the loss epilogue's target powers and weight, loaded now so that their
+        // latency passes during the forward (N2 <= 8: a few registers)
+        constexpr bool PREF = LOSS && N2 <= 8;
+        float tgt[PREF ? N2 : 1];
+        float wr_pref = 0.0f;
+        if (PREF) {
+            const int64_t hrow0 = (int64_t)r * S.N + (int64_t)m * N2;
+#pragma unroll
+            for (int c2 = 0; c2 < N2; ++c2) tgt[c2] = __ldg(target + hrow0 + c2);
+            wr_pref = __ldg(w + r);
+        }
         // a receiver of at most TC_PH_CAP paths: its phases and c_i once, all loads at once
         const bool cached = !direct && P <= TC_PH_CAP;
         if (cached) {
@@ -1179,11 +1190,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
         }
         float gre[N2], gim[N2];
         if (LOSS) {
-            const float wr = w[r];
+            const float wr = PREF ? wr_pref : w[r];
             float lsum = 0.0f;   // FP32 within a receiver, FP64 across receivers
 #pragma unroll
             for (int c2 = 0; c2 < N2; ++c2) {
-                const float e = hre[c2] * hre[c2] + him[c2] * him[c2] - target[hrow + c2];
+                const float pt = PREF ? tgt[PREF ? c2 : 0] : target[hrow + c2];
+                const float e = hre[c2] * hre[c2] + him[c2] * him[c2] - pt;
                 const float we = wr * e;
                 lsum = fmaf(we, we, lsum);
                 const float s = 4.0f * wr * wr * e * inv_rn;   // dL/dH = 4 w^2 (|H|^2 - P*) H / (R N)
@@ -1297,24 +1309,31 @@ __global__ void __launch_bounds__(TC_THREADS) k_cfr_tc(CfrShape S, const int64_t
                 vr[ii] = p.x;
                 vi[ii] = p.y;
             }
-            // transposed reduction: lane l ends with this warp's sum for path l (mod TC_CP)
-            constexpr int RED_TOP = TC_CP > 16 ? 16 : TC_CP / 2;
+            // transposed reduction: lane l ends with this warp's sum for path l (mod
+            // 2 TOP); a direct receiver (at most TC_DIRECT paths) needs half the stages
+            auto reduce = [&](auto top) {
+                constexpr int TOP = decltype(top)::value;
 #pragma unroll
-            for (int o = RED_TOP; o >= 1; o >>= 1) {
-                const bool up = (lane & o) != 0;
+                for (int o = TOP; o >= 1; o >>= 1) {
+                    const bool up = (lane & o) != 0;
 #pragma unroll
-                for (int j = 0; j < o; ++j) {
-                    const float sr = up ? vr[j] : vr[j + o], si = up ? vi[j] : vi[j + o];
-                    const float kr = up ? vr[j + o] : vr[j], ki = up ? vi[j + o] : vi[j];
-                    vr[j] = kr + __shfl_xor_sync(0xffffffffu, sr, o);
-                    vi[j] = ki + __shfl_xor_sync(0xffffffffu, si, o);
+                    for (int j = 0; j < o; ++j) {
+                        const float sr = up ? vr[j] : vr[j + o], si = up ? vi[j] : vi[j + o];
+                        const float kr = up ? vr[j + o] : vr[j], ki = up ? vi[j + o] : vi[j];
+                        vr[j] = kr + __shfl_xor_sync(0xffffffffu, sr, o);
+                        vi[j] = ki + __shfl_xor_sync(0xffffffffu, si, o);
+                    }
                 }
-            }
 #pragma unroll
-            for (int o = 2 * RED_TOP; o < 32; o <<= 1) {   // lanes l and l ^ o hold the same paths
-                vr[0] += __shfl_xor_sync(0xffffffffu, vr[0], o);
-                vi[0] += __shfl_xor_sync(0xffffffffu, vi[0], o);
-            }
+                for (int o = 2 * TOP; o < 32; o <<= 1) {   // lanes l and l ^ o hold the same paths
+                    vr[0] += __shfl_xor_sync(0xffffffffu, vr[0], o);
+                    vi[0] += __shfl_xor_sync(0xffffffffu, vi[0], o);
+                }
+            };
+            constexpr int RED_TOP = TC_CP > 16 ? 16 : TC_CP / 2;
+            static_assert(TC_DIRECT % 2 == 0 && TC_DIRECT / 2 <= RED_TOP, "direct receivers use a shorter reduction");
+            if (direct) reduce(std::integral_constant<int, TC_DIRECT / 2>());
+            else reduce(std::integral_constant<int, RED_TOP>());
             tRed[warp * 32 + lane] = make_float2(vr[0], vi[0]);
             __syncthreads();
             if (warp == 0 && lane < n) {
