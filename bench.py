@@ -413,6 +413,14 @@ def run_ours(args):
         raise RuntimeError(f"device status {status_after} after the timed steps")
     rt.set_trace_async(ctx, False)
 
+    # ---------------- the same step captured once in a CUDA graph and replayed (the
+    # trace inside a capture runs from the capacities of the steps above)
+    try:
+        step_graph = time_step_graph(rt, ctx, step, rx_dev, target, eps, sig, flush, args.steps, sc.n_rays)
+    except Exception as e:   # reported, not fatal: the device-timed step above is the headline
+        step_graph = {"error": f"{type(e).__name__}: {e}"[:300]}
+        torch.cuda.synchronize()
+
     # ---------------- calibration kernels alone on the same paths (roofline inputs)
     ctx.set_profiling(0)
     p = rt.trace_paths(ctx, scene, sc.tx, rx_dev, sc.n_rays, sc.max_depth)
@@ -481,6 +489,7 @@ def run_ours(args):
             "paths_per_step": n_paths, "paths_per_s": n_paths * args.steps * world / total_s,
             "step_ms_spread": {"min": round(min(step_ms), 4), "median": round(float(np.median(step_ms)), 4),
                                "max": round(max(step_ms), 4)},
+            "step_graph": step_graph,
             "stage_ms": {k: round(v, 4) for k, v in stages.items()},
             "calibration_ms": {k: round(v, 4) for k, v in cal.items()},
             "calibration_indoor": calib_indoor,
@@ -513,6 +522,7 @@ def summary(line):
     ci, df_, fh, lr, bt = (line.get(k) for k in ("calibration_indoor", "diffuse", "fields_hbm", "learned", "batch"))
     return {
         "rays_per_s": g(line, "value"), "ms_per_step": g(line, "ms_per_step"), "e2e_rays_per_s": g(line, "e2e", "value"),
+        "graph_ms_per_step": g(line, "step_graph", "ms_per_step"),
         "calibration_step_ms": g(line, "calibration_step_ms"), "calibration_plain_ms": g(line, "calibration_plain_ms"),
         "frac": {"k_sbr": g(line, "roofline", "frac"), "k_cfr_tc": g(ci, "roofline_cfr", "frac"),
                  "k_fields_fwd": g(fh, "fields_fwd", "frac"), "k_fields_bwd": g(fh, "fields_bwd", "frac"),
@@ -592,6 +602,43 @@ def time_diffraction(rt, ctx, scene, sc, p_spec, rx_dev, eps, sig, flush, steps,
                                                 "unit": "GB/s", "frac": gb / hbm, "traffic": None,
                                                 "peak_source": peak_src, "algorithmic": f"{DIF_BYTES_BWD} B/path"},
             "l2": "flushed: 256 MiB written between timed runs"}
+
+
+def time_step_graph(rt, ctx, step, rx_dev, target, eps, sig, flush, steps, n_rays):
+    """The street-canyon step (trace + fields + fused CFR/loss/adjoint + fields
+    adjoint) captured in one CUDA graph and replayed: every replay does the whole
+    step's work (a new trace, new fields, the loss and both adjoints); only the
+    host's launch work is gone."""
+    import torch
+    ctx.set_profiling(0)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step(rx_dev, target, eps, sig)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step(rx_dev, target, eps, sig)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(max(steps, 10)):
+        flush.zero_()
+        s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        g.replay()
+        e0.record(stream)
+        e0.synchronize()
+        times.append(s0.elapsed_time(e0))
+    if ctx.status_word() != 0:
+        raise RuntimeError("device status set during the graph-replayed steps")
+    ms = float(np.median(times))
+    del g
+    return {"ms_per_step": ms, "rays_per_s": n_rays / (ms * 1e-3), "replays": len(times),
+            "l2": "flushed: 256 MiB written between replays"}
 
 
 def time_calibration(rt, ctx, p, eps, sig, target, weight, freq, fc, df, N, flush, steps):

@@ -1097,7 +1097,8 @@ __device__ __forceinline__ bool prefilter32(const CandView& C, int64_t k, int q,
         V3<float> dir = mk(I4.x, I4.y, I4.z) - P;
         float den = dot(n, dir);
         if (fabsf(den) < 1e-20f) return true;   // undecided in FP32
-        float u = (pl.w - dot(n, P)) / den;
+        // approximate division (a few ulp): far inside the prefilter's margin
+        float u = __fdividef(pl.w - dot(n, P), den);
         if (u < -m || u > 1.0f + m) return false;
         V3<float> s = P + u * dir;
         float l0 = g0.x * s.x + g0.y * s.y + g0.z * s.z + g0.w;
@@ -1236,7 +1237,8 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_segments(VisArgs A) {
     unsigned long long c_vis = 0, c_tri = 0, c_seg = 0;
     for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < total;
          t += (unsigned long long)gridDim.x * blockDim.x) {
-        const int j = (int)(t / n);
+        // segment index and pair: 32-bit division whenever the item count fits
+        const int j = total <= 0xffffffffull ? (int)((unsigned)t / (unsigned)n) : (int)(t / n);
         const unsigned long long w = t - (unsigned long long)j * n;
         const int q = A.seg_q[w];
         if (q < j) continue;
@@ -2374,7 +2376,8 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_segments_batch(BatchVis A) {
     unsigned long long c_vis = 0, c_tri = 0, c_seg = 0;
     for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < total;
          t += (unsigned long long)gridDim.x * blockDim.x) {
-        const int j = (int)(t / n);
+        // segment index and pair: 32-bit division whenever the item count fits
+        const int j = total <= 0xffffffffull ? (int)((unsigned)t / (unsigned)n) : (int)(t / n);
         const unsigned long long w = t - (unsigned long long)j * n;
         const int q = A.seg_q[w];
         if (q < j) continue;
