@@ -252,11 +252,16 @@ __device__ __forceinline__ void traverse(const BvhNode* __restrict__ nodes, cons
     int ref = 0;
     int visits = 0;
     for (;;) {
-        if (++visits > RT_MAX_VISITS) {
-            rt_set_status(status, RT_ERR_ITER_LIMIT);
-            return;
-        }
-        if (ref >= 0) {
+        // "while-while" order (Aila and Laine, High Performance Graphics 2009): a
+        // lane descends through inner nodes until it holds a leaf, so that the
+        // lanes of a warp test their leaves together instead of interleaving leaf
+        // tests with node visits.  Each lane visits the same nodes in the same
+        // order as a one-node-per-step loop.
+        while (ref >= 0) {
+            if (++visits > RT_MAX_VISITS) {
+                rt_set_status(status, RT_ERR_ITER_LIMIT);
+                return;
+            }
             nvis++;
             const float4* np = reinterpret_cast<const float4*>(nodes + ref);
             float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
@@ -273,16 +278,20 @@ __device__ __forceinline__ void traverse(const BvhNode* __restrict__ nodes, cons
                 stack[sp * stride] = t0 <= t1 ? r1 : r0;
                 sp++;
                 ref = t0 <= t1 ? r0 : r1;
-                continue;
-            }
-            if (h0 || h1) {
+            } else if (h0 || h1) {
                 ref = h0 ? r0 : r1;
-                continue;
+            } else {
+                if (sp == 0) return;
+                sp--;
+                ref = stack[sp * stride];
             }
-        } else {
-            int e = ~ref;
-            if (leaf(e >> 3, (e & 7) + 1)) return;
         }
+        if (++visits > RT_MAX_VISITS) {
+            rt_set_status(status, RT_ERR_ITER_LIMIT);
+            return;
+        }
+        const int e = ~ref;
+        if (leaf(e >> 3, (e & 7) + 1)) return;
         if (sp == 0) return;
         sp--;
         ref = stack[sp * stride];
@@ -664,20 +673,19 @@ __device__ __forceinline__ void warp_count(unsigned long long* c, unsigned long 
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(c, v);
 }
 
-__device__ __forceinline__ float3 tri_normal_f(const float4* tris_orig, int id) {
-    float4 p0 = __ldg(tris_orig + 3 * id), p1 = __ldg(tris_orig + 3 * id + 1), p2 = __ldg(tris_orig + 3 * id + 2);
-    float ex = p1.x - p0.x, ey = p1.y - p0.y, ez = p1.z - p0.z;
-    float fx = p2.x - p0.x, fy = p2.y - p0.y, fz = p2.z - p0.z;
-    float nx = ey * fz - ez * fy, ny = ez * fx - ex * fz, nz = ex * fy - ey * fx;
-    float inv = rsqrtf(nx * nx + ny * ny + nz * nz);
-    return make_float3(nx * inv, ny * inv, nz * inv);
+// FP32 unit normal of triangle id: the FP64 normal rounded to FP32, read from the
+// plane record (n, n.v0) of the triangle table (one load, and within one rounding
+// of the normal the FP64 re-trace reflects about).
+__device__ __forceinline__ float3 tri_normal_f(const float4* tri_plane, int id) {
+    const float4 pl = __ldg(tri_plane + 3 * id);
+    return make_float3(pl.x, pl.y, pl.z);
 }
 
 // Persistent SBR: every lane owns one ray; a lane whose ray ended takes the next
 // ray index from a global counter (one atomic per warp refill), so warps stay
 // full across bounces (warp-level compaction of the active rays).  One loop
 // iteration = one closest-hit query per active lane.
-__global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* __restrict__ tris_orig) {
+__global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* __restrict__ tri_plane) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -744,7 +752,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
             ray = -1;
             continue;
         }
-        float3 n = tri_normal_f(tris_orig, id);
+        float3 n = tri_normal_f(tri_plane, id);
         V3<float> nn = mk(n.x, n.y, n.z);
         V3<float> p = r.o + th * r.d;
         r.d = r.d - (2.0f * dot(r.d, nn)) * nn;
@@ -1725,7 +1733,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         }
         int blocks = ctx->num_sms * ctx->tune_sbr_blocks_per_sm;
         mark(ctx, 6);
-        k_sbr<<<blocks, TRACE_THREADS, stack_bytes, st>>>(A, sc->d_tri_v); RT_COUNT(ctx);
+        k_sbr<<<blocks, TRACE_THREADS, stack_bytes, st>>>(A, sc->d_tri_bary); RT_COUNT(ctx);
         mark(ctx, 7);
         RT_CK_LAUNCH(ctx);
         k_sbr_redo<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 2 * CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(
@@ -2059,7 +2067,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
     WRay<float> r;
     const BvhNode* nodes = nullptr;
     const float4* bvh_tris = nullptr;
-    const float4* tri_v = nullptr;
+    const float4* tri_plane = nullptr;   // the scene's plane records (tri_normal_f)
     unsigned long long* table = nullptr;
     unsigned long long* uniq = nullptr;
     float eps = 0.f;
@@ -2085,7 +2093,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
                     key = 0;
                     nodes = d.nodes;
                     bvh_tris = d.bvh_tris;
-                    tri_v = d.tri_v;
+                    tri_plane = d.tri_bary;
                     eps = (float)d.eps;
                     table = A.tables + (uint64_t)s * A.cap;
                     uniq = A.uniq + s;
@@ -2129,7 +2137,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
             ray = -1;
             continue;
         }
-        float3 nrm = tri_normal_f(tri_v, id);
+        float3 nrm = tri_normal_f(tri_plane, id);
         V3<float> nn = mk(nrm.x, nrm.y, nrm.z);
         V3<float> p = r.o + th * r.d;
         r.d = r.d - (2.0f * dot(r.d, nn)) * nn;

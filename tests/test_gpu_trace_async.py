@@ -47,8 +47,11 @@ def test_async_trace_matches_waiting_trace(rt):
             assert p1.n_paths >= p0.n_paths           # slots
             got = _step(rt, ctx, p1, sc, eps, sig, T, w, N)   # on unresolved paths
             assert got[0] == ref[0]
-            for x, y in zip(got[1:], ref[1:]):   # float atomics: the order of the sums varies
-                np.testing.assert_allclose(x, y, rtol=1e-6, atol=0)
+            # the gradients are sums over all paths with float atomics, whose order
+            # varies from run to run; the gain gradient sums terms of both signs, so
+            # its rounding is relative to the largest terms, not to the sum
+            for x, y in zip(got[1:], ref[1:]):
+                np.testing.assert_allclose(x, y, rtol=1e-5, atol=0)
             assert torch.equal(p1.rx_offsets, p0.rx_offsets)
             p1.resolve()
             assert p1.n_paths == p0.n_paths
