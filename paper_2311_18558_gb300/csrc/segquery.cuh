@@ -102,11 +102,14 @@ __device__ __forceinline__ void walk(const BvhNode* __restrict__ nodes, const Ra
     int stack[DF_STACK];
     int sp = 0, ref = 0, visits = 0;
     for (;;) {
-        if (++visits > DF_MAX_VISITS) {
-            rt_set_status(status, RT_ERR_ITER_LIMIT);
-            return;
-        }
-        if (ref >= 0) {
+        // descend until this lane holds a leaf, so that a warp's lanes test their
+        // leaves together ("while-while" order; the nodes and their order per lane
+        // are those of a one-node-per-step loop)
+        while (ref >= 0) {
+            if (++visits > DF_MAX_VISITS) {
+                rt_set_status(status, RT_ERR_ITER_LIMIT);
+                return;
+            }
             const float4* np = reinterpret_cast<const float4*>(nodes + ref);
             const float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
             const int4 d = __ldg(reinterpret_cast<const int4*>(np + 3));
@@ -119,16 +122,19 @@ __device__ __forceinline__ void walk(const BvhNode* __restrict__ nodes, const Ra
                 }
                 stack[sp++] = d.y;
                 ref = d.x;
-                continue;
-            }
-            if (h0 || h1) {
+            } else if (h0 || h1) {
                 ref = h0 ? d.x : d.y;
-                continue;
+            } else {
+                if (sp == 0) return;
+                ref = stack[--sp];
             }
-        } else {
-            const int e = ~ref;
-            if (leaf(e >> 3, (e & 7) + 1)) return;
         }
+        if (++visits > DF_MAX_VISITS) {
+            rt_set_status(status, RT_ERR_ITER_LIMIT);
+            return;
+        }
+        const int e = ~ref;
+        if (leaf(e >> 3, (e & 7) + 1)) return;
         if (sp == 0) return;
         ref = stack[--sp];
     }
