@@ -561,6 +561,20 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_upload(rt_c
     sc->ctx = ctx;
     sc->n_tris = n_tris;
     sc->n_nodes = (int)dn.size();
+    {
+        // most inner nodes on a root-to-leaf path: a traversal pushes at most one
+        // child per inner node of its current path
+        std::vector<std::pair<int, int>> st{{0, 1}};
+        int depth = 1;
+        while (!st.empty()) {
+            const auto [n, dd] = st.back();
+            st.pop_back();
+            depth = std::max(depth, dd);
+            for (int c : {dn[n].d.x, dn[n].d.y})
+                if (c >= 0) st.push_back({c, dd + 1});
+        }
+        sc->bvh_depth = depth;
+    }
     sc->n_materials = n_materials;
     sc->diag = diag;
     for (int k = 0; k < 3; ++k) {

@@ -78,6 +78,7 @@ struct __align__(16) BvhNode {
 struct rt_scene {
     rt_ctx* ctx = nullptr;
     int n_tris = 0, n_nodes = 0, n_materials = 0;
+    int bvh_depth = 0;                 // most inner nodes on a root-to-leaf path (traversal stack bound)
     double diag = 0.0;
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};   // bounding box of the vertices [m]
     double eps = 0.0;                  // 1e-6 * diag: hit and segment guard [m]

@@ -244,7 +244,7 @@ __device__ __forceinline__ bool slab(const R& r, float lx, float ly, float lz, f
 // (stack[k * blockDim.x + threadIdx.x]), nearer child first.  `leaf(first,
 // count)` tests the triangles of a leaf and returns true to stop; it may lower
 // `thi`, the far end of the box tests.  Node visits are bounded.
-template <typename R, typename Leaf>
+template <int STACK = RT_STACK, typename R, typename Leaf>
 __device__ __forceinline__ void traverse(const BvhNode* __restrict__ nodes, const R& r, float tlo, const float& thi,
                                          int* stack, int32_t* status, unsigned& nvis, Leaf&& leaf) {
     const int stride = blockDim.x;
@@ -271,7 +271,7 @@ __device__ __forceinline__ void traverse(const BvhNode* __restrict__ nodes, cons
             bool h1 = slab(r, b.z, b.w, c.x, c.y, c.z, c.w, tlo, thi, t1);
             const int r0 = d.x, r1 = d.y;
             if (h0 && h1) {
-                if (sp >= RT_STACK) {
+                if (sp >= STACK) {
                     rt_set_status(status, RT_ERR_STACK_OVERFLOW);
                     return;
                 }
@@ -300,13 +300,14 @@ __device__ __forceinline__ void traverse(const BvhNode* __restrict__ nodes, cons
 
 // FP32 closest hit with t > tmin (skipping `skip`): exact ties go to the lower
 // triangle index; `und` is set if any decision that could matter was marginal.
+template <int STACK = RT_STACK>
 __device__ __forceinline__ int closest32(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris,
                                          const WRay<float>& r, float tmin, int skip, int* stack, float& t_out,
                                          bool& und, int32_t* status, unsigned& nvis, unsigned& ntri,
                                          bool launch_ray = false) {
     float tb = INFINITY, thi = INFINITY;
     int best = -1;
-    traverse(nodes, r, tmin * 0.5f, thi, stack, status, nvis, [&](int first, int count) {
+    traverse<STACK>(nodes, r, tmin * 0.5f, thi, stack, status, nvis, [&](int first, int count) {
         for (int k = first; k < first + count; ++k) {
             float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
             int id = __float_as_int(p0.w);
@@ -685,6 +686,7 @@ __device__ __forceinline__ float3 tri_normal_f(const float4* tri_plane, int id) 
 // ray index from a global counter (one atomic per warp refill), so warps stay
 // full across bounces (warp-level compaction of the active rays).  One loop
 // iteration = one closest-hit query per active lane.
+template <int STACK>
 __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* __restrict__ tri_plane) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
@@ -726,7 +728,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
         float th;
         bool und = false;
         unsigned nv = 0, nt = 0;
-        int id = closest32(A.nodes, A.tris, r, eps, prev, stack, th, und, A.status, nv, nt, bounce == 0);
+        int id = closest32<STACK>(A.nodes, A.tris, r, eps, prev, stack, th, und, A.status, nv, nt, bounce == 0);
         c_vis += nv;
         c_tri += nt;
         c_q++;
@@ -1733,7 +1735,13 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         }
         int blocks = ctx->num_sms * ctx->tune_sbr_blocks_per_sm;
         mark(ctx, 6);
-        k_sbr<<<blocks, TRACE_THREADS, stack_bytes, st>>>(A, sc->d_tri_bary); RT_COUNT(ctx);
+        // a stack of 32 entries when the scene's tree allows it: half the shared
+        // memory per block, so more blocks of the latency-bound kernel per SM
+        if (sc->bvh_depth <= 32)
+            k_sbr<32><<<blocks, TRACE_THREADS, (size_t)32 * TRACE_THREADS * sizeof(int), st>>>(A, sc->d_tri_bary);
+        else
+            k_sbr<RT_STACK><<<blocks, TRACE_THREADS, stack_bytes, st>>>(A, sc->d_tri_bary);
+        RT_COUNT(ctx);
         mark(ctx, 7);
         RT_CK_LAUNCH(ctx);
         k_sbr_redo<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 2 * CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(
