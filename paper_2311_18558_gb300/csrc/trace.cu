@@ -2063,6 +2063,7 @@ struct BatchSbr {
 // Scene descriptor fields a lane needs on every bounce are loaded once, when the
 // lane takes a ray, and kept in registers (lanes of one warp may hold rays of
 // different scenes).
+template <int STACK>
 __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
@@ -2119,7 +2120,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
         float th;
         bool und = false;
         unsigned nv = 0, nt = 0;
-        int id = closest32(nodes, bvh_tris, r, eps, prev, stack, th, und, A.status, nv, nt, bounce == 0);
+        int id = closest32<STACK>(nodes, bvh_tris, r, eps, prev, stack, th, und, A.status, nv, nt, bounce == 0);
         c_vis += nv;
         c_tri += nt;
         c_q++;
@@ -2861,7 +2862,13 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         }
         mark(ctx, 0);
         mark(ctx, 6);
-        k_sbr_batch<<<ctx->num_sms * ctx->tune_sbr_blocks_per_sm, TRACE_THREADS, stack_bytes, st>>>(A);
+        int depth_max = 0;   // the deepest tree of the batch sizes the traversal stack (as rt_trace_paths)
+        for (int s2 = 0; s2 < n; ++s2) depth_max = std::max(depth_max, scenes[s2]->bvh_depth);
+        if (depth_max <= 32)
+            k_sbr_batch<32><<<ctx->num_sms * ctx->tune_sbr_blocks_per_sm, TRACE_THREADS,
+                              (size_t)32 * TRACE_THREADS * sizeof(int), st>>>(A);
+        else
+            k_sbr_batch<RT_STACK><<<ctx->num_sms * ctx->tune_sbr_blocks_per_sm, TRACE_THREADS, stack_bytes, st>>>(A);
         RT_COUNT(ctx);
         mark(ctx, 7);
         BCK(cudaGetLastError());
