@@ -197,6 +197,57 @@ __device__ __forceinline__ int tri_test32_launch(const WRay<float>& r, float4 p0
     return 2;
 }
 
+// tri_test32 for the FP32 rounding rf of an FP64 ray r (the re-trace): rf's origin
+// and direction differ from r's by one rounding each, so the margin is that of
+// tri_test32_launch for the origin plus the direction's rounding.  That moves
+// S_x, S_y by at most 2 sqrt(3) u (kz the largest component of a unit-length
+// direction) and so a sheared vertex coordinate by 3.47 u Z, Z the vertices'
+// largest |X_kz|, and an edge function by 4 L (3.47 u Z).  A robust hit also gets
+// t_err, a bound on |t - tf| with t the exact hit distance along r: for a robust
+// hit det = |U| + |V| + |W| = sum, each edge function is off by at most e (half
+// the rounding part of the margin), a translated coordinate X_kz by
+// u (|X_kz| + |o_kz|), so Tn = (U Akz + V Bkz + W Ckz) Sz is off by at most
+// |Sz| (e (|Akz| + |Bkz| + |Ckz|) + 8 u sum (Z + |o_kz|)) + 6 u |Tn| (the
+// roundings of the products and sums included), det by 3 e + 2 u sum, and
+// t_err = (|dTn| + t |ddet|) / (sum - 3 e) + 2 u t.
+__device__ __forceinline__ int tri_test32_exact(const WRay<float>& r, float4 p0, float4 p1, float4 p2,
+                                                float& t_out, float& t_err) {
+    const V3<float> A = from4<float>(p0) - r.o, B = from4<float>(p1) - r.o, C = from4<float>(p2) - r.o;
+    const float Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
+    const float Akx = comp(A, r.kx), Aky = comp(A, r.ky), Bkx = comp(B, r.kx), Bky = comp(B, r.ky);
+    const float Ckx = comp(C, r.kx), Cky = comp(C, r.ky);
+    const float Ax = Akx - r.Sx * Akz, Ay = Aky - r.Sy * Akz;
+    const float Bx = Bkx - r.Sx * Bkz, By = Bky - r.Sy * Bkz;
+    const float Cx = Ckx - r.Sx * Ckz, Cy = Cky - r.Sy * Ckz;
+    const float U = Cx * By - Cy * Bx, V = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
+    const float Sab = fabsf(r.Sx) + fabsf(r.Sy);
+    const float Mv = fmaxf(fmaxf(fabsf(Akx) + fabsf(Aky) + fabsf(Akz) * Sab, fabsf(Bkx) + fabsf(Bky) + fabsf(Bkz) * Sab),
+                           fabsf(Ckx) + fabsf(Cky) + fabsf(Ckz) * Sab);
+    const float okz = fabsf(comp(r.o, r.kz));
+    const float Mo = fabsf(comp(r.o, r.kx)) + fabsf(comp(r.o, r.ky)) + okz * Sab;
+    const float L = fmaxf(fmaxf(fmaxf(fabsf(Ax), fabsf(Ay)), fmaxf(fabsf(Bx), fabsf(By))), fmaxf(fabsf(Cx), fabsf(Cy)));
+    const float Z = fmaxf(fmaxf(fabsf(Akz), fabsf(Bkz)), fabsf(Ckz));
+    const float u = 5.9604645e-8f;
+    const float e = 1.01f * (u * (4.0f * L * L + 12.0f * (Mv + Mo) * L) + 4.0f * L * 3.47f * u * Z);
+    const float sum = fabsf(U) + fabsf(V) + fabsf(W);
+    const float m = 2.0f * e + 2.0f * (float)TRI_TOL * sum;
+    const bool pos = U > m && V > m && W > m;
+    const bool neg = U < -m && V < -m && W < -m;
+    const float det = U + V + W;
+    const float Tn = (U * Akz + V * Bkz + W * Ckz) * r.Sz;
+    if (pos || neg) {
+        t_out = Tn / det;
+        const float dTn = fabsf(r.Sz) * (e * (fabsf(Akz) + fabsf(Bkz) + fabsf(Ckz)) + 8.0f * u * sum * (Z + okz)) +
+                          6.0f * u * fabsf(Tn);
+        const float ddet = 3.0f * e + 2.0f * u * sum;
+        t_err = 1.01f * ((dTn + fabsf(t_out) * ddet) / (sum - 3.0f * e) + 2.0f * u * fabsf(t_out));
+        return 1;
+    }
+    if ((U < -m || V < -m || W < -m) && (U > m || V > m || W > m)) return 0;
+    t_out = det != 0.0f ? Tn / det : 0.0f;
+    return 2;
+}
+
 // FP64 final decision: the triangle grown by TRI_TOL; a ray in its plane misses.
 // On a hit returns true with det > 0 and t = Tn / det (not divided here).
 __device__ __forceinline__ bool tri_test64(const WRay<double>& r, float4 p0, float4 p1, float4 p2, double& Tn,
@@ -436,6 +487,21 @@ __device__ int closest64_inline(const BvhNode* __restrict__ nodes, const float4*
     return low == 0x7fffffff ? best : low;
 }
 
+// The hit of a bounce whose triangle is known (a robust prefix bounce of the
+// re-trace, or a closest hit decided in FP32 with error bounds): t where the FP64 ray meets the triangle's FP64 plane n.x = c,
+// t = (c - n.o) / (n.d), a dozen FP64 operations instead of the full
+// ray/triangle test (the FP64 pipe bounds this kernel).  False if the ray is
+// (nearly) parallel to the plane or t <= tmin, which the caller treats as
+// undecided.
+__device__ __forceinline__ bool replay_plane(const double* __restrict__ tri_n64, int id, const WRay<double>& r,
+                                             double tmin, double& t_out) {
+    const double nx = tri_n64[4 * id], ny = tri_n64[4 * id + 1], nz = tri_n64[4 * id + 2], c = tri_n64[4 * id + 3];
+    const double nd = nx * r.d.x + ny * r.d.y + nz * r.d.z;
+    if (!(fabs(nd) > 1e-9)) return false;
+    t_out = (c - (nx * r.o.x + ny * r.o.y + nz * r.o.z)) * rcp64(nd);
+    return t_out > tmin;
+}
+
 // Same decisions as closest64_inline, with the FP64 work taken out of the
 // divergent traversal.  An FP64 warp instruction costs the same with one active
 // lane as with 32, so FP64 tests inside the traversal loop are paid on every
@@ -450,9 +516,9 @@ __device__ int closest64_inline(const BvhNode* __restrict__ nodes, const float4*
 // closest64_inline.
 constexpr int CAND_CAP = 16;
 
-__device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const WRay<double>& r,
-                         const WRay<float>& rf, double tmin, int skip, int* stack, int* cand, float* cand_t,
-                         double& t_out, int32_t* status) {
+__device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, WRay<double>& r,
+                         const WRay<float>& rf, const double* __restrict__ tri_n64, double tmin, int skip, int* stack,
+                         int* cand, float* cand_t, float* cand_e, double& t_out, int32_t* status) {
     const int stride = blockDim.x;
     const float tminf = (float)tmin;
     float thi = INFINITY;
@@ -463,29 +529,66 @@ __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __rest
             float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
             int id = __float_as_int(p0.w);
             if (id == skip) continue;
-            float tf;
-            int cls = tri_test32(rf, p0, p1, p2, tf);
+            float tf, te = 0.0f;
+            int cls = tri_test32_exact(rf, p0, p1, p2, tf, te);
             if (cls == 0) continue;
             if (cls == 1) {
-                if (tf > thi) continue;   // beyond a robust hit
-                if (tf > tminf * 2.0f) thi = fminf(thi, tf * 1.001f + 10.0f * tminf);
+                if (tf - te > thi) continue;   // beyond a robust hit
+                if (tf > tminf * 2.0f) thi = fminf(thi, tf * 1.001f + 10.0f * tminf + 4.0f * te);
             } else {
                 tf = -1.0f;   // undecided: always goes to the FP64 test
             }
             if (n < CAND_CAP) {
                 cand[n * stride] = k;
                 cand_t[n * stride] = tf;
+                cand_e[n * stride] = te;
             }
             n++;
         }
         return false;
     });
+    if (n <= CAND_CAP) {
+        // decided in FP32 when every candidate is a robust hit and the nearest one
+        // beyond tmin is separated from tmin and from every other by more than
+        // their error bounds: that triangle is the FP64 test's closest hit, and its
+        // distance along r comes from its FP64 plane
+        bool fast = true;
+        int ib = -1;
+        float tb = INFINITY, eb = 0.0f;
+        for (int i = 0; i < n && fast; ++i) {
+            const float t = cand_t[i * stride], te = cand_e[i * stride];
+            if (t < 0.0f) fast = false;                       // undecided edge
+            else if (t - te > tminf) {
+                if (t < tb) {
+                    tb = t;
+                    eb = te;
+                    ib = i;
+                }
+            } else if (t + te >= tminf) fast = false;         // not clear of tmin
+        }
+        for (int i = 0; i < n && fast && ib >= 0; ++i) {
+            if (i == ib) continue;
+            const float t = cand_t[i * stride], te = cand_e[i * stride];
+            if (t - te > tminf && !(t - te > tb + eb)) fast = false;   // not clearly farther
+        }
+        if (fast) {
+            if (ib < 0) return -1;   // every candidate clearly before tmin
+            const int k = cand[ib * stride];
+            const int id = __float_as_int(__ldg(tris + 3 * k).w);
+            double th;
+            if (replay_plane(tri_n64, id, r, tmin, th)) {
+                t_out = th;
+                return id;
+            }
+        }
+    }
+    wray_init(r);   // the FP64 tests below need the ray's shear
     if (n > CAND_CAP) return closest64_inline(nodes, tris, r, rf, tmin, skip, stack, t_out, status);
     double bT = 0.0, bD = 1.0;
     bool have = false, near_tie = false;
     int best = -1;
     for (int i = 0; i < n; ++i) {
-        if (cand_t[i * stride] > thi) continue;   // a robust hit beyond the final far end
+        if (cand_t[i * stride] - cand_e[i * stride] > thi) continue;   // a robust hit beyond the final far end
         const int k = cand[i * stride];
         float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
         int id = __float_as_int(p0.w);
@@ -501,13 +604,13 @@ __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __rest
         }
     }
     if (!have) return -1;
-    const double tb = bT * rcp64(bD);
-    t_out = tb;
+    const double tb64 = bT * rcp64(bD);
+    t_out = tb64;
     if (!near_tie) return best;
-    const double tmax = tb + TIE_TOL * tb;
+    const double tmax = tb64 + TIE_TOL * tb64;
     int low = 0x7fffffff;
     for (int i = 0; i < n; ++i) {
-        if (cand_t[i * stride] > thi) continue;
+        if (cand_t[i * stride] - cand_e[i * stride] > thi) continue;
         const int k = cand[i * stride];
         float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
         int id = __float_as_int(p0.w);
@@ -776,21 +879,6 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
 // left undecided were decided robustly, so their triangles (in the stored key)
 // are replayed with one FP64 ray/triangle test each; the BVH search in
 // mixed precision (closest64) starts at the undecided bounce.
-// The hit of a robust prefix bounce, whose triangle the FP32 pass decided with
-// margin: t where the FP64 ray meets the triangle's FP64 plane n.x = c,
-// t = (c - n.o) / (n.d), a dozen FP64 operations instead of the full
-// ray/triangle test (the FP64 pipe bounds this kernel).  False if the ray is
-// (nearly) parallel to the plane or t <= tmin, which the caller treats as
-// undecided.
-__device__ __forceinline__ bool replay_plane(const double* __restrict__ tri_n64, int id, const WRay<double>& r,
-                                             double tmin, double& t_out) {
-    const double nx = tri_n64[4 * id], ny = tri_n64[4 * id + 1], nz = tri_n64[4 * id + 2], c = tri_n64[4 * id + 3];
-    const double nd = nx * r.d.x + ny * r.d.y + nz * r.d.z;
-    if (!(fabs(nd) > 1e-9)) return false;
-    t_out = (c - (nx * r.o.x + ny * r.o.y + nz * r.o.z)) * rcp64(nd);
-    return t_out > tmin;
-}
-
 __device__ __forceinline__ uint64_t key_prefix(uint64_t key, int b) {   // the fields of bounces < b
     return b <= 0 ? 0ull : key & (~0ull << (48 - 16 * (b - 1)));
 }
@@ -801,6 +889,7 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const doub
     int* stack = smem_stack + threadIdx.x;
     int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
     float* cand_t = reinterpret_cast<float*>(smem_stack + (RT_STACK + CAND_CAP) * blockDim.x) + threadIdx.x;
+    float* cand_e = reinterpret_cast<float*>(smem_stack + (RT_STACK + 2 * CAND_CAP) * blockDim.x) + threadIdx.x;
     unsigned long long n = *A.redo_count;
     if (n > (unsigned long long)A.redo_cap) n = A.redo_cap;
     if (A.counters && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.counters + 3, n);
@@ -833,11 +922,10 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const doub
                 }
             }
             if (b >= b0) {
-                wray_init(r);
                 rf.o = mk((float)r.o.x, (float)r.o.y, (float)r.o.z);
                 rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
                 wray_init(rf);
-                id = closest64(A.nodes, A.tris, r, rf, A.eps, prev, stack, cand, cand_t, th, A.status);
+                id = closest64(A.nodes, A.tris, r, rf, tri_n64, A.eps, prev, stack, cand, cand_t, cand_e, th, A.status);
                 if (id < 0) break;
                 key = rt_key_push(key_prefix(key, b), b, id);
                 hash_insert(A.table, A.mask, key, A.uniq, A.uniq_limit, A.overflow);
@@ -1744,7 +1832,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         RT_COUNT(ctx);
         mark(ctx, 7);
         RT_CK_LAUNCH(ctx);
-        k_sbr_redo<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 2 * CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(
+        k_sbr_redo<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 3 * CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(
             A, sc->d_tri_n64, sc->d_tri_v);
         RT_COUNT(ctx);
         mark(ctx, 1);
@@ -2166,6 +2254,7 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo_batch(BatchSbr A) {
     int* stack = smem_stack + threadIdx.x;
     int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
     float* cand_t = reinterpret_cast<float*>(smem_stack + (RT_STACK + CAND_CAP) * blockDim.x) + threadIdx.x;
+    float* cand_e = reinterpret_cast<float*>(smem_stack + (RT_STACK + 2 * CAND_CAP) * blockDim.x) + threadIdx.x;
     unsigned long long n = *A.redo_count;
     if (n > (unsigned long long)A.redo_cap) n = A.redo_cap;
     if (A.counters && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.counters + 3, n);
@@ -2200,11 +2289,11 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo_batch(BatchSbr A) {
                 }
             }
             if (b >= b0) {
-                wray_init(r);
                 rf.o = mk((float)r.o.x, (float)r.o.y, (float)r.o.z);
                 rf.d = mk((float)r.d.x, (float)r.d.y, (float)r.d.z);
                 wray_init(rf);
-                id = closest64(d.nodes, d.bvh_tris, r, rf, d.eps, prev, stack, cand, cand_t, th, A.status);
+                id = closest64(d.nodes, d.bvh_tris, r, rf, d.tri_n64, d.eps, prev, stack, cand, cand_t, cand_e, th,
+                               A.status);
                 if (id < 0) break;
                 key = rt_key_push(key_prefix(key, b), b, id);
                 hash_insert(A.tables + (uint64_t)s * A.cap, A.cap - 1, key, A.uniq + s, A.uniq_limit, A.overflow);
@@ -2872,7 +2961,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         RT_COUNT(ctx);
         mark(ctx, 7);
         BCK(cudaGetLastError());
-        k_sbr_redo_batch<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 2 * CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(A);
+        k_sbr_redo_batch<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 3 * CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(A);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
         mark(ctx, 1);
