@@ -536,7 +536,19 @@ __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __rest
                 if (tf - te > thi) continue;   // beyond a robust hit
                 if (tf > tminf * 2.0f) thi = fminf(thi, tf * 1.001f + 10.0f * tminf + 4.0f * te);
             } else {
-                tf = -1.0f;   // undecided: always goes to the FP64 test
+                // undecided (NaN: always goes to the FP64 test); te becomes a lower
+                // bound of t over the whole triangle: a hit point is a convex
+                // combination of the vertices, so t >= min_k (X_k - o).d / |d|^2.
+                // The FP32 dots with rf differ from those with the FP64 ray by at
+                // most 8 u (max_k |X_k - o|_1 + |o|_1) for a unit d (roundings of the
+                // subtractions and products, and rf's own rounding of o and d)
+                const V3<float> da = from4<float>(p0) - rf.o, db = from4<float>(p1) - rf.o, dc = from4<float>(p2) - rf.o;
+                const float lo = fminf(fminf(dot(da, rf.d), dot(db, rf.d)), dot(dc, rf.d));
+                const float R = fmaxf(fmaxf(fabsf(da.x) + fabsf(da.y) + fabsf(da.z), fabsf(db.x) + fabsf(db.y) + fabsf(db.z)),
+                                      fabsf(dc.x) + fabsf(dc.y) + fabsf(dc.z)) +
+                                fabsf(rf.o.x) + fabsf(rf.o.y) + fabsf(rf.o.z);
+                te = (lo - 8.0f * 5.9604645e-8f * R) * (1.0f - 1e-6f) - 1e-30f;
+                tf = __int_as_float(0x7fc00000);
             }
             if (n < CAND_CAP) {
                 cand[n * stride] = k;
@@ -557,8 +569,8 @@ __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __rest
         float tb = INFINITY, eb = 0.0f;
         for (int i = 0; i < n && fast; ++i) {
             const float t = cand_t[i * stride], te = cand_e[i * stride];
-            if (t < 0.0f) fast = false;                       // undecided edge
-            else if (t - te > tminf) {
+            if (t != t) continue;                             // undecided edge: checked below
+            if (t - te > tminf) {
                 if (t < tb) {
                     tb = t;
                     eb = te;
@@ -566,10 +578,15 @@ __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __rest
                 }
             } else if (t + te >= tminf) fast = false;         // not clear of tmin
         }
-        for (int i = 0; i < n && fast && ib >= 0; ++i) {
+        for (int i = 0; i < n && fast; ++i) {
             if (i == ib) continue;
             const float t = cand_t[i * stride], te = cand_e[i * stride];
-            if (t - te > tminf && !(t - te > tb + eb)) fast = false;   // not clearly farther
+            if (t != t) {
+                // an undecided triangle only matters if some of it lies before the best
+                if (!(ib >= 0 && te > tb + eb)) fast = false;
+            } else if (ib >= 0 && t - te > tminf && !(t - te > tb + eb)) {
+                fast = false;                                 // not clearly farther
+            }
         }
         if (fast) {
             if (ib < 0) return -1;   // every candidate clearly before tmin
@@ -588,7 +605,8 @@ __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __rest
     bool have = false, near_tie = false;
     int best = -1;
     for (int i = 0; i < n; ++i) {
-        if (cand_t[i * stride] - cand_e[i * stride] > thi) continue;   // a robust hit beyond the final far end
+        // a robust hit beyond the final far end (NaN, undecided, compares false)
+        if (cand_t[i * stride] - cand_e[i * stride] > thi) continue;
         const int k = cand[i * stride];
         float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
         int id = __float_as_int(p0.w);
