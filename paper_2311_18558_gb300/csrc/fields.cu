@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(256, 3) k_fields_bwd(FieldArgs A, const float2
     __shared__ float s_col[REGM > 0 ? 2 * REGM * 256 : 1];
     if (REGM > 0)
         for (int k = threadIdx.x; k < 2 * REGM * 256; k += blockDim.x) s_col[k] = 0.0f;
+    __shared__ float4 s_fr[RT_MAX_DEPTH][256];   // (r_perp, r_par) of each bounce, per thread
     __syncthreads();
     float gain_acc = 0.0f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.P; i += (int64_t)gridDim.x * blockDim.x) {
@@ -254,16 +255,19 @@ __global__ void __launch_bounds__(256, 3) k_fields_bwd(FieldArgs A, const float2
         rec_slots(A, i, r);
         const float scale = A.amp / r.len;
         float2 v0 = make_float2(r.D[0].x, 0.0f), v1 = make_float2(r.D[0].z, 0.0f);
-        // forward walk: keep only the field entering every bounce
-        float2 in0[RT_MAX_DEPTH], in1[RT_MAX_DEPTH];
+        // forward walk: the Fresnel coefficients with their derivatives, once per
+        // bounce; the reverse walk needs the coefficients (kept in shared memory) and
+        // the derivatives times the field entering the bounce (p0, p1, in registers)
+        float2 p0[RT_MAX_DEPTH], p1[RT_MAX_DEPTH];
         float4 last = r.D[0];   // D_{q+1}
 #pragma unroll
         for (int j = 0; j < RT_MAX_DEPTH; ++j) {
             if (j < r.q) {
-                float2 rp, rl, unused;
-                bounce_coeffs<false>(A, s_eta, r, j, rp, rl, unused, unused);
-                in0[j] = v0;
-                in1[j] = v1;
+                float2 rp, rl, drp = make_float2(0.0f, 0.0f), drl = make_float2(0.0f, 0.0f);
+                bounce_coeffs<true>(A, s_eta, r, j, rp, rl, drp, drl);
+                p0[j] = cmul(drp, v0);
+                p1[j] = cmul(drl, v1);
+                s_fr[j][threadIdx.x] = make_float4(rp.x, rp.y, rl.x, rl.y);
                 const float2 g0 = cmul(rp, v0), g1 = cmul(rl, v1);
                 const float4 e = r.D[j + 1];
                 v0 = cadd(cscale(e.x, g0), cscale(e.y, g1));
@@ -275,16 +279,16 @@ __global__ void __launch_bounds__(256, 3) k_fields_bwd(FieldArgs A, const float2
         // Re(conj(g) a) / (2 g_T) and / (2 g_R) share Re(conj(g) a)
         gain_acc += g.x * a.x + g.y * a.y;
         // reverse walk: l = scale * (row 0 of D_{q+1}) . Gamma_q D_q ... is the row
-        // vector after bounce j; da/dr_perp_j = l[0] in0_j, da/dr_par_j = l[1] in1_j.
-        // The bounce's Fresnel coefficients are recomputed with their derivatives.
+        // vector after bounce j; da/deta_j = l[0] in0_j dr_perp_j + l[1] in1_j dr_par_j.
         float2 l0 = make_float2(scale * last.x, 0.0f), l1 = make_float2(scale * last.y, 0.0f);
 #pragma unroll
         for (int j = RT_MAX_DEPTH - 1; j >= 0; --j) {
             if (j < r.q) {
-                float2 rp, rl, drp, drl;
-                const int m = bounce_coeffs<true>(A, s_eta, r, j, rp, rl, drp, drl);
+                const float4 c = s_fr[j][threadIdx.x];
+                const float2 rp = make_float2(c.x, c.y), rl = make_float2(c.z, c.w);
+                const int m = (r.w[j].x & MAT_PEC) ? -1 : (PER_TRI ? r.t[PER_TRI ? j : 0] : r.w[j].x);
                 if (m >= 0) {
-                    const float2 da = cadd(cmul(cmul(l0, in0[j]), drp), cmul(cmul(l1, in1[j]), drl));
+                    const float2 da = cadd(cmul(l0, p0[j]), cmul(l1, p1[j]));
                     // Re(conj(g) da) and Im(conj(g) da)
                     const float re = g.x * da.x + g.y * da.y;
                     const float im = g.x * da.y - g.y * da.x;
