@@ -1106,14 +1106,85 @@ __global__ void k_cand_keys(const uint64_t* __restrict__ sorted, const unsigned 
     if (blockIdx.x == 0 && threadIdx.x == 0) *K_dev = n + 1;
 }
 
+// Last-bounce frustum of a candidate (image method, Sec. II-F).  A receiver x
+// completes the path only if the segment from x to the last image source I_q
+// crosses the last triangle: x lies beyond the triangle's plane as seen from
+// I_q, and inside the three planes through I_q and the triangle's edges.  Each
+// plane is stored in FP32 as a unit normal and offset, f(x) = N.x + w with
+// f >= 0 on the inside; F holds 4 such float4 and then (I_q, rho), plane-major
+// with stride `stride`.  Everything is formed in FP32 with u = 2^-24:
+//  * dI = n.(I_q - v0), the signed distance of I_q from the plane, to within
+//    8u (|I_q|_1 + |n.v0|); the frustum is used only where |dI| is 8 times
+//    that, so that its sign, which orients every plane, is exact
+//    (det(v0 - I, v1 - I, v2 - I) = -dI |(v1 - v0) x (v2 - v0)| fixes the edge
+//    planes' orientation too).
+//  * an edge normal a_i x a_{i+1}, a_i = v_i - I_q, carries the roundings of
+//    I_q and a_i (e_i = u (|I_q|_1 + |a_i|_1) per component) and of the cross
+//    product, so its unit normal is off by at most
+//    E_i = 2 (2 e_i |a_j|_1 + 2 e_j |a_i|_1 + 4 e_i e_j + 6 u |a_i|_1 |a_j|_1) / |N_i| + 5u,
+//    which moves f_i(x) by E_i |x - I_q|.
+//  * the grown triangle (barycentric >= -TRI_TOL): the crossing point p has
+//    f_i(p) >= -TRI_TOL |v_opp - I_q|, and x = I_q + s (p - I_q) with
+//    s <= |x - I_q| / |dI|, so f_i(x) >= -TRI_TOL max_v |v - I_q| / |dI| |x - I_q|.
+// rho bounds the sum of the last two per unit |x - I_q| (with a factor 2 of
+// room); the remaining roundings (of I_q, the offsets, the planes at a box) are
+// below 10u of the magnitudes |x|_1, |I_q|_1, |w_0|, which the tile test's
+// 1e-5 term covers.  The test is correct for any rho (at E >= 1 its margin
+// exceeds every |f_i|); rho < 0 marks a candidate whose frustum is not used
+// (no robust sign of dI, a degenerate edge, or rho > 0.5).
+__device__ __forceinline__ void frustum_store(V3<double> I64, const float4* __restrict__ tri_v,
+                                              const float4* __restrict__ tri_bary, int t, float4* F, int64_t stride,
+                                              int64_t k) {
+    const float u = 5.9604645e-8f;
+    const V3<float> I = mk((float)I64.x, (float)I64.y, (float)I64.z);
+    const float4 pl = __ldg(tri_bary + 3 * t);
+    const V3<float> v[3] = {from4<float>(__ldg(tri_v + 3 * t)), from4<float>(__ldg(tri_v + 3 * t + 1)),
+                            from4<float>(__ldg(tri_v + 3 * t + 2))};
+    const float I1 = fabsf(I.x) + fabsf(I.y) + fabsf(I.z);
+    const float dI = pl.x * I.x + pl.y * I.y + pl.z * I.z - pl.w;
+    const float errdI = 8.0f * u * (I1 + fabsf(pl.w));
+    float4 P[4];
+    float rho = -1.0f;
+    if (fabsf(dI) > 8.0f * errdI) {
+        const float sg = dI > 0.0f ? -1.0f : 1.0f;   // f(I_q) < 0 for plane 0, f(v_opp) > 0 for the edges
+        P[0] = make_float4(sg * pl.x, sg * pl.y, sg * pl.z, -sg * pl.w);
+        const V3<float> a[3] = {v[0] - I, v[1] - I, v[2] - I};
+        float a1[3], e[3], r2 = 0.0f, E = 0.0f;
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            a1[i] = fabsf(a[i].x) + fabsf(a[i].y) + fabsf(a[i].z);
+            e[i] = u * (I1 + a1[i]);
+            r2 = fmaxf(r2, dot(a[i], a[i]));
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int j = (i + 1) % 3;
+            const V3<float> N = cross(a[i], a[j]);
+            const float l2 = dot(N, N);
+            if (!(l2 > 1e-30f && l2 < 1e30f)) ok = false;
+            const float il = rsqrtf(l2);
+            const float dN = 2.0f * e[i] * a1[j] + 2.0f * e[j] * a1[i] + 4.0f * e[i] * e[j] + 6.0f * u * a1[i] * a1[j];
+            E = fmaxf(E, 2.0f * dN * il + 5.0f * u);
+            const float s = sg * il;
+            const V3<float> Nh = mk(s * N.x, s * N.y, s * N.z);
+            P[i + 1] = make_float4(Nh.x, Nh.y, Nh.z, -dot(Nh, I));
+        }
+        if (ok) rho = 2.0f * (1.2f * (float)TRI_TOL * sqrtf(r2) / fabsf(dI) + E);
+        if (!(rho <= 0.5f)) rho = -1.0f;   // a wider margin than that rejects almost nothing
+    }
+    for (int i = 0; i < 4; ++i) F[i * stride + k] = rho < 0.0f ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : P[i];
+    F[4 * stride + k] = make_float4(I.x, I.y, I.z, rho);
+}
+
 // Per candidate: length q, triangles, and the image sources I_1..I_q of the
 // transmitter (I_j = I_{j-1} - 2 ((I_{j-1} - a_j).n_j) n_j), FP64 and FP32.
 // The arrays hold Kc slots (slot-major, stride Kc); the slots from *K_dev on are
 // marked empty (depth -1) and produce no pairs.
 __global__ void k_candidates(const uint64_t* __restrict__ keys, int64_t Kc, const int64_t* __restrict__ K_dev, int D,
                              double tx, double ty, double tz, const float4* __restrict__ tri_v,
-                             const double* __restrict__ tri_n64, int32_t* cand_depth, int32_t* cand_tri, double* img64,
-                             float4* img32) {
+                             const double* __restrict__ tri_n64, const float4* __restrict__ tri_bary,
+                             int32_t* cand_depth, int32_t* cand_tri, double* img64, float4* img32, float4* frus) {
     const int64_t K = *K_dev;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Kc; k += (int64_t)gridDim.x * blockDim.x) {
         if (k >= K) {
@@ -1137,6 +1208,7 @@ __global__ void k_candidates(const uint64_t* __restrict__ keys, int64_t Kc, cons
             o[1] = I.y;
             o[2] = I.z;
             img32[(int64_t)j * Kc + k] = make_float4((float)I.x, (float)I.y, (float)I.z, 0.0f);
+            if (j == q - 1) frustum_store(I, tri_v, tri_bary, t, frus, Kc, k);
         }
     }
 }
@@ -1160,6 +1232,7 @@ struct CandView {
     const int32_t* tri;   // D x K
     const double* img64;  // D x K x 3
     const float4* img32;  // D x K
+    const float4* frus;   // 5 x K: last-bounce frustum (frustum_store); set for the prefilter only
 };
 
 // Back-trace of candidate k from receiver position rx (image method, FP64):
@@ -1199,56 +1272,178 @@ __device__ __forceinline__ bool backtrace64(const CandView& C, int64_t k, int q,
     return true;
 }
 
-// FP32 prefilter of one (candidate, receiver) pair: false only if the pair is
-// invalid by a clear margin.
-__device__ __forceinline__ bool prefilter32(const CandView& C, int64_t k, int q, float3 rx,
-                                           const float4* __restrict__ tri_bary) {
+// One back-trace step of the FP32 prefilter (Sec. II-F image method): from P
+// towards the image source I4 through the triangle with plane record pl and
+// barycentric planes g0, g1.  0 = the pair is invalid by a clear margin, 1 = the
+// step passes (P moves to the crossing point), 2 = undecided in FP32 (keep).
+__device__ __forceinline__ int prefilter_step(V3<float>& P, float4 I4, float4 pl, float4 g0, float4 g1) {
     const float m = PREFILTER_MARGIN;
-    V3<float> P = mk(rx.x, rx.y, rx.z);
+    V3<float> n = mk(pl.x, pl.y, pl.z);
+    V3<float> dir = mk(I4.x, I4.y, I4.z) - P;
+    float den = dot(n, dir);
+    if (fabsf(den) < 1e-20f) return 2;
+    // approximate division (a few ulp): far inside the prefilter's margin
+    float u = __fdividef(pl.w - dot(n, P), den);
+    if (u < -m || u > 1.0f + m) return 0;
+    V3<float> s = P + u * dir;
+    float l0 = g0.x * s.x + g0.y * s.y + g0.z * s.z + g0.w;
+    float l1 = g1.x * s.x + g1.y * s.y + g1.z * s.z + g1.w;
+    float l2 = 1.0f - l0 - l1;
+    if (l0 < -m || l1 < -m || l2 < -m) return 0;
+    P = s;
+    return 1;
+}
+
+// FP32 prefilter of bounces j = q..1 of candidate k from P (the receiver, or
+// the crossing point of bounce q + 1), as prefilter_step: 0 = invalid by a
+// clear margin, 1 = every step passes, 2 = undecided in FP32.
+__device__ __forceinline__ int prefilter32(const CandView& C, int64_t k, int q, V3<float> P,
+                                          const float4* __restrict__ tri_bary) {
     for (int j = q; j >= 1; --j) {
         int t = C.tri[(int64_t)(j - 1) * C.K + k];
         float4 I4 = C.img32[(int64_t)(j - 1) * C.K + k];
-        float4 pl = __ldg(tri_bary + 3 * t), g0 = __ldg(tri_bary + 3 * t + 1), g1 = __ldg(tri_bary + 3 * t + 2);
-        V3<float> n = mk(pl.x, pl.y, pl.z);
-        V3<float> dir = mk(I4.x, I4.y, I4.z) - P;
-        float den = dot(n, dir);
-        if (fabsf(den) < 1e-20f) return true;   // undecided in FP32
-        // approximate division (a few ulp): far inside the prefilter's margin
-        float u = __fdividef(pl.w - dot(n, P), den);
-        if (u < -m || u > 1.0f + m) return false;
-        V3<float> s = P + u * dir;
-        float l0 = g0.x * s.x + g0.y * s.y + g0.z * s.z + g0.w;
-        float l1 = g1.x * s.x + g1.y * s.y + g1.z * s.z + g1.w;
-        float l2 = 1.0f - l0 - l1;
-        if (l0 < -m || l1 < -m || l2 < -m) return false;
-        P = s;
+        const int st = prefilter_step(P, I4, __ldg(tri_bary + 3 * t), __ldg(tri_bary + 3 * t + 1),
+                                      __ldg(tri_bary + 3 * t + 2));
+        if (st != 1) return st;
     }
-    return true;
+    return 1;
+}
+
+// The FP32 back-trace of a queued pair (the prefilter's steps again, from the
+// receiver R): the crossing points s_q..s_1 and segment j from s_j to s_{j+1}
+// (s_0 = Tx, s_{q+1} = Rx), stored as origin with 1 / length in .w and vector.
+// Returns the prefilter's verdict (0 invalid, 1 valid, 2 undecided in FP32);
+// the segments are complete only for 1.
+__device__ __forceinline__ int backtrace32(const CandView& C, int64_t k, int q, V3<float> R, float3 txf,
+                                          const float4* __restrict__ tri_bary, unsigned long long w,
+                                          unsigned long long qcap, float4* seg_o, float4* seg_d) {
+    V3<float> next = R;
+    for (int j = q; j >= 0; --j) {
+        V3<float> P = mk(txf.x, txf.y, txf.z);
+        if (j >= 1) {
+            const int t = C.tri[(int64_t)(j - 1) * C.K + k];
+            P = next;
+            const int st = prefilter_step(P, C.img32[(int64_t)(j - 1) * C.K + k], __ldg(tri_bary + 3 * t),
+                                          __ldg(tri_bary + 3 * t + 1), __ldg(tri_bary + 3 * t + 2));
+            if (st != 1) return st;
+        }
+        const V3<float> d = next - P;
+        seg_o[(size_t)j * qcap + w] = make_float4(P.x, P.y, P.z, rsqrtf(dot(d, d)));
+        seg_d[(size_t)j * qcap + w] = make_float4(d.x, d.y, d.z, 0.0f);
+        next = P;
+    }
+    return 1;
+}
+
+// The prefilter's queue of surviving (candidate, receiver) pairs.
+struct PairSink {
+    uint2* queue;
+    unsigned long long* qcount;
+    unsigned long long qcap;
+    int32_t* overflow;
+};
+
+__device__ __forceinline__ float4 shfl4(float4 v, int src) {
+    return make_float4(__shfl_sync(FULL, v.x, src), __shfl_sync(FULL, v.y, src), __shfl_sync(FULL, v.z, src),
+                       __shfl_sync(FULL, v.w, src));
 }
 
 constexpr int PAIR_CC = 32;   // candidates per warp tile (receivers per tile: 32 lanes)
+static_assert(PAIR_CC == 32, "one candidate per lane in the tile's frustum test");
+
+// Order-preserving map of a float to an int and back, for warp min/max.
+__device__ __forceinline__ int float_order(float x) {
+    const int i = __float_as_int(x);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float order_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+__device__ __forceinline__ float warp_minf(float x) { return order_float(__reduce_min_sync(FULL, float_order(x))); }
+__device__ __forceinline__ float warp_maxf(float x) { return order_float(__reduce_max_sync(FULL, float_order(x))); }
+
+// False only if no receiver in the box (centre c, half extents h) can complete
+// candidate k's path through its last triangle (frustum_store): some plane's
+// largest value over the box is below minus the margin, which covers the
+// grown triangle (rho |x - I_q|) and the FP32 roundings of the planes, the
+// receivers and the box (1e-5 of the magnitudes involved, far above them).
+__device__ __forceinline__ bool frustum_pass(const float4* __restrict__ F, int64_t stride, int64_t k, float3 c,
+                                             float3 h) {
+    const float4 Ir = __ldg(F + 4 * stride + k);
+    if (Ir.w < 0.0f) return true;
+    const float hs = h.x + h.y + h.z;
+    const float4 p0 = __ldg(F + k);
+    const float m = 1e-5f * (fabsf(c.x) + fabsf(c.y) + fabsf(c.z) + hs + fabsf(Ir.x) + fabsf(Ir.y) + fabsf(Ir.z) +
+                             fabsf(p0.w)) +
+                    Ir.w * (fabsf(c.x - Ir.x) + fabsf(c.y - Ir.y) + fabsf(c.z - Ir.z) + hs);
+    bool pass = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 P = i == 0 ? p0 : __ldg(F + i * stride + k);
+        const float f = P.x * c.x + P.y * c.y + P.z * c.z + P.w + fabsf(P.x) * h.x + fabsf(P.y) * h.y + fabsf(P.z) * h.z;
+        pass = pass && f >= -m;
+    }
+    return pass;
+}
 
 // One warp tile of the image-method prefilter: 32 receivers (one per lane, kept
-// in registers) against up to PAIR_CC consecutive candidates (candidate data is
-// read once per warp and broadcast).  Survivors are appended to the queue as
-// (global candidate, global receiver), one atomic per warp and candidate.
+// in registers) against up to PAIR_CC consecutive candidates.  First each lane
+// tests one candidate's last-bounce frustum against the bounding box of the
+// tile's receivers; only the candidates that pass are prefiltered per receiver
+// (candidate data read once per warp and broadcast).  Survivors are appended to
+// the queue as (global candidate, global receiver), one atomic per warp and
+// candidate.
 __device__ __forceinline__ void pairs_tile(const CandView& C, int64_t k0, int64_t k1, int64_t r_glob, bool r_ok,
-                                           float3 rxf, const float4* __restrict__ tri_bary, uint2* queue,
-                                           unsigned long long* qcount, unsigned long long qcap, int32_t* overflow) {
+                                           float3 rxf, const float4* __restrict__ tri_bary, const PairSink& S) {
     const int lane = threadIdx.x & 31;
-    for (int64_t k = k0; k < k1; ++k) {
-        const int q = C.depth[k];
-        const bool ok = r_ok && q >= 0 && (q == 0 || prefilter32(C, k, q, rxf, tri_bary));
+    if (!__any_sync(FULL, r_ok)) return;
+    const float inf = INFINITY;
+    const float lx = warp_minf(r_ok ? rxf.x : inf), ly = warp_minf(r_ok ? rxf.y : inf),
+                lz = warp_minf(r_ok ? rxf.z : inf);
+    const float ux = warp_maxf(r_ok ? rxf.x : -inf), uy = warp_maxf(r_ok ? rxf.y : -inf),
+                uz = warp_maxf(r_ok ? rxf.z : -inf);
+    const float3 c = make_float3(0.5f * (lx + ux), 0.5f * (ly + uy), 0.5f * (lz + uz));
+    const float3 h = make_float3(0.5f * (ux - lx), 0.5f * (uy - ly), 0.5f * (uz - lz));
+    // lane l: candidate k0 + l, its frustum test and the data of its last bounce
+    // (image source and the triangle's planes), broadcast below to the lanes
+    bool want = false;
+    int q_l = -1;
+    float4 I_l = make_float4(0.0f, 0.0f, 0.0f, 0.0f), pl_l = I_l, g0_l = I_l, g1_l = I_l;
+    if (k0 + lane < k1) {
+        const int64_t k = k0 + lane;
+        q_l = C.depth[k];
+        want = q_l == 0 || (q_l > 0 && frustum_pass(C.frus, C.K, k, c, h));
+        if (want && q_l > 0) {
+            const int t = C.tri[(int64_t)(q_l - 1) * C.K + k];
+            I_l = C.img32[(int64_t)(q_l - 1) * C.K + k];
+            pl_l = __ldg(tri_bary + 3 * t);
+            g0_l = __ldg(tri_bary + 3 * t + 1);
+            g1_l = __ldg(tri_bary + 3 * t + 2);
+        }
+    }
+    unsigned M = __ballot_sync(FULL, want);
+    const V3<float> R = mk(rxf.x, rxf.y, rxf.z);
+    while (M) {
+        const int b = __ffs(M) - 1;
+        M &= M - 1;
+        const int64_t k = k0 + b;
+        const int q = __shfl_sync(FULL, q_l, b);
+        const float4 I4 = shfl4(I_l, b), pl = shfl4(pl_l, b), g0 = shfl4(g0_l, b), g1 = shfl4(g1_l, b);
+        bool ok = r_ok;
+        if (q > 0 && ok) {
+            V3<float> P = R;
+            int st = prefilter_step(P, I4, pl, g0, g1);
+            if (st == 1 && q > 1) st = prefilter32(C, k, q - 1, P, tri_bary);
+            ok = st != 0;
+        }
         const unsigned m = __ballot_sync(FULL, ok);
         if (m) {
             unsigned long long base = 0;
             const int leader = __ffs(m) - 1;
-            if (lane == leader) base = atomicAdd(qcount, (unsigned long long)__popc(m));
+            if (lane == leader) base = atomicAdd(S.qcount, (unsigned long long)__popc(m));
             base = __shfl_sync(FULL, base, leader);
             if (ok) {
                 const unsigned long long slot = base + __popc(m & ((1u << lane) - 1));
-                if (slot < qcap) queue[slot] = make_uint2((unsigned)k, (unsigned)r_glob);
-                else atomicExch(overflow, 1);
+                if (slot < S.qcap) S.queue[slot] = make_uint2((unsigned)k, (unsigned)r_glob);
+                else atomicExch(S.overflow, 1);
             }
         }
     }
@@ -1259,10 +1454,7 @@ struct PairArgs {
     int R;
     const double* rx;
     const float4* tri_bary;
-    uint2* queue;
-    unsigned long long* qcount;
-    unsigned long long qcap;
-    int32_t* overflow;
+    PairSink S;
 };
 
 // Image-method prefilter over all (candidate, receiver) pairs, FP32 only, in
@@ -1280,7 +1472,7 @@ __global__ void k_pairs(PairArgs A) {
         float3 rxf = make_float3(0.0f, 0.0f, 0.0f);
         if (r_ok) rxf = make_float3((float)A.rx[3 * r], (float)A.rx[3 * r + 1], (float)A.rx[3 * r + 2]);
         const int64_t k0 = kt * PAIR_CC, k1 = min(A.C.K, k0 + PAIR_CC);
-        pairs_tile(A.C, k0, k1, r, r_ok, rxf, A.tri_bary, A.queue, A.qcount, A.qcap, A.overflow);
+        pairs_tile(A.C, k0, k1, r, r_ok, rxf, A.tri_bary, A.S);
     }
 }
 
@@ -1293,6 +1485,8 @@ struct VisArgs {
     const float4* tri_v;
     const double* tri_n64;
     const double* bary64;
+    const float4* tri_bary;   // FP32 plane records (FP32 back-trace)
+    float3 txf;               // Tx rounded to FP32
     double eps;
     const uint2* queue;
     const unsigned long long* qcount;
@@ -1308,38 +1502,31 @@ struct VisArgs {
 };
 
 // Visibility in two launches.  k_backtrace: one thread per queued pair, the
-// FP64 image-method confirmation (dense FP64 work); a confirmed pair sets its
-// bit and stores its segments in FP32.  k_segments: one thread per (pair,
-// segment), segment-major so that the first segments of all pairs run before
-// the second ones: any hit with eps < t*len < len - eps (end triangles
-// excluded), FP32 first and FP64 for a marginal segment; a blocked segment
-// clears the pair's bit, and a segment whose pair is already cleared is
-// skipped.
+// FP32 back-trace of the prefilter again, which stores the pair's FP32 segments
+// and sets its bit (a pair undecided in FP32 is marked -2 and gets its
+// segments from the FP64 points in k_segments).  k_segments: one thread per
+// (pair, segment), segment-major so that the first segments of all pairs run
+// before the second ones: any hit with eps < t*len < len - eps (end triangles
+// excluded), FP32 first and FP64 for a marginal segment or a pair marked -2,
+// whose FP64 image-method geometry is checked there; a blocked segment clears
+// the pair's bit, and a segment whose pair is already cleared is skipped.  The
+// FP64 image-method confirmation of the other pairs (0 < u < 1, the point in
+// the grown triangle, segments longer than eps) runs in k_points on the dense
+// list of the pairs left visible, where an invalid pair is dropped.
 __global__ void __launch_bounds__(TRACE_THREADS) k_backtrace(VisArgs A) {
     unsigned long long n = *A.qcount;
     if (n > A.qcap) n = A.qcap;
     for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
          w += (unsigned long long)gridDim.x * blockDim.x) {
-        uint2 e = A.queue[w];
-        int64_t k = e.x;
-        int r = (int)e.y;
-        int q = A.C.depth[k];
+        const uint2 e = A.queue[w];
+        const int64_t k = e.x;
+        const int r = (int)e.y;
+        const int q = A.C.depth[k];
         const double* rp = A.rx + 3 * (int64_t)r;
-        V3<double> pts[RT_MAX_DEPTH + 2];
-        if (!backtrace64(A.C, k, q, mk(A.tx, A.ty, A.tz), mk(rp[0], rp[1], rp[2]), A.tri_v, A.tri_n64, A.bary64,
-                         A.eps, pts, nullptr)) {
-            A.seg_q[w] = -1;
-            continue;
-        }
-        A.seg_q[w] = q;
-        for (int j = 0; j <= q; ++j) {
-            V3<double> d = pts[j + 1] - pts[j];
-            float dx = (float)d.x, dy = (float)d.y, dz = (float)d.z;
-            const float il = rsqrtf(dx * dx + dy * dy + dz * dz);   // only scales the guard band
-            A.seg_o[(size_t)j * A.qcap + w] = make_float4((float)pts[j].x, (float)pts[j].y, (float)pts[j].z, il);
-            A.seg_d[(size_t)j * A.qcap + w] = make_float4(dx, dy, dz, 0.0f);
-        }
-        atomicOr(A.bits + (int64_t)r * A.words + (k >> 5), 1u << (k & 31));
+        const int st = backtrace32(A.C, k, q, mk((float)rp[0], (float)rp[1], (float)rp[2]), A.txf, A.tri_bary, w,
+                                   A.qcap, A.seg_o, A.seg_d);
+        A.seg_q[w] = st == 1 ? q : st == 2 ? -2 : -1;
+        if (st != 0) atomicOr(A.bits + (int64_t)r * A.words + (k >> 5), 1u << (k & 31));
     }
 }
 
@@ -1356,41 +1543,55 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_segments(VisArgs A) {
         // segment index and pair: 32-bit division whenever the item count fits
         const int j = total <= 0xffffffffull ? (int)((unsigned)t / (unsigned)n) : (int)(t / n);
         const unsigned long long w = t - (unsigned long long)j * n;
-        const int q = A.seg_q[w];
-        if (q < j) continue;
+        const int qs = A.seg_q[w];
+        if (qs == -1) continue;
         uint2 e = A.queue[w];
         const int64_t k = e.x;
         const int r = (int)e.y;
+        const int q = qs >= 0 ? qs : A.C.depth[k];
+        if (q < j) continue;
         uint32_t* word = A.bits + (int64_t)r * A.words + (k >> 5);
         const uint32_t bit = 1u << (k & 31);
         if (!(*(volatile uint32_t*)word & bit)) continue;   // another segment already blocked it
-        const float4 o4 = A.seg_o[(size_t)j * A.qcap + w], d4 = A.seg_d[(size_t)j * A.qcap + w];
         const int s0 = j >= 1 ? A.C.tri[(int64_t)(j - 1) * A.C.K + k] : -1;
         const int s1 = j + 1 <= q ? A.C.tri[(int64_t)j * A.C.K + k] : -1;
         const float epsf = (float)A.eps;
         WRay<float> rf;
-        rf.o = mk(o4.x, o4.y, o4.z);
-        rf.d = mk(d4.x, d4.y, d4.z);
-        wray_init(rf);
-        bool und = false;
-        unsigned nv = 0, nt = 0;
-        bool hit = any32(A.nodes, A.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, stack, und, A.status, nv,
-                         nt);
-        c_vis += nv;
-        c_tri += nt;
-        c_seg++;
+        bool hit = false, und = true;
+        if (qs >= 0) {
+            const float4 o4 = A.seg_o[(size_t)j * A.qcap + w], d4 = A.seg_d[(size_t)j * A.qcap + w];
+            rf.o = mk(o4.x, o4.y, o4.z);
+            rf.d = mk(d4.x, d4.y, d4.z);
+            wray_init(rf);
+            und = false;
+            unsigned nv = 0, nt = 0;
+            hit = any32(A.nodes, A.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, stack, und, A.status, nv,
+                        nt);
+            c_vis += nv;
+            c_tri += nt;
+            c_seg++;
+        }
         if (!hit && und) {
-            // marginal: the segment again from the FP64 points, final decision in FP64
+            // marginal, or no FP32 segments: the segment from the FP64 points,
+            // final decision in FP64 (a pair invalid in FP64 is cleared here)
             const double* rp = A.rx + 3 * (int64_t)r;
             V3<double> pts[RT_MAX_DEPTH + 2];
-            backtrace64(A.C, k, q, mk(A.tx, A.ty, A.tz), mk(rp[0], rp[1], rp[2]), A.tri_v, A.tri_n64, A.bary64,
-                        A.eps, pts, nullptr);
+            if (!backtrace64(A.C, k, q, mk(A.tx, A.ty, A.tz), mk(rp[0], rp[1], rp[2]), A.tri_v, A.tri_n64, A.bary64,
+                             A.eps, pts, nullptr)) {
+                atomicAnd(word, ~bit);
+                continue;
+            }
             V3<double> d = pts[j + 1] - pts[j];
             double il = rsqrt(dot(d, d));
             WRay<double> rd;
             rd.o = pts[j];
             rd.d = d;
             wray_init(rd);
+            if (qs < 0) {
+                rf.o = mk((float)pts[j].x, (float)pts[j].y, (float)pts[j].z);
+                rf.d = mk((float)d.x, (float)d.y, (float)d.z);
+                wray_init(rf);
+            }
             hit = any64(A.nodes, A.bvh_tris, rd, rf, A.eps * il, 1.0 - A.eps * il, s0, s1, stack, cand, A.status);
         }
         if (hit) atomicAnd(word, ~bit);
@@ -1487,14 +1688,16 @@ __global__ void k_expand(const uint32_t* __restrict__ bits, int R, int64_t words
 }
 
 // FP64 points of every emitted path, its triangle slots, and whether any
-// reflection point lies on a triangle edge (input of the duplicate rule).
+// reflection point lies on a triangle edge (input of the duplicate rule).  A
+// path whose FP64 image-method geometry is invalid is dropped here (path_cand
+// -1, bit cleared), before the duplicate rule and the final compaction.
 // P: the number of emitted paths (*P_dev, at most cap), also the slot stride of tri_out.
 __global__ void k_points(CandView C, const int64_t* __restrict__ P_dev, int64_t cap, int D,
                          const int32_t* __restrict__ path_rx,
-                         const int32_t* __restrict__ path_cand, const double* __restrict__ rx, double tx, double ty,
+                         int32_t* __restrict__ path_cand, const double* __restrict__ rx, double tx, double ty,
                          double tz, const float4* __restrict__ tri_v, const double* __restrict__ tri_n64,
                          const double* __restrict__ bary64, double eps, double* pts_out, int32_t* depth_out,
-                         int32_t* rx_out, int32_t* tri_out, int32_t* edge_flag, int32_t* status) {
+                         int32_t* rx_out, int32_t* tri_out, int32_t* edge_flag, uint32_t* bits, int64_t words) {
     const int64_t P = min(*P_dev, cap);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t k = path_cand[i];
@@ -1503,8 +1706,14 @@ __global__ void k_points(CandView C, const int64_t* __restrict__ P_dev, int64_t 
         const double* rp = rx + 3 * (int64_t)r;
         V3<double> pts[RT_MAX_DEPTH + 2];
         double mb = 1.0;
-        if (!backtrace64(C, k, q, mk(tx, ty, tz), mk(rp[0], rp[1], rp[2]), tri_v, tri_n64, bary64, eps, pts, &mb))
-            rt_set_status(status, RT_ERR_NUMERIC);
+        if (!backtrace64(C, k, q, mk(tx, ty, tz), mk(rp[0], rp[1], rp[2]), tri_v, tri_n64, bary64, eps, pts, &mb)) {
+            // invalid in FP64 (the image-method confirmation): dropped like a duplicate
+            path_cand[i] = -1;
+            atomicAnd(bits + (int64_t)r * words + (k >> 5), ~(1u << (k & 31)));
+            mb = 1.0;
+            q = 0;
+            pts[0] = pts[1] = mk(0.0, 0.0, 0.0);
+        }
         for (int j = 0; j < D + 2; ++j) {
             V3<double> v = j <= q + 1 ? pts[j] : mk(0.0, 0.0, 0.0);
             double* o = pts_out + ((int64_t)i * (D + 2) + j) * 3;
@@ -1912,7 +2121,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         // sorted keys above are consumed first, in stream order)
         const size_t need2 = Kc * 4 + (size_t)D * Kc * 4 + (size_t)D * Kc * 24 + (size_t)D * Kc * 16 + qcap * 8 +
                              (size_t)n_rx * words * 4 + (size_t)(n_rx + 1) * 8 * 2 + qcap * 4 +
-                             2 * (size_t)(D + 1) * qcap * 16 + 20 * 256;
+                             2 * (size_t)(D + 1) * qcap * 16 + 5 * Kc * 16 + 20 * 256;
         s = rt_scratch(ctx, need2, &base);
         if (s != RT_OK) return fail(s);
         Arena ar2{(char*)base};
@@ -1926,20 +2135,18 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         int32_t* seg_q = ar2.take<int32_t>(qcap);
         float4* seg_o = ar2.take<float4>((size_t)(D + 1) * qcap);
         float4* seg_d = ar2.take<float4>((size_t)(D + 1) * qcap);
+        float4* frus = ar2.take<float4>(5 * (size_t)Kc);
         TCK(cudaMemsetAsync(bits, 0, (size_t)n_rx * words * 4, st));
-        k_candidates<<<grid_for(ctx, Kc, 256), 256, 0, st>>>(p->d_cand, Kc, K_dev, D, tx_host[0], tx_host[1], tx_host[2],
-                                                             sc->d_tri_v, sc->d_tri_n64, cand_depth, cand_tri, img64,
-                                                             img32); RT_COUNT(ctx);
+        k_candidates<<<grid_for(ctx, Kc, 32, 32), 32, 0, st>>>(p->d_cand, Kc, K_dev, D, tx_host[0], tx_host[1], tx_host[2],
+                                                             sc->d_tri_v, sc->d_tri_n64, sc->d_tri_bary, cand_depth,
+                                                             cand_tri, img64, img32, frus); RT_COUNT(ctx);
         TCK(cudaGetLastError());
         PairArgs PA;
-        PA.C = CandView{Kc, cand_depth, cand_tri, img64, img32};
+        PA.C = CandView{Kc, cand_depth, cand_tri, img64, img32, frus};
         PA.R = n_rx;
         PA.rx = rx_dev;
         PA.tri_bary = sc->d_tri_bary;
-        PA.queue = queue;
-        PA.qcount = c2;
-        PA.qcap = qcap;
-        PA.overflow = f2;
+        PA.S = PairSink{queue, c2, qcap, f2};
         mark(ctx, 2);
         k_pairs<<<grid_for(ctx, ((Kc + PAIR_CC - 1) / PAIR_CC) * ((n_rx + 31) / 32) * 32, 256,
                            ctx->tune_pairs_blocks_per_sm),
@@ -1957,6 +2164,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         VA.tri_v = sc->d_tri_v;
         VA.tri_n64 = sc->d_tri_n64;
         VA.bary64 = sc->d_tri_bary64;
+        VA.tri_bary = sc->d_tri_bary;
+        VA.txf = make_float3((float)tx_host[0], (float)tx_host[1], (float)tx_host[2]);
         VA.eps = sc->eps;
         VA.queue = queue;
         VA.qcount = c2;
@@ -2022,10 +2231,10 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         k_expand<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, off_e, rx_e, path_cand,
                                                                              pcap); RT_COUNT(ctx);
         CandView C{Kc, cand_depth, cand_tri, img64, img32};
-        k_points<<<grid_for(ctx, pcap, 256), 256, 0, st>>>(C, P_e, pcap, D, rx_e, path_cand, rx_dev, tx_host[0],
+        k_points<<<grid_for(ctx, pcap, 64, 32), 64, 0, st>>>(C, P_e, pcap, D, rx_e, path_cand, rx_dev, tx_host[0],
                                                            tx_host[1], tx_host[2], sc->d_tri_v, sc->d_tri_n64,
                                                            sc->d_tri_bary64, sc->eps, pts_e, depth_e, rx_e, tri_e, edge,
-                                                           status); RT_COUNT(ctx);
+                                                           bits, words); RT_COUNT(ctx);
         k_dedup<<<grid_for(ctx, pcap, 256), 256, 0, st>>>(P_e, pcap, D, off_e, rx_e, path_cand, depth_e, tri_e, pts_e,
                                                           edge, sc->d_tri_n64, sc->d_tri_v, sc->diag, bits, words,
                                                           c2 + 4); RT_COUNT(ctx);
@@ -2370,7 +2579,8 @@ __global__ void k_cand_keys_batch(const uint64_t* __restrict__ sorted, uint64_t 
 // slots of a scene from its K_dev on are marked empty (depth -1).
 __global__ void k_candidates_batch(const uint64_t* __restrict__ keys, int64_t K, int D, const SceneDev* sd,
                                    const int64_t* cand_off, int n, const int64_t* __restrict__ K_dev,
-                                   int32_t* cand_depth, int32_t* cand_tri, double* img64, float4* img32) {
+                                   int32_t* cand_depth, int32_t* cand_tri, double* img64, float4* img32,
+                                   float4* frus) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
         const int sc = find_seg(cand_off, n + 1, k);
         if (k - cand_off[sc] >= K_dev[sc]) {
@@ -2395,6 +2605,7 @@ __global__ void k_candidates_batch(const uint64_t* __restrict__ keys, int64_t K,
             o[1] = I.y;
             o[2] = I.z;
             img32[(int64_t)j * K + k] = make_float4((float)I.x, (float)I.y, (float)I.z, 0.0f);
+            if (j == q - 1) frustum_store(I, d.tri_v, d.tri_bary, t, frus, K, k);
         }
     }
 }
@@ -2407,10 +2618,7 @@ struct BatchPairs {
     const int64_t* rx_off;     // n + 1
     int n;
     const double* rx;          // all receivers
-    uint2* queue;
-    unsigned long long* qcount;
-    unsigned long long qcap;
-    int32_t* overflow;
+    PairSink S;
 };
 
 // Batched prefilter: warp tiles of every scene in one index space (the scene of
@@ -2433,7 +2641,7 @@ __global__ void k_pairs_batch(BatchPairs A) {
         float3 rxf = make_float3(0.0f, 0.0f, 0.0f);
         if (r_ok) rxf = make_float3((float)A.rx[3 * rg], (float)A.rx[3 * rg + 1], (float)A.rx[3 * rg + 2]);
         const int64_t k0 = A.cand_off[s] + kt * PAIR_CC, k1 = A.cand_off[s] + min(K, (kt + 1) * PAIR_CC);
-        pairs_tile(A.C, k0, k1, rg, r_ok, rxf, A.sd[s].tri_bary, A.queue, A.qcount, A.qcap, A.overflow);
+        pairs_tile(A.C, k0, k1, rg, r_ok, rxf, A.sd[s].tri_bary, A.S);
     }
 }
 
@@ -2464,29 +2672,20 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_backtrace_batch(BatchVis A) {
     if (n > A.qcap) n = A.qcap;
     for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
          w += (unsigned long long)gridDim.x * blockDim.x) {
-        uint2 e = A.queue[w];
-        int64_t kg = e.x, rg = e.y;
-        int s = find_seg(A.cand_off, A.n + 1, kg);
+        const uint2 e = A.queue[w];
+        const int64_t kg = e.x, rg = e.y;
+        const int s = find_seg(A.cand_off, A.n + 1, kg);
         const SceneDev& d = A.sd[s];
-        int q = A.C.depth[kg];
+        const int q = A.C.depth[kg];
         const double* rp = A.rx + 3 * rg;
-        V3<double> pts[RT_MAX_DEPTH + 2];
-        if (!backtrace64(A.C, kg, q, mk(d.tx, d.ty, d.tz), mk(rp[0], rp[1], rp[2]), d.tri_v, d.tri_n64, d.bary64,
-                         d.eps, pts, nullptr)) {
-            A.seg_q[w] = -1;
-            continue;
+        const int st = backtrace32(A.C, kg, q, mk((float)rp[0], (float)rp[1], (float)rp[2]), d.txf, d.tri_bary, w,
+                                   A.qcap, A.seg_o, A.seg_d);
+        A.seg_q[w] = st == 1 ? q : st == 2 ? -2 : -1;
+        if (st != 0) {
+            const int64_t words = (A.cand_off[s + 1] - A.cand_off[s] + 31) / 32;
+            const int64_t kl = kg - A.cand_off[s];
+            atomicOr(A.bits + A.bits_off[s] + (rg - A.rx_off[s]) * words + (kl >> 5), 1u << (kl & 31));
         }
-        A.seg_q[w] = q;
-        for (int j = 0; j <= q; ++j) {
-            V3<double> dv = pts[j + 1] - pts[j];
-            float dx = (float)dv.x, dy = (float)dv.y, dz = (float)dv.z;
-            const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-            A.seg_o[(size_t)j * A.qcap + w] = make_float4((float)pts[j].x, (float)pts[j].y, (float)pts[j].z, il);
-            A.seg_d[(size_t)j * A.qcap + w] = make_float4(dx, dy, dz, 0.0f);
-        }
-        const int64_t words = (A.cand_off[s + 1] - A.cand_off[s] + 31) / 32;
-        const int64_t kl = kg - A.cand_off[s];
-        atomicOr(A.bits + A.bits_off[s] + (rg - A.rx_off[s]) * words + (kl >> 5), 1u << (kl & 31));
     }
 }
 
@@ -2503,10 +2702,12 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_segments_batch(BatchVis A) {
         // segment index and pair: 32-bit division whenever the item count fits
         const int j = total <= 0xffffffffull ? (int)((unsigned)t / (unsigned)n) : (int)(t / n);
         const unsigned long long w = t - (unsigned long long)j * n;
-        const int q = A.seg_q[w];
-        if (q < j) continue;
+        const int qs = A.seg_q[w];
+        if (qs == -1) continue;
         uint2 e = A.queue[w];
         const int64_t kg = e.x, rg = e.y;
+        const int q = qs >= 0 ? qs : A.C.depth[kg];
+        if (q < j) continue;
         const int s = find_seg(A.cand_off, A.n + 1, kg);
         const SceneDev& d = A.sd[s];
         const int64_t words = (A.cand_off[s + 1] - A.cand_off[s] + 31) / 32;
@@ -2514,32 +2715,43 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_segments_batch(BatchVis A) {
         uint32_t* word = A.bits + A.bits_off[s] + (rg - A.rx_off[s]) * words + (kl >> 5);
         const uint32_t bit = 1u << (kl & 31);
         if (!(*(volatile uint32_t*)word & bit)) continue;
-        const float4 o4 = A.seg_o[(size_t)j * A.qcap + w], d4 = A.seg_d[(size_t)j * A.qcap + w];
         const int s0 = j >= 1 ? A.C.tri[(int64_t)(j - 1) * A.C.K + kg] : -1;
         const int s1 = j + 1 <= q ? A.C.tri[(int64_t)j * A.C.K + kg] : -1;
         const float epsf = (float)d.eps;
         WRay<float> rf;
-        rf.o = mk(o4.x, o4.y, o4.z);
-        rf.d = mk(d4.x, d4.y, d4.z);
-        wray_init(rf);
-        bool und = false;
-        unsigned nv = 0, nt = 0;
-        bool hit = any32(d.nodes, d.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, stack, und, A.status, nv,
-                         nt);
-        c_vis += nv;
-        c_tri += nt;
-        c_seg++;
+        bool hit = false, und = true;
+        if (qs >= 0) {
+            const float4 o4 = A.seg_o[(size_t)j * A.qcap + w], d4 = A.seg_d[(size_t)j * A.qcap + w];
+            rf.o = mk(o4.x, o4.y, o4.z);
+            rf.d = mk(d4.x, d4.y, d4.z);
+            wray_init(rf);
+            und = false;
+            unsigned nv = 0, nt = 0;
+            hit = any32(d.nodes, d.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, stack, und, A.status, nv,
+                        nt);
+            c_vis += nv;
+            c_tri += nt;
+            c_seg++;
+        }
         if (!hit && und) {
             const double* rp = A.rx + 3 * rg;
             V3<double> pts[RT_MAX_DEPTH + 2];
-            backtrace64(A.C, kg, q, mk(d.tx, d.ty, d.tz), mk(rp[0], rp[1], rp[2]), d.tri_v, d.tri_n64, d.bary64,
-                        d.eps, pts, nullptr);
+            if (!backtrace64(A.C, kg, q, mk(d.tx, d.ty, d.tz), mk(rp[0], rp[1], rp[2]), d.tri_v, d.tri_n64, d.bary64,
+                             d.eps, pts, nullptr)) {
+                atomicAnd(word, ~bit);
+                continue;
+            }
             V3<double> dv = pts[j + 1] - pts[j];
             double il = rsqrt(dot(dv, dv));
             WRay<double> rd;
             rd.o = pts[j];
             rd.d = dv;
             wray_init(rd);
+            if (qs < 0) {
+                rf.o = mk((float)pts[j].x, (float)pts[j].y, (float)pts[j].z);
+                rf.d = mk((float)dv.x, (float)dv.y, (float)dv.z);
+                wray_init(rf);
+            }
             hit = any64(d.nodes, d.bvh_tris, rd, rf, d.eps * il, 1.0 - d.eps * il, s0, s1, stack, cand, A.status);
         }
         if (hit) atomicAnd(word, ~bit);
@@ -2607,21 +2819,30 @@ __global__ void k_expand_batch(const uint32_t* __restrict__ bits, const int64_t*
 // FP64 points of every path; triangle slots carry global (offset) ids.
 __global__ void k_points_batch(CandView C, const int64_t* __restrict__ P_dev, int64_t cap, int D, const SceneDev* sd,
                                const int64_t* cand_off, int n, const int32_t* __restrict__ path_rx,
-                               const int32_t* __restrict__ path_cand, const double* __restrict__ rx, double* pts_out,
+                               int32_t* __restrict__ path_cand, const double* __restrict__ rx, double* pts_out,
                                int32_t* depth_out, int32_t* rx_out, int32_t* tri_out, int32_t* edge_flag,
-                               int32_t* status) {
+                               uint32_t* bits, const int64_t* rx_off, const int64_t* bits_off) {
     const int64_t P = min(*P_dev, cap);   // also the slot stride of tri_out
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t kg = path_cand[i];
         int r = path_rx[i];
-        const SceneDev& d = sd[find_seg(cand_off, n + 1, kg)];
+        const int s = find_seg(cand_off, n + 1, kg);
+        const SceneDev& d = sd[s];
         int q = C.depth[kg];
         const double* rp = rx + 3 * (int64_t)r;
         V3<double> pts[RT_MAX_DEPTH + 2];
         double mb = 1.0;
         if (!backtrace64(C, kg, q, mk(d.tx, d.ty, d.tz), mk(rp[0], rp[1], rp[2]), d.tri_v, d.tri_n64, d.bary64, d.eps,
-                         pts, &mb))
-            rt_set_status(status, RT_ERR_NUMERIC);
+                         pts, &mb)) {
+            // invalid in FP64: dropped like a duplicate (as k_points)
+            path_cand[i] = -1;
+            const int64_t words = (cand_off[s + 1] - cand_off[s] + 31) / 32;
+            const int64_t kl = kg - cand_off[s];
+            atomicAnd(bits + bits_off[s] + (r - rx_off[s]) * words + (kl >> 5), ~(1u << (kl & 31)));
+            mb = 1.0;
+            q = 0;
+            pts[0] = pts[1] = mk(0.0, 0.0, 0.0);
+        }
         for (int j = 0; j < D + 2; ++j) {
             V3<double> v = j <= q + 1 ? pts[j] : mk(0.0, 0.0, 0.0);
             double* o = pts_out + ((int64_t)i * (D + 2) + j) * 3;
@@ -3032,7 +3253,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         RT_COUNT(ctx);
         size_t need2 = KT * 4 + (size_t)D * KT * 4 + (size_t)D * KT * 24 + (size_t)D * KT * 16 + qcap * 8 +
                        (size_t)bits_off[n] * 4 + (size_t)(RT + 1) * 8 * 2 + qcap * 4 +
-                       2 * (size_t)(D + 1) * qcap * 16 + 20 * 256;
+                       2 * (size_t)(D + 1) * qcap * 16 + 5 * KT * 16 + 20 * 256;
         s0 = rt_scratch(ctx, need2, &base);
         if (s0 != RT_OK) return fail(s0);
         Arena ar2{(char*)base};
@@ -3046,23 +3267,21 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         int32_t* seg_q = ar2.take<int32_t>(qcap);
         float4* seg_o = ar2.take<float4>((size_t)(D + 1) * qcap);
         float4* seg_d = ar2.take<float4>((size_t)(D + 1) * qcap);
+        float4* frus = ar2.take<float4>(5 * (size_t)KT);
         BCK(cudaMemsetAsync(bits, 0, (size_t)bits_off[n] * 4, st));
-        k_candidates_batch<<<grid_for(ctx, KT, 256), 256, 0, st>>>(p->d_cand, KT, D, d_sd, d_cand_off, n, K_dev,
-                                                                    cand_depth, cand_tri, img64, img32);
+        k_candidates_batch<<<grid_for(ctx, KT, 32, 32), 32, 0, st>>>(p->d_cand, KT, D, d_sd, d_cand_off, n, K_dev,
+                                                                    cand_depth, cand_tri, img64, img32, frus);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
         BatchPairs PA;
-        PA.C = CandView{KT, cand_depth, cand_tri, img64, img32};
+        PA.C = CandView{KT, cand_depth, cand_tri, img64, img32, frus};
         PA.sd = d_sd;
         PA.tile_off = d_pair_off;
         PA.cand_off = d_cand_off;
         PA.rx_off = d_rx_off;
         PA.n = n;
         PA.rx = rx_dev;
-        PA.queue = queue;
-        PA.qcount = c2;
-        PA.qcap = qcap;
-        PA.overflow = f2;
+        PA.S = PairSink{queue, c2, qcap, f2};
         mark(ctx, 2);
         k_pairs_batch<<<grid_for(ctx, pair_off[n] * 32, 256, ctx->tune_pairs_blocks_per_sm), 256, 0, st>>>(PA);
         RT_COUNT(ctx);
@@ -3142,8 +3361,9 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
                                                                         off_e, rx_e, path_cand, pcap);
         RT_COUNT(ctx);
         CandView C{KT, cand_depth, cand_tri, img64, img32};
-        k_points_batch<<<grid_for(ctx, pcap, 256), 256, 0, st>>>(C, P_e, pcap, D, d_sd, d_cand_off, n, rx_e, path_cand,
-                                                                 rx_dev, pts_e, depth_e, rx_e, tri_e, edge, status);
+        k_points_batch<<<grid_for(ctx, pcap, 64, 32), 64, 0, st>>>(C, P_e, pcap, D, d_sd, d_cand_off, n, rx_e, path_cand,
+                                                                 rx_dev, pts_e, depth_e, rx_e, tri_e, edge, bits,
+                                                                 d_rx_off, d_bits_off);
         RT_COUNT(ctx);
         k_dedup_batch<<<grid_for(ctx, pcap, 256), 256, 0, st>>>(P_e, pcap, D, off_e, rx_e, path_cand, depth_e, tri_e,
                                                                 pts_e, edge, comb->d_tri_n64, comb->d_tri_v, comb->diag,
