@@ -34,7 +34,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int TRACE_THREADS = 128;
 constexpr int REDO_THREADS = 32;
 constexpr int REDO_BLOCKS_PER_SM = 16;
-constexpr float SBR_MARGIN = 1e-3f;     // relative barycentric margin of the FP32 passes
+constexpr float SBR_MARGIN = 1e-3f;     // relative barycentric margin of the FP32 visibility passes
 constexpr float PREFILTER_MARGIN = 1e-3f;
 // Degenerate geometry: every triangle is closed and grown by TRI_TOL (relative
 // barycentric), so a point or ray exactly on an edge shared by two triangles
@@ -157,18 +157,24 @@ __device__ __forceinline__ int tri_test32(const WRay<float>& r, float4 p0, float
     return 2;
 }
 
-// tri_test32 for a launch ray: the FP64 ray of the final decision has the same
-// (canonical FP32) direction, and its origin differs from the FP32 one only by
-// the rounding of the transmitter, so the signs of the edge functions need only
-// cover this test's FP32 rounding.  With u = 2^-24, the translated and sheared
-// coordinates carry errors below 3u (Mv + Mo), Mv = max over the vertices of
-// |X_kx| + |X_ky| + |X_kz| (|Sx| + |Sy|) and Mo the same of the origin, so
-// |dU| <= u (4 L^2 + 12 (Mv + Mo) L) with L = max |sheared x, y|.  The margin is
-// twice that plus the FP64 test's growth TRI_TOL (|U| + |V| + |W|) (doubled):
-// usually far below the relative band of tri_test32, and rigorous where that
-// band is not (small, distant triangles).
-__device__ __forceinline__ int tri_test32_launch(const WRay<float>& r, float4 p0, float4 p1, float4 p2,
-                                                 float& t_out) {
+// tri_test32 for a ray of the FP32 SBR pass with a rigorous undecided band.
+// Rounding part: with u = 2^-24 the translated and sheared coordinates carry
+// errors below 3u (Mv + Mo), Mv = max over the vertices of |X_kx| + |X_ky| +
+// |X_kz| (|S_x| + |S_y|) and Mo the same of the origin, so an edge function is
+// off by at most u (4 L^2 + 12 (Mv + Mo) L), L = max |sheared x, y|; Mv is
+// bounded here by 2 L + 2 (|S_x| + |S_y|) Z (|X_kx| <= L + |S_x| Z, Z the
+// vertices' largest |X_kz|).  The launch ray is the FP64 ray's canonical FP32
+// direction from the transmitter's FP32 rounding, which the origin term covers,
+// and is tested with no drift.  A reflected ray has drifted from the FP64 ray
+// of the final decision by at most Do (origin) and Dd (direction), 2-norm
+// bounds from sbr_bounce: an origin shift Do moves a sheared vertex coordinate
+// by Do (1 + |S_x|) <= 2 Do, a direction shift Dd moves S_x, S_y by at most
+// 3.47 Dd (d_kz >= 1/sqrt 3) and so a sheared coordinate by 3.47 Dd (Z + Do);
+// with sigma the sum, an edge function moves by at most 4 L sigma + 2 sigma^2.
+// The margin is twice the sum of both parts plus the FP64 test's growth
+// TRI_TOL (|U| + |V| + |W|), doubled.
+__device__ __forceinline__ int tri_test32_dev(const WRay<float>& r, float4 p0, float4 p1, float4 p2, float Do,
+                                              float Dd, float& t_out) {
     const V3<float> A = from4<float>(p0) - r.o, B = from4<float>(p1) - r.o, C = from4<float>(p2) - r.o;
     const float Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
     const float Akx = comp(A, r.kx), Aky = comp(A, r.ky), Bkx = comp(B, r.kx), Bky = comp(B, r.ky);
@@ -177,13 +183,15 @@ __device__ __forceinline__ int tri_test32_launch(const WRay<float>& r, float4 p0
     const float Bx = Bkx - r.Sx * Bkz, By = Bky - r.Sy * Bkz;
     const float Cx = Ckx - r.Sx * Ckz, Cy = Cky - r.Sy * Ckz;
     const float U = Cx * By - Cy * Bx, V = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
-    const float Sab = fabsf(r.Sx) + fabsf(r.Sy);
-    const float Mv = fmaxf(fmaxf(fabsf(Akx) + fabsf(Aky) + fabsf(Akz) * Sab, fabsf(Bkx) + fabsf(Bky) + fabsf(Bkz) * Sab),
-                           fabsf(Ckx) + fabsf(Cky) + fabsf(Ckz) * Sab);
-    const float Mo = fabsf(comp(r.o, r.kx)) + fabsf(comp(r.o, r.ky)) + fabsf(comp(r.o, r.kz)) * Sab;
     const float L = fmaxf(fmaxf(fmaxf(fabsf(Ax), fabsf(Ay)), fmaxf(fabsf(Bx), fabsf(By))), fmaxf(fabsf(Cx), fabsf(Cy)));
+    const float Z = fmaxf(fmaxf(fabsf(Akz), fabsf(Bkz)), fabsf(Ckz));
+    const float Sab = fabsf(r.Sx) + fabsf(r.Sy);
+    const float Mv = 2.0f * (L + Sab * Z);
+    const float Mo = fabsf(comp(r.o, r.kx)) + fabsf(comp(r.o, r.ky)) + fabsf(comp(r.o, r.kz)) * Sab;
+    const float sg = 2.0f * Do + 3.47f * Dd * (Z + Do);
     const float sum = fabsf(U) + fabsf(V) + fabsf(W);
-    const float m = 2.0f * 5.9604645e-8f * (4.0f * L * L + 12.0f * (Mv + Mo) * L) + 2.0f * (float)TRI_TOL * sum;
+    const float e = 1.01f * (5.9604645e-8f * (4.0f * L * L + 12.0f * (Mv + Mo) * L) + 4.0f * L * sg + 2.0f * sg * sg);
+    const float m = 2.0f * e + 2.0f * (float)TRI_TOL * sum;
     const bool pos = U > m && V > m && W > m;
     const bool neg = U < -m && V < -m && W < -m;
     const float det = U + V + W;
@@ -198,8 +206,9 @@ __device__ __forceinline__ int tri_test32_launch(const WRay<float>& r, float4 p0
 }
 
 // tri_test32 for the FP32 rounding rf of an FP64 ray r (the re-trace): rf's origin
-// and direction differ from r's by one rounding each, so the margin is that of
-// tri_test32_launch for the origin plus the direction's rounding.  That moves
+// and direction differ from r's by one rounding each, so the margin is the
+// rounding part of tri_test32_dev (whose origin term covers the origin's
+// rounding) plus the direction's rounding.  That moves
 // S_x, S_y by at most 2 sqrt(3) u (kz the largest component of a unit-length
 // direction) and so a sheared vertex coordinate by 3.47 u Z, Z the vertices'
 // largest |X_kz|, and an edge function by 4 L (3.47 u Z).  A robust hit also gets
@@ -355,7 +364,7 @@ template <int STACK = RT_STACK>
 __device__ __forceinline__ int closest32(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris,
                                          const WRay<float>& r, float tmin, int skip, int* stack, float& t_out,
                                          bool& und, int32_t* status, unsigned& nvis, unsigned& ntri,
-                                         bool launch_ray = false) {
+                                         float Do, float Dd) {
     float tb = INFINITY, thi = INFINITY;
     int best = -1;
     traverse<STACK>(nodes, r, tmin * 0.5f, thi, stack, status, nvis, [&](int first, int count) {
@@ -365,7 +374,7 @@ __device__ __forceinline__ int closest32(const BvhNode* __restrict__ nodes, cons
             if (id == skip) continue;
             ntri++;
             float th;
-            int cls = launch_ray ? tri_test32_launch(r, p0, p1, p2, th) : tri_test32(r, p0, p1, p2, th);
+            int cls = tri_test32_dev(r, p0, p1, p2, Do, Dd, th);
             if (cls == 0) continue;
             if (cls == 2) {
                 if (th > tmin * 0.5f && th < tb * 1.00001f) und = true;
@@ -795,12 +804,45 @@ __device__ __forceinline__ void warp_count(unsigned long long* c, unsigned long 
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(c, v);
 }
 
-// FP32 unit normal of triangle id: the FP64 normal rounded to FP32, read from the
-// plane record (n, n.v0) of the triangle table (one load, and within one rounding
-// of the normal the FP64 re-trace reflects about).
-__device__ __forceinline__ float3 tri_normal_f(const float4* tri_plane, int id) {
-    const float4 pl = __ldg(tri_plane + 3 * id);
-    return make_float3(pl.x, pl.y, pl.z);
+// One specular bounce of the FP32 SBR ray at triangle id (plane record pl =
+// FP32 unit normal n and n.v0): the hit point from the plane, o' = o + t d with
+// t = (n.v0 - n.o) / (n.d), and the mirror direction d' = d - 2 (d.n) n
+// (Sec. II-B).  Do and Dd bound the drift of the FP32 ray from the FP64 ray of
+// the final decision, which reflects at its own plane hit about the FP64
+// normal; with u = 2^-24 they grow as
+//   Do' = 1.01 ((Do + t Dd + dN + 4u t) / (|n.d| - 4u) + u (|o|_1 + 4t)),
+//   Dd' = Dd + 14u,
+// dN = u (|n.v0| + 4 |o|_1 + |n.v0 - n.o|) and 4u bounding the roundings of
+// the plane's numerator and of n.d (n one rounding off the FP64 normal), the
+// first term the hit point's shift along the plane (an oblique projection of
+// norm 1 / cos), the last the roundings of t (an approximate division, within
+// 2 ulp) and of o + t d; the reflection is an isometry and adds the normal's
+// rounding (4u) and its own (10u).  At an axis-aligned plane (two components
+// of the unit normal zero, so the third is +-1 and n.v0 a vertex coordinate, in
+// FP32 and in FP64 alike) both reflections are exact and n.d, n.o are exact:
+// the direction's drift does not grow, and only the rounding of n.v0 - n.o
+// remains in dN (an FP64 normal component below the FP32 range is absorbed by
+// the 1 % slack).  Returns false if the ray meets the plane too obliquely for
+// the bound (|n.d| <= 4u).
+__device__ __forceinline__ bool sbr_bounce(WRay<float>& r, float4 pl, float& Do, float& Dd) {
+    const float u = 5.9604645e-8f;
+    const V3<float> n = mk(pl.x, pl.y, pl.z);
+    const float N = pl.w - dot(n, r.o);
+    const float Dn = dot(n, r.d);
+    const bool axis = (int)(pl.x == 0.0f) + (int)(pl.y == 0.0f) + (int)(pl.z == 0.0f) == 2;
+    const float eD = axis ? 0.0f : 4.0f * u;
+    const float aD = fabsf(Dn) - 4.0f * u;
+    if (!(aD > 0.0f)) return false;
+    const float ts = __fdividef(N, Dn), t = fabsf(ts);
+    const float o1 = fabsf(r.o.x) + fabsf(r.o.y) + fabsf(r.o.z);
+    const float dN = axis ? u * fabsf(N) : u * (fabsf(pl.w) + 4.0f * o1 + fabsf(N));
+    Do = 1.01f * ((Do + t * Dd + dN + eD * t) / aD + u * (o1 + 4.0f * t));
+    if (!axis) Dd = Dd + 14.0f * u;
+    const V3<float> p = r.o + ts * r.d;
+    r.d = r.d - (2.0f * Dn) * n;
+    r.o = p;
+    wray_init(r);
+    return true;
 }
 
 // Persistent SBR: every lane owns one ray; a lane whose ray ended takes the next
@@ -817,6 +859,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
     int bounce = 0, prev = -1;
     uint64_t key = 0;
     WRay<float> r;
+    float Do = 0.0f, Dd = 0.0f;   // drift of the FP32 ray from the FP64 one (sbr_bounce)
     const float eps = (float)A.eps;
     unsigned long long c_vis = 0, c_tri = 0, c_q = 0;
     for (;;) {
@@ -839,6 +882,9 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
                     r.o = mk(A.txf.x, A.txf.y, A.txf.z);
                     r.d = mk(d.x, d.y, d.z);
                     wray_init(r);
+                    // the transmitter's rounding; the direction is the FP64 ray's
+                    Do = 5.9604645e-8f * (fabsf(A.txf.x) + fabsf(A.txf.y) + fabsf(A.txf.z));
+                    Dd = 0.0f;
                 } else {
                     done = true;
                 }
@@ -849,7 +895,10 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
         float th;
         bool und = false;
         unsigned nv = 0, nt = 0;
-        int id = closest32<STACK>(A.nodes, A.tris, r, eps, prev, stack, th, und, A.status, nv, nt, bounce == 0);
+        // the launch ray: its drift is the transmitter's rounding, which the test's
+        // origin term covers, so it is tested with none
+        int id = closest32<STACK>(A.nodes, A.tris, r, eps, prev, stack, th, und, A.status, nv, nt,
+                                  bounce == 0 ? 0.0f : Do, Dd);
         c_vis += nv;
         c_tri += nt;
         c_q++;
@@ -875,12 +924,18 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
             ray = -1;
             continue;
         }
-        float3 n = tri_normal_f(tri_plane, id);
-        V3<float> nn = mk(n.x, n.y, n.z);
-        V3<float> p = r.o + th * r.d;
-        r.d = r.d - (2.0f * dot(r.d, nn)) * nn;
-        r.o = p;
-        wray_init(r);
+        if (!sbr_bounce(r, __ldg(tri_plane + 3 * id), Do, Dd)) {
+            // too oblique for the drift bound: the next bounce is decided in FP64
+            unsigned long long slot = atomicAdd(A.redo_count, 1ull);
+            if ((int64_t)slot < A.redo_cap) {
+                A.redo[slot] = ray | ((int64_t)bounce << 32);
+                A.redo_key[slot] = key;
+            } else {
+                atomicExch(A.overflow, 2);
+            }
+            ray = -1;
+            continue;
+        }
         prev = id;
     }
     if (A.counters) {
@@ -2379,7 +2434,7 @@ struct BatchSbr {
 // lane takes a ray, and kept in registers (lanes of one warp may hold rays of
 // different scenes).
 template <int STACK>
-__global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
+__global__ void __launch_bounds__(TRACE_THREADS, 6) k_sbr_batch(BatchSbr A) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -2391,10 +2446,11 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
     WRay<float> r;
     const BvhNode* nodes = nullptr;
     const float4* bvh_tris = nullptr;
-    const float4* tri_plane = nullptr;   // the scene's plane records (tri_normal_f)
+    const float4* tri_plane = nullptr;   // the scene's plane records (sbr_bounce)
     unsigned long long* table = nullptr;
     unsigned long long* uniq = nullptr;
     float eps = 0.f;
+    float Do = 0.0f, Dd = 0.0f;   // drift of the FP32 ray from the FP64 one (sbr_bounce)
     unsigned long long c_vis = 0, c_tri = 0, c_q = 0;
     for (;;) {
         bool need = (ray < 0) && !done;
@@ -2425,6 +2481,8 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
                     r.o = mk(d.txf.x, d.txf.y, d.txf.z);
                     r.d = mk(dir.x, dir.y, dir.z);
                     wray_init(r);
+                    Do = 5.9604645e-8f * (fabsf(d.txf.x) + fabsf(d.txf.y) + fabsf(d.txf.z));
+                    Dd = 0.0f;
                 } else {
                     done = true;
                 }
@@ -2435,7 +2493,8 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
         float th;
         bool und = false;
         unsigned nv = 0, nt = 0;
-        int id = closest32<STACK>(nodes, bvh_tris, r, eps, prev, stack, th, und, A.status, nv, nt, bounce == 0);
+        int id = closest32<STACK>(nodes, bvh_tris, r, eps, prev, stack, th, und, A.status, nv, nt,
+                                  bounce == 0 ? 0.0f : Do, Dd);
         c_vis += nv;
         c_tri += nt;
         c_q++;
@@ -2461,12 +2520,17 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr_batch(BatchSbr A) {
             ray = -1;
             continue;
         }
-        float3 nrm = tri_normal_f(tri_plane, id);
-        V3<float> nn = mk(nrm.x, nrm.y, nrm.z);
-        V3<float> p = r.o + th * r.d;
-        r.d = r.d - (2.0f * dot(r.d, nn)) * nn;
-        r.o = p;
-        wray_init(r);
+        if (!sbr_bounce(r, __ldg(tri_plane + 3 * id), Do, Dd)) {
+            unsigned long long slot = atomicAdd(A.redo_count, 1ull);
+            if ((int64_t)slot < A.redo_cap) {
+                A.redo[slot] = ray | ((int64_t)bounce << 32);
+                A.redo_key[slot] = key;
+            } else {
+                atomicExch(A.overflow, 2);
+            }
+            ray = -1;
+            continue;
+        }
         prev = id;
     }
     if (A.counters) {
