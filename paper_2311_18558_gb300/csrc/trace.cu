@@ -2196,7 +2196,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
                                                              sc->d_tri_v, sc->d_tri_n64, sc->d_tri_bary, cand_depth,
                                                              cand_tri, img64, img32, frus); RT_COUNT(ctx);
         TCK(cudaGetLastError());
-        PairArgs PA;
+        PairArgs PA{};
         PA.C = CandView{Kc, cand_depth, cand_tri, img64, img32, frus};
         PA.R = n_rx;
         PA.rx = rx_dev;
@@ -2208,7 +2208,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
                   256, 0, st>>>(PA); RT_COUNT(ctx);
         mark(ctx, 3);
         TCK(cudaGetLastError());
-        VisArgs VA;
+        VisArgs VA{};
         VA.C = PA.C;
         VA.rx = rx_dev;
         VA.tx = tx_host[0];
@@ -3337,7 +3337,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
                                                                     cand_depth, cand_tri, img64, img32, frus);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
-        BatchPairs PA;
+        BatchPairs PA{};
         PA.C = CandView{KT, cand_depth, cand_tri, img64, img32, frus};
         PA.sd = d_sd;
         PA.tile_off = d_pair_off;
@@ -3351,7 +3351,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
         mark(ctx, 3);
-        BatchVis VA;
+        BatchVis VA{};
         VA.C = PA.C;
         VA.sd = d_sd;
         VA.cand_off = d_cand_off;
