@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <unordered_map>
 #include <vector>
 
 #include "rt_internal.cuh"
@@ -476,6 +477,36 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_scene_upload(rt_c
     }
     for (int m = 0; m < n_materials; ++m)
         if (is_pec[m] > 1) return rt_fail(ctx, RT_ERR_INVALID_ARG, "material_is_pec must be 0 or 1");
+    // plane ids: triangles whose FP64 plane records (unit normal, offset) are
+    // bitwise equal share the id of the first of them.  A segment meets such a
+    // plane once, so a triangle in the plane of a segment's end triangle can only
+    // be met at that end (the visibility test skips it).  Stored in the .w of
+    // the second vertex record (copied into the BVH triangle records).
+    {
+        struct Key {
+            uint64_t b[4];
+            bool operator==(const Key& o) const {
+                return b[0] == o.b[0] && b[1] == o.b[1] && b[2] == o.b[2] && b[3] == o.b[3];
+            }
+        };
+        struct KeyHash {
+            size_t operator()(const Key& k) const {
+                uint64_t h = 1469598103934665603ull;   // FNV-1a over the four words
+                for (int i = 0; i < 4; ++i) h = (h ^ k.b[i]) * 1099511628211ull;
+                return (size_t)h;
+            }
+        };
+        std::unordered_map<Key, int32_t, KeyHash> first;
+        first.reserve((size_t)n_tris * 2);
+        for (int t = 0; t < n_tris; ++t) {
+            Key k;
+            double v[4];
+            for (int i = 0; i < 4; ++i) v[i] = tn[4 * (size_t)t + i] + 0.0;   // -0.0 as +0.0
+            std::memcpy(k.b, v, 32);
+            const int32_t id = first.emplace(k, t).first->second;
+            std::memcpy(&tv[3 * (size_t)t + 1].w, &id, 4);
+        }
+    }
     const double diag = std::sqrt((ghi[0] - glo[0]) * (ghi[0] - glo[0]) + (ghi[1] - glo[1]) * (ghi[1] - glo[1]) +
                                   (ghi[2] - glo[2]) * (ghi[2] - glo[2]));
     if (!(diag > 0.0)) return rt_fail(ctx, RT_ERR_INVALID_ARG, "scene has zero extent");

@@ -398,18 +398,24 @@ __device__ __forceinline__ int closest32(const BvhNode* __restrict__ nodes, cons
     return best;
 }
 
-// FP32 any hit with tmin < t < tmax (skipping skip0, skip1): true on a robust
-// hit; `und` set if no robust hit was found but a marginal one might exist.
+// FP32 any hit with tmin < t < tmax (skipping skip0, skip1 and every triangle
+// in the plane pl0 or pl1 of a segment's end triangle: the segment meets that
+// plane only at its end, at t = 0 or 1, outside (tmin, tmax) in exact arithmetic
+// and in the FP64 test): true on a robust hit; `und` set if no robust hit was
+// found but a marginal one might exist.  A triangle's plane id is the .w of
+// its second vertex record.
 __device__ __forceinline__ bool any32(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris,
-                                     const WRay<float>& r, float tmin, float tmax, int skip0, int skip1, int* stack,
-                                     bool& und, int32_t* status, unsigned& nvis, unsigned& ntri) {
+                                     const WRay<float>& r, float tmin, float tmax, int skip0, int skip1, int pl0,
+                                     int pl1, int* stack, bool& und, int32_t* status, unsigned& nvis,
+                                     unsigned& ntri) {
     bool hit = false;
     const float thi = tmax * 1.00001f;
     traverse(nodes, r, tmin * 0.5f, thi, stack, status, nvis, [&](int first, int count) {
         for (int k = first; k < first + count; ++k) {
             float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
             int id = __float_as_int(p0.w);
-            if (id == skip0 || id == skip1) continue;
+            const int pid = __float_as_int(p1.w);
+            if (id == skip0 || id == skip1 || pid == pl0 || pid == pl1) continue;
             ntri++;
             float th;
             int cls = tri_test32(r, p0, p1, p2, th);
@@ -1620,8 +1626,10 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_segments(VisArgs A) {
             wray_init(rf);
             und = false;
             unsigned nv = 0, nt = 0;
-            hit = any32(A.nodes, A.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, stack, und, A.status, nv,
-                        nt);
+            const int pl0 = s0 >= 0 ? __float_as_int(__ldg(A.tri_v + 3 * s0 + 1).w) : -1;
+            const int pl1 = s1 >= 0 ? __float_as_int(__ldg(A.tri_v + 3 * s1 + 1).w) : -1;
+            hit = any32(A.nodes, A.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, pl0, pl1, stack, und,
+                        A.status, nv, nt);
             c_vis += nv;
             c_tri += nt;
             c_seg++;
@@ -2791,8 +2799,10 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_segments_batch(BatchVis A) {
             wray_init(rf);
             und = false;
             unsigned nv = 0, nt = 0;
-            hit = any32(d.nodes, d.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, stack, und, A.status, nv,
-                        nt);
+            const int pl0 = s0 >= 0 ? __float_as_int(__ldg(d.tri_v + 3 * s0 + 1).w) : -1;
+            const int pl1 = s1 >= 0 ? __float_as_int(__ldg(d.tri_v + 3 * s1 + 1).w) : -1;
+            hit = any32(d.nodes, d.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, pl0, pl1, stack, und,
+                        A.status, nv, nt);
             c_vis += nv;
             c_tri += nt;
             c_seg++;
