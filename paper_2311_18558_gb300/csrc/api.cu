@@ -171,6 +171,12 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_create(int device
         delete ctx;
         return RT_ERR_OOM;
     }
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        delete ctx;
+        return RT_ERR_CUDA;
+    }
     *out = ctx;
     return RT_OK;
 }
@@ -236,6 +242,11 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_destroy(rt_ctx* c
     for (int k = 0; k < 8; ++k)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
     if (ctx->d_counters) cudaFree(ctx->d_counters);
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
+    if (ctx->d_rx_order) cudaFree(ctx->d_rx_order);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     if (ctx->d_sched_order) cudaFree(ctx->d_sched_order);
     if (ctx->d_sched_wrap) cudaFree(ctx->d_sched_wrap);
     if (ctx->d_sched_z) cudaFree(ctx->d_sched_z);

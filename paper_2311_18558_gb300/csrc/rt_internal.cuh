@@ -45,6 +45,12 @@ struct rt_ctx {
     unsigned long long* d_counters = nullptr;   // 8 device counters (bit 1)
     int64_t h_counters[8] = {0};                // host-side counts of the same slots
     cudaEvent_t ev[8] = {};                     // trace stage events (bit 0)
+    // side stream for trace work that depends only on the inputs (the receivers'
+    // tile order), forked from and joined back into the trace's stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int32_t* d_rx_order = nullptr;   // rx_order_cap entries
+    int64_t rx_order_cap = 0;
     int32_t stage_pending = 0;                  // the last trace's events are recorded, not yet read
     // coherent processing order of the launch directions, per ray count (see trace.cu)
     int64_t sched_n = 0, sched_band = 0, sched_full = 0;

@@ -358,20 +358,24 @@ __device__ __forceinline__ void traverse(const BvhNode* __restrict__ nodes, cons
     }
 }
 
-// FP32 closest hit with t > tmin (skipping `skip`): exact ties go to the lower
-// triangle index; `und` is set if any decision that could matter was marginal.
+// FP32 closest hit with t > tmin (skipping `skip` and every triangle in the
+// plane `skip_plane` of the ray's start: the ray meets that plane only at
+// t = 0, which no test takes as a hit): exact ties go to the lower triangle
+// index; `und` is set if any decision that could matter was marginal.  The
+// plane id of the hit (the .w of its second vertex record) is returned in
+// `plane_out`.
 template <int STACK = RT_STACK>
 __device__ __forceinline__ int closest32(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris,
                                          const WRay<float>& r, float tmin, int skip, int* stack, float& t_out,
                                          bool& und, int32_t* status, unsigned& nvis, unsigned& ntri,
-                                         float Do, float Dd) {
+                                         float Do, float Dd, int skip_plane, int& plane_out) {
     float tb = INFINITY, thi = INFINITY;
     int best = -1;
     traverse<STACK>(nodes, r, tmin * 0.5f, thi, stack, status, nvis, [&](int first, int count) {
         for (int k = first; k < first + count; ++k) {
             float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
             int id = __float_as_int(p0.w);
-            if (id == skip) continue;
+            if (id == skip || __float_as_int(p1.w) == skip_plane) continue;
             ntri++;
             float th;
             int cls = tri_test32_dev(r, p0, p1, p2, Do, Dd, th);
@@ -389,6 +393,7 @@ __device__ __forceinline__ int closest32(const BvhNode* __restrict__ nodes, cons
             if (th < tb || (th == tb && id < best)) {
                 tb = th;
                 best = id;
+                plane_out = __float_as_int(p1.w);
                 thi = tb * 1.00001f;
             }
         }
@@ -862,7 +867,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
     const int lane = threadIdx.x & 31;
     int64_t ray = -1;
     bool done = false;
-    int bounce = 0, prev = -1;
+    int bounce = 0, prev = -1, prev_plane = -1;
     uint64_t key = 0;
     WRay<float> r;
     float Do = 0.0f, Dd = 0.0f;   // drift of the FP32 ray from the FP64 one (sbr_bounce)
@@ -883,6 +888,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
                     ray = idx;
                     bounce = 0;
                     prev = -1;
+                    prev_plane = -1;
                     key = 0;
                     float3 d = launch_dir(idx, __ldg(A.sched.z + idx));
                     r.o = mk(A.txf.x, A.txf.y, A.txf.z);
@@ -903,8 +909,9 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
         unsigned nv = 0, nt = 0;
         // the launch ray: its drift is the transmitter's rounding, which the test's
         // origin term covers, so it is tested with none
+        int plane = -1;
         int id = closest32<STACK>(A.nodes, A.tris, r, eps, prev, stack, th, und, A.status, nv, nt,
-                                  bounce == 0 ? 0.0f : Do, Dd);
+                                  bounce == 0 ? 0.0f : Do, Dd, prev_plane, plane);
         c_vis += nv;
         c_tri += nt;
         c_q++;
@@ -943,6 +950,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_sbr(SbrArgs A, const float4* 
             continue;
         }
         prev = id;
+        prev_plane = plane;
     }
     if (A.counters) {
         warp_count(A.counters + 0, c_vis);
@@ -1510,10 +1518,154 @@ __device__ __forceinline__ void pairs_tile(const CandView& C, int64_t k0, int64_
     }
 }
 
+// Spatial order of the receivers for the image method's warp tiles (a tile's
+// frustum test rejects more candidates when its 32 receivers are close): a
+// counting sort, in one block of 1024 threads, by a coarse Morton cell of each
+// receiver (4 bits per axis of its position in the receivers' bounding box,
+// 4096 cells).  The order only decides which receivers share a tile, not any
+// result; within a cell it follows the shared-memory atomics.  Positions are
+// narrowed to FP32 with integer operations (truncation), which leaves the FP64
+// unit of the one SM alone.
+constexpr int RX_ORDER_MAX = 1 << 20;   // receivers of one sort (one block)
+constexpr int RX_CELLS = 4096;
+
+__device__ __forceinline__ float narrow_trunc(double v) {   // FP64 -> FP32 toward zero, normal range
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    if (e <= 0) return 0.0f;
+    const uint32_t f = (uint32_t)(b >> 32) & 0x80000000u;
+    if (e >= 255) return __int_as_float((int)(f | 0x7f7fffffu));
+    return __int_as_float((int)(f | ((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7fffffu)));
+}
+
+__device__ __forceinline__ uint32_t morton_spread4(uint32_t x) {   // bits 0..3 to every third bit
+    x &= 0xfu;
+    return (x & 1u) | ((x & 2u) << 2) | ((x & 4u) << 4) | ((x & 8u) << 6);
+}
+
+// One block orders the receivers rx[0..R) into order[0..R) (indices into rx).
+// Each thread holds up to RX_PER_THREAD receivers' positions and cells in
+// registers, so the positions are read once; beyond that they are read again.
+constexpr int RX_PER_THREAD = 8;
+
+__device__ __forceinline__ void rx_order_block(const double* __restrict__ rx, int R, int32_t* order) {
+    __shared__ int cnt[RX_CELLS];
+    __shared__ float sbox[6][32];
+    __shared__ int wsum[32];
+    for (int c = threadIdx.x; c < RX_CELLS; c += blockDim.x) cnt[c] = 0;
+    float px[RX_PER_THREAD][3];
+#pragma unroll
+    for (int k = 0; k < RX_PER_THREAD; ++k) {
+        const int i = threadIdx.x + k * (int)blockDim.x;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) px[k][c] = i < R ? narrow_trunc(rx[3 * (int64_t)i + c]) : 0.0f;
+    }
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+    for (int k = 0; k < RX_PER_THREAD; ++k)
+        if (threadIdx.x + k * (int)blockDim.x < R)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = fminf(lo[c], px[k][c]);
+                hi[c] = fmaxf(hi[c], px[k][c]);
+            }
+    for (int i = threadIdx.x + RX_PER_THREAD * (int)blockDim.x; i < R; i += blockDim.x)
+        for (int c = 0; c < 3; ++c) {
+            const float v = narrow_trunc(rx[3 * (int64_t)i + c]);
+            lo[c] = fminf(lo[c], v);
+            hi[c] = fmaxf(hi[c], v);
+        }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = warp_minf(lo[c]);
+        hi[c] = warp_maxf(hi[c]);
+        if (lane == 0) {
+            sbox[c][wid] = lo[c];
+            sbox[3 + c][wid] = hi[c];
+        }
+    }
+    __syncthreads();
+    float sc[3];
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = warp_minf(lane < nw ? sbox[c][lane] : INFINITY);
+        hi[c] = warp_maxf(lane < nw ? sbox[3 + c][lane] : -INFINITY);
+        sc[c] = hi[c] > lo[c] ? 15.999f / (hi[c] - lo[c]) : 0.0f;
+    }
+    auto cell_of = [&](float x, float y, float z) {
+        const float v[3] = {x, y, z};
+        uint32_t m = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float q = fminf(fmaxf((v[c] - lo[c]) * sc[c], 0.0f), 15.0f);
+            m |= morton_spread4((uint32_t)q) << c;
+        }
+        return (int)m;
+    };
+    auto cell_far = [&](int i) {
+        return cell_of(narrow_trunc(rx[3 * (int64_t)i]), narrow_trunc(rx[3 * (int64_t)i + 1]),
+                       narrow_trunc(rx[3 * (int64_t)i + 2]));
+    };
+    int myc[RX_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < RX_PER_THREAD; ++k) {
+        myc[k] = cell_of(px[k][0], px[k][1], px[k][2]);
+        if (threadIdx.x + k * (int)blockDim.x < R) atomicAdd(&cnt[myc[k]], 1);
+    }
+    for (int i = threadIdx.x + RX_PER_THREAD * (int)blockDim.x; i < R; i += blockDim.x) atomicAdd(&cnt[cell_far(i)], 1);
+    __syncthreads();
+    // exclusive scan of the cell counts: RX_CELLS / blockDim.x consecutive cells per thread
+    const int per = RX_CELLS / (int)blockDim.x;
+    int run = 0;
+    for (int k = 0; k < per; ++k) run += cnt[threadIdx.x * per + k];
+    int x = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int v = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, v, o);
+            if (lane >= o) v += y;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int base = x - run + (wid > 0 ? wsum[wid - 1] : 0);
+    for (int k = 0; k < per; ++k) {
+        const int c = cnt[threadIdx.x * per + k];
+        cnt[threadIdx.x * per + k] = base;   // the cell's next slot
+        base += c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RX_PER_THREAD; ++k) {
+        const int i = threadIdx.x + k * (int)blockDim.x;
+        if (i < R) order[atomicAdd(&cnt[myc[k]], 1)] = i;
+    }
+    for (int i = threadIdx.x + RX_PER_THREAD * (int)blockDim.x; i < R; i += blockDim.x)
+        order[atomicAdd(&cnt[cell_far(i)], 1)] = i;
+}
+
+__global__ void __launch_bounds__(1024) k_rx_order(const double* __restrict__ rx, int R, int32_t* order) {
+    rx_order_block(rx, R, order);
+}
+
+// One block per scene of a batch: order[rx_off[s] + j] = the scene-local index
+// of its j-th receiver in tile order.
+__global__ void __launch_bounds__(1024) k_rx_order_batch(const double* __restrict__ rx, const int64_t* rx_off,
+                                                         int32_t* order) {
+    const int64_t o = rx_off[blockIdx.x];
+    rx_order_block(rx + 3 * o, (int)(rx_off[blockIdx.x + 1] - o), order + o);
+}
+
 struct PairArgs {
     CandView C;
     int R;
     const double* rx;
+    const int32_t* order;   // tile order of the receivers (k_rx_order), or null: as given
     const float4* tri_bary;
     PairSink S;
 };
@@ -1528,8 +1680,9 @@ __global__ void k_pairs(PairArgs A) {
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t t = warp0; t < tiles; t += nwarps) {
         const int64_t kt = t / rt_n, rt = t - kt * rt_n;
-        const int64_t r = rt * 32 + lane;
-        const bool r_ok = r < A.R;
+        const int64_t rs = rt * 32 + lane;
+        const bool r_ok = rs < A.R;
+        const int64_t r = r_ok && A.order ? (int64_t)A.order[rs] : rs;
         float3 rxf = make_float3(0.0f, 0.0f, 0.0f);
         if (r_ok) rxf = make_float3((float)A.rx[3 * r], (float)A.rx[3 * r + 1], (float)A.rx[3 * r + 2]);
         const int64_t k0 = kt * PAIR_CC, k1 = min(A.C.K, k0 + PAIR_CC);
@@ -2057,6 +2210,27 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
     unsigned long long* c2 = tw + 16;               // visibility queue count, .., [4] duplicates dropped
     int32_t* f2 = reinterpret_cast<int32_t*>(tw + 24);  // queue overflow
     int64_t* K_dev = reinterpret_cast<int64_t*>(tw + 28);
+    // the receivers' tile order for the image method (k_rx_order) depends only on
+    // the receivers: it runs on the side stream, beside the SBR, and the image
+    // method waits for it (inside a stream capture, a parallel branch)
+    int32_t* rx_order = nullptr;
+    if (n_rx > 32 && n_rx <= RX_ORDER_MAX) {
+        if (ctx->rx_order_cap < n_rx && !in_capture) {
+            if (ctx->d_rx_order) RT_CK(ctx, cudaFree(ctx->d_rx_order));
+            ctx->d_rx_order = nullptr;
+            ctx->rx_order_cap = 0;
+            RT_CK(ctx, cudaMalloc((void**)&ctx->d_rx_order, (size_t)n_rx * sizeof(int32_t)));
+            ctx->rx_order_cap = n_rx;
+        }
+        if (ctx->rx_order_cap >= n_rx) {   // (a capture with too small a buffer keeps the given order)
+            RT_CK(ctx, cudaEventRecord(ctx->ev_fork, st));
+            RT_CK(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+            k_rx_order<<<1, 1024, 0, ctx->side>>>(rx_dev, n_rx, ctx->d_rx_order);
+            RT_COUNT(ctx);
+            RT_CK(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+            rx_order = ctx->d_rx_order;
+        }
+    }
     for (int attempt = 0;; ++attempt) {
         if (attempt >= 8) return rt_fail(ctx, RT_ERR_CAPACITY, "trace capacities did not converge");
         const size_t cap = sc->hash_cap;
@@ -2208,6 +2382,8 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         PA.C = CandView{Kc, cand_depth, cand_tri, img64, img32, frus};
         PA.R = n_rx;
         PA.rx = rx_dev;
+        PA.order = rx_order;
+        if (rx_order) TCK(cudaStreamWaitEvent(st, ctx->ev_join, 0));   // the side stream's tile order
         PA.tri_bary = sc->d_tri_bary;
         PA.S = PairSink{queue, c2, qcap, f2};
         mark(ctx, 2);
@@ -2449,7 +2625,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 6) k_sbr_batch(BatchSbr A) {
     const int64_t total = A.ray_off[A.n];
     int64_t ray = -1;
     bool done = false;
-    int bounce = 0, prev = -1;
+    int bounce = 0, prev = -1, prev_plane = -1;
     uint64_t key = 0;
     WRay<float> r;
     const BvhNode* nodes = nullptr;
@@ -2478,6 +2654,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 6) k_sbr_batch(BatchSbr A) {
                     ray = r0 + local;
                     bounce = 0;
                     prev = -1;
+                    prev_plane = -1;
                     key = 0;
                     nodes = d.nodes;
                     bvh_tris = d.bvh_tris;
@@ -2501,8 +2678,9 @@ __global__ void __launch_bounds__(TRACE_THREADS, 6) k_sbr_batch(BatchSbr A) {
         float th;
         bool und = false;
         unsigned nv = 0, nt = 0;
+        int plane = -1;
         int id = closest32<STACK>(nodes, bvh_tris, r, eps, prev, stack, th, und, A.status, nv, nt,
-                                  bounce == 0 ? 0.0f : Do, Dd);
+                                  bounce == 0 ? 0.0f : Do, Dd, prev_plane, plane);
         c_vis += nv;
         c_tri += nt;
         c_q++;
@@ -2540,6 +2718,7 @@ __global__ void __launch_bounds__(TRACE_THREADS, 6) k_sbr_batch(BatchSbr A) {
             continue;
         }
         prev = id;
+        prev_plane = plane;
     }
     if (A.counters) {
         warp_count(A.counters + 0, c_vis);
@@ -2690,6 +2869,7 @@ struct BatchPairs {
     const int64_t* rx_off;     // n + 1
     int n;
     const double* rx;          // all receivers
+    const int32_t* order;      // per scene, the tile order of its receivers (scene-local), or null
     PairSink S;
 };
 
@@ -2707,9 +2887,9 @@ __global__ void k_pairs_batch(BatchPairs A) {
         const int64_t rt_n = (R + 31) / 32;
         const int64_t lt = t - A.tile_off[s];
         const int64_t kt = lt / rt_n, rt = lt - kt * rt_n;
-        const int64_t r = rt * 32 + lane;
-        const bool r_ok = r < R;
-        const int64_t rg = A.rx_off[s] + r;
+        const int64_t rs = rt * 32 + lane;
+        const bool r_ok = rs < R;
+        const int64_t rg = A.rx_off[s] + (r_ok && A.order ? (int64_t)A.order[A.rx_off[s] + rs] : rs);
         float3 rxf = make_float3(0.0f, 0.0f, 0.0f);
         if (r_ok) rxf = make_float3((float)A.rx[3 * rg], (float)A.rx[3 * rg + 1], (float)A.rx[3 * rg + 2]);
         const int64_t k0 = A.cand_off[s] + kt * PAIR_CC, k1 = A.cand_off[s] + min(K, (kt + 1) * PAIR_CC);
@@ -3327,7 +3507,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         RT_COUNT(ctx);
         size_t need2 = KT * 4 + (size_t)D * KT * 4 + (size_t)D * KT * 24 + (size_t)D * KT * 16 + qcap * 8 +
                        (size_t)bits_off[n] * 4 + (size_t)(RT + 1) * 8 * 2 + qcap * 4 +
-                       2 * (size_t)(D + 1) * qcap * 16 + 5 * KT * 16 + 20 * 256;
+                       2 * (size_t)(D + 1) * qcap * 16 + 5 * KT * 16 + (size_t)RT * 4 + 20 * 256;
         s0 = rt_scratch(ctx, need2, &base);
         if (s0 != RT_OK) return fail(s0);
         Arena ar2{(char*)base};
@@ -3342,7 +3522,10 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         float4* seg_o = ar2.take<float4>((size_t)(D + 1) * qcap);
         float4* seg_d = ar2.take<float4>((size_t)(D + 1) * qcap);
         float4* frus = ar2.take<float4>(5 * (size_t)KT);
+        int32_t* rx_order = ar2.take<int32_t>((size_t)RT);
         BCK(cudaMemsetAsync(bits, 0, (size_t)bits_off[n] * 4, st));
+        k_rx_order_batch<<<n, 1024, 0, st>>>(rx_dev, d_rx_off, rx_order);
+        RT_COUNT(ctx);
         k_candidates_batch<<<grid_for(ctx, KT, 32, 32), 32, 0, st>>>(p->d_cand, KT, D, d_sd, d_cand_off, n, K_dev,
                                                                     cand_depth, cand_tri, img64, img32, frus);
         RT_COUNT(ctx);
@@ -3355,6 +3538,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         PA.rx_off = d_rx_off;
         PA.n = n;
         PA.rx = rx_dev;
+        PA.order = rx_order;
         PA.S = PairSink{queue, c2, qcap, f2};
         mark(ctx, 2);
         k_pairs_batch<<<grid_for(ctx, pair_off[n] * 32, 256, ctx->tune_pairs_blocks_per_sm), 256, 0, st>>>(PA);
