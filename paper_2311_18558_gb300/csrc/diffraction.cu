@@ -262,8 +262,10 @@ __device__ __forceinline__ bool keller(const WedgeDev& w, D3 T, D3 R, double eps
 }
 
 // Segment p0 -> p1 free of every triangle but f0, f1 for t in (eps, len - eps).
+// One end is on the wedge's edge, which lies in the planes pl0, pl1 of both faces,
+// so the segment meets those planes only at that end: their triangles are skipped.
 __device__ __forceinline__ bool seg_clear(const BvhNode* nodes, const float4* tris, D3 p0, D3 p1, double eps, int f0,
-                                          int f1, int32_t* status) {
+                                          int f1, int pl0, int pl1, int32_t* status) {
     Ray64 r;
     r.o[0] = p0.x;
     r.o[1] = p0.y;
@@ -275,7 +277,7 @@ __device__ __forceinline__ bool seg_clear(const BvhNode* nodes, const float4* tr
     const float3 o32 = make_float3((float)p0.x, (float)p0.y, (float)p0.z);
     const float3 d32 = make_float3((float)d.x, (float)d.y, (float)d.z);
     const float len2f = d32.x * d32.x + d32.y * d32.y + d32.z * d32.z;
-    return !any_hit_seg(nodes, tris, r, o32, d32, len2f, eps, f0, status, f1);
+    return !any_hit_seg(nodes, tris, r, o32, d32, len2f, eps, f0, status, f1, pl0, pl1);
 }
 
 // ------------------------------------------------------------------ tracing kernels
@@ -388,6 +390,7 @@ struct DifArgs {
     double eps;
     const BvhNode* nodes;
     const float4* tris;
+    const float4* tri_v;   // vertex records (plane ids in the second's .w)
     uint32_t* bits;
     int64_t words;
     int32_t* status;
@@ -410,8 +413,10 @@ __global__ void __launch_bounds__(DIF_THREADS) k_dif_pairs(DifArgs A) {
         // the receiver's segment first: it rejects more pairs than the transmitter's
         // (measured on the street canyon: 25 % of the Keller-valid pairs see the
         // receiver, 64 % the transmitter), so fewer long segments are queried
-        if (!seg_clear(A.nodes, A.tris, kp.Q, R, A.eps, f.x, f.y, A.status)) continue;
-        if (!seg_clear(A.nodes, A.tris, A.tx, kp.Q, A.eps, f.x, f.y, A.status)) continue;
+        const int pl0 = __float_as_int(__ldg(A.tri_v + 3 * f.x + 1).w);
+        const int pl1 = __float_as_int(__ldg(A.tri_v + 3 * f.y + 1).w);
+        if (!seg_clear(A.nodes, A.tris, kp.Q, R, A.eps, f.x, f.y, pl0, pl1, A.status)) continue;
+        if (!seg_clear(A.nodes, A.tris, A.tx, kp.Q, A.eps, f.x, f.y, pl0, pl1, A.status)) continue;
         atomicOr(A.bits + (int64_t)r * A.words + (k >> 5), 1u << (k & 31));
     }
 }
@@ -995,7 +1000,7 @@ RT_EXPORT rt_status rt_trace_diffraction(rt_ctx* ctx, const rt_scene* scene, con
         DCK(cudaMallocAsync((void**)&wf, (size_t)Kw * 5 * sizeof(float4), st));
         k_dif_prep<<<dif_grid(ctx, Kw, 128, 4), 128, 0, st>>>(scene->d_wedge, list, Kw, D3{tx[0], tx[1], tx[2]}, wf);
         RT_COUNT(ctx);
-        DifArgs A;
+        DifArgs A{};
         A.wf = wf;
         A.wedge = scene->d_wedge;
         A.wfaces = scene->d_wedge_faces;
@@ -1007,6 +1012,7 @@ RT_EXPORT rt_status rt_trace_diffraction(rt_ctx* ctx, const rt_scene* scene, con
         A.eps = scene->eps;
         A.nodes = scene->d_nodes;
         A.tris = scene->d_bvh_tris;
+        A.tri_v = scene->d_tri_v;
         A.bits = bits;
         A.words = words;
         A.status = ctx->d_status;

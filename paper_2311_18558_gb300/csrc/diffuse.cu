@@ -62,6 +62,7 @@ struct Scn {
     const double* n64;       // 4 per triangle: unit normal, n.v0
     const float4* plane32;   // 3 per triangle, the first = (unit normal, n.v0) in FP32
     double eps;
+    const float4* tri_v;     // 3 per triangle (vertices; the plane id in the second record's .w)
 };
 
 __device__ __forceinline__ void load_n(const double* n64, int t, double n[3]) {
@@ -179,7 +180,9 @@ __device__ __forceinline__ void nee_pair(int64_t N, int b, int i, int s, int r, 
         const double len2 = ray.d[0] * ray.d[0] + ray.d[1] * ray.d[1] + ray.d[2] * ray.d[2];
         if (!(len2 > S.eps * S.eps)) return;
     }
-    if (any_hit_seg(S.nodes, S.tris, ray, o32, d32, len2f, S.eps, t, status)) return;
+    // the source triangle's plane: the segment meets it only at its start
+    const int pl = __float_as_int(__ldg(S.tri_v + 3 * t + 1).w);
+    if (any_hit_seg(S.nodes, S.tris, ray, o32, d32, len2f, S.eps, t, status, -1, pl)) return;
     atomicOr(mask + (int64_t)r * W + (s >> 5), 1u << (s & 31));
 }
 
@@ -1024,7 +1027,7 @@ RT_EXPORT rt_status rt_trace_diffuse(rt_ctx* ctx, const rt_scene* scene, const d
         cleanup();
         return rt_cuda_fail(ctx, e, "diffuse trace buffers");
     }
-    const Scn S{scene->d_nodes, scene->d_bvh_tris, scene->d_tri_n64, scene->d_tri_bary, scene->eps};
+    const Scn S{scene->d_nodes, scene->d_bvh_tris, scene->d_tri_n64, scene->d_tri_bary, scene->eps, scene->d_tri_v};
     k_df_rays<<<grid_of(ctx, std::max<int64_t>(N, R), DF_THREADS, 16), DF_THREADS, 0, st>>>(
         N, (int)D, tx_host[0], tx_host[1], tx_host[2], z, S, hit_tri, hit_pt, hit_pt32, (int)R, rx_dev, rx32,
         status); RT_COUNT(ctx);

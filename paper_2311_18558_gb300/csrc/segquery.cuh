@@ -280,15 +280,17 @@ __device__ int closest_hit64(const BvhNode* __restrict__ nodes, const float4* __
     return best;
 }
 
-// Any hit with tlo < t < thi, skipping triangles `skip` and `skip2`: FP32 prefilter, FP64
-// test only where the prefilter is undecided.
+// Any hit with tlo < t < thi, skipping triangles `skip` and `skip2` and every
+// triangle in the plane `pl0` or `pl1` (plane ids, the .w of a triangle's second
+// vertex record) of a segment end, which the segment meets only at that end:
+// FP32 prefilter, FP64 test only where the prefilter is undecided.
 // The segment is origin + t d, t in (eps / |d|, 1 - eps / |d|); len2f is |d|^2
 // from the FP32 direction (the FP32 bounds only), the FP64 |d| is formed from r.d;
 // only r.o and r.d need to be set: the FP64 shear and bounds are formed the first
 // time a triangle is undecided (most queries never need them).
 __device__ bool any_hit_seg(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, Ray64& r,
                             float3 o32, float3 d32, float len2f, double eps, int skip, int32_t* status,
-                            int skip2 = -1) {
+                            int skip2 = -1, int pl0 = -1, int pl1 = -1) {
     r.of = o32;
     {
         const float dk[3] = {d32.x, d32.y, d32.z};
@@ -306,7 +308,10 @@ __device__ bool any_hit_seg(const BvhNode* __restrict__ nodes, const float4* __r
         for (int k = first; k < first + count; ++k) {
             const float4 p0 = __ldg(tris + 3 * k);
             if (__float_as_int(p0.w) == skip || __float_as_int(p0.w) == skip2) continue;
-            const float4 p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
+            const float4 p1 = __ldg(tris + 3 * k + 1);
+            const int pid = __float_as_int(p1.w);
+            if (pid == pl0 || pid == pl1) continue;
+            const float4 p2 = __ldg(tris + 3 * k + 2);
             const int c = tri_seg32(q, p0, p1, p2, flo, fthi);
             if (c == 0) continue;
             if (c == 1) {
