@@ -391,7 +391,7 @@ rt_status rt_launch_paths_records(rt_ctx* ctx, rt_paths* p, const int64_t* P_dev
     p->d_Dm = reinterpret_cast<float4*>(b + o_Dm);
     p->d_dir = reinterpret_cast<float4*>(b + o_dir);
     if (p->P == 0) return RT_OK;
-    k_records<<<grid_for(ctx, p->P, 128, 16), 128, 0, st>>>(p->P, P_dev, p->D, p->d_pts, p->d_depth, p->d_tri,
+    k_records<<<grid_for(ctx, p->P, 32, 32), 32, 0, st>>>(p->P, P_dev, p->D, p->d_pts, p->d_depth, p->d_tri,
                                                            p->scene->d_tri_n64, p->scene->d_tri_material,
                                                            p->scene->d_is_pec, p->d_tau, p->d_len, p->d_mc,
                                                            p->d_Dm, p->d_dir); RT_COUNT(ctx);

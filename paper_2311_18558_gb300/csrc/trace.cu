@@ -1839,8 +1839,15 @@ __global__ void k_scan(const int64_t* __restrict__ counts, int n, int64_t* offse
     const int T = blockDim.x;   // a multiple of 32, at most 1024
     const int per = (n + T - 1) / T;
     const int lo = threadIdx.x * per, hi = min(n, lo + per);
+    // up to 8 counts per thread are loaded at once and kept (n <= 8 T)
+    constexpr int KEEP = 8;
+    int64_t v[KEEP];
+#pragma unroll
+    for (int k = 0; k < KEEP; ++k) v[k] = lo + k < hi ? counts[lo + k] : 0;
     int64_t s = 0;
-    for (int i = lo; i < hi; ++i) s += counts[i];
+#pragma unroll
+    for (int k = 0; k < KEEP; ++k) s += v[k];
+    for (int i = lo + KEEP; i < hi; ++i) s += counts[i];
     // inclusive scan of the per-thread sums: within each warp by shuffles, then
     // over the warp totals by the first warp
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1862,7 +1869,13 @@ __global__ void k_scan(const int64_t* __restrict__ counts, int n, int64_t* offse
     }
     __syncthreads();
     int64_t run = x - s + (w > 0 ? wsum[w - 1] : 0);
-    for (int i = lo; i < hi; ++i) {
+#pragma unroll
+    for (int k = 0; k < KEEP; ++k)
+        if (lo + k < hi) {
+            offsets[lo + k] = run;
+            run += v[k];
+        }
+    for (int i = lo + KEEP; i < hi; ++i) {
         offsets[i] = run;
         run += counts[i];
     }
@@ -2470,7 +2483,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         k_expand<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, off_e, rx_e, path_cand,
                                                                              pcap); RT_COUNT(ctx);
         CandView C{Kc, cand_depth, cand_tri, img64, img32};
-        k_points<<<grid_for(ctx, pcap, 64, 32), 64, 0, st>>>(C, P_e, pcap, D, rx_e, path_cand, rx_dev, tx_host[0],
+        k_points<<<grid_for(ctx, pcap, 32, 32), 32, 0, st>>>(C, P_e, pcap, D, rx_e, path_cand, rx_dev, tx_host[0],
                                                            tx_host[1], tx_host[2], sc->d_tri_v, sc->d_tri_n64,
                                                            sc->d_tri_bary64, sc->eps, pts_e, depth_e, rx_e, tri_e, edge,
                                                            bits, words); RT_COUNT(ctx);
@@ -3619,7 +3632,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
                                                                         off_e, rx_e, path_cand, pcap);
         RT_COUNT(ctx);
         CandView C{KT, cand_depth, cand_tri, img64, img32};
-        k_points_batch<<<grid_for(ctx, pcap, 64, 32), 64, 0, st>>>(C, P_e, pcap, D, d_sd, d_cand_off, n, rx_e, path_cand,
+        k_points_batch<<<grid_for(ctx, pcap, 32, 32), 32, 0, st>>>(C, P_e, pcap, D, d_sd, d_cand_off, n, rx_e, path_cand,
                                                                  rx_dev, pts_e, depth_e, rx_e, tri_e, edge, bits,
                                                                  d_rx_off, d_bits_off);
         RT_COUNT(ctx);
