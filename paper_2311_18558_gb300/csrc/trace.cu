@@ -31,6 +31,20 @@
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+
+
+// Programmatic dependent launch (sm_90 and later): a kernel launched with
+// launch_pdl may be launched while the previous kernel of its stream finishes.
+// Its first statement, pdl_entry, waits for that kernel's completion and memory
+// (griddepcontrol.wait) before anything is read, then lets the next kernel
+// launch (griddepcontrol.launch_dependents).  A dependent is launched only once
+// every block of this kernel has started, so its waiting blocks never hold
+// resources that this kernel's blocks still need.  Launched normally, the wait
+// returns at once.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
 constexpr int TRACE_THREADS = 128;
 constexpr int REDO_THREADS = 32;
 constexpr int REDO_BLOCKS_PER_SM = 16;
@@ -972,6 +986,7 @@ __device__ __forceinline__ uint64_t key_prefix(uint64_t key, int b) {   // the f
 
 __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const double* __restrict__ tri_n64,
                                                            const float4* __restrict__ tri_v) {
+    pdl_entry();
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
     int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
@@ -1031,6 +1046,7 @@ __global__ void __launch_bounds__(REDO_THREADS) k_sbr_redo(SbrArgs A, const doub
 // counting past it, which the host reads as an overflow).
 __global__ void k_table_compact(const unsigned long long* __restrict__ table, uint64_t cap, uint64_t* out,
                                 unsigned long long* count, uint64_t out_cap) {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i - lane < cap;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -1122,6 +1138,7 @@ __device__ __forceinline__ uint64_t rank_value(uint64_t key) {
 // n: the number of keys, read from the compaction count (at most cap).
 __global__ void k_rank_count(const uint64_t* __restrict__ keys, const unsigned long long* __restrict__ n_dev, int cap,
                              int* __restrict__ rank) {
+    pdl_entry();
     __shared__ uint64_t sj[RANK_TILE];
     const int n = (int)min(*n_dev, (unsigned long long)cap);
     const int j0 = blockIdx.x * RANK_TILE;
@@ -1140,6 +1157,7 @@ __global__ void k_rank_count(const uint64_t* __restrict__ keys, const unsigned l
 
 __global__ void k_rank_scatter(const uint64_t* __restrict__ keys, const int* __restrict__ rank,
                                const unsigned long long* __restrict__ n_dev, int cap, uint64_t* __restrict__ out) {
+    pdl_entry();
     const int n = (int)min(*n_dev, (unsigned long long)cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[rank[i]] = keys[i];
 }
@@ -1169,6 +1187,7 @@ __global__ void k_fill_u64(uint64_t* p, uint64_t n, uint64_t v) {
 // for the later kernels and the host.
 __global__ void k_cand_keys(const uint64_t* __restrict__ sorted, const unsigned long long* __restrict__ n_dev,
                             int64_t cap, uint64_t* __restrict__ cand, int64_t* __restrict__ K_dev) {
+    pdl_entry();
     const int64_t n = (int64_t)min(*n_dev, (unsigned long long)cap);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
         cand[i] = i == 0 ? 0ull : sorted[i - 1];
@@ -1254,6 +1273,7 @@ __global__ void k_candidates(const uint64_t* __restrict__ keys, int64_t Kc, cons
                              double tx, double ty, double tz, const float4* __restrict__ tri_v,
                              const double* __restrict__ tri_n64, const float4* __restrict__ tri_bary,
                              int32_t* cand_depth, int32_t* cand_tri, double* img64, float4* img32, float4* frus) {
+    pdl_entry();
     const int64_t K = *K_dev;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Kc; k += (int64_t)gridDim.x * blockDim.x) {
         if (k >= K) {
@@ -1673,6 +1693,7 @@ struct PairArgs {
 // Image-method prefilter over all (candidate, receiver) pairs, FP32 only, in
 // warp tiles (see pairs_tile).  The FP64 work happens on the dense queue.
 __global__ void k_pairs(PairArgs A) {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     const int64_t rt_n = (A.R + 31) / 32, kt_n = (A.C.K + PAIR_CC - 1) / PAIR_CC;
     const int64_t tiles = rt_n * kt_n;
@@ -1728,6 +1749,7 @@ struct VisArgs {
 // the grown triangle, segments longer than eps) runs in k_points on the dense
 // list of the pairs left visible, where an invalid pair is dropped.
 __global__ void __launch_bounds__(TRACE_THREADS) k_backtrace(VisArgs A) {
+    pdl_entry();
     unsigned long long n = *A.qcount;
     if (n > A.qcap) n = A.qcap;
     for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < n;
@@ -1745,6 +1767,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_backtrace(VisArgs A) {
 }
 
 __global__ void __launch_bounds__(TRACE_THREADS) k_segments(VisArgs A) {
+    pdl_entry();
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
     int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
@@ -1823,6 +1846,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_segments(VisArgs A) {
 
 // Per-receiver popcount of the validity bitmask (one warp per receiver).
 __global__ void k_row_count(const uint32_t* __restrict__ bits, int R, int64_t words, int64_t* counts) {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R;
          r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -1835,6 +1859,7 @@ __global__ void k_row_count(const uint32_t* __restrict__ bits, int R, int64_t wo
 
 // Exclusive scan of n int64 counts into offsets[0..n] (single block).
 __global__ void k_scan(const int64_t* __restrict__ counts, int n, int64_t* offsets) {
+    pdl_entry();
     __shared__ int64_t wsum[32];
     const int T = blockDim.x;   // a multiple of 32, at most 1024
     const int per = (n + T - 1) / T;
@@ -1888,6 +1913,7 @@ __global__ void k_scan(const int64_t* __restrict__ counts, int n, int64_t* offse
 // overflow and traces again with more room).
 __global__ void k_expand(const uint32_t* __restrict__ bits, int R, int64_t words, const int64_t* __restrict__ offsets,
                          int32_t* path_rx, int32_t* path_cand, int64_t cap) {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R;
          r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -1927,6 +1953,7 @@ __global__ void k_points(CandView C, const int64_t* __restrict__ P_dev, int64_t 
                          double tz, const float4* __restrict__ tri_v, const double* __restrict__ tri_n64,
                          const double* __restrict__ bary64, double eps, double* pts_out, int32_t* depth_out,
                          int32_t* rx_out, int32_t* tri_out, int32_t* edge_flag, uint32_t* bits, int64_t words) {
+    pdl_entry();
     const int64_t P = min(*P_dev, cap);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t k = path_cand[i];
@@ -1981,6 +2008,7 @@ __global__ void k_dedup(const int64_t* __restrict__ P_dev, int64_t cap, int D, c
                         const int32_t* __restrict__ edge_flag, const double* __restrict__ tri_n64,
                         const float4* __restrict__ tri_v, double diag, uint32_t* bits, int64_t words,
                         unsigned long long* drops) {
+    pdl_entry();
     const int64_t P = min(*P_dev, cap);
     const double tol2 = (1e-9 * diag) * (1e-9 * diag);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
@@ -2028,6 +2056,7 @@ __global__ void k_compact_paths(int R, int D, int64_t cap, const int64_t* __rest
                                 const double* __restrict__ pts, const int32_t* __restrict__ depth,
                                 const int32_t* __restrict__ rx, const int32_t* __restrict__ tri, double* __restrict__ pts_n,
                                 int32_t* __restrict__ depth_n, int32_t* __restrict__ rx_n, int32_t* __restrict__ tri_n) {
+    pdl_entry();
     const int lane = threadIdx.x & 31;
     const int64_t P = min(off[R], cap), Pn = min(off_n[R], cap);
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R;
@@ -2058,6 +2087,7 @@ __global__ void k_compact_paths(int R, int D, int64_t cap, const int64_t* __rest
 __global__ void k_trace_check(const unsigned long long* __restrict__ tw, const int64_t* __restrict__ P_emit,
                               const int64_t* __restrict__ P_kept, int64_t ucap, int64_t pcap, int64_t* meta,
                               int32_t* status, int report) {
+    pdl_entry();
     if (threadIdx.x != 0) return;
     const int32_t f1 = reinterpret_cast<const int32_t*>(tw + 8)[0];
     const int32_t f2 = reinterpret_cast<const int32_t*>(tw + 24)[0];
@@ -2072,6 +2102,7 @@ __global__ void k_trace_check(const unsigned long long* __restrict__ tw, const i
 // After an overflowed pass (meta[2] != 0) the receiver offsets may point past the
 // slots: every receiver is emptied, so that no later kernel reads beyond them.
 __global__ void k_trace_guard(const int64_t* __restrict__ meta, int64_t* offsets, int R) {
+    pdl_entry();
     if (meta[2] == 0) return;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= R; r += (int64_t)gridDim.x * blockDim.x)
         offsets[r] = 0;
@@ -2086,6 +2117,25 @@ inline int grid_for(rt_ctx* ctx, int64_t n, int threads, int per_sm = 8) {
 }
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// A kernel launch with programmatic stream serialization (see pdl_entry, which
+// every kernel launched this way calls first).  Errors are left to
+// cudaGetLastError, as for the <<<>>> launches.
+template <typename... KP, typename... Args>
+void launch_pdl(void (*kern)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    static_assert(sizeof...(KP) == sizeof...(Args), "launch_pdl: argument count");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, kern, static_cast<KP>(args)...);
+}
 
 }  // namespace
 
@@ -2309,8 +2359,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         RT_COUNT(ctx);
         mark(ctx, 7);
         RT_CK_LAUNCH(ctx);
-        k_sbr_redo<<<ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 3 * CAND_CAP) * REDO_THREADS * sizeof(int), st>>>(
-            A, sc->d_tri_n64, sc->d_tri_v);
+        launch_pdl(k_sbr_redo, ctx->num_sms * REDO_BLOCKS_PER_SM, REDO_THREADS, (size_t)(RT_STACK + 3 * CAND_CAP) * REDO_THREADS * sizeof(int), st, A, sc->d_tri_n64, sc->d_tri_v);
         RT_COUNT(ctx);
         mark(ctx, 1);
         RT_CK_LAUNCH(ctx);
@@ -2325,17 +2374,17 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         // ---------------- compact + sort (length, lexicographic), at most ucap keys
         if (rank_sort) {
             RT_CK(ctx, cudaMemsetAsync(rank, 0, (size_t)RANK_SORT_MAX * 4, st));
-            k_table_compact<<<grid_for(ctx, cap, 256, 16), 256, 0, st>>>(table, cap, unsorted, c1 + 3, (uint64_t)ucap);
+            launch_pdl(k_table_compact, grid_for(ctx, cap, 256, 16), 256, 0, st, table, cap, unsorted, c1 + 3, (uint64_t)ucap);
             RT_COUNT(ctx);
             const int n = (int)ucap;
-            k_rank_count<<<dim3((n + RANK_TILE - 1) / RANK_TILE, (n + 255) / 256), 256, 0, st>>>(unsorted, c1 + 3, n,
+            launch_pdl(k_rank_count, dim3((n + RANK_TILE - 1) / RANK_TILE, (n + 255) / 256), 256, 0, st, unsorted, c1 + 3, n,
                                                                                                  rank);
             RT_COUNT(ctx);
-            k_rank_scatter<<<grid_for(ctx, n, 256), 256, 0, st>>>(unsorted, rank, c1 + 3, n, sorted);
+            launch_pdl(k_rank_scatter, grid_for(ctx, n, 256), 256, 0, st, unsorted, rank, c1 + 3, n, sorted);
             RT_COUNT(ctx);
         } else {
             k_fill_u64<<<grid_for(ctx, n_pad, 256), 256, 0, st>>>(sorted, n_pad, ~0ull); RT_COUNT(ctx);
-            k_table_compact<<<grid_for(ctx, cap, 256, 16), 256, 0, st>>>(table, cap, sorted, c1 + 3, (uint64_t)ucap);
+            launch_pdl(k_table_compact, grid_for(ctx, cap, 256, 16), 256, 0, st, table, cap, sorted, c1 + 3, (uint64_t)ucap);
             RT_COUNT(ctx);
             k_bitonic_local<<<(unsigned)(n_pad / SORT_BLOCK), 1024, 0, st>>>(sorted); RT_COUNT(ctx);
             for (uint64_t k = 2 * SORT_BLOCK; k <= (uint64_t)n_pad; k <<= 1) {
@@ -2364,7 +2413,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         if (_e != cudaSuccess) return fail(rt_cuda_fail(ctx, _e, #call)); \
     } while (0)
         TCK(cudaMallocAsync((void**)&p->d_cand, Kc * 8, st));
-        k_cand_keys<<<grid_for(ctx, Kc, 256), 256, 0, st>>>(sorted, c1 + 3, ucap, p->d_cand, K_dev); RT_COUNT(ctx);
+        launch_pdl(k_cand_keys, grid_for(ctx, Kc, 256), 256, 0, st, sorted, c1 + 3, ucap, p->d_cand, K_dev); RT_COUNT(ctx);
         TCK(cudaGetLastError());
 
         // candidate arrays + visibility queue + bitmask: a fresh scratch layout (the
@@ -2387,7 +2436,7 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         float4* seg_d = ar2.take<float4>((size_t)(D + 1) * qcap);
         float4* frus = ar2.take<float4>(5 * (size_t)Kc);
         TCK(cudaMemsetAsync(bits, 0, (size_t)n_rx * words * 4, st));
-        k_candidates<<<grid_for(ctx, Kc, 32, 32), 32, 0, st>>>(p->d_cand, Kc, K_dev, D, tx_host[0], tx_host[1], tx_host[2],
+        launch_pdl(k_candidates, grid_for(ctx, Kc, 32, 32), 32, 0, st, p->d_cand, Kc, K_dev, D, tx_host[0], tx_host[1], tx_host[2],
                                                              sc->d_tri_v, sc->d_tri_n64, sc->d_tri_bary, cand_depth,
                                                              cand_tri, img64, img32, frus); RT_COUNT(ctx);
         TCK(cudaGetLastError());
@@ -2400,9 +2449,9 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         PA.tri_bary = sc->d_tri_bary;
         PA.S = PairSink{queue, c2, qcap, f2};
         mark(ctx, 2);
-        k_pairs<<<grid_for(ctx, ((Kc + PAIR_CC - 1) / PAIR_CC) * ((n_rx + 31) / 32) * 32, 256,
+        launch_pdl(k_pairs, grid_for(ctx, ((Kc + PAIR_CC - 1) / PAIR_CC) * ((n_rx + 31) / 32) * 32, 256,
                            ctx->tune_pairs_blocks_per_sm),
-                  256, 0, st>>>(PA); RT_COUNT(ctx);
+                  256, 0, st, PA); RT_COUNT(ctx);
         mark(ctx, 3);
         TCK(cudaGetLastError());
         VisArgs VA{};
@@ -2430,15 +2479,15 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         VA.seg_q = seg_q;
         VA.seg_o = seg_o;
         VA.seg_d = seg_d;
-        k_backtrace<<<ctx->num_sms * 8, TRACE_THREADS, 0, st>>>(VA); RT_COUNT(ctx);
+        launch_pdl(k_backtrace, ctx->num_sms * 8, TRACE_THREADS, 0, st, VA); RT_COUNT(ctx);
         TCK(cudaGetLastError());
-        k_segments<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st>>>(VA); RT_COUNT(ctx);
+        launch_pdl(k_segments, ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st, VA); RT_COUNT(ctx);
         mark(ctx, 4);
         TCK(cudaGetLastError());
         int64_t* off_e = nullptr;   // offsets of the emitted paths (before the duplicate rule)
         TCK(cudaMallocAsync((void**)&off_e, (size_t)(n_rx + 1) * 8, st));
-        k_row_count<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, counts); RT_COUNT(ctx);
-        k_scan<<<1, 1024, 0, st>>>(counts, n_rx, off_e); RT_COUNT(ctx);
+        launch_pdl(k_row_count, grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st, bits, n_rx, words, counts); RT_COUNT(ctx);
+        launch_pdl(k_scan, 1, 1024, 0, st, counts, n_rx, off_e); RT_COUNT(ctx);
         TCK(cudaGetLastError());
         if (sc->paths_hint == 0) {
             // the scene's first trace: learn the number of emitted paths
@@ -2480,25 +2529,24 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         }
         TCK(cudaMallocAsync((void**)&p->d_rx_offsets, (size_t)(n_rx + 1) * 8, st));
         const int64_t* P_e = off_e + n_rx;
-        k_expand<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, off_e, rx_e, path_cand,
+        launch_pdl(k_expand, grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st, bits, n_rx, words, off_e, rx_e, path_cand,
                                                                              pcap); RT_COUNT(ctx);
         CandView C{Kc, cand_depth, cand_tri, img64, img32};
-        k_points<<<grid_for(ctx, pcap, 32, 32), 32, 0, st>>>(C, P_e, pcap, D, rx_e, path_cand, rx_dev, tx_host[0],
+        launch_pdl(k_points, grid_for(ctx, pcap, 32, 32), 32, 0, st, C, P_e, pcap, D, rx_e, path_cand, rx_dev, tx_host[0],
                                                            tx_host[1], tx_host[2], sc->d_tri_v, sc->d_tri_n64,
                                                            sc->d_tri_bary64, sc->eps, pts_e, depth_e, rx_e, tri_e, edge,
                                                            bits, words); RT_COUNT(ctx);
-        k_dedup<<<grid_for(ctx, pcap, 256), 256, 0, st>>>(P_e, pcap, D, off_e, rx_e, path_cand, depth_e, tri_e, pts_e,
+        launch_pdl(k_dedup, grid_for(ctx, pcap, 256), 256, 0, st, P_e, pcap, D, off_e, rx_e, path_cand, depth_e, tri_e, pts_e,
                                                           edge, sc->d_tri_n64, sc->d_tri_v, sc->diag, bits, words,
                                                           c2 + 4); RT_COUNT(ctx);
-        k_row_count<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(bits, n_rx, words, counts); RT_COUNT(ctx);
-        k_scan<<<1, 1024, 0, st>>>(counts, n_rx, p->d_rx_offsets); RT_COUNT(ctx);
-        k_compact_paths<<<grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st>>>(
-            n_rx, D, pcap, off_e, p->d_rx_offsets, path_cand, pts_e, depth_e, rx_e, tri_e, p->d_pts, p->d_depth,
+        launch_pdl(k_row_count, grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st, bits, n_rx, words, counts); RT_COUNT(ctx);
+        launch_pdl(k_scan, 1, 1024, 0, st, counts, n_rx, p->d_rx_offsets); RT_COUNT(ctx);
+        launch_pdl(k_compact_paths, grid_for(ctx, (int64_t)n_rx * 32, 256, 16), 256, 0, st, n_rx, D, pcap, off_e, p->d_rx_offsets, path_cand, pts_e, depth_e, rx_e, tri_e, p->d_pts, p->d_depth,
             p->d_rx, p->d_tri); RT_COUNT(ctx);
         TCK(cudaGetLastError());
-        k_trace_check<<<1, 32, 0, st>>>(tw, off_e + n_rx, p->d_rx_offsets + n_rx, ucap, pcap, meta, status, async);
+        launch_pdl(k_trace_check, 1, 32, 0, st, tw, off_e + n_rx, p->d_rx_offsets + n_rx, ucap, pcap, meta, status, async);
         RT_COUNT(ctx);
-        k_trace_guard<<<grid_for(ctx, n_rx + 1, 256), 256, 0, st>>>(meta, p->d_rx_offsets, n_rx);
+        launch_pdl(k_trace_guard, grid_for(ctx, n_rx + 1, 256), 256, 0, st, meta, p->d_rx_offsets, n_rx);
         RT_COUNT(ctx);
         TCK(cudaGetLastError());
         p->P = pcap;   // the slots of the record arrays; set to the count below
