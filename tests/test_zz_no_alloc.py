@@ -121,3 +121,43 @@ def test_noalloc_rejects_too_many_receivers():
                                             _p(a), None)
     assert st == 1
     assert b"exceeds" in lib.rt_last_error(ctx.h)
+
+
+def test_noalloc_inside_graph_capture():
+    # A call captured in a CUDA graph after a first eager call on the device
+    # (which looks up the fixed array's address): every replay redoes the whole
+    # computation and must match the eager result.
+    import paper_2311_18558_gb300 as rt
+    ctx = rt.Context(0)
+    lib = ctx.lib
+    rt.set_cfr_tensor_cores(ctx, 1)
+    N = 1024
+    a, tau, offs = scenegen.random_cfr_inputs(2024, 64, 40, empty_every=9)
+    fc, df = 3.5e9, 50e6 / N
+    rng = np.random.default_rng(5)
+    T = rng.uniform(1e-8, 1e-5, (64, N)).astype(np.float32)
+    w = (1.0 / T.mean(axis=1)).astype(np.float32)
+    args = (_dev(offs, torch.int64), _dev(a, torch.complex64), _dev(tau, torch.float64), fc, df, N,
+            _dev(T, torch.float32), _dev(w, torch.float32))
+    L_ref, ga_ref, H_ref = _call(lib, "rt_cfr_power_mse_fused_noalloc", ctx, *args)
+    offs_d, a_d, tau_d, _, _, _, T_d, w_d = args
+    R = offs_d.shape[0] - 1
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    ga = torch.zeros_like(a_d)
+    H = torch.zeros((R, N), dtype=torch.complex64, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ctx._stream()
+        st = lib.rt_cfr_power_mse_fused_noalloc(ctx.h, _p(offs_d), R, _p(a_d), _p(tau_d), fc, df, N, _p(T_d),
+                                                _p(w_d), _p(loss), _p(ga), _p(H))
+        assert st == 0, lib.rt_last_error(ctx.h)
+    for _ in range(2):
+        loss.fill_(float("nan"))
+        ga.fill_(float("nan"))
+        H.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert abs(loss.item() - L_ref) <= 1e-6 * abs(L_ref)
+        np.testing.assert_allclose(ga.cpu().numpy(), ga_ref, rtol=1e-5, atol=1e-12)
+        np.testing.assert_allclose(H.cpu().numpy(), H_ref, rtol=1e-5, atol=1e-12)
+    assert ctx.status_word() == 0
