@@ -423,13 +423,14 @@ __device__ __forceinline__ int closest32(const BvhNode* __restrict__ nodes, cons
 // and in the FP64 test): true on a robust hit; `und` set if no robust hit was
 // found but a marginal one might exist.  A triangle's plane id is the .w of
 // its second vertex record.
+template <int STACK = RT_STACK>
 __device__ __forceinline__ bool any32(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris,
                                      const WRay<float>& r, float tmin, float tmax, int skip0, int skip1, int pl0,
                                      int pl1, int* stack, bool& und, int32_t* status, unsigned& nvis,
                                      unsigned& ntri) {
     bool hit = false;
     const float thi = tmax * 1.00001f;
-    traverse(nodes, r, tmin * 0.5f, thi, stack, status, nvis, [&](int first, int count) {
+    traverse<STACK>(nodes, r, tmin * 0.5f, thi, stack, status, nvis, [&](int first, int count) {
         for (int k = first; k < first + count; ++k) {
             float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
             int id = __float_as_int(p0.w);
@@ -676,13 +677,14 @@ __device__ int closest64(const BvhNode* __restrict__ nodes, const float4* __rest
 
 // Any hit with tmin < t < tmax of an FP64 ray (skipping skip0 and skip1),
 // final decisions in FP64; robust FP32 misses on the rounded ray rf are final.
+template <int STACK = RT_STACK>
 __device__ bool any64_inline(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris,
                              const WRay<double>& r, const WRay<float>& rf, double tmin, double tmax, int skip0,
                              int skip1, int* stack, int32_t* status) {
     bool hit = false;
     const float thi = (float)tmax * 1.00001f;
     unsigned nv = 0;
-    traverse(nodes, rf, (float)tmin * 0.5f, thi, stack, status, nv, [&](int first, int count) {
+    traverse<STACK>(nodes, rf, (float)tmin * 0.5f, thi, stack, status, nv, [&](int first, int count) {
         for (int k = first; k < first + count; ++k) {
             float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
             int id = __float_as_int(p0.w);
@@ -709,6 +711,7 @@ __device__ bool any64_inline(const BvhNode* __restrict__ nodes, const float4* __
 // any64_inline.
 constexpr int VIS_CAND_CAP = 8;
 
+template <int STACK = RT_STACK>
 __device__ bool any64(const BvhNode* __restrict__ nodes, const float4* __restrict__ tris, const WRay<double>& r,
                       const WRay<float>& rf, double tmin, double tmax, int skip0, int skip1, int* stack, int* cand,
                       int32_t* status) {
@@ -717,7 +720,7 @@ __device__ bool any64(const BvhNode* __restrict__ nodes, const float4* __restric
     const float tcut = (float)tmax * 1.001f + 10.0f * (float)tmin;
     int n = 0;
     unsigned nv = 0;
-    traverse(nodes, rf, (float)tmin * 0.5f, thi, stack, status, nv, [&](int first, int count) {
+    traverse<STACK>(nodes, rf, (float)tmin * 0.5f, thi, stack, status, nv, [&](int first, int count) {
         for (int k = first; k < first + count; ++k) {
             float4 p0 = __ldg(tris + 3 * k), p1 = __ldg(tris + 3 * k + 1), p2 = __ldg(tris + 3 * k + 2);
             int id = __float_as_int(p0.w);
@@ -730,7 +733,7 @@ __device__ bool any64(const BvhNode* __restrict__ nodes, const float4* __restric
         }
         return false;
     });
-    if (n > VIS_CAND_CAP) return any64_inline(nodes, tris, r, rf, tmin, tmax, skip0, skip1, stack, status);
+    if (n > VIS_CAND_CAP) return any64_inline<STACK>(nodes, tris, r, rf, tmin, tmax, skip0, skip1, stack, status);
     for (int i = 0; i < n; ++i) {
         const int k = cand[i * stride];
         double Tn, det;
@@ -1766,11 +1769,12 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_backtrace(VisArgs A) {
     }
 }
 
+template <int STACK>
 __global__ void __launch_bounds__(TRACE_THREADS) k_segments(VisArgs A) {
     pdl_entry();
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
-    int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
+    int* cand = smem_stack + STACK * blockDim.x + threadIdx.x;
     unsigned long long n = *A.qcount;
     if (n > A.qcap) n = A.qcap;
     const unsigned long long total = n * (unsigned long long)(A.D + 1);
@@ -1804,7 +1808,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_segments(VisArgs A) {
             unsigned nv = 0, nt = 0;
             const int pl0 = s0 >= 0 ? __float_as_int(__ldg(A.tri_v + 3 * s0 + 1).w) : -1;
             const int pl1 = s1 >= 0 ? __float_as_int(__ldg(A.tri_v + 3 * s1 + 1).w) : -1;
-            hit = any32(A.nodes, A.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, pl0, pl1, stack, und,
+            hit = any32<STACK>(A.nodes, A.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, pl0, pl1, stack, und,
                         A.status, nv, nt);
             c_vis += nv;
             c_tri += nt;
@@ -1831,7 +1835,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_segments(VisArgs A) {
                 rf.d = mk((float)d.x, (float)d.y, (float)d.z);
                 wray_init(rf);
             }
-            hit = any64(A.nodes, A.bvh_tris, rd, rf, A.eps * il, 1.0 - A.eps * il, s0, s1, stack, cand, A.status);
+            hit = any64<STACK>(A.nodes, A.bvh_tris, rd, rf, A.eps * il, 1.0 - A.eps * il, s0, s1, stack, cand, A.status);
         }
         if (hit) atomicAnd(word, ~bit);
     }
@@ -2481,7 +2485,15 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_paths(rt_ct
         VA.seg_d = seg_d;
         launch_pdl(k_backtrace, ctx->num_sms * 8, TRACE_THREADS, 0, st, VA); RT_COUNT(ctx);
         TCK(cudaGetLastError());
-        launch_pdl(k_segments, ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st, VA); RT_COUNT(ctx);
+        // a 32-entry traversal stack when the scene's tree allows it (as k_sbr): less
+        // shared memory per block, so more of L1 holds the BVH
+        if (sc->bvh_depth <= 32)
+            launch_pdl(k_segments<32>, ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS,
+                       (size_t)(32 + VIS_CAND_CAP) * TRACE_THREADS * sizeof(int), st, VA);
+        else
+            launch_pdl(k_segments<RT_STACK>, ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st,
+                       VA);
+        RT_COUNT(ctx);
         mark(ctx, 4);
         TCK(cudaGetLastError());
         int64_t* off_e = nullptr;   // offsets of the emitted paths (before the duplicate rule)
@@ -3002,10 +3014,11 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_backtrace_batch(BatchVis A) {
     }
 }
 
+template <int STACK>
 __global__ void __launch_bounds__(TRACE_THREADS) k_segments_batch(BatchVis A) {
     extern __shared__ int smem_stack[];
     int* stack = smem_stack + threadIdx.x;
-    int* cand = smem_stack + RT_STACK * blockDim.x + threadIdx.x;
+    int* cand = smem_stack + STACK * blockDim.x + threadIdx.x;
     unsigned long long n = *A.qcount;
     if (n > A.qcap) n = A.qcap;
     const unsigned long long total = n * (unsigned long long)(A.D + 1);
@@ -3042,7 +3055,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_segments_batch(BatchVis A) {
             unsigned nv = 0, nt = 0;
             const int pl0 = s0 >= 0 ? __float_as_int(__ldg(d.tri_v + 3 * s0 + 1).w) : -1;
             const int pl1 = s1 >= 0 ? __float_as_int(__ldg(d.tri_v + 3 * s1 + 1).w) : -1;
-            hit = any32(d.nodes, d.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, pl0, pl1, stack, und,
+            hit = any32<STACK>(d.nodes, d.bvh_tris, rf, epsf * o4.w, 1.0f - epsf * o4.w, s0, s1, pl0, pl1, stack, und,
                         A.status, nv, nt);
             c_vis += nv;
             c_tri += nt;
@@ -3067,7 +3080,7 @@ __global__ void __launch_bounds__(TRACE_THREADS) k_segments_batch(BatchVis A) {
                 rf.d = mk((float)dv.x, (float)dv.y, (float)dv.z);
                 wray_init(rf);
             }
-            hit = any64(d.nodes, d.bvh_tris, rd, rf, d.eps * il, 1.0 - d.eps * il, s0, s1, stack, cand, A.status);
+            hit = any64<STACK>(d.nodes, d.bvh_tris, rd, rf, d.eps * il, 1.0 - d.eps * il, s0, s1, stack, cand, A.status);
         }
         if (hit) atomicAnd(word, ~bit);
     }
@@ -3627,7 +3640,11 @@ extern "C" __attribute__((visibility("default"))) rt_status rt_trace_batch(
         k_backtrace_batch<<<ctx->num_sms * 8, TRACE_THREADS, 0, st>>>(VA);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
-        k_segments_batch<<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st>>>(VA);
+        if (depth_max <= 32)
+            k_segments_batch<32><<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS,
+                                   (size_t)(32 + VIS_CAND_CAP) * TRACE_THREADS * sizeof(int), st>>>(VA);
+        else
+            k_segments_batch<RT_STACK><<<ctx->num_sms * ctx->tune_vis_blocks_per_sm, TRACE_THREADS, vis_bytes, st>>>(VA);
         RT_COUNT(ctx);
         BCK(cudaGetLastError());
         mark(ctx, 4);
